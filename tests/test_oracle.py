@@ -1,0 +1,268 @@
+"""Pins for the CPU oracle: nothing here compares the oracle with itself.
+
+* pairwise brute force (tests/brute.py) on tiny random launches;
+* the paper's worked examples (tests/golden/, each with its citation);
+* closed forms worked out by hand for the stride sweep, the planted stencil
+  row stride and the all-threads-one-address kernel;
+* invariants of the race definition (an extra barrier, a removed access or a
+  write turned into a read never adds a witness; relabelling threads inside a
+  block keeps the witness set).
+"""
+import json
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+import workloads
+from workloads import Binding
+import brute
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cmp_brute(w):
+    r = oracle.check(w.text, w.binding)
+    b = brute.check(w.text, w.binding)
+    assert r.witnesses == b["witnesses"]
+    assert r.n_witness == len(b["witnesses"])
+    assert r.n_keys == b["n_keys"] and r.n_oob == b["n_oob"]
+    assert r.n_instances == b["n_instances"]
+    for k in range(3):
+        assert r.n_by_kind[k] == sum(1 for x in b["witnesses"] if x[5] >> k & 1)
+    if b["witnesses"]:
+        assert r.min_w == b["witnesses"][0]
+        kx, ky = b["min_pair"]
+        assert r.min_x[:6] == kx and r.min_y[:6] == ky
+        assert r.min_x[6] == r.min_w[3] and r.min_y[6] == r.min_w[4]
+    else:
+        assert not r.racy
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_oracle_matches_brute_force_tiny(seed):
+    w = workloads.random_tiny(1000 + seed, max_instances=500)
+    _cmp_brute(w)
+
+
+def test_oracle_matches_brute_force_config1():
+    _cmp_brute(workloads.config1(0))
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", sorted(os.listdir(GOLD)))
+def test_paper_worked_examples(name):
+    g = _gold(name)
+    for case in g["cases"]:
+        text = g["descriptor"] if case.get("assert", True) else g["descriptor_without_assert"]
+        b = Binding(tuple(case["grid"]), tuple(case["block"]), tuple(case["params"]))
+        if case["expect"] == "EHOSTCONSTRAINT":
+            with pytest.raises(oracle.OracleError) as ei:
+                oracle.check(text, b)
+            assert ei.value.code == -4
+            continue
+        r = oracle.check(text, b)
+        assert r.racy == (case["expect"] == "racy"), (name, case)
+        if "kind_bits_include" in case:
+            assert any(w[5] & case["kind_bits_include"] for w in r.witnesses)
+        if "witnesses" in case:
+            assert [list(w) for w in r.witnesses] == case["witnesses"]
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_all_threads_one_address():
+    text = "kernel one\narray res global 64\naccess W res ; width 4 ; idx 0\n"
+    # 3 blocks x 40 threads: threads 0..39 span warps 0 and 1
+    r = oracle.check(text, Binding((3, 1, 1), (40, 1, 1), ()))
+    assert r.witnesses == [(0, 0, 0, 0, 0, 7)]
+    # one warp per block: no intra-block (different warp) pair exists
+    r = oracle.check(text, Binding((2, 1, 1), (32, 1, 1), ()))
+    assert r.witnesses == [(0, 0, 0, 0, 0, 5)]
+    # a single thread cannot race with itself
+    r = oracle.check(text, Binding((1, 1, 1), (1, 1, 1), ()))
+    assert not r.racy
+    # shared memory: per-block copies, so no inter-block bit
+    text_s = "kernel one\narray res shared 64\naccess W res ; width 4 ; idx 0\n"
+    r = oracle.check(text_s, Binding((3, 1, 1), (40, 1, 1), ()))
+    assert r.witnesses == [(1, 0, 0, 0, 0, 6)]
+
+
+def test_atomics_and_scopes():
+    base = "kernel at\narray a global 64\narray s shared 64\n"
+    # device-scope atomics never race (Appendix A, trivially race free)
+    t = base + "access A a ; width 4 ; idx 0 ; scope device\n"
+    assert not oracle.check(t, Binding((2, 1, 1), (64, 1, 1), ())).racy
+    # block-scope atomics race across blocks only (insufficient scope)
+    t = base + "access A a ; width 4 ; idx 0 ; scope block\n"
+    assert oracle.check(t, Binding((2, 1, 1), (64, 1, 1), ())).witnesses == [(0, 0, 0, 0, 0, 1)]
+    assert not oracle.check(t, Binding((1, 1, 1), (64, 1, 1), ())).racy
+    # a read against an atomic is a race
+    t = base + "access A a ; width 4 ; idx 0\naccess R a ; width 4 ; idx 0\n"
+    r = oracle.check(t, Binding((1, 1, 1), (64, 1, 1), ()))
+    assert r.witnesses == [(0, 0, 0, 0, 1, 6)]
+    # shared-memory block-scope atomics never race
+    t = base + "access A s ; width 4 ; idx 0 ; scope block\n"
+    assert not oracle.check(t, Binding((4, 1, 1), (64, 1, 1), ())).racy
+
+
+def _stride_closed_form(N, S, bd):
+    """Witnesses of the A array of the strided sweep kernel, derived by hand.
+
+    Thread g (g < N) writes A[g*S + i], i < 8, in interval 0 (access 0) and
+    reads the same elements in interval 1 (access 1).  Element e is touched by
+    the threads g in [ceil((e-7)/S), floor(e/S)] ∩ [0, N).  (0,0) races when at
+    least two threads touch e; (0,1) only across blocks (the reads follow a
+    barrier inside a block); (1,1) never (two loads).
+    """
+    out = []
+    for e in range(0, (N - 1) * S + 8):
+        lo = max(0, -((7 - e) // S) if e >= 7 else 0)
+        lo = max(0, math.ceil((e - 7) / S))
+        hi = min(N - 1, e // S)
+        gs = list(range(lo, hi + 1))
+        if len(gs) < 2:
+            continue
+        blocks = {g // bd for g in gs}
+        m = 0
+        if len(blocks) > 1:
+            m |= 1
+        for b in blocks:
+            ws = [g % bd // 32 for g in gs if g // bd == b]
+            if len(ws) > 1:
+                if len(set(ws)) > 1:
+                    m |= 2
+                if any(ws.count(x) > 1 for x in set(ws)):
+                    m |= 4
+        out.append((0, 0, 4 * e, 0, 0, m))
+        if len(blocks) > 1:
+            out.append((0, 0, 4 * e, 0, 1, 1))
+    return out
+
+
+@pytest.mark.parametrize("N,S,bd", [(96, 1, 64), (100, 3, 64), (64, 4, 32), (70, 8, 64), (40, 32, 64), (130, 2, 128)])
+def test_stride_sweep_closed_form(N, S, bd):
+    text = workloads.config3_kernel_text()
+    grid = (N + bd - 1) // bd
+    r = oracle.check(text, Binding((grid, 1, 1), (bd, 1, 1), (N, S)))
+    want = sorted(_stride_closed_form(N, S, bd))
+    assert r.witnesses == want
+    assert r.racy == (S < 8)
+
+
+@pytest.mark.parametrize("planted", [False, True])
+def test_stencil_planted_row_stride(planted):
+    # the tiled stencil on a 64x64 image with a 4-row window: the planted row
+    # stride R = W - 1 collides (r, W-1) with (r+1, 0), W-1 inter-block pairs
+    w = workloads.config2(0, planted=planted, W=64, H=64, K=4)
+    r = oracle.check(w.text, w.binding)
+    if planted:
+        want = [(0, 2, 4 * (rr + 1) * 63, 15, 15, 1) for rr in range(63)]
+        assert r.witnesses == want
+        assert r.n_by_kind == (63, 0, 0)
+    else:
+        assert not r.racy
+    assert r.n_instances == 4 * 4 * 256 * 4 * 16
+    assert r.n_oob == 0
+
+
+def test_host_classes_reject_bindings():
+    t = workloads.fig1_copy_upp_low(with_assert=True)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.check(t, Binding((1, 1, 1), (4, 4, 1), (4,)))
+    assert ei.value.code == -3  # missing parameter
+    bad_div = "kernel d\nparam Q\narray a global 64\naccess W a ; width 4 ; idx tx / Q\n"
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.check(bad_div, Binding((1, 1, 1), (4, 1, 1), (0,)))
+    assert ei.value.code == -3
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.check("kernel d\narray a global 64\naccess W a ; width 4 ; idx tx*ty\n",
+                     Binding((1, 1, 1), (4, 1, 1), ()))
+    assert ei.value.code == -2
+
+
+def test_c_division_truncates_toward_zero():
+    # idx = (tx - 5) / 2 and (tx - 5) % 3 evaluated for tx < 10 with C semantics
+    t = ("kernel neg\narray a global 4096\n"
+         "access W a ; width 4 ; idx 100 + (tx - 5) / 2\n"
+         "access W a ; width 4 ; idx 200 + (tx - 5) % 3 ; iv 1\n")
+    r = oracle.check(t, Binding((1, 1, 1), (10, 1, 1), ()))
+    # truncation: tx=3,4 -> -1,0; tx=5,6 -> 0,0 ... elements hit by two threads
+    q = [int((x - 5) / 2) for x in range(10)]
+    m = [(x - 5) - 3 * int((x - 5) / 3) for x in range(10)]
+    want = []
+    for v in sorted(set(q)):
+        if q.count(v) > 1:
+            want.append((0, 0, 4 * (100 + v), 0, 0, 4))
+    for v in sorted(set(m)):
+        if m.count(v) > 1:
+            want.append((0, 0, 4 * (200 + v), 1, 1, 4))
+    assert r.witnesses == sorted(want)
+
+
+# ---------------------------------------------------------------- invariants
+
+def _acc_lines(text):
+    return [i for i, l in enumerate(text.splitlines()) if l.startswith("access")]
+
+
+def _set_of(r):
+    return {w[:5]: w[5] for w in r.witnesses}
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_invariant_more_barriers_never_add_races(seed):
+    w = workloads.random_tiny(5000 + seed, max_instances=600)
+    lines = w.text.splitlines()
+    base = _set_of(oracle.check(w.text, w.binding))
+    # split every interval: give access k its own interval k (a barrier between all)
+    for k, li in enumerate(_acc_lines(w.text)):
+        f = [x for x in lines[li].split(" ; ") if not x.startswith("iv ")]
+        f.insert(1, f"iv {k}")
+        lines[li] = " ; ".join(f)
+    split = _set_of(oracle.check("\n".join(lines) + "\n", w.binding))
+    for key, m in split.items():
+        assert key in base and (m & ~base[key]) == 0
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_invariant_removal_and_read_only(seed):
+    w = workloads.random_tiny(7000 + seed, max_instances=600)
+    base = _set_of(oracle.check(w.text, w.binding))
+    lines = w.text.splitlines()
+    acc = _acc_lines(w.text)
+    # writes turned into reads: a subset (witness access ids unchanged)
+    ro = list(lines)
+    for li in acc:
+        ro[li] = re.sub(r"^access [WA] ", "access R ", ro[li])
+        ro[li] = ro[li].replace(" ; scope block", "").replace(" ; scope device", "")
+    assert _set_of(oracle.check("\n".join(ro) + "\n", w.binding)) == {}
+    # drop the last access: witnesses of the remaining pairs only, none new
+    drop = [l for i, l in enumerate(lines) if i != acc[-1]]
+    last = len(acc) - 1
+    sub = _set_of(oracle.check("\n".join(drop) + "\n", w.binding))
+    want = {k: m for k, m in base.items() if k[3] != last and k[4] != last}
+    assert sub == want
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_invariant_thread_relabelling(seed):
+    # tx -> bdx-1-tx is a bijection of the threads of a block; the witness set
+    # is unchanged, the inter-block bit is unchanged, and "some same-block race"
+    # (intra-block or intra-warp) is unchanged
+    w = workloads.random_tiny(9000 + seed, max_instances=600)
+    lines = w.text.splitlines()
+    for li in _acc_lines(w.text):
+        lines[li] = re.sub(r"\btx\b", "(bdx - 1 - tx)", lines[li])
+    a = _set_of(oracle.check(w.text, w.binding))
+    b = _set_of(oracle.check("\n".join(lines) + "\n", w.binding))
+    assert a.keys() == b.keys()
+    for k in a:
+        assert (a[k] & 1) == (b[k] & 1)
+        assert bool(a[k] & 6) == bool(b[k] & 6)

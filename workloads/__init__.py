@@ -1,0 +1,398 @@
+"""Seeded synthetic inputs for the host-guided race check.
+
+This module only *writes inputs*: kernel descriptors in the text format below
+plus the host-side binding (grid, block, parameter values) a launch supplies.
+It holds none of the checking arithmetic, so both the CPU oracle and the GPU
+path can consume what it produces without sharing any of the method.
+
+Descriptor text format (one directive per line, ``#`` starts a comment,
+fields of ``array`` and ``access`` lines are separated by ``;``)::
+
+    kernel NAME
+    param P1 P2 ...                  kernel parameters, bound in this order
+    loop VAR BOUND                   0 <= VAR < BOUND, outermost first, at most 4
+    array NAME global|shared BYTES [; granule G]
+    let NAME = EXPR                  textual macro over everything declared
+    access R|W|A ARRAY ; width W [; iv EXPR] ; idx EXPR [; if COND]* [; scope block|device] [; line N]
+    assert COND                      host-code fact over params and launch dims
+
+Expressions use + - * / % (C semantics: division truncates toward zero),
+unary minus, parentheses, integer literals and the names tx ty tz bx by bz
+(threadIdx/blockIdx), bdx bdy bdz gdx gdy gdz (blockDim/gridDim), loop
+variables, params and lets.  COND is ``EXPR op EXPR`` with op one of
+``< <= > >= ==`` (and ``!=`` in asserts only).  ``idx`` is an element index
+in units of the access width (C pointer arithmetic on a typed pointer), ``iv``
+is the barrier-interval id (affine in loop variables), R/W/A = read, write,
+atomic.
+
+The workload shapes follow the five benchmark configurations of this project
+(plain 4x64 check, tiled 64x64x(16x16) stencil, 64-tuple host sweep,
+10,000-kernel corpus, ranker corpus) and the paper's Fig. 1-5 listings.
+Seeds are ``0x4847524400 + config*10000 + item``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+MASK64 = (1 << 64) - 1
+SEED_BASE = 0x4847524400
+
+
+def seed_for(config: int, item: int) -> int:
+    return SEED_BASE + config * 10000 + item
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as published by Vigna."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def below(self, n: int) -> int:
+        """Uniform integer in [0, n) (rejection-free multiply-high)."""
+        return (self.next() * n) >> 64
+
+    def range(self, lo: int, hi: int) -> int:
+        """Uniform integer in [lo, hi] inclusive."""
+        return lo + self.below(hi - lo + 1)
+
+    def uniform(self) -> float:
+        return (self.next() >> 11) * (1.0 / (1 << 53))
+
+    def choice(self, seq):
+        return seq[self.below(len(seq))]
+
+
+@dataclass
+class Binding:
+    grid: tuple = (1, 1, 1)
+    block: tuple = (1, 1, 1)
+    params: tuple = ()
+
+    def instances_per_access(self, loop_bounds) -> int:
+        n = math.prod(self.grid) * math.prod(self.block)
+        for b in loop_bounds:
+            n *= max(0, b)
+        return n
+
+
+@dataclass
+class Workload:
+    name: str
+    text: str
+    binding: Binding
+    meta: dict = field(default_factory=dict)
+
+
+# --------------------------------------------------------------------------
+# helpers to write descriptor text
+
+class _Writer:
+    def __init__(self, name):
+        self.lines = [f"kernel {name}"]
+
+    def add(self, line):
+        self.lines.append(line)
+
+    def access(self, kind, array, width, idx, iv=None, guards=(), scope=None, line=None):
+        f = [f"access {kind} {array}", f"width {width}"]
+        if iv is not None:
+            f.append(f"iv {iv}")
+        f.append(f"idx {idx}")
+        for g in guards:
+            f.append(f"if {g}")
+        if scope is not None:
+            f.append(f"scope {scope}")
+        if line is not None:
+            f.append(f"line {line}")
+        self.lines.append(" ; ".join(f))
+
+    def text(self):
+        return "\n".join(self.lines) + "\n"
+
+
+def _lin(a, v):
+    """Render coefficient*variable with sign handling."""
+    if a == 0:
+        return ""
+    if a == 1:
+        return f" + {v}"
+    if a == -1:
+        return f" - {v}"
+    if a < 0:
+        return f" - {-a}*{v}"
+    return f" + {a}*{v}"
+
+
+# --------------------------------------------------------------------------
+# Config 1: plain check of one small kernel.
+#   1D grid of 4 blocks x 64 threads, S = 256 int32 shared, G = 4096 int32
+#   global, 6 accesses idx = a*tx + b*bx + c*i + d*N + e with a,b,c,d drawn
+#   in [-4, 4], N = 64 bound by the host, loop i < 8, barrier intervals
+#   {0,1,2}.  The offset e makes the smallest index of the access zero.  The
+#   last access is the planted race: thread 0 of every block writes one
+#   G element (the shape of the paper's reduceFinal, Fig. 2).
+
+def config1(item: int = 0) -> Workload:
+    rng = SplitMix64(seed_for(1, item))
+    N, TB, GB, ITER = 64, 64, 4, 8
+    w = _Writer(f"plain_c1_{item}")
+    w.add("param N")
+    w.add("loop i 8")
+    w.add("array S shared 1024")
+    w.add("array G global 16384")
+    for a_id in range(5):
+        arr = "S" if rng.below(2) == 0 else "G"
+        kind = "R" if rng.below(2) == 0 else "W"
+        a, b, c, d = (rng.range(-4, 4) for _ in range(4))
+        lo = min(0, a * (TB - 1)) + min(0, b * (GB - 1)) + min(0, c * (ITER - 1)) + d * N
+        e = -lo
+        expr = "0" + _lin(a, "tx") + _lin(b, "bx") + _lin(c, "i") + _lin(d, "N")
+        expr += f" + {e}" if e >= 0 else f" - {-e}"
+        w.access(kind, arr, 4, expr, iv=rng.below(3), line=10 + a_id)
+    d = rng.range(-4, 4)
+    e = -d * N + rng.below(64)
+    w.access("W", "G", 4, f"{d}*N + {e}", iv=rng.below(3), guards=["tx == 0"], line=20)
+    return Workload(f"c1_{item}", w.text(), Binding((GB, 1, 1), (TB, 1, 1), (N,)),
+                    {"config": 1, "loop_bounds": [ITER], "n_access": 6})
+
+
+# --------------------------------------------------------------------------
+# Config 2: tiled-stencil shape.
+#   2D grid (W/16) x (H/16) of 16x16 threads, an 18x18 fp32 shared tile with
+#   a one-cell halo, In/Out W x H fp32 global arrays, loop k < 32 (a 32-row
+#   running window of In, rows and columns wrapping with mod H / mod W), 16
+#   accesses over 4 barrier intervals.  The planted off-by-one race is an Out
+#   row stride R = W - 1: element (r, W-1) collides with (r+1, 0), which lie in
+#   blocks bx = W/16 - 1 and bx = 0, giving W - 1 inter-block write-write
+#   witnesses.  Whether item `item` is planted is decided by its seed.
+
+def config2(item: int = 0, planted=None, W: int = 1024, H: int = 1024, K: int = 32) -> Workload:
+    rng = SplitMix64(seed_for(2, item))
+    bit = rng.next() & 1
+    if planted is None:
+        planted = bool(bit)
+    R = W - 1 if planted else W
+    w = _Writer(f"stencil2d_window_{item}")
+    w.add("param W H R")
+    w.add(f"loop k {K}")
+    w.add("array S shared 1296")
+    w.add("array In global 4*W*H")
+    w.add("array Out global 4*W*H")
+    w.add("let lin = ty*16 + tx")
+    w.add("let l2 = lin + 256")
+    w.add("assert gdx*16 == W")
+    w.add("assert gdy*16 == H")
+    w.add("assert bdx == 16")
+    w.add("assert bdy == 16")
+    # iv 0: stage the halo tile (324 cells, two per thread) from a k-shifted row
+    w.access("R", "In", 4, "((by*16 - 1 + lin/18 + k + H) % H)*W + (bx*16 - 1 + lin%18 + W) % W", iv=0, line=11)
+    w.access("W", "S", 4, "lin", iv=0, line=11)
+    w.access("R", "In", 4, "((by*16 - 1 + l2/18 + k + H) % H)*W + (bx*16 - 1 + l2%18 + W) % W", iv=0,
+             guards=["l2 < 324"], line=12)
+    w.access("W", "S", 4, "l2", iv=0, guards=["l2 < 324"], line=12)
+    # iv 1: 3x3 neighbourhood reads of the tile
+    for dy in range(3):
+        for dx in range(3):
+            w.access("R", "S", 4, f"(ty + {dy})*18 + tx + {dx}", iv=1, line=15)
+    # iv 2: centre update on the last window row
+    w.access("W", "S", 4, "(ty + 1)*18 + tx + 1", iv=2, guards=[f"k == {K - 1}"], line=18)
+    # iv 3: read back the centre and store the output pixel
+    w.access("R", "S", 4, "(ty + 1)*18 + tx + 1", iv=3, guards=["k == 0"], line=21)
+    w.access("W", "Out", 4, "(by*16 + ty)*R + bx*16 + tx", iv=3, guards=["k == 0"], line=21)
+    return Workload(f"c2_{item}", w.text(), Binding((W // 16, H // 16, 1), (16, 16, 1), (W, H, R)),
+                    {"config": 2, "planted": planted, "loop_bounds": [K], "n_access": 16,
+                     "expected_witnesses": (W - 1) if planted else 0})
+
+
+# --------------------------------------------------------------------------
+# Config 3: host-guided parameter sweep of one 12-access strided kernel.
+#   Thread g = bx*bdx + tx (guard g < N) writes A[g*STRIDE + i] for i < 8 and
+#   reads it back; STRIDE < 8 makes neighbouring threads overlap (racy),
+#   STRIDE >= 8 keeps them disjoint (clean).  The other arrays follow
+#   race-free patterns.  64 tuples: N = 2^8..2^20 x STRIDE in {1,2,3,4,32},
+#   N-major, the first 64; blockDim drawn from {64,...,1024}, grid = ceil(N/bd).
+
+C3_STRIDES = (1, 2, 3, 4, 32)
+
+
+def config3_kernel_text() -> str:
+    w = _Writer("strided_sweep")
+    w.add("param N STRIDE")
+    w.add("loop i 8")
+    w.add("array A global 4*(N*STRIDE + 8)")
+    w.add("array B global 32*N")
+    w.add("array C global 32*N")
+    w.add("array T shared 4*bdx")
+    w.add("let g = bx*bdx + tx")
+    w.add("assert N > 0")
+    w.add("assert STRIDE > 0")
+    w.add("assert gdx*bdx >= N")
+    w.add("assert (gdx - 1)*bdx < N")
+    w.access("W", "A", 4, "g*STRIDE + i", iv=0, guards=["g < N"], line=5)        # 0
+    w.access("R", "A", 4, "g*STRIDE + i", iv=1, guards=["g < N"], line=6)        # 1
+    w.access("R", "B", 4, "g*8 + i", iv=0, guards=["g < N"], line=7)             # 2
+    w.access("R", "B", 4, "((g + 1) % N)*8 + i", iv=0, guards=["g < N"], line=8)  # 3
+    w.access("W", "C", 4, "g*8 + i", iv=0, guards=["g < N"], line=9)             # 4
+    w.access("R", "C", 4, "g*8 + 7 - i", iv=2, guards=["g < N"], line=10)        # 5
+    w.access("W", "T", 4, "tx", iv=0, line=11)                                    # 6
+    w.access("R", "T", 4, "(tx + 1) % bdx", iv=1, line=12)                        # 7
+    w.access("R", "T", 4, "(tx + bdx - 1) % bdx", iv=1, line=13)                  # 8
+    w.access("W", "T", 4, "tx", iv=2, guards=["i == 7"], line=14)                 # 9
+    w.access("A", "C", 4, "g*8", iv=3, guards=["g < N", "i == 0"], scope="device", line=15)  # 10
+    w.access("R", "B", 16, "g*2 + i/4", iv=1, guards=["g < N"], line=16)         # 11
+    return w.text()
+
+
+def config3(n_items: int = 64):
+    text = config3_kernel_text()
+    items = []
+    for e in range(8, 21):
+        for s in C3_STRIDES:
+            if len(items) == n_items:
+                break
+            rng = SplitMix64(seed_for(3, len(items)))
+            N = 1 << e
+            bd = 64 * (1 << rng.below(5))  # 64..1024
+            grid = (N + bd - 1) // bd
+            items.append(Workload(f"c3_{len(items)}", text, Binding((grid, 1, 1), (bd, 1, 1), (N, s)),
+                                  {"config": 3, "N": N, "stride": s, "loop_bounds": [8], "n_access": 12}))
+    return items
+
+
+# --------------------------------------------------------------------------
+# Paper listings (Fig. 1-5) as descriptors, used as fixtures in the tests.
+
+def fig1_copy_upp_low(with_assert=True) -> str:
+    w = _Writer("copyUppLowKernel")
+    w.add("param rows cols")
+    w.add("array A global 4*rows*cols")
+    w.add("let i = bx*bdx + tx")
+    w.add("let j = by*bdy + ty")
+    if with_assert:
+        w.add("assert rows == cols")
+    w.access("R", "A", 4, "i*cols + j", guards=["j > i", "j < rows"], line=7)
+    w.access("W", "A", 4, "j*cols + i", guards=["j > i", "j < rows"], line=7)
+    return w.text()
+
+
+def fig2_reduce_final() -> str:
+    w = _Writer("reduceFinal")
+    w.add("param n")
+    w.add("array res global 4*n")
+    w.access("W", "res", 4, "0", guards=["tx == 0"], line=5)
+    return w.text()
+
+
+def fig3_tone_mapping(with_assert=True) -> str:
+    w = _Writer("toneMapping")
+    w.add("param width channels height")
+    w.add("array output global 4*width*channels*height")
+    w.add("let x = bx*bdx + tx")
+    w.add("let y = by*bdy + ty")
+    if with_assert:
+        # grid.x = hWidth/16 and width = hWidth come from the same host variable
+        w.add("assert gdx == width / 16")
+    w.access("W", "output", 4, "width*channels*y + x*channels", line=7)
+    return w.text()
+
+
+def fig4_lud_internal() -> str:
+    w = _Writer("ludInternal")
+    w.add("param dim offset BS")
+    w.add("array m global 4*dim*dim")
+    w.add("let rid = offset + (by + 1)*BS")
+    w.add("let cid = offset + (bx + 1)*BS")
+    w.add("assert offset >= 0")
+    w.access("W", "m", 4, "(rid + ty)*dim + cid + tx", line=7)
+    return w.text()
+
+
+def fig5_shift(with_assert=True) -> str:
+    w = _Writer("shift")
+    w.add("param rowSize width height")
+    w.add("array matrix global 4*width*height")
+    w.add("array tex global 4*width*height")
+    w.add("let xid = bx*bdx + tx")
+    w.add("let yid = by*bdy + ty")
+    if with_assert:
+        # rowSize is the pitch cudaMallocPitch returned for this allocation
+        w.add("assert rowSize > 0")
+    w.access("R", "tex", 4, "yid*width + xid", line=6)
+    w.access("W", "matrix", 4, "yid*(rowSize/4) + xid", line=6)
+    return w.text()
+
+
+# --------------------------------------------------------------------------
+# Tiny random kernels (a few hundred to a few thousand instances) used to pin
+# the oracle against pairwise brute force.
+
+def random_tiny(seed: int, max_instances: int = 2048) -> Workload:
+    rng = SplitMix64(seed)
+    ndim_g = rng.range(1, 2)
+    ndim_b = rng.range(1, 2)
+    grid = [1, 1, 1]
+    block = [1, 1, 1]
+    for d in range(ndim_g):
+        grid[d] = rng.range(1, 3)
+    for d in range(ndim_b):
+        block[d] = rng.choice([1, 2, 3, 5, 8, 16, 33, 40])
+    nthreads = math.prod(block) * math.prod(grid)
+    nloops = rng.range(0, 2)
+    bounds = [rng.range(1, 3) for _ in range(nloops)]
+    nacc = rng.range(1, 5)
+    while nthreads * math.prod(bounds) * nacc > max_instances and nacc > 1:
+        nacc -= 1
+    while nthreads * math.prod(bounds) * nacc > max_instances and bounds:
+        bounds.pop()
+    while nthreads * math.prod(bounds) * nacc > max_instances and block[0] > 1:
+        block[0] = max(1, block[0] // 2)
+    w = _Writer(f"tiny_{seed & 0xffff}")
+    P = rng.range(1, 9)
+    Q = rng.range(1, 5)
+    w.add("param P Q")
+    lv = ["i", "j"][:len(bounds)]
+    for v, b in zip(lv, bounds):
+        w.add(f"loop {v} {b}")
+    w.add(f"array S shared {4 * rng.range(4, 40)} ; granule 4")
+    w.add(f"array G global {4 * rng.range(4, 64)}")
+    if rng.below(2):
+        w.add("array H global 64")
+    names = ["tx", "ty", "bx", "by"] + lv + ["P", "Q"]
+    for a_id in range(nacc):
+        arr = rng.choice(["S", "G", "G"])
+        r = rng.below(10)
+        kind = "R" if r < 4 else ("W" if r < 8 else "A")
+        expr = str(rng.range(0, 3))
+        for v in names:
+            if rng.below(3) == 0:
+                expr += _lin(rng.range(-3, 3), v)
+        if rng.below(4) == 0:
+            expr = f"({expr}) / {rng.range(1, 3)}"
+        if rng.below(5) == 0:
+            expr = f"({expr}) % {rng.choice(['P', 'Q', '3', '5'])}"
+        width = rng.choice([4, 4, 4, 8, 16]) if arr != "S" else 4
+        guards = []
+        if rng.below(3) == 0:
+            v = rng.choice(names[:4] + lv)
+            guards.append(f"{v} {rng.choice(['<', '<=', '>', '>=', '=='])} {rng.range(0, 3)}")
+        iv = None
+        if rng.below(2):
+            iv = str(rng.range(0, 2))
+            if lv and rng.below(3) == 0:
+                iv = f"{iv} + {rng.choice(lv)}"
+        scope = None
+        if kind == "A":
+            scope = rng.choice(["block", "device"])
+        w.access(kind, arr, width, expr, iv=iv, guards=guards, scope=scope, line=a_id + 1)
+    params = (P, Q)
+    return Workload(f"tiny_{seed}", w.text(), Binding(tuple(grid), tuple(block), params),
+                    {"loop_bounds": bounds, "n_access": nacc})
