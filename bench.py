@@ -1,0 +1,271 @@
+#!/usr/bin/env python
+"""Benchmark of the exhaustive host-guided race check on the tiled-stencil
+workload: a 64x64 grid of 16x16 threads, 16 accesses, loop k < 32 =
+536,870,912 access instances (1024x1024 fp32 In/Out, 18x18 shared tile).
+
+One step = the whole hot path on one batch: expansion into keys, the radix
+sort passes, the conflict scan and the witness canonicalisation, enqueued
+through the library's C ABI (hgrd_check_enqueue) with the compiled program
+resident; `e2e` times the public synchronous call (hgrd_check) with its
+host<->device copies.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hgrd|reference]
+
+--impl reference times the CPU oracle (the slow definition the GPU path is
+checked against) on a bounded sample of the same workload on the host cores.
+Under torchrun each rank checks its own seeded stencil (independent replicas,
+no data-path collective); rank 0 prints the aggregate.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "access instances checked/s"
+UNIT = "instances/s"
+WORKLOAD = "tiled-stencil 64x64 blocks x 16x16 threads, loop k<32, 16 accesses (536,870,912 instances)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6400.0), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def run_reference(args, rank):
+    """CPU oracle on a bounded sample of the same workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    oracle.build()
+    side = args.ref_side
+    w = workloads.config2(0, planted=True, W=side, H=side, K=32)
+    for _ in range(args.warmup if args.ref_warmup else 0):
+        oracle.check(w.text, w.binding)
+    t = []
+    n = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.check(w.text, w.binding)
+        t.append(time.perf_counter() - t0)
+        n += r.n_instances
+    total = sum(t)
+    value = n / total
+    sample = (f"same stencil kernel on a {side}x{side} image ({side // 16}x{side // 16} blocks, "
+              f"{r.n_instances:,} instances per step), whole oracle per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_side": side},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(side):
+    import oracle
+    import workloads
+    oracle.build()
+    w = workloads.config2(0, planted=True, W=side, H=side, K=32)
+    t0 = time.perf_counter()
+    r = oracle.check(w.text, w.binding)
+    dt = time.perf_counter() - t0
+    return {"value": r.n_instances / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same stencil kernel on a {side}x{side} image ({r.n_instances:,} instances), "
+                      f"one whole oracle run, {dt:.1f} s"}
+
+
+# algorithmic bytes per key of each stage (the roofline's numerator)
+STAGE_BYTES = {"expand_write": 8, "candidates": 8}
+for _p in range(8):
+    STAGE_BYTES[f"sort_pass{_p}"] = 16
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hgrd", choices=["hgrd", "reference"])
+    ap.add_argument("--ref-side", type=int, default=256)
+    ap.add_argument("--ref-warmup", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=1024)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import workloads
+    import paper_2604_02106_b300 as hg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = workloads.config2(rank, planted=True, W=args.side, H=args.side)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    ws = k.workspace()
+    s = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        k.enqueue(ws, stream=s)
+    res = k.collect(ws, cap=1 << 16, stream=s)
+    assert res.n_witness == w.meta["expected_witnesses"], "verdict differs from the closed form"
+    launches = hg.stats()["kernel_launches"]
+    n_inst = res.n_instances
+    n_keys = res.n_keys
+
+    # ---- device-timed steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            k.enqueue(ws, stream=s)
+        e1.record(s)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    res2 = k.collect(ws, cap=1 << 16, stream=s)
+    assert res2.witnesses == res.witnesses
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    ms_step = ms / args.steps
+    value = world * n_inst * args.steps / (ms / 1000.0)
+
+    # ---- per-stage times (CUDA events on the launch stream, same steps again)
+    stages = {}
+    for _ in range(args.steps):
+        k.enqueue(ws, stream=s, flags=hg.PROFILE)
+        for name, t in hg.last_profile():
+            stages.setdefault(name, []).append(t)
+    stage_ms = {n: sum(v) / len(v) for n, v in stages.items()}
+    hbm_peak, peak_kind = _peaks()
+    hbm_stages = {n: t for n, t in stage_ms.items() if n in STAGE_BYTES}
+    dom = max(hbm_stages, key=hbm_stages.get)
+    achieved = STAGE_BYTES[dom] * n_keys / (hbm_stages[dom] / 1000.0) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2604_02106_b300", "csrc", "kernels.cu"), "rb").read()
+        import hashlib
+        if tr.get("kernels_cu_sha1") == hashlib.sha1(src).hexdigest() and dom in tr.get("per_launch_bytes", {}):
+            traffic = tr["per_launch_bytes"][dom]
+    except Exception:
+        traffic = None
+
+    # ---- end to end through the public synchronous call
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_e2e = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = k.check(cap=1 << 16, stream=s)
+        t_e2e.append(time.perf_counter() - t0)
+    st = hg.stats()
+    e2e_s = sum(t_e2e)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e = {"value": world * n_inst * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(st["h2d_bytes"]), "d2h_bytes_per_step": int(st["d2h_bytes"]),
+           "ms_per_step": 1000 * e2e_s / args.steps}
+    assert r.witnesses == res.witnesses
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "instances": n_inst, "keys": n_keys,
+                           "witnesses": res.n_witness, "sort_passes": hg.stats()["sort_passes"],
+                           "l2": f"keys {8 * n_keys / 1e9:.2f} GB per buffer > 126 MB L2; no flush needed",
+                           "parallelism": f"replicas{world}"},
+                "e2e": e2e,
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                             "traffic": traffic,
+                             "bytes_per_key": STAGE_BYTES[dom], "keys_per_launch": n_keys},
+                "stages_ms": {n: round(t, 4) for n, t in stage_ms.items()},
+                "clocks": clk.summary(),
+                "gpu_launches": int(launches * args.steps)}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.ref_side)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

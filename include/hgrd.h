@@ -1,0 +1,186 @@
+/*
+ * hgrd.h — C ABI of libhgrd.so, the B300 (sm_103a) exhaustive host-guided
+ * GPU data-race check.
+ *
+ * Model (the paper's race definition, made concrete by the host binding):
+ *   A kernel descriptor lists a kernel's memory accesses as quasi-affine
+ *   index expressions over threadIdx, blockIdx, loop counters and kernel
+ *   parameters, each with guards, a read/write/atomic flag, an access width
+ *   and a barrier-interval id.  A binding supplies every parameter and the
+ *   launch dimensions, as the launching host code does (Sec. 4 and Sec. 5.1,
+ *   host classes (1)-(5)).  Two instances race when they come from different
+ *   threads, touch a common byte granule, at least one writes, they are not
+ *   both atomic with enough scope, and they are unordered: in shared memory
+ *   only inside one block and one barrier interval, in global memory also
+ *   across blocks in any interval, because block barriers do not order blocks
+ *   (Sec. 2 "Data races on GPUs", Sec. 6.1, Table 2, Appendix A).
+ *
+ * Pipeline behind hgrd_check (all on one GPU, stream ordered): instance
+ * expansion into 64-bit keys, a stable onesweep LSD radix sort on the key's
+ * (array, granule, interval) bits, a segmented conflict scan over runs of
+ * equal (array, granule), and witness compaction + canonicalisation.
+ *
+ * Conventions for every entry point:
+ *   * Return value: HGRD_OK (0), HGRD_ETRUNCATED (1: more witnesses than the
+ *     caller's capacity; the verdict's counts stay exact and the first `cap`
+ *     canonical witnesses are written), or a negative error.  No entry point
+ *     aborts or exits; hgrd_last_error() returns a thread-local message about
+ *     the last failure on the calling thread.
+ *   * Ownership: descriptors are created and freed by the library.  Device
+ *     workspace and CUDA streams are owned by the caller (the Python binding
+ *     allocates them with PyTorch).  Host output arrays are owned by the caller.
+ *   * Pointers named d_* are device pointers; all others are host pointers.
+ *   * The library keeps no device state between calls.
+ */
+#ifndef HGRD_H
+#define HGRD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HGRD_OK = 0,
+  HGRD_ETRUNCATED = 1,
+  HGRD_EINVAL = -1,          /* null pointer, bad option, descriptor not bound */
+  HGRD_EPARSE = -2,          /* descriptor text malformed or not quasi-affine */
+  HGRD_EBIND = -3,           /* parameter count, launch dims, divisor <= 0, negative size */
+  HGRD_EHOSTCONSTRAINT = -4, /* a host `assert` of the descriptor is false for the binding */
+  HGRD_EOVERFLOW = -5,       /* an index expression can leave int64, or the key exceeds 64 bits */
+  HGRD_ENOMEM = -6,          /* workspace smaller than hgrd_workspace_size, or raw witness cap hit */
+  HGRD_EDEVICE = -7,         /* a CUDA call failed */
+  HGRD_ETIMEOUT = -8,        /* a bounded device-side wait gave up */
+  HGRD_EUNSUPPORTED = -9     /* descriptor exceeds a fixed limit of this build */
+};
+
+enum { HGRD_SPACE_GLOBAL = 0, HGRD_SPACE_SHARED = 1 };
+/* kind_mask bits: race type of a witness (Sec. 2, Table 2) */
+enum { HGRD_INTER_BLOCK = 1, HGRD_INTRA_BLOCK = 2, HGRD_INTRA_WARP = 4 };
+
+typedef struct hgrd_desc hgrd_desc; /* opaque, library owned */
+
+/* Host binding (Sec. 5.1, classes (1)-(5)): launch dims and parameter values
+ * in the descriptor's `param` order. */
+typedef struct {
+  int32_t grid[3], block[3];
+  uint32_t nparams;
+  const int64_t* params;
+} hgrd_binding;
+
+/* One racy (access pair, location) — the paper's report unit (Sec. 5, Sec. 6
+ * component 5): array, byte address of the granule (the in-block offset for
+ * shared memory, merged over blocks), the two access ids (acc_lo <= acc_hi,
+ * descriptor order), and the race types seen there. */
+typedef struct {
+  uint8_t space, array, acc_lo, acc_hi, kind_mask, pad[3];
+  uint64_t byte_addr;
+} hgrd_witness;
+
+/* One concrete access instance: linear block, linear thread (tx + ty*bdx +
+ * tz*bdx*bdy), loop counters (outermost first), access id. */
+typedef struct {
+  uint32_t lin_block, lin_thread;
+  uint32_t iter[4];
+  uint8_t access, pad[3];
+} hgrd_inst;
+
+/* Verdict.  Witnesses are ordered by (space, array, byte_addr, acc_lo,
+ * acc_hi); min_w is the first.  min_x/min_y is the lexicographically smallest
+ * racing instance pair realising min_w (x of acc_lo, y of acc_hi, keys
+ * (lin_block, lin_thread, iter...)), valid when pair_found is 1.
+ * n_instances counts every (block, thread, loop vector, access) tuple before
+ * guards; n_keys the granule keys of live in-bounds instances; n_oob the live
+ * instances outside their array. */
+typedef struct {
+  int32_t racy, pair_found;
+  uint64_t n_witness, n_by_kind[3], n_instances, n_keys, n_oob;
+  hgrd_witness min_w;
+  hgrd_inst min_x, min_y;
+} hgrd_verdict;
+
+/* Options.  Zero-initialised means defaults. */
+typedef struct {
+  uint64_t max_raw_witness; /* device buffer for per-run witnesses before merging; 0 = 1<<22 */
+  uint32_t pair_cap;        /* instances gathered to find min_x/min_y; 0 = 1<<20 */
+  uint32_t flags;           /* HGRD_NO_PAIR: skip the canonical instance pair;
+                               HGRD_PROFILE: time every pipeline stage with CUDA events */
+} hgrd_check_opts;
+enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2 };
+
+/* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
+ * stream around the stage's kernels. */
+typedef struct {
+  char name[24];
+  float ms;
+} hgrd_stage_time;
+
+/* Per-call counters of the last hgrd_check* on the calling thread. */
+typedef struct {
+  uint64_t kernel_launches; /* kernels of this library enqueued by the call */
+  uint64_t n_candidates;    /* runs the exact conflict scan examined */
+  uint64_t n_raw_witness;   /* per-run witnesses before the cross-block merge */
+  uint32_t sort_passes;     /* radix passes over the instance keys */
+  uint32_t int64_path;      /* 1 when index arithmetic needed 64-bit integers */
+  uint64_t h2d_bytes;       /* host->device bytes the call copied (the compiled program) */
+  uint64_t d2h_bytes;       /* device->host bytes the call copied (counters, witnesses, pair search) */
+} hgrd_stats;
+
+/* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,
+ * documented in the project's workload module).  Static checks: names, at
+ * most 32 accesses, 32 arrays, 4 loops, quasi-affine expressions (a product
+ * needs one uniform factor, divisors are uniform), intervals free of thread
+ * and block ids, uniform loop bounds, sizes and asserts.  `text` need not be
+ * NUL terminated.  On success *out owns a new descriptor. */
+int hgrd_load_desc(const char* text, size_t len, hgrd_desc** out);
+
+/* Bind host values (Sec. 5.1, classes (1)-(5); Sec. 6.3): checks the
+ * parameter count, 1 <= dims, <= 1024 threads per block, every divisor > 0,
+ * array sizes >= 0 and every `assert` (HGRD_EHOSTCONSTRAINT when one fails),
+ * folds the values into per-access coefficient tables, bounds every
+ * expression over the instance box (HGRD_EOVERFLOW when int64 can
+ * overflow) and plans the key layout.  Rebinding replaces the old binding. */
+int hgrd_bind_host_params(hgrd_desc* d, const hgrd_binding* b);
+
+/* Device workspace bytes hgrd_check needs for the bound descriptor.  The
+ * workspace must be 256-byte aligned. */
+int hgrd_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes);
+
+/* Exhaustive check of the bound descriptor on `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream).  Synchronous on return: writes up to `cap`
+ * canonical witnesses to host_out (may be NULL when cap is 0) and the verdict
+ * to *v.  The workspace contents are scratch. */
+int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* cuda_stream,
+               hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v);
+
+/* Same pipeline, enqueue only: no host synchronisation and no host copies.
+ * The verdict (without the instance pair) and the canonical witnesses stay in
+ * the workspace; hgrd_check_collect reads them after the stream reaches
+ * this point.  Used to time the device path alone. */
+int hgrd_check_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* cuda_stream);
+int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                       hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v);
+
+/* Counters of the last check on this thread. */
+int hgrd_last_stats(hgrd_stats* s);
+
+/* Stage times of the last check enqueued with HGRD_PROFILE on this thread;
+ * waits for the stream to reach the last stage.  Writes up to `cap` entries
+ * and the number of stages to *n. */
+int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n);
+
+void hgrd_free_desc(hgrd_desc* d);
+const char* hgrd_last_error(void);
+
+/* Self-test hook for the division-by-constant method used by the kernels
+ * (Granlund & Montgomery 1994, Thm. 4.2, with C truncation for negative
+ * numerators): q = n / d, r = n % d for d > 0; wide selects the 64-bit form.
+ * Host-side computation of exactly the arithmetic the device performs. */
+int hgrd_debug_divmod(int64_t n, int64_t d, int wide, int64_t* q, int64_t* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGRD_H */

@@ -1,0 +1,241 @@
+"""Python binding of libhgrd.so, the B300 exhaustive host-guided race check.
+
+Argument marshalling only: every step of the check runs in the library's CUDA
+kernels.  PyTorch provides the device workspace and the stream.  When the
+compiled library is missing this module raises on use; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhgrd.so")
+
+OK, ETRUNCATED = 0, 1
+ERRORS = {1: "ETRUNCATED", -1: "EINVAL", -2: "EPARSE", -3: "EBIND", -4: "EHOSTCONSTRAINT", -5: "EOVERFLOW",
+          -6: "ENOMEM", -7: "EDEVICE", -8: "ETIMEOUT", -9: "EUNSUPPORTED"}
+NO_PAIR = 1
+PROFILE = 2
+
+# symbols include/hgrd.h declares
+EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
+           "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile", "hgrd_free_desc", "hgrd_last_error",
+           "hgrd_debug_divmod"]
+
+
+class HgrdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Binding(C.Structure):
+    _fields_ = [("grid", C.c_int32 * 3), ("block", C.c_int32 * 3), ("nparams", C.c_uint32),
+                ("params", C.POINTER(C.c_int64))]
+
+
+class Witness(C.Structure):
+    _fields_ = [("space", C.c_uint8), ("array", C.c_uint8), ("acc_lo", C.c_uint8), ("acc_hi", C.c_uint8),
+                ("kind_mask", C.c_uint8), ("pad", C.c_uint8 * 3), ("byte_addr", C.c_uint64)]
+
+
+class Inst(C.Structure):
+    _fields_ = [("lin_block", C.c_uint32), ("lin_thread", C.c_uint32), ("iter", C.c_uint32 * 4),
+                ("access", C.c_uint8), ("pad", C.c_uint8 * 3)]
+
+
+class Verdict(C.Structure):
+    _fields_ = [("racy", C.c_int32), ("pair_found", C.c_int32), ("n_witness", C.c_uint64),
+                ("n_by_kind", C.c_uint64 * 3), ("n_instances", C.c_uint64), ("n_keys", C.c_uint64),
+                ("n_oob", C.c_uint64), ("min_w", Witness), ("min_x", Inst), ("min_y", Inst)]
+
+
+class CheckOpts(C.Structure):
+    _fields_ = [("max_raw_witness", C.c_uint64), ("pair_cap", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class StageTime(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("ms", C.c_float)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("n_candidates", C.c_uint64), ("n_raw_witness", C.c_uint64),
+                ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
+                ("d2h_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhgrd.so (built in-tree by __graft_entry__.build / _build.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhgrd.so is not built ({LIB_PATH}); run paper_2604_02106_b300._build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, sz, u64 = C.c_void_p, C.c_size_t, C.c_uint64
+        L.hgrd_load_desc.argtypes = [C.c_char_p, sz, C.POINTER(vp)]
+        L.hgrd_bind_host_params.argtypes = [vp, C.POINTER(Binding)]
+        L.hgrd_workspace_size.argtypes = [vp, C.POINTER(CheckOpts), C.POINTER(sz)]
+        L.hgrd_check.argtypes = [vp, C.POINTER(CheckOpts), vp, sz, vp, C.POINTER(Witness), u64, C.POINTER(Verdict)]
+        L.hgrd_check_enqueue.argtypes = [vp, C.POINTER(CheckOpts), vp, sz, vp]
+        L.hgrd_check_collect.argtypes = [vp, C.POINTER(CheckOpts), vp, sz, vp, C.POINTER(Witness), u64,
+                                         C.POINTER(Verdict)]
+        L.hgrd_last_stats.argtypes = [C.POINTER(Stats)]
+        L.hgrd_last_profile.argtypes = [C.POINTER(StageTime), C.c_uint32, C.POINTER(C.c_uint32)]
+        L.hgrd_free_desc.argtypes = [vp]
+        L.hgrd_free_desc.restype = None
+        L.hgrd_last_error.restype = C.c_char_p
+        L.hgrd_debug_divmod.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        for f in ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check",
+                  "hgrd_check_enqueue", "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile",
+                  "hgrd_debug_divmod"]:
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _raise(rc):
+    if rc < 0:
+        raise HgrdError(rc, lib().hgrd_last_error().decode(errors="replace"))
+
+
+def _opts(max_raw_witness=0, pair_cap=0, flags=0):
+    return CheckOpts(max_raw_witness, pair_cap, flags)
+
+
+@dataclass
+class Result:
+    racy: bool
+    n_witness: int
+    n_by_kind: tuple
+    n_instances: int
+    n_keys: int
+    n_oob: int
+    witnesses: list        # (space, array, byte_addr, acc_lo, acc_hi, kind_mask), canonical order
+    min_w: tuple | None
+    min_x: tuple | None    # (lin_block, lin_thread, i0, i1, i2, i3, access)
+    min_y: tuple | None
+    truncated: bool = False
+
+
+def _wt(w):
+    return (w.space, w.array, w.byte_addr, w.acc_lo, w.acc_hi, w.kind_mask)
+
+
+def _it(i):
+    return (i.lin_block, i.lin_thread, *i.iter, i.access)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Kernel:
+    """A kernel descriptor (library owned) plus its current host binding."""
+
+    def __init__(self, text: str):
+        h = C.c_void_p()
+        b = text.encode()
+        _raise(lib().hgrd_load_desc(b, len(b), C.byref(h)))
+        self._h = h
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hgrd_free_desc(h)
+            self._h = None
+
+    def bind(self, grid, block, params):
+        params = tuple(int(p) for p in params)
+        arr = (C.c_int64 * max(1, len(params)))(*params)
+        b = Binding((C.c_int32 * 3)(*grid), (C.c_int32 * 3)(*block), len(params), arr)
+        _raise(lib().hgrd_bind_host_params(self._h, C.byref(b)))
+        return self
+
+    def workspace_size(self, **opts) -> int:
+        n = C.c_size_t()
+        o = _opts(**opts)
+        _raise(lib().hgrd_workspace_size(self._h, C.byref(o), C.byref(n)))
+        return n.value
+
+    def workspace(self, device="cuda", **opts):
+        """A device workspace sized for the current binding (reused when large enough)."""
+        import torch
+        need = self.workspace_size(**opts)
+        if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
+            self._ws = None
+            self._ws = torch.empty(need, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def check(self, cap: int = 1 << 16, stream=None, workspace=None, **opts) -> Result:
+        """Exhaustive check; synchronous.  Retries once with a larger raw-witness buffer."""
+        for attempt in range(2):
+            ws = workspace if workspace is not None else self.workspace(**opts)
+            out = (Witness * max(1, cap))()
+            v = Verdict()
+            o = _opts(**opts)
+            rc = lib().hgrd_check(self._h, C.byref(o), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
+                                  out, cap, C.byref(v))
+            if rc == -6 and workspace is None and attempt == 0:
+                st = stats()
+                if st["n_raw_witness"] > opts.get("max_raw_witness", 0):
+                    opts = dict(opts, max_raw_witness=int(st["n_raw_witness"] * 1.25) + 1024)
+                    continue
+            _raise(rc)
+            n = min(cap, v.n_witness)
+            return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
+                          [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None,
+                          _it(v.min_x) if v.pair_found else None, _it(v.min_y) if v.pair_found else None,
+                          rc == ETRUNCATED)
+
+    def enqueue(self, workspace, stream=None, **opts):
+        """Enqueue the device pipeline only (no host synchronisation)."""
+        o = _opts(**opts)
+        _raise(lib().hgrd_check_enqueue(self._h, C.byref(o), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                        _stream_ptr(stream)))
+
+    def collect(self, workspace, cap: int = 1 << 16, stream=None, **opts) -> Result:
+        out = (Witness * max(1, cap))()
+        v = Verdict()
+        o = _opts(**opts)
+        rc = lib().hgrd_check_collect(self._h, C.byref(o), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                      _stream_ptr(stream), out, cap, C.byref(v))
+        _raise(rc)
+        n = min(cap, v.n_witness)
+        return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
+                      [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
+                      rc == ETRUNCATED)
+
+
+def stats() -> dict:
+    s = Stats()
+    _raise(lib().hgrd_last_stats(C.byref(s)))
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def last_profile() -> list:
+    """[(stage, ms)] of the last check enqueued with flags=PROFILE on this thread."""
+    buf = (StageTime * 64)()
+    n = C.c_uint32()
+    _raise(lib().hgrd_last_profile(buf, 64, C.byref(n)))
+    return [(buf[k].name.decode(), buf[k].ms) for k in range(min(64, n.value))]
+
+
+def check(text: str, binding, cap: int = 1 << 16, **opts) -> Result:
+    """Parse, bind and check in one call (binding has .grid, .block, .params)."""
+    k = Kernel(text).bind(binding.grid, binding.block, binding.params)
+    return k.check(cap=cap, **opts)
+
+
+def debug_divmod(n: int, d: int, wide: bool):
+    q, r = C.c_int64(), C.c_int64()
+    _raise(lib().hgrd_debug_divmod(n, d, int(wide), C.byref(q), C.byref(r)))
+    return q.value, r.value

@@ -1,0 +1,376 @@
+// hgrd_check and friends: workspace layout and the stream-ordered pipeline
+//   expand(count) -> scan -> expand(write) -> onesweep passes ->
+//   candidates -> exact -> witness sort -> merge -> kind counts
+// All sizes the kernels need at run time are read from device counters, so
+// nothing between the first and the last kernel waits on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hgrd_host.h"
+#include "kernels.cuh"
+
+namespace hgrd {
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
+      pairs, total;
+  uint64_t raw_cap, pair_cap, status_words;
+};
+
+Layout layout(const Bound& B, const hgrd_check_opts* o) {
+  Layout L{};
+  const DProg& P = B.prog;
+  const uint64_t nk = std::max<uint64_t>(B.nkeys_max, 1);
+  // defaults scale with the problem: per-run witnesses rarely exceed twice
+  // the keys, and the instances on one granule never exceed the keys
+  L.raw_cap = (o && o->max_raw_witness) ? o->max_raw_witness
+                                        : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 12, 2 * nk));
+  L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
+  const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
+  const uint64_t scan_n = std::max(nunits, L.raw_cap);
+  const uint64_t tiles = std::max((nk + RS_TILE - 1) / RS_TILE, (L.raw_cap + RS_TILE - 1) / RS_TILE);
+  L.status_words = tiles * RS_RADIX;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  L.counters = take(C_WORDS * 8);
+  L.prog = take(sizeof(DProg));
+  L.unit_cnt = take(nunits * 8);
+  L.unit_off = take(nunits * 8);
+  L.partials = take(((scan_n + SCAN_TILE - 1) / SCAN_TILE + 1) * 8);
+  L.hist = take(MAX_PASSES * 256 * 8);
+  L.gbase = take(MAX_PASSES * 256 * 8);
+  L.status = take(L.status_words * 8);
+  L.keysA = take(nk * 8);
+  L.keysB = take(nk * 8);
+  L.raw = take(L.raw_cap * 8);
+  L.raw2 = take(L.raw_cap * 8);
+  L.flags = take(L.raw_cap * 8);
+  L.excl = take(L.raw_cap * 8);
+  L.pairs = take((size_t)L.pair_cap * sizeof(PairRec));
+  L.total = off;
+  return L;
+}
+
+int nsm_of_current_device() {
+  static thread_local int cached_dev = -1, cached_n = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != cached_dev) {
+    cudaDeviceGetAttribute(&cached_n, cudaDevAttrMultiProcessorCount, dev);
+    cached_dev = dev;
+  }
+  return cached_n > 0 ? cached_n : 1;
+}
+
+// stage timing (HGRD_PROFILE): one event before the first stage and one after each
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::string> names;
+  void reset(bool enable, cudaStream_t st) {
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    names.clear();
+    on = enable;
+    s = st;
+    if (on) mark("");
+  }
+  void mark(const char* name) {
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    names.push_back(name);
+  }
+};
+thread_local Prof g_prof;
+
+#define CK(x)                                                                               \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess) return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+int prechecks(const hgrd_desc* d, void* d_ws, size_t ws_bytes, const hgrd_check_opts* o, Layout* Lo) {
+  if (!d) return fail(HGRD_EINVAL, "null descriptor");
+  if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  *Lo = layout(*d->bound, o);
+  if (!d_ws) return fail(HGRD_EINVAL, "null workspace");
+  if (((uintptr_t)d_ws & 255) != 0) return fail(HGRD_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < Lo->total)
+    return fail(HGRD_ENOMEM, "workspace too small: need " + std::to_string(Lo->total) + " bytes");
+  return HGRD_OK;
+}
+
+int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  Layout W;
+  int rc = prechecks(d, d_ws, ws_bytes, o, &W);
+  if (rc) return rc;
+  const Bound& B = *d->bound;
+  const DProg& HP = B.prog;
+  char* ws = (char*)d_ws;
+  auto U = [&](size_t off) { return (uint64_t*)(ws + off); };
+  uint64_t* cnt = U(W.counters);
+  DProg* dprog = (DProg*)(ws + W.prog);
+  g_stats = hgrd_stats{};
+  g_stats.int64_path = B.wide;
+  g_stats.sort_passes = (uint32_t)B.sort_passes;
+  Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
+  g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
+
+  CK(cudaMemsetAsync(cnt, 0, C_WORDS * 8, s));
+  CK(cudaMemsetAsync(U(W.hist), 0, MAX_PASSES * 256 * 8, s));
+  CK(cudaMemsetAsync(U(W.status), 0, W.status_words * 8, s));
+  bool any = false;
+  for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
+  if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
+  CK(cudaMemcpyAsync(dprog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
+  g_stats.h2d_bytes += sizeof(DProg);
+  g_prof.mark("setup");
+
+  const int P = B.sort_passes;
+  uint64_t* keysA = U(W.keysA);
+  uint64_t* keysB = U(W.keysB);
+  uint64_t* nkeys = cnt + C_NKEYS;
+  CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), P, cnt, nullptr, nullptr, 0));
+  g_prof.mark("expand_count");
+  CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+  g_prof.mark("unit_scan");
+  CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
+  g_prof.mark("expand_write");
+  CK(launch_hist_scan(L, U(W.hist), U(W.gbase), P));
+  uint64_t* in = keysA;
+  uint64_t* out = keysB;
+  for (int p = 0; p < P; p++) {
+    CK(launch_onesweep(L, in, out, nkeys, B.nkeys_max, HP.PB + 8 * p, U(W.gbase) + p * 256, U(W.status),
+                       cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR));
+    std::swap(in, out);
+    static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
+                                "sort_pass4", "sort_pass5", "sort_pass6", "sort_pass7"};
+    g_prof.mark(pn[p & 7]);
+  }
+  // `in` holds the sorted keys; `out` is free for the candidate list
+  const uint64_t cand_cap = std::max<uint64_t>(B.nkeys_max / 2, 1);
+  CK(launch_candidates(L, in, nkeys, dprog, out, cand_cap, cnt));
+  g_prof.mark("candidates");
+  CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt));
+  g_prof.mark("exact");
+  // canonical order of the witnesses: radix sort of the packed words
+  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
+  uint64_t* nraw = cnt + C_NRAW;
+  uint64_t* whist = U(W.hist) + 8 * 256;
+  uint64_t* wgb = U(W.gbase) + 8 * 256;
+  CK(launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist));
+  CK(launch_hist_scan(L, whist, wgb, WP));
+  uint64_t* win = U(W.raw);
+  uint64_t* wout = U(W.raw2);
+  for (int p = 0; p < WP; p++) {
+    CK(launch_onesweep(L, win, wout, nraw, W.raw_cap, WIT_SORT_LO + 8 * p, wgb + p * 256, U(W.status),
+                       cnt + C_TICKET0 + P + p, (uint32_t)(P + p + 1), cnt + C_ERR));
+    std::swap(win, wout);
+  }
+  // win: sorted raw witnesses; wout receives the merged set
+  CK(cudaMemsetAsync(wout, 0, W.raw_cap * 8, s));
+  CK(launch_heads(L, win, nraw, W.raw_cap, U(W.flags)));
+  CK(launch_scan(L, U(W.flags), U(W.excl), nraw, W.raw_cap, U(W.partials), cnt + C_NUNIQ));
+  CK(launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout));
+  CK(launch_kind_counts(L, wout, cnt));
+  g_prof.mark("witness_merge");
+  return HGRD_OK;
+}
+
+// the buffer holding the merged witnesses after enqueue
+uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
+  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
+  (void)d;
+  return (uint64_t*)(ws + ((WP % 2 == 0) ? W.raw2 : W.raw));
+}
+
+struct Inst {
+  uint32_t blk, thr;
+  uint32_t it[4];
+  int acc;
+  int64_t iv;
+};
+bool key_less(const Inst& a, const Inst& b) {
+  return std::tie(a.blk, a.thr, a.it[0], a.it[1], a.it[2], a.it[3]) <
+         std::tie(b.blk, b.thr, b.it[0], b.it[1], b.it[2], b.it[3]);
+}
+
+int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
+            hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, bool want_pair) {
+  Layout W;
+  int rc = prechecks(d, d_ws, ws_bytes, o, &W);
+  if (rc) return rc;
+  if (!v) return fail(HGRD_EINVAL, "null verdict");
+  if (cap && !host_out) return fail(HGRD_EINVAL, "null witness buffer with nonzero capacity");
+  const Bound& B = *d->bound;
+  const DProg& HP = B.prog;
+  char* ws = (char*)d_ws;
+  uint64_t cnt[C_WORDS];
+  CK(cudaMemcpyAsync(cnt, ws + W.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  g_stats.d2h_bytes += sizeof(cnt);
+  CK(cudaStreamSynchronize(s));
+  if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
+  g_stats.n_candidates = cnt[C_NCAND];
+  g_stats.n_raw_witness = cnt[C_NRAW];
+  if (cnt[C_NCAND] > std::max<uint64_t>(B.nkeys_max / 2, 1))
+    return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
+  if (cnt[C_NRAW] > W.raw_cap)
+    return fail(HGRD_ENOMEM, "raw witness buffer too small: need " + std::to_string(cnt[C_NRAW]) +
+                                 " (hgrd_check_opts.max_raw_witness)");
+  memset(v, 0, sizeof(*v));
+  v->n_instances = B.n_instances;
+  v->n_keys = cnt[C_NKEYS];
+  v->n_oob = cnt[C_NOOB];
+  v->n_witness = cnt[C_NUNIQ];
+  v->n_by_kind[0] = cnt[C_KIND0];
+  v->n_by_kind[1] = cnt[C_KIND1];
+  v->n_by_kind[2] = cnt[C_KIND2];
+  v->racy = v->n_witness > 0;
+  const uint64_t* duniq = uniq_buffer(d, W, ws);
+  const uint64_t ncopy = std::min<uint64_t>(std::max<uint64_t>(cap, 1), v->n_witness);
+  std::vector<uint64_t> hw(ncopy);
+  if (ncopy) {
+    CK(cudaMemcpyAsync(hw.data(), duniq, ncopy * 8, cudaMemcpyDeviceToHost, s));
+    g_stats.d2h_bytes += ncopy * 8;
+    CK(cudaStreamSynchronize(s));
+  }
+  auto unpack = [&](uint64_t w) {
+    hgrd_witness x{};
+    x.space = (uint8_t)((w >> 58) & 1);
+    x.array = (uint8_t)((w >> 53) & 31);
+    const uint64_t gran = (w >> 13) & ((1ull << 40) - 1);
+    x.acc_lo = (uint8_t)((w >> 8) & 31);
+    x.acc_hi = (uint8_t)((w >> 3) & 31);
+    x.kind_mask = (uint8_t)(w & 7);
+    x.byte_addr = gran * (uint64_t)B.array_granule[x.array];
+    return x;
+  };
+  for (uint64_t k = 0; k < std::min<uint64_t>(cap, v->n_witness); k++) host_out[k] = unpack(hw[k]);
+  if (v->racy) v->min_w = unpack(hw[0]);
+
+  if (v->racy && want_pair && !(o && (o->flags & HGRD_NO_PAIR))) {
+    // canonical instance pair: gather the instances of acc_lo / acc_hi on the
+    // minimal witness's granule, then take the smallest racing (x, y)
+    Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
+    PairRec* pr = (PairRec*)(ws + W.pairs);
+    uint64_t zero = 0;
+    CK(cudaMemcpyAsync(ws + W.counters + 8 * C_NPAIR, &zero, 8, cudaMemcpyHostToDevice, s));
+    CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, nullptr, nullptr, nullptr, 0,
+                     (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
+    uint64_t np = 0;
+    CK(cudaMemcpyAsync(&np, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
+    g_stats.h2d_bytes += 8;
+    g_stats.d2h_bytes += 8;
+    CK(cudaStreamSynchronize(s));
+    if (np <= W.pair_cap) {
+      std::vector<PairRec> recs(np);
+      if (np) {
+        CK(cudaMemcpyAsync(recs.data(), pr, np * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+        g_stats.d2h_bytes += np * sizeof(PairRec);
+        CK(cudaStreamSynchronize(s));
+      }
+      std::vector<Inst> X, Y;
+      for (auto& r : recs) {
+        Inst in{r.blk, r.thr, {r.it[0], r.it[1], r.it[2], r.it[3]}, r.acc, r.iv};
+        if (r.acc == v->min_w.acc_lo) X.push_back(in);
+        if (r.acc == v->min_w.acc_hi) Y.push_back(in);
+      }
+      std::sort(X.begin(), X.end(), key_less);
+      std::sort(Y.begin(), Y.end(), key_less);
+      const int lo = v->min_w.acc_lo, hi = v->min_w.acc_hi;
+      const uint32_t allow = ((HP.einter[lo] >> hi) & 1u) | (((HP.eintra[lo] >> hi) & 1u) ? 6u : 0u);
+      const bool shared = v->min_w.space == HGRD_SPACE_SHARED;
+      bool found = false;
+      for (size_t i = 0; i < X.size() && !found; i++)
+        for (size_t j = 0; j < Y.size(); j++) {
+          const Inst &x = X[i], &y = Y[j];
+          if (lo == hi && !key_less(x, y)) continue;
+          uint32_t kind = 0;
+          if (x.blk == y.blk && x.thr == y.thr) kind = 0;
+          else if (x.blk != y.blk) kind = shared ? 0 : 1;
+          else if (x.iv != y.iv) kind = 0;
+          else kind = (x.thr / 32 == y.thr / 32) ? 4 : 2;
+          if (kind & allow) {
+            auto put = [](hgrd_inst& o2, const Inst& s2) {
+              o2.lin_block = s2.blk;
+              o2.lin_thread = s2.thr;
+              for (int l = 0; l < 4; l++) o2.iter[l] = s2.it[l];
+              o2.access = (uint8_t)s2.acc;
+            };
+            put(v->min_x, x);
+            put(v->min_y, y);
+            found = true;
+            break;
+          }
+        }
+      v->pair_found = found;
+    }
+  }
+  return (host_out && v->n_witness > cap) ? HGRD_ETRUNCATED : HGRD_OK;
+}
+
+}  // namespace
+}  // namespace hgrd
+
+using namespace hgrd;
+
+extern "C" {
+
+int hgrd_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes) {
+  if (!d || !bytes) return fail(HGRD_EINVAL, "null argument");
+  if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound");
+  *bytes = layout(*d->bound, o).total;
+  return HGRD_OK;
+}
+
+int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n) {
+  if (!n || (cap && !out)) return fail(HGRD_EINVAL, "null argument");
+  Prof& p = g_prof;
+  const uint32_t stages = p.ev.empty() ? 0 : (uint32_t)p.ev.size() - 1;
+  *n = stages;
+  if (!stages) return HGRD_OK;
+  if (cudaEventSynchronize(p.ev.back()) != cudaSuccess) return fail(HGRD_EDEVICE, "event synchronize failed");
+  for (uint32_t k = 0; k < stages && k < cap; k++) {
+    memset(out[k].name, 0, sizeof(out[k].name));
+    strncpy(out[k].name, p.names[k + 1].c_str(), sizeof(out[k].name) - 1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p.ev[k], p.ev[k + 1]);
+    out[k].ms = ms;
+  }
+  return HGRD_OK;
+}
+
+int hgrd_check_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream) {
+  return enqueue(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
+                       hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
+  return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, false);
+}
+
+int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
+               hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
+  int rc = enqueue(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
+  if (rc) return rc;
+  return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, true);
+}
+
+}  // extern "C"

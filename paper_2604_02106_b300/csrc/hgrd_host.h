@@ -1,0 +1,66 @@
+// Host-side library state: parsed descriptors and their bindings.
+#pragma once
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hgrd_internal.h"
+
+struct AstNode {
+  char op;  // n num, v instance var (val = slot), d launch dim (val 0..5), p param (val = index), ~ neg, + - * / %
+  int64_t val = 0;
+  int a = -1, b = -1;
+  bool varies = false;  // depends on thread, block or loop ids
+  bool thread = false;  // depends on thread or block ids
+};
+struct CondDecl {
+  int lhs = -1, rhs = -1;
+  char op = '<';  // < L(<=) > G(>=) E(==) N(!=)
+};
+struct LoopDecl {
+  std::string name;
+  int bound = -1;
+};
+struct ArrayDecl {
+  std::string name;
+  int space = HGRD_SPACE_GLOBAL;
+  int bytes = -1;
+  int64_t granule = 0;
+};
+struct AccessDecl {
+  int kind = 0;  // 0 read, 1 write, 2 atomic
+  int arr = -1;
+  int64_t width = 0;
+  int scope = 1;  // 0 block, 1 device (atomics)
+  int idx = -1, iv = -1;
+  int line = 0;
+  std::vector<CondDecl> guards;
+};
+
+namespace hgrd {
+// Result of hgrd_bind_host_params: the compiled program and host facts.
+struct Bound {
+  DProg prog;
+  std::vector<int64_t> array_bytes, array_granule;
+  uint64_t n_instances = 0;
+  uint64_t nkeys_max = 0;
+  int sort_passes = 0;
+  bool wide = false;
+};
+extern thread_local std::string g_err;
+extern thread_local hgrd_stats g_stats;
+int fail(int code, const std::string& msg);
+}  // namespace hgrd
+
+struct hgrd_desc {
+  std::string name;
+  std::vector<AstNode> ast;
+  std::vector<std::string> params;
+  std::vector<LoopDecl> loops;
+  std::vector<ArrayDecl> arrays;
+  std::vector<AccessDecl> acc;
+  std::vector<CondDecl> asserts;
+  std::map<std::string, int> lets;
+  std::unique_ptr<hgrd::Bound> bound;
+};

@@ -1,0 +1,142 @@
+// Library-internal definitions shared by the host compiler (desc.cpp) and the
+// kernels (*.cu).  Nothing here is part of the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/hgrd.h"
+
+#if defined(__CUDACC__)
+#define HGRD_HD __host__ __device__ __forceinline__
+#else
+#define HGRD_HD inline
+#endif
+
+namespace hgrd {
+
+constexpr int MAXACC = 32;
+constexpr int MAXARR = 32;
+constexpr int MAXLOOP = 4;
+constexpr int NVAR = 10;  // slots 0..5: tx ty tz bx by bz; 6..9: loop counters
+constexpr int MAXTERM = 768;
+constexpr int MAXOP = 192;
+constexpr int MAXGUARD = 128;
+constexpr int MAXSLOT = 128;
+
+// Division by a positive constant d of a numerator whose magnitude is below
+// 2^N (N = 31 on the 32-bit path, 62 on the 64-bit path): Granlund &
+// Montgomery, "Division by invariant integers using multiplication" (PLDI
+// 1994), Theorem 4.2 with l = ceil(log2 d), m = floor(2^(N+l)/d) + 1,
+// q = floor(|n| * m / 2^(N+l)); the sign follows C truncation.
+struct Magic {
+  uint64_t m;
+  int32_t shift;  // N + l
+  int32_t pad;
+};
+
+HGRD_HD uint64_t magic_udiv(uint64_t n, const Magic& g) {
+#if defined(__CUDA_ARCH__)
+  uint64_t lo = n * g.m, hi = __umul64hi(n, g.m);
+#else
+  unsigned __int128 p = (unsigned __int128)n * g.m;
+  uint64_t lo = (uint64_t)p, hi = (uint64_t)(p >> 64);
+#endif
+  if (g.shift >= 64) return hi >> (g.shift - 64);
+  return (hi << (64 - g.shift)) | (lo >> g.shift);
+}
+
+// 32-bit path: |n| < 2^31 and m <= 2^32 + 1, so |n| * m < 2^64 fits a
+// single 64-bit product.
+HGRD_HD int32_t magic_div32(int32_t n, const Magic& g) {
+  uint64_t a = (uint64_t)(n < 0 ? -(int64_t)n : (int64_t)n);
+  int32_t q = (int32_t)((a * g.m) >> g.shift);
+  return n < 0 ? -q : q;
+}
+HGRD_HD int64_t magic_div64(int64_t n, const Magic& g) {
+  uint64_t a = (uint64_t)(n < 0 ? -n : n);
+  int64_t q = (int64_t)magic_udiv(a, g);
+  return n < 0 ? -q : q;
+}
+
+struct DTerm {
+  int32_t slot, pad;
+  int64_t coef;
+};
+struct DLin {
+  int32_t first, n;  // terms [first, first + n)
+  int64_t c0;
+};
+enum { OP_LIN = 0, OP_DIV = 1, OP_MOD = 2 };
+struct DOp {
+  int32_t kind, dst;
+  DLin lin;
+  int64_t d;
+  Magic mg;
+};
+struct DAcc {
+  DLin idx, iv;
+  int32_t gfirst, ng;  // guards: each DLin must be >= 0
+  int32_t G;           // granule keys per instance (width / granule)
+  int32_t arr;         // descriptor array id
+  int64_t maxidx;      // in bounds iff 0 <= idx <= maxidx
+  uint64_t cbase;      // first cell code of the array
+  uint64_t ngran;      // granules of one copy of the array
+  int32_t shared, dead;
+  int32_t bounds_free, pad;
+};
+
+// Everything the kernels need about one bound descriptor.  Lives in the
+// device workspace; all lanes read it with uniform addresses.
+struct DProg {
+  int32_t grid[3], block[3];
+  int32_t nthr, wpb;  // threads and warps per block
+  int64_t nblk, nunits;
+  int32_t nloop, nacc;
+  int32_t ub[MAXLOOP];
+  int64_t nit;  // loop vectors per thread
+  int32_t wide, nfix, niter, nslot;
+  int32_t nterm, nguard, pad0, pad1;
+  // key layout: key = ((cell << IVB | iv - ivmin) << PB) | lin_b << (TB+AB) | lin_t << AB | access
+  int32_t AB, TB, BB, IVB, PB, RB;
+  int64_t ivmin;
+  uint64_t shared_cell_base;  // cell codes at or above this belong to shared arrays
+  uint32_t wmask;             // accesses that write (W or A)
+  int32_t nlay;               // arrays in layout order (global first)
+  uint32_t einter[MAXACC], eintra[MAXACC];
+  uint64_t lay_cbase[MAXARR + 1];
+  uint64_t lay_ngran[MAXARR];
+  int32_t lay_arr[MAXARR], lay_shared[MAXARR];
+  DOp ops[MAXOP];  // [0, nfix): once per (block, warp); [nfix, nfix+niter): per loop vector
+  DAcc acc[MAXACC];
+  DLin guard[MAXGUARD];
+  DTerm term[MAXTERM];
+};
+
+// Raw / canonical witness packed into 64 bits so the same radix sort orders
+// them: space(1) array(5) granule(40) acc_lo(5) acc_hi(5) kind(3), low to high
+// significance reversed (kind in the low bits).
+HGRD_HD uint64_t pack_witness(uint32_t space, uint32_t arr, uint64_t gran, uint32_t lo, uint32_t hi, uint32_t kind) {
+  return ((uint64_t)space << 58) | ((uint64_t)arr << 53) | (gran << 13) | ((uint64_t)lo << 8) | ((uint64_t)hi << 3) |
+         kind;
+}
+constexpr int WIT_SORT_LO = 3;   // lowest sorted bit (the kind mask is merged, not sorted)
+constexpr int WIT_SORT_HI = 59;  // one past the highest used bit
+
+// Device counters block at the start of the workspace (uint64 words).
+enum {
+  C_NKEYS = 0,
+  C_NOOB,
+  C_NCAND,
+  C_NRAW,
+  C_ERR,
+  C_NUNIQ,
+  C_KIND0,
+  C_KIND1,
+  C_KIND2,
+  C_NPAIR,
+  C_TICKET0 = 16,  // one tile ticket per sort pass (up to 32 passes)
+  C_WORDS = 64
+};
+enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
+
+}  // namespace hgrd

@@ -1,0 +1,806 @@
+// Kernels of the exhaustive race check (sm_103a).
+//
+//  expand     every (block, thread, loop vector, access) instance of the user
+//             kernel -> 64-bit keys (Table 1's addr / tb / id made concrete).
+//             One CUDA warp evaluates one simulated warp of the user kernel,
+//             lane = simulated thread, so each (loop vector, access) step is a
+//             warp-uniform instruction stream and live keys compact with a
+//             ballot into coalesced stores.
+//  onesweep   stable LSD radix sort, 8-bit digits: per-warp shared-memory
+//             digit histograms ranked with __match_any_sync, decoupled
+//             look-back across tiles with a bounded spin.
+//  candidates phase A of the conflict scan: one streaming read of the sorted
+//             keys flags the runs of equal (array, granule) that can hold a
+//             race (a writer plus two threads in one interval, or a writer plus
+//             two blocks in global memory).
+//  exact      phase B: per flagged run, lane = access id keeps min/max of
+//             block, warp and thread per barrier interval and block; pairs
+//             are decided with ballots and __match_any_sync (Table 2).
+//  witness    merge per-run witnesses into the canonical set.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace hgrd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t shr64(uint64_t x, int s) { return s >= 64 ? 0 : x >> s; }
+__device__ __forceinline__ uint64_t lowbits(uint64_t x, int n) { return n >= 64 ? x : (x & ((1ull << n) - 1)); }
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T divq(T n, const Magic& g);
+template <>
+__device__ __forceinline__ int32_t divq<int32_t>(int32_t n, const Magic& g) {
+  return magic_div32(n, g);
+}
+template <>
+__device__ __forceinline__ int64_t divq<int64_t>(int64_t n, const Magic& g) {
+  return magic_div64(n, g);
+}
+
+// c0 + sum(coef * slot) over the lane's column of the warp's slot file
+template <typename T>
+__device__ __forceinline__ T lin_eval(const DProg* __restrict__ P, const DLin& L, const T* sl, int lane) {
+  T v = (T)L.c0;
+  for (int t = 0; t < L.n; ++t) {
+    const DTerm tm = P->term[L.first + t];
+    v += (T)tm.coef * sl[tm.slot * 32 + lane];
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void run_ops(const DProg* __restrict__ P, int first, int count, T* sl, int lane) {
+  for (int k = first; k < first + count; ++k) {
+    const DOp op = P->ops[k];
+    T v = lin_eval<T>(P, op.lin, sl, lane);
+    if (op.kind == OP_DIV) {
+      v = divq<T>(v, op.mg);
+    } else if (op.kind == OP_MOD) {
+      v = v - divq<T>(v, op.mg) * (T)op.d;
+    }
+    sl[op.dst * 32 + lane] = v;
+  }
+}
+
+// ------------------------------------------------------------------ expand
+template <typename T, int MODE>
+__global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __restrict__ P, uint64_t* __restrict__ unit_cnt,
+                                                             const uint64_t* __restrict__ unit_off,
+                                                             uint64_t* __restrict__ keys, uint64_t* __restrict__ hist,
+                                                             int npass, uint64_t* __restrict__ counters,
+                                                             const uint64_t* __restrict__ uniq,
+                                                             PairRec* __restrict__ pairs, uint64_t pair_cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int WPC = EXP_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nslot = P->nslot;
+  T* sl = reinterpret_cast<T*>(smem) + (size_t)warp * nslot * 32;
+  uint32_t* shist = reinterpret_cast<uint32_t*>(smem + (size_t)WPC * nslot * 32 * sizeof(T));
+  if (MODE == 0) {
+    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS) shist[i] = 0;
+    __syncthreads();
+  }
+  // the minimal witness for the pair search
+  uint32_t t_arr = 0, t_lo = 0, t_hi = 0;
+  uint64_t t_gran = 0;
+  if (MODE == 2) {
+    if (counters[C_NUNIQ] == 0) return;
+    const uint64_t w0 = uniq[0];
+    t_arr = (uint32_t)(w0 >> 53) & 31;
+    t_gran = (w0 >> 13) & ((1ull << 40) - 1);
+    t_lo = (uint32_t)(w0 >> 8) & 31;
+    t_hi = (uint32_t)(w0 >> 3) & 31;
+  }
+  const int nthr = P->nthr, wpb = P->wpb, nacc = P->nacc, nloop = P->nloop;
+  const int bdx = P->block[0], bdy = P->block[1];
+  const int64_t gdx = P->grid[0], gdy = P->grid[1];
+  const int64_t nit = P->nit, nunits = P->nunits;
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB;
+  const int64_t ivmin = P->ivmin;
+  uint64_t oob = 0;
+  for (int l = 0; l < MAXLOOP; ++l) sl[(6 + l) * 32 + lane] = 0;
+  for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
+    const int64_t b = u / wpb;
+    const int lt = (int)(u - b * wpb) * 32 + lane;
+    const bool act = lt < nthr;
+    sl[0 * 32 + lane] = (T)(lt % bdx);
+    sl[1 * 32 + lane] = (T)((lt / bdx) % bdy);
+    sl[2 * 32 + lane] = (T)(lt / (bdx * bdy));
+    sl[3 * 32 + lane] = (T)(b % gdx);
+    sl[4 * 32 + lane] = (T)((b / gdx) % gdy);
+    sl[5 * 32 + lane] = (T)(b / (gdx * gdy));
+    run_ops<T>(P, 0, P->nfix, sl, lane);
+    const uint64_t payload = ((uint64_t)b << (TB + AB)) | ((uint64_t)lt << AB);
+    uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
+    int32_t ic[MAXLOOP] = {0, 0, 0, 0};
+    for (int64_t it = 0; it < nit; ++it) {
+      if (it > 0) {
+        int l = nloop - 1;
+        while (l >= 0) {
+          if (++ic[l] < P->ub[l]) break;
+          ic[l] = 0;
+          --l;
+        }
+      }
+      for (int l = 0; l < nloop; ++l) sl[(6 + l) * 32 + lane] = (T)ic[l];
+      run_ops<T>(P, P->nfix, P->niter, sl, lane);
+      for (int a = 0; a < nacc; ++a) {
+        const DAcc& A = P->acc[a];
+        if (A.dead) continue;
+        if (MODE == 2 && (uint32_t)a != t_lo && (uint32_t)a != t_hi) continue;
+        bool live = act;
+        const int ng = A.ng, gf = A.gfirst;
+        for (int g = 0; g < ng; ++g) {
+          const DLin gl = P->guard[gf + g];
+          live = live && lin_eval<T>(P, gl, sl, lane) >= 0;
+        }
+        const DLin il = A.idx;
+        const T idx = lin_eval<T>(P, il, sl, lane);
+        const bool inb = live && (A.bounds_free || (idx >= 0 && (int64_t)idx <= A.maxidx));
+        if (MODE == 0) oob += (live && !inb) ? 1 : 0;
+        const unsigned bal = __ballot_sync(FULL, inb);
+        if (bal == 0) continue;
+        const int G = A.G;
+        if (MODE == 2) {
+          if (inb) {
+            const uint64_t g0 = (uint64_t)idx * (uint64_t)G;
+            if ((uint32_t)A.arr == t_arr && t_gran >= g0 && t_gran < g0 + (uint64_t)G) {
+              const uint64_t slot = atomicAdd((unsigned long long*)&counters[C_NPAIR], 1ull);
+              if (slot < pair_cap) {
+                PairRec r;
+                r.blk = (uint32_t)b;
+                r.thr = (uint32_t)lt;
+                for (int l = 0; l < MAXLOOP; ++l) r.it[l] = (uint32_t)ic[l];
+                r.acc = a;
+                r.pad = 0;
+                const DLin vl = A.iv;
+                r.iv = (int64_t)lin_eval<T>(P, vl, sl, lane);
+                pairs[slot] = r;
+              }
+            }
+          }
+          continue;
+        }
+        if (inb) {
+          const DLin vl = A.iv;
+          const uint64_t ivc = (uint64_t)((int64_t)lin_eval<T>(P, vl, sl, lane) - ivmin);
+          const uint64_t cell0 = A.cbase + (A.shared ? (uint64_t)b * A.ngran : 0ull) + (uint64_t)idx * (uint64_t)G;
+          const int rank = __popc(bal & lanemask_lt());
+          for (int j = 0; j < G; ++j) {
+            const uint64_t key = ((((cell0 + j) << IVB) | ivc) << PB) | payload | (uint64_t)a;
+            if (MODE == 1) {
+              keys[cursor + (uint64_t)rank * G + j] = key;
+            } else {
+              for (int p = 0; p < npass; ++p) {
+                const uint32_t dg = (uint32_t)(key >> (PB + 8 * p)) & 255u;
+                const unsigned peers = __match_any_sync(bal, dg);
+                if (lane == __ffs(peers) - 1) atomicAdd(&shist[p * 256 + dg], (uint32_t)__popc(peers));
+              }
+            }
+          }
+        }
+        cursor += (uint64_t)__popc(bal) * G;
+      }
+    }
+    if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
+  }
+  if (MODE == 0) {
+    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS)
+      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
+  }
+}
+
+// ------------------------------------------------------------------ scan
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t x, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// exclusive scan of the 256 threads' values; `ws` holds 8 words
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = warp_incl_scan(v, lane);
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t s = lane < 8 ? ws[lane] : 0;
+    uint64_t si = warp_incl_scan(s, lane);
+    if (lane < 8) ws[lane] = si - s;
+    if (lane == 7 && total) *total = si;
+  }
+  __syncthreads();
+  uint64_t r = x - v + ws[warp];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ uint64_t dev_n(const uint64_t* n_dev, uint64_t n_max) {
+  if (!n_dev) return n_max;
+  uint64_t n = *n_dev;
+  return n < n_max ? n : n_max;
+}
+
+__global__ void __launch_bounds__(256) scan_reduce(const uint64_t* __restrict__ in, const uint64_t* n_dev, uint64_t n_max,
+                                                   uint64_t* __restrict__ partials) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  __shared__ uint64_t ws[8];
+  __shared__ uint64_t tot;
+  for (uint64_t tile = blockIdx.x; tile * SCAN_TILE < n; tile += gridDim.x) {
+    uint64_t s = 0;
+    for (int k = 0; k < SCAN_TILE / 256; ++k) {
+      uint64_t i = tile * SCAN_TILE + (uint64_t)k * 256 + threadIdx.x;
+      if (i < n) s += in[i];
+    }
+    block_excl_scan(s, ws, &tot);
+    if (threadIdx.x == 0) partials[tile] = tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) scan_partials(uint64_t* partials, const uint64_t* n_dev, uint64_t n_max,
+                                                     uint64_t* total) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  const uint64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  __shared__ uint64_t ws[8];
+  __shared__ uint64_t tot;
+  uint64_t carry = 0;
+  for (uint64_t c = 0; c < nt; c += 256) {
+    uint64_t i = c + threadIdx.x;
+    uint64_t v = i < nt ? partials[i] : 0;
+    uint64_t e = block_excl_scan(v, ws, &tot);
+    if (i < nt) partials[i] = carry + e;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                  const uint64_t* n_dev, uint64_t n_max,
+                                                  const uint64_t* __restrict__ partials) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  __shared__ uint64_t ws[8];
+  __shared__ uint64_t tot;
+  for (uint64_t tile = blockIdx.x; tile * SCAN_TILE < n; tile += gridDim.x) {
+    // each thread owns 16 consecutive elements of the tile
+    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * 16;
+    uint64_t v[16], s = 0;
+    for (int k = 0; k < 16; ++k) {
+      v[k] = (b0 + k < n) ? in[b0 + k] : 0;
+      s += v[k];
+    }
+    uint64_t run = partials[tile] + block_excl_scan(s, ws, &tot);
+    for (int k = 0; k < 16; ++k) {
+      if (b0 + k < n) out[b0 + k] = run;
+      run += v[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ radix sort
+__global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                        uint64_t n_max, int shift0, int npass,
+                                                        uint64_t* __restrict__ hist) {
+  __shared__ uint32_t sh[MAX_PASSES * 256];
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((k >> (shift0 + 8 * p)) & 255)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x)
+    if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
+}
+
+__global__ void __launch_bounds__(256) hist_scan_kernel(const uint64_t* __restrict__ hist, uint64_t* __restrict__ gbase,
+                                                        int npass) {
+  __shared__ uint64_t ws[8];
+  for (int p = 0; p < npass; ++p) {
+    uint64_t v = hist[p * 256 + threadIdx.x];
+    gbase[p * 256 + threadIdx.x] = block_excl_scan(v, ws, nullptr);
+  }
+}
+
+constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull << 54) - 1;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+__global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                             const uint64_t* n_dev, uint64_t n_max, int shift,
+                                                             const uint64_t* __restrict__ gbase, uint64_t* status,
+                                                             unsigned long long* ticket, uint32_t epoch,
+                                                             uint64_t* err) {
+  __shared__ uint32_t whist[RS_THREADS / 32][RS_RADIX];
+  __shared__ uint32_t tstart[RS_RADIX];
+  __shared__ uint64_t gofs[RS_RADIX];
+  __shared__ uint64_t ws[8];
+  __shared__ uint64_t stage[RS_TILE];
+  __shared__ uint64_t s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t n = dev_n(n_dev, n_max);
+  const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const uint64_t ep = (uint64_t)epoch << 56;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1ull);
+    for (int i = threadIdx.x; i < (RS_THREADS / 32) * RS_RADIX; i += RS_THREADS) (&whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const uint64_t base = tile * RS_TILE;
+    const uint64_t wbase = base + (uint64_t)warp * (RS_KPT * 32);
+    uint64_t k[RS_KPT];
+    uint32_t dg[RS_KPT], rk[RS_KPT];
+#pragma unroll
+    for (int s = 0; s < RS_KPT; ++s) {
+      const uint64_t i = wbase + (uint64_t)s * 32 + lane;
+      k[s] = i < n ? in[i] : 0;
+      dg[s] = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
+    }
+    // warp-level stable ranking, slot-major = memory order
+#pragma unroll
+    for (int s = 0; s < RS_KPT; ++s) {
+      const uint32_t d = dg[s];
+      const unsigned peers = __match_any_sync(FULL, d);
+      uint32_t old = 0;
+      if (d < 256u) old = whist[warp][d];
+      rk[s] = old + __popc(peers & lanemask_lt());
+      __syncwarp();
+      if (d < 256u && lane == __ffs(peers) - 1) whist[warp][d] = old + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // thread t owns digit t: counts across warps, warp-exclusive prefixes
+    const int t = threadIdx.x;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < RS_THREADS / 32; ++w) {
+      const uint32_t c = whist[w][t];
+      whist[w][t] = sum;
+      sum += c;
+    }
+    uint64_t* my = status + tile * RS_RADIX + t;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_relaxed(my, ep | ST_PREFIX | sum);
+    } else {
+      st_relaxed(my, ep | ST_AGG | sum);
+      uint64_t p = tile - 1;
+      uint32_t spins = 0;
+      for (;;) {
+        const uint64_t wv = ld_relaxed(status + p * RS_RADIX + t);
+        const bool ready = (wv >> 56) == epoch && (wv & (3ull << 54)) != 0;
+        if (!ready) {
+          if (++spins > SPIN_LIMIT) {
+            atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += wv & ST_VAL;
+        if ((wv & ST_PREFIX) || p == 0) break;
+        --p;
+      }
+      st_relaxed(my, ep | ST_PREFIX | (excl + sum));
+    }
+    gofs[t] = gbase[t] + excl;
+    tstart[t] = (uint32_t)block_excl_scan(sum, ws, nullptr);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < RS_KPT; ++s) {
+      const uint32_t d = dg[s];
+      if (d < 256u) stage[tstart[d] + whist[warp][d] + rk[s]] = k[s];
+    }
+    __syncthreads();
+    const uint64_t cnt = (n - base) < (uint64_t)RS_TILE ? (n - base) : (uint64_t)RS_TILE;
+    for (uint32_t i = threadIdx.x; i < cnt; i += RS_THREADS) {
+      const uint64_t key = stage[i];
+      const uint32_t d = (uint32_t)((key >> shift) & 255);
+      out[gofs[d] + (i - tstart[d])] = key;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ conflict scan, phase A
+__global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                               const DProg* __restrict__ P, uint64_t* __restrict__ cand,
+                                                               uint64_t cand_cap, uint64_t* counters) {
+  __shared__ uint64_t st[CA_THREADS * (CA_KPT + 1)];
+  __shared__ uint64_t sc[2 * 512];
+  __shared__ uint32_t scount;
+  __shared__ uint64_t sbase;
+  const uint64_t n = *n_dev;
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
+  const int rsh = PB + IVB;
+  const uint32_t wmask = P->wmask;
+  const uint64_t shbase = P->shared_cell_base;
+  for (uint64_t tile = blockIdx.x; tile * CA_TILE < n; tile += gridDim.x) {
+    const uint64_t base = tile * CA_TILE;
+    if (threadIdx.x == 0) scount = 0;
+    for (int i = threadIdx.x; i < CA_TILE; i += CA_THREADS) {
+      const uint64_t idx = base + i;
+      st[(i >> 4) * (CA_KPT + 1) + (i & 15)] = idx < n ? keys[idx] : 0;
+    }
+    __syncthreads();
+    auto key_at = [&](uint64_t idx) -> uint64_t {
+      const uint64_t r = idx - base;
+      return r < (uint64_t)CA_TILE ? st[(r >> 4) * (CA_KPT + 1) + (r & 15)] : keys[idx];
+    };
+    const uint64_t c0 = base + (uint64_t)threadIdx.x * CA_KPT;
+    const uint64_t c1 = c0 + CA_KPT < n ? c0 + CA_KPT : n;
+    if (c0 < n) {
+      uint64_t j = c0;
+      if (c0 > 0) {
+        const uint64_t rprev = shr64(key_at(c0 - 1), rsh);
+        while (j < c1 && shr64(key_at(j), rsh) == rprev) ++j;
+      }
+      while (j < c1) {
+        const uint64_t s = j;
+        uint64_t prev = key_at(j);
+        const uint64_t rid = shr64(prev, rsh);
+        const bool glob = rid < shbase;
+        bool w = (wmask >> lowbits(prev, AB)) & 1u;
+        bool anyw_run = w, anyw_sub = w, thr_sub = false, blkdiff = false, cnd = false, lng = false;
+        ++j;
+        while (j < n) {
+          const uint64_t k2 = key_at(j);
+          if (shr64(k2, rsh) != rid) break;
+          if (j - s >= (uint64_t)CA_LONG) {
+            lng = true;
+            break;
+          }
+          if (shr64(k2, PB) != shr64(prev, PB)) {
+            cnd |= anyw_sub && thr_sub;
+            anyw_sub = false;
+            thr_sub = false;
+          } else {
+            thr_sub |= lowbits(k2 >> AB, BB + TB) != lowbits(prev >> AB, BB + TB);
+          }
+          blkdiff |= lowbits(k2 >> (AB + TB), BB) != lowbits(prev >> (AB + TB), BB);
+          w = (wmask >> lowbits(k2, AB)) & 1u;
+          anyw_sub |= w;
+          anyw_run |= w;
+          prev = k2;
+          ++j;
+        }
+        cnd |= anyw_sub && thr_sub;
+        if (glob) cnd |= anyw_run && blkdiff;
+        if (cnd || lng) {
+          const uint32_t slot = atomicAdd(&scount, 1u);
+          const uint64_t e = lng ? 0 : j;
+          if (slot < 512) {
+            sc[2 * slot] = s;
+            sc[2 * slot + 1] = e;
+          } else {
+            const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
+            if (g < cand_cap) {
+              cand[2 * g] = s;
+              cand[2 * g + 1] = e;
+            }
+          }
+        }
+        if (lng)
+          while (j < c1 && shr64(key_at(j), rsh) == rid) ++j;
+      }
+    }
+    __syncthreads();
+    const uint32_t m = scount < 512 ? scount : 512;
+    if (threadIdx.x == 0 && m) sbase = atomicAdd((unsigned long long*)&counters[C_NCAND], (unsigned long long)m);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += CA_THREADS) {
+      const uint64_t g = sbase + i;
+      if (g < cand_cap) {
+        cand[2 * g] = sc[2 * i];
+        cand[2 * g + 1] = sc[2 * i + 1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ conflict scan, phase B
+struct Sum {
+  bool p;
+  uint32_t lo, hi;
+  __device__ __forceinline__ void reset() { p = false; }
+  __device__ __forceinline__ void add(uint32_t v) {
+    if (!p) {
+      p = true;
+      lo = hi = v;
+    } else {
+      lo = v < lo ? v : lo;
+      hi = v > hi ? v : hi;
+    }
+  }
+};
+
+// pairs (this lane's access a, access b) with two different ids among their
+// instances: every b present unless a and b are both one and the same id
+__device__ __forceinline__ uint32_t racy_row(const Sum& s, int lane) {
+  const unsigned P = __ballot_sync(FULL, s.p);
+  if (!P) return 0;
+  const bool single = s.p && s.lo == s.hi;
+  const unsigned S = __ballot_sync(FULL, single);
+  const unsigned eq = __match_any_sync(FULL, single ? s.lo : (0x80000000u | (unsigned)lane));
+  const unsigned nonr = single ? (eq & S) : 0u;
+  return s.p ? (P & ~nonr) : 0u;
+}
+
+__global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                    const DProg* __restrict__ P, const uint64_t* __restrict__ cand,
+                                                    uint64_t cand_cap, uint64_t* __restrict__ raw, uint64_t raw_cap,
+                                                    uint64_t* counters) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t n = *n_dev;
+  uint64_t ncand = counters[C_NCAND];
+  if (ncand > cand_cap) ncand = cand_cap;
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
+  const int rsh = PB + IVB;
+  const uint32_t einter = lane < P->nacc ? P->einter[lane] : 0u;
+  const uint32_t eintra = lane < P->nacc ? P->eintra[lane] : 0u;
+  const uint64_t shbase = P->shared_cell_base;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t c = gw; c < ncand; c += nw) {
+    const uint64_t s = cand[2 * c], e = cand[2 * c + 1];
+    const uint64_t rid = shr64(keys[s], rsh);
+    const bool glob = rid < shbase;
+    Sum tw, wb, br;  // thread per (iv, block, warp); warp per (iv, block); block per run
+    tw.reset();
+    wb.reset();
+    br.reset();
+    uint32_t m_inter = 0, m_blk = 0, m_warp = 0;
+    uint64_t cur_sub = ~0ull;
+    uint32_t cur_b = 0xffffffffu, cur_w = 0xffffffffu;
+    for (uint64_t pos = s;; pos += 32) {
+      const uint64_t i = pos + lane;
+      const bool ok = i < n && (e == 0 || i < e);
+      const uint64_t kk = ok ? keys[i] : 0;
+      const bool inrun = ok && shr64(kk, rsh) == rid;
+      const unsigned m = __ballot_sync(FULL, inrun);
+      const int cnt = __popc(m);
+      for (int jj = 0; jj < cnt; ++jj) {
+        const uint64_t key = __shfl_sync(FULL, kk, jj);
+        const uint64_t sub = shr64(key, PB);
+        const uint32_t b = (uint32_t)lowbits(key >> (AB + TB), BB);
+        const uint32_t t = (uint32_t)lowbits(key >> AB, TB);
+        const uint32_t wpi = t >> 5;
+        const uint32_t a = (uint32_t)lowbits(key, AB);
+        if (sub != cur_sub || b != cur_b) {
+          m_warp |= racy_row(tw, lane) & eintra;
+          m_blk |= racy_row(wb, lane) & eintra;
+          tw.reset();
+          wb.reset();
+          cur_sub = sub;
+          cur_b = b;
+          cur_w = wpi;
+        } else if (wpi != cur_w) {
+          m_warp |= racy_row(tw, lane) & eintra;
+          tw.reset();
+          cur_w = wpi;
+        }
+        if ((uint32_t)lane == a) {
+          tw.add(t);
+          wb.add(wpi);
+          br.add(b);
+        }
+      }
+      if (cnt < 32) break;
+    }
+    m_warp |= racy_row(tw, lane) & eintra;
+    m_blk |= racy_row(wb, lane) & eintra;
+    if (glob) m_inter |= racy_row(br, lane) & einter;
+    // emit (lane, b >= lane) witnesses
+    const uint32_t ge = lane == 0 ? FULL : ~((1u << lane) - 1u);
+    uint32_t row = (m_inter | m_blk | m_warp) & ge;
+    const uint32_t cntw = (uint32_t)__popc(row);
+    uint32_t incl = cntw;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) continue;
+    uint64_t wbase = 0;
+    if (lane == 0) wbase = atomicAdd((unsigned long long*)&counters[C_NRAW], (unsigned long long)total);
+    wbase = __shfl_sync(FULL, wbase, 0);
+    // location of the run
+    int li = 0;
+    while (li + 1 < P->nlay && P->lay_cbase[li + 1] <= rid) ++li;
+    const uint64_t cell = rid - P->lay_cbase[li];
+    const bool sh = P->lay_shared[li];
+    const uint64_t gran = sh ? cell % P->lay_ngran[li] : cell;
+    const uint32_t arr = (uint32_t)P->lay_arr[li];
+    uint64_t o = wbase + incl - cntw;
+    while (row) {
+      const int bb = __ffs(row) - 1;
+      row &= row - 1;
+      const uint32_t kind = ((m_inter >> bb) & 1u) | (((m_blk >> bb) & 1u) << 1) | (((m_warp >> bb) & 1u) << 2);
+      if (o < raw_cap) raw[o] = pack_witness(sh ? 1u : 0u, arr, gran, (uint32_t)lane, (uint32_t)bb, kind);
+      ++o;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ witness merge
+__global__ void heads_kernel(const uint64_t* __restrict__ w, const uint64_t* n_dev, uint64_t n_max,
+                             uint64_t* __restrict__ flags) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = (i == 0 || (w[i] >> WIT_SORT_LO) != (w[i - 1] >> WIT_SORT_LO)) ? 1 : 0;
+}
+
+__global__ void merge_kernel(const uint64_t* __restrict__ w, const uint64_t* __restrict__ flags,
+                             const uint64_t* __restrict__ excl, const uint64_t* n_dev, uint64_t n_max,
+                             uint64_t* __restrict__ uniq) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = excl[i] + flags[i] - 1;
+    atomicOr((unsigned long long*)&uniq[u], (unsigned long long)w[i]);
+  }
+}
+
+__global__ void kind_counts_kernel(const uint64_t* __restrict__ uniq, uint64_t* counters) {
+  const uint64_t n = counters[C_NUNIQ];
+  uint64_t c0 = 0, c1 = 0, c2 = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = uniq[i] & 7;
+    c0 += k & 1;
+    c1 += (k >> 1) & 1;
+    c2 += (k >> 2) & 1;
+  }
+  for (int o = 16; o; o >>= 1) {
+    c0 += __shfl_down_sync(FULL, c0, o);
+    c1 += __shfl_down_sync(FULL, c1, o);
+    c2 += __shfl_down_sync(FULL, c2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd((unsigned long long*)&counters[C_KIND0], (unsigned long long)c0);
+    if (c1) atomicAdd((unsigned long long*)&counters[C_KIND1], (unsigned long long)c1);
+    if (c2) atomicAdd((unsigned long long*)&counters[C_KIND2], (unsigned long long)c2);
+  }
+}
+
+int occupancy_grid(const void* fn, int threads, size_t smem, int nsm) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+  if (per < 1) per = 1;
+  return per * nsm;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
+                          uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys, uint64_t* hist, int npass,
+                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {
+  const size_t esz = wide ? 8 : 4;
+  const size_t smem = (size_t)(EXP_THREADS / 32) * h_prog.nslot * 32 * esz + (mode == 0 ? (size_t)npass * 256 * 4 : 0);
+  const void* fn = nullptr;
+  if (!wide) {
+    fn = mode == 0   ? (const void*)expand_kernel<int32_t, 0>
+         : mode == 1 ? (const void*)expand_kernel<int32_t, 1>
+                     : (const void*)expand_kernel<int32_t, 2>;
+  } else {
+    fn = mode == 0   ? (const void*)expand_kernel<int64_t, 0>
+         : mode == 1 ? (const void*)expand_kernel<int64_t, 1>
+                     : (const void*)expand_kernel<int64_t, 2>;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (h_prog.nunits + EXP_THREADS / 32 - 1) / (EXP_THREADS / 32);
+  int64_t grid = occupancy_grid(fn, EXP_THREADS, smem, L.nsm);
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  void* args[] = {(void*)&d_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys, (void*)&hist,
+                  (void*)&npass,  (void*)&counters, (void*)&uniq,     (void*)&pairs, (void*)&pair_cap};
+  (*L.launches)++;
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
+}
+
+cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                        uint64_t* partials, uint64_t* total) {
+  uint64_t tiles = (n_max + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 0) tiles = 1;
+  unsigned grid = (unsigned)(tiles < (uint64_t)L.nsm * 8 ? tiles : (uint64_t)L.nsm * 8);
+  scan_reduce<<<grid, 256, 0, L.s>>>(in, n_dev, n_max, partials);
+  scan_partials<<<1, 256, 0, L.s>>>(partials, n_dev, n_max, total);
+  scan_apply<<<grid, 256, 0, L.s>>>(in, out, n_dev, n_max, partials);
+  (*L.launches) += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max, int shift0,
+                             int npass, uint64_t* hist) {
+  uint64_t blocks = (n_max + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 4 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 4);
+  histogram_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, shift0, npass, hist);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass) {
+  hist_scan_kernel<<<1, 256, 0, L.s>>>(hist, gbase, npass);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                            int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
+                            uint64_t* err) {
+  uint64_t tiles = (n_max + RS_TILE - 1) / RS_TILE;
+  int grid = occupancy_grid((const void*)onesweep_kernel, RS_THREADS, 0, L.nsm);
+  if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
+  onesweep_kernel<<<grid, RS_THREADS, 0, L.s>>>(in, out, n_dev, n_max, shift, gbase, status,
+                                                (unsigned long long*)ticket, epoch, err);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                              uint64_t* cand, uint64_t cand_cap, uint64_t* counters) {
+  int grid = occupancy_grid((const void*)candidates_kernel, CA_THREADS, 0, L.nsm);
+  candidates_kernel<<<grid, CA_THREADS, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, counters);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                         const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
+                         uint64_t* counters) {
+  int grid = occupancy_grid((const void*)exact_kernel, 256, 0, L.nsm);
+  exact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, raw, raw_cap, counters);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_dev, uint64_t n_max, uint64_t* flags) {
+  uint64_t blocks = (n_max + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
+  heads_kernel<<<grid, 256, 0, L.s>>>(w, n_dev, n_max, flags);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* flags, const uint64_t* excl,
+                         const uint64_t* n_dev, uint64_t n_max, uint64_t* uniq) {
+  uint64_t blocks = (n_max + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
+  merge_kernel<<<grid, 256, 0, L.s>>>(w, flags, excl, n_dev, n_max, uniq);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters) {
+  kind_counts_kernel<<<L.nsm, 256, 0, L.s>>>(uniq, counters);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+}  // namespace hgrd

@@ -1,0 +1,70 @@
+// Launch wrappers of the check pipeline's kernels (all enqueue only).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hgrd_internal.h"
+
+namespace hgrd {
+
+// Work shapes
+constexpr int EXP_THREADS = 256;   // 8 warps; one simulated warp of the user kernel per warp
+constexpr int RS_THREADS = 256;    // onesweep: 8 warps x 16 keys
+constexpr int RS_KPT = 16;
+constexpr int RS_TILE = RS_THREADS * RS_KPT;
+constexpr int RS_RADIX = 256;
+constexpr int CA_THREADS = 256;    // candidate scan: 16 consecutive keys per thread
+constexpr int CA_KPT = 16;
+constexpr int CA_TILE = CA_THREADS * CA_KPT;
+constexpr int CA_LONG = 4096;      // a run longer than this is handed to the exact scan unmeasured
+constexpr int SCAN_TILE = 4096;
+constexpr int MAX_PASSES = 16;
+
+// Pair-search record of one instance touching the minimal witness's granule.
+struct PairRec {
+  uint32_t blk, thr;
+  uint32_t it[4];
+  int32_t acc, pad;
+  int64_t iv;
+};
+
+struct Launch {
+  cudaStream_t s;
+  int nsm;
+  uint64_t* launches;  // incremented per kernel enqueued
+};
+
+// expansion: mode 0 = count keys per unit + digit histograms + out-of-bounds,
+// 1 = write keys, 2 = gather the instances of the minimal witness
+cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
+                          uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys, uint64_t* hist, int npass,
+                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap);
+
+// exclusive scan of uint64 values; n = min(*n_dev, n_max) when n_dev is given
+cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                        uint64_t* partials, uint64_t* total);
+
+// histograms of npass 8-bit digits starting at bit `shift0` of n keys
+cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max, int shift0,
+                             int npass, uint64_t* hist);
+// per-pass exclusive prefix of the digit counts
+cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass);
+// one stable onesweep pass on the digit at `shift`
+cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                            int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
+                            uint64_t* err);
+
+// conflict scan, phase A: runs that may hold a race -> (start, end) list
+cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                              uint64_t* cand, uint64_t cand_cap, uint64_t* counters);
+// conflict scan, phase B: exact per-access summaries -> packed raw witnesses
+cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                         const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
+                         uint64_t* counters);
+
+// witness merge: head flags, merge by atomic OR into uniq, kind counts
+cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_dev, uint64_t n_max, uint64_t* flags);
+cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* flags, const uint64_t* excl,
+                         const uint64_t* n_dev, uint64_t n_max, uint64_t* uniq);
+cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters);
+
+}  // namespace hgrd

@@ -1,0 +1,95 @@
+"""Host-side tests of the C ABI (no GPU): the library loads, exports every
+symbol include/hgrd.h declares, and its parser / binder / division method
+behave as documented."""
+import os
+import random
+import re
+
+import pytest
+
+import paper_2604_02106_b300 as hg
+import workloads
+from workloads import Binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "hgrd.h")).read()
+    declared = set(re.findall(r"\b(hgrd_[a-z_]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    L = hg.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared == set(hg.EXPORTS)
+
+
+def _err(text, grid=(1, 1, 1), block=(32, 1, 1), params=()):
+    with pytest.raises(hg.HgrdError) as ei:
+        hg.Kernel(text).bind(grid, block, params)
+    return ei.value.code
+
+
+def test_parse_errors():
+    base = "kernel k\narray a global 64\n"
+    assert _err(base + "access W a ; width 4 ; idx tx*ty\n") == -2          # not quasi-affine
+    assert _err(base + "access W a ; width 4 ; idx 4 / tx\n") == -2         # divisor varies
+    assert _err(base + "access W a ; width 4 ; idx q\n") == -2              # unknown name
+    assert _err(base + "access W b ; width 4 ; idx 0\n") == -2              # unknown array
+    assert _err(base + "access W a ; width 4 ; iv tx ; idx 0\n") == -2      # interval uses tid
+    assert _err("kernel k\narray a global 64 ; granule 8\naccess W a ; width 4 ; idx 0\n") == -2  # width vs granule
+    assert _err("array a global 4\n") == -2                                  # no kernel line
+    assert _err(base + "access W a ; width 4 ; idx 0 ; if tx != 3\n") == -2  # != only in asserts
+
+
+def test_bind_errors_match_host_classes():
+    t = "kernel k\nparam Q\narray a global 4*Q\nassert Q > 2\naccess W a ; width 4 ; idx tx / Q\n"
+    assert _err(t, params=()) == -3               # parameter count
+    assert _err(t, params=(2,)) == -4             # host assert (class 1)
+    assert _err(t, block=(0, 1, 1), params=(3,)) == -3
+    assert _err(t, block=(64, 32, 1), params=(3,)) == -3   # > 1024 threads
+    t2 = "kernel k\nparam Q\narray a global 64\naccess W a ; width 4 ; idx tx % Q\n"
+    assert _err(t2, params=(0,)) == -3            # divisor <= 0
+    t3 = "kernel k\nparam Q\narray a global 64\naccess W a ; width 4 ; idx tx * Q\n"
+    assert _err(t3, params=(1 << 62,)) == -5      # int64 overflow
+    hg.Kernel(t3).bind((1, 1, 1), (32, 1, 1), (3,))
+
+
+def test_paper_fixtures_bind_like_the_oracle():
+    import json
+    gold = os.path.join(ROOT, "tests", "golden")
+    for name in sorted(os.listdir(gold)):
+        g = json.load(open(os.path.join(gold, name)))
+        for case in g["cases"]:
+            text = g["descriptor"] if case.get("assert", True) else g["descriptor_without_assert"]
+            k = hg.Kernel(text)
+            if case["expect"] == "EHOSTCONSTRAINT":
+                with pytest.raises(hg.HgrdError) as ei:
+                    k.bind(case["grid"], case["block"], case["params"])
+                assert ei.value.code == -4
+            else:
+                k.bind(case["grid"], case["block"], case["params"])
+
+
+def test_division_by_constant_method():
+    # Granlund-Montgomery with C truncation, both widths, against exact integer division
+    rnd = random.Random(7)
+    def ref(n, d):
+        q = abs(n) // d
+        q = q if n >= 0 else -q
+        return q, n - q * d
+    for wide, N in ((False, 31), (True, 62)):
+        ds = list(range(1, 200)) + [rnd.randrange(1, 1 << (N - 1)) for _ in range(200)] + [(1 << N) - 1, 1 << (N - 1)]
+        for d in ds:
+            ns = [0, 1, -1, d, -d, d - 1, 1 - d, (1 << N) - 1, 1 - (1 << N)] + \
+                 [rnd.randrange(-(1 << N) + 1, 1 << N) for _ in range(20)]
+            for n in ns:
+                assert hg.debug_divmod(n, d, wide) == ref(n, d), (n, d, wide)
+
+
+def test_workspace_scales_with_problem():
+    w = workloads.config2(0)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    ws = k.workspace_size()
+    # two 8-byte key buffers for every possible key dominate
+    assert 16 * 536870912 <= ws < 16 * 536870912 * 1.2

@@ -1,0 +1,193 @@
+"""GPU path (through the C ABI) against the CPU oracle, bit for bit.
+
+Every case compares the canonical witness list, the per-kind counts, the
+instance / key / out-of-bounds counts, the minimal witness and the canonical
+instance pair.  Sizes run from tiny launches to the full 64x64x(16x16)
+stencil the bench times, where the oracle checks a sample of the address
+space and closed forms check the rest.
+"""
+import math
+
+import pytest
+
+import oracle
+import paper_2604_02106_b300 as hg
+import workloads
+from workloads import Binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _same(g, o, pair=True):
+    assert g.witnesses == o.witnesses
+    assert g.n_witness == o.n_witness
+    assert g.n_by_kind == o.n_by_kind
+    assert g.n_instances == o.n_instances
+    assert g.n_keys == o.n_keys
+    assert g.n_oob == o.n_oob
+    assert g.racy == o.racy
+    assert g.min_w == o.min_w
+    if pair and o.racy:
+        assert g.min_x == o.min_x and g.min_y == o.min_y
+
+
+def _both(text, binding, cap=1 << 20, **kw):
+    g = hg.check(text, binding, cap=cap, **kw)
+    o = oracle.check(text, binding, cap=cap)
+    return g, o
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_tiny_random_launches(seed):
+    w = workloads.random_tiny(1000 + seed, max_instances=500)
+    _same(*_both(w.text, w.binding))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_small_random_launches(seed):
+    w = workloads.random_tiny(20000 + seed, max_instances=20000)
+    _same(*_both(w.text, w.binding))
+
+
+@pytest.mark.parametrize("item", range(6))
+def test_config1_plain(item):
+    w = workloads.config1(item)
+    _same(*_both(w.text, w.binding))
+
+
+def test_paper_fixtures():
+    import json, os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    for name in sorted(os.listdir(gold)):
+        g = json.load(open(os.path.join(gold, name)))
+        for case in g["cases"]:
+            if case["expect"] == "EHOSTCONSTRAINT":
+                continue
+            text = g["descriptor"] if case.get("assert", True) else g["descriptor_without_assert"]
+            b = Binding(tuple(case["grid"]), tuple(case["block"]), tuple(case["params"]))
+            gr, orr = _both(text, b)
+            _same(gr, orr)
+            assert gr.racy == (case["expect"] == "racy")
+
+
+@pytest.mark.parametrize("W,K,planted", [(64, 4, True), (64, 4, False), (128, 8, True), (256, 6, True)])
+def test_stencil_small(W, K, planted):
+    w = workloads.config2(0, planted=planted, W=W, H=W, K=K)
+    g, o = _both(w.text, w.binding)
+    _same(g, o)
+    assert g.n_witness == (W - 1 if planted else 0)
+
+
+@pytest.mark.parametrize("item", [0, 1, 2, 5, 6, 7, 10, 11, 12])
+def test_stride_sweep_items(item):
+    w = workloads.config3()[item]
+    _same(*_both(w.text, w.binding))
+
+
+def test_stride_sweep_large_closed_form():
+    # N = 2^16, stride 3: thread g writes A[3g .. 3g+7]; elements touched by
+    # two or more threads are exactly 3 <= e < 3(N-1)+8 except the first three
+    from test_oracle import _stride_closed_form
+    items = [w for w in workloads.config3() if w.meta["N"] == 1 << 14]
+    for w in items:
+        g = hg.check(w.text, w.binding, cap=1 << 22)
+        want = sorted(_stride_closed_form(w.meta["N"], w.meta["stride"], w.binding.block[0]))
+        assert g.witnesses == want
+        assert g.n_instances == w.binding.grid[0] * w.binding.block[0] * 8 * 12
+
+
+def test_full_stencil_sampled_against_oracle():
+    # the full 1024x1024 stencil in the bench's launch shape: closed form for
+    # the witness set, the oracle on every instance for the counts and on the
+    # Out rows holding the planted collisions plus a band of In
+    w = workloads.config2(0, planted=True)
+    g = hg.check(w.text, w.binding, cap=1 << 16)
+    want = [(0, 2, 4 * (r + 1) * 1023, 15, 15, 1) for r in range(1023)]
+    assert g.witnesses == want
+    assert g.n_instances == 536870912
+    o = oracle.check(w.text, w.binding, filter_array=2, gran_lo=1023 * 500, gran_hi=1023 * 540)
+    assert g.n_keys == o.n_keys and g.n_oob == o.n_oob
+    assert [x for x in g.witnesses if 1023 * 500 <= x[2] // 4 < 1023 * 540] == o.witnesses
+    assert g.min_x == (0, 16, 0, 0, 0, 0, 15) and g.min_y == (63, 15, 0, 0, 0, 0, 15)
+    o2 = oracle.check(w.text, w.binding, filter_array=1, gran_lo=300000, gran_hi=301000)
+    assert o2.witnesses == []
+
+
+def test_full_stencil_clean():
+    w = workloads.config2(0, planted=False)
+    g = hg.check(w.text, w.binding)
+    assert not g.racy and g.n_witness == 0
+
+
+# ---------------------------------------------------------------- edge cases
+
+EDGE = {
+    "empty_loop": ("kernel e\nparam U\nloop i U\narray a global 64\naccess W a ; width 4 ; idx 0\n",
+                   Binding((2, 1, 1), (32, 1, 1), (0,))),
+    "dead_guard": ("kernel e\narray a global 64\naccess W a ; width 4 ; idx 0 ; if tx > 100\n",
+                   Binding((2, 1, 1), (32, 1, 1), ())),
+    "single_thread": ("kernel e\nloop i 5\narray a global 64\naccess W a ; width 4 ; idx i % 2\n",
+                      Binding((1, 1, 1), (1, 1, 1), ())),
+    "ragged_warps": ("kernel e\narray a global 4096\naccess W a ; width 4 ; idx tx / 3\n",
+                     Binding((3, 1, 1), (45, 1, 1), ())),
+    "grid_3d": ("kernel e\narray a global 4096\narray s shared 256\n"
+                "access W a ; width 4 ; idx (bx + 2*by + 4*bz) * 8 + tx / 4\n"
+                "access W s ; width 4 ; idx tz * 4 + tx % 4 ; iv 1\n",
+                Binding((2, 2, 2), (8, 2, 3), ())),
+    "all_oob": ("kernel e\narray a global 16\naccess W a ; width 4 ; idx tx + 8\n",
+                Binding((2, 1, 1), (32, 1, 1), ())),
+    "wide_int64": ("kernel e\nparam BIG\narray a global 64\n"
+                   "access W a ; width 4 ; idx (tx * BIG) % 3 + BIG - BIG\n",
+                   Binding((2, 1, 1), (64, 1, 1), (1 << 40,))),
+    "float4_mixed": ("kernel e\narray a global 1024\naccess W a ; width 16 ; idx tx\n"
+                     "access R a ; width 4 ; idx 4*tx + 5\n", Binding((2, 1, 1), (32, 1, 1), ())),
+    "atomics": ("kernel e\narray a global 64\naccess A a ; width 4 ; idx tx % 2 ; scope block\n"
+                "access A a ; width 4 ; idx tx % 2 ; scope device\naccess R a ; width 4 ; idx 1 ; iv 1\n",
+                Binding((3, 1, 1), (64, 1, 1), ())),
+    "negative_mod": ("kernel e\narray a global 400\naccess W a ; width 4 ; idx 50 + (tx - 40) % 7\n"
+                     "access W a ; width 4 ; idx 50 + (tx - 40) / 7 ; iv 2\n",
+                     Binding((1, 1, 1), (80, 1, 1), ())),
+    "one_hot_address_long_run": ("kernel e\nloop i 4\narray a global 64\naccess W a ; width 4 ; idx 3\n",
+                                 Binding((64, 1, 1), (256, 1, 1), ())),
+    "many_intervals": ("kernel e\nloop i 40\narray s shared 512\naccess W s ; width 4 ; iv i ; idx (tx + i) % 128\n"
+                       "access R s ; width 4 ; iv i ; idx (tx + i + 1) % 128\n", Binding((2, 1, 1), (128, 1, 1), ())),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE))
+def test_edge_cases(name):
+    text, b = EDGE[name]
+    _same(*_both(text, b))
+
+
+def test_truncation_keeps_exact_counts():
+    w = workloads.config1(0)
+    full = hg.check(w.text, w.binding, cap=1 << 20)
+    part = hg.check(w.text, w.binding, cap=7)
+    assert part.truncated and part.witnesses == full.witnesses[:7]
+    assert part.n_witness == full.n_witness and part.n_by_kind == full.n_by_kind
+
+
+def test_raw_witness_buffer_retry():
+    # more per-run witnesses than a tiny raw buffer: ENOMEM then an automatic retry
+    w = workloads.config1(0)
+    g = hg.check(w.text, w.binding, cap=1 << 20, max_raw_witness=64)
+    o = oracle.check(w.text, w.binding)
+    _same(g, o)
+
+
+def test_deterministic_and_enqueue_collect():
+    import torch
+    w = workloads.config1(3)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    a = k.check(cap=1 << 20)
+    b = k.check(cap=1 << 20)
+    assert a == b
+    ws = k.workspace()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        k.enqueue(ws, stream=s)
+        c = k.collect(ws, cap=1 << 20, stream=s)
+    assert c.witnesses == a.witnesses and c.n_by_kind == a.n_by_kind
+    st = hg.stats()
+    assert st["kernel_launches"] > 0

@@ -345,6 +345,8 @@ def random_tiny(seed: int, max_instances: int = 2048) -> Workload:
         grid[d] = rng.range(1, 3)
     for d in range(ndim_b):
         block[d] = rng.choice([1, 2, 3, 5, 8, 16, 33, 40])
+    while math.prod(block) > 1024:
+        block[block.index(max(block))] //= 2
     nthreads = math.prod(block) * math.prod(grid)
     nloops = rng.range(0, 2)
     bounds = [rng.range(1, 3) for _ in range(nloops)]
