@@ -171,6 +171,27 @@ int hgrd_last_stats(hgrd_stats* s);
  * and the number of stages to *n. */
 int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n);
 
+/* hgrd_check without a caller workspace, for callers that cannot allocate
+ * device memory: code running while another component owns all device memory
+ * (a caching allocator or pool that must not be bypassed), code called from
+ * inside such an allocator, or embedders without access to cudaMalloc.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *   * Scratch: a 64 MiB array compiled into the library.  Every device that
+ *     loads the library holds it until the process exits.
+ *   * Bindings whose hgrd_workspace_size exceeds 64 MiB are rejected with
+ *     HGRD_ENOMEM before any work is enqueued.
+ *   * The call allocates nothing: no cudaMalloc/cudaFree, no CUDA events, no
+ *     host staging buffer (witnesses are widened in place inside host_out).
+ *   * The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   * All calls share the one array, which keeps the previous call's data;
+ *     each call clears what must start at zero.  Calls whose GPU work
+ *     overlaps (other host threads, other streams) race on the array.
+ *   * Outputs as hgrd_check, except that the canonical instance pair is not
+ *     searched (pair_found = 0).  Synchronous on return. */
+int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, void* cuda_stream, hgrd_witness* host_out,
+                       uint64_t cap, hgrd_verdict* v);
+
 void hgrd_free_desc(hgrd_desc* d);
 const char* hgrd_last_error(void);
 

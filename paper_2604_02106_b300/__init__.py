@@ -22,7 +22,7 @@ PROFILE = 2
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
            "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile", "hgrd_free_desc", "hgrd_last_error",
-           "hgrd_debug_divmod"]
+           "hgrd_debug_divmod", "hgrd_check_noalloc"]
 
 
 class HgrdError(RuntimeError):
@@ -84,6 +84,8 @@ def lib():
         L.hgrd_check_enqueue.argtypes = [vp, C.POINTER(CheckOpts), vp, sz, vp]
         L.hgrd_check_collect.argtypes = [vp, C.POINTER(CheckOpts), vp, sz, vp, C.POINTER(Witness), u64,
                                          C.POINTER(Verdict)]
+        L.hgrd_check_noalloc.argtypes = [vp, C.POINTER(CheckOpts), vp, C.POINTER(Witness), u64, C.POINTER(Verdict)]
+        L.hgrd_check_noalloc.restype = C.c_int
         L.hgrd_last_stats.argtypes = [C.POINTER(Stats)]
         L.hgrd_last_profile.argtypes = [C.POINTER(StageTime), C.c_uint32, C.POINTER(C.c_uint32)]
         L.hgrd_free_desc.argtypes = [vp]
@@ -195,6 +197,20 @@ class Kernel:
                           [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None,
                           _it(v.min_x) if v.pair_found else None, _it(v.min_y) if v.pair_found else None,
                           rc == ETRUNCATED)
+
+    def check_noalloc(self, cap: int = 1 << 16, stream=None, **opts) -> Result:
+        """hgrd_check_noalloc: the check on the library's built-in 64 MiB device
+        scratch, for callers that cannot allocate device memory.  No instance
+        pair search (min_x / min_y are None)."""
+        out = (Witness * max(1, cap))()
+        v = Verdict()
+        o = _opts(**opts)
+        rc = lib().hgrd_check_noalloc(self._h, C.byref(o), _stream_ptr(stream), out, cap, C.byref(v))
+        _raise(rc)
+        n = min(cap, v.n_witness)
+        return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
+                      [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
+                      rc == ETRUNCATED)
 
     def enqueue(self, workspace, stream=None, **opts):
         """Enqueue the device pipeline only (no host synchronisation)."""

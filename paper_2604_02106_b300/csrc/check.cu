@@ -374,3 +374,117 @@ int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hgrd_check_noalloc: the same check with the workspace taken from a fixed
+// device array compiled into this library, for callers that cannot allocate
+// device memory themselves: code that runs while another component owns all
+// device memory (a caching allocator or a memory pool that must not be
+// bypassed), code called from inside such an allocator, or embedders that
+// have no access to cudaMalloc.  The array exists once per device that loads
+// the library and lives until the process exits.
+#include <mutex>
+
+namespace hgrd {
+namespace {
+
+constexpr size_t NOALLOC_BYTES = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_ws[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+// Device address of the array for the current device.  In host code the
+// symbol is only a stand-in, so the address is looked up once per device,
+// with that device current, and kept.
+int noalloc_base(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(HGRD_EUNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess || !p)
+      return fail(HGRD_EDEVICE, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HGRD_OK;
+}
+
+}  // namespace
+}  // namespace hgrd
+
+extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, void* stream,
+                                  hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
+  if (!d || !v) return fail(HGRD_EINVAL, "null argument");
+  if (cap && !host_out) return fail(HGRD_EINVAL, "null witness buffer with nonzero capacity");
+  if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  hgrd_check_opts oo{};
+  if (o) oo = *o;
+  oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
+  const Layout W = layout(*d->bound, &oo);
+  if (W.total > NOALLOC_BYTES)
+    return fail(HGRD_ENOMEM, "hgrd_check_noalloc: this binding needs " + std::to_string(W.total) +
+                                 " bytes of scratch; the built-in array holds " + std::to_string(NOALLOC_BYTES) +
+                                 " (use hgrd_check with a caller workspace)");
+  void* base = nullptr;
+  int rc = noalloc_base(&base);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = enqueue(d, &oo, base, NOALLOC_BYTES, s);
+  if (rc) return rc;
+  char* ws = (char*)base;
+  uint64_t cnt[C_WORDS];
+  CK(cudaMemcpyAsync(cnt, ws + W.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
+  if (cnt[C_NCAND] > std::max<uint64_t>(d->bound->nkeys_max / 2, 1))
+    return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
+  if (cnt[C_NRAW] > W.raw_cap)
+    return fail(HGRD_ENOMEM, "raw witness buffer too small: need " + std::to_string(cnt[C_NRAW]) +
+                                 " (hgrd_check_opts.max_raw_witness)");
+  const Bound& B = *d->bound;
+  memset(v, 0, sizeof(*v));
+  v->n_instances = B.n_instances;
+  v->n_keys = cnt[C_NKEYS];
+  v->n_oob = cnt[C_NOOB];
+  v->n_witness = cnt[C_NUNIQ];
+  v->n_by_kind[0] = cnt[C_KIND0];
+  v->n_by_kind[1] = cnt[C_KIND1];
+  v->n_by_kind[2] = cnt[C_KIND2];
+  v->racy = v->n_witness > 0;
+  auto unpack = [&](uint64_t w) {
+    hgrd_witness x{};
+    x.space = (uint8_t)((w >> 58) & 1);
+    x.array = (uint8_t)((w >> 53) & 31);
+    x.acc_lo = (uint8_t)((w >> 8) & 31);
+    x.acc_hi = (uint8_t)((w >> 3) & 31);
+    x.kind_mask = (uint8_t)(w & 7);
+    x.byte_addr = ((w >> 13) & ((1ull << 40) - 1)) * (uint64_t)B.array_granule[x.array];
+    return x;
+  };
+  const uint64_t* duniq = uniq_buffer(d, W, ws);
+  if (v->racy) {
+    uint64_t w0 = 0;
+    CK(cudaMemcpyAsync(&w0, duniq, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    v->min_w = unpack(w0);
+  }
+  // the packed 8-byte words land in the caller's 16-byte records and are
+  // widened in place from the back, so no host staging buffer is needed
+  const uint64_t n = std::min<uint64_t>(cap, v->n_witness);
+  if (n) {
+    CK(cudaMemcpyAsync(host_out, duniq, n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t* packed = (const uint64_t*)host_out;
+    for (uint64_t k = n; k-- > 0;) {
+      const uint64_t w = packed[k];
+      host_out[k] = unpack(w);
+    }
+  }
+  return (host_out && v->n_witness > cap) ? HGRD_ETRUNCATED : HGRD_OK;
+}
