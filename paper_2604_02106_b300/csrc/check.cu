@@ -147,18 +147,20 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   uint64_t* keysA = U(W.keysA);
   uint64_t* keysB = U(W.keysB);
   uint64_t* nkeys = cnt + C_NKEYS;
-  CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), P, cnt, nullptr, nullptr, 0));
+  CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), 1, cnt, nullptr, nullptr, 0));
   g_prof.mark("expand_count");
   CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
   g_prof.mark("unit_scan");
   CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
   g_prof.mark("expand_write");
-  CK(launch_hist_scan(L, U(W.hist), U(W.gbase), P));
   uint64_t* in = keysA;
   uint64_t* out = keysB;
+  // the expansion counted digit 0; each pass counts the digit of the next
   for (int p = 0; p < P; p++) {
+    CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
     CK(launch_onesweep(L, in, out, nkeys, B.nkeys_max, HP.PB + 8 * p, U(W.gbase) + p * 256, U(W.status),
-                       cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR));
+                       cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
+                       p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.PB + 8 * (p + 1)));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
                                 "sort_pass4", "sort_pass5", "sort_pass6", "sort_pass7"};

@@ -87,7 +87,7 @@ struct DAcc {
 
 // Everything the kernels need about one bound descriptor.  Lives in the
 // device workspace; all lanes read it with uniform addresses.
-struct DProg {
+struct alignas(16) DProg {
   int32_t grid[3], block[3];
   int32_t nthr, wpb;  // threads and warps per block
   int64_t nblk, nunits;
@@ -140,3 +140,5 @@ enum {
 enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
 
 }  // namespace hgrd
+
+static_assert(sizeof(hgrd::DProg) % 16 == 0, "DProg is copied to shared memory in 16-byte words");

@@ -82,7 +82,7 @@ __device__ __forceinline__ void run_ops(const DProg* __restrict__ P, int first, 
 
 // ------------------------------------------------------------------ expand
 template <typename T, int MODE>
-__global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __restrict__ P, uint64_t* __restrict__ unit_cnt,
+__global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __restrict__ Pg, uint64_t* __restrict__ unit_cnt,
                                                              const uint64_t* __restrict__ unit_off,
                                                              uint64_t* __restrict__ keys, uint64_t* __restrict__ hist,
                                                              int npass, uint64_t* __restrict__ counters,
@@ -91,9 +91,18 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __rest
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int WPC = EXP_THREADS / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the compiled program, staged once per CTA (uniform shared-memory reads)
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Pg);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += EXP_THREADS) dst[i] = src[i];
+    __syncthreads();
+  }
+  const DProg* __restrict__ P = reinterpret_cast<const DProg*>(smem);
   const int nslot = P->nslot;
-  T* sl = reinterpret_cast<T*>(smem) + (size_t)warp * nslot * 32;
-  uint32_t* shist = reinterpret_cast<uint32_t*>(smem + (size_t)WPC * nslot * 32 * sizeof(T));
+  unsigned char* after = smem + sizeof(DProg);
+  T* sl = reinterpret_cast<T*>(after) + (size_t)warp * nslot * 32;
+  uint32_t* shist = reinterpret_cast<uint32_t*>(after + (size_t)WPC * nslot * 32 * sizeof(T));
   if (MODE == 0) {
     for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS) shist[i] = 0;
     __syncthreads();
@@ -189,11 +198,7 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __rest
             if (MODE == 1) {
               keys[cursor + (uint64_t)rank * G + j] = key;
             } else {
-              for (int p = 0; p < npass; ++p) {
-                const uint32_t dg = (uint32_t)(key >> (PB + 8 * p)) & 255u;
-                const unsigned peers = __match_any_sync(bal, dg);
-                if (lane == __ffs(peers) - 1) atomicAdd(&shist[p * 256 + dg], (uint32_t)__popc(peers));
-              }
+              for (int p = 0; p < npass; ++p) atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
             }
           }
         }
@@ -330,12 +335,13 @@ __global__ void __launch_bounds__(256) hist_scan_kernel(const uint64_t* __restri
 constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull << 54) - 1;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-__global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+__global__ void __launch_bounds__(RS_THREADS, 3) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                              const uint64_t* n_dev, uint64_t n_max, int shift,
                                                              const uint64_t* __restrict__ gbase, uint64_t* status,
                                                              unsigned long long* ticket, uint32_t epoch,
-                                                             uint64_t* err) {
+                                                             uint64_t* err, uint64_t* next_hist, int next_shift) {
   __shared__ uint32_t whist[RS_THREADS / 32][RS_RADIX];
+  __shared__ uint32_t nhist[RS_RADIX];  // digit counts of the next pass, over the tiles this CTA ranks
   __shared__ uint32_t tstart[RS_RADIX];
   __shared__ uint64_t gofs[RS_RADIX];
   __shared__ uint64_t ws[8];
@@ -345,6 +351,7 @@ __global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
   const uint64_t ep = (uint64_t)epoch << 56;
+  nhist[threadIdx.x] = 0;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1ull);
     for (int i = threadIdx.x; i < (RS_THREADS / 32) * RS_RADIX; i += RS_THREADS) (&whist[0][0])[i] = 0;
@@ -353,22 +360,25 @@ __global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __
     if (tile >= ntiles) break;
     const uint64_t base = tile * RS_TILE;
     const uint64_t wbase = base + (uint64_t)warp * (RS_KPT * 32);
+    static_assert(RS_THREADS == RS_RADIX, "one thread per digit");
     uint64_t k[RS_KPT];
-    uint32_t dg[RS_KPT], rk[RS_KPT];
+    uint32_t dr[RS_KPT];  // digit in bits 0..8 (256 = no key), warp-local rank above
 #pragma unroll
     for (int s = 0; s < RS_KPT; ++s) {
       const uint64_t i = wbase + (uint64_t)s * 32 + lane;
       k[s] = i < n ? in[i] : 0;
-      dg[s] = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
     }
+    const unsigned lt = lanemask_lt();
     // warp-level stable ranking, slot-major = memory order
 #pragma unroll
     for (int s = 0; s < RS_KPT; ++s) {
-      const uint32_t d = dg[s];
+      const uint64_t i = wbase + (uint64_t)s * 32 + lane;
+      const uint32_t d = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
+      if (next_hist && d < 256u) atomicAdd(&nhist[(uint32_t)(k[s] >> next_shift) & 255u], 1u);
       const unsigned peers = __match_any_sync(FULL, d);
       uint32_t old = 0;
       if (d < 256u) old = whist[warp][d];
-      rk[s] = old + __popc(peers & lanemask_lt());
+      dr[s] = d | ((old + __popc(peers & lt)) << 9);
       __syncwarp();
       if (d < 256u && lane == __ffs(peers) - 1) whist[warp][d] = old + __popc(peers);
       __syncwarp();
@@ -413,8 +423,8 @@ __global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < RS_KPT; ++s) {
-      const uint32_t d = dg[s];
-      if (d < 256u) stage[tstart[d] + whist[warp][d] + rk[s]] = k[s];
+      const uint32_t d = dr[s] & 511u;
+      if (d < 256u) stage[tstart[d] + whist[warp][d] + (dr[s] >> 9)] = k[s];
     }
     __syncthreads();
     const uint64_t cnt = (n - base) < (uint64_t)RS_TILE ? (n - base) : (uint64_t)RS_TILE;
@@ -425,102 +435,181 @@ __global__ void __launch_bounds__(RS_THREADS) onesweep_kernel(const uint64_t* __
     }
     __syncthreads();
   }
+  if (next_hist && nhist[threadIdx.x])
+    atomicAdd((unsigned long long*)&next_hist[threadIdx.x], (unsigned long long)nhist[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ conflict scan, phase A
+// One warp walks a range of CA_RANGE sorted keys, 32 keys per step, lane =
+// key.  Each lane compares its key with the previous one; ballots give the
+// run starts, sub-run (interval) starts, thread changes, block changes and
+// writers of the step, and bit arithmetic on those masks gives every run's
+// OR-reductions.  Flags of the run and sub-run still open at the end of a
+// step are carried to the next one.  A run belongs to the warp whose range
+// holds its first key; the warp reads past its range to finish that run.
+//   sub-run (same array, granule, interval) may race inside a block:
+//       it has a writer and two different threads;
+//   run (same array, granule) in global memory may race across blocks:
+//       it has a writer and two different blocks.
+__device__ __forceinline__ unsigned m_le(int l) { return l >= 31 ? FULL : ((2u << l) - 1u); }
+__device__ __forceinline__ unsigned m_lt(int l) { return l <= 0 ? 0u : (l >= 32 ? FULL : ((1u << l) - 1u)); }
+__device__ __forceinline__ int top_bit(unsigned m) { return m ? 31 - __clz(m) : -1; }
+
+struct CandCarry {
+  uint64_t prev, start;
+  bool owned, runW, runBD, runC, subW, subTD;
+};
+
+struct CandCtx {
+  uint64_t n, r0, r1, m_run, m_sub, m_thr, m_blk, g_lim;
+  uint32_t wmask, amask;
+  bool g_all;
+  unsigned below;
+  int lane;
+  uint64_t* cand;
+  uint64_t cand_cap;
+  uint64_t* counters;
+};
+
+// One 32-key step at position p (keys already loaded).  Returns true when the
+// warp is past its range and holds no open run of its own.
+__device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64_t k, uint64_t p) {
+  const int lane = X.lane;
+  const uint64_t i = p + lane;
+  const bool valid = i < X.n;
+  uint64_t pk = __shfl_up_sync(FULL, k, 1);
+  if (lane == 0) pk = c.prev;
+  const uint64_t x = k ^ pk;
+  const bool rs = valid && (i == 0 || (x & X.m_run) != 0);
+  const bool ss = valid && (rs || (x & X.m_sub) != 0);
+  const bool td = valid && !ss && (x & X.m_thr) != 0;
+  const bool bd = valid && !rs && (x & X.m_blk) != 0;
+  const bool w = valid && ((X.wmask >> ((uint32_t)k & X.amask)) & 1u);
+  const unsigned RS = __ballot_sync(FULL, rs), SS = __ballot_sync(FULL, ss), TD = __ballot_sync(FULL, td);
+  const unsigned BD = __ballot_sync(FULL, bd), WM = __ballot_sync(FULL, w);
+  const unsigned below = X.below;
+  // candidacy of the sub-run that ends just before this lane's sub-run start
+  const int t = top_bit(SS & below);
+  const unsigned rs_sub = t >= 0 ? (below & ~m_lt(t)) : below;
+  const bool subW = (WM & rs_sub) || (t < 0 && c.subW);
+  const bool subTD = (TD & rs_sub) || (t < 0 && c.subTD);
+  const unsigned CS = __ballot_sync(FULL, ss && subW && subTD);
+  // the run that ends just before this lane's run start
+  const int q = top_bit(RS & below);
+  const unsigned rw = q >= 0 ? (below & ~m_lt(q)) : below;            // [q, lane-1]
+  const unsigned rc = q >= 0 ? (m_le(lane) & ~m_le(q)) : m_le(lane);  // (q, lane]
+  const bool rW = (WM & rw) || (q < 0 && c.runW);
+  const bool rBD = (BD & rw) || (q < 0 && c.runBD);
+  const bool rC = (CS & rc) || (q < 0 && c.runC);
+  const uint64_t rstart = q >= 0 ? p + q : c.start;
+  const bool owned = q >= 0 ? (rstart >= X.r0 && rstart < X.r1) : c.owned;
+  const bool emit = rs && i > 0 && owned && (rC || ((X.g_all || pk < X.g_lim) && rW && rBD));
+  const unsigned EM = __ballot_sync(FULL, emit);
+  if (EM) {
+    uint64_t base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long*)&X.counters[C_NCAND], (unsigned long long)__popc(EM));
+    base = __shfl_sync(FULL, base, 0);
+    if (emit) {
+      const uint64_t g = base + __popc(EM & below);
+      if (g < X.cand_cap) {
+        X.cand[2 * g] = rstart;
+        X.cand[2 * g + 1] = i;
+      }
+    }
+  }
+  // carries for the next step
+  const int ql = top_bit(RS);
+  if (ql >= 0) {
+    c.start = p + ql;
+    c.owned = c.start >= X.r0 && c.start < X.r1;
+    c.runW = (WM & ~m_lt(ql)) != 0;
+    c.runBD = (BD & ~m_lt(ql)) != 0;
+    c.runC = (CS & ~m_le(ql)) != 0;
+  } else {
+    c.runW |= WM != 0;
+    c.runBD |= BD != 0;
+    c.runC |= CS != 0;
+  }
+  const int tl = top_bit(SS);
+  if (tl >= 0) {
+    c.subW = (WM & ~m_lt(tl)) != 0;
+    c.subTD = (TD & ~m_lt(tl)) != 0;
+  } else {
+    c.subW |= WM != 0;
+    c.subTD |= TD != 0;
+  }
+  const uint64_t rem = X.n - p;  // keys left from this step on
+  c.prev = __shfl_sync(FULL, k, rem >= 32 ? 31 : (int)rem - 1);
+  // a run longer than CA_LONG goes to the exact scan with its end unknown
+  if (c.owned && p + 32 - c.start > (uint64_t)CA_LONG) {
+    if (lane == 0) {
+      const uint64_t g = atomicAdd((unsigned long long*)&X.counters[C_NCAND], 1ull);
+      if (g < X.cand_cap) {
+        X.cand[2 * g] = c.start;
+        X.cand[2 * g + 1] = 0;
+      }
+    }
+    c.owned = false;
+  }
+  return p + 32 >= X.r1 && !c.owned;
+}
+
 __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                                const DProg* __restrict__ P, uint64_t* __restrict__ cand,
                                                                uint64_t cand_cap, uint64_t* counters) {
-  __shared__ uint64_t st[CA_THREADS * (CA_KPT + 1)];
-  __shared__ uint64_t sc[2 * 512];
-  __shared__ uint32_t scount;
-  __shared__ uint64_t sbase;
-  const uint64_t n = *n_dev;
+  CandCtx X;
+  X.lane = threadIdx.x & 31;
+  X.n = *n_dev;
   const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
   const int rsh = PB + IVB;
-  const uint32_t wmask = P->wmask;
+  X.wmask = P->wmask;
+  X.amask = AB ? (1u << AB) - 1u : 0u;
   const uint64_t shbase = P->shared_cell_base;
-  for (uint64_t tile = blockIdx.x; tile * CA_TILE < n; tile += gridDim.x) {
-    const uint64_t base = tile * CA_TILE;
-    if (threadIdx.x == 0) scount = 0;
-    for (int i = threadIdx.x; i < CA_TILE; i += CA_THREADS) {
-      const uint64_t idx = base + i;
-      st[(i >> 4) * (CA_KPT + 1) + (i & 15)] = idx < n ? keys[idx] : 0;
-    }
-    __syncthreads();
-    auto key_at = [&](uint64_t idx) -> uint64_t {
-      const uint64_t r = idx - base;
-      return r < (uint64_t)CA_TILE ? st[(r >> 4) * (CA_KPT + 1) + (r & 15)] : keys[idx];
-    };
-    const uint64_t c0 = base + (uint64_t)threadIdx.x * CA_KPT;
-    const uint64_t c1 = c0 + CA_KPT < n ? c0 + CA_KPT : n;
-    if (c0 < n) {
-      uint64_t j = c0;
-      if (c0 > 0) {
-        const uint64_t rprev = shr64(key_at(c0 - 1), rsh);
-        while (j < c1 && shr64(key_at(j), rsh) == rprev) ++j;
+  // field tests on k ^ previous key: run id, run+interval, block+thread, block
+  X.m_run = rsh >= 64 ? 0 : ~0ull << rsh;
+  X.m_sub = PB >= 64 ? 0 : ~0ull << PB;
+  X.m_thr = lowbits(~0ull, BB + TB) << AB;
+  X.m_blk = lowbits(~0ull, BB) << (AB + TB);
+  // keys below g_lim belong to global-memory runs
+  X.g_all = rsh >= 64 ? shbase > 0 : (rsh > 0 && shbase >= (1ull << (64 - rsh)));
+  X.g_lim = X.g_all ? ~0ull : (rsh >= 64 ? 0ull : shbase << rsh);
+  X.below = m_lt(X.lane);
+  X.cand = cand;
+  X.cand_cap = cand_cap;
+  X.counters = counters;
+  const uint64_t n = X.n;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t nranges = (n + CA_RANGE - 1) / CA_RANGE;
+  for (uint64_t rg = gw; rg < nranges; rg += nw) {
+    X.r0 = rg * CA_RANGE;
+    X.r1 = X.r0 + CA_RANGE;
+    CandCarry c;
+    c.prev = X.r0 > 0 ? keys[X.r0 - 1] : 0;
+    c.start = 0;
+    c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
+    bool done = false;
+    for (uint64_t p = X.r0; !done && p < n; p += 32 * CA_AHEAD) {
+      uint64_t kk[CA_AHEAD];
+#pragma unroll
+      for (int j = 0; j < CA_AHEAD; ++j) {
+        const uint64_t i = p + 32 * j + X.lane;
+        kk[j] = i < n ? keys[i] : 0;
       }
-      while (j < c1) {
-        const uint64_t s = j;
-        uint64_t prev = key_at(j);
-        const uint64_t rid = shr64(prev, rsh);
-        const bool glob = rid < shbase;
-        bool w = (wmask >> lowbits(prev, AB)) & 1u;
-        bool anyw_run = w, anyw_sub = w, thr_sub = false, blkdiff = false, cnd = false, lng = false;
-        ++j;
-        while (j < n) {
-          const uint64_t k2 = key_at(j);
-          if (shr64(k2, rsh) != rid) break;
-          if (j - s >= (uint64_t)CA_LONG) {
-            lng = true;
-            break;
-          }
-          if (shr64(k2, PB) != shr64(prev, PB)) {
-            cnd |= anyw_sub && thr_sub;
-            anyw_sub = false;
-            thr_sub = false;
-          } else {
-            thr_sub |= lowbits(k2 >> AB, BB + TB) != lowbits(prev >> AB, BB + TB);
-          }
-          blkdiff |= lowbits(k2 >> (AB + TB), BB) != lowbits(prev >> (AB + TB), BB);
-          w = (wmask >> lowbits(k2, AB)) & 1u;
-          anyw_sub |= w;
-          anyw_run |= w;
-          prev = k2;
-          ++j;
+#pragma unroll
+      for (int j = 0; j < CA_AHEAD; ++j)
+        if (!done && p + 32 * j < n) done = cand_step(X, c, kk[j], p + 32 * j);
+    }
+    if (!done && c.owned) {  // the array ended inside a run of this warp
+      const bool last = c.runC || (c.subW && c.subTD) || ((X.g_all || c.prev < X.g_lim) && c.runW && c.runBD);
+      if (last && X.lane == 0) {
+        const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
+        if (g < cand_cap) {
+          cand[2 * g] = c.start;
+          cand[2 * g + 1] = n;
         }
-        cnd |= anyw_sub && thr_sub;
-        if (glob) cnd |= anyw_run && blkdiff;
-        if (cnd || lng) {
-          const uint32_t slot = atomicAdd(&scount, 1u);
-          const uint64_t e = lng ? 0 : j;
-          if (slot < 512) {
-            sc[2 * slot] = s;
-            sc[2 * slot + 1] = e;
-          } else {
-            const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
-            if (g < cand_cap) {
-              cand[2 * g] = s;
-              cand[2 * g + 1] = e;
-            }
-          }
-        }
-        if (lng)
-          while (j < c1 && shr64(key_at(j), rsh) == rid) ++j;
       }
     }
-    __syncthreads();
-    const uint32_t m = scount < 512 ? scount : 512;
-    if (threadIdx.x == 0 && m) sbase = atomicAdd((unsigned long long*)&counters[C_NCAND], (unsigned long long)m);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += CA_THREADS) {
-      const uint64_t g = sbase + i;
-      if (g < cand_cap) {
-        cand[2 * g] = sc[2 * i];
-        cand[2 * g + 1] = sc[2 * i + 1];
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -701,7 +790,8 @@ cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_p
                           uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys, uint64_t* hist, int npass,
                           uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {
   const size_t esz = wide ? 8 : 4;
-  const size_t smem = (size_t)(EXP_THREADS / 32) * h_prog.nslot * 32 * esz + (mode == 0 ? (size_t)npass * 256 * 4 : 0);
+  const size_t smem = sizeof(DProg) + (size_t)(EXP_THREADS / 32) * h_prog.nslot * 32 * esz +
+                      (mode == 0 ? (size_t)npass * 256 * 4 : 0);
   const void* fn = nullptr;
   if (!wide) {
     fn = mode == 0   ? (const void*)expand_kernel<int32_t, 0>
@@ -753,12 +843,12 @@ cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gb
 
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
-                            uint64_t* err) {
+                            uint64_t* err, uint64_t* next_hist, int next_shift) {
   uint64_t tiles = (n_max + RS_TILE - 1) / RS_TILE;
   int grid = occupancy_grid((const void*)onesweep_kernel, RS_THREADS, 0, L.nsm);
   if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
   onesweep_kernel<<<grid, RS_THREADS, 0, L.s>>>(in, out, n_dev, n_max, shift, gbase, status,
-                                                (unsigned long long*)ticket, epoch, err);
+                                                (unsigned long long*)ticket, epoch, err, next_hist, next_shift);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -12,10 +12,10 @@ constexpr int RS_THREADS = 256;    // onesweep: 8 warps x 16 keys
 constexpr int RS_KPT = 16;
 constexpr int RS_TILE = RS_THREADS * RS_KPT;
 constexpr int RS_RADIX = 256;
-constexpr int CA_THREADS = 256;    // candidate scan: 16 consecutive keys per thread
-constexpr int CA_KPT = 16;
-constexpr int CA_TILE = CA_THREADS * CA_KPT;
-constexpr int CA_LONG = 4096;      // a run longer than this is handed to the exact scan unmeasured
+constexpr int CA_THREADS = 256;    // candidate scan
+constexpr int CA_LONG = 1 << 16;   // a run longer than this is handed to the exact scan unmeasured
+constexpr int CA_RANGE = 2048;     // keys owned by one warp of the candidate scan
+constexpr int CA_AHEAD = 4;        // 32-key steps loaded ahead by each warp
 constexpr int SCAN_TILE = 4096;
 constexpr int MAX_PASSES = 16;
 
@@ -48,10 +48,11 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
                              int npass, uint64_t* hist);
 // per-pass exclusive prefix of the digit counts
 cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass);
-// one stable onesweep pass on the digit at `shift`
+// one stable onesweep pass on the digit at `shift`; when next_hist is given,
+// also counts the digit at `next_shift` for the following pass
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
-                            uint64_t* err);
+                            uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0);
 
 // conflict scan, phase A: runs that may hold a race -> (start, end) list
 cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
