@@ -171,6 +171,45 @@ int hgrd_last_stats(hgrd_stats* s);
  * and the number of stages to *n. */
 int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n);
 
+/* ---- Batched check of many (kernel, binding) items ------------------------
+ * The host-code classes of Sec. 4 (a host loop bounding a parameter, class
+ * (4); several launch sites of one kernel) give many bound descriptors to
+ * check.  A batch runs them together: items whose keys fit on chip go to one
+ * persistent, work-queued kernel (a CTA checks a whole item in shared memory,
+ * largest items first); the others run the device-wide pipeline, spread over
+ * streams longest-first.  Verdicts are per item and exact (the same as
+ * hgrd_check on the item); only the first `witness_cap` canonical witnesses
+ * of each item are kept.  Items must stay alive and bound as they were at
+ * hgrd_batch_create until hgrd_batch_free. */
+typedef struct hgrd_batch hgrd_batch; /* opaque, library owned */
+typedef struct {
+  uint32_t small_keys;  /* items with at most this many keys run on chip (0 = 4096, the maximum) */
+  uint32_t streams;     /* streams: one for the on-chip kernel plus large-item streams (0 = 4, 2..16) */
+  uint32_t witness_cap; /* canonical witnesses kept per item (0 = 64) */
+  uint32_t flags;       /* HGRD_BATCH_GRAPH: capture the whole batch into a CUDA graph on the first
+                           run and replay it on later runs with the same workspace and stream */
+} hgrd_batch_opts;
+enum { HGRD_BATCH_GRAPH = 1 };
+typedef struct {
+  int32_t status;   /* HGRD_OK, or HGRD_ENOMEM (a witness buffer overflowed: rerun with hgrd_check) */
+  int32_t racy, small, n_copied;
+  uint64_t n_witness, n_by_kind[3], n_instances, n_keys, n_oob;
+} hgrd_item_verdict;
+
+int hgrd_batch_create(const hgrd_desc* const* items, uint32_t n, const hgrd_batch_opts* o, hgrd_batch** out);
+int hgrd_batch_workspace_size(const hgrd_batch* b, size_t* bytes);
+/* Enqueue the whole batch on `cuda_stream` (no host synchronisation). */
+int hgrd_batch_run(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_stream);
+/* Wait for the stream and read every item's verdict (v[n]) and its first
+ * min(wcap, witness_cap) witnesses (w[n * wcap], item i at w + i * wcap). */
+int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_item_verdict* v,
+                       hgrd_witness* w, uint32_t wcap);
+/* Autotuner: times the batch under each (small-item threshold, stream count)
+ * in {0, 1024, 4096} x {2, 4, 8, 16}, keeps the fastest for later runs and
+ * reports it in *chosen (may be NULL). */
+int hgrd_batch_tune(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_batch_opts* chosen);
+void hgrd_batch_free(hgrd_batch* b);
+
 /* hgrd_check without a caller workspace, for callers that cannot allocate
  * device memory: code running while another component owns all device memory
  * (a caching allocator or pool that must not be bypassed), code called from

@@ -22,7 +22,9 @@ PROFILE = 2
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
            "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile", "hgrd_free_desc", "hgrd_last_error",
-           "hgrd_debug_divmod", "hgrd_check_noalloc"]
+           "hgrd_debug_divmod", "hgrd_check_noalloc", "hgrd_batch_create", "hgrd_batch_workspace_size",
+           "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free"]
+BATCH_GRAPH = 1
 
 
 class HgrdError(RuntimeError):
@@ -56,6 +58,17 @@ class CheckOpts(C.Structure):
     _fields_ = [("max_raw_witness", C.c_uint64), ("pair_cap", C.c_uint32), ("flags", C.c_uint32)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("small_keys", C.c_uint32), ("streams", C.c_uint32), ("witness_cap", C.c_uint32),
+                ("flags", C.c_uint32)]
+
+
+class ItemVerdict(C.Structure):
+    _fields_ = [("status", C.c_int32), ("racy", C.c_int32), ("small", C.c_int32), ("n_copied", C.c_int32),
+                ("n_witness", C.c_uint64), ("n_by_kind", C.c_uint64 * 3), ("n_instances", C.c_uint64),
+                ("n_keys", C.c_uint64), ("n_oob", C.c_uint64)]
+
+
 class StageTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_float)]
 
@@ -86,6 +99,16 @@ def lib():
                                          C.POINTER(Verdict)]
         L.hgrd_check_noalloc.argtypes = [vp, C.POINTER(CheckOpts), vp, C.POINTER(Witness), u64, C.POINTER(Verdict)]
         L.hgrd_check_noalloc.restype = C.c_int
+        L.hgrd_batch_create.argtypes = [C.POINTER(vp), C.c_uint32, C.POINTER(BatchOpts), C.POINTER(vp)]
+        L.hgrd_batch_workspace_size.argtypes = [vp, C.POINTER(sz)]
+        L.hgrd_batch_run.argtypes = [vp, vp, sz, vp]
+        L.hgrd_batch_collect.argtypes = [vp, vp, sz, vp, C.POINTER(ItemVerdict), C.POINTER(Witness), C.c_uint32]
+        L.hgrd_batch_tune.argtypes = [vp, vp, sz, vp, C.POINTER(BatchOpts)]
+        L.hgrd_batch_free.argtypes = [vp]
+        L.hgrd_batch_free.restype = None
+        for f in ["hgrd_batch_create", "hgrd_batch_workspace_size", "hgrd_batch_run", "hgrd_batch_collect",
+                  "hgrd_batch_tune"]:
+            getattr(L, f).restype = C.c_int
         L.hgrd_last_stats.argtypes = [C.POINTER(Stats)]
         L.hgrd_last_profile.argtypes = [C.POINTER(StageTime), C.c_uint32, C.POINTER(C.c_uint32)]
         L.hgrd_free_desc.argtypes = [vp]
@@ -229,6 +252,79 @@ class Kernel:
         return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
                       [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
                       rc == ETRUNCATED)
+
+
+@dataclass
+class ItemResult:
+    status: int
+    racy: bool
+    small: bool
+    n_witness: int
+    n_by_kind: tuple
+    n_instances: int
+    n_keys: int
+    n_oob: int
+    witnesses: list   # first min(witness_cap, n_witness) canonical witnesses
+
+
+class Batch:
+    """Many bound kernels checked together (hgrd_batch_*).  Keeps its kernels alive."""
+
+    def __init__(self, kernels, small_keys=0, streams=0, witness_cap=64, graph=False):
+        self.kernels = list(kernels)
+        arr = (C.c_void_p * len(self.kernels))(*[k._h.value for k in self.kernels])
+        o = BatchOpts(small_keys, streams, witness_cap, BATCH_GRAPH if graph else 0)
+        h = C.c_void_p()
+        _raise(lib().hgrd_batch_create(arr, len(self.kernels), C.byref(o), C.byref(h)))
+        self._h = h
+        self.witness_cap = witness_cap
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hgrd_batch_free(h)
+            self._h = None
+
+    def workspace(self, device="cuda"):
+        import torch
+        n = C.c_size_t()
+        _raise(lib().hgrd_batch_workspace_size(self._h, C.byref(n)))
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = None
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def run(self, stream=None):
+        ws = self.workspace()
+        _raise(lib().hgrd_batch_run(self._h, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+
+    def collect(self, stream=None):
+        ws = self.workspace()
+        n = len(self.kernels)
+        v = (ItemVerdict * n)()
+        wc = self.witness_cap
+        w = (Witness * max(1, n * wc))()
+        rc = lib().hgrd_batch_collect(self._h, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), v, w, wc)
+        if rc < 0 and rc != -6:
+            _raise(rc)
+        out = []
+        for i in range(n):
+            x = v[i]
+            out.append(ItemResult(x.status, bool(x.racy), bool(x.small), x.n_witness, tuple(x.n_by_kind),
+                                  x.n_instances, x.n_keys, x.n_oob,
+                                  [_wt(w[i * wc + k]) for k in range(x.n_copied)]))
+        return out
+
+    def check(self, stream=None):
+        self.run(stream)
+        return self.collect(stream)
+
+    def tune(self, stream=None) -> dict:
+        ws = self.workspace()
+        o = BatchOpts()
+        _raise(lib().hgrd_batch_tune(self._h, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), C.byref(o)))
+        return {"small_keys": o.small_keys, "streams": o.streams}
 
 
 def stats() -> dict:

@@ -117,7 +117,8 @@ int prechecks(const hgrd_desc* d, void* d_ws, size_t ws_bytes, const hgrd_check_
   return HGRD_OK;
 }
 
-int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
+            const DProg* dprog_resident = nullptr) {
   Layout W;
   int rc = prechecks(d, d_ws, ws_bytes, o, &W);
   if (rc) return rc;
@@ -126,7 +127,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   char* ws = (char*)d_ws;
   auto U = [&](size_t off) { return (uint64_t*)(ws + off); };
   uint64_t* cnt = U(W.counters);
-  DProg* dprog = (DProg*)(ws + W.prog);
+  // the compiled program: uploaded into the workspace, or already resident
+  const DProg* dprog = dprog_resident ? dprog_resident : (const DProg*)(ws + W.prog);
   g_stats = hgrd_stats{};
   g_stats.int64_path = B.wide;
   g_stats.sort_passes = (uint32_t)B.sort_passes;
@@ -139,8 +141,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
-  CK(cudaMemcpyAsync(dprog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
-  g_stats.h2d_bytes += sizeof(DProg);
+  if (!dprog_resident) {
+    CK(cudaMemcpyAsync(ws + W.prog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    g_stats.h2d_bytes += sizeof(DProg);
+  }
   g_prof.mark("setup");
 
   const int P = B.sort_passes;
@@ -329,6 +333,23 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
 }
 
 }  // namespace
+
+// entry points for the batched path (batch.cu)
+size_t item_workspace_bytes(const Bound& B, const hgrd_check_opts* o) { return layout(B, o).total; }
+
+int item_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* ws, size_t bytes, cudaStream_t s,
+                 const DProg* dprog_resident, uint64_t** counters, const uint64_t** uniq, uint64_t* raw_cap,
+                 uint64_t* cand_cap) {
+  int rc = enqueue(d, o, ws, bytes, s, dprog_resident);
+  if (rc) return rc;
+  const Layout W = layout(*d->bound, o);
+  *counters = (uint64_t*)((char*)ws + W.counters);
+  *uniq = uniq_buffer(d, W, (char*)ws);
+  *raw_cap = W.raw_cap;
+  *cand_cap = std::max<uint64_t>(d->bound->nkeys_max / 2, 1);
+  return HGRD_OK;
+}
+
 }  // namespace hgrd
 
 using namespace hgrd;

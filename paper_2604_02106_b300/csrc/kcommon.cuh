@@ -1,0 +1,251 @@
+// Device code shared by the single-check kernels (kernels.cu) and the batched
+// kernels (batch.cu): evaluation of the compiled affine program, the
+// expansion of one simulated warp, and the exact scan of one run.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace hgrd {
+namespace dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t shr64(uint64_t x, int s) { return s >= 64 ? 0 : x >> s; }
+__device__ __forceinline__ uint64_t lowbits(uint64_t x, int n) { return n >= 64 ? x : (x & ((1ull << n) - 1)); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T divq(T n, const Magic& g);
+template <>
+__device__ __forceinline__ int32_t divq<int32_t>(int32_t n, const Magic& g) {
+  return magic_div32(n, g);
+}
+template <>
+__device__ __forceinline__ int64_t divq<int64_t>(int64_t n, const Magic& g) {
+  return magic_div64(n, g);
+}
+
+// c0 + sum(coef * slot) over the lane's column of the warp's slot file
+template <typename T>
+__device__ __forceinline__ T lin_eval(const DProg* __restrict__ P, const DLin& L, const T* sl, int lane) {
+  T v = (T)L.c0;
+  for (int t = 0; t < L.n; ++t) {
+    const DTerm tm = P->term[L.first + t];
+    v += (T)tm.coef * sl[tm.slot * 32 + lane];
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void run_ops(const DProg* __restrict__ P, int first, int count, T* sl, int lane) {
+  for (int k = first; k < first + count; ++k) {
+    const DOp op = P->ops[k];
+    T v = lin_eval<T>(P, op.lin, sl, lane);
+    if (op.kind == OP_DIV) {
+      v = divq<T>(v, op.mg);
+    } else if (op.kind == OP_MOD) {
+      v = v - divq<T>(v, op.mg) * (T)op.d;
+    }
+    sl[op.dst * 32 + lane] = v;
+  }
+}
+
+// Expansion of unit u = (block b, warp w of the block) of the user kernel,
+// lane = simulated thread.  For every loop vector and every access in `only`
+// (bit per access id), evaluates guards and index and calls
+//   step(a, A, inb, bal, idx, iv, b, lt, ic)
+// whenever some lane of the warp holds a live in-bounds instance (inb for
+// this lane, bal = ballot of inb).  Returns this lane's live instances that
+// fell outside their array.
+template <typename T, typename Step>
+__device__ __forceinline__ uint64_t expand_unit(const DProg* __restrict__ P, T* sl, int lane, int64_t u,
+                                                uint32_t only, Step&& step) {
+  const int nthr = P->nthr, wpb = P->wpb, nacc = P->nacc, nloop = P->nloop;
+  const int bdx = P->block[0], bdy = P->block[1];
+  const int64_t gdx = P->grid[0], gdy = P->grid[1];
+  const int64_t nit = P->nit;
+  const int64_t b = u / wpb;
+  const int lt = (int)(u - b * wpb) * 32 + lane;
+  const bool act = lt < nthr;
+  sl[0 * 32 + lane] = (T)(lt % bdx);
+  sl[1 * 32 + lane] = (T)((lt / bdx) % bdy);
+  sl[2 * 32 + lane] = (T)(lt / (bdx * bdy));
+  sl[3 * 32 + lane] = (T)(b % gdx);
+  sl[4 * 32 + lane] = (T)((b / gdx) % gdy);
+  sl[5 * 32 + lane] = (T)(b / (gdx * gdy));
+  for (int l = 0; l < MAXLOOP; ++l) sl[(6 + l) * 32 + lane] = 0;
+  run_ops<T>(P, 0, P->nfix, sl, lane);
+  uint64_t oob = 0;
+  int32_t ic[MAXLOOP] = {0, 0, 0, 0};
+  for (int64_t it = 0; it < nit; ++it) {
+    if (it > 0) {
+      int l = nloop - 1;
+      while (l >= 0) {
+        if (++ic[l] < P->ub[l]) break;
+        ic[l] = 0;
+        --l;
+      }
+    }
+    for (int l = 0; l < nloop; ++l) sl[(6 + l) * 32 + lane] = (T)ic[l];
+    run_ops<T>(P, P->nfix, P->niter, sl, lane);
+    for (int a = 0; a < nacc; ++a) {
+      const DAcc& A = P->acc[a];
+      if (A.dead || !((only >> a) & 1u)) continue;
+      bool live = act;
+      const int ng = A.ng, gf = A.gfirst;
+      for (int g = 0; g < ng; ++g) {
+        const DLin gl = P->guard[gf + g];
+        live = live && lin_eval<T>(P, gl, sl, lane) >= 0;
+      }
+      const DLin il = A.idx;
+      const T idx = lin_eval<T>(P, il, sl, lane);
+      const bool inb = live && (A.bounds_free || (idx >= 0 && (int64_t)idx <= A.maxidx));
+      oob += (live && !inb) ? 1 : 0;
+      const unsigned bal = __ballot_sync(FULL, inb);
+      if (bal == 0) continue;
+      int64_t iv = 0;
+      if (inb) {
+        const DLin vl = A.iv;
+        iv = (int64_t)lin_eval<T>(P, vl, sl, lane);
+      }
+      step(a, A, inb, bal, (int64_t)idx, iv, b, lt, ic);
+    }
+  }
+  return oob;
+}
+
+// granule j of a live in-bounds instance as a sort key:
+// ((cell << IVB | interval - ivmin) << PB) | block << (TB+AB) | thread << AB | access
+__device__ __forceinline__ uint64_t make_key(const DProg* __restrict__ P, const DAcc& A, int a, int64_t idx,
+                                             int64_t iv, int64_t b, int lt, int j) {
+  const uint64_t cell = A.cbase + (A.shared ? (uint64_t)b * A.ngran : 0ull) + (uint64_t)idx * (uint64_t)A.G + j;
+  const uint64_t ivc = (uint64_t)(iv - P->ivmin);
+  return (((cell << P->IVB) | ivc) << P->PB) | ((uint64_t)b << (P->TB + P->AB)) | ((uint64_t)lt << P->AB) |
+         (uint64_t)a;
+}
+
+// min / max of one id over a group of instances
+struct Sum {
+  bool p;
+  uint32_t lo, hi;
+  __device__ __forceinline__ void reset() { p = false; }
+  __device__ __forceinline__ void add(uint32_t v) {
+    if (!p) {
+      p = true;
+      lo = hi = v;
+    } else {
+      lo = v < lo ? v : lo;
+      hi = v > hi ? v : hi;
+    }
+  }
+};
+
+// lane = access a: the accesses b present in the group that form a pair with
+// two different ids among their instances (every present b, unless a and b
+// are both one and the same single id)
+__device__ __forceinline__ uint32_t racy_row(const Sum& s, int lane) {
+  const unsigned P = __ballot_sync(FULL, s.p);
+  if (!P) return 0;
+  const bool single = s.p && s.lo == s.hi;
+  const unsigned S = __ballot_sync(FULL, single);
+  const unsigned eq = __match_any_sync(FULL, single ? s.lo : (0x80000000u | (unsigned)lane));
+  const unsigned nonr = single ? (eq & S) : 0u;
+  return s.p ? (P & ~nonr) : 0u;
+}
+
+// Exact race kinds of the run starting at key s (end e, or 0 = until the run
+// id changes) of sorted keys[0, n).  Lane a gets, for each access b, whether
+// the pair (a, b) races across blocks (global memory, any interval), inside a
+// block between warps, or inside a warp, in the same interval (Table 2).
+struct RunMasks {
+  uint64_t rid;
+  uint32_t inter, blk, warp;
+};
+__device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, uint64_t e, uint64_t n,
+                                              const DProg* __restrict__ P, int lane, uint32_t einter,
+                                              uint32_t eintra) {
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
+  const int rsh = PB + IVB;
+  RunMasks R;
+  R.rid = shr64(keys[s], rsh);
+  const bool glob = R.rid < P->shared_cell_base;
+  Sum tw, wb, br;  // thread per (iv, block, warp); warp per (iv, block); block per run
+  tw.reset();
+  wb.reset();
+  br.reset();
+  uint32_t m_inter = 0, m_blk = 0, m_warp = 0;
+  uint64_t cur_sub = ~0ull;
+  uint32_t cur_b = 0xffffffffu, cur_w = 0xffffffffu;
+  for (uint64_t pos = s;; pos += 32) {
+    const uint64_t i = pos + lane;
+    const bool ok = i < n && (e == 0 || i < e);
+    const uint64_t kk = ok ? keys[i] : 0;
+    const bool inrun = ok && shr64(kk, rsh) == R.rid;
+    const unsigned m = __ballot_sync(FULL, inrun);
+    const int cnt = __popc(m);
+    for (int jj = 0; jj < cnt; ++jj) {
+      const uint64_t key = __shfl_sync(FULL, kk, jj);
+      const uint64_t sub = shr64(key, PB);
+      const uint32_t b = (uint32_t)lowbits(key >> (AB + TB), BB);
+      const uint32_t t = (uint32_t)lowbits(key >> AB, TB);
+      const uint32_t wpi = t >> 5;
+      const uint32_t a = (uint32_t)lowbits(key, AB);
+      if (sub != cur_sub || b != cur_b) {
+        m_warp |= racy_row(tw, lane) & eintra;
+        m_blk |= racy_row(wb, lane) & eintra;
+        tw.reset();
+        wb.reset();
+        cur_sub = sub;
+        cur_b = b;
+        cur_w = wpi;
+      } else if (wpi != cur_w) {
+        m_warp |= racy_row(tw, lane) & eintra;
+        tw.reset();
+        cur_w = wpi;
+      }
+      if ((uint32_t)lane == a) {
+        tw.add(t);
+        wb.add(wpi);
+        br.add(b);
+      }
+    }
+    if (cnt < 32) break;
+  }
+  m_warp |= racy_row(tw, lane) & eintra;
+  m_blk |= racy_row(wb, lane) & eintra;
+  if (glob) m_inter |= racy_row(br, lane) & einter;
+  R.inter = m_inter;
+  R.blk = m_blk;
+  R.warp = m_warp;
+  return R;
+}
+
+// (space, array, granule) of run id `rid` in the array layout
+__device__ __forceinline__ void run_location(const DProg* __restrict__ P, uint64_t rid, uint32_t* space, uint32_t* arr,
+                                             uint64_t* gran) {
+  int li = 0;
+  while (li + 1 < P->nlay && P->lay_cbase[li + 1] <= rid) ++li;
+  const uint64_t cell = rid - P->lay_cbase[li];
+  const bool sh = P->lay_shared[li];
+  *gran = sh ? cell % P->lay_ngran[li] : cell;
+  *arr = (uint32_t)P->lay_arr[li];
+  *space = sh ? 1u : 0u;
+}
+
+// witness words of lane a for accesses b >= a; `n` counts them
+__device__ __forceinline__ uint32_t witness_row(const RunMasks& R, int lane) {
+  const uint32_t ge = lane == 0 ? FULL : ~((1u << lane) - 1u);
+  return (R.inter | R.blk | R.warp) & ge;
+}
+__device__ __forceinline__ uint32_t witness_kind(const RunMasks& R, int b) {
+  return ((R.inter >> b) & 1u) | (((R.blk >> b) & 1u) << 1) | (((R.warp >> b) & 1u) << 2);
+}
+
+}  // namespace dev
+}  // namespace hgrd

@@ -19,16 +19,13 @@
 //  witness    merge per-run witnesses into the canonical set.
 #include <cuda_runtime.h>
 
-#include "kernels.cuh"
+#include "kcommon.cuh"
 
 namespace hgrd {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ uint64_t shr64(uint64_t x, int s) { return s >= 64 ? 0 : x >> s; }
-__device__ __forceinline__ uint64_t lowbits(uint64_t x, int n) { return n >= 64 ? x : (x & ((1ull << n) - 1)); }
+using namespace dev;
 
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
   uint64_t v;
@@ -37,47 +34,6 @@ __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
 }
 __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-template <typename T>
-__device__ __forceinline__ T divq(T n, const Magic& g);
-template <>
-__device__ __forceinline__ int32_t divq<int32_t>(int32_t n, const Magic& g) {
-  return magic_div32(n, g);
-}
-template <>
-__device__ __forceinline__ int64_t divq<int64_t>(int64_t n, const Magic& g) {
-  return magic_div64(n, g);
-}
-
-// c0 + sum(coef * slot) over the lane's column of the warp's slot file
-template <typename T>
-__device__ __forceinline__ T lin_eval(const DProg* __restrict__ P, const DLin& L, const T* sl, int lane) {
-  T v = (T)L.c0;
-  for (int t = 0; t < L.n; ++t) {
-    const DTerm tm = P->term[L.first + t];
-    v += (T)tm.coef * sl[tm.slot * 32 + lane];
-  }
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ void run_ops(const DProg* __restrict__ P, int first, int count, T* sl, int lane) {
-  for (int k = first; k < first + count; ++k) {
-    const DOp op = P->ops[k];
-    T v = lin_eval<T>(P, op.lin, sl, lane);
-    if (op.kind == OP_DIV) {
-      v = divq<T>(v, op.mg);
-    } else if (op.kind == OP_MOD) {
-      v = v - divq<T>(v, op.mg) * (T)op.d;
-    }
-    sl[op.dst * 32 + lane] = v;
-  }
 }
 
 // ------------------------------------------------------------------ expand
@@ -118,93 +74,49 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __rest
     t_lo = (uint32_t)(w0 >> 8) & 31;
     t_hi = (uint32_t)(w0 >> 3) & 31;
   }
-  const int nthr = P->nthr, wpb = P->wpb, nacc = P->nacc, nloop = P->nloop;
-  const int bdx = P->block[0], bdy = P->block[1];
-  const int64_t gdx = P->grid[0], gdy = P->grid[1];
-  const int64_t nit = P->nit, nunits = P->nunits;
-  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB;
-  const int64_t ivmin = P->ivmin;
+  const int64_t nunits = P->nunits;
+  const int PB = P->PB;
   uint64_t oob = 0;
-  for (int l = 0; l < MAXLOOP; ++l) sl[(6 + l) * 32 + lane] = 0;
+  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : 0xffffffffu;
   for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
-    const int64_t b = u / wpb;
-    const int lt = (int)(u - b * wpb) * 32 + lane;
-    const bool act = lt < nthr;
-    sl[0 * 32 + lane] = (T)(lt % bdx);
-    sl[1 * 32 + lane] = (T)((lt / bdx) % bdy);
-    sl[2 * 32 + lane] = (T)(lt / (bdx * bdy));
-    sl[3 * 32 + lane] = (T)(b % gdx);
-    sl[4 * 32 + lane] = (T)((b / gdx) % gdy);
-    sl[5 * 32 + lane] = (T)(b / (gdx * gdy));
-    run_ops<T>(P, 0, P->nfix, sl, lane);
-    const uint64_t payload = ((uint64_t)b << (TB + AB)) | ((uint64_t)lt << AB);
     uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
-    int32_t ic[MAXLOOP] = {0, 0, 0, 0};
-    for (int64_t it = 0; it < nit; ++it) {
-      if (it > 0) {
-        int l = nloop - 1;
-        while (l >= 0) {
-          if (++ic[l] < P->ub[l]) break;
-          ic[l] = 0;
-          --l;
-        }
-      }
-      for (int l = 0; l < nloop; ++l) sl[(6 + l) * 32 + lane] = (T)ic[l];
-      run_ops<T>(P, P->nfix, P->niter, sl, lane);
-      for (int a = 0; a < nacc; ++a) {
-        const DAcc& A = P->acc[a];
-        if (A.dead) continue;
-        if (MODE == 2 && (uint32_t)a != t_lo && (uint32_t)a != t_hi) continue;
-        bool live = act;
-        const int ng = A.ng, gf = A.gfirst;
-        for (int g = 0; g < ng; ++g) {
-          const DLin gl = P->guard[gf + g];
-          live = live && lin_eval<T>(P, gl, sl, lane) >= 0;
-        }
-        const DLin il = A.idx;
-        const T idx = lin_eval<T>(P, il, sl, lane);
-        const bool inb = live && (A.bounds_free || (idx >= 0 && (int64_t)idx <= A.maxidx));
-        if (MODE == 0) oob += (live && !inb) ? 1 : 0;
-        const unsigned bal = __ballot_sync(FULL, inb);
-        if (bal == 0) continue;
-        const int G = A.G;
-        if (MODE == 2) {
-          if (inb) {
-            const uint64_t g0 = (uint64_t)idx * (uint64_t)G;
-            if ((uint32_t)A.arr == t_arr && t_gran >= g0 && t_gran < g0 + (uint64_t)G) {
-              const uint64_t slot = atomicAdd((unsigned long long*)&counters[C_NPAIR], 1ull);
-              if (slot < pair_cap) {
-                PairRec r;
-                r.blk = (uint32_t)b;
-                r.thr = (uint32_t)lt;
-                for (int l = 0; l < MAXLOOP; ++l) r.it[l] = (uint32_t)ic[l];
-                r.acc = a;
-                r.pad = 0;
-                const DLin vl = A.iv;
-                r.iv = (int64_t)lin_eval<T>(P, vl, sl, lane);
-                pairs[slot] = r;
-              }
-            }
-          }
-          continue;
-        }
-        if (inb) {
-          const DLin vl = A.iv;
-          const uint64_t ivc = (uint64_t)((int64_t)lin_eval<T>(P, vl, sl, lane) - ivmin);
-          const uint64_t cell0 = A.cbase + (A.shared ? (uint64_t)b * A.ngran : 0ull) + (uint64_t)idx * (uint64_t)G;
-          const int rank = __popc(bal & lanemask_lt());
-          for (int j = 0; j < G; ++j) {
-            const uint64_t key = ((((cell0 + j) << IVB) | ivc) << PB) | payload | (uint64_t)a;
-            if (MODE == 1) {
-              keys[cursor + (uint64_t)rank * G + j] = key;
-            } else {
-              for (int p = 0; p < npass; ++p) atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
-            }
-          }
-        }
-        cursor += (uint64_t)__popc(bal) * G;
-      }
-    }
+    oob += expand_unit<T>(P, sl, lane, u, only,
+                          [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b,
+                              int lt, const int32_t* ic) {
+                            const int G = A.G;
+                            if (MODE == 2) {
+                              if (inb) {
+                                const uint64_t g0 = (uint64_t)idx * (uint64_t)G;
+                                if ((uint32_t)A.arr == t_arr && t_gran >= g0 && t_gran < g0 + (uint64_t)G) {
+                                  const uint64_t slot = atomicAdd((unsigned long long*)&counters[C_NPAIR], 1ull);
+                                  if (slot < pair_cap) {
+                                    PairRec r;
+                                    r.blk = (uint32_t)b;
+                                    r.thr = (uint32_t)lt;
+                                    for (int l = 0; l < MAXLOOP; ++l) r.it[l] = (uint32_t)ic[l];
+                                    r.acc = a;
+                                    r.pad = 0;
+                                    r.iv = iv;
+                                    pairs[slot] = r;
+                                  }
+                                }
+                              }
+                              return;
+                            }
+                            if (inb) {
+                              const int rank = __popc(bal & lanemask_lt());
+                              for (int j = 0; j < G; ++j) {
+                                const uint64_t key = make_key(P, A, a, idx, iv, b, lt, j);
+                                if (MODE == 1) {
+                                  keys[cursor + (uint64_t)rank * G + j] = key;
+                                } else {
+                                  for (int p = 0; p < npass; ++p)
+                                    atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
+                                }
+                              }
+                            }
+                            cursor += (uint64_t)__popc(bal) * G;
+                          });
     if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
   }
   if (MODE == 0) {
@@ -614,33 +526,6 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
 }
 
 // ------------------------------------------------------------------ conflict scan, phase B
-struct Sum {
-  bool p;
-  uint32_t lo, hi;
-  __device__ __forceinline__ void reset() { p = false; }
-  __device__ __forceinline__ void add(uint32_t v) {
-    if (!p) {
-      p = true;
-      lo = hi = v;
-    } else {
-      lo = v < lo ? v : lo;
-      hi = v > hi ? v : hi;
-    }
-  }
-};
-
-// pairs (this lane's access a, access b) with two different ids among their
-// instances: every b present unless a and b are both one and the same id
-__device__ __forceinline__ uint32_t racy_row(const Sum& s, int lane) {
-  const unsigned P = __ballot_sync(FULL, s.p);
-  if (!P) return 0;
-  const bool single = s.p && s.lo == s.hi;
-  const unsigned S = __ballot_sync(FULL, single);
-  const unsigned eq = __match_any_sync(FULL, single ? s.lo : (0x80000000u | (unsigned)lane));
-  const unsigned nonr = single ? (eq & S) : 0u;
-  return s.p ? (P & ~nonr) : 0u;
-}
-
 __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                     const DProg* __restrict__ P, const uint64_t* __restrict__ cand,
                                                     uint64_t cand_cap, uint64_t* __restrict__ raw, uint64_t raw_cap,
@@ -649,65 +534,13 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
   const uint64_t n = *n_dev;
   uint64_t ncand = counters[C_NCAND];
   if (ncand > cand_cap) ncand = cand_cap;
-  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
-  const int rsh = PB + IVB;
   const uint32_t einter = lane < P->nacc ? P->einter[lane] : 0u;
   const uint32_t eintra = lane < P->nacc ? P->eintra[lane] : 0u;
-  const uint64_t shbase = P->shared_cell_base;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t c = gw; c < ncand; c += nw) {
-    const uint64_t s = cand[2 * c], e = cand[2 * c + 1];
-    const uint64_t rid = shr64(keys[s], rsh);
-    const bool glob = rid < shbase;
-    Sum tw, wb, br;  // thread per (iv, block, warp); warp per (iv, block); block per run
-    tw.reset();
-    wb.reset();
-    br.reset();
-    uint32_t m_inter = 0, m_blk = 0, m_warp = 0;
-    uint64_t cur_sub = ~0ull;
-    uint32_t cur_b = 0xffffffffu, cur_w = 0xffffffffu;
-    for (uint64_t pos = s;; pos += 32) {
-      const uint64_t i = pos + lane;
-      const bool ok = i < n && (e == 0 || i < e);
-      const uint64_t kk = ok ? keys[i] : 0;
-      const bool inrun = ok && shr64(kk, rsh) == rid;
-      const unsigned m = __ballot_sync(FULL, inrun);
-      const int cnt = __popc(m);
-      for (int jj = 0; jj < cnt; ++jj) {
-        const uint64_t key = __shfl_sync(FULL, kk, jj);
-        const uint64_t sub = shr64(key, PB);
-        const uint32_t b = (uint32_t)lowbits(key >> (AB + TB), BB);
-        const uint32_t t = (uint32_t)lowbits(key >> AB, TB);
-        const uint32_t wpi = t >> 5;
-        const uint32_t a = (uint32_t)lowbits(key, AB);
-        if (sub != cur_sub || b != cur_b) {
-          m_warp |= racy_row(tw, lane) & eintra;
-          m_blk |= racy_row(wb, lane) & eintra;
-          tw.reset();
-          wb.reset();
-          cur_sub = sub;
-          cur_b = b;
-          cur_w = wpi;
-        } else if (wpi != cur_w) {
-          m_warp |= racy_row(tw, lane) & eintra;
-          tw.reset();
-          cur_w = wpi;
-        }
-        if ((uint32_t)lane == a) {
-          tw.add(t);
-          wb.add(wpi);
-          br.add(b);
-        }
-      }
-      if (cnt < 32) break;
-    }
-    m_warp |= racy_row(tw, lane) & eintra;
-    m_blk |= racy_row(wb, lane) & eintra;
-    if (glob) m_inter |= racy_row(br, lane) & einter;
-    // emit (lane, b >= lane) witnesses
-    const uint32_t ge = lane == 0 ? FULL : ~((1u << lane) - 1u);
-    uint32_t row = (m_inter | m_blk | m_warp) & ge;
+    const RunMasks R = exact_run(keys, cand[2 * c], cand[2 * c + 1], n, P, lane, einter, eintra);
+    uint32_t row = witness_row(R, lane);
     const uint32_t cntw = (uint32_t)__popc(row);
     uint32_t incl = cntw;
     for (int o = 1; o < 32; o <<= 1) {
@@ -719,19 +552,14 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
     uint64_t wbase = 0;
     if (lane == 0) wbase = atomicAdd((unsigned long long*)&counters[C_NRAW], (unsigned long long)total);
     wbase = __shfl_sync(FULL, wbase, 0);
-    // location of the run
-    int li = 0;
-    while (li + 1 < P->nlay && P->lay_cbase[li + 1] <= rid) ++li;
-    const uint64_t cell = rid - P->lay_cbase[li];
-    const bool sh = P->lay_shared[li];
-    const uint64_t gran = sh ? cell % P->lay_ngran[li] : cell;
-    const uint32_t arr = (uint32_t)P->lay_arr[li];
+    uint32_t space, arr;
+    uint64_t gran;
+    run_location(P, R.rid, &space, &arr, &gran);
     uint64_t o = wbase + incl - cntw;
     while (row) {
       const int bb = __ffs(row) - 1;
       row &= row - 1;
-      const uint32_t kind = ((m_inter >> bb) & 1u) | (((m_blk >> bb) & 1u) << 1) | (((m_warp >> bb) & 1u) << 2);
-      if (o < raw_cap) raw[o] = pack_witness(sh ? 1u : 0u, arr, gran, (uint32_t)lane, (uint32_t)bb, kind);
+      if (o < raw_cap) raw[o] = pack_witness(space, arr, gran, (uint32_t)lane, (uint32_t)bb, witness_kind(R, bb));
       ++o;
     }
   }

@@ -398,3 +398,158 @@ def random_tiny(seed: int, max_instances: int = 2048) -> Workload:
     params = (P, Q)
     return Workload(f"tiny_{seed}", w.text(), Binding(tuple(grid), tuple(block), params),
                     {"loop_bounds": bounds, "n_access": nacc})
+
+
+# --------------------------------------------------------------------------
+# Config 4: corpus of seeded synthetic kernels of uneven size.
+#   2..32 accesses, 1-3D grids and blocks, 1..4 nested loops (bounds <= 64),
+#   affine guards, int32 and float4 widths, about 10% atomics and 30% with a
+#   planted race; the instance count is drawn log-uniform on [1e3, 1e7] and
+#   the launch dims are fitted to it.  Without the planted race every kernel
+#   is race free by construction: each thread writes a private region of the
+#   data arrays (idx = gid * SPAN + loop offset), reads go to read-only inputs
+#   or to the thread's own region, shared-memory neighbour reads sit in a
+#   later barrier interval than the writes, and atomics are device scoped on
+#   their own counters.  The planted race is one of: a write that drops the
+#   thread term, a private stride one too small, a neighbour read in the
+#   writer's interval, block-scoped atomics on a grid-wide counter, or a
+#   shared-memory neighbour read before the barrier.
+
+PLANTS = ("shared_write", "short_stride", "neighbour_read", "block_atomic", "shared_early_read")
+
+
+def _dims(total, rng, maxdims):
+    nd = rng.range(1, maxdims)
+    dims = [1, 1, 1]
+    rest = max(1, total)
+    for d in range(nd - 1):
+        f = 1
+        for _ in range(rng.range(0, 3)):
+            if rest % 2 == 0 and rest > 1:
+                f *= 2
+                rest //= 2
+        dims[d] = max(1, f)
+    dims[nd - 1] = rest
+    return dims
+
+
+def config4(item: int, lo_exp: float = 3.0, hi_exp: float = 7.0, planted=None) -> Workload:
+    rng = SplitMix64(seed_for(4, item))
+    target = int(10 ** (lo_exp + (hi_exp - lo_exp) * rng.uniform()))
+    nacc = rng.range(2, 32)
+    nloops = rng.range(1, 4)
+    bounds = [rng.choice([1, 2, 2, 3, 4, 4, 8, 16, 64]) for _ in range(nloops)]
+    while math.prod(bounds) * nacc > max(target, nacc) and max(bounds) > 1:
+        k = bounds.index(max(bounds))
+        bounds[k] = max(1, bounds[k] // 2)
+    span = math.prod(bounds)
+    if planted is None:
+        planted = rng.below(10) < 3
+    threads = max(2 if planted else 1, target // (nacc * span))
+    nthr = min(threads, rng.choice([32, 64, 128, 256, 512, 1024]))
+    nthr = max(2 if planted else 1, nthr)
+    nblk = max(1, (threads + nthr - 1) // nthr)
+    block = _dims(nthr, rng, 3)
+    while math.prod(block) > 1024:
+        block[block.index(max(block))] //= 2
+    grid = _dims(nblk, rng, 3)
+    nthr = math.prod(block)
+    nblk = math.prod(grid)
+    plant = rng.choice(PLANTS) if planted else None
+    lv = ["i", "j", "k", "l"][:nloops]
+    w = _Writer(f"corpus_{item}")
+    w.add("param SPAN NT")
+    for v, b in zip(lv, bounds):
+        w.add(f"loop {v} {b}")
+    # linear ids and the loop offset inside the thread's private region
+    w.add("let lt = (tz*bdy + ty)*bdx + tx")
+    w.add("let lb = (bz*gdy + by)*gdx + bx")
+    w.add("let gid = lb*(bdx*bdy*bdz) + lt")
+    off = lv[0]
+    for v, b in zip(lv[1:], bounds[1:]):
+        off = f"({off})*{b} + {v}"
+    w.add(f"let off = {off}")
+    total_threads = nthr * nblk
+    w.add(f"array D global {4 * (total_threads + 1) * span}")
+    w.add(f"array E global {16 * (total_threads + 1) * span}")
+    w.add(f"array In global {16 * 4096}")
+    w.add("array Cnt global 256")
+    has_shared = nthr * span <= 12288
+    if has_shared:
+        w.add(f"array S shared {4 * nthr * span}")
+    w.add("assert SPAN > 0")
+    w.add("assert NT > 0")
+    nvalid = max(1, total_threads - rng.below(max(1, total_threads // 4)))
+    kinds = []
+    for a in range(nacc):
+        r = rng.below(100)
+        if r < 10:
+            kinds.append("atomic")
+        elif r < 30:
+            kinds.append("input")
+        elif r < 55:
+            kinds.append("write_D")
+        elif r < 70:
+            kinds.append("read_D")
+        elif r < 80:
+            kinds.append("write_E")
+        elif r < 88 and has_shared:
+            kinds.append("shared_write")
+        elif has_shared:
+            kinds.append("shared_read")
+        else:
+            kinds.append("input")
+    plant_at = rng.below(nacc) if planted else -1
+    if plant == "block_atomic" and nblk < 2:
+        plant = "shared_write"
+    if plant == "shared_early_read" and not has_shared:
+        plant = "neighbour_read"
+    if plant in ("neighbour_read", "shared_early_read") and len(kinds) == 32:
+        kinds.pop()  # the plant adds a second access; stay within 32
+        plant_at = min(plant_at, len(kinds) - 1)
+    for a, kind in enumerate(kinds):
+        guards = []
+        if rng.below(3) == 0:
+            guards.append("gid < NT")
+        if nloops and rng.below(5) == 0:
+            v = rng.choice(lv)
+            guards.append(f"{v} <= {rng.below(bounds[lv.index(v)])}")
+        iv = rng.below(3)
+        line = 100 + a
+        if a == plant_at:
+            # the planted race: unguarded so that it always fires
+            if plant == "shared_write":
+                w.access("W", "D", 4, "off", iv=iv, line=line)
+            elif plant == "short_stride":
+                w.access("W", "D", 4, "gid*(SPAN - 1) + off" if span > 1 else "gid / 2", iv=iv, line=line)
+            elif plant == "neighbour_read":
+                w.access("W", "D", 4, "gid*SPAN + off", iv=0, line=line)
+                w.access("R", "D", 4, "(gid + 1)*SPAN + off", iv=0, line=line)
+            elif plant == "block_atomic":
+                w.access("A", "Cnt", 4, f"{rng.below(8)}", iv=iv, scope="block", line=line)
+            else:  # shared_early_read
+                w.access("W", "S", 4, "lt*SPAN + off", iv=1, line=line)
+                w.access("R", "S", 4, f"((lt + 1) % {nthr})*SPAN + off", iv=1, line=line)
+            continue
+        if kind == "atomic":
+            w.access("A", "Cnt", 4, f"gid % {rng.range(1, 64)}", iv=iv, guards=guards, scope="device", line=line)
+        elif kind == "input":
+            c1, c2 = rng.range(1, 7), rng.range(0, 5)
+            wid = 16 if rng.below(3) == 0 else 4
+            n_el = (16 * 4096) // wid
+            w.access("R", "In", wid, f"(gid*{c1} + off*{c2} + {rng.below(97)}) % {n_el}", iv=iv, guards=guards,
+                     line=line)
+        elif kind == "write_D":
+            w.access("W", "D", 4, "gid*SPAN + off", iv=iv, guards=guards, line=line)
+        elif kind == "read_D":
+            w.access("R", "D", 4, "gid*SPAN + off", iv=iv, guards=guards, line=line)
+        elif kind == "write_E":
+            w.access("W", "E", 16, "gid*SPAN + off", iv=iv, guards=guards, line=line)
+        elif kind == "shared_write":
+            w.access("W", "S", 4, "lt*SPAN + off", iv=1, guards=guards, line=line)
+        elif kind == "shared_read":
+            w.access("R", "S", 4, f"((lt + 1) % {nthr})*SPAN + off", iv=2, guards=guards, line=line)
+    inst = nblk * nthr * span * len([l for l in w.lines if l.startswith("access")])
+    return Workload(f"c4_{item}", w.text(), Binding(tuple(grid), tuple(block), (span, nvalid)),
+                    {"config": 4, "planted": plant, "target": target, "instances": inst,
+                     "n_access": sum(1 for l in w.lines if l.startswith("access"))})
