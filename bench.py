@@ -138,8 +138,77 @@ for _p in range(8):
     STAGE_BYTES[f"sort_pass{_p}"] = 16
 
 
+def run_suite(args):
+    """Batched form vs the plain checker on a set of items (time to all verdicts)."""
+    import torch
+    import workloads
+    import paper_2604_02106_b300 as hg
+
+    torch.cuda.set_device(0)
+    if args.suite == "sweep":
+        ws = workloads.config3()
+        name = "host-loop sweep: one 12-access kernel under 64 bindings (N 2^8..2^20 x stride {1,2,3,4,32})"
+    else:
+        ws = [workloads.config4(i) for i in range(args.items)]
+        name = f"corpus of {args.items} seeded kernels, log-uniform 1e3..1e7 instances"
+    ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in ws]
+    s = torch.cuda.Stream()
+    # plain: one hgrd_check_enqueue per item, one stream, one shared workspace
+    need = max(k.workspace_size(flags=hg.NO_PAIR) for k in ks)
+    wsp = torch.empty(need, dtype=torch.uint8, device="cuda")
+    res_plain = []
+    for k in ks:
+        k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
+        res_plain.append(k.collect(wsp, cap=64, stream=s, flags=hg.NO_PAIR))
+    n_inst = sum(r.n_instances for r in res_plain)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        for k in ks:
+            k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
+    e1.record(s)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.steps
+    # batched: tuned, captured into one CUDA graph, replayed
+    b = hg.Batch(ks, graph=True)
+    choice = b.tune(stream=s)
+    res_b = b.check(stream=s)
+    for rp, rb in zip(res_plain, res_b):
+        assert rb.status == 0 and rb.n_witness == rp.n_witness and rb.n_by_kind == rp.n_by_kind
+        assert rb.witnesses == rp.witnesses[:len(rb.witnesses)]
+    for _ in range(max(3, args.warmup)):
+        b.run(stream=s)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            b.run(stream=s)
+        e1.record(s)
+        e1.synchronize()
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.check(stream=s)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    line = {"metric": METRIC, "value": n_inst / (batch_ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": name, "items": len(ks), "instances": n_inst,
+                       "racy_items": sum(r.racy for r in res_b), "small_items": sum(r.small for r in res_b),
+                       "tuned": choice, "form": "batched, CUDA graph"},
+            "plain": {"value": n_inst / (plain_ms / 1000), "ms_per_step": plain_ms,
+                      "form": "hgrd_check_enqueue per item, one stream"},
+            "batched_over_plain": plain_ms / batch_ms,
+            "e2e": {"value": n_inst / e2e_s, "unit": UNIT, "ms_per_step": 1000 * e2e_s},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus"])
+    ap.add_argument("--items", type=int, default=1000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -155,6 +224,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.suite != "stencil":
+        run_suite(args)
         return
 
     import torch

@@ -103,8 +103,9 @@ typedef struct {
 
 /* Options.  Zero-initialised means defaults. */
 typedef struct {
-  uint64_t max_raw_witness; /* device buffer for per-run witnesses before merging; 0 = 1<<22 */
-  uint32_t pair_cap;        /* instances gathered to find min_x/min_y; 0 = 1<<20 */
+  uint64_t max_raw_witness; /* device buffer for per-run witnesses before merging;
+                               0 = twice the key bound, between 1<<12 and 1<<24 */
+  uint32_t pair_cap;        /* instances gathered to find min_x/min_y; 0 = min(key bound, 1<<20) */
   uint32_t flags;           /* HGRD_NO_PAIR: skip the canonical instance pair;
                                HGRD_PROFILE: time every pipeline stage with CUDA events */
 } hgrd_check_opts;
