@@ -99,6 +99,10 @@ typedef struct {
   uint64_t n_witness, n_by_kind[3], n_instances, n_keys, n_oob;
   hgrd_witness min_w;
   hgrd_inst min_x, min_y;
+  /* racy access pairs, the paper's report unit (Sec. 5, Sec. 6 component 5):
+   * bit b of pair_kind[k][a] is set when accesses a and b race with kind
+   * 1 << k somewhere (symmetric in a, b) */
+  uint32_t pair_kind[3][32];
 } hgrd_verdict;
 
 /* Options.  Zero-initialised means defaults. */
@@ -107,9 +111,16 @@ typedef struct {
                                0 = twice the key bound, between 1<<12 and 1<<24 */
   uint32_t pair_cap;        /* instances gathered to find min_x/min_y; 0 = min(key bound, 1<<20) */
   uint32_t flags;           /* HGRD_NO_PAIR: skip the canonical instance pair;
-                               HGRD_PROFILE: time every pipeline stage with CUDA events */
+                               HGRD_PROFILE: time every pipeline stage with CUDA events;
+                               HGRD_STOP_FIRST: stop the exact scan once one race is confirmed
+                               (the verdict is racy/clean exactly; witnesses and counts are then
+                               a subset, each witness a real race) */
+  uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
+                               check: every witness is a real race of the full kernel, but a
+                               clean result says nothing about the other accesses) */
+  uint32_t reserved;
 } hgrd_check_opts;
-enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2 };
+enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
  * stream around the stage's kernels. */
@@ -195,6 +206,7 @@ typedef struct {
   int32_t status;   /* HGRD_OK, or HGRD_ENOMEM (a witness buffer overflowed: rerun with hgrd_check) */
   int32_t racy, small, n_copied;
   uint64_t n_witness, n_by_kind[3], n_instances, n_keys, n_oob;
+  uint32_t pair_kind[3][32]; /* racy access pairs, as in hgrd_verdict */
 } hgrd_item_verdict;
 
 int hgrd_batch_create(const hgrd_desc* const* items, uint32_t n, const hgrd_batch_opts* o, hgrd_batch** out);

@@ -18,6 +18,7 @@ ERRORS = {1: "ETRUNCATED", -1: "EINVAL", -2: "EPARSE", -3: "EBIND", -4: "EHOSTCO
           -6: "ENOMEM", -7: "EDEVICE", -8: "ETIMEOUT", -9: "EUNSUPPORTED"}
 NO_PAIR = 1
 PROFILE = 2
+STOP_FIRST = 4
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -51,11 +52,13 @@ class Inst(C.Structure):
 class Verdict(C.Structure):
     _fields_ = [("racy", C.c_int32), ("pair_found", C.c_int32), ("n_witness", C.c_uint64),
                 ("n_by_kind", C.c_uint64 * 3), ("n_instances", C.c_uint64), ("n_keys", C.c_uint64),
-                ("n_oob", C.c_uint64), ("min_w", Witness), ("min_x", Inst), ("min_y", Inst)]
+                ("n_oob", C.c_uint64), ("min_w", Witness), ("min_x", Inst), ("min_y", Inst),
+                ("pair_kind", (C.c_uint32 * 32) * 3)]
 
 
 class CheckOpts(C.Structure):
-    _fields_ = [("max_raw_witness", C.c_uint64), ("pair_cap", C.c_uint32), ("flags", C.c_uint32)]
+    _fields_ = [("max_raw_witness", C.c_uint64), ("pair_cap", C.c_uint32), ("flags", C.c_uint32),
+                ("only_accesses", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class BatchOpts(C.Structure):
@@ -66,7 +69,7 @@ class BatchOpts(C.Structure):
 class ItemVerdict(C.Structure):
     _fields_ = [("status", C.c_int32), ("racy", C.c_int32), ("small", C.c_int32), ("n_copied", C.c_int32),
                 ("n_witness", C.c_uint64), ("n_by_kind", C.c_uint64 * 3), ("n_instances", C.c_uint64),
-                ("n_keys", C.c_uint64), ("n_oob", C.c_uint64)]
+                ("n_keys", C.c_uint64), ("n_oob", C.c_uint64), ("pair_kind", (C.c_uint32 * 32) * 3)]
 
 
 class StageTime(C.Structure):
@@ -128,8 +131,24 @@ def _raise(rc):
         raise HgrdError(rc, lib().hgrd_last_error().decode(errors="replace"))
 
 
-def _opts(max_raw_witness=0, pair_cap=0, flags=0):
-    return CheckOpts(max_raw_witness, pair_cap, flags)
+def _opts(max_raw_witness=0, pair_cap=0, flags=0, only_accesses=0):
+    return CheckOpts(max_raw_witness, pair_cap, flags, only_accesses, 0)
+
+
+def _pairs(pk):
+    """{(a, b): kind_mask} for a <= b from the three 32x32 bit matrices."""
+    out = {}
+    for k in range(3):
+        for a in range(32):
+            row = pk[k][a]
+            b = a
+            row >>= a
+            while row:
+                if row & 1:
+                    out[(a, b)] = out.get((a, b), 0) | (1 << k)
+                row >>= 1
+                b += 1
+    return out
 
 
 @dataclass
@@ -145,6 +164,7 @@ class Result:
     min_x: tuple | None    # (lin_block, lin_thread, i0, i1, i2, i3, access)
     min_y: tuple | None
     truncated: bool = False
+    pairs: dict = None     # {(acc_lo, acc_hi): kind_mask}: the racy access pairs
 
 
 def _wt(w):
@@ -219,7 +239,7 @@ class Kernel:
             return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
                           [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None,
                           _it(v.min_x) if v.pair_found else None, _it(v.min_y) if v.pair_found else None,
-                          rc == ETRUNCATED)
+                          rc == ETRUNCATED, _pairs(v.pair_kind))
 
     def check_noalloc(self, cap: int = 1 << 16, stream=None, **opts) -> Result:
         """hgrd_check_noalloc: the check on the library's built-in 64 MiB device
@@ -233,7 +253,7 @@ class Kernel:
         n = min(cap, v.n_witness)
         return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
                       [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
-                      rc == ETRUNCATED)
+                      rc == ETRUNCATED, _pairs(v.pair_kind))
 
     def enqueue(self, workspace, stream=None, **opts):
         """Enqueue the device pipeline only (no host synchronisation)."""
@@ -251,7 +271,7 @@ class Kernel:
         n = min(cap, v.n_witness)
         return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
                       [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
-                      rc == ETRUNCATED)
+                      rc == ETRUNCATED, _pairs(v.pair_kind))
 
 
 @dataclass
@@ -265,6 +285,7 @@ class ItemResult:
     n_keys: int
     n_oob: int
     witnesses: list   # first min(witness_cap, n_witness) canonical witnesses
+    pairs: dict = None
 
 
 class Batch:
@@ -313,7 +334,7 @@ class Batch:
             x = v[i]
             out.append(ItemResult(x.status, bool(x.racy), bool(x.small), x.n_witness, tuple(x.n_by_kind),
                                   x.n_instances, x.n_keys, x.n_oob,
-                                  [_wt(w[i * wc + k]) for k in range(x.n_copied)]))
+                                  [_wt(w[i * wc + k]) for k in range(x.n_copied)], _pairs(x.pair_kind)))
         return out
 
     def check(self, stream=None):

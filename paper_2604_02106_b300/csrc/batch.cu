@@ -42,7 +42,7 @@ constexpr int SB_UNITS = 1024;  // simulated warps of one small item
 constexpr int SB_RAW = 1024;    // per-run witnesses of one small item
 constexpr int SB_SLOTS = 64;    // slot file entries per simulated lane
 constexpr int SB_PASSES = 4;    // radix passes (32 sorted bits)
-constexpr int OUT_WORDS = 8;    // n_keys, n_oob, n_witness, kind0..2, flags, n_raw
+constexpr int OUT_WORDS = 56;   // n_keys, n_oob, n_witness, kind0..2, flags, n_raw, 48 racy-pair words
 enum { F_RAW_OVERFLOW = 1, F_TIMEOUT = 2, F_CAND_OVERFLOW = 4 };
 
 struct SmallSmem {
@@ -54,6 +54,7 @@ struct SmallSmem {
   uint32_t dstart[256];
   uint64_t raw[SB_RAW];
   uint64_t ws[SB_WARPS + 1];
+  uint64_t pairs[48];
   uint64_t oob;
   uint32_t item, nraw, nkeys, nuniq;
   uint32_t kinds[3];
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __
       S.nraw = 0;
       S.kinds[0] = S.kinds[1] = S.kinds[2] = 0;
     }
+    if (threadIdx.x < 48) S.pairs[threadIdx.x] = 0;
     __syncthreads();
     const DProg* P = &S.prog;
     const int64_t nunits = P->nunits;
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __
           const uint32_t s0 = c + l;
           if (s0 + 1 >= n || shr64(src[s0 + 1], rsh) != shr64(src[s0], rsh)) continue;  // one key: no pair
           const RunMasks R = exact_run(src, s0, 0, n, P, lane, einter, eintra);
+          record_pairs(S.pairs, R, lane);
           uint32_t row = witness_row(R, lane);
           const uint32_t cntw = (uint32_t)__popc(row);
           uint32_t incl = cntw;
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __
         o[6] = nraw > SB_RAW ? F_RAW_OVERFLOW : 0;
         o[7] = nraw;
       }
+      if (threadIdx.x < 48) o[8 + threadIdx.x] = S.pairs[threadIdx.x];
       const uint32_t nc = total < wcap ? total : wcap;
       for (uint32_t i = threadIdx.x; i < nc; i += SB_THREADS) wits[(size_t)item * wcap + i] = uq[i];
     }
@@ -342,6 +346,7 @@ __global__ void gather_kernel(const uint64_t* __restrict__ cnt, const uint64_t* 
              (cnt[C_NCAND] > cand_cap ? F_CAND_OVERFLOW : 0);
     out[7] = cnt[C_NRAW];
   }
+  if (threadIdx.x < 48) out[8 + threadIdx.x] = cnt[C_PAIRS + threadIdx.x];
   const uint64_t nc = nu < wcap ? nu : wcap;
   if (!(cnt[C_NRAW] > raw_cap))
     for (uint64_t i = threadIdx.x; i < nc; i += blockDim.x) wits[i] = uniq[i];
@@ -590,6 +595,8 @@ int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream,
     x.n_by_kind[1] = o[4];
     x.n_by_kind[2] = o[5];
     x.racy = o[2] > 0;
+    for (int k = 0; k < 3; k++)
+      for (int a = 0; a < 32; a++) x.pair_kind[k][a] = (uint32_t)(o[8 + k * 16 + a / 2] >> (32 * (a & 1)));
     x.small = std::find(b->small.begin(), b->small.end(), (uint32_t)i) != b->small.end();
     x.status = (o[6] & F_TIMEOUT) ? HGRD_ETIMEOUT : (o[6] & (F_RAW_OVERFLOW | F_CAND_OVERFLOW)) ? HGRD_ENOMEM : HGRD_OK;
     if (x.status) {

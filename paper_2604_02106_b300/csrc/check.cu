@@ -129,6 +129,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   uint64_t* cnt = U(W.counters);
   // the compiled program: uploaded into the workspace, or already resident
   const DProg* dprog = dprog_resident ? dprog_resident : (const DProg*)(ws + W.prog);
+  // a check restricted to a subset of the accesses runs a copy of the
+  // program with the other accesses removed (their keys are never made)
+  const uint32_t only = o ? o->only_accesses : 0u;
+  const bool restricted = only != 0 && only != 0xffffffffu && !dprog_resident;
   g_stats = hgrd_stats{};
   g_stats.int64_path = B.wide;
   g_stats.sort_passes = (uint32_t)B.sort_passes;
@@ -142,7 +146,15 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
   if (!dprog_resident) {
-    CK(cudaMemcpyAsync(ws + W.prog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    if (restricted) {
+      static thread_local DProg tmp;
+      tmp = HP;
+      for (int a = 0; a < tmp.nacc; a++)
+        if (!((only >> a) & 1u)) tmp.acc[a].dead = 1;
+      CK(cudaMemcpyAsync(ws + W.prog, &tmp, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    } else {
+      CK(cudaMemcpyAsync(ws + W.prog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    }
     g_stats.h2d_bytes += sizeof(DProg);
   }
   g_prof.mark("setup");
@@ -174,7 +186,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const uint64_t cand_cap = std::max<uint64_t>(B.nkeys_max / 2, 1);
   CK(launch_candidates(L, in, nkeys, dprog, out, cand_cap, cnt));
   g_prof.mark("candidates");
-  CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt));
+  CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt, o && (o->flags & HGRD_STOP_FIRST)));
   g_prof.mark("exact");
   // canonical order of the witnesses: radix sort of the packed words
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
@@ -249,6 +261,8 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   v->n_by_kind[1] = cnt[C_KIND1];
   v->n_by_kind[2] = cnt[C_KIND2];
   v->racy = v->n_witness > 0;
+  for (int k = 0; k < 3; k++)
+    for (int a = 0; a < 32; a++) v->pair_kind[k][a] = (uint32_t)(cnt[C_PAIRS + k * 16 + a / 2] >> (32 * (a & 1)));
   const uint64_t* duniq = uniq_buffer(d, W, ws);
   const uint64_t ncopy = std::min<uint64_t>(std::max<uint64_t>(cap, 1), v->n_witness);
   std::vector<uint64_t> hw(ncopy);

@@ -134,8 +134,9 @@ enum {
   C_KIND1,
   C_KIND2,
   C_NPAIR,
-  C_TICKET0 = 16,  // one tile ticket per sort pass (up to 32 passes)
-  C_WORDS = 64
+  C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
+  C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
+  C_WORDS = 128
 };
 enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
 

@@ -169,7 +169,7 @@ struct RunMasks {
 };
 __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, uint64_t e, uint64_t n,
                                               const DProg* __restrict__ P, int lane, uint32_t einter,
-                                              uint32_t eintra) {
+                                              uint32_t eintra, bool stop_first = false) {
   const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
   const int rsh = PB + IVB;
   RunMasks R;
@@ -216,6 +216,11 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
       }
     }
     if (cnt < 32) break;
+    // stop-at-first: every pair found so far is a real race; quit once one exists
+    if (stop_first) {
+      const uint32_t mi = glob ? (racy_row(br, lane) & einter) : 0u;
+      if (__any_sync(FULL, (m_warp | m_blk | mi) != 0)) break;
+    }
   }
   m_warp |= racy_row(tw, lane) & eintra;
   m_blk |= racy_row(wb, lane) & eintra;
@@ -236,6 +241,14 @@ __device__ __forceinline__ void run_location(const DProg* __restrict__ P, uint64
   *gran = sh ? cell % P->lay_ngran[li] : cell;
   *arr = (uint32_t)P->lay_arr[li];
   *space = sh ? 1u : 0u;
+}
+
+// OR this lane's rows of the run into the racy-pair matrices (two 32-bit rows per word)
+__device__ __forceinline__ void record_pairs(uint64_t* pairs, const RunMasks& R, int lane) {
+  const int sh = 32 * (lane & 1);
+  if (R.inter) atomicOr((unsigned long long*)&pairs[0 * 16 + (lane >> 1)], (unsigned long long)R.inter << sh);
+  if (R.blk) atomicOr((unsigned long long*)&pairs[1 * 16 + (lane >> 1)], (unsigned long long)R.blk << sh);
+  if (R.warp) atomicOr((unsigned long long*)&pairs[2 * 16 + (lane >> 1)], (unsigned long long)R.warp << sh);
 }
 
 // witness words of lane a for accesses b >= a; `n` counts them

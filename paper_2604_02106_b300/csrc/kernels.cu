@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
 __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                     const DProg* __restrict__ P, const uint64_t* __restrict__ cand,
                                                     uint64_t cand_cap, uint64_t* __restrict__ raw, uint64_t raw_cap,
-                                                    uint64_t* counters) {
+                                                    uint64_t* counters, int stop_first) {
   const int lane = threadIdx.x & 31;
   const uint64_t n = *n_dev;
   uint64_t ncand = counters[C_NCAND];
@@ -539,7 +539,9 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t c = gw; c < ncand; c += nw) {
-    const RunMasks R = exact_run(keys, cand[2 * c], cand[2 * c + 1], n, P, lane, einter, eintra);
+    if (stop_first && *(volatile uint64_t*)&counters[C_NRAW] != 0) break;
+    const RunMasks R = exact_run(keys, cand[2 * c], cand[2 * c + 1], n, P, lane, einter, eintra, stop_first != 0);
+    record_pairs(counters + C_PAIRS, R, lane);
     uint32_t row = witness_row(R, lane);
     const uint32_t cntw = (uint32_t)__popc(row);
     uint32_t incl = cntw;
@@ -691,9 +693,9 @@ cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint6
 
 cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                          const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
-                         uint64_t* counters) {
+                         uint64_t* counters, bool stop_first) {
   int grid = occupancy_grid((const void*)exact_kernel, 256, 0, L.nsm);
-  exact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, raw, raw_cap, counters);
+  exact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, raw, raw_cap, counters, stop_first ? 1 : 0);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -60,7 +60,7 @@ cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint6
 // conflict scan, phase B: exact per-access summaries -> packed raw witnesses
 cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                          const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
-                         uint64_t* counters);
+                         uint64_t* counters, bool stop_first = false);
 
 // witness merge: head flags, merge by atomic OR into uniq, kind counts
 cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_dev, uint64_t n_max, uint64_t* flags);

@@ -25,6 +25,11 @@ def _same_item(r, o, cap):
     assert r.n_by_kind == o.n_by_kind
     assert r.n_keys == o.n_keys and r.n_oob == o.n_oob and r.n_instances == o.n_instances
     assert r.witnesses == o.witnesses[:cap]
+    if len(o.witnesses) == o.n_witness:
+        pairs = {}
+        for w in o.witnesses:
+            pairs[(w[3], w[4])] = pairs.get((w[3], w[4]), 0) | w[5]
+        assert r.pairs == pairs
 
 
 def _check_batch(ws, **kw):

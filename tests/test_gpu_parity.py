@@ -29,6 +29,16 @@ def _same(g, o, pair=True):
     assert g.min_w == o.min_w
     if pair and o.racy:
         assert g.min_x == o.min_x and g.min_y == o.min_y
+    if g.pairs is not None and not g.truncated and len(o.witnesses) == o.n_witness:
+        assert g.pairs == oracle_pairs(o)
+
+
+def oracle_pairs(o):
+    """Racy access pairs with their kinds, from the oracle's witness list."""
+    out = {}
+    for w in o.witnesses:
+        out[(w[3], w[4])] = out.get((w[3], w[4]), 0) | w[5]
+    return out
 
 
 def _both(text, binding, cap=1 << 20, **kw):
@@ -191,3 +201,22 @@ def test_deterministic_and_enqueue_collect():
     assert c.witnesses == a.witnesses and c.n_by_kind == a.n_by_kind
     st = hg.stats()
     assert st["kernel_launches"] > 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_restricted_and_stop_first(seed):
+    # a check of a subset of the accesses finds exactly the oracle's witnesses
+    # among those accesses; stop-at-first keeps the verdict and reports real races
+    w = workloads.random_tiny(30000 + seed, max_instances=20000)
+    o = oracle.check(w.text, w.binding)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    nacc = w.meta["n_access"]
+    mask = 0b101 & ((1 << nacc) - 1) or 1
+    r = k.check(cap=1 << 20, only_accesses=mask)
+    want = [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
+    assert r.witnesses == want
+    f = k.check(cap=1 << 20, flags=hg.STOP_FIRST)
+    assert f.racy == o.racy
+    full = {x[:5]: x[5] for x in o.witnesses}
+    for x in f.witnesses:
+        assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
