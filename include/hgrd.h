@@ -223,6 +223,67 @@ int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_st
 int hgrd_batch_tune(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_batch_opts* chosen);
 void hgrd_batch_free(hgrd_batch* b);
 
+/* ---- The learned ranker (an AI-systems addition; the paper has no learned part)
+ * An MLP 96 -> 256 -> 256 -> 1 (ReLU) scores access pairs of a bound kernel
+ * so that likely races are checked first.  BF16 operands, FP32 accumulation
+ * and FP32 master weights; trained with weighted binary cross-entropy and
+ * AdamW by the library's own forward and backward kernels on labels from the
+ * exact check.  It never changes a verdict. */
+enum { HGRD_MLP_IN = 96, HGRD_MLP_HIDDEN = 256, HGRD_MLP_PARAMS = 90881 };
+
+/* The eligible pairs a <= b of a bound descriptor (same array, not both loads,
+ * not both atomics of sufficient scope: the pair rule of Sec. 6.1 and
+ * Appendix A; neither access dead) with 96 features each: per access, its kind
+ * and scope, width, memory space, the folded coefficients on thread, block
+ * and loop ids, div/mod and guard counts, its index range against the array;
+ * per pair, interval overlap, race kinds the pair rule allows, byte-range
+ * overlap, coefficient differences, launch and array sizes.  Host memory:
+ * out[cap * 96], pairs[cap * 2]; *n = number of eligible pairs (ETRUNCATED
+ * when it exceeds cap). */
+int hgrd_pair_features(const hgrd_desc* d, float* out, uint8_t* pairs, uint32_t cap, uint32_t* n);
+
+/* Model buffer (device, caller allocated, 256-byte aligned): FP32 parameters,
+ * gradients, AdamW moments, then BF16 parameters.  Workspace for a batch of
+ * n samples: activations. */
+size_t hgrd_mlp_model_bytes(void);
+size_t hgrd_mlp_workspace_bytes(uint32_t n);
+/* Uniform(+-1/sqrt(fan_in)) weights from a counter-based generator, zero biases and moments. */
+int hgrd_mlp_init(void* d_model, uint64_t seed, void* cuda_stream);
+/* Logits of n feature rows d_x[n * 96] (FP32, converted to BF16) into d_logits[n]. */
+int hgrd_mlp_predict(const void* d_model, const float* d_x, uint32_t n, float* d_logits, void* d_ws,
+                     size_t ws_bytes, void* cuda_stream);
+/* Gradients (into the model buffer) of the weighted mean BCE loss
+ * sum_i w_i * bce(z_i, y_i) / wsum; d_w may be NULL (all weights 1). */
+int hgrd_mlp_grad(void* d_model, const float* d_x, const float* d_y, const float* d_w, float wsum, uint32_t n,
+                  void* d_ws, size_t ws_bytes, void* cuda_stream);
+/* hgrd_mlp_grad, then one AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled
+ * weight decay); the batch loss is written to *d_loss (device) when given. */
+int hgrd_mlp_train_step(void* d_model, const float* d_x, const float* d_y, const float* d_w, float wsum, uint32_t n,
+                        float lr, float weight_decay, uint32_t step, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                        float* d_loss);
+/* Device pointers of the FP32 parameters and gradients inside the model buffer. */
+int hgrd_mlp_params(const void* d_model, float** d_params, float** d_grads);
+/* Refresh the BF16 copies after the FP32 parameters were written directly. */
+int hgrd_mlp_sync_bf16(void* d_model, void* cuda_stream);
+
+/* Ranked check.  Scores the eligible pairs (with the model, or with
+ * host_scores[n_pairs] in hgrd_pair_features order when given), runs a
+ * restricted exact check of the accesses of the top `topk` pairs that stops
+ * at its first race, and only if that finds none runs the full check (also
+ * stopping at its first race).  The verdict's racy flag is exact; when racy,
+ * the witnesses are the races found (each a real race), not the full set.
+ * Workspace: hgrd_ranked_workspace_size. */
+typedef struct {
+  uint32_t n_pairs, stage; /* stage 1: race found by the ranked check; 2: the full check decided */
+  uint32_t access_mask, pad;
+  uint64_t keys_ranked, keys_full; /* keys the two checks expanded */
+  float ms_rank, pad2;             /* host time of features + scoring */
+} hgrd_rank_info;
+int hgrd_ranked_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes);
+int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* d_model, const float* host_scores,
+                      uint32_t topk, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_witness* host_out,
+                      uint64_t cap, hgrd_verdict* v, hgrd_rank_info* info);
+
 /* hgrd_check without a caller workspace, for callers that cannot allocate
  * device memory: code running while another component owns all device memory
  * (a caching allocator or pool that must not be bypassed), code called from

@@ -24,7 +24,10 @@ STOP_FIRST = 4
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
            "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile", "hgrd_free_desc", "hgrd_last_error",
            "hgrd_debug_divmod", "hgrd_check_noalloc", "hgrd_batch_create", "hgrd_batch_workspace_size",
-           "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free"]
+           "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free", "hgrd_pair_features",
+           "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
+           "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
+           "hgrd_check_ranked"]
 BATCH_GRAPH = 1
 
 

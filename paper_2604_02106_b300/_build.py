@@ -7,7 +7,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhgrd.so")
-SOURCES = ["desc.cpp", "kernels.cu", "check.cu", "batch.cu"]
+SOURCES = ["desc.cpp", "kernels.cu", "check.cu", "batch.cu", "mlp.cu", "rank.cu"]
 HEADERS = ["hgrd_internal.h", "hgrd_host.h", "kernels.cuh", "kcommon.cuh", os.path.join("..", "..", "include", "hgrd.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -12,6 +12,7 @@
 //   ten instance variables and div/mod nodes, bounded by interval arithmetic
 //   over the instance box, and compiled into a DProg for the kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -845,6 +846,27 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       ivmin = std::min(ivmin, lo);
       ivmax = std::max(ivmax, hi);
     }
+    // facts kept for the ranker's pair features
+    B.acc_info.resize(d.acc.size());
+    for (size_t a = 0; a < d.acc.size(); a++) {
+      AccInfo& I = B.acc_info[a];
+      const AccessDecl& A = d.acc[a];
+      I.kind = A.kind;
+      I.scope = A.scope;
+      I.arr = A.arr;
+      I.shared = d.arrays[A.arr].space == HGRD_SPACE_SHARED;
+      I.width = A.width;
+      I.G = P.acc[a].G;
+      I.maxidx = P.acc[a].maxidx;
+      I.dead = af[a].dead;
+      I.nguards = (int)af[a].guards.size();
+      if (I.dead) continue;
+      for (int k = 0; k < NVAR; k++) I.cv[k] = af[a].idx.cv[k];
+      I.nnodes = (int)af[a].idx.cn.size();
+      for (auto& kv : af[a].idx.cn) I.loop_nodes += F.nodes[kv.first].loop ? 1 : 0;
+      C.range(af[a].idx, I.idx_lo, I.idx_hi);
+      C.range(af[a].iv, I.iv_lo, I.iv_hi);
+    }
     if (fix.size() + iter.size() > (size_t)MAXOP || terms.size() > (size_t)MAXTERM ||
         guards.size() > (size_t)MAXGUARD || nslot > MAXSLOT)
       raise(HGRD_EUNSUPPORTED, "descriptor too complex for the device program limits");
@@ -931,6 +953,77 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
   }
 }
 
+// 96 features of the access pair (a, b) of a bound descriptor; see
+// hgrd_pair_features for the list
+static float sgnlog(double x) { return (float)((x < 0 ? -1 : 1) * std::log2(1.0 + std::fabs(x)) / 16.0); }
+
+void pair_features(const hgrd_desc& d, int a, int b, float* f) {
+  const Bound& B = *d.bound;
+  const DProg& P = B.prog;
+  for (int k = 0; k < HGRD_MLP_IN; k++) f[k] = 0.f;
+  const AccInfo* X[2] = {&B.acc_info[a], &B.acc_info[b]};
+  for (int s = 0; s < 2; s++) {
+    const AccInfo& I = *X[s];
+    float* g = f + 32 * s;
+    g[I.kind] = 1.f;
+    g[3] = (I.kind == 2 && I.scope == 0) ? 1.f : 0.f;
+    g[4] = (float)std::log2((double)I.width) / 4.f;
+    g[5] = (float)I.shared;
+    for (int k = 0; k < NVAR; k++) g[6 + k] = sgnlog((double)I.cv[k]);
+    g[16] = I.nnodes / 4.f;
+    g[17] = I.nguards / 4.f;
+    g[18] = (float)(std::log2(1.0 + (double)(I.idx_hi - I.idx_lo)) / 32.0);
+    const double cover = (double)(I.idx_hi - I.idx_lo + 1) / (double)std::max<int64_t>(1, I.maxidx + 1);
+    g[19] = (float)std::min(1.0, std::max(0.0, cover));
+    g[20] = I.idx_lo < 0 ? 1.f : 0.f;
+    g[21] = I.idx_hi > I.maxidx ? 1.f : 0.f;
+    g[22] = I.iv_lo == I.iv_hi ? 1.f : 0.f;
+    g[23] = (float)std::min<int64_t>(8, std::max<int64_t>(-8, I.iv_lo)) / 8.f;
+    g[24] = (I.cv[0] | I.cv[1] | I.cv[2]) == 0 ? 1.f : 0.f;
+    g[25] = (I.cv[3] | I.cv[4] | I.cv[5]) == 0 ? 1.f : 0.f;
+    g[26] = ((I.cv[6] | I.cv[7] | I.cv[8] | I.cv[9]) == 0 && I.loop_nodes == 0) ? 1.f : 0.f;
+    bool cst = I.nnodes == 0;
+    for (int k = 0; k < NVAR; k++) cst = cst && I.cv[k] == 0;
+    g[27] = cst ? 1.f : 0.f;
+    for (int l = 0; l < 4; l++) g[28 + l] = I.cv[6 + l] != 0 ? 1.f : 0.f;
+  }
+  const AccInfo &A = *X[0], &Bb = *X[1];
+  float* h = f + 64;
+  h[0] = a == b ? 1.f : 0.f;
+  h[1] = (A.iv_lo <= Bb.iv_hi && Bb.iv_lo <= A.iv_hi) ? 1.f : 0.f;
+  h[2] = (A.iv_lo == A.iv_hi && Bb.iv_lo == Bb.iv_hi && A.iv_lo == Bb.iv_lo) ? 1.f : 0.f;
+  h[3] = (float)((P.einter[a] >> b) & 1u);
+  h[4] = (float)((P.eintra[a] >> b) & 1u);
+  h[5] = (A.kind != 0 && Bb.kind != 0) ? 1.f : 0.f;
+  h[6] = (A.kind == 2 && Bb.kind == 2) ? 1.f : 0.f;
+  // the two index ranges in bytes overlap
+  const double alo = (double)A.idx_lo * A.width, ahi = (double)A.idx_hi * A.width + A.width;
+  const double blo = (double)Bb.idx_lo * Bb.width, bhi = (double)Bb.idx_hi * Bb.width + Bb.width;
+  h[7] = (alo < bhi && blo < ahi) ? 1.f : 0.f;
+  bool same = A.nnodes == Bb.nnodes && A.width == Bb.width;
+  for (int k = 0; k < NVAR; k++) same = same && A.cv[k] == Bb.cv[k];
+  h[8] = same ? 1.f : 0.f;
+  for (int k = 0; k < NVAR; k++) h[9 + k] = sgnlog((double)(A.cv[k] * A.width - Bb.cv[k] * Bb.width));
+  h[19] = (float)std::log2((double)P.nthr) / 10.f;
+  h[20] = (float)std::log2((double)P.nblk) / 24.f;
+  h[21] = (float)std::log2((double)std::max<int64_t>(1, P.nit)) / 24.f;
+  h[22] = P.nacc / 32.f;
+  h[23] = (float)std::log2(1.0 + (double)B.array_bytes[A.arr]) / 32.f;
+  h[24] = A.shared ? 0.f : 1.f;
+  h[25] = A.width == Bb.width ? 1.f : 0.f;
+  // smallest thread stride in bytes against the access widths: strides below
+  // the width make neighbouring threads overlap
+  const double sa = std::fabs((double)A.cv[0] * A.width), sb = std::fabs((double)Bb.cv[0] * Bb.width);
+  h[26] = (sa > 0 && sa < A.width) ? 1.f : 0.f;
+  h[27] = (sb > 0 && sb < Bb.width) ? 1.f : 0.f;
+  h[28] = (A.cv[0] == 0 && A.cv[1] == 0 && A.cv[2] == 0 && A.cv[3] == 0 && A.cv[4] == 0 && A.cv[5] == 0) ? 1.f : 0.f;
+  h[29] = (Bb.cv[0] == 0 && Bb.cv[1] == 0 && Bb.cv[2] == 0 && Bb.cv[3] == 0 && Bb.cv[4] == 0 && Bb.cv[5] == 0) ? 1.f
+                                                                                                                : 0.f;
+  h[30] = (float)std::min(1.0, (std::min(ahi, bhi) - std::max(alo, blo)) / std::max(1.0, std::min(ahi - alo, bhi - blo)));
+  if (h[30] < 0) h[30] = 0;
+  h[31] = 1.f;  // bias-like constant
+}
+
 int load_desc(const char* text, size_t len, hgrd_desc** out) {
   try {
     if (!text || !out) raise(HGRD_EINVAL, "null argument");
@@ -964,6 +1057,26 @@ int hgrd_last_stats(hgrd_stats* s) {
   if (!s) return hgrd::fail(HGRD_EINVAL, "null argument");
   *s = hgrd::g_stats;
   return HGRD_OK;
+}
+
+int hgrd_pair_features(const hgrd_desc* d, float* out, uint8_t* pairs, uint32_t cap, uint32_t* n) {
+  if (!d || !n || (cap && (!out || !pairs))) return hgrd::fail(HGRD_EINVAL, "null argument");
+  if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound");
+  const hgrd::DProg& P = d->bound->prog;
+  uint32_t k = 0;
+  for (int a = 0; a < P.nacc; a++)
+    for (int b = a; b < P.nacc; b++) {
+      if (!(((P.einter[a] | P.eintra[a]) >> b) & 1u)) continue;  // never races (Sec. 6.1)
+      if (P.acc[a].dead || P.acc[b].dead) continue;
+      if (k < cap) {
+        hgrd::pair_features(*d, a, b, out + (size_t)k * HGRD_MLP_IN);
+        pairs[2 * k] = (uint8_t)a;
+        pairs[2 * k + 1] = (uint8_t)b;
+      }
+      k++;
+    }
+  *n = k;
+  return k > cap ? HGRD_ETRUNCATED : HGRD_OK;
 }
 
 int hgrd_debug_divmod(int64_t n, int64_t d, int wide, int64_t* q, int64_t* r) {

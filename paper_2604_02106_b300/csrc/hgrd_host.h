@@ -39,8 +39,18 @@ struct AccessDecl {
 };
 
 namespace hgrd {
+// What the ranker's features need about one bound access.
+struct AccInfo {
+  int kind = 0, scope = 1, arr = 0, shared = 0;
+  int64_t width = 4, G = 1;
+  int64_t cv[NVAR] = {};  // folded coefficients on tx ty tz bx by bz and the loop counters
+  int nnodes = 0, nguards = 0, loop_nodes = 0, dead = 0;
+  int64_t idx_lo = 0, idx_hi = 0, maxidx = 0, iv_lo = 0, iv_hi = 0;
+};
+
 // Result of hgrd_bind_host_params: the compiled program and host facts.
 struct Bound {
+  std::vector<AccInfo> acc_info;
   DProg prog;
   std::vector<int64_t> array_bytes, array_granule;
   uint64_t n_instances = 0;

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_library_exports_every_declared_symbol():
     hdr = open(os.path.join(ROOT, "include", "hgrd.h")).read()
-    declared = set(re.findall(r"\b(hgrd_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(hgrd_[a-z0-9_]+)\s*\(", hdr))
     assert declared, "no declarations found"
     L = hg.lib()
     for name in sorted(declared):

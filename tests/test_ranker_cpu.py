@@ -1,0 +1,52 @@
+"""CPU tests of the ranker's pieces: the FP64 MLP reference is pinned by
+central finite differences, and the host feature extractor lists exactly the
+pairs the race rule allows."""
+import numpy as np
+
+import paper_2604_02106_b300 as hg
+from paper_2604_02106_b300 import ranker
+import workloads
+from oracle import mlp_ref
+
+
+def test_reference_gradients_match_finite_differences():
+    rng = np.random.default_rng(1)
+    p = rng.normal(0, 0.15, mlp_ref.NPARAM)
+    x = rng.normal(0, 1, (7, mlp_ref.IN))
+    y = (rng.random(7) < 0.4).astype(float)
+    w = rng.uniform(0.5, 2.0, 7)
+    _, g = mlp_ref.loss_and_grad(p, x, y, w, rnd=False)
+    idx = np.concatenate([rng.choice(mlp_ref.NPARAM - 600, 40, replace=False), np.arange(mlp_ref.NPARAM - 600,
+                                                                                         mlp_ref.NPARAM, 37)])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp, _ = mlp_ref.loss_and_grad(p + e, x, y, w, rnd=False)
+        lm, _ = mlp_ref.loss_and_grad(p - e, x, y, w, rnd=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-4 * abs(fd), (i, fd, g[i])
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 3.0e38, 1e-30])
+    r = mlp_ref.bf16(vals)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -6 and r[3] == -2.5
+    assert abs(r[4] / 3.0e38 - 1) < 2 ** -8 and abs(r[5] / 1e-30 - 1) < 2 ** -8
+
+
+def test_pair_features_list_the_eligible_pairs():
+    w = workloads.config1(0)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    f, ab = ranker.pair_features(k)
+    assert f.shape == (len(ab), 96) and np.isfinite(f).all()
+    # accesses: array and kind per access line, pair rule of Sec. 6.1
+    acc = [l.split(" ; ")[0].split()[1:] for l in w.text.splitlines() if l.startswith("access")]
+    want = []
+    for a in range(len(acc)):
+        for b in range(a, len(acc)):
+            if acc[a][1] == acc[b][1] and not (acc[a][0] == "R" and acc[b][0] == "R"):
+                want.append((a, b))
+    assert ab == want
+    f2, ab2 = ranker.pair_features(k)
+    assert ab2 == ab and (f2 == f).all()
