@@ -205,9 +205,111 @@ def run_suite(args):
     print(json.dumps(line), flush=True)
 
 
+def _auc(scores, labels):
+    import numpy as np
+    order = np.argsort(scores)
+    ranks = np.empty(len(scores))
+    ranks[order] = np.arange(1, len(scores) + 1)
+    pos = labels > 0.5
+    npos, nneg = pos.sum(), (~pos).sum()
+    if npos == 0 or nneg == 0:
+        return None
+    return float((ranks[pos].sum() - npos * (npos + 1) / 2) / (npos * nneg))
+
+
+def run_ranked(args):
+    """Config 5: train the ranker on exact labels, then time-to-verdict on held-out kernels."""
+    import numpy as np
+    import torch
+    import workloads
+    import paper_2604_02106_b300 as hg
+    from paper_2604_02106_b300 import ranker as rk
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    X, y, i, nk = [], [], 0, 0
+    while sum(len(v) for v in y) < args.train_pairs:
+        ws = [workloads.config4(100000 + i + j, hi_exp=5.5) for j in range(2000)]
+        ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in ws]
+        res = hg.Batch(ks, witness_cap=1).check()
+        xb, yb = rk.labelled_pairs(ks, res)
+        X.append(xb)
+        y.append(yb)
+        i += 2000
+        nk += len(ks)
+    X, y = np.concatenate(X), np.concatenate(y)
+    t_label = time.perf_counter() - t0
+    r = rk.Ranker(seed=1)
+    t1 = time.perf_counter()
+    losses = r.fit(X, y, epochs=args.epochs, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    # held-out kernels
+    hw = [workloads.config4(200000 + j, hi_exp=6.0) for j in range(args.heldout)]
+    hk = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in hw]
+    modes = {}
+    rng = np.random.default_rng(0)
+    rand_scores = [rng.random(len(rk.pair_features(k)[1])) for k in hk]
+    # one workspace for every check (no allocation inside the timed loops)
+    wsb = torch.empty(max(rk.ranked_workspace_size(k) for k in hk), dtype=torch.uint8, device="cuda")
+    for k in hk[:20]:  # warm-up
+        k.check(cap=1 << 10, flags=hg.NO_PAIR, workspace=wsb)
+        rk.check_ranked(k, r, topk=args.topk, workspace=wsb)
+    plain_res = []
+    torch.cuda.synchronize()
+    ts = time.perf_counter()
+    for k in hk:
+        plain_res.append(k.check(cap=1 << 10, flags=hg.NO_PAIR, workspace=wsb))
+    modes["plain"] = {"s": time.perf_counter() - ts, "keys": sum(x.n_keys for x in plain_res),
+                      "form": "hgrd_check, full witness set"}
+    n_inst = sum(x.n_instances for x in plain_res)
+    for name, kw in (("unranked", {}), ("ranked", {"ranker": r, "min_score": 0.0}),
+                     ("ranked_always", {"ranker": r}), ("random_order", None)):
+        ts = time.perf_counter()
+        keys = stage1 = 0
+        for j, k in enumerate(hk):
+            if kw is None:
+                res, info = rk.check_ranked(k, scores=rand_scores[j], topk=args.topk, workspace=wsb)
+            else:
+                res, info = rk.check_ranked(k, topk=args.topk, workspace=wsb, **kw)
+            assert res.racy == plain_res[j].racy
+            keys += info["keys_ranked"] + info["keys_full"]
+            stage1 += info["stage"] == 1
+        modes[name] = {"s": time.perf_counter() - ts, "keys": keys, "ranked_stage_confirms": stage1}
+    # pair-score quality on the held-out pairs
+    S, L = [], []
+    for k, pr in zip(hk, plain_res):
+        f, ab = rk.pair_features(k)
+        if not ab:
+            continue
+        S.append(r.predict(torch.tensor(f, device="cuda")).cpu().numpy())
+        L.append(np.array([1.0 if (a, b) in pr.pairs else 0.0 for a, b in ab]))
+    auc = _auc(np.concatenate(S), np.concatenate(L))
+    for m in modes.values():
+        m["value"] = n_inst / m["s"]
+        m["ms_per_kernel"] = 1000 * m["s"] / len(hk)
+    line = {"metric": METRIC, "value": modes["ranked"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1000 * modes["ranked"]["s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64+bf16", "data": "synthetic",
+            "config": {"workload": f"{args.heldout} held-out corpus kernels (1e3..1e6 instances), "
+                                   f"ranker trained on {len(y)} exact pair labels from {nk} kernels",
+                       "instances": n_inst, "racy": sum(x.racy for x in plain_res), "topk": args.topk,
+                       "train_positive": int(y.sum()), "label_s": t_label, "train_s": t_train,
+                       "final_loss": float(np.mean(losses[-20:])), "pair_auc": auc},
+            "modes": modes,
+            "ranked_over_plain": modes["plain"]["s"] / modes["ranked"]["s"],
+            "ranked_over_unranked": modes["unranked"]["s"] / modes["ranked"]["s"],
+            "ranked_over_random": modes["random_order"]["s"] / modes["ranked"]["s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus"])
+    ap.add_argument("--train-pairs", type=int, default=1000000)
+    ap.add_argument("--heldout", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--topk", type=int, default=4)
+    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus", "ranked"])
     ap.add_argument("--items", type=int, default=1000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -224,6 +326,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.suite == "ranked":
+        run_ranked(args)
         return
     if args.suite != "stencil":
         run_suite(args)

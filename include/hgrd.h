@@ -270,7 +270,9 @@ int hgrd_mlp_sync_bf16(void* d_model, void* cuda_stream);
  * host_scores[n_pairs] in hgrd_pair_features order when given), runs a
  * restricted exact check of the accesses of the top `topk` pairs that stops
  * at its first race, and only if that finds none runs the full check (also
- * stopping at its first race).  The verdict's racy flag is exact; when racy,
+ * stopping at its first race).  The ranked check runs only when the best
+ * pair's score (a logit) reaches min_score, so kernels the model deems clean
+ * go straight to the full check.  The verdict's racy flag is exact; when racy,
  * the witnesses are the races found (each a real race), not the full set.
  * Workspace: hgrd_ranked_workspace_size. */
 typedef struct {
@@ -281,8 +283,8 @@ typedef struct {
 } hgrd_rank_info;
 int hgrd_ranked_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes);
 int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* d_model, const float* host_scores,
-                      uint32_t topk, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_witness* host_out,
-                      uint64_t cap, hgrd_verdict* v, hgrd_rank_info* info);
+                      uint32_t topk, float min_score, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                      hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, hgrd_rank_info* info);
 
 /* hgrd_check without a caller workspace, for callers that cannot allocate
  * device memory: code running while another component owns all device memory

@@ -882,7 +882,16 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     P.nthr = (int32_t)nthr;
     P.wpb = (int32_t)((nthr + 31) / 32);
     P.nblk = nblk;
-    P.nunits = nblk * P.wpb;
+    // long loops over few threads: split each simulated warp's loop vectors
+    // into chunks so that the expansion has enough independent units
+    {
+      const int64_t base_units = nblk * P.wpb;
+      int64_t chunks = 1;
+      if (nit > 64 && base_units < 32768) chunks = std::min<int64_t>((nit + 63) / 64, (32768 + base_units - 1) / base_units);
+      P.itc = std::max<int64_t>(1, (nit + chunks - 1) / chunks);
+      P.nchunk = nit > 0 ? (nit + P.itc - 1) / P.itc : 1;
+    }
+    P.nunits = nblk * P.wpb * P.nchunk;
     P.nloop = (int32_t)d.loops.size();
     for (int l = 0; l < MAXLOOP; l++) P.ub[l] = (int32_t)(l < P.nloop ? ub[l] : 1);
     for (int l = 0; l < P.nloop; l++)

@@ -93,7 +93,9 @@ struct alignas(16) DProg {
   int64_t nblk, nunits;
   int32_t nloop, nacc;
   int32_t ub[MAXLOOP];
-  int64_t nit;  // loop vectors per thread
+  int64_t nit;     // loop vectors per thread
+  int64_t itc;     // loop vectors per unit: a unit is (block, warp, chunk of itc loop vectors)
+  int64_t nchunk;  // chunks per (block, warp)
   int32_t wide, nfix, niter, nslot;
   int32_t nterm, nguard, pad0, pad1;
   // key layout: key = ((cell << IVB | iv - ivmin) << PB) | lin_b << (TB+AB) | lin_t << AB | access

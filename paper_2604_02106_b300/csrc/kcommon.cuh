@@ -70,8 +70,11 @@ __device__ __forceinline__ uint64_t expand_unit(const DProg* __restrict__ P, T* 
   const int bdx = P->block[0], bdy = P->block[1];
   const int64_t gdx = P->grid[0], gdy = P->grid[1];
   const int64_t nit = P->nit;
-  const int64_t b = u / wpb;
-  const int lt = (int)(u - b * wpb) * 32 + lane;
+  const int64_t bw = u / P->nchunk;                // (block, warp)
+  const int64_t it0 = (u - bw * P->nchunk) * P->itc;  // first loop vector of the chunk
+  const int64_t it1 = min(nit, it0 + P->itc);
+  const int64_t b = bw / wpb;
+  const int lt = (int)(bw - b * wpb) * 32 + lane;
   const bool act = lt < nthr;
   sl[0 * 32 + lane] = (T)(lt % bdx);
   sl[1 * 32 + lane] = (T)((lt / bdx) % bdy);
@@ -82,9 +85,17 @@ __device__ __forceinline__ uint64_t expand_unit(const DProg* __restrict__ P, T* 
   for (int l = 0; l < MAXLOOP; ++l) sl[(6 + l) * 32 + lane] = 0;
   run_ops<T>(P, 0, P->nfix, sl, lane);
   uint64_t oob = 0;
+  // loop counters of it0 (mixed radix, innermost loop fastest)
   int32_t ic[MAXLOOP] = {0, 0, 0, 0};
-  for (int64_t it = 0; it < nit; ++it) {
-    if (it > 0) {
+  if (it0 > 0) {  // it0 > 0 implies every loop bound is at least 1
+    int64_t r = it0;
+    for (int l = nloop - 1; l >= 0; --l) {
+      ic[l] = (int32_t)(r % P->ub[l]);
+      r /= P->ub[l];
+    }
+  }
+  for (int64_t it = it0; it < it1; ++it) {
+    if (it > it0) {
       int l = nloop - 1;
       while (l >= 0) {
         if (++ic[l] < P->ub[l]) break;

@@ -39,8 +39,8 @@ int hgrd_ranked_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, siz
 }
 
 int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* d_model, const float* host_scores,
-                      uint32_t topk, void* d_ws, size_t ws_bytes, void* stream, hgrd_witness* host_out,
-                      uint64_t cap, hgrd_verdict* v, hgrd_rank_info* info) {
+                      uint32_t topk, float min_score, void* d_ws, size_t ws_bytes, void* stream,
+                      hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, hgrd_rank_info* info) {
   if (!d || !v || !d_ws) return fail(HGRD_EINVAL, "null argument");
   if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound");
   size_t need = 0, base = 0;
@@ -57,8 +57,10 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
   std::vector<float> feat((size_t)MAXPAIRS * HGRD_MLP_IN);
   std::vector<uint8_t> ab(2 * MAXPAIRS);
   uint32_t np = 0;
-  rc = hgrd_pair_features(d, feat.data(), ab.data(), MAXPAIRS, &np);
-  if (rc < 0) return rc;
+  if (d_model || host_scores) {
+    rc = hgrd_pair_features(d, feat.data(), ab.data(), MAXPAIRS, &np);
+    if (rc < 0) return rc;
+  }
   inf.n_pairs = np;
   std::vector<float> score(np, 0.f);
   if (np && host_scores) {
@@ -81,7 +83,8 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
   if (o) oo = *o;
   oo.flags |= HGRD_NO_PAIR | HGRD_STOP_FIRST;
   // 2. restricted check of the accesses of the top-k pairs
-  if (np && (d_model || host_scores) && topk) {
+  const float best = np ? *std::max_element(score.begin(), score.end()) : 0.f;
+  if (np && (d_model || host_scores) && topk && best >= min_score) {
     std::vector<uint32_t> ord(np);
     std::iota(ord.begin(), ord.end(), 0u);
     std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return score[x] > score[y]; });

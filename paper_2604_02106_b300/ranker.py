@@ -39,7 +39,7 @@ def _setup():
                                       sz, vp, vp]
     L.hgrd_mlp_sync_bf16.argtypes = [vp, vp]
     L.hgrd_ranked_workspace_size.argtypes = [vp, C.POINTER(CheckOpts), C.POINTER(sz)]
-    L.hgrd_check_ranked.argtypes = [vp, C.POINTER(CheckOpts), vp, f32p, C.c_uint32, vp, sz, vp,
+    L.hgrd_check_ranked.argtypes = [vp, C.POINTER(CheckOpts), vp, f32p, C.c_uint32, C.c_float, vp, sz, vp,
                                     C.POINTER(Witness), C.c_uint64, C.POINTER(Verdict), C.POINTER(RankInfo)]
     for f in ["hgrd_pair_features", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad", "hgrd_mlp_train_step",
               "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size", "hgrd_check_ranked"]:
@@ -146,8 +146,16 @@ class Ranker:
         return torch.cat(losses).cpu().numpy() if losses else np.zeros(0)
 
 
+def ranked_workspace_size(kernel: Kernel) -> int:
+    L = _setup()
+    o = _opts()
+    n = C.c_size_t()
+    _raise(L.hgrd_ranked_workspace_size(kernel._h, C.byref(o), C.byref(n)))
+    return n.value
+
+
 def check_ranked(kernel: Kernel, ranker: Ranker | None = None, scores=None, topk: int = 4, cap: int = 1 << 16,
-                 stream=None):
+                 stream=None, min_score: float = float("-inf"), workspace=None):
     """hgrd_check_ranked: (Result, info dict).  With neither a ranker nor scores
     only the full check runs (stopping at its first race)."""
     import torch
@@ -155,7 +163,7 @@ def check_ranked(kernel: Kernel, ranker: Ranker | None = None, scores=None, topk
     o = _opts()
     n = C.c_size_t()
     _raise(L.hgrd_ranked_workspace_size(kernel._h, C.byref(o), C.byref(n)))
-    ws = getattr(kernel, "_rws", None)
+    ws = workspace if workspace is not None else getattr(kernel, "_rws", None)
     if ws is None or ws.numel() < n.value:
         ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
         kernel._rws = ws
@@ -167,7 +175,7 @@ def check_ranked(kernel: Kernel, ranker: Ranker | None = None, scores=None, topk
         sc = np.ascontiguousarray(scores, dtype=np.float32)
     rc = L.hgrd_check_ranked(kernel._h, C.byref(o), C.c_void_p(ranker.model.data_ptr()) if ranker else None,
                              sc.ctypes.data_as(C.POINTER(C.c_float)) if sc is not None else None, topk,
-                             C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), out, cap, C.byref(v),
+                             min_score, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), out, cap, C.byref(v),
                              C.byref(info))
     _raise(rc)
     k = min(cap, v.n_witness)

@@ -220,3 +220,18 @@ def test_restricted_and_stop_first(seed):
     full = {x[:5]: x[5] for x in o.witnesses}
     for x in f.witnesses:
         assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
+
+
+@pytest.mark.parametrize("bounds", [(300,), (7, 130), (3, 5, 7, 11)])
+def test_long_loops_few_threads(bounds):
+    # loop vectors of one simulated warp are split into chunks; the chunk seams
+    # must keep emission order and the counters exact
+    loops = "".join(f"loop i{l} {b}\n" for l, b in enumerate(bounds))
+    off = "i0"
+    for l, b in enumerate(bounds[1:], 1):
+        off = f"({off})*{b} + i{l}"
+    text = ("kernel ll\n" + loops + "array a global 1048576\narray s shared 4096\n"
+            f"access W a ; width 4 ; idx ({off}) % 997 + tx\n"
+            f"access R a ; width 4 ; iv 1 ; idx ({off}) % 13\n"
+            f"access W s ; width 4 ; idx ({off}) % 64 + tx\n")
+    _same(*_both(text, Binding((1, 1, 1), (3, 1, 1), ())))
