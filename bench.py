@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--ref-warmup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=1024)
+    ap.add_argument("--no-sort-tune", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,6 +345,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    tuned = None
+    if not args.no_sort_tune:
+        best, ms = hg.sort_tune()
+        tuned = {"variant": best, "pass_ms_32M_keys": [round(x, 4) for x in ms]}
     w = workloads.config2(rank, planted=True, W=args.side, H=args.side)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     ws = k.workspace()
@@ -427,7 +432,7 @@ def main():
                 "config": {"workload": WORKLOAD, "instances": n_inst, "keys": n_keys,
                            "witnesses": res.n_witness, "sort_passes": hg.stats()["sort_passes"],
                            "l2": f"keys {8 * n_keys / 1e9:.2f} GB per buffer > 126 MB L2; no flush needed",
-                           "parallelism": f"replicas{world}"},
+                           "parallelism": f"replicas{world}", "sort_tuning": tuned},
                 "e2e": e2e,
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
                              "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": peak_kind,

@@ -27,7 +27,7 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free", "hgrd_pair_features",
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
-           "hgrd_check_ranked"]
+           "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant"]
 BATCH_GRAPH = 1
 
 
@@ -349,6 +349,33 @@ class Batch:
         o = BatchOpts()
         _raise(lib().hgrd_batch_tune(self._h, C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), C.byref(o)))
         return {"small_keys": o.small_keys, "streams": o.streams}
+
+
+def sort_tune(workspace_bytes: int = 600 << 20, stream=None):
+    """hgrd_sort_tune: time the onesweep CTA shapes, keep the fastest; returns (best, [ms...])."""
+    import torch
+    L = lib()
+    L.hgrd_sort_tune.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                 C.c_int]
+    L.hgrd_sort_tune.restype = C.c_int
+    ws = torch.empty(workspace_bytes, dtype=torch.uint8, device="cuda")
+    best = C.c_int()
+    ms = (C.c_float * 16)()
+    _raise(L.hgrd_sort_tune(C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), C.byref(best), ms, 16))
+    n = C.c_int()
+    L.hgrd_sort_variant.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    _raise(L.hgrd_sort_variant(-1, None, C.byref(n)))
+    return best.value, [ms[i] for i in range(n.value)]
+
+
+def sort_variant(v: int = -1):
+    """Select (v >= 0) or query the onesweep CTA shape of the current device."""
+    L = lib()
+    L.hgrd_sort_variant.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.hgrd_sort_variant.restype = C.c_int
+    cur, n = C.c_int(), C.c_int()
+    _raise(L.hgrd_sort_variant(v, C.byref(cur), C.byref(n)))
+    return cur.value, n.value
 
 
 def stats() -> dict:

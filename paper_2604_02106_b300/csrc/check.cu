@@ -37,7 +37,7 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
   const uint64_t scan_n = std::max(nunits, L.raw_cap);
-  const uint64_t tiles = std::max((nk + RS_TILE - 1) / RS_TILE, (L.raw_cap + RS_TILE - 1) / RS_TILE);
+  const uint64_t tiles = std::max((nk + RS_MIN_TILE - 1) / RS_MIN_TILE, (L.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   L.status_words = tiles * RS_RADIX;
   size_t off = 0;
   auto take = [&](size_t bytes) {

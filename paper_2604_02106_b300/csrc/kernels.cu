@@ -247,108 +247,141 @@ __global__ void __launch_bounds__(256) hist_scan_kernel(const uint64_t* __restri
 constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull << 54) - 1;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-__global__ void __launch_bounds__(RS_THREADS, 3) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                             const uint64_t* n_dev, uint64_t n_max, int shift,
-                                                             const uint64_t* __restrict__ gbase, uint64_t* status,
-                                                             unsigned long long* ticket, uint32_t epoch,
-                                                             uint64_t* err, uint64_t* next_hist, int next_shift) {
-  __shared__ uint32_t whist[RS_THREADS / 32][RS_RADIX];
-  __shared__ uint32_t nhist[RS_RADIX];  // digit counts of the next pass, over the tiles this CTA ranks
-  __shared__ uint32_t tstart[RS_RADIX];
-  __shared__ uint64_t gofs[RS_RADIX];
-  __shared__ uint64_t ws[8];
-  __shared__ uint64_t stage[RS_TILE];
-  __shared__ uint64_t s_tile;
+// Onesweep pass, templated on the CTA shape (threads T, keys per thread KPT,
+// CTAs per SM the registers are budgeted for); the sort autotuner picks the
+// shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
+// handled in increasing order and the look-back only waits on tiles held by
+// running CTAs.
+template <int T, int KPT, int MINB>
+__global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                          const uint64_t* n_dev, uint64_t n_max, int shift,
+                                                          const uint64_t* __restrict__ gbase, uint64_t* status,
+                                                          unsigned long long* ticket, uint32_t epoch, uint64_t* err,
+                                                          uint64_t* next_hist, int next_shift) {
+  constexpr int W = T / 32, TILE = T * KPT;
+  extern __shared__ __align__(16) unsigned char osm[];
+  uint32_t* whist = reinterpret_cast<uint32_t*>(osm);  // [W][256]
+  uint32_t* nhist = whist + W * RS_RADIX;               // digit counts of the next pass
+  uint32_t* tstart = nhist + RS_RADIX;                  // tile-local start of each digit
+  uint32_t* dsum = tstart + RS_RADIX;                   // tile count of each digit
+  uint64_t* gofs = reinterpret_cast<uint64_t*>(dsum + RS_RADIX);
+  uint64_t* stage = gofs + RS_RADIX;
+  uint64_t* s_tile = stage + TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t n = dev_n(n_dev, n_max);
-  const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const uint64_t ntiles = (n + TILE - 1) / TILE;
   const uint64_t ep = (uint64_t)epoch << 56;
-  nhist[threadIdx.x] = 0;
+  for (int d = threadIdx.x; d < RS_RADIX; d += T) nhist[d] = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1ull);
-    for (int i = threadIdx.x; i < (RS_THREADS / 32) * RS_RADIX; i += RS_THREADS) (&whist[0][0])[i] = 0;
+    if (threadIdx.x == 0) *s_tile = atomicAdd(ticket, 1ull);
+    for (int i = threadIdx.x; i < W * RS_RADIX; i += T) whist[i] = 0;
     __syncthreads();
-    const uint64_t tile = s_tile;
+    const uint64_t tile = *s_tile;
     if (tile >= ntiles) break;
-    const uint64_t base = tile * RS_TILE;
-    const uint64_t wbase = base + (uint64_t)warp * (RS_KPT * 32);
-    static_assert(RS_THREADS == RS_RADIX, "one thread per digit");
-    uint64_t k[RS_KPT];
-    uint32_t dr[RS_KPT];  // digit in bits 0..8 (256 = no key), warp-local rank above
+    const uint64_t base = tile * TILE;
+    const uint64_t wbase = base + (uint64_t)warp * (KPT * 32);
+    uint64_t k[KPT];
+    uint32_t dr[KPT];  // digit in bits 0..8 (256 = no key), warp-local rank above
 #pragma unroll
-    for (int s = 0; s < RS_KPT; ++s) {
+    for (int s = 0; s < KPT; ++s) {
       const uint64_t i = wbase + (uint64_t)s * 32 + lane;
       k[s] = i < n ? in[i] : 0;
     }
     const unsigned lt = lanemask_lt();
     // warp-level stable ranking, slot-major = memory order
 #pragma unroll
-    for (int s = 0; s < RS_KPT; ++s) {
+    for (int s = 0; s < KPT; ++s) {
       const uint64_t i = wbase + (uint64_t)s * 32 + lane;
       const uint32_t d = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
       if (next_hist && d < 256u) atomicAdd(&nhist[(uint32_t)(k[s] >> next_shift) & 255u], 1u);
       const unsigned peers = __match_any_sync(FULL, d);
       uint32_t old = 0;
-      if (d < 256u) old = whist[warp][d];
+      if (d < 256u) old = whist[warp * RS_RADIX + d];
       dr[s] = d | ((old + __popc(peers & lt)) << 9);
       __syncwarp();
-      if (d < 256u && lane == __ffs(peers) - 1) whist[warp][d] = old + __popc(peers);
+      if (d < 256u && lane == __ffs(peers) - 1) whist[warp * RS_RADIX + d] = old + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
-    // thread t owns digit t: counts across warps, warp-exclusive prefixes
-    const int t = threadIdx.x;
-    uint32_t sum = 0;
+    // digits: counts across warps, warp-exclusive prefixes, look-back
+    for (int t = threadIdx.x; t < RS_RADIX; t += T) {
+      uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < RS_THREADS / 32; ++w) {
-      const uint32_t c = whist[w][t];
-      whist[w][t] = sum;
-      sum += c;
-    }
-    uint64_t* my = status + tile * RS_RADIX + t;
-    uint64_t excl = 0;
-    if (tile == 0) {
-      st_relaxed(my, ep | ST_PREFIX | sum);
-    } else {
-      st_relaxed(my, ep | ST_AGG | sum);
-      uint64_t p = tile - 1;
-      uint32_t spins = 0;
-      for (;;) {
-        const uint64_t wv = ld_relaxed(status + p * RS_RADIX + t);
-        const bool ready = (wv >> 56) == epoch && (wv & (3ull << 54)) != 0;
-        if (!ready) {
-          if (++spins > SPIN_LIMIT) {
-            atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-          continue;
-        }
-        excl += wv & ST_VAL;
-        if ((wv & ST_PREFIX) || p == 0) break;
-        --p;
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = whist[w * RS_RADIX + t];
+        whist[w * RS_RADIX + t] = sum;
+        sum += c;
       }
-      st_relaxed(my, ep | ST_PREFIX | (excl + sum));
+      dsum[t] = sum;
+      uint64_t* my = status + tile * RS_RADIX + t;
+      uint64_t excl = 0;
+      if (tile == 0) {
+        st_relaxed(my, ep | ST_PREFIX | sum);
+      } else {
+        st_relaxed(my, ep | ST_AGG | sum);
+        uint64_t p = tile - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const uint64_t wv = ld_relaxed(status + p * RS_RADIX + t);
+          const bool ready = (wv >> 56) == epoch && (wv & (3ull << 54)) != 0;
+          if (!ready) {
+            if (++spins > SPIN_LIMIT) {
+              atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+            continue;
+          }
+          excl += wv & ST_VAL;
+          if ((wv & ST_PREFIX) || p == 0) break;
+          --p;
+        }
+        st_relaxed(my, ep | ST_PREFIX | (excl + sum));
+      }
+      gofs[t] = gbase[t] + excl;
     }
-    gofs[t] = gbase[t] + excl;
-    tstart[t] = (uint32_t)block_excl_scan(sum, ws, nullptr);
+    __syncthreads();
+    if (warp == 0) {  // tile-local digit starts: lane l scans digits 8l .. 8l+7
+      uint32_t v[8], s8 = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = dsum[lane * 8 + j];
+        s8 += v[j];
+      }
+      uint32_t x = s8;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t run = x - s8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        tstart[lane * 8 + j] = run;
+        run += v[j];
+      }
+    }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < RS_KPT; ++s) {
+    for (int s = 0; s < KPT; ++s) {
       const uint32_t d = dr[s] & 511u;
-      if (d < 256u) stage[tstart[d] + whist[warp][d] + (dr[s] >> 9)] = k[s];
+      if (d < 256u) stage[tstart[d] + whist[warp * RS_RADIX + d] + (dr[s] >> 9)] = k[s];
     }
     __syncthreads();
-    const uint64_t cnt = (n - base) < (uint64_t)RS_TILE ? (n - base) : (uint64_t)RS_TILE;
-    for (uint32_t i = threadIdx.x; i < cnt; i += RS_THREADS) {
+    const uint64_t cnt = (n - base) < (uint64_t)TILE ? (n - base) : (uint64_t)TILE;
+    for (uint32_t i = threadIdx.x; i < cnt; i += T) {
       const uint64_t key = stage[i];
       const uint32_t d = (uint32_t)((key >> shift) & 255);
       out[gofs[d] + (i - tstart[d])] = key;
     }
     __syncthreads();
   }
-  if (next_hist && nhist[threadIdx.x])
-    atomicAdd((unsigned long long*)&next_hist[threadIdx.x], (unsigned long long)nhist[threadIdx.x]);
+  for (int d = threadIdx.x; d < RS_RADIX; d += T)
+    if (next_hist && nhist[d]) atomicAdd((unsigned long long*)&next_hist[d], (unsigned long long)nhist[d]);
+}
+
+template <int T, int KPT>
+constexpr size_t onesweep_smem() {
+  return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16;
 }
 
 // ------------------------------------------------------------------ conflict scan, phase A
@@ -400,6 +433,34 @@ __device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64
   const unsigned RS = __ballot_sync(FULL, rs), SS = __ballot_sync(FULL, ss), TD = __ballot_sync(FULL, td);
   const unsigned BD = __ballot_sync(FULL, bd), WM = __ballot_sync(FULL, w);
   const unsigned below = X.below;
+  if (WM == 0 && !c.subW && !c.runW) {
+    // no writer in this step and none open: no run can become a candidate
+    // here; only the boundaries and the thread / block flags move on
+    const int ql = top_bit(RS);
+    if (ql >= 0) {
+      c.start = p + ql;
+      c.owned = c.start >= X.r0 && c.start < X.r1;
+      c.runBD = (BD & ~m_lt(ql)) != 0;
+      c.runC = false;
+    } else {
+      c.runBD |= BD != 0;
+    }
+    const int tl = top_bit(SS);
+    c.subTD = tl >= 0 ? (TD & ~m_lt(tl)) != 0 : (c.subTD || TD != 0);
+    const uint64_t rem = X.n - p;
+    c.prev = __shfl_sync(FULL, k, rem >= 32 ? 31 : (int)rem - 1);
+    if (c.owned && p + 32 - c.start > (uint64_t)CA_LONG) {  // as below: a writer may still follow
+      if (lane == 0) {
+        const uint64_t g = atomicAdd((unsigned long long*)&X.counters[C_NCAND], 1ull);
+        if (g < X.cand_cap) {
+          X.cand[2 * g] = c.start;
+          X.cand[2 * g + 1] = 0;
+        }
+      }
+      c.owned = false;
+    }
+    return p + 32 >= X.r1 && !c.owned;
+  }
   // candidacy of the sub-run that ends just before this lane's sub-run start
   const int t = top_bit(SS & below);
   const unsigned rs_sub = t >= 0 ? (below & ~m_lt(t)) : below;
@@ -671,16 +732,43 @@ cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gb
   return cudaGetLastError();
 }
 
+struct SortVariant {
+  const void* fn;
+  int threads, kpt;
+  size_t smem;
+};
+const SortVariant* sort_variants(int* count) {
+  static const SortVariant v[] = {
+      {(const void*)onesweep_kernel<256, 16, 3>, 256, 16, onesweep_smem<256, 16>()},
+      {(const void*)onesweep_kernel<256, 12, 4>, 256, 12, onesweep_smem<256, 12>()},
+      {(const void*)onesweep_kernel<512, 8, 2>, 512, 8, onesweep_smem<512, 8>()},
+      {(const void*)onesweep_kernel<384, 12, 2>, 384, 12, onesweep_smem<384, 12>()},
+      {(const void*)onesweep_kernel<256, 24, 2>, 256, 24, onesweep_smem<256, 24>()},
+      {(const void*)onesweep_kernel<128, 16, 8>, 128, 16, onesweep_smem<128, 16>()},
+  };
+  *count = (int)(sizeof(v) / sizeof(v[0]));
+  return v;
+}
+int g_sort_variant[64];  // per device; 0 = the default shape
+
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist, int next_shift) {
-  uint64_t tiles = (n_max + RS_TILE - 1) / RS_TILE;
-  int grid = occupancy_grid((const void*)onesweep_kernel, RS_THREADS, 0, L.nsm);
+  int nv = 0, dev = 0;
+  const SortVariant* V = sort_variants(&nv);
+  cudaGetDevice(&dev);
+  const SortVariant& S = V[(dev >= 0 && dev < 64 && g_sort_variant[dev] < nv) ? g_sort_variant[dev] : 0];
+  const uint64_t tile = (uint64_t)S.threads * S.kpt;
+  const uint64_t tiles = (n_max + tile - 1) / tile;
+  cudaError_t e = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
+  if (e != cudaSuccess) return e;
+  int grid = occupancy_grid(S.fn, S.threads, S.smem, L.nsm);
   if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
-  onesweep_kernel<<<grid, RS_THREADS, 0, L.s>>>(in, out, n_dev, n_max, shift, gbase, status,
-                                                (unsigned long long*)ticket, epoch, err, next_hist, next_shift);
+  unsigned long long* tk = (unsigned long long*)ticket;
+  void* args[] = {(void*)&in, (void*)&out, (void*)&n_dev, (void*)&n_max, (void*)&shift, (void*)&gbase,
+                  (void*)&status, (void*)&tk, (void*)&epoch, (void*)&err, (void*)&next_hist, (void*)&next_shift};
   (*L.launches)++;
-  return cudaGetLastError();
+  return cudaLaunchKernel(S.fn, dim3(grid), dim3(S.threads), args, S.smem, L.s);
 }
 
 cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
@@ -724,3 +812,102 @@ cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* 
 }
 
 }  // namespace hgrd
+
+// ------------------------------------------------------------------ sort autotuner
+namespace hgrd {
+namespace {
+__global__ void random_keys_kernel(uint64_t* k, uint64_t n, uint64_t seed) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    k[i] = z ^ (z >> 31);
+  }
+}
+}  // namespace
+}  // namespace hgrd
+
+#include "hgrd_host.h"
+
+extern "C" int hgrd_sort_variant(int set, int* current, int* count) {
+  using namespace hgrd;
+  int nv = 0, dev = 0;
+  sort_variants(&nv);
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return fail(HGRD_EUNSUPPORTED, "device index too large");
+  if (set >= nv) return fail(HGRD_EINVAL, "no such sort variant");
+  if (set >= 0) g_sort_variant[dev] = set;
+  if (current) *current = g_sort_variant[dev];
+  if (count) *count = nv;
+  return HGRD_OK;
+}
+
+extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* best, float* ms, int cap) {
+  using namespace hgrd;
+  if (!d_ws) return fail(HGRD_EINVAL, "null workspace");
+  cudaStream_t s = (cudaStream_t)stream;
+  int nv = 0, dev = 0;
+  const SortVariant* V = sort_variants(&nv);
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return fail(HGRD_EUNSUPPORTED, "device index too large");
+  // keys in | keys out | status | hist | gbase | counters
+  const size_t fixed = 3 * 4096 + 256;
+  uint64_t n = ws_bytes > fixed ? (uint64_t)((ws_bytes - fixed) / (16.0 + 256.0 * 8 / RS_MIN_TILE)) : 0;
+  n = std::min<uint64_t>(n, 1ull << 25) & ~(uint64_t)4095;
+  if (n < 4096) return fail(HGRD_ENOMEM, "sort tuning workspace too small");
+  char* w = (char*)d_ws;
+  uint64_t* kin = (uint64_t*)w;
+  uint64_t* kout = kin + n;
+  uint64_t* status = kout + n;
+  const size_t sw = ((n + RS_MIN_TILE - 1) / RS_MIN_TILE) * RS_RADIX;
+  uint64_t* hist = status + sw;
+  uint64_t* gb = hist + 256;
+  uint64_t* cnt = gb + 256;  // n, ticket, err
+  uint64_t launches = 0;
+  Launch L{s, 1, &launches};
+  cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
+  random_keys_kernel<<<L.nsm * 4, 256, 0, s>>>(kin, n, 0x5EED);
+  cudaMemcpyAsync(cnt, &n, 8, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(hist, 0, 256 * 8, s);
+  launch_histogram(L, kin, cnt, n, 0, 1, hist);
+  launch_hist_scan(L, hist, gb, 1);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved = g_sort_variant[dev];
+  float best_ms = 1e30f;
+  int best_v = saved;
+  uint32_t epoch = 1;
+  for (int v = 0; v < nv; v++) {
+    g_sort_variant[dev] = v;
+    float vbest = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+      cudaMemsetAsync(status, 0, sw * 8, s);
+      cudaMemsetAsync(cnt + 1, 0, 16, s);
+      cudaEventRecord(e0, s);
+      cudaError_t e = launch_onesweep(L, kin, kout, cnt, n, 0, gb, status, cnt + 1, epoch, cnt + 2);
+      cudaEventRecord(e1, s);
+      if (e != cudaSuccess) {
+        g_sort_variant[dev] = saved;
+        return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e));
+      }
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) vbest = std::min(vbest, t);
+    }
+    if (ms && v < cap) ms[v] = vbest;
+    if (vbest < best_ms) {
+      best_ms = vbest;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  uint64_t errw = 0;
+  cudaMemcpy(&errw, cnt + 2, 8, cudaMemcpyDeviceToHost);
+  g_sort_variant[dev] = best_v;
+  if (best) *best = best_v;
+  if (errw) return fail(HGRD_ETIMEOUT, "a bounded device wait gave up during sort tuning");
+  return HGRD_OK;
+}

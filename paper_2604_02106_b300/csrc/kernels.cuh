@@ -8,9 +8,7 @@ namespace hgrd {
 
 // Work shapes
 constexpr int EXP_THREADS = 256;   // 8 warps; one simulated warp of the user kernel per warp
-constexpr int RS_THREADS = 256;    // onesweep: 8 warps x 16 keys
-constexpr int RS_KPT = 16;
-constexpr int RS_TILE = RS_THREADS * RS_KPT;
+constexpr int RS_MIN_TILE = 1536;  // smallest onesweep tile of the shapes the sort autotuner picks from
 constexpr int RS_RADIX = 256;
 constexpr int CA_THREADS = 256;    // candidate scan
 constexpr int CA_LONG = 1 << 16;   // a run longer than this is handed to the exact scan unmeasured

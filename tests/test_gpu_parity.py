@@ -235,3 +235,17 @@ def test_long_loops_few_threads(bounds):
             f"access R a ; width 4 ; iv 1 ; idx ({off}) % 13\n"
             f"access W s ; width 4 ; idx ({off}) % 64 + tx\n")
     _same(*_both(text, Binding((1, 1, 1), (3, 1, 1), ())))
+
+
+def test_every_sort_shape_gives_the_same_result():
+    # the sort autotuner chooses among onesweep CTA shapes; each must be exact
+    cur, n = hg.sort_variant()
+    try:
+        ws = [workloads.config1(2), workloads.config2(0, planted=True, W=128, H=128, K=8)]
+        want = [oracle.check(w.text, w.binding) for w in ws]
+        for v in range(n):
+            hg.sort_variant(v)
+            for w, o in zip(ws, want):
+                _same(hg.check(w.text, w.binding, cap=1 << 20), o)
+    finally:
+        hg.sort_variant(cur)
