@@ -402,7 +402,7 @@ __device__ __forceinline__ int top_bit(unsigned m) { return m ? 31 - __clz(m) : 
 
 struct CandCarry {
   uint64_t prev, start;
-  bool owned, runW, runBD, runC, subW, subTD;
+  bool owned, runW, runBD, runC, subW, subTD, glob;  // glob: the open run is in global memory
 };
 
 struct CandCtx {
@@ -433,15 +433,19 @@ __device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64
   const unsigned RS = __ballot_sync(FULL, rs), SS = __ballot_sync(FULL, ss), TD = __ballot_sync(FULL, td);
   const unsigned BD = __ballot_sync(FULL, bd), WM = __ballot_sync(FULL, w);
   const unsigned below = X.below;
-  if (WM == 0 && !c.subW && !c.runW) {
-    // no writer in this step and none open: no run can become a candidate
-    // here; only the boundaries and the thread / block flags move on
+  if (WM == 0 && !c.subW && !(c.runW && c.glob) && !c.runC) {
+    // no writer in this step and none open that could still race: no run can
+    // become a candidate here (in shared memory only the open sub-run's
+    // writer matters); only the boundaries and the thread / block flags move on
     const int ql = top_bit(RS);
     if (ql >= 0) {
       c.start = p + ql;
       c.owned = c.start >= X.r0 && c.start < X.r1;
       c.runBD = (BD & ~m_lt(ql)) != 0;
       c.runC = false;
+      c.runW = false;
+      const uint64_t kq = __shfl_sync(FULL, k, ql);
+      c.glob = X.g_all || kq < X.g_lim;
     } else {
       c.runBD |= BD != 0;
     }
@@ -498,6 +502,8 @@ __device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64
     c.runW = (WM & ~m_lt(ql)) != 0;
     c.runBD = (BD & ~m_lt(ql)) != 0;
     c.runC = (CS & ~m_le(ql)) != 0;
+    const uint64_t kq = __shfl_sync(FULL, k, ql);
+    c.glob = X.g_all || kq < X.g_lim;
   } else {
     c.runW |= WM != 0;
     c.runBD |= BD != 0;
@@ -561,6 +567,7 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
     c.prev = X.r0 > 0 ? keys[X.r0 - 1] : 0;
     c.start = 0;
     c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
+    c.glob = X.g_all || c.prev < X.g_lim;
     bool done = false;
     for (uint64_t p = X.r0; !done && p < n; p += 32 * CA_AHEAD) {
       uint64_t kk[CA_AHEAD];
