@@ -114,13 +114,16 @@ typedef struct {
                                HGRD_PROFILE: time every pipeline stage with CUDA events;
                                HGRD_STOP_FIRST: stop the exact scan once one race is confirmed
                                (the verdict is racy/clean exactly; witnesses and counts are then
-                               a subset, each witness a real race) */
+                               a subset, each witness a real race);
+                               HGRD_NO_SPLIT: sort the keys of shared arrays with the global ones
+                               instead of checking them in per-block bins (same result; for
+                               comparison and testing) */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
   uint32_t reserved;
 } hgrd_check_opts;
-enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4 };
+enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4, HGRD_NO_SPLIT = 8 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
  * stream around the stage's kernels. */
@@ -138,6 +141,10 @@ typedef struct {
   uint32_t int64_path;      /* 1 when index arithmetic needed 64-bit integers */
   uint64_t h2d_bytes;       /* host->device bytes the call copied (the compiled program) */
   uint64_t d2h_bytes;       /* device->host bytes the call copied (counters, witnesses, pair search) */
+  uint64_t n_sorted_keys;   /* keys that went through the radix sort */
+  uint64_t n_binned_keys;   /* shared-array keys written into candidate bins (block-local mode) */
+  uint32_t shared_bins;     /* 1 when the shared-array keys were checked in per-block bins */
+  uint32_t reserved;
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,

@@ -19,6 +19,7 @@ ERRORS = {1: "ETRUNCATED", -1: "EINVAL", -2: "EPARSE", -3: "EBIND", -4: "EHOSTCO
 NO_PAIR = 1
 PROFILE = 2
 STOP_FIRST = 4
+NO_SPLIT = 8
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -82,7 +83,8 @@ class StageTime(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("n_candidates", C.c_uint64), ("n_raw_witness", C.c_uint64),
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
-                ("d2h_bytes", C.c_uint64)]
+                ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
+                ("shared_bins", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 _lib = None

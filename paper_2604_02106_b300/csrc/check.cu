@@ -22,7 +22,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
-      pairs, total;
+      pairs, stbl, sbase, total;
   uint64_t raw_cap, pair_cap, status_words;
 };
 
@@ -60,6 +60,10 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   L.flags = take(L.raw_cap * 8);
   L.excl = take(L.raw_cap * 8);
   L.pairs = take((size_t)L.pair_cap * sizeof(PairRec));
+  // block-local mode: bin table (start << 32 | count per candidate bin) and
+  // the base of every block's candidate keys
+  L.stbl = take(P.smode ? (size_t)P.nblk * (size_t)P.nsbins * 8 : 0);
+  L.sbase = take(P.smode ? (size_t)P.nblk * 8 : 0);
   L.total = off;
   return L;
 }
@@ -133,9 +137,12 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // program with the other accesses removed (their keys are never made)
   const uint32_t only = o ? o->only_accesses : 0u;
   const bool restricted = only != 0 && only != 0xffffffffu && !dprog_resident;
+  // block-local mode for shared-array keys unless the caller asks for one global sort
+  const bool split = HP.smode && !(o && (o->flags & HGRD_NO_SPLIT));
   g_stats = hgrd_stats{};
   g_stats.int64_path = B.wide;
-  g_stats.sort_passes = (uint32_t)B.sort_passes;
+  g_stats.sort_passes = (uint32_t)(split ? B.sort_passes_split : B.sort_passes);
+  g_stats.shared_bins = split ? 1u : 0u;
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
@@ -159,16 +166,30 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   g_prof.mark("setup");
 
-  const int P = B.sort_passes;
+  const int P = split ? B.sort_passes_split : B.sort_passes;
   uint64_t* keysA = U(W.keysA);
   uint64_t* keysB = U(W.keysB);
-  uint64_t* nkeys = cnt + C_NKEYS;
-  CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), 1, cnt, nullptr, nullptr, 0));
-  g_prof.mark("expand_count");
-  CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
-  g_prof.mark("unit_scan");
-  CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
-  g_prof.mark("expand_write");
+  // keys the sort and the candidate scan walk: all of them, or the global
+  // ones in block-local mode (the candidate bins follow them in the final buffer)
+  uint64_t* nkeys = cnt + (split ? C_NG : C_NKEYS);
+  if (split) {
+    CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), cnt,
+                           U(W.stbl), U(W.sbase)));
+    g_prof.mark("expand_count");
+    CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    g_prof.mark("unit_scan");
+    CK(launch_expand_block(L, 4, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr,
+                           cnt, U(W.stbl), U(W.sbase)));
+    g_prof.mark("expand_write");
+  } else {
+    CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), 1, cnt, nullptr, nullptr,
+                     0));
+    g_prof.mark("expand_count");
+    CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    g_prof.mark("unit_scan");
+    CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
+    g_prof.mark("expand_write");
+  }
   uint64_t* in = keysA;
   uint64_t* out = keysB;
   // the expansion counted digit 0; each pass counts the digit of the next
@@ -185,8 +206,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // `in` holds the sorted keys; `out` is free for the candidate list
   const uint64_t cand_cap = std::max<uint64_t>(B.nkeys_max / 2, 1);
   CK(launch_candidates(L, in, nkeys, dprog, out, cand_cap, cnt));
+  if (split) CK(launch_shared_cand(L, HP, U(W.stbl), U(W.sbase), out, cand_cap, cnt));
   g_prof.mark("candidates");
-  CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt, o && (o->flags & HGRD_STOP_FIRST)));
+  CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt, o && (o->flags & HGRD_STOP_FIRST),
+                  split));
   g_prof.mark("exact");
   // canonical order of the witnesses: radix sort of the packed words
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
@@ -246,6 +269,8 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(cudaStreamSynchronize(s));
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
+  g_stats.n_sorted_keys = g_stats.shared_bins ? cnt[C_NG] : cnt[C_NKEYS];
+  g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
   g_stats.n_raw_witness = cnt[C_NRAW];
   if (cnt[C_NCAND] > std::max<uint64_t>(B.nkeys_max / 2, 1))
     return fail(HGRD_EUNSUPPORTED, "candidate list overflow");

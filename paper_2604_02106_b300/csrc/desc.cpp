@@ -951,7 +951,39 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (!P.acc[a].dead) kmax += (unsigned __int128)nblk * nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
     if (kmax >= ((unsigned __int128)1 << 40)) raise(HGRD_EUNSUPPORTED, "more than 2^40 keys");
     B.nkeys_max = (uint64_t)kmax;
+    // Block-local mode: shared-memory runs never leave their block and a
+    // shared-memory race needs two threads of one block in one interval
+    // (Table 2), so shared keys can be counted per (granule, interval) bin of
+    // their block instead of being sorted with the global ones.  Worth it when
+    // a block has several simulated warps to keep one CTA busy; the bins of a
+    // block must fit shared memory next to the program and the slot files,
+    // the bin table of all blocks must stay at most 2^25 entries, and one
+    // block's shared keys must be countable in 32 bits.
+    {
+      uint64_t sgran = 0;
+      for (int li = 0; li < P.nlay; li++)
+        if (P.lay_shared[li]) {
+          for (int a = 0; a < P.nacc; a++)
+            if (d.acc[a].arr == P.lay_arr[li]) P.acc[a].sgbase = (int64_t)sgran;
+          sgran += P.lay_ngran[li];
+        }
+      P.niv = (int32_t)((ivmax - ivmin) + 1);
+      P.nsbins = (int64_t)(sgran * (uint64_t)P.niv);
+      const int64_t upb = (int64_t)P.wpb * P.nchunk;
+      bool any_shared_live = false;
+      for (int a = 0; a < P.nacc; a++) any_shared_live |= !P.acc[a].dead && P.acc[a].shared;
+      unsigned __int128 per_block = 0;
+      for (int a = 0; a < P.nacc; a++)
+        if (!P.acc[a].dead && P.acc[a].shared) per_block += (unsigned __int128)nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
+      const uint64_t smem = sizeof(DProg) + (uint64_t)EXP_THREADS * nslot * (wide ? 8 : 4) +
+                            (uint64_t)P.nsbins * 13 + 2048;
+      P.smode = any_shared_live && upb >= 4 && P.nsbins > 0 && P.nsbins <= SBIN_MAX &&
+                (unsigned __int128)P.nsbins * (uint64_t)nblk <= ((unsigned __int128)1 << 25) &&
+                per_block < 0xffffffffu && smem <= 200 * 1024;
+      P.RBG = P.smode ? ceil_log2(std::max<uint64_t>(P.shared_cell_base, 1)) + P.IVB : P.RB;
+    }
     B.sort_passes = (P.RB + 7) / 8;
+    B.sort_passes_split = (P.RBG + 7) / 8;
     B.wide = wide;
     d.bound = std::move(bp);
     return HGRD_OK;

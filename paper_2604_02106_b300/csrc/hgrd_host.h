@@ -55,7 +55,8 @@ struct Bound {
   std::vector<int64_t> array_bytes, array_granule;
   uint64_t n_instances = 0;
   uint64_t nkeys_max = 0;
-  int sort_passes = 0;
+  int sort_passes = 0;        // radix passes over all keys
+  int sort_passes_split = 0;  // radix passes over the global-array keys (block-local mode)
   bool wide = false;
 };
 extern thread_local std::string g_err;

@@ -83,6 +83,7 @@ struct DAcc {
   uint64_t ngran;      // granules of one copy of the array
   int32_t shared, dead;
   int32_t bounds_free, pad;
+  int64_t sgbase;  // shared arrays: first granule of the array among one block's shared granules
 };
 
 // Everything the kernels need about one bound descriptor.  Lives in the
@@ -104,6 +105,12 @@ struct alignas(16) DProg {
   uint64_t shared_cell_base;  // cell codes at or above this belong to shared arrays
   uint32_t wmask;             // accesses that write (W or A)
   int32_t nlay;               // arrays in layout order (global first)
+  // block-local ordering of shared-array keys: their runs never leave a block,
+  // so they are written straight into per-block (granule, interval) bins
+  // instead of going through the global sort
+  int32_t smode, niv;         // smode: shared keys use the bins; niv: intervals
+  int64_t nsbins;             // bins of one block: shared granules x intervals
+  int32_t RBG, pad2;          // run-code bits of the global-array keys (the sorted ones)
   uint32_t einter[MAXACC], eintra[MAXACC];
   uint64_t lay_cbase[MAXARR + 1];
   uint64_t lay_ngran[MAXARR];
@@ -136,11 +143,19 @@ enum {
   C_KIND1,
   C_KIND2,
   C_NPAIR,
+  C_NG,   // keys of global arrays (the sorted stream)
+  C_NS,   // keys of shared arrays (smode: counted per block bin, not sorted)
+  C_NSC,  // keys of shared arrays in candidate bins (smode: written behind the sorted keys)
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_WORDS = 128
 };
 enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
+
+// the expansion kernels run 8 warps per CTA, one simulated warp per warp
+constexpr int EXP_THREADS = 256;
+// most (shared granule, interval) bins of one block in the block-local mode
+constexpr int SBIN_MAX = 4096;
 
 }  // namespace hgrd
 

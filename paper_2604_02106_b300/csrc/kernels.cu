@@ -19,6 +19,8 @@
 //  witness    merge per-run witnesses into the canonical set.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kcommon.cuh"
 
 namespace hgrd {
@@ -214,6 +216,190 @@ __global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ i
     for (int k = 0; k < 16; ++k) {
       if (b0 + k < n) out[b0 + k] = run;
       run += v[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ expand, block-local shared bins
+// One CTA per simulated block (grid-stride over blocks); its warps take the
+// block's units.  A shared-memory race needs a writer and two threads of one
+// block in one interval (Table 2), so a (shared granule, interval) bin of the
+// block can only race when it has both; such a bin is a candidate, the rest
+// never reach the key buffer.
+//   MODE 3 (count): global-array keys per unit and their digit-0 histogram,
+//     as expansion mode 0; per bin the instance count, min / max thread and a
+//     writer bit.  The block's candidate bins get consecutive room in the
+//     shared-key region (base from a device counter, so blocks land in any
+//     order); table row b keeps (start << 32 | count) per candidate bin, 0
+//     for the others.
+//   MODE 4 (write): global keys at their unit offsets (emission order, as
+//     mode 1); keys of candidate bins into their bin, in any order, at
+//     shared_out[n_global + base(b) + start + slot].
+template <typename T, int MODE>
+__global__ void __launch_bounds__(EXP_THREADS) expand_block_kernel(
+    const DProg* __restrict__ Pg, uint64_t* __restrict__ unit_cnt, const uint64_t* __restrict__ unit_off,
+    uint64_t* __restrict__ keys_g, uint64_t* __restrict__ keys_s, uint64_t* __restrict__ hist,
+    uint64_t* __restrict__ counters, uint64_t* __restrict__ stbl, uint64_t* __restrict__ sbase) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int WPC = EXP_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Pg);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += EXP_THREADS) dst[i] = src[i];
+    __syncthreads();
+  }
+  const DProg* __restrict__ P = reinterpret_cast<const DProg*>(smem);
+  const int nslot = P->nslot;
+  unsigned char* after = smem + sizeof(DProg);
+  T* sl = reinterpret_cast<T*>(after) + (size_t)warp * nslot * 32;
+  uint32_t* bins = reinterpret_cast<uint32_t*>(after + (size_t)WPC * nslot * 32 * sizeof(T));
+  const int NB = (int)P->nsbins;
+  const int niv = P->niv;
+  const int64_t ivmin = P->ivmin;
+  // MODE 3: count | min thread | max thread | writer bits | digit-0 histogram
+  uint32_t* s_cnt = bins;
+  uint32_t* s_mn = bins + NB;
+  uint32_t* s_mx = bins + 2 * NB;
+  uint32_t* s_wb = bins + 3 * NB;
+  const int NW = (NB + 31) >> 5;
+  uint32_t* shist = s_wb + NW;
+  // scan scratch: 8 words + the total, 8-byte aligned
+  uint64_t* ws = reinterpret_cast<uint64_t*>(bins + ((3 * NB + NW + 256 + 1) & ~1));
+  // MODE 4: write cursors (start of the bin's room, or NONE)
+  constexpr uint32_t NONE = 0xffffffffu;
+  uint32_t* s_cur = bins;
+  const int64_t nblk = P->nblk;
+  const int64_t upb = (int64_t)P->wpb * P->nchunk;
+  const int PB = P->PB;
+  const uint32_t wmask = P->wmask;
+  uint64_t oob = 0;
+  if (MODE == 3) {
+    for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+      s_cnt[i] = 0;
+      s_mn[i] = NONE;
+      s_mx[i] = 0;
+    }
+    for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += EXP_THREADS) shist[i] = 0;
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    counters[C_NKEYS] = counters[C_NG] + counters[C_NS];
+  }
+  const uint64_t n_g = MODE == 4 ? counters[C_NG] : 0;
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    uint64_t sb = 0;
+    if (MODE == 4) {
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint64_t e = stbl[(uint64_t)b * NB + i];
+        s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
+      }
+      sb = n_g + sbase[b];
+      __syncthreads();
+    }
+    for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
+      uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
+      oob += expand_unit<T>(P, sl, lane, u, 0xffffffffu,
+                            [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb,
+                                int lt, const int32_t*) {
+                              const int G = A.G;
+                              if (A.shared) {
+                                if (!inb) return;
+                                const uint32_t bin0 =
+                                    (uint32_t)(((uint64_t)A.sgbase + (uint64_t)idx * G) * niv + (uint64_t)(iv - ivmin));
+                                for (int j = 0; j < G; ++j) {
+                                  const uint32_t bin = bin0 + (uint32_t)(j * niv);
+                                  if (MODE == 3) {
+                                    atomicAdd(&s_cnt[bin], 1u);
+                                    atomicMin(&s_mn[bin], (uint32_t)lt);
+                                    atomicMax(&s_mx[bin], (uint32_t)lt);
+                                    if ((wmask >> a) & 1u) atomicOr(&s_wb[bin >> 5], 1u << (bin & 31));
+                                  } else if (s_cur[bin] != NONE) {
+                                    const uint32_t pos = atomicAdd(&s_cur[bin], 1u);
+                                    keys_s[sb + pos] = make_key(P, A, a, idx, iv, bb, lt, j);
+                                  }
+                                }
+                                return;
+                              }
+                              if (inb) {
+                                const int rank = __popc(bal & lanemask_lt());
+                                for (int j = 0; j < G; ++j) {
+                                  const uint64_t key = make_key(P, A, a, idx, iv, bb, lt, j);
+                                  if (MODE == 4)
+                                    keys_g[cursor + (uint64_t)rank * G + j] = key;
+                                  else
+                                    atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], 1u);
+                                }
+                              }
+                              cursor += (uint64_t)__popc(bal) * G;
+                            });
+      if (MODE == 3 && lane == 0) unit_cnt[u] = cursor;
+    }
+    __syncthreads();
+    if (MODE == 3) {
+      // candidate bins of block b: room in bin order of a strided walk
+      uint64_t csum = 0, asum = 0;
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint32_t c = s_cnt[i];
+        asum += c;
+        if (((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i]) csum += c;
+      }
+      for (int o = 16; o; o >>= 1) asum += __shfl_down_sync(FULL, asum, o);
+      if (lane == 0 && asum) atomicAdd((unsigned long long*)&counters[C_NS], (unsigned long long)asum);
+      uint64_t start = block_excl_scan(csum, ws, ws + 8);
+      if (threadIdx.x == 0) {
+        const uint64_t tot = ws[8];
+        sbase[b] = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
+      }
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint32_t c = s_cnt[i];
+        const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
+        stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
+        if (cand) start += c;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        s_cnt[i] = 0;
+        s_mn[i] = NONE;
+        s_mx[i] = 0;
+      }
+      for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
+      __syncthreads();
+    }
+  }
+  if (MODE == 3) {
+    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    for (int i = threadIdx.x; i < 256; i += EXP_THREADS)
+      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
+  }
+}
+
+// candidate bins of the block-local mode -> exact-scan entries, after the
+// global candidates; an entry's start carries SHARED_ENTRY and both ends are
+// relative to the first shared key (the exact scan adds the global key count)
+constexpr uint64_t SHARED_ENTRY = 1ull << 63;
+__global__ void shared_cand_kernel(const uint64_t* __restrict__ stbl, const uint64_t* __restrict__ sbase, int64_t nblk,
+                                   int64_t nb, uint64_t* __restrict__ cand, uint64_t cand_cap, uint64_t* counters) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t total = (uint64_t)nblk * (uint64_t)nb;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total; i0 += stride) {
+    const uint64_t i = i0 + threadIdx.x;
+    const uint64_t e = i < total ? stbl[i] : 0ull;
+    const bool has = (uint32_t)e != 0;
+    const unsigned m = __ballot_sync(FULL, has);
+    if (!m) continue;
+    uint64_t base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd((unsigned long long*)&counters[C_NCAND], (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL, base, __ffs(m) - 1);
+    if (has) {
+      const uint64_t g = base + __popc(m & lanemask_lt());
+      const uint64_t s = sbase[i / (uint64_t)nb] + (e >> 32);
+      if (g < cand_cap) {
+        cand[2 * g] = SHARED_ENTRY | s;
+        cand[2 * g + 1] = s + (uint32_t)e;
+      }
     }
   }
 }
@@ -594,21 +780,95 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
 }
 
 // ------------------------------------------------------------------ conflict scan, phase B
+// Exact kinds of one candidate bin of the block-local mode: keys [s, e) of one
+// shared granule, one interval and one block, in any order.  Lane = access a:
+// min / max warp of a over the bin and, per warp w, min / max thread of a in
+// w, kept in the warp's shared-memory tables (reset to empty after use).
+// Diff-warp pairs come from the warp sums, same-warp pairs from the thread
+// sums of each warp present (Table 2, intra-block kinds).
+struct BinTables {
+  uint32_t tlo[32 * 32], thi[32 * 32], wlo[32], whi[32];
+};
+__device__ __forceinline__ void bin_tables_reset(BinTables* T, int lane) {
+  for (int i = lane; i < 32 * 32; i += 32) {
+    T->tlo[i] = 0xffffffffu;
+    T->thi[i] = 0;
+  }
+  T->wlo[lane] = 0xffffffffu;
+  T->whi[lane] = 0;
+  __syncwarp();
+}
+__device__ __forceinline__ RunMasks exact_bin(const uint64_t* keys, uint64_t s, uint64_t e,
+                                              const DProg* __restrict__ P, int lane, uint32_t eintra, BinTables* T) {
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB;
+  RunMasks R;
+  R.rid = shr64(keys[s], PB + IVB);
+  uint32_t pw = 0;  // warps present
+  for (uint64_t pos = s; pos < e; pos += 32) {
+    const uint64_t i = pos + lane;
+    uint32_t bit = 0;
+    if (i < e) {
+      const uint64_t key = keys[i];
+      const uint32_t t = (uint32_t)lowbits(key >> AB, TB);
+      const uint32_t a = (uint32_t)lowbits(key, AB);
+      const uint32_t w = t >> 5;
+      atomicMin(&T->tlo[a * 32 + w], t);
+      atomicMax(&T->thi[a * 32 + w], t);
+      atomicMin(&T->wlo[a], w);
+      atomicMax(&T->whi[a], w);
+      bit = 1u << w;
+    }
+    pw |= __reduce_or_sync(FULL, bit);
+  }
+  __syncwarp();
+  Sum ws;
+  ws.p = T->wlo[lane] <= T->whi[lane];
+  ws.lo = T->wlo[lane];
+  ws.hi = T->whi[lane];
+  R.blk = racy_row(ws, lane) & eintra;
+  R.warp = 0;
+  for (uint32_t m = pw; m; m &= m - 1) {
+    const int w = __ffs(m) - 1;
+    Sum ts;
+    ts.lo = T->tlo[lane * 32 + w];
+    ts.hi = T->thi[lane * 32 + w];
+    ts.p = ts.lo <= ts.hi;
+    R.warp |= racy_row(ts, lane) & eintra;
+    T->tlo[lane * 32 + w] = 0xffffffffu;
+    T->thi[lane * 32 + w] = 0;
+  }
+  T->wlo[lane] = 0xffffffffu;
+  T->whi[lane] = 0;
+  R.inter = 0;
+  __syncwarp();
+  return R;
+}
+
+// Entries of the block-local mode's candidate bins carry SHARED_ENTRY and
+// offsets relative to the first shared key, which sits right after the
+// *n_dev global keys; their kinds come from exact_bin and the warp's tables
+// in dynamic shared memory (launched with `bins` set).
 __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                     const DProg* __restrict__ P, const uint64_t* __restrict__ cand,
                                                     uint64_t cand_cap, uint64_t* __restrict__ raw, uint64_t raw_cap,
-                                                    uint64_t* counters, int stop_first) {
+                                                    uint64_t* counters, int stop_first, int bins) {
+  extern __shared__ __align__(16) unsigned char xsm[];
   const int lane = threadIdx.x & 31;
   const uint64_t n = *n_dev;
   uint64_t ncand = counters[C_NCAND];
   if (ncand > cand_cap) ncand = cand_cap;
   const uint32_t einter = lane < P->nacc ? P->einter[lane] : 0u;
   const uint32_t eintra = lane < P->nacc ? P->eintra[lane] : 0u;
+  BinTables* T = bins ? reinterpret_cast<BinTables*>(xsm) + (threadIdx.x >> 5) : nullptr;
+  if (bins) bin_tables_reset(T, lane);
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t c = gw; c < ncand; c += nw) {
     if (stop_first && *(volatile uint64_t*)&counters[C_NRAW] != 0) break;
-    const RunMasks R = exact_run(keys, cand[2 * c], cand[2 * c + 1], n, P, lane, einter, eintra, stop_first != 0);
+    const uint64_t c0 = cand[2 * c], c1 = cand[2 * c + 1];
+    const RunMasks R = (c0 & SHARED_ENTRY)
+                           ? exact_bin(keys, n + (c0 & ~SHARED_ENTRY), n + c1, P, lane, eintra, T)
+                           : exact_run(keys, c0, c1, n, P, lane, einter, eintra, stop_first != 0);
     record_pairs(counters + C_PAIRS, R, lane);
     uint32_t row = witness_row(R, lane);
     const uint32_t cntw = (uint32_t)__popc(row);
@@ -788,9 +1048,48 @@ cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint6
 
 cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                          const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
-                         uint64_t* counters, bool stop_first) {
-  int grid = occupancy_grid((const void*)exact_kernel, 256, 0, L.nsm);
-  exact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, raw, raw_cap, counters, stop_first ? 1 : 0);
+                         uint64_t* counters, bool stop_first, bool bins) {
+  const size_t smem = bins ? 8 * sizeof(BinTables) : 0;
+  if (bins) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = occupancy_grid((const void*)exact_kernel, 256, smem, L.nsm);
+  exact_kernel<<<grid, 256, smem, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, raw, raw_cap, counters,
+                                         stop_first ? 1 : 0, bins ? 1 : 0);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_block(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
+                                uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s,
+                                uint64_t* hist, uint64_t* counters, uint64_t* stbl, uint64_t* sbase) {
+  const size_t esz = wide ? 8 : 4;
+  const uint64_t NB = (uint64_t)h_prog.nsbins, NW = (NB + 31) / 32;
+  const size_t tables = mode == 3 ? (((3 * NB + NW + 256 + 1) & ~1ull) * 4 + 9 * 8) : NB * 4;
+  const size_t smem = sizeof(DProg) + (size_t)EXP_THREADS * h_prog.nslot * esz + tables;
+  const void* fn = nullptr;
+  if (!wide)
+    fn = mode == 3 ? (const void*)expand_block_kernel<int32_t, 3> : (const void*)expand_block_kernel<int32_t, 4>;
+  else
+    fn = mode == 3 ? (const void*)expand_block_kernel<int64_t, 3> : (const void*)expand_block_kernel<int64_t, 4>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = occupancy_grid(fn, EXP_THREADS, smem, L.nsm);
+  if (grid > h_prog.nblk) grid = h_prog.nblk;
+  if (grid < 1) grid = 1;
+  void* args[] = {(void*)&d_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s,
+                  (void*)&hist,   (void*)&counters, (void*)&stbl,     (void*)&sbase};
+  (*L.launches)++;
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
+}
+
+cudaError_t launch_shared_cand(const Launch& L, const DProg& h_prog, const uint64_t* stbl, const uint64_t* sbase,
+                               uint64_t* cand, uint64_t cand_cap, uint64_t* counters) {
+  const uint64_t total = (uint64_t)h_prog.nblk * (uint64_t)h_prog.nsbins;
+  const uint64_t blocks = (total + 255) / 256;
+  const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(blocks, 1), (uint64_t)L.nsm * 8);
+  shared_cand_kernel<<<grid, 256, 0, L.s>>>(stbl, sbase, h_prog.nblk, h_prog.nsbins, cand, cand_cap, counters);
   (*L.launches)++;
   return cudaGetLastError();
 }

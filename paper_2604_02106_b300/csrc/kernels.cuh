@@ -7,7 +7,6 @@
 namespace hgrd {
 
 // Work shapes
-constexpr int EXP_THREADS = 256;   // 8 warps; one simulated warp of the user kernel per warp
 constexpr int RS_MIN_TILE = 1536;  // smallest onesweep tile of the shapes the sort autotuner picks from
 constexpr int RS_RADIX = 256;
 constexpr int CA_THREADS = 256;    // candidate scan
@@ -58,7 +57,17 @@ cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint6
 // conflict scan, phase B: exact per-access summaries -> packed raw witnesses
 cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                          const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,
-                         uint64_t* counters, bool stop_first = false);
+                         uint64_t* counters, bool stop_first = false, bool bins = false);
+
+// block-local mode (DProg::smode): mode 3 = count global keys per unit and
+// summarise the shared bins of every block, 4 = write global keys and the
+// keys of candidate bins (behind the *n_global sorted keys, in keys_s)
+cudaError_t launch_expand_block(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
+                                uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s,
+                                uint64_t* hist, uint64_t* counters, uint64_t* stbl, uint64_t* sbase);
+// candidate bins -> exact-scan entries appended to the candidate list
+cudaError_t launch_shared_cand(const Launch& L, const DProg& h_prog, const uint64_t* stbl, const uint64_t* sbase,
+                               uint64_t* cand, uint64_t cand_cap, uint64_t* counters);
 
 // witness merge: head flags, merge by atomic OR into uniq, kind counts
 cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_dev, uint64_t n_max, uint64_t* flags);

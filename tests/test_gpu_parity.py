@@ -249,3 +249,57 @@ def test_every_sort_shape_gives_the_same_result():
                 _same(hg.check(w.text, w.binding, cap=1 << 20), o)
     finally:
         hg.sort_variant(cur)
+
+
+# ---------------------------------------------------------------- block-local shared bins
+
+@pytest.mark.parametrize("seed", range(48))
+def test_shared_bins_against_oracle(seed):
+    # shared-memory keys checked in per-block (granule, interval) bins and the
+    # same check with one global sort must both equal the oracle
+    w = workloads.random_shared(5000 + seed)
+    o = oracle.check(w.text, w.binding, cap=1 << 20)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    g = k.check(cap=1 << 20)
+    st = hg.stats()
+    _same(g, o)
+    if st["shared_bins"]:
+        assert st["n_sorted_keys"] + st["n_binned_keys"] <= g.n_keys
+    n = k.check(cap=1 << 20, flags=hg.NO_SPLIT)
+    assert hg.stats()["shared_bins"] == 0 and hg.stats()["n_sorted_keys"] == n.n_keys
+    _same(n, o)
+
+
+def test_shared_bins_are_used():
+    used = 0
+    for seed in range(48):
+        w = workloads.random_shared(5000 + seed)
+        hg.check(w.text, w.binding, cap=16)
+        used += hg.stats()["shared_bins"]
+    assert used >= 12
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_shared_bins_restricted_and_stop_first(seed):
+    w = workloads.random_shared(7000 + seed)
+    o = oracle.check(w.text, w.binding)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    mask = 0b1011 & ((1 << w.meta["n_access"]) - 1)
+    r = k.check(cap=1 << 20, only_accesses=mask)
+    assert r.witnesses == [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
+    f = k.check(cap=1 << 20, flags=hg.STOP_FIRST)
+    assert f.racy == o.racy
+    full = {x[:5]: x[5] for x in o.witnesses}
+    for x in f.witnesses:
+        assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
+
+
+def test_stencil_bins_skip_the_sort():
+    # the shared tile's keys never enter the sort; the clean tile has no candidate bin
+    w = workloads.config2(0, planted=True, W=256, H=256, K=8)
+    g = hg.check(w.text, w.binding, cap=1 << 20)
+    st = hg.stats()
+    assert st["shared_bins"] == 1 and st["n_binned_keys"] == 0
+    assert st["n_sorted_keys"] < g.n_keys // 4
+    n = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.NO_SPLIT)
+    assert n == g

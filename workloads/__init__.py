@@ -400,6 +400,84 @@ def random_tiny(seed: int, max_instances: int = 2048) -> Workload:
                     {"loop_bounds": bounds, "n_access": nacc})
 
 
+def random_shared(seed: int, max_instances: int = 60000) -> Workload:
+    """Random kernel dominated by shared-memory accesses on blocks of 4..32
+    warps (1-2D), 1-2 loops, 1-3 shared arrays with 4- or 8-byte elements,
+    barrier intervals that may follow a loop, block / device atomics and a
+    few global accesses.  Index forms favour collisions between neighbouring
+    threads and warps (tx / 2, tx % Q, lin + k, lin / 40) so that races of
+    every intra-block kind occur in some seeds and not in others."""
+    rng = SplitMix64(seed)
+    bdx = rng.choice([32, 64, 128, 256, 40, 96])
+    bdy = rng.choice([1, 1, 2, 3, 4])
+    while bdx * bdy > 1024:
+        bdy -= 1
+    grid = (rng.range(1, 4), rng.range(1, 2), 1)
+    nloops = rng.range(1, 2)
+    bounds = [rng.range(1, 4) for _ in range(nloops)]
+    nacc = rng.range(3, 12)
+    nthr = bdx * bdy * math.prod(grid)
+    while nthr * math.prod(bounds) * nacc > max_instances and nacc > 3:
+        nacc -= 1
+    while nthr * math.prod(bounds) * nacc > max_instances and len(bounds) > 1:
+        bounds.pop()
+    w = _Writer(f"shr_{seed & 0xffff}")
+    Q = rng.range(2, 9)
+    w.add("param Q")
+    lv = ["i", "j"][:len(bounds)]
+    for v, b in zip(lv, bounds):
+        w.add(f"loop {v} {b}")
+    nsh = rng.range(1, 3)
+    sizes = []
+    for k in range(nsh):
+        el = rng.choice([4, 4, 8])
+        n_el = rng.range(16, 600)
+        sizes.append((el, n_el))
+        w.add(f"array S{k} shared {el * n_el} ; granule 4")
+    w.add("array G global 65536")
+    w.add("let lin = ty*bdx + tx")
+    forms = ["lin", "lin / 2", "tx / 2", "tx % Q", "lin + 1", "lin / 40", "(lin + {v}) % 97", "ty", "tx",
+             "lin / 32 + {v}", "3"]
+    # half the seeds follow a race-free discipline: a thread writes only its
+    # own element (arrays at least a block long), in even intervals, and
+    # reads others' elements only in odd ones
+    disciplined = rng.below(2) == 0
+    if disciplined:
+        w.lines = [x for x in w.lines if not x.startswith("array S")]
+        sizes = [(el, max(n_el, bdx * bdy)) for el, n_el in sizes]
+        for k, (el, n_el) in enumerate(sizes):
+            w.add(f"array S{k} shared {el * n_el} ; granule 4")
+        w.lines.append(w.lines.pop(w.lines.index("array G global 65536")))
+        w.lines.append(w.lines.pop(w.lines.index("let lin = ty*bdx + tx")))
+    for a_id in range(nacc):
+        if rng.below(6) == 0:
+            kind = rng.choice(["R", "W"])
+            w.access(kind, "G", 4, f"(bx*bdx*bdy + lin) % 16384", iv=str(rng.range(0, 2)), line=a_id + 1)
+            continue
+        k = rng.below(nsh)
+        el, n_el = sizes[k]
+        r = rng.below(10)
+        kind = "R" if r < 5 else ("W" if r < 9 else "A")
+        form = rng.choice(forms).replace("{v}", rng.choice(lv))
+        iv = str(rng.range(0, 2))
+        if disciplined:
+            kind = "W" if kind == "A" else kind
+            if kind == "W":
+                form, iv = "lin", str(2 * rng.below(2))
+            elif form != "lin":
+                iv = str(2 * rng.below(2) + 1)
+        expr = f"({form}) % {n_el}"
+        if rng.below(3) == 0:
+            iv = f"{iv} + 4*{rng.choice(lv)}"
+        guards = []
+        if rng.below(4) == 0:
+            guards.append(f"{rng.choice(['tx', 'ty', 'lin'])} {rng.choice(['<', '>='])} {rng.range(1, 40)}")
+        scope = rng.choice(["block", "device"]) if kind == "A" else None
+        w.access(kind, f"S{k}", el, expr, iv=iv, guards=guards, scope=scope, line=a_id + 1)
+    return Workload(f"shr_{seed}", w.text(), Binding(grid, (bdx, bdy, 1), (Q,)),
+                    {"loop_bounds": bounds, "n_access": nacc})
+
+
 # --------------------------------------------------------------------------
 # Config 4: corpus of seeded synthetic kernels of uneven size.
 #   2..32 accesses, 1-3D grids and blocks, 1..4 nested loops (bounds <= 64),
