@@ -117,13 +117,17 @@ typedef struct {
                                a subset, each witness a real race);
                                HGRD_NO_SPLIT: sort the keys of shared arrays with the global ones
                                instead of checking them in per-block bins (same result; for
-                               comparison and testing) */
+                               comparison and testing);
+                               HGRD_JIT / HGRD_NO_JIT: always / never expand with kernels
+                               specialised to the program's structure, compiled at run time
+                               (default: when hgrd_jit_compile or an HGRD_JIT check already
+                               compiled them for this binding); same result */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
   uint32_t reserved;
 } hgrd_check_opts;
-enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4, HGRD_NO_SPLIT = 8 };
+enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4, HGRD_NO_SPLIT = 8, HGRD_JIT = 16, HGRD_NO_JIT = 32 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
  * stream around the stage's kernels. */
@@ -144,7 +148,7 @@ typedef struct {
   uint64_t n_sorted_keys;   /* keys that went through the radix sort */
   uint64_t n_binned_keys;   /* shared-array keys written into candidate bins (block-local mode) */
   uint32_t shared_bins;     /* 1 when the shared-array keys were checked in per-block bins */
-  uint32_t reserved;
+  uint32_t jit;             /* 1 when the expansion ran specialised kernels (HGRD_JIT) */
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,
@@ -322,6 +326,28 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
  *     searched (pair_found = 0).  Synchronous on return. */
 int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, void* cuda_stream, hgrd_witness* host_out,
                        uint64_t cap, hgrd_verdict* v);
+
+/* ---- Specialised expansion ---------------------------------------------------
+ * The expansion (every instance's guards, index and interval, Sec. 6.2's
+ * addr / tb / id) normally interprets the bound program.  These calls build
+ * kernels specialised to the program's structure instead: CUDA source where
+ * each op, guard, index and interval is straight-line code, with the bound
+ * values (coefficients, divisors, sizes) read from the kernel's parameters,
+ * compiled for sm_103a at run time (seconds) and cached for the process, so
+ * bindings of one structure share a module.  Results are identical to the
+ * interpreted kernels.  Once compiled for a bound descriptor, every check of
+ * it uses them unless HGRD_NO_JIT is set.
+ *   hgrd_jit_compile: compile now (or find in the cache) for the bound
+ *     descriptor `d` and the pipeline `o` selects (o->flags HGRD_NO_SPLIT;
+ *     o may be NULL); *compile_ms (may be NULL) = time this call spent
+ *     compiling (0 on a cache hit).  HGRD_EUNSUPPORTED with the compiler's
+ *     log (hgrd_last_error) when compiling or loading fails, e.g. without a
+ *     device.  Needs a current CUDA device to load the module.
+ *   hgrd_jit_source: the generated source for the same choice,
+ *     NUL-terminated into out[0, cap); *len = its full length (out may be
+ *     NULL to size it). */
+int hgrd_jit_compile(const hgrd_desc* d, const hgrd_check_opts* o, double* compile_ms);
+int hgrd_jit_source(const hgrd_desc* d, const hgrd_check_opts* o, char* out, size_t cap, size_t* len);
 
 void hgrd_free_desc(hgrd_desc* d);
 const char* hgrd_last_error(void);

@@ -20,6 +20,8 @@ NO_PAIR = 1
 PROFILE = 2
 STOP_FIRST = 4
 NO_SPLIT = 8
+JIT = 16
+NO_JIT = 32
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -28,7 +30,7 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free", "hgrd_pair_features",
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
-           "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant"]
+           "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source"]
 BATCH_GRAPH = 1
 
 
@@ -84,7 +86,7 @@ class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("n_candidates", C.c_uint64), ("n_raw_witness", C.c_uint64),
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
-                ("shared_bins", C.c_uint32), ("reserved", C.c_uint32)]
+                ("shared_bins", C.c_uint32), ("jit", C.c_uint32)]
 
 
 _lib = None
@@ -123,9 +125,11 @@ def lib():
         L.hgrd_free_desc.restype = None
         L.hgrd_last_error.restype = C.c_char_p
         L.hgrd_debug_divmod.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.hgrd_jit_compile.argtypes = [vp, C.POINTER(CheckOpts), C.POINTER(C.c_double)]
+        L.hgrd_jit_source.argtypes = [vp, C.POINTER(CheckOpts), C.c_char_p, sz, C.POINTER(sz)]
         for f in ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check",
                   "hgrd_check_enqueue", "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile",
-                  "hgrd_debug_divmod"]:
+                  "hgrd_debug_divmod", "hgrd_jit_compile", "hgrd_jit_source"]:
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -245,6 +249,24 @@ class Kernel:
                           [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None,
                           _it(v.min_x) if v.pair_found else None, _it(v.min_y) if v.pair_found else None,
                           rc == ETRUNCATED, _pairs(v.pair_kind))
+
+    def jit_compile(self, **opts) -> float:
+        """Compile (or find cached) the specialised expansion kernels for the
+        pipeline `opts` selects; returns the milliseconds spent compiling.
+        Later checks of this binding use them (unless flags has NO_JIT)."""
+        ms = C.c_double()
+        o = _opts(**opts)
+        _raise(lib().hgrd_jit_compile(self._h, C.byref(o), C.byref(ms)))
+        return ms.value
+
+    def jit_source(self, **opts) -> str:
+        """The generated source of the specialised expansion kernels."""
+        n = C.c_size_t()
+        o = _opts(**opts)
+        _raise(lib().hgrd_jit_source(self._h, C.byref(o), None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        _raise(lib().hgrd_jit_source(self._h, C.byref(o), buf, n.value + 1, C.byref(n)))
+        return buf.value.decode()
 
     def check_noalloc(self, cap: int = 1 << 16, stream=None, **opts) -> Result:
         """hgrd_check_noalloc: the check on the library's built-in 64 MiB device

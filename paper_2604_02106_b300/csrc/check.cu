@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "hgrd_host.h"
+#include "jit.h"
 #include "kernels.cuh"
 
 namespace hgrd {
@@ -143,6 +144,21 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   g_stats.int64_path = B.wide;
   g_stats.sort_passes = (uint32_t)(split ? B.sort_passes_split : B.sort_passes);
   g_stats.shared_bins = split ? 1u : 0u;
+  // specialised expansion kernels: compiled on request (HGRD_JIT, or
+  // hgrd_jit_compile ahead of time), then used for every check of this binding
+  const uint32_t fl = o ? o->flags : 0u;
+  bool jit = false;
+  if (!(fl & HGRD_NO_JIT)) {
+    if (fl & HGRD_JIT) {
+      const int jrc = jit_prepare(B, split, nullptr);
+      if (jrc != HGRD_OK) return jrc;
+      jit = true;
+    } else {
+      jit = jit_ready(B, split);
+    }
+  }
+  g_stats.jit = jit ? 1u : 0u;
+  const uint32_t only_mask = (jit && restricted) ? only : 0xffffffffu;
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
@@ -172,7 +188,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // keys the sort and the candidate scan walk: all of them, or the global
   // ones in block-local mode (the candidate bins follow them in the final buffer)
   uint64_t* nkeys = cnt + (split ? C_NG : C_NKEYS);
-  if (split) {
+  if (jit) {
+    const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
+    CK(launch_jit_expand(L, B, m0, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
+                         U(W.sbase), only_mask));
+    g_prof.mark("expand_count");
+    CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    g_prof.mark("unit_scan");
+    CK(launch_jit_expand(L, B, m1, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
+                         U(W.stbl), U(W.sbase), only_mask));
+    g_prof.mark("expand_write");
+  } else if (split) {
     CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), cnt,
                            U(W.stbl), U(W.sbase)));
     g_prof.mark("expand_count");
@@ -488,6 +514,8 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   hgrd_check_opts oo{};
   if (o) oo = *o;
   oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
+  oo.flags &= ~(uint32_t)HGRD_JIT;      // loading a compiled module takes device memory
+  oo.flags |= HGRD_NO_JIT;
   const Layout W = layout(*d->bound, &oo);
   if (W.total > NOALLOC_BYTES)
     return fail(HGRD_ENOMEM, "hgrd_check_noalloc: this binding needs " + std::to_string(W.total) +

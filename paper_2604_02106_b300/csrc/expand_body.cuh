@@ -1,0 +1,253 @@
+// Bodies of the expansion kernels.  Two kinds of kernels run them:
+//   interpreted  (kernels.cu) the compiled affine program is staged in shared
+//                memory and evaluated term by term (expand_unit);
+//   specialised  (jit.cpp) source generated from the program's structure and
+//                compiled at run time: every guard, index and interval becomes
+//                straight-line code over registers, the coefficients are read
+//                from the kernel's parameter block.
+// Both hand a unit expander X to the same bodies, so the keys, counts and bins
+// they produce are the same by construction.  X provides
+//   template <class Step> uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step)
+// with expand_unit's contract (step called per access and loop vector with a
+// live in-bounds lane in the warp; returns this lane's out-of-bounds instances).
+#pragma once
+#include "kcommon.cuh"
+
+namespace hgrd {
+namespace dev {
+
+// Modes 0 (count keys per unit + digit histograms of `npass` digits), 1 (write
+// keys at the unit offsets) and 2 (gather the instances of the minimal
+// witness's granule).  Warp = unit, grid-stride over units.  shist: npass x 256
+// words of shared memory (mode 0).
+template <typename T, int MODE, class X>
+__device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X& ex, uint32_t* shist,
+                                                  uint64_t* __restrict__ unit_cnt,
+                                                  const uint64_t* __restrict__ unit_off, uint64_t* __restrict__ keys,
+                                                  uint64_t* __restrict__ hist, int npass, uint64_t* __restrict__ counters,
+                                                  const uint64_t* __restrict__ uniq, PairRec* __restrict__ pairs,
+                                                  uint64_t pair_cap, uint32_t only_in) {
+  constexpr int WPC = EXP_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (MODE == 0) {
+    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS) shist[i] = 0;
+    __syncthreads();
+  }
+  // the minimal witness for the pair search
+  uint32_t t_arr = 0, t_lo = 0, t_hi = 0;
+  uint64_t t_gran = 0;
+  if (MODE == 2) {
+    if (counters[C_NUNIQ] == 0) return;
+    const uint64_t w0 = uniq[0];
+    t_arr = (uint32_t)(w0 >> 53) & 31;
+    t_gran = (w0 >> 13) & ((1ull << 40) - 1);
+    t_lo = (uint32_t)(w0 >> 8) & 31;
+    t_hi = (uint32_t)(w0 >> 3) & 31;
+  }
+  const int64_t nunits = P->nunits;
+  const int PB = P->PB;
+  uint64_t oob = 0;
+  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
+  for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
+    uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
+    oob += ex.unit(lane, u, only,
+                   [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,
+                       const int32_t* ic) {
+                     const int G = A.G;
+                     if (MODE == 2) {
+                       if (inb) {
+                         const uint64_t g0 = (uint64_t)idx * (uint64_t)G;
+                         if ((uint32_t)A.arr == t_arr && t_gran >= g0 && t_gran < g0 + (uint64_t)G) {
+                           const uint64_t slot = atomicAdd((unsigned long long*)&counters[C_NPAIR], 1ull);
+                           if (slot < pair_cap) {
+                             PairRec r;
+                             r.blk = (uint32_t)b;
+                             r.thr = (uint32_t)lt;
+                             for (int l = 0; l < MAXLOOP; ++l) r.it[l] = (uint32_t)ic[l];
+                             r.acc = a;
+                             r.pad = 0;
+                             r.iv = iv;
+                             pairs[slot] = r;
+                           }
+                         }
+                       }
+                       return;
+                     }
+                     if (inb) {
+                       const int rank = __popc(bal & lanemask_lt());
+                       for (int j = 0; j < G; ++j) {
+                         const uint64_t key = make_key(P, A, a, idx, iv, b, lt, j);
+                         if (MODE == 1) {
+                           keys[cursor + (uint64_t)rank * G + j] = key;
+                         } else {
+                           for (int p = 0; p < npass; ++p)
+                             atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
+                         }
+                       }
+                     }
+                     cursor += (uint64_t)__popc(bal) * G;
+                   });
+    if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
+  }
+  if (MODE == 0) {
+    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS)
+      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
+  }
+}
+
+// Block-local mode: one CTA per simulated block (grid-stride over blocks); its
+// warps take the block's units.  A shared-memory race needs a writer and two
+// threads of one block in one interval (Table 2), so a (shared granule,
+// interval) bin of the block can only race when it has both; such a bin is a
+// candidate, the rest never reach the key buffer.
+//   MODE 3 (count): global-array keys per unit and their digit-0 histogram,
+//     as mode 0; per bin the instance count, min / max thread and a writer
+//     bit.  The block's candidate bins get consecutive room in the shared-key
+//     region (base from a device counter, so blocks land in any order); table
+//     row b keeps (start << 32 | count) per candidate bin, 0 for the others.
+//   MODE 4 (write): global keys at their unit offsets (emission order, as
+//     mode 1); keys of candidate bins into their bin, in any order, at
+//     keys_s[n_global + base(b) + start + slot].  A block without candidate
+//     bins expands its global-array accesses only.
+// bins: block_body_words(MODE, nsbins) words of shared memory.
+template <typename T, int MODE, class X>
+__device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X& ex, uint32_t* bins,
+                                                  uint64_t* __restrict__ unit_cnt,
+                                                  const uint64_t* __restrict__ unit_off, uint64_t* __restrict__ keys_g,
+                                                  uint64_t* __restrict__ keys_s, uint64_t* __restrict__ hist,
+                                                  uint64_t* __restrict__ counters, uint64_t* __restrict__ stbl,
+                                                  uint64_t* __restrict__ sbase, uint32_t only_in) {
+  constexpr int WPC = EXP_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NB = (int)P->nsbins;
+  const int niv = P->niv;
+  const int64_t ivmin = P->ivmin;
+  // MODE 3: count | min thread | max thread | writer bits | digit-0 histogram | scan scratch
+  uint32_t* s_cnt = bins;
+  uint32_t* s_mn = bins + NB;
+  uint32_t* s_mx = bins + 2 * NB;
+  uint32_t* s_wb = bins + 3 * NB;
+  const int NW = (NB + 31) >> 5;
+  uint32_t* shist = s_wb + NW;
+  uint64_t* ws = reinterpret_cast<uint64_t*>(bins + ((3 * NB + NW + 256 + 1) & ~1));
+  // MODE 4: write cursors (start of the bin's room, or NONE)
+  constexpr uint32_t NONE = 0xffffffffu;
+  uint32_t* s_cur = bins;
+  const int64_t nblk = P->nblk;
+  const int64_t upb = (int64_t)P->wpb * P->nchunk;
+  const int PB = P->PB;
+  const uint32_t wmask = P->wmask;
+  uint64_t oob = 0;
+  if (MODE == 3) {
+    for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+      s_cnt[i] = 0;
+      s_mn[i] = NONE;
+      s_mx[i] = 0;
+    }
+    for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += EXP_THREADS) shist[i] = 0;
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    counters[C_NKEYS] = counters[C_NG] + counters[C_NS];
+  }
+  const uint64_t n_g = MODE == 4 ? counters[C_NG] : 0;
+  // accesses to global arrays: all that a block without candidate bins writes
+  uint32_t gmask = 0;
+  for (int a = 0; a < P->nacc; ++a)
+    if (!P->acc[a].shared) gmask |= 1u << a;
+  __syncthreads();
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    uint64_t sb = 0;
+    uint32_t only = only_in;
+    if (MODE == 4) {
+      int has = 0;
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint64_t e = stbl[(uint64_t)b * NB + i];
+        s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
+        has |= (uint32_t)e != 0;
+      }
+      sb = n_g + sbase[b];
+      if (!__syncthreads_or(has)) only &= gmask;
+    }
+    for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
+      uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
+      oob += ex.unit(lane, u, only,
+                     [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb, int lt,
+                         const int32_t*) {
+                       const int G = A.G;
+                       if (A.shared) {
+                         if (!inb) return;
+                         const uint32_t bin0 =
+                             (uint32_t)(((uint64_t)A.sgbase + (uint64_t)idx * G) * niv + (uint64_t)(iv - ivmin));
+                         for (int j = 0; j < G; ++j) {
+                           const uint32_t bin = bin0 + (uint32_t)(j * niv);
+                           if (MODE == 3) {
+                             atomicAdd(&s_cnt[bin], 1u);
+                             atomicMin(&s_mn[bin], (uint32_t)lt);
+                             atomicMax(&s_mx[bin], (uint32_t)lt);
+                             if ((wmask >> a) & 1u) atomicOr(&s_wb[bin >> 5], 1u << (bin & 31));
+                           } else if (s_cur[bin] != NONE) {
+                             const uint32_t pos = atomicAdd(&s_cur[bin], 1u);
+                             keys_s[sb + pos] = make_key(P, A, a, idx, iv, bb, lt, j);
+                           }
+                         }
+                         return;
+                       }
+                       if (inb) {
+                         const int rank = __popc(bal & lanemask_lt());
+                         for (int j = 0; j < G; ++j) {
+                           const uint64_t key = make_key(P, A, a, idx, iv, bb, lt, j);
+                           if (MODE == 4)
+                             keys_g[cursor + (uint64_t)rank * G + j] = key;
+                           else
+                             atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], 1u);
+                         }
+                       }
+                       cursor += (uint64_t)__popc(bal) * G;
+                     });
+      if (MODE == 3 && lane == 0) unit_cnt[u] = cursor;
+    }
+    __syncthreads();
+    if (MODE == 3) {
+      // candidate bins of block b: room in the order of a strided walk
+      uint64_t csum = 0, asum = 0;
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint32_t c = s_cnt[i];
+        asum += c;
+        if (((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i]) csum += c;
+      }
+      for (int o = 16; o; o >>= 1) asum += __shfl_down_sync(FULL, asum, o);
+      if (lane == 0 && asum) atomicAdd((unsigned long long*)&counters[C_NS], (unsigned long long)asum);
+      uint64_t start = block_excl_scan(csum, ws, ws + 8);
+      if (threadIdx.x == 0) {
+        const uint64_t tot = ws[8];
+        sbase[b] = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
+      }
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        const uint32_t c = s_cnt[i];
+        const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
+        stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
+        if (cand) start += c;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        s_cnt[i] = 0;
+        s_mn[i] = NONE;
+        s_mx[i] = 0;
+      }
+      for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
+      __syncthreads();
+    }
+  }
+  if (MODE == 3) {
+    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    for (int i = threadIdx.x; i < 256; i += EXP_THREADS)
+      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
+  }
+}
+
+}  // namespace dev
+}  // namespace hgrd

@@ -58,6 +58,9 @@ struct Bound {
   int sort_passes = 0;        // radix passes over all keys
   int sort_passes_split = 0;  // radix passes over the global-array keys (block-local mode)
   bool wide = false;
+  // specialised expansion modules of the plain [0] and block-local [1]
+  // pipelines, once tried (owned by the process cache)
+  mutable const void* jit[2] = {nullptr, nullptr};
 };
 extern thread_local std::string g_err;
 extern thread_local hgrd_stats g_stats;

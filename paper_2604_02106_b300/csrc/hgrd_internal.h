@@ -4,7 +4,9 @@
 #include <cstddef>
 #include <cstdint>
 
+#if !defined(__CUDACC_RTC__)  // the run-time compiled kernels need none of the C ABI
 #include "../../include/hgrd.h"
+#endif
 
 #if defined(__CUDACC__)
 #define HGRD_HD __host__ __device__ __forceinline__
@@ -121,6 +123,14 @@ struct alignas(16) DProg {
   DTerm term[MAXTERM];
 };
 
+// Pair-search record of one instance touching the minimal witness's granule.
+struct PairRec {
+  uint32_t blk, thr;
+  uint32_t it[4];
+  int32_t acc, pad;
+  int64_t iv;
+};
+
 // Raw / canonical witness packed into 64 bits so the same radix sort orders
 // them: space(1) array(5) granule(40) acc_lo(5) acc_hi(5) kind(3), low to high
 // significance reversed (kind in the low bits).
@@ -156,6 +166,12 @@ enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
 constexpr int EXP_THREADS = 256;
 // most (shared granule, interval) bins of one block in the block-local mode
 constexpr int SBIN_MAX = 4096;
+// 32-bit shared-memory words the block-local expansion needs for nb bins:
+// mode 3 = count, min / max thread, writer bits, digit histogram, scan scratch;
+// mode 4 = write cursors
+HGRD_HD uint64_t block_body_words(int mode, uint64_t nb) {
+  return mode == 3 ? ((3 * nb + (nb + 31) / 32 + 256 + 1) & ~1ull) + 2 * 9 : nb;
+}
 
 }  // namespace hgrd
 

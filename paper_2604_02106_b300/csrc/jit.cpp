@@ -1,0 +1,312 @@
+// Specialised expansion kernels, compiled at run time.
+//
+// The interpreted expansion evaluates the bound program term by term from
+// shared memory: every instance pays for loads of the program's terms and
+// slot values and for the loop over them.  Here the program's STRUCTURE
+// (which slots each op, guard, index and interval reads, which ops divide,
+// which accesses are live, how many loops) is turned into CUDA source where
+// all of that is straight-line code over registers; the VALUES (coefficients,
+// divisors' magic numbers, bounds, launch shape) stay in the DProg, passed by
+// value as the kernel's parameter block, so every binding with the same
+// structure (a parameter sweep, the same kernel at another size) reuses one
+// compiled module.  The kernel bodies are the ones the interpreted kernels
+// run (expand_body.cuh): only the unit expander differs.
+//
+// NVRTC compiles the source for sm_103a to a cubin, loaded with the runtime's
+// library API.  Modules are cached per process by their source text.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hgrd_host.h"
+#include "jit.h"
+
+namespace hgrd {
+
+namespace {
+
+#include "jit_headers.inc"  // kJitHeaderNames / kJitHeaders: the device headers as text (written by the build)
+
+// Fixed-width integer and size types for the run-time compiler, which has no C library headers.
+const char* kStdInt =
+    "#pragma once\n"
+    "typedef signed char int8_t; typedef short int16_t; typedef int int32_t; typedef long long int64_t;\n"
+    "typedef unsigned char uint8_t; typedef unsigned short uint16_t; typedef unsigned int uint32_t;\n"
+    "typedef unsigned long long uint64_t; typedef unsigned long long uintptr_t;\n";
+const char* kStdDef = "#pragma once\ntypedef unsigned long size_t; typedef long ptrdiff_t;\n";
+
+std::string S(long long v) { return std::to_string(v); }
+
+// c0 + sum coef * slot, all in T, reading the values from the parameter block
+std::string lin(const DProg& P, const std::string& at, const DLin& L) {
+  std::string e = "((T)" + at + ".c0";
+  for (int t = 0; t < L.n; t++)
+    e += " + (T)P->term[" + S(L.first + t) + "].coef * s" + S(P.term[L.first + t].slot);
+  return e + ")";
+}
+
+std::string op_code(const DProg& P, int k, bool declare) {
+  const DOp& op = P.ops[k];
+  const std::string at = "P->ops[" + S(k) + "]";
+  std::string v = lin(P, at + ".lin", op.lin);
+  if (op.kind == OP_DIV)
+    v = "divq<T>(" + v + ", " + at + ".mg)";
+  else if (op.kind == OP_MOD)
+    v = "modq<T>(" + v + ", " + at + ".mg, (T)" + at + ".d)";
+  return std::string("      ") + (declare ? "const T " : "") + "s" + S(op.dst) + " = " + v + ";\n";
+}
+
+}  // namespace
+
+std::string jit_source(const DProg& P, bool split) {
+  const int nl = P.nloop;
+  std::string src;
+  src += "#include \"expand_body.cuh\"\n";
+  src += "namespace hgrd { namespace dev {\n";
+  src += std::string("typedef ") + (P.wide ? "int64_t" : "int32_t") + " T;\n";
+  src += "template <typename U> __device__ __forceinline__ U modq(U v, const Magic& g, U d) { return v - divq<U>(v, g) * d; }\n";
+  src += "struct GenX {\n  const DProg* __restrict__ P;\n";
+  src += "  template <class Step>\n";
+  src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
+  src += "    const int64_t bw = u / P->nchunk;\n";
+  src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
+  src += "    const int64_t it1 = min(P->nit, it0 + P->itc);\n";
+  src += "    const int64_t b = bw / P->wpb;\n";
+  src += "    const int lt = (int)(bw - b * P->wpb) * 32 + lane;\n";
+  src += "    const bool act = lt < P->nthr;\n";
+  src += "    const int bdx = P->block[0], bdy = P->block[1];\n";
+  src += "    const int64_t gdx = P->grid[0], gdy = P->grid[1];\n";
+  src += "    const T s0 = (T)(lt % bdx), s1 = (T)((lt / bdx) % bdy), s2 = (T)(lt / (bdx * bdy));\n";
+  src += "    const T s3 = (T)(b % gdx), s4 = (T)((b / gdx) % gdy), s5 = (T)(b / (gdx * gdy));\n";
+  // loop counters: slots 6.. for the live loops, zero for the others
+  for (int l = nl; l < MAXLOOP; l++) src += "    const T s" + S(6 + l) + " = 0; (void)s" + S(6 + l) + ";\n";
+  src += "    (void)s0; (void)s1; (void)s2; (void)s3; (void)s4; (void)s5;\n";
+  // fixed ops: the loop slots are zero while they run; they never read them
+  for (int l = 0; l < nl; l++) src += "    T s" + S(6 + l) + " = 0;\n";
+  for (int k = 0; k < P.nfix; k++) src += op_code(P, k, true).substr(2);
+  src += "    int32_t ic[4] = {0, 0, 0, 0};\n";
+  src += "    if (it0 > 0) {\n      int64_t r = it0;\n";
+  for (int l = nl - 1; l >= 0; l--)
+    src += "      ic[" + S(l) + "] = (int32_t)(r % P->ub[" + S(l) + "]); r /= P->ub[" + S(l) + "];\n";
+  src += "    }\n    uint64_t oob = 0;\n";
+  src += "    for (int64_t it = it0; it < it1; ++it) {\n";
+  if (nl > 0) {
+    src += "      if (it > it0) {\n";
+    std::string close;
+    for (int l = nl - 1; l >= 0; l--) {
+      src += std::string(8 + 2 * (nl - 1 - l), ' ') + "if (++ic[" + S(l) + "] >= P->ub[" + S(l) + "]) {\n";
+      src += std::string(10 + 2 * (nl - 1 - l), ' ') + "ic[" + S(l) + "] = 0;\n";
+      close = std::string(8 + 2 * (nl - 1 - l), ' ') + "}\n" + close;
+    }
+    src += close + "      }\n";
+    for (int l = 0; l < nl; l++) src += "      s" + S(6 + l) + " = (T)ic[" + S(l) + "];\n";
+  }
+  for (int k = P.nfix; k < P.nfix + P.niter; k++) src += op_code(P, k, true);
+  for (int a = 0; a < P.nacc; a++) {
+    const DAcc& A = P.acc[a];
+    if (A.dead) continue;
+    const std::string at = "P->acc[" + S(a) + "]";
+    src += "      if (only & " + S(1ll << a) + "u) {  // access " + S(a) + "\n";
+    src += "        bool live = act;\n";
+    for (int g = 0; g < A.ng; g++)
+      src += "        live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
+    src += "        const T idx = " + lin(P, at + ".idx", A.idx) + ";\n";
+    if (A.bounds_free)
+      src += "        const bool inb = live;\n";
+    else
+      src += "        const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
+    src += "        oob += (live && !inb) ? 1 : 0;\n";
+    src += "        const unsigned bal = __ballot_sync(0xffffffffu, inb);\n";
+    src += "        if (bal) {\n";
+    src += "          int64_t iv = 0;\n";
+    src += "          if (inb) iv = (int64_t)" + lin(P, at + ".iv", A.iv) + ";\n";
+    // the access's structural fields as literals, so the step's granule loop
+    // and its shared / global branch fold away
+    src += "          DAcc A = " + at + ";\n";
+    src += "          A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
+    src += "          step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, ic);\n";
+    src += "        }\n      }\n";
+  }
+  src += "    }\n    return oob;\n  }\n};\n}}  // namespace hgrd::dev\n";
+  src += "using namespace hgrd;\nusing namespace hgrd::dev;\n";
+  const char* sig =
+      "(const __grid_constant__ DProg Pp, uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, "
+      "uint64_t* keys_s, uint64_t* hist, int npass, uint64_t* counters, uint64_t* stbl, uint64_t* sbase, "
+      "uint32_t only) {\n  extern __shared__ __align__(16) unsigned char smem[];\n  GenX ex{&Pp};\n";
+  // the count and write kernels of one pipeline: block-local (3, 4) or plain (0, 1)
+  if (!split) {
+    for (int m : {0, 1}) {
+      src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand" + S(m) + sig;
+      src += "  expand_units_body<T, " + S(m) +
+             ">(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, hist, npass, counters, "
+             "nullptr, nullptr, 0, only);\n}\n";
+    }
+  }
+  for (int m : {3, 4}) {
+    if (!split) break;
+    src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand" + S(m) + sig;
+    src += "  expand_block_body<T, " + S(m) +
+           ">(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, keys_s, hist, counters, "
+           "stbl, sbase, only);\n}\n";
+  }
+  return src;
+}
+
+namespace {
+
+struct JitModule {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t k[5] = {};
+  bool ok = false;
+  std::string log;
+};
+
+std::mutex g_jit_mu;
+std::map<std::string, std::unique_ptr<JitModule>> g_jit_cache;
+
+JitModule* compile(const std::string& src, double* ms) {
+  auto t0 = std::chrono::steady_clock::now();
+  auto mod = std::make_unique<JitModule>();
+  std::vector<const char*> names, texts;
+  names.push_back("cstdint");
+  texts.push_back(kStdInt);
+  names.push_back("stdint.h");
+  texts.push_back(kStdInt);
+  names.push_back("cstddef");
+  texts.push_back(kStdDef);
+  names.push_back("stddef.h");
+  texts.push_back(kStdDef);
+  for (size_t i = 0; i < sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]); i++) {
+    names.push_back(kJitHeaderNames[i]);
+    texts.push_back(kJitHeaders[i]);
+  }
+  nvrtcProgram prog = nullptr;
+  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "hgrd_expand_jit.cu", (int)names.size(), texts.data(),
+                                     names.data());
+  if (r != NVRTC_SUCCESS) {
+    mod->log = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
+  } else {
+    const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
+    r = nvrtcCompileProgram(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    if (r != NVRTC_SUCCESS) {
+      mod->log = "nvrtcCompileProgram: " + std::string(nvrtcGetErrorString(r)) + "\n" + log;
+    } else {
+      size_t n = 0;
+      nvrtcGetCUBINSize(prog, &n);
+      std::vector<char> cubin(n);
+      nvrtcGetCUBIN(prog, cubin.data());
+      cudaError_t e = cudaLibraryLoadData(&mod->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      if (e != cudaSuccess) {
+        mod->log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+      } else {
+        static const char* kn[5] = {"hgrd_jit_expand0", "hgrd_jit_expand1", nullptr, "hgrd_jit_expand3",
+                                    "hgrd_jit_expand4"};
+        const bool split = src.find("hgrd_jit_expand3") != std::string::npos;
+        mod->ok = true;
+        for (int m = 0; m < 5 && mod->ok; m++) {
+          if (!kn[m] || (split != (m >= 3))) continue;
+          e = cudaLibraryGetKernel(&mod->k[m], mod->lib, kn[m]);
+          if (e != cudaSuccess) {
+            mod->ok = false;
+            mod->log = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+          }
+        }
+      }
+    }
+    nvrtcDestroyProgram(&prog);
+  }
+  *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  JitModule* raw = mod.get();
+  g_jit_cache[src] = std::move(mod);
+  return raw;
+}
+
+}  // namespace
+
+int jit_prepare(const Bound& B, bool split, double* ms) {
+  if (ms) *ms = 0;
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  const void*& slot = B.jit[split ? 1 : 0];
+  if (slot) return ((const JitModule*)slot)->ok ? HGRD_OK : fail(HGRD_EUNSUPPORTED, ((const JitModule*)slot)->log);
+  const std::string src = jit_source(B.prog, split);
+  auto it = g_jit_cache.find(src);
+  JitModule* m = nullptr;
+  if (it != g_jit_cache.end()) {
+    m = it->second.get();
+  } else {
+    double t = 0;
+    m = compile(src, &t);
+    if (ms) *ms = t;
+  }
+  slot = m;
+  return m->ok ? HGRD_OK : fail(HGRD_EUNSUPPORTED, "specialised expansion unavailable: " + m->log);
+}
+
+bool jit_ready(const Bound& B, bool split) {
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  const void* m = B.jit[split ? 1 : 0];
+  return m && ((const JitModule*)m)->ok;
+}
+
+cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const DProg& h_prog, uint64_t* unit_cnt,
+                              const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s, uint64_t* hist, int npass,
+                              uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only) {
+  const JitModule* m = (const JitModule*)B.jit[mode >= 3 ? 1 : 0];
+  const void* fn = (const void*)m->k[mode];
+  size_t smem = 0;
+  int64_t need = 0;
+  if (mode == 0 || mode == 1) {
+    smem = mode == 0 ? (size_t)npass * 256 * 4 : 0;
+    need = (h_prog.nunits + EXP_THREADS / 32 - 1) / (EXP_THREADS / 32);
+  } else {
+    smem = block_body_words(mode, (uint64_t)h_prog.nsbins) * 4;
+    need = h_prog.nblk;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXP_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)(per < 1 ? 1 : per) * L.nsm;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  void* args[] = {(void*)&h_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s, (void*)&hist,
+                  (void*)&npass,  (void*)&counters, (void*)&stbl,     (void*)&sbase,  (void*)&only};
+  (*L.launches)++;
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
+}
+
+}  // namespace hgrd
+
+extern "C" int hgrd_jit_compile(const hgrd_desc* d, const hgrd_check_opts* o, double* compile_ms) {
+  if (!d) return hgrd::fail(HGRD_EINVAL, "null descriptor");
+  if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  const bool split = d->bound->prog.smode && !(o && (o->flags & HGRD_NO_SPLIT));
+  return hgrd::jit_prepare(*d->bound, split, compile_ms);
+}
+
+extern "C" int hgrd_jit_source(const hgrd_desc* d, const hgrd_check_opts* o, char* out, size_t cap,
+                               size_t* len) {
+  if (!d) return hgrd::fail(HGRD_EINVAL, "null descriptor");
+  if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  const bool split = d->bound->prog.smode && !(o && (o->flags & HGRD_NO_SPLIT));
+  const std::string s = hgrd::jit_source(d->bound->prog, split);
+  if (len) *len = s.size();
+  if (out && cap) {
+    const size_t n = s.size() < cap - 1 ? s.size() : cap - 1;
+    memcpy(out, s.data(), n);
+    out[n] = 0;
+  }
+  return HGRD_OK;
+}

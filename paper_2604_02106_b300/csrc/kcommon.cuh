@@ -1,10 +1,15 @@
-// Device code shared by the single-check kernels (kernels.cu) and the batched
-// kernels (batch.cu): evaluation of the compiled affine program, the
-// expansion of one simulated warp, and the exact scan of one run.
+// Device code shared by the single-check kernels (kernels.cu), the batched
+// kernels (batch.cu) and the specialised expansion kernels compiled at run
+// time: evaluation of the compiled affine program, the expansion of one
+// simulated warp, and the exact scan of one run.
 #pragma once
+#if !defined(__CUDACC_RTC__)
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#else
+#include "hgrd_internal.h"
+#endif
 
 namespace hgrd {
 namespace dev {
@@ -54,6 +59,32 @@ __device__ __forceinline__ void run_ops(const DProg* __restrict__ P, int first, 
     }
     sl[op.dst * 32 + lane] = v;
   }
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t x, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// exclusive scan over a CTA of 256 threads' values; `ws` holds 8 words
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = warp_incl_scan(v, lane);
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t s = lane < 8 ? ws[lane] : 0;
+    uint64_t si = warp_incl_scan(s, lane);
+    if (lane < 8) ws[lane] = si - s;
+    if (lane == 7 && total) *total = si;
+  }
+  __syncthreads();
+  uint64_t r = x - v + ws[warp];
+  __syncthreads();
+  return r;
 }
 
 // Expansion of unit u = (block b, warp w of the block) of the user kernel,

@@ -21,7 +21,7 @@
 
 #include <algorithm>
 
-#include "kcommon.cuh"
+#include "expand_body.cuh"
 
 namespace hgrd {
 
@@ -39,6 +39,33 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
 }
 
 // ------------------------------------------------------------------ expand
+// The interpreted expander: the compiled program staged in shared memory,
+// one slot file of 32 lanes per warp.
+template <typename T>
+struct InterpX {
+  const DProg* P;
+  T* sl;
+  template <class Step>
+  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {
+    return expand_unit<T>(P, sl, lane, u, only, step);
+  }
+};
+
+// Stages the program into shared memory; returns the byte after the warps' slot files.
+template <typename T>
+__device__ __forceinline__ unsigned char* stage_program(const DProg* Pg, unsigned char* smem, InterpX<T>* ex) {
+  const uint4* src = reinterpret_cast<const uint4*>(Pg);
+  uint4* dst = reinterpret_cast<uint4*>(smem);
+  for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += EXP_THREADS) dst[i] = src[i];
+  __syncthreads();
+  const DProg* P = reinterpret_cast<const DProg*>(smem);
+  const int nslot = P->nslot;
+  unsigned char* after = smem + sizeof(DProg);
+  ex->P = P;
+  ex->sl = reinterpret_cast<T*>(after) + (size_t)(threadIdx.x >> 5) * nslot * 32;
+  return after + (size_t)(EXP_THREADS / 32) * nslot * 32 * sizeof(T);
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __restrict__ Pg, uint64_t* __restrict__ unit_cnt,
                                                              const uint64_t* __restrict__ unit_off,
@@ -47,115 +74,13 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __rest
                                                              const uint64_t* __restrict__ uniq,
                                                              PairRec* __restrict__ pairs, uint64_t pair_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int WPC = EXP_THREADS / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the compiled program, staged once per CTA (uniform shared-memory reads)
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(Pg);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += EXP_THREADS) dst[i] = src[i];
-    __syncthreads();
-  }
-  const DProg* __restrict__ P = reinterpret_cast<const DProg*>(smem);
-  const int nslot = P->nslot;
-  unsigned char* after = smem + sizeof(DProg);
-  T* sl = reinterpret_cast<T*>(after) + (size_t)warp * nslot * 32;
-  uint32_t* shist = reinterpret_cast<uint32_t*>(after + (size_t)WPC * nslot * 32 * sizeof(T));
-  if (MODE == 0) {
-    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS) shist[i] = 0;
-    __syncthreads();
-  }
-  // the minimal witness for the pair search
-  uint32_t t_arr = 0, t_lo = 0, t_hi = 0;
-  uint64_t t_gran = 0;
-  if (MODE == 2) {
-    if (counters[C_NUNIQ] == 0) return;
-    const uint64_t w0 = uniq[0];
-    t_arr = (uint32_t)(w0 >> 53) & 31;
-    t_gran = (w0 >> 13) & ((1ull << 40) - 1);
-    t_lo = (uint32_t)(w0 >> 8) & 31;
-    t_hi = (uint32_t)(w0 >> 3) & 31;
-  }
-  const int64_t nunits = P->nunits;
-  const int PB = P->PB;
-  uint64_t oob = 0;
-  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : 0xffffffffu;
-  for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
-    uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
-    oob += expand_unit<T>(P, sl, lane, u, only,
-                          [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b,
-                              int lt, const int32_t* ic) {
-                            const int G = A.G;
-                            if (MODE == 2) {
-                              if (inb) {
-                                const uint64_t g0 = (uint64_t)idx * (uint64_t)G;
-                                if ((uint32_t)A.arr == t_arr && t_gran >= g0 && t_gran < g0 + (uint64_t)G) {
-                                  const uint64_t slot = atomicAdd((unsigned long long*)&counters[C_NPAIR], 1ull);
-                                  if (slot < pair_cap) {
-                                    PairRec r;
-                                    r.blk = (uint32_t)b;
-                                    r.thr = (uint32_t)lt;
-                                    for (int l = 0; l < MAXLOOP; ++l) r.it[l] = (uint32_t)ic[l];
-                                    r.acc = a;
-                                    r.pad = 0;
-                                    r.iv = iv;
-                                    pairs[slot] = r;
-                                  }
-                                }
-                              }
-                              return;
-                            }
-                            if (inb) {
-                              const int rank = __popc(bal & lanemask_lt());
-                              for (int j = 0; j < G; ++j) {
-                                const uint64_t key = make_key(P, A, a, idx, iv, b, lt, j);
-                                if (MODE == 1) {
-                                  keys[cursor + (uint64_t)rank * G + j] = key;
-                                } else {
-                                  for (int p = 0; p < npass; ++p)
-                                    atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
-                                }
-                              }
-                            }
-                            cursor += (uint64_t)__popc(bal) * G;
-                          });
-    if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
-  }
-  if (MODE == 0) {
-    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
-    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
-    __syncthreads();
-    for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS)
-      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
-  }
+  InterpX<T> ex;
+  uint32_t* shist = reinterpret_cast<uint32_t*>(stage_program<T>(Pg, smem, &ex));
+  expand_units_body<T, MODE>(ex.P, ex, shist, unit_cnt, unit_off, keys, hist, npass, counters, uniq, pairs, pair_cap,
+                             0xffffffffu);
 }
 
 // ------------------------------------------------------------------ scan
-__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t x, int lane) {
-  for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
-
-// exclusive scan of the 256 threads' values; `ws` holds 8 words
-__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, uint64_t* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t x = warp_incl_scan(v, lane);
-  if (lane == 31) ws[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint64_t s = lane < 8 ? ws[lane] : 0;
-    uint64_t si = warp_incl_scan(s, lane);
-    if (lane < 8) ws[lane] = si - s;
-    if (lane == 7 && total) *total = si;
-  }
-  __syncthreads();
-  uint64_t r = x - v + ws[warp];
-  __syncthreads();
-  return r;
-}
 
 __device__ __forceinline__ uint64_t dev_n(const uint64_t* n_dev, uint64_t n_max) {
   if (!n_dev) return n_max;
@@ -221,158 +146,16 @@ __global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ i
 }
 
 // ------------------------------------------------------------------ expand, block-local shared bins
-// One CTA per simulated block (grid-stride over blocks); its warps take the
-// block's units.  A shared-memory race needs a writer and two threads of one
-// block in one interval (Table 2), so a (shared granule, interval) bin of the
-// block can only race when it has both; such a bin is a candidate, the rest
-// never reach the key buffer.
-//   MODE 3 (count): global-array keys per unit and their digit-0 histogram,
-//     as expansion mode 0; per bin the instance count, min / max thread and a
-//     writer bit.  The block's candidate bins get consecutive room in the
-//     shared-key region (base from a device counter, so blocks land in any
-//     order); table row b keeps (start << 32 | count) per candidate bin, 0
-//     for the others.
-//   MODE 4 (write): global keys at their unit offsets (emission order, as
-//     mode 1); keys of candidate bins into their bin, in any order, at
-//     shared_out[n_global + base(b) + start + slot].
 template <typename T, int MODE>
 __global__ void __launch_bounds__(EXP_THREADS) expand_block_kernel(
     const DProg* __restrict__ Pg, uint64_t* __restrict__ unit_cnt, const uint64_t* __restrict__ unit_off,
     uint64_t* __restrict__ keys_g, uint64_t* __restrict__ keys_s, uint64_t* __restrict__ hist,
     uint64_t* __restrict__ counters, uint64_t* __restrict__ stbl, uint64_t* __restrict__ sbase) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int WPC = EXP_THREADS / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(Pg);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += EXP_THREADS) dst[i] = src[i];
-    __syncthreads();
-  }
-  const DProg* __restrict__ P = reinterpret_cast<const DProg*>(smem);
-  const int nslot = P->nslot;
-  unsigned char* after = smem + sizeof(DProg);
-  T* sl = reinterpret_cast<T*>(after) + (size_t)warp * nslot * 32;
-  uint32_t* bins = reinterpret_cast<uint32_t*>(after + (size_t)WPC * nslot * 32 * sizeof(T));
-  const int NB = (int)P->nsbins;
-  const int niv = P->niv;
-  const int64_t ivmin = P->ivmin;
-  // MODE 3: count | min thread | max thread | writer bits | digit-0 histogram
-  uint32_t* s_cnt = bins;
-  uint32_t* s_mn = bins + NB;
-  uint32_t* s_mx = bins + 2 * NB;
-  uint32_t* s_wb = bins + 3 * NB;
-  const int NW = (NB + 31) >> 5;
-  uint32_t* shist = s_wb + NW;
-  // scan scratch: 8 words + the total, 8-byte aligned
-  uint64_t* ws = reinterpret_cast<uint64_t*>(bins + ((3 * NB + NW + 256 + 1) & ~1));
-  // MODE 4: write cursors (start of the bin's room, or NONE)
-  constexpr uint32_t NONE = 0xffffffffu;
-  uint32_t* s_cur = bins;
-  const int64_t nblk = P->nblk;
-  const int64_t upb = (int64_t)P->wpb * P->nchunk;
-  const int PB = P->PB;
-  const uint32_t wmask = P->wmask;
-  uint64_t oob = 0;
-  if (MODE == 3) {
-    for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-      s_cnt[i] = 0;
-      s_mn[i] = NONE;
-      s_mx[i] = 0;
-    }
-    for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
-    for (int i = threadIdx.x; i < 256; i += EXP_THREADS) shist[i] = 0;
-  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-    counters[C_NKEYS] = counters[C_NG] + counters[C_NS];
-  }
-  const uint64_t n_g = MODE == 4 ? counters[C_NG] : 0;
-  __syncthreads();
-  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
-    uint64_t sb = 0;
-    if (MODE == 4) {
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        const uint64_t e = stbl[(uint64_t)b * NB + i];
-        s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
-      }
-      sb = n_g + sbase[b];
-      __syncthreads();
-    }
-    for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
-      uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
-      oob += expand_unit<T>(P, sl, lane, u, 0xffffffffu,
-                            [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb,
-                                int lt, const int32_t*) {
-                              const int G = A.G;
-                              if (A.shared) {
-                                if (!inb) return;
-                                const uint32_t bin0 =
-                                    (uint32_t)(((uint64_t)A.sgbase + (uint64_t)idx * G) * niv + (uint64_t)(iv - ivmin));
-                                for (int j = 0; j < G; ++j) {
-                                  const uint32_t bin = bin0 + (uint32_t)(j * niv);
-                                  if (MODE == 3) {
-                                    atomicAdd(&s_cnt[bin], 1u);
-                                    atomicMin(&s_mn[bin], (uint32_t)lt);
-                                    atomicMax(&s_mx[bin], (uint32_t)lt);
-                                    if ((wmask >> a) & 1u) atomicOr(&s_wb[bin >> 5], 1u << (bin & 31));
-                                  } else if (s_cur[bin] != NONE) {
-                                    const uint32_t pos = atomicAdd(&s_cur[bin], 1u);
-                                    keys_s[sb + pos] = make_key(P, A, a, idx, iv, bb, lt, j);
-                                  }
-                                }
-                                return;
-                              }
-                              if (inb) {
-                                const int rank = __popc(bal & lanemask_lt());
-                                for (int j = 0; j < G; ++j) {
-                                  const uint64_t key = make_key(P, A, a, idx, iv, bb, lt, j);
-                                  if (MODE == 4)
-                                    keys_g[cursor + (uint64_t)rank * G + j] = key;
-                                  else
-                                    atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], 1u);
-                                }
-                              }
-                              cursor += (uint64_t)__popc(bal) * G;
-                            });
-      if (MODE == 3 && lane == 0) unit_cnt[u] = cursor;
-    }
-    __syncthreads();
-    if (MODE == 3) {
-      // candidate bins of block b: room in bin order of a strided walk
-      uint64_t csum = 0, asum = 0;
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        const uint32_t c = s_cnt[i];
-        asum += c;
-        if (((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i]) csum += c;
-      }
-      for (int o = 16; o; o >>= 1) asum += __shfl_down_sync(FULL, asum, o);
-      if (lane == 0 && asum) atomicAdd((unsigned long long*)&counters[C_NS], (unsigned long long)asum);
-      uint64_t start = block_excl_scan(csum, ws, ws + 8);
-      if (threadIdx.x == 0) {
-        const uint64_t tot = ws[8];
-        sbase[b] = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
-      }
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        const uint32_t c = s_cnt[i];
-        const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
-        stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
-        if (cand) start += c;
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        s_cnt[i] = 0;
-        s_mn[i] = NONE;
-        s_mx[i] = 0;
-      }
-      for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
-      __syncthreads();
-    }
-  }
-  if (MODE == 3) {
-    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
-    if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
-    for (int i = threadIdx.x; i < 256; i += EXP_THREADS)
-      if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
-  }
+  InterpX<T> ex;
+  uint32_t* bins = reinterpret_cast<uint32_t*>(stage_program<T>(Pg, smem, &ex));
+  expand_block_body<T, MODE>(ex.P, ex, bins, unit_cnt, unit_off, keys_g, keys_s, hist, counters, stbl, sbase,
+                             0xffffffffu);
 }
 
 // candidate bins of the block-local mode -> exact-scan entries, after the
@@ -1065,8 +848,7 @@ cudaError_t launch_expand_block(const Launch& L, int mode, bool wide, const DPro
                                 uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s,
                                 uint64_t* hist, uint64_t* counters, uint64_t* stbl, uint64_t* sbase) {
   const size_t esz = wide ? 8 : 4;
-  const uint64_t NB = (uint64_t)h_prog.nsbins, NW = (NB + 31) / 32;
-  const size_t tables = mode == 3 ? (((3 * NB + NW + 256 + 1) & ~1ull) * 4 + 9 * 8) : NB * 4;
+  const size_t tables = block_body_words(mode, (uint64_t)h_prog.nsbins) * 4;
   const size_t smem = sizeof(DProg) + (size_t)EXP_THREADS * h_prog.nslot * esz + tables;
   const void* fn = nullptr;
   if (!wide)

@@ -16,14 +16,6 @@ constexpr int CA_AHEAD = 4;        // 32-key steps loaded ahead by each warp
 constexpr int SCAN_TILE = 4096;
 constexpr int MAX_PASSES = 16;
 
-// Pair-search record of one instance touching the minimal witness's granule.
-struct PairRec {
-  uint32_t blk, thr;
-  uint32_t it[4];
-  int32_t acc, pad;
-  int64_t iv;
-};
-
 struct Launch {
   cudaStream_t s;
   int nsm;
