@@ -185,9 +185,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const int P = split ? B.sort_passes_split : B.sort_passes;
   uint64_t* keysA = U(W.keysA);
   uint64_t* keysB = U(W.keysB);
-  // keys the sort and the candidate scan walk: all of them, or the global
-  // ones in block-local mode (the candidate bins follow them in the final buffer)
-  uint64_t* nkeys = cnt + (split ? C_NG : C_NKEYS);
+  // keys the sort and the candidate scan walk: the written ones (of accesses
+  // that may race), only those of global arrays in block-local mode (the
+  // candidate bins follow them in the final buffer)
+  uint64_t* nkeys = cnt + C_NG;
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
     CK(launch_jit_expand(L, B, m0, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
@@ -295,7 +296,7 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(cudaStreamSynchronize(s));
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
-  g_stats.n_sorted_keys = g_stats.shared_bins ? cnt[C_NG] : cnt[C_NKEYS];
+  g_stats.n_sorted_keys = cnt[C_NG];
   g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
   g_stats.n_raw_witness = cnt[C_NRAW];
   if (cnt[C_NCAND] > std::max<uint64_t>(B.nkeys_max / 2, 1))

@@ -913,6 +913,17 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       }
     }
 
+    // an access that may race with no live access (every partner a read when
+    // it reads, two device-scope atomics, or never executed) can be in no
+    // witness: its instances are still evaluated and counted, its keys dropped
+    {
+      uint32_t live = 0;
+      for (int a = 0; a < P.nacc; a++)
+        if (!P.acc[a].dead) live |= 1u << a;
+      for (int a = 0; a < P.nacc; a++)
+        if (((P.einter[a] | P.eintra[a]) & live) && !P.acc[a].dead) P.emask |= 1u << a;
+    }
+
     // ---- key layout
     uint64_t cells = 0;
     int nl = 0;

@@ -46,8 +46,11 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
   }
   const int64_t nunits = P->nunits;
   const int PB = P->PB;
-  uint64_t oob = 0;
-  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
+  const uint32_t emask = P->emask;
+  uint64_t oob = 0, drop = 0;
+  // the write pass expands only the accesses whose keys are kept
+  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : MODE == 1 ? (only_in & emask) : only_in;
+  if (MODE == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[C_NKEYS] = counters[C_NG] + counters[C_NDROP];
   for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
     uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
     oob += ex.unit(lane, u, only,
@@ -73,6 +76,10 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                        }
                        return;
                      }
+                     if (MODE == 0 && !((emask >> a) & 1u)) {  // counted, never written
+                       if (inb) drop += (uint64_t)G;
+                       return;
+                     }
                      if (inb) {
                        const int rank = __popc(bal & lanemask_lt());
                        for (int j = 0; j < G; ++j) {
@@ -90,8 +97,12 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
     if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
   }
   if (MODE == 0) {
-    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    for (int o = 16; o; o >>= 1) {
+      oob += __shfl_down_sync(FULL, oob, o);
+      drop += __shfl_down_sync(FULL, drop, o);
+    }
     if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    if (lane == 0 && drop) atomicAdd((unsigned long long*)&counters[C_NDROP], (unsigned long long)drop);
     __syncthreads();
     for (int i = threadIdx.x; i < npass * 256; i += EXP_THREADS)
       if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
@@ -140,7 +151,8 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
   const int64_t upb = (int64_t)P->wpb * P->nchunk;
   const int PB = P->PB;
   const uint32_t wmask = P->wmask;
-  uint64_t oob = 0;
+  const uint32_t emask = P->emask;
+  uint64_t oob = 0, drop = 0;
   if (MODE == 3) {
     for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
       s_cnt[i] = 0;
@@ -150,7 +162,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
     for (int i = threadIdx.x; i < 256; i += EXP_THREADS) shist[i] = 0;
   } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-    counters[C_NKEYS] = counters[C_NG] + counters[C_NS];
+    counters[C_NKEYS] = counters[C_NG] + counters[C_NS] + counters[C_NDROP];
   }
   const uint64_t n_g = MODE == 4 ? counters[C_NG] : 0;
   // accesses to global arrays: all that a block without candidate bins writes
@@ -160,7 +172,8 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
   __syncthreads();
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     uint64_t sb = 0;
-    uint32_t only = only_in;
+    // the write pass expands only the accesses whose keys are kept
+    uint32_t only = MODE == 4 ? (only_in & emask) : only_in;
     if (MODE == 4) {
       int has = 0;
       for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
@@ -177,6 +190,10 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                      [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb, int lt,
                          const int32_t*) {
                        const int G = A.G;
+                       if (MODE == 3 && !((emask >> a) & 1u)) {  // counted, never written
+                         if (inb) drop += (uint64_t)G;
+                         return;
+                       }
                        if (A.shared) {
                          if (!inb) return;
                          const uint32_t bin0 =
@@ -242,8 +259,12 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     }
   }
   if (MODE == 3) {
-    for (int o = 16; o; o >>= 1) oob += __shfl_down_sync(FULL, oob, o);
+    for (int o = 16; o; o >>= 1) {
+      oob += __shfl_down_sync(FULL, oob, o);
+      drop += __shfl_down_sync(FULL, drop, o);
+    }
     if (lane == 0 && oob) atomicAdd((unsigned long long*)&counters[C_NOOB], (unsigned long long)oob);
+    if (lane == 0 && drop) atomicAdd((unsigned long long*)&counters[C_NDROP], (unsigned long long)drop);
     for (int i = threadIdx.x; i < 256; i += EXP_THREADS)
       if (shist[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shist[i]);
   }

@@ -107,6 +107,9 @@ struct alignas(16) DProg {
   uint64_t shared_cell_base;  // cell codes at or above this belong to shared arrays
   uint32_t wmask;             // accesses that write (W or A)
   int32_t nlay;               // arrays in layout order (global first)
+  // accesses with at least one live access they may race with (pair rule E);
+  // the others are counted but their keys are never written
+  uint32_t emask, pad3;
   // block-local ordering of shared-array keys: their runs never leave a block,
   // so they are written straight into per-block (granule, interval) bins
   // instead of going through the global sort
@@ -156,6 +159,7 @@ enum {
   C_NG,   // keys of global arrays (the sorted stream)
   C_NS,   // keys of shared arrays (smode: counted per block bin, not sorted)
   C_NSC,  // keys of shared arrays in candidate bins (smode: written behind the sorted keys)
+  C_NDROP,  // keys of accesses that cannot race with any access (counted, never written)
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_WORDS = 128
