@@ -50,6 +50,18 @@ class Witness(C.Structure):
                 ("kind_mask", C.c_uint8), ("pad", C.c_uint8 * 3), ("byte_addr", C.c_uint64)]
 
 
+def _witness_dtype():
+    import numpy as np
+    return np.dtype({"names": ["space", "array", "acc_lo", "acc_hi", "kind_mask", "byte_addr"],
+                     "formats": ["u1", "u1", "u1", "u1", "u1", "<u8"],
+                     "offsets": [Witness.space.offset, Witness.array.offset, Witness.acc_lo.offset,
+                                 Witness.acc_hi.offset, Witness.kind_mask.offset, Witness.byte_addr.offset],
+                     "itemsize": C.sizeof(Witness)})
+
+
+_WITNESS_DTYPE = _witness_dtype()
+
+
 class Inst(C.Structure):
     _fields_ = [("lin_block", C.c_uint32), ("lin_thread", C.c_uint32), ("iter", C.c_uint32 * 4),
                 ("access", C.c_uint8), ("pad", C.c_uint8 * 3)]
@@ -180,6 +192,17 @@ def _wt(w):
     return (w.space, w.array, w.byte_addr, w.acc_lo, w.acc_hi, w.kind_mask)
 
 
+def _witness_list(out, n: int) -> list:
+    """The first n hgrd_witness records of `out` as (space, array, byte_addr,
+    acc_lo, acc_hi, kind_mask) tuples (one vectorised view, no per-record ctypes access)."""
+    if n <= 0:
+        return []
+    import numpy as np
+    a = np.frombuffer(out, dtype=_WITNESS_DTYPE, count=n)
+    return list(zip(a["space"].tolist(), a["array"].tolist(), a["byte_addr"].tolist(), a["acc_lo"].tolist(),
+                    a["acc_hi"].tolist(), a["kind_mask"].tolist()))
+
+
 def _it(i):
     return (i.lin_block, i.lin_thread, *i.iter, i.access)
 
@@ -246,7 +269,7 @@ class Kernel:
             _raise(rc)
             n = min(cap, v.n_witness)
             return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
-                          [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None,
+                          _witness_list(out, n), _wt(v.min_w) if v.racy else None,
                           _it(v.min_x) if v.pair_found else None, _it(v.min_y) if v.pair_found else None,
                           rc == ETRUNCATED, _pairs(v.pair_kind))
 
@@ -279,7 +302,7 @@ class Kernel:
         _raise(rc)
         n = min(cap, v.n_witness)
         return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
-                      [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
+                      _witness_list(out, n), _wt(v.min_w) if v.racy else None, None, None,
                       rc == ETRUNCATED, _pairs(v.pair_kind))
 
     def enqueue(self, workspace, stream=None, **opts):
@@ -297,7 +320,7 @@ class Kernel:
         _raise(rc)
         n = min(cap, v.n_witness)
         return Result(bool(v.racy), v.n_witness, tuple(v.n_by_kind), v.n_instances, v.n_keys, v.n_oob,
-                      [_wt(out[k]) for k in range(n)], _wt(v.min_w) if v.racy else None, None, None,
+                      _witness_list(out, n), _wt(v.min_w) if v.racy else None, None, None,
                       rc == ETRUNCATED, _pairs(v.pair_kind))
 
 

@@ -38,7 +38,10 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
   const uint64_t scan_n = std::max(nunits, L.raw_cap);
-  const uint64_t tiles = std::max((nk + RS_MIN_TILE - 1) / RS_MIN_TILE, (L.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
+  // look-back status of the sort passes: tiles of the larger of the key sort
+  // and the witness sort
+  const uint64_t ns = std::max<uint64_t>(B.nsort_max_all, 1);
+  const uint64_t tiles = std::max((ns + RS_MIN_TILE - 1) / RS_MIN_TILE, (L.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   L.status_words = tiles * RS_RADIX;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -162,9 +165,12 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
+  // status words this check's sorts can touch (stale epochs must not survive)
+  const uint64_t nsort = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
+  const uint64_t st_tiles = std::max((nsort + RS_MIN_TILE - 1) / RS_MIN_TILE, (W.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   CK(cudaMemsetAsync(cnt, 0, C_WORDS * 8, s));
   CK(cudaMemsetAsync(U(W.hist), 0, MAX_PASSES * 256 * 8, s));
-  CK(cudaMemsetAsync(U(W.status), 0, W.status_words * 8, s));
+  CK(cudaMemsetAsync(U(W.status), 0, std::min<uint64_t>(st_tiles * RS_RADIX, W.status_words) * 8, s));
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
@@ -192,12 +198,12 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
     CK(launch_jit_expand(L, B, m0, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
-                         U(W.sbase), only_mask));
+                         U(W.sbase), only_mask, split));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
     g_prof.mark("unit_scan");
     CK(launch_jit_expand(L, B, m1, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
-                         U(W.stbl), U(W.sbase), only_mask));
+                         U(W.stbl), U(W.sbase), only_mask, split));
     g_prof.mark("expand_write");
   } else if (split) {
     CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), cnt,
@@ -222,7 +228,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // the expansion counted digit 0; each pass counts the digit of the next
   for (int p = 0; p < P; p++) {
     CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
-    CK(launch_onesweep(L, in, out, nkeys, B.nkeys_max, HP.PB + 8 * p, U(W.gbase) + p * 256, U(W.status),
+    CK(launch_onesweep(L, in, out, nkeys, nsort, HP.PB + 8 * p, U(W.gbase) + p * 256, U(W.status),
                        cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
                        p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.PB + 8 * (p + 1)));
     std::swap(in, out);
@@ -238,9 +244,12 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt, o && (o->flags & HGRD_STOP_FIRST),
                   split));
   g_prof.mark("exact");
-  // canonical order of the witnesses: radix sort of the packed words
+  // canonical order of the witnesses: up to WSMALL_MAX merged by one CTA in
+  // shared memory, more by the device-wide radix sort and merge (whose kernels
+  // see zero witnesses in the other case)
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
-  uint64_t* nraw = cnt + C_NRAW;
+  CK(launch_witness_split(L, cnt, W.raw_cap));
+  uint64_t* nraw = cnt + C_NRAWBIG;
   uint64_t* whist = U(W.hist) + 8 * 256;
   uint64_t* wgb = U(W.gbase) + 8 * 256;
   CK(launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist));
@@ -253,10 +262,11 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     std::swap(win, wout);
   }
   // win: sorted raw witnesses; wout receives the merged set
-  CK(cudaMemsetAsync(wout, 0, W.raw_cap * 8, s));
+  CK(launch_zero(L, wout, nraw, W.raw_cap));
   CK(launch_heads(L, win, nraw, W.raw_cap, U(W.flags)));
   CK(launch_scan(L, U(W.flags), U(W.excl), nraw, W.raw_cap, U(W.partials), cnt + C_NUNIQ));
   CK(launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout));
+  CK(launch_witness_small(L, U(W.raw), wout, cnt, W.raw_cap));
   CK(launch_kind_counts(L, wout, cnt));
   g_prof.mark("witness_merge");
   return HGRD_OK;
@@ -344,8 +354,14 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     PairRec* pr = (PairRec*)(ws + W.pairs);
     uint64_t zero = 0;
     CK(cudaMemcpyAsync(ws + W.counters + 8 * C_NPAIR, &zero, 8, cudaMemcpyHostToDevice, s));
-    CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, nullptr, nullptr, nullptr, 0,
-                     (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
+    // the specialised kernels when this binding has them (either module holds the search)
+    const bool jsplit = jit_ready(B, true), jplain = !jsplit && jit_ready(B, false);
+    if ((jsplit || jplain) && !(o && (o->flags & HGRD_NO_JIT)))
+      CK(launch_jit_expand(L, B, 2, HP, nullptr, nullptr, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
+                           nullptr, nullptr, 0xffffffffu, jsplit, duniq, pr, W.pair_cap));
+    else
+      CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, nullptr, nullptr, nullptr, 0,
+                       (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
     uint64_t np = 0;
     CK(cudaMemcpyAsync(&np, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
     g_stats.h2d_bytes += 8;

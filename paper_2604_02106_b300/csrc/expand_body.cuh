@@ -7,14 +7,28 @@
 //                from the kernel's parameter block.
 // Both hand a unit expander X to the same bodies, so the keys, counts and bins
 // they produce are the same by construction.  X provides
-//   template <class Step> uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step)
+//   template <int SEL, class Step> uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step)
 // with expand_unit's contract (step called per access and loop vector with a
-// live in-bounds lane in the warp; returns this lane's out-of-bounds instances).
+// live in-bounds lane in the warp; returns this lane's out-of-bounds
+// instances), over the accesses in `only` and in the set SEL names:
+//   SEL_ALL every access; SEL_KEPT accesses whose keys are written (emask);
+//   SEL_KEPT_GLOBAL those of them on global arrays.
+// The specialised expander fixes SEL's set at compile time, so work only
+// the other accesses need (their ops, guards, indexes) is never emitted.
+// X also provides unit_combine(lane, u, only, step, flush), the same walk for
+// the block-local count pass, where an expander may hand the instances of a
+// shared-array access with one granule per instance to
+//   flush(a, bin, count, lt)
+// instead of step: `count` instances of thread lt on (granule, interval) bin
+// `bin`, combined while consecutive instances of the access stay in one bin.
+// The bin's count, min / max thread and writer bit end up the same.
 #pragma once
 #include "kcommon.cuh"
 
 namespace hgrd {
 namespace dev {
+
+enum { SEL_ALL = 0, SEL_KEPT = 1, SEL_KEPT_GLOBAL = 2 };
 
 // Modes 0 (count keys per unit + digit histograms of `npass` digits), 1 (write
 // keys at the unit offsets) and 2 (gather the instances of the minimal
@@ -48,12 +62,12 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
   const int PB = P->PB;
   const uint32_t emask = P->emask;
   uint64_t oob = 0, drop = 0;
-  // the write pass expands only the accesses whose keys are kept
-  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : MODE == 1 ? (only_in & emask) : only_in;
+  const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
   if (MODE == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[C_NKEYS] = counters[C_NG] + counters[C_NDROP];
   for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
     uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
-    oob += ex.unit(lane, u, only,
+    // the write pass expands only the accesses whose keys are kept
+    oob += ex.template unit<MODE == 1 ? SEL_KEPT : SEL_ALL>(lane, u, only,
                    [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,
                        const int32_t* ic) {
                      const int G = A.G;
@@ -165,29 +179,23 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     counters[C_NKEYS] = counters[C_NG] + counters[C_NS] + counters[C_NDROP];
   }
   const uint64_t n_g = MODE == 4 ? counters[C_NG] : 0;
-  // accesses to global arrays: all that a block without candidate bins writes
-  uint32_t gmask = 0;
-  for (int a = 0; a < P->nacc; ++a)
-    if (!P->acc[a].shared) gmask |= 1u << a;
   __syncthreads();
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     uint64_t sb = 0;
-    // the write pass expands only the accesses whose keys are kept
-    uint32_t only = MODE == 4 ? (only_in & emask) : only_in;
+    bool has = true;  // the block has candidate bins
     if (MODE == 4) {
-      int has = 0;
+      int hb = 0;
       for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
         const uint64_t e = stbl[(uint64_t)b * NB + i];
         s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
-        has |= (uint32_t)e != 0;
+        hb |= (uint32_t)e != 0;
       }
       sb = n_g + sbase[b];
-      if (!__syncthreads_or(has)) only &= gmask;
+      has = __syncthreads_or(hb) != 0;
     }
     for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
       uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
-      oob += ex.unit(lane, u, only,
-                     [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb, int lt,
+      auto step = [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb, int lt,
                          const int32_t*) {
                        const int G = A.G;
                        if (MODE == 3 && !((emask >> a) & 1u)) {  // counted, never written
@@ -223,7 +231,21 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                          }
                        }
                        cursor += (uint64_t)__popc(bal) * G;
-                     });
+                     };
+      auto flush = [&](int a, uint32_t bin, uint32_t count, int lt) {
+        atomicAdd(&s_cnt[bin], count);
+        atomicMin(&s_mn[bin], (uint32_t)lt);
+        atomicMax(&s_mx[bin], (uint32_t)lt);
+        if ((wmask >> a) & 1u) atomicOr(&s_wb[bin >> 5], 1u << (bin & 31));
+      };
+      // the write pass expands only the accesses whose keys are kept, and of
+      // those only the global ones in a block without candidate bins
+      if (MODE == 3)
+        oob += ex.template unit_combine<SEL_ALL>(lane, u, only_in, step, flush);
+      else if (has)
+        oob += ex.template unit<SEL_KEPT>(lane, u, only_in, step);
+      else
+        oob += ex.template unit<SEL_KEPT_GLOBAL>(lane, u, only_in, step);
       if (MODE == 3 && lane == 0) unit_cnt[u] = cursor;
     }
     __syncthreads();

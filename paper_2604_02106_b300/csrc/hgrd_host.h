@@ -55,6 +55,9 @@ struct Bound {
   std::vector<int64_t> array_bytes, array_granule;
   uint64_t n_instances = 0;
   uint64_t nkeys_max = 0;
+  // bounds of the keys the global sort sees: written keys of every access
+  // (one sort of everything) or of global-array accesses (block-local mode)
+  uint64_t nsort_max_all = 0, nsort_max_split = 0;
   int sort_passes = 0;        // radix passes over all keys
   int sort_passes_split = 0;  // radix passes over the global-array keys (block-local mode)
   bool wide = false;

@@ -73,8 +73,15 @@ std::string jit_source(const DProg& P, bool split) {
   src += std::string("typedef ") + (P.wide ? "int64_t" : "int32_t") + " T;\n";
   src += "template <typename U> __device__ __forceinline__ U modq(U v, const Magic& g, U d) { return v - divq<U>(v, g) * d; }\n";
   src += "struct GenX {\n  const DProg* __restrict__ P;\n";
-  src += "  template <class Step>\n";
+  src += "  template <int SEL, class Step>\n";
   src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
+  src += "    return walk<SEL, false>(lane, u, only, step, [](int, uint32_t, uint32_t, int) {});\n  }\n";
+  src += "  template <int SEL, class Step, class Flush>\n";
+  src += "  __device__ __forceinline__ uint64_t unit_combine(int lane, int64_t u, uint32_t only, Step&& step, "
+         "Flush&& flush) {\n";
+  src += "    return walk<SEL, true>(lane, u, only, step, flush);\n  }\n";
+  src += "  template <int SEL, bool COMBINE, class Step, class Flush>\n";
+  src += "  __device__ __forceinline__ uint64_t walk(int lane, int64_t u, uint32_t only, Step&& step, Flush&& flush) {\n";
   src += "    const int64_t bw = u / P->nchunk;\n";
   src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
   src += "    const int64_t it1 = min(P->nit, it0 + P->itc);\n";
@@ -96,6 +103,14 @@ std::string jit_source(const DProg& P, bool split) {
   for (int l = nl - 1; l >= 0; l--)
     src += "      ic[" + S(l) + "] = (int32_t)(r % P->ub[" + S(l) + "]); r /= P->ub[" + S(l) + "];\n";
   src += "    }\n    uint64_t oob = 0;\n";
+  // combined bin updates: per shared-array access with one granule per
+  // instance, the bin and count of this lane's run of instances
+  auto combinable = [&](int a) {
+    const DAcc& A = P.acc[a];
+    return !A.dead && A.shared && A.G == 1 && ((P.emask >> a) & 1u);
+  };
+  for (int a = 0; a < P.nacc; a++)
+    if (combinable(a)) src += "    uint32_t pb" + S(a) + " = 0xffffffffu, pc" + S(a) + " = 0;\n";
   src += "    for (int64_t it = it0; it < it1; ++it) {\n";
   if (nl > 0) {
     src += "      if (it > it0) {\n";
@@ -113,7 +128,11 @@ std::string jit_source(const DProg& P, bool split) {
     const DAcc& A = P.acc[a];
     if (A.dead) continue;
     const std::string at = "P->acc[" + S(a) + "]";
-    src += "      if (only & " + S(1ll << a) + "u) {  // access " + S(a) + "\n";
+    // in the selected set at compile time (SEL_KEPT: keys written; SEL_KEPT_GLOBAL: and a global array)
+    const bool kept = (P.emask >> a) & 1u;
+    const std::string in_sel = "(SEL == SEL_ALL || (SEL == SEL_KEPT && " + S(kept) + ") || (SEL == SEL_KEPT_GLOBAL && " +
+                               S(kept && !A.shared) + "))";
+    src += "      if (" + in_sel + " && (only & " + S(1ll << a) + "u)) {  // access " + S(a) + "\n";
     src += "        bool live = act;\n";
     for (int g = 0; g < A.ng; g++)
       src += "        live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
@@ -123,6 +142,17 @@ std::string jit_source(const DProg& P, bool split) {
     else
       src += "        const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
     src += "        oob += (live && !inb) ? 1 : 0;\n";
+    if (combinable(a)) {
+      src += "        if constexpr (COMBINE) {\n";
+      src += "          if (inb) {\n";
+      src += "            const uint32_t bin = (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + "
+             "(uint64_t)((int64_t)" + lin(P, at + ".iv", A.iv) + " - P->ivmin));\n";
+      src += "            if (bin != pb" + S(a) + ") {\n";
+      src += "              if (pc" + S(a) + ") flush(" + S(a) + ", pb" + S(a) + ", pc" + S(a) + ", lt);\n";
+      src += "              pb" + S(a) + " = bin;\n              pc" + S(a) + " = 0;\n            }\n";
+      src += "            ++pc" + S(a) + ";\n          }\n";
+      src += "        } else {\n";
+    }
     src += "        const unsigned bal = __ballot_sync(0xffffffffu, inb);\n";
     src += "        if (bal) {\n";
     src += "          int64_t iv = 0;\n";
@@ -132,15 +162,26 @@ std::string jit_source(const DProg& P, bool split) {
     src += "          DAcc A = " + at + ";\n";
     src += "          A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
     src += "          step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, ic);\n";
-    src += "        }\n      }\n";
+    src += "        }\n";
+    if (combinable(a)) src += "        }\n";
+    src += "      }\n";
   }
-  src += "    }\n    return oob;\n  }\n};\n}}  // namespace hgrd::dev\n";
+  src += "    }\n";
+  for (int a = 0; a < P.nacc; a++)
+    if (combinable(a))
+      src += "    if constexpr (COMBINE) { if (pc" + S(a) + ") flush(" + S(a) + ", pb" + S(a) + ", pc" + S(a) + ", lt); }\n";
+  src += "    return oob;\n  }\n};\n}}  // namespace hgrd::dev\n";
   src += "using namespace hgrd;\nusing namespace hgrd::dev;\n";
   const char* sig =
       "(const __grid_constant__ DProg Pp, uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, "
       "uint64_t* keys_s, uint64_t* hist, int npass, uint64_t* counters, uint64_t* stbl, uint64_t* sbase, "
-      "uint32_t only) {\n  extern __shared__ __align__(16) unsigned char smem[];\n  GenX ex{&Pp};\n";
-  // the count and write kernels of one pipeline: block-local (3, 4) or plain (0, 1)
+      "uint32_t only, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {\n"
+      "  extern __shared__ __align__(16) unsigned char smem[];\n  GenX ex{&Pp};\n";
+  // the pair search (2), and the count and write kernels of one pipeline:
+  // block-local (3, 4) or plain (0, 1)
+  src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand2" + std::string(sig);
+  src += "  expand_units_body<T, 2>(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, hist, "
+         "npass, counters, uniq, pairs, pair_cap, only);\n}\n";
   if (!split) {
     for (int m : {0, 1}) {
       src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand" + S(m) + sig;
@@ -210,12 +251,12 @@ JitModule* compile(const std::string& src, double* ms) {
       if (e != cudaSuccess) {
         mod->log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
       } else {
-        static const char* kn[5] = {"hgrd_jit_expand0", "hgrd_jit_expand1", nullptr, "hgrd_jit_expand3",
+        static const char* kn[5] = {"hgrd_jit_expand0", "hgrd_jit_expand1", "hgrd_jit_expand2", "hgrd_jit_expand3",
                                     "hgrd_jit_expand4"};
         const bool split = src.find("hgrd_jit_expand3") != std::string::npos;
         mod->ok = true;
         for (int m = 0; m < 5 && mod->ok; m++) {
-          if (!kn[m] || (split != (m >= 3))) continue;
+          if (m != 2 && split != (m >= 3)) continue;
           e = cudaLibraryGetKernel(&mod->k[m], mod->lib, kn[m]);
           if (e != cudaSuccess) {
             mod->ok = false;
@@ -261,12 +302,13 @@ bool jit_ready(const Bound& B, bool split) {
 
 cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const DProg& h_prog, uint64_t* unit_cnt,
                               const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s, uint64_t* hist, int npass,
-                              uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only) {
-  const JitModule* m = (const JitModule*)B.jit[mode >= 3 ? 1 : 0];
+                              uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only, bool split,
+                              const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {
+  const JitModule* m = (const JitModule*)B.jit[split ? 1 : 0];
   const void* fn = (const void*)m->k[mode];
   size_t smem = 0;
   int64_t need = 0;
-  if (mode == 0 || mode == 1) {
+  if (mode <= 2) {
     smem = mode == 0 ? (size_t)npass * 256 * 4 : 0;
     need = (h_prog.nunits + EXP_THREADS / 32 - 1) / (EXP_THREADS / 32);
   } else {
@@ -281,8 +323,9 @@ cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const D
   int64_t grid = (int64_t)(per < 1 ? 1 : per) * L.nsm;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  void* args[] = {(void*)&h_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s, (void*)&hist,
-                  (void*)&npass,  (void*)&counters, (void*)&stbl,     (void*)&sbase,  (void*)&only};
+  void* args[] = {(void*)&h_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s,
+                  (void*)&hist,   (void*)&npass,    (void*)&counters, (void*)&stbl,   (void*)&sbase,
+                  (void*)&only,   (void*)&uniq,     (void*)&pairs,    (void*)&pair_cap};
   (*L.launches)++;
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
 }

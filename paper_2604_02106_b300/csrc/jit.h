@@ -18,9 +18,11 @@ std::string jit_source(const DProg& P, bool split);
 int jit_prepare(const Bound& B, bool split, double* ms);
 // whether B already holds loaded kernels for the pipeline
 bool jit_ready(const Bound& B, bool split);
-// one expansion launch (mode 0, 1, 3 or 4) on the specialised kernels of B
+// one expansion launch (mode 0..4) on the specialised kernels of B's plain
+// or block-local (split) module; mode 2 (pair search) is in both
 cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const DProg& h_prog, uint64_t* unit_cnt,
                               const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s, uint64_t* hist, int npass,
-                              uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only);
+                              uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only, bool split,
+                              const uint64_t* uniq = nullptr, PairRec* pairs = nullptr, uint64_t pair_cap = 0);
 
 }  // namespace hgrd

@@ -45,9 +45,18 @@ template <typename T>
 struct InterpX {
   const DProg* P;
   T* sl;
-  template <class Step>
+  template <int SEL, class Step>
   __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {
+    if (SEL != SEL_ALL) only &= P->emask;
+    if (SEL == SEL_KEPT_GLOBAL)
+      for (int a = 0; a < P->nacc; ++a)
+        if (P->acc[a].shared) only &= ~(1u << a);
     return expand_unit<T>(P, sl, lane, u, only, step);
+  }
+  // the interpreter hands every instance to step
+  template <int SEL, class Step, class Flush>
+  __device__ __forceinline__ uint64_t unit_combine(int lane, int64_t u, uint32_t only, Step&& step, Flush&&) {
+    return unit<SEL>(lane, u, only, step);
   }
 };
 
@@ -696,6 +705,82 @@ __global__ void merge_kernel(const uint64_t* __restrict__ w, const uint64_t* __r
   }
 }
 
+__global__ void witness_split_kernel(uint64_t* counters, uint64_t raw_cap) {
+  uint64_t n = counters[C_NRAW];
+  if (n > raw_cap) n = raw_cap;
+  counters[C_NRAWBIG] = n > (uint64_t)WSMALL_MAX ? n : 0;
+}
+
+__global__ void zero_kernel(uint64_t* __restrict__ p, const uint64_t* n_dev, uint64_t n_max) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = 0;
+}
+
+// One CTA merges up to WSMALL_MAX raw witnesses: bitonic sort of the packed
+// words in shared memory (the kind mask sits in the lowest bits, so the words
+// of one (space, array, granule, acc_lo, acc_hi) end up adjacent and in
+// canonical order), then one output word per group with the kinds OR-ed.
+__global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __restrict__ raw,
+                                                             uint64_t* __restrict__ uniq, uint64_t* counters,
+                                                             uint64_t raw_cap) {
+  __shared__ uint64_t s[WSMALL_MAX];
+  __shared__ uint32_t wsum[32];
+  uint64_t n64 = counters[C_NRAW];
+  if (n64 > raw_cap) n64 = raw_cap;
+  if (n64 == 0 || n64 > (uint64_t)WSMALL_MAX) return;
+  const uint32_t n = (uint32_t)n64;
+  uint32_t m = 1;
+  while (m < n) m <<= 1;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? raw[i] : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= m; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < m; i += 1024) {
+        const uint32_t x = i ^ j;
+        if (x > i) {
+          const uint64_t a = s[i], b = s[x];
+          if ((a > b) == ((i & k) == 0)) {
+            s[i] = b;
+            s[x] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // group heads over contiguous chunks, a CTA-wide exclusive scan of their counts
+  const uint32_t chunk = (n + 1023) / 1024;
+  const uint32_t c0 = min(n, tid * chunk), c1 = min(n, c0 + chunk);
+  uint32_t heads = 0;
+  for (uint32_t i = c0; i < c1; ++i) heads += (i == 0 || (s[i] >> WIT_SORT_LO) != (s[i - 1] >> WIT_SORT_LO)) ? 1u : 0u;
+  uint32_t x = heads;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = wsum[lane];
+    uint32_t t = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, t, o);
+      if (lane >= (uint32_t)o) t += y;
+    }
+    wsum[lane] = t - v;
+    if (lane == 31) counters[C_NUNIQ] = t;
+  }
+  __syncthreads();
+  uint32_t u = wsum[warp] + x - heads;
+  for (uint32_t i = c0; i < c1; ++i) {
+    if (!(i == 0 || (s[i] >> WIT_SORT_LO) != (s[i - 1] >> WIT_SORT_LO))) continue;
+    uint64_t w = s[i];
+    for (uint32_t j = i + 1; j < n && (s[j] >> WIT_SORT_LO) == (s[i] >> WIT_SORT_LO); ++j) w |= s[j];
+    uniq[u++] = w;
+  }
+}
+
 __global__ void kind_counts_kernel(const uint64_t* __restrict__ uniq, uint64_t* counters) {
   const uint64_t n = counters[C_NUNIQ];
   uint64_t c0 = 0, c1 = 0, c2 = 0;
@@ -889,6 +974,27 @@ cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* fla
   uint64_t blocks = (n_max + 255) / 256;
   unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
   merge_kernel<<<grid, 256, 0, L.s>>>(w, flags, excl, n_dev, n_max, uniq);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap) {
+  witness_split_kernel<<<1, 1, 0, L.s>>>(counters, raw_cap);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
+                                 uint64_t raw_cap) {
+  witness_small_kernel<<<1, 1024, 0, L.s>>>(raw, uniq, counters, raw_cap);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(const Launch& L, uint64_t* p, const uint64_t* n_dev, uint64_t n_max) {
+  uint64_t blocks = (n_max + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
+  zero_kernel<<<grid, 256, 0, L.s>>>(p, n_dev, n_max);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -66,5 +66,14 @@ cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_d
 cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* flags, const uint64_t* excl,
                          const uint64_t* n_dev, uint64_t n_max, uint64_t* uniq);
 cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters);
+// at most WSMALL_MAX raw witnesses are merged by one CTA: witness_split sets
+// counters[C_NRAWBIG] (0 in that case, else the count) for the device-wide
+// kernels; witness_small then merges the few from `raw` into `uniq`
+constexpr int WSMALL_MAX = 4096;
+cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap);
+cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
+                                 uint64_t raw_cap);
+// zero the first min(*n_dev, n_max) words of p
+cudaError_t launch_zero(const Launch& L, uint64_t* p, const uint64_t* n_dev, uint64_t n_max);
 
 }  // namespace hgrd
