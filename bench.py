@@ -422,11 +422,11 @@ def main():
         dist.barrier()
     t_e2e = []
     # warm-up of the synchronous path: first use of its kernels, and clocks
-    # back up after the idle gap that ends the sampled region (at least W
-    # calls and 0.3 s)
+    # back at steady state after the idle gap that ends the sampled region
+    # (measured: about a second of calls; at least W calls and 1 s)
     t_w = time.perf_counter()
     n_w = 0
-    while n_w < max(3, args.warmup) or time.perf_counter() - t_w < 0.3:
+    while n_w < max(3, args.warmup) or time.perf_counter() - t_w < 1.0:
         k.check(cap=1 << 16, stream=s)
         n_w += 1
     torch.cuda.synchronize()

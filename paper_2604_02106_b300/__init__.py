@@ -76,7 +76,7 @@ class Verdict(C.Structure):
 
 class CheckOpts(C.Structure):
     _fields_ = [("max_raw_witness", C.c_uint64), ("pair_cap", C.c_uint32), ("flags", C.c_uint32),
-                ("only_accesses", C.c_uint32), ("reserved", C.c_uint32)]
+                ("only_accesses", C.c_uint32), ("max_shared_keys", C.c_uint32)]
 
 
 class BatchOpts(C.Structure):
@@ -152,8 +152,8 @@ def _raise(rc):
         raise HgrdError(rc, lib().hgrd_last_error().decode(errors="replace"))
 
 
-def _opts(max_raw_witness=0, pair_cap=0, flags=0, only_accesses=0):
-    return CheckOpts(max_raw_witness, pair_cap, flags, only_accesses, 0)
+def _opts(max_raw_witness=0, pair_cap=0, flags=0, only_accesses=0, max_shared_keys=0):
+    return CheckOpts(max_raw_witness, pair_cap, flags, only_accesses, max_shared_keys)
 
 
 def _pairs(pk):
@@ -262,7 +262,12 @@ class Kernel:
             rc = lib().hgrd_check(self._h, C.byref(o), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
                                   out, cap, C.byref(v))
             if rc == -6 and workspace is None and attempt == 0:
+                # a buffer sized by default was short: retry once with the count the device reported
                 st = stats()
+                msg = lib().hgrd_last_error().decode(errors="replace")
+                if "max_shared_keys" in msg:
+                    opts = dict(opts, max_shared_keys=min(0xffffffff, int(st["n_binned_keys"] * 1.25) + 1024))
+                    continue
                 if st["n_raw_witness"] > opts.get("max_raw_witness", 0):
                     opts = dict(opts, max_raw_witness=int(st["n_raw_witness"] * 1.25) + 1024)
                     continue

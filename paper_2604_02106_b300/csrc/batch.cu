@@ -43,7 +43,7 @@ constexpr int SB_RAW = 1024;    // per-run witnesses of one small item
 constexpr int SB_SLOTS = 64;    // slot file entries per simulated lane
 constexpr int SB_PASSES = 4;    // radix passes (32 sorted bits)
 constexpr int OUT_WORDS = 56;   // n_keys, n_oob, n_witness, kind0..2, flags, n_raw, 48 racy-pair words
-enum { F_RAW_OVERFLOW = 1, F_TIMEOUT = 2, F_CAND_OVERFLOW = 4 };
+enum { F_RAW_OVERFLOW = 1, F_TIMEOUT = 2, F_CAND_OVERFLOW = 4, F_SHARED_OVERFLOW = 8 };
 
 struct SmallSmem {
   DProg prog;
@@ -343,7 +343,7 @@ __global__ void gather_kernel(const uint64_t* __restrict__ cnt, const uint64_t* 
     out[4] = cnt[C_KIND1];
     out[5] = cnt[C_KIND2];
     out[6] = (cnt[C_NRAW] > raw_cap ? F_RAW_OVERFLOW : 0) | ((cnt[C_ERR] & ERR_TIMEOUT) ? F_TIMEOUT : 0) |
-             (cnt[C_NCAND] > cand_cap ? F_CAND_OVERFLOW : 0);
+             (cnt[C_NCAND] > cand_cap ? F_CAND_OVERFLOW : 0) | ((cnt[C_ERR] & ERR_SHARED_FULL) ? F_SHARED_OVERFLOW : 0);
     out[7] = cnt[C_NRAW];
   }
   if (threadIdx.x < 48) out[8 + threadIdx.x] = cnt[C_PAIRS + threadIdx.x];
@@ -598,7 +598,9 @@ int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream,
     for (int k = 0; k < 3; k++)
       for (int a = 0; a < 32; a++) x.pair_kind[k][a] = (uint32_t)(o[8 + k * 16 + a / 2] >> (32 * (a & 1)));
     x.small = std::find(b->small.begin(), b->small.end(), (uint32_t)i) != b->small.end();
-    x.status = (o[6] & F_TIMEOUT) ? HGRD_ETIMEOUT : (o[6] & (F_RAW_OVERFLOW | F_CAND_OVERFLOW)) ? HGRD_ENOMEM : HGRD_OK;
+    x.status = (o[6] & F_TIMEOUT)                                               ? HGRD_ETIMEOUT
+               : (o[6] & (F_RAW_OVERFLOW | F_CAND_OVERFLOW | F_SHARED_OVERFLOW)) ? HGRD_ENOMEM
+                                                                                  : HGRD_OK;
     if (x.status) {
       worst = x.status;
       continue;

@@ -25,22 +25,35 @@ struct Layout {
   size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
       pairs, stbl, sbase, total;
   uint64_t raw_cap, pair_cap, status_words;
+  uint64_t scap;       // room for keys of candidate shared bins (block-local mode)
+  uint64_t key_words;  // length of each key buffer
+  uint64_t cand_cap;   // candidate entries (two words each) the spare key buffer holds
 };
 
 Layout layout(const Bound& B, const hgrd_check_opts* o) {
   Layout L{};
   const DProg& P = B.prog;
   const uint64_t nk = std::max<uint64_t>(B.nkeys_max, 1);
-  // defaults scale with the problem: per-run witnesses rarely exceed twice
-  // the keys, and the instances on one granule never exceed the keys
-  L.raw_cap = (o && o->max_raw_witness) ? o->max_raw_witness
-                                        : std::min<uint64_t>(1ull << 24, std::max<uint64_t>(1ull << 12, 2 * nk));
+  // the key buffers hold what can be written: kept keys of every access (one
+  // sort of everything), or kept global keys plus room for candidate shared
+  // bins (block-local mode)
+  const bool split = P.smode && !(o && (o->flags & HGRD_NO_SPLIT));
+  L.scap = split ? ((o && o->max_shared_keys) ? o->max_shared_keys : P.scap) : 0;
+  L.key_words = std::max<uint64_t>(split ? B.nsort_max_split + L.scap : B.nsort_max_all, 1);
+  // a candidate run holds at least two keys
+  L.cand_cap = std::max<uint64_t>(L.key_words / 2, 1);
+  // defaults scale with the problem and come back as HGRD_ENOMEM (with the
+  // count needed) when a check outgrows them: per-run witnesses rarely exceed
+  // the written keys, and the instances on one granule never exceed the keys
+  L.raw_cap = (o && o->max_raw_witness)
+                  ? o->max_raw_witness
+                  : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 12, 2 * L.key_words));
   L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
   const uint64_t scan_n = std::max(nunits, L.raw_cap);
   // look-back status of the sort passes: tiles of the larger of the key sort
   // and the witness sort
-  const uint64_t ns = std::max<uint64_t>(B.nsort_max_all, 1);
+  const uint64_t ns = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
   const uint64_t tiles = std::max((ns + RS_MIN_TILE - 1) / RS_MIN_TILE, (L.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   L.status_words = tiles * RS_RADIX;
   size_t off = 0;
@@ -57,8 +70,8 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   L.hist = take(MAX_PASSES * 256 * 8);
   L.gbase = take(MAX_PASSES * 256 * 8);
   L.status = take(L.status_words * 8);
-  L.keysA = take(nk * 8);
-  L.keysB = take(nk * 8);
+  L.keysA = take(L.key_words * 8);
+  L.keysB = take(L.key_words * 8);
   L.raw = take(L.raw_cap * 8);
   L.raw2 = take(L.raw_cap * 8);
   L.flags = take(L.raw_cap * 8);
@@ -174,16 +187,20 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
+  // the program this check runs: a copy when it is restricted to a subset of
+  // the accesses (the others marked dead) or has its own room for shared keys
+  const DProg* hprog = &HP;
   if (!dprog_resident) {
-    if (restricted) {
-      static thread_local DProg tmp;
-      tmp = HP;
-      for (int a = 0; a < tmp.nacc; a++)
-        if (!((only >> a) & 1u)) tmp.acc[a].dead = 1;
-      CK(cudaMemcpyAsync(ws + W.prog, &tmp, sizeof(DProg), cudaMemcpyHostToDevice, s));
-    } else {
-      CK(cudaMemcpyAsync(ws + W.prog, &HP, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    if (restricted || (split && W.scap != HP.scap)) {
+      static thread_local DProg run_prog;
+      run_prog = HP;
+      if (restricted)
+        for (int a = 0; a < run_prog.nacc; a++)
+          if (!((only >> a) & 1u)) run_prog.acc[a].dead = 1;
+      if (split) run_prog.scap = W.scap;
+      hprog = &run_prog;
     }
+    CK(cudaMemcpyAsync(ws + W.prog, hprog, sizeof(DProg), cudaMemcpyHostToDevice, s));
     g_stats.h2d_bytes += sizeof(DProg);
   }
   g_prof.mark("setup");
@@ -197,12 +214,12 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   uint64_t* nkeys = cnt + C_NG;
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
-    CK(launch_jit_expand(L, B, m0, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
+    CK(launch_jit_expand(L, B, m0, *hprog, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
                          U(W.sbase), only_mask, split));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
     g_prof.mark("unit_scan");
-    CK(launch_jit_expand(L, B, m1, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
+    CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
                          U(W.stbl), U(W.sbase), only_mask, split));
     g_prof.mark("expand_write");
   } else if (split) {
@@ -237,7 +254,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     g_prof.mark(pn[p & 7]);
   }
   // `in` holds the sorted keys; `out` is free for the candidate list
-  const uint64_t cand_cap = std::max<uint64_t>(B.nkeys_max / 2, 1);
+  const uint64_t cand_cap = W.cand_cap;
   CK(launch_candidates(L, in, nkeys, dprog, out, cand_cap, cnt));
   if (split) CK(launch_shared_cand(L, HP, U(W.stbl), U(W.sbase), out, cand_cap, cnt));
   g_prof.mark("candidates");
@@ -309,8 +326,10 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   g_stats.n_sorted_keys = cnt[C_NG];
   g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
   g_stats.n_raw_witness = cnt[C_NRAW];
-  if (cnt[C_NCAND] > std::max<uint64_t>(B.nkeys_max / 2, 1))
-    return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
+  if (cnt[C_ERR] & ERR_SHARED_FULL)
+    return fail(HGRD_ENOMEM, "room for keys of candidate shared-memory bins too small: need " +
+                                 std::to_string(cnt[C_NSC]) + " (hgrd_check_opts.max_shared_keys)");
+  if (cnt[C_NCAND] > W.cand_cap) return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
   if (cnt[C_NRAW] > W.raw_cap)
     return fail(HGRD_ENOMEM, "raw witness buffer too small: need " + std::to_string(cnt[C_NRAW]) +
                                  " (hgrd_check_opts.max_raw_witness)");
@@ -428,7 +447,7 @@ int item_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* ws, size_t 
   *counters = (uint64_t*)((char*)ws + W.counters);
   *uniq = uniq_buffer(d, W, (char*)ws);
   *raw_cap = W.raw_cap;
-  *cand_cap = std::max<uint64_t>(d->bound->nkeys_max / 2, 1);
+  *cand_cap = W.cand_cap;
   return HGRD_OK;
 }
 
@@ -549,8 +568,10 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   CK(cudaMemcpyAsync(cnt, ws + W.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
-  if (cnt[C_NCAND] > std::max<uint64_t>(d->bound->nkeys_max / 2, 1))
-    return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
+  if (cnt[C_ERR] & ERR_SHARED_FULL)
+    return fail(HGRD_ENOMEM, "room for keys of candidate shared-memory bins too small: need " +
+                                 std::to_string(cnt[C_NSC]) + " (hgrd_check_opts.max_shared_keys)");
+  if (cnt[C_NCAND] > W.cand_cap) return fail(HGRD_EUNSUPPORTED, "candidate list overflow");
   if (cnt[C_NRAW] > W.raw_cap)
     return fail(HGRD_ENOMEM, "raw witness buffer too small: need " + std::to_string(cnt[C_NRAW]) +
                                  " (hgrd_check_opts.max_raw_witness)");

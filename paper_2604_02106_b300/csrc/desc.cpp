@@ -962,12 +962,19 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (!P.acc[a].dead) kmax += (unsigned __int128)nblk * nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
     if (kmax >= ((unsigned __int128)1 << 40)) raise(HGRD_EUNSUPPORTED, "more than 2^40 keys");
     B.nkeys_max = (uint64_t)kmax;
+    uint64_t nshared_kept = 0;
     for (int a = 0; a < P.nacc; a++) {
       if (P.acc[a].dead || !((P.emask >> a) & 1u)) continue;
       const uint64_t k = (uint64_t)nblk * (uint64_t)nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
       B.nsort_max_all += k;
       if (!P.acc[a].shared) B.nsort_max_split += k;
+      else nshared_kept += k;
     }
+    // default room for keys of candidate shared bins: a sixteenth of the
+    // shared keys (at least 2^20, at most all of them, below 2^32); a check
+    // that needs more reports HGRD_ENOMEM with the count
+    P.scap = std::min<uint64_t>(std::min<uint64_t>(nshared_kept, 0xffffffffull),
+                                std::max<uint64_t>(1ull << 20, nshared_kept / 16));
     // Block-local mode: shared-memory runs never leave their block and a
     // shared-memory race needs two threads of one block in one interval
     // (Table 2), so shared keys can be counted per (granule, interval) bin of

@@ -262,11 +262,19 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
       uint64_t start = block_excl_scan(csum, ws, ws + 8);
       if (threadIdx.x == 0) {
         const uint64_t tot = ws[8];
-        sbase[b] = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
+        uint64_t base = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
+        if (base + tot > P->scap) {  // no room: the check reports it, the block writes nothing
+          atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_SHARED_FULL);
+          base = ~0ull;
+        }
+        sbase[b] = base;
+        ws[9] = base;
       }
+      __syncthreads();
+      const bool full = ws[9] == ~0ull;
       for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
         const uint32_t c = s_cnt[i];
-        const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
+        const bool cand = !full && ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
         stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
         if (cand) start += c;
       }

@@ -116,6 +116,7 @@ struct alignas(16) DProg {
   int32_t smode, niv;         // smode: shared keys use the bins; niv: intervals
   int64_t nsbins;             // bins of one block: shared granules x intervals
   int32_t RBG, pad2;          // run-code bits of the global-array keys (the sorted ones)
+  uint64_t scap;              // room for keys of candidate bins (more: HGRD_ENOMEM)
   uint32_t einter[MAXACC], eintra[MAXACC];
   uint64_t lay_cbase[MAXARR + 1];
   uint64_t lay_ngran[MAXARR];
@@ -165,7 +166,7 @@ enum {
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_WORDS = 128
 };
-enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2 };
+enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4 };
 
 // the expansion kernels run 8 warps per CTA, one simulated warp per warp
 constexpr int EXP_THREADS = 256;
@@ -175,7 +176,7 @@ constexpr int SBIN_MAX = 4096;
 // mode 3 = count, min / max thread, writer bits, digit histogram, scan scratch;
 // mode 4 = write cursors
 HGRD_HD uint64_t block_body_words(int mode, uint64_t nb) {
-  return mode == 3 ? ((3 * nb + (nb + 31) / 32 + 256 + 1) & ~1ull) + 2 * 9 : nb;
+  return mode == 3 ? ((3 * nb + (nb + 31) / 32 + 256 + 1) & ~1ull) + 2 * 10 : nb;
 }
 
 }  // namespace hgrd

@@ -91,5 +91,14 @@ def test_workspace_scales_with_problem():
     w = workloads.config2(0)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     ws = k.workspace_size()
-    # two 8-byte key buffers for every possible key dominate
-    assert 16 * 536870912 <= ws < 16 * 536870912 * 1.2
+    # two 8-byte key buffers dominate: for the kept keys of the one global
+    # write (the reads of the read-only input race with nothing) plus room for
+    # candidate shared-memory bins, a sixteenth of the kept shared keys
+    out_keys = 64 * 64 * 256 * 32
+    shared_kept = 13 * out_keys
+    keys = out_keys + shared_kept // 16
+    assert 16 * keys <= ws < 16 * keys * 1.3
+    # one global sort of every kept key needs buffers for all of them
+    assert k.workspace_size(flags=hg.NO_SPLIT) >= 16 * (out_keys + shared_kept)
+    # a caller-given room for shared keys sizes the buffers
+    assert k.workspace_size(max_shared_keys=1 << 20) < ws

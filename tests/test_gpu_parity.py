@@ -328,3 +328,21 @@ def test_stencil_sorts_only_the_output_keys():
     st = hg.stats()
     assert st["n_sorted_keys"] == 256 * 256  # one Out write per thread; the In reads race with nothing
     _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+
+
+def test_room_for_shared_keys_reports_and_retries():
+    # every thread of a block writes and reads one of 8 shared cells: 2048 keys
+    # in candidate bins; a smaller room is an HGRD_ENOMEM naming the count,
+    # and the synchronous call retries with it
+    text = "kernel s\narray S shared 1024\naccess W S ; width 4 ; idx tx % 8\naccess R S ; width 4 ; idx tx % 8 ; iv 0\n"
+    b = Binding((4, 1, 1), (256, 1, 1), ())
+    o = oracle.check(text, b, cap=1 << 20)
+    k = hg.Kernel(text).bind(b.grid, b.block, b.params)
+    ws = k.workspace(max_shared_keys=100)
+    k.enqueue(ws, max_shared_keys=100)
+    with pytest.raises(hg.HgrdError) as e:
+        k.collect(ws, cap=1 << 20, max_shared_keys=100)
+    assert "ENOMEM" in str(e.value) and "need 2048" in str(e.value)
+    g = k.check(cap=1 << 20, max_shared_keys=100)
+    assert hg.stats()["shared_bins"] == 1 and hg.stats()["n_binned_keys"] == 2048
+    _same(g, o)
