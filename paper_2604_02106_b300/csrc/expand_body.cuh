@@ -13,6 +13,11 @@
 // instances), over the accesses in `only` and in the set SEL names:
 //   SEL_ALL every access; SEL_KEPT accesses whose keys are written (emask);
 //   SEL_KEPT_GLOBAL those of them on global arrays.
+// step's last argument `mult` (at least 1) says how many identical instances
+// the call stands for: the specialised count pass evaluates an access whose
+// guards, index and interval do not depend on the loop counters once per unit
+// and hands over all the unit's loop vectors at once (the keys, counts and
+// bins are those of mult calls with 1); the other callers always pass 1.
 // The specialised expander fixes SEL's set at compile time, so work only
 // the other accesses need (their ops, guards, indexes) is never emitted.
 // X also provides unit_combine(lane, u, only, step, flush), the same walk for
@@ -69,7 +74,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
     // the write pass expands only the accesses whose keys are kept
     oob += ex.template unit<MODE == 1 ? SEL_KEPT : SEL_ALL>(lane, u, only,
                    [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,
-                       const int32_t* ic) {
+                       const int32_t* ic, uint32_t mult) {
                      const int G = A.G;
                      if (MODE == 2) {
                        if (inb) {
@@ -91,7 +96,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                        return;
                      }
                      if (MODE == 0 && !((emask >> a) & 1u)) {  // counted, never written
-                       if (inb) drop += (uint64_t)G;
+                       if (inb) drop += (uint64_t)G * mult;
                        return;
                      }
                      if (inb) {
@@ -102,11 +107,11 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                            keys[cursor + (uint64_t)rank * G + j] = key;
                          } else {
                            for (int p = 0; p < npass; ++p)
-                             atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], 1u);
+                             atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], mult);
                          }
                        }
                      }
-                     cursor += (uint64_t)__popc(bal) * G;
+                     cursor += (uint64_t)__popc(bal) * G * mult;
                    });
     if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
   }
@@ -196,10 +201,10 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
       uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
       auto step = [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t bb, int lt,
-                         const int32_t*) {
+                         const int32_t*, uint32_t mult) {
                        const int G = A.G;
                        if (MODE == 3 && !((emask >> a) & 1u)) {  // counted, never written
-                         if (inb) drop += (uint64_t)G;
+                         if (inb) drop += (uint64_t)G * mult;
                          return;
                        }
                        if (A.shared) {
@@ -209,7 +214,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                          for (int j = 0; j < G; ++j) {
                            const uint32_t bin = bin0 + (uint32_t)(j * niv);
                            if (MODE == 3) {
-                             atomicAdd(&s_cnt[bin], 1u);
+                             atomicAdd(&s_cnt[bin], mult);
                              atomicMin(&s_mn[bin], (uint32_t)lt);
                              atomicMax(&s_mx[bin], (uint32_t)lt);
                              if ((wmask >> a) & 1u) atomicOr(&s_wb[bin >> 5], 1u << (bin & 31));
@@ -227,10 +232,10 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                            if (MODE == 4)
                              keys_g[cursor + (uint64_t)rank * G + j] = key;
                            else
-                             atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], 1u);
+                             atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], mult);
                          }
                        }
-                       cursor += (uint64_t)__popc(bal) * G;
+                       cursor += (uint64_t)__popc(bal) * G * mult;
                      };
       auto flush = [&](int a, uint32_t bin, uint32_t count, int lt) {
         atomicAdd(&s_cnt[bin], count);

@@ -109,8 +109,94 @@ std::string jit_source(const DProg& P, bool split) {
     const DAcc& A = P.acc[a];
     return !A.dead && A.shared && A.G == 1 && ((P.emask >> a) & 1u);
   };
+  // slots whose value depends on the loop counters (the counters, and ops
+  // reading one, directly or through another op)
+  std::vector<char> dep(MAXSLOT + 16, 0);
+  for (int l = 0; l < nl; l++) dep[6 + l] = 1;
+  auto lin_dep = [&](const DLin& L) {
+    for (int t = 0; t < L.n; t++)
+      if (dep[P.term[L.first + t].slot]) return true;
+    return false;
+  };
+  for (int k = 0; k < P.nfix + P.niter; k++)
+    if (lin_dep(P.ops[k].lin)) dep[P.ops[k].dst] = 1;
+  // an access whose guards, index and interval read no such slot has the same
+  // instances at every loop vector of a unit
+  auto invariant = [&](int a) {
+    const DAcc& A = P.acc[a];
+    if (lin_dep(A.idx) || lin_dep(A.iv)) return false;
+    for (int g = 0; g < A.ng; g++)
+      if (lin_dep(P.guard[A.gfirst + g])) return false;
+    return true;
+  };
+  // one access: per loop vector (once = false), or once per unit standing for
+  // the unit's nrep loop vectors (once = true, count pass only)
+  auto access_code = [&](int a, bool once) {
+    const DAcc& A = P.acc[a];
+    const std::string at = "P->acc[" + S(a) + "]";
+    const std::string ind = once ? "        " : "      ";
+    // in the selected set at compile time (SEL_KEPT: keys written; SEL_KEPT_GLOBAL: and a global array)
+    const bool kept = (P.emask >> a) & 1u;
+    const std::string in_sel = "(SEL == SEL_ALL || (SEL == SEL_KEPT && " + S(kept) + ") || (SEL == SEL_KEPT_GLOBAL && " +
+                               S(kept && !A.shared) + "))";
+    std::string c;
+    c += ind + "if (" + in_sel + " && (only & " + S(1ll << a) + "u)) {  // access " + S(a) +
+         (once ? ", loop-invariant\n" : "\n");
+    c += ind + "  bool live = act;\n";
+    for (int g = 0; g < A.ng; g++)
+      c += ind + "  live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
+    c += ind + "  const T idx = " + lin(P, at + ".idx", A.idx) + ";\n";
+    if (A.bounds_free)
+      c += ind + "  const bool inb = live;\n";
+    else
+      c += ind + "  const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
+    c += ind + "  oob += (live && !inb) ? " + std::string(once ? "nrep" : "1") + " : 0;\n";
+    const std::string iv = "(int64_t)" + lin(P, at + ".iv", A.iv);
+    bool closing = false;
+    if (combinable(a) && once) {
+      c += ind + "  if (inb) flush(" + S(a) + ", (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
+           "(uint64_t)(" + iv + " - P->ivmin)), nrep, lt);\n";
+      c += ind + "}\n";
+      return c;
+    }
+    if (combinable(a)) {
+      c += ind + "  if constexpr (COMBINE) {\n";
+      c += ind + "    if (inb) {\n";
+      c += ind + "      const uint32_t bin = (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
+           "(uint64_t)(" + iv + " - P->ivmin));\n";
+      c += ind + "      if (bin != pb" + S(a) + ") {\n";
+      c += ind + "        if (pc" + S(a) + ") flush(" + S(a) + ", pb" + S(a) + ", pc" + S(a) + ", lt);\n";
+      c += ind + "        pb" + S(a) + " = bin;\n" + ind + "        pc" + S(a) + " = 0;\n" + ind + "      }\n";
+      c += ind + "      ++pc" + S(a) + ";\n" + ind + "    }\n";
+      c += ind + "  } else {\n";
+      closing = true;
+    }
+    c += ind + "  const unsigned bal = __ballot_sync(0xffffffffu, inb);\n";
+    c += ind + "  if (bal) {\n";
+    c += ind + "    int64_t iv = 0;\n";
+    c += ind + "    if (inb) iv = " + iv + ";\n";
+    // the access's structural fields as literals, so the step's granule loop
+    // and its shared / global branch fold away
+    c += ind + "    DAcc A = " + at + ";\n";
+    c += ind + "    A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
+    c += ind + "    step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, ic, " + (once ? "nrep" : "1u") + ");\n";
+    c += ind + "  }\n";
+    if (closing) c += ind + "  }\n";
+    c += ind + "}\n";
+    return c;
+  };
   for (int a = 0; a < P.nacc; a++)
     if (combinable(a)) src += "    uint32_t pb" + S(a) + " = 0xffffffffu, pc" + S(a) + " = 0;\n";
+  // the count pass takes loop-invariant accesses once per unit
+  {
+    std::string once;
+    for (int a = 0; a < P.nacc; a++)
+      if (!P.acc[a].dead && invariant(a)) once += access_code(a, true);
+    if (!once.empty()) {
+      src += "    if constexpr (COMBINE) {\n      const uint32_t nrep = (uint32_t)(it1 - it0);\n";
+      src += "      if (nrep) {\n" + once + "      }\n    }\n";
+    }
+  }
   src += "    for (int64_t it = it0; it < it1; ++it) {\n";
   if (nl > 0) {
     src += "      if (it > it0) {\n";
@@ -125,46 +211,12 @@ std::string jit_source(const DProg& P, bool split) {
   }
   for (int k = P.nfix; k < P.nfix + P.niter; k++) src += op_code(P, k, true);
   for (int a = 0; a < P.nacc; a++) {
-    const DAcc& A = P.acc[a];
-    if (A.dead) continue;
-    const std::string at = "P->acc[" + S(a) + "]";
-    // in the selected set at compile time (SEL_KEPT: keys written; SEL_KEPT_GLOBAL: and a global array)
-    const bool kept = (P.emask >> a) & 1u;
-    const std::string in_sel = "(SEL == SEL_ALL || (SEL == SEL_KEPT && " + S(kept) + ") || (SEL == SEL_KEPT_GLOBAL && " +
-                               S(kept && !A.shared) + "))";
-    src += "      if (" + in_sel + " && (only & " + S(1ll << a) + "u)) {  // access " + S(a) + "\n";
-    src += "        bool live = act;\n";
-    for (int g = 0; g < A.ng; g++)
-      src += "        live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
-    src += "        const T idx = " + lin(P, at + ".idx", A.idx) + ";\n";
-    if (A.bounds_free)
-      src += "        const bool inb = live;\n";
-    else
-      src += "        const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
-    src += "        oob += (live && !inb) ? 1 : 0;\n";
-    if (combinable(a)) {
-      src += "        if constexpr (COMBINE) {\n";
-      src += "          if (inb) {\n";
-      src += "            const uint32_t bin = (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + "
-             "(uint64_t)((int64_t)" + lin(P, at + ".iv", A.iv) + " - P->ivmin));\n";
-      src += "            if (bin != pb" + S(a) + ") {\n";
-      src += "              if (pc" + S(a) + ") flush(" + S(a) + ", pb" + S(a) + ", pc" + S(a) + ", lt);\n";
-      src += "              pb" + S(a) + " = bin;\n              pc" + S(a) + " = 0;\n            }\n";
-      src += "            ++pc" + S(a) + ";\n          }\n";
-      src += "        } else {\n";
+    if (P.acc[a].dead) continue;
+    if (invariant(a)) {
+      src += "      if constexpr (!COMBINE) {\n" + access_code(a, false) + "      }\n";
+    } else {
+      src += access_code(a, false);
     }
-    src += "        const unsigned bal = __ballot_sync(0xffffffffu, inb);\n";
-    src += "        if (bal) {\n";
-    src += "          int64_t iv = 0;\n";
-    src += "          if (inb) iv = (int64_t)" + lin(P, at + ".iv", A.iv) + ";\n";
-    // the access's structural fields as literals, so the step's granule loop
-    // and its shared / global branch fold away
-    src += "          DAcc A = " + at + ";\n";
-    src += "          A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
-    src += "          step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, ic);\n";
-    src += "        }\n";
-    if (combinable(a)) src += "        }\n";
-    src += "      }\n";
   }
   src += "    }\n";
   for (int a = 0; a < P.nacc; a++)

@@ -51,7 +51,9 @@ struct InterpX {
     if (SEL == SEL_KEPT_GLOBAL)
       for (int a = 0; a < P->nacc; ++a)
         if (P->acc[a].shared) only &= ~(1u << a);
-    return expand_unit<T>(P, sl, lane, u, only, step);
+    return expand_unit<T>(P, sl, lane, u, only,
+                          [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b,
+                              int lt, const int32_t* ic) { step(a, A, inb, bal, idx, iv, b, lt, ic, 1u); });
   }
   // the interpreter hands every instance to step
   template <int SEL, class Step, class Flush>

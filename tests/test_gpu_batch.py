@@ -63,10 +63,10 @@ def test_graph_replay_and_tuning_keep_results():
     b = hg.Batch(_kernels(ws), graph=True)
     first = b.check()
     second = b.check()
-    assert first == second
+    assert [i for i in range(len(ws)) if first[i] != second[i]] == [], "graph replay changed items"
     choice = b.tune()
     assert choice["streams"] in (2, 4, 8, 16)
     third = b.check()
-    assert third == first
+    assert [i for i in range(len(ws)) if first[i] != third[i]] == [], f"tuned plan {choice} changed items"
     for w, r in zip(ws, first):
         _same_item(r, oracle.check(w.text, w.binding), b.witness_cap)

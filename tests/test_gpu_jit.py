@@ -78,3 +78,24 @@ def test_jit_compile_reports_time_and_caches():
     k.jit_compile()
     k2 = hg.Kernel(w.text).bind((8, 8, 1), (16, 16, 1), (128, 128, 128))
     assert k2.jit_compile() == 0.0  # same structure: a cache hit
+
+
+@pytest.mark.parametrize("block", [(40, 1, 1), (128, 2, 1)])
+def test_jit_loop_invariant_accesses(block):
+    # accesses whose guards, index and interval ignore the loop counters are
+    # taken once per unit in the count pass (multiplicity = the unit's loop
+    # vectors, chunked when the loops are long): counts, out-of-bounds
+    # instances and bins must be those of the full walk
+    text = ("kernel inv\nloop i 100\nloop j 3\narray s shared 256\narray g global 4096\n"
+            "access W s ; width 4 ; idx tx % 5\n"
+            "access R s ; width 4 ; idx tx + 60 ; iv 1\n"
+            "access W s ; width 4 ; idx tx ; if tx < 3 ; iv 1\n"
+            "access R s ; width 4 ; idx (i + j) % 64 ; iv 1\n"
+            "access W g ; width 4 ; idx tx + 4*j\n")
+    b = Binding((2, 1, 1), block, ())
+    o = oracle.check(text, b, cap=1 << 20)
+    k, r = _jit_check(text, b)
+    assert hg.stats()["shared_bins"] == 1
+    _same(r, o)
+    assert r.n_oob == o.n_oob > 0
+    _same(k.check(cap=1 << 20, flags=hg.JIT | hg.NO_SPLIT), o)
