@@ -151,6 +151,9 @@ typedef struct {
   uint64_t n_binned_keys;   /* shared-array keys written into candidate bins (block-local mode) */
   uint32_t shared_bins;     /* 1 when the shared-array keys were checked in per-block bins */
   uint32_t jit;             /* 1 when the expansion ran specialised kernels (HGRD_JIT) */
+  uint64_t eval_ops;        /* integer operations of evaluating every instance once (guards,
+                               index, bound tests, interval, the ops they read; a term is one
+                               multiply-add, a division by a constant 3, a remainder 5) */
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,

@@ -158,6 +158,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const bool split = HP.smode && !(o && (o->flags & HGRD_NO_SPLIT));
   g_stats = hgrd_stats{};
   g_stats.int64_path = B.wide;
+  g_stats.eval_ops = B.eval_ops;
   g_stats.sort_passes = (uint32_t)(split ? B.sort_passes_split : B.sort_passes);
   g_stats.shared_bins = split ? 1u : 0u;
   // specialised expansion kernels: compiled on request (HGRD_JIT, or

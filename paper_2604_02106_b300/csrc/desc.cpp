@@ -1009,6 +1009,27 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     B.sort_passes = (P.RB + 7) / 8;
     B.sort_passes_split = (P.RBG + 7) / 8;
     B.wide = wide;
+    // integer operations of evaluating every instance once (the count pass's
+    // algorithmic work): a term is one multiply-add, a guard or bound test
+    // one compare, a division by a constant three (multiply-high, shift,
+    // sign), a remainder two more; per thread the ops fixed for the unit, per
+    // thread and loop vector the loop ops, then each live access's guards,
+    // index with its two bound tests, and interval
+    {
+      auto op_cost = [&](const DOp& op) {
+        return (uint64_t)op.lin.n + (op.kind == OP_DIV ? 3u : op.kind == OP_MOD ? 5u : 0u);
+      };
+      uint64_t fixed = 0, per_it = 0;
+      for (int k = 0; k < P.nfix; k++) fixed += op_cost(P.ops[k]);
+      for (int k = P.nfix; k < P.nfix + P.niter; k++) per_it += op_cost(P.ops[k]);
+      for (int a = 0; a < P.nacc; a++) {
+        const DAcc& A = P.acc[a];
+        if (A.dead) continue;
+        per_it += (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n;
+        for (int g = 0; g < A.ng; g++) per_it += (uint64_t)P.guard[A.gfirst + g].n + 1;
+      }
+      B.eval_ops = (uint64_t)nblk * (uint64_t)nthr * (fixed + (uint64_t)nit * per_it);
+    }
     d.bound = std::move(bp);
     return HGRD_OK;
   } catch (const Err& e) {

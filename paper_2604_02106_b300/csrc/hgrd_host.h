@@ -58,6 +58,7 @@ struct Bound {
   // bounds of the keys the global sort sees: written keys of every access
   // (one sort of everything) or of global-array accesses (block-local mode)
   uint64_t nsort_max_all = 0, nsort_max_split = 0;
+  uint64_t eval_ops = 0;  // integer operations of evaluating every instance once
   int sort_passes = 0;        // radix passes over all keys
   int sort_passes_split = 0;  // radix passes over the global-array keys (block-local mode)
   bool wide = false;
