@@ -179,12 +179,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
-  // status words this check's sorts can touch (stale epochs must not survive)
   const uint64_t nsort = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
-  const uint64_t st_tiles = std::max((nsort + RS_MIN_TILE - 1) / RS_MIN_TILE, (W.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   CK(cudaMemsetAsync(cnt, 0, C_WORDS * 8, s));
   CK(cudaMemsetAsync(U(W.hist), 0, MAX_PASSES * 256 * 8, s));
-  CK(cudaMemsetAsync(U(W.status), 0, std::min<uint64_t>(st_tiles * RS_RADIX, W.status_words) * 8, s));
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live
@@ -219,6 +216,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                          U(W.sbase), only_mask, split));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    // look-back status of the tiles the key sort will use: no stale epoch may survive
+    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
                          U(W.stbl), U(W.sbase), only_mask, split));
@@ -228,6 +227,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                            U(W.stbl), U(W.sbase)));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    // look-back status of the tiles the key sort will use: no stale epoch may survive
+    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_expand_block(L, 4, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr,
                            cnt, U(W.stbl), U(W.sbase)));
@@ -237,6 +238,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                      0));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
+    // look-back status of the tiles the key sort will use: no stale epoch may survive
+    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
     g_prof.mark("expand_write");
@@ -268,6 +271,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
   CK(launch_witness_split(L, cnt, W.raw_cap));
   uint64_t* nraw = cnt + C_NRAWBIG;
+  CK(launch_zero_status(L, U(W.status), nraw, W.status_words));
   uint64_t* whist = U(W.hist) + 8 * 256;
   uint64_t* wgb = U(W.gbase) + 8 * 256;
   CK(launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist));

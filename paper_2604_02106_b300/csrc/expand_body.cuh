@@ -20,8 +20,10 @@
 // bins are those of mult calls with 1); the other callers always pass 1.
 // The specialised expander fixes SEL's set at compile time, so work only
 // the other accesses need (their ops, guards, indexes) is never emitted.
-// X also provides unit_combine(lane, u, only, step, flush), the same walk for
-// the block-local count pass, where an expander may hand the instances of a
+// X also provides unit_once(lane, u, only, step), the same walk for a count
+// pass, where an expander may take loop-invariant accesses once per unit
+// with mult > 1, and unit_combine(lane, u, only, step, flush), the same for
+// the block-local count pass, where it may also hand the instances of a
 // shared-array access with one granule per instance to
 //   flush(a, bin, count, lt)
 // instead of step: `count` instances of thread lt on (granule, interval) bin
@@ -72,8 +74,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
   for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
     uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
     // the write pass expands only the accesses whose keys are kept
-    oob += ex.template unit<MODE == 1 ? SEL_KEPT : SEL_ALL>(lane, u, only,
-                   [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,
+    auto step = [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,
                        const int32_t* ic, uint32_t mult) {
                      const int G = A.G;
                      if (MODE == 2) {
@@ -112,7 +113,13 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                        }
                      }
                      cursor += (uint64_t)__popc(bal) * G * mult;
-                   });
+                   };
+    // the count pass may take loop-invariant accesses once per unit; the write
+    // pass expands only the accesses whose keys are kept
+    if (MODE == 0)
+      oob += ex.template unit_once<SEL_ALL>(lane, u, only, step);
+    else
+      oob += ex.template unit<MODE == 1 ? SEL_KEPT : SEL_ALL>(lane, u, only, step);
     if (MODE == 0 && lane == 0) unit_cnt[u] = cursor;
   }
   if (MODE == 0) {
@@ -189,14 +196,16 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     uint64_t sb = 0;
     bool has = true;  // the block has candidate bins
     if (MODE == 4) {
-      int hb = 0;
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        const uint64_t e = stbl[(uint64_t)b * NB + i];
-        s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
-        hb |= (uint32_t)e != 0;
+      const uint64_t base = sbase[b];
+      has = base != NO_ROW;
+      if (has) {
+        for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+          const uint64_t e = stbl[(uint64_t)b * NB + i];
+          s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
+        }
+        sb = n_g + base;
       }
-      sb = n_g + sbase[b];
-      has = __syncthreads_or(hb) != 0;
+      __syncthreads();
     }
     for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
       uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
@@ -267,22 +276,28 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
       uint64_t start = block_excl_scan(csum, ws, ws + 8);
       if (threadIdx.x == 0) {
         const uint64_t tot = ws[8];
-        uint64_t base = tot ? atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot) : 0ull;
-        if (base + tot > P->scap) {  // no room: the check reports it, the block writes nothing
-          atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_SHARED_FULL);
-          base = ~0ull;
+        // base of the block's candidate keys, or NO_ROW: no candidate bin, or no
+        // room (the check then reports it); a block without a row writes no
+        // bin-table row and no shared keys
+        uint64_t base = NO_ROW;
+        if (tot) {
+          base = atomicAdd((unsigned long long*)&counters[C_NSC], (unsigned long long)tot);
+          if (base + tot > P->scap) {
+            atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_SHARED_FULL);
+            base = NO_ROW;
+          }
         }
         sbase[b] = base;
         ws[9] = base;
       }
       __syncthreads();
-      const bool full = ws[9] == ~0ull;
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
-        const uint32_t c = s_cnt[i];
-        const bool cand = !full && ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
-        stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
-        if (cand) start += c;
-      }
+      if (ws[9] != NO_ROW)
+        for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+          const uint32_t c = s_cnt[i];
+          const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
+          stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
+          if (cand) start += c;
+        }
       __syncthreads();
       for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
         s_cnt[i] = 0;

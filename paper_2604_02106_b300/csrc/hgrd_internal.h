@@ -172,6 +172,8 @@ enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4 };
 constexpr int EXP_THREADS = 256;
 // most (shared granule, interval) bins of one block in the block-local mode
 constexpr int SBIN_MAX = 4096;
+// block-local mode: base of a block that has no bin-table row (no candidate bin)
+constexpr uint64_t NO_ROW = ~0ull;
 // 32-bit shared-memory words the block-local expansion needs for nb bins:
 // mode 3 = count, min / max thread, writer bits, digit histogram, scan scratch;
 // mode 4 = write cursors

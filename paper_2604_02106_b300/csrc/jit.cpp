@@ -75,12 +75,15 @@ std::string jit_source(const DProg& P, bool split) {
   src += "struct GenX {\n  const DProg* __restrict__ P;\n";
   src += "  template <int SEL, class Step>\n";
   src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
-  src += "    return walk<SEL, false>(lane, u, only, step, [](int, uint32_t, uint32_t, int) {});\n  }\n";
+  src += "    return walk<SEL, false, false>(lane, u, only, step, [](int, uint32_t, uint32_t, int) {});\n  }\n";
+  src += "  template <int SEL, class Step>\n";
+  src += "  __device__ __forceinline__ uint64_t unit_once(int lane, int64_t u, uint32_t only, Step&& step) {\n";
+  src += "    return walk<SEL, false, true>(lane, u, only, step, [](int, uint32_t, uint32_t, int) {});\n  }\n";
   src += "  template <int SEL, class Step, class Flush>\n";
   src += "  __device__ __forceinline__ uint64_t unit_combine(int lane, int64_t u, uint32_t only, Step&& step, "
          "Flush&& flush) {\n";
-  src += "    return walk<SEL, true>(lane, u, only, step, flush);\n  }\n";
-  src += "  template <int SEL, bool COMBINE, class Step, class Flush>\n";
+  src += "    return walk<SEL, true, true>(lane, u, only, step, flush);\n  }\n";
+  src += "  template <int SEL, bool COMBINE, bool ONCE, class Step, class Flush>\n";
   src += "  __device__ __forceinline__ uint64_t walk(int lane, int64_t u, uint32_t only, Step&& step, Flush&& flush) {\n";
   src += "    const int64_t bw = u / P->nchunk;\n";
   src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
@@ -121,13 +124,23 @@ std::string jit_source(const DProg& P, bool split) {
   for (int k = 0; k < P.nfix + P.niter; k++)
     if (lin_dep(P.ops[k].lin)) dep[P.ops[k].dst] = 1;
   // an access whose guards, index and interval read no such slot has the same
-  // instances at every loop vector of a unit
-  auto invariant = [&](int a) {
+  // instances at every loop vector of a unit; so does, for the count pass,
+  // one whose keys are dropped and whose index is always in bounds, once its
+  // guards read no such slot (it only counts its live instances)
+  auto guards_invariant = [&](int a) {
     const DAcc& A = P.acc[a];
-    if (lin_dep(A.idx) || lin_dep(A.iv)) return false;
     for (int g = 0; g < A.ng; g++)
       if (lin_dep(P.guard[A.gfirst + g])) return false;
     return true;
+  };
+  auto count_only = [&](int a) {
+    const DAcc& A = P.acc[a];
+    return !((P.emask >> a) & 1u) && A.bounds_free && guards_invariant(a);
+  };
+  auto invariant = [&](int a) {
+    const DAcc& A = P.acc[a];
+    if (count_only(a)) return true;
+    return !lin_dep(A.idx) && !lin_dep(A.iv) && guards_invariant(a);
   };
   // one access: per loop vector (once = false), or once per unit standing for
   // the unit's nrep loop vectors (once = true, count pass only)
@@ -145,21 +158,23 @@ std::string jit_source(const DProg& P, bool split) {
     c += ind + "  bool live = act;\n";
     for (int g = 0; g < A.ng; g++)
       c += ind + "  live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
-    c += ind + "  const T idx = " + lin(P, at + ".idx", A.idx) + ";\n";
+    // a count-only access taken once per unit never reads its index or interval
+    const bool no_idx = once && count_only(a) && (lin_dep(A.idx) || lin_dep(A.iv));
+    c += ind + "  const T idx = " + (no_idx ? std::string("0") : lin(P, at + ".idx", A.idx)) + ";\n";
     if (A.bounds_free)
       c += ind + "  const bool inb = live;\n";
     else
       c += ind + "  const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
     c += ind + "  oob += (live && !inb) ? " + std::string(once ? "nrep" : "1") + " : 0;\n";
-    const std::string iv = "(int64_t)" + lin(P, at + ".iv", A.iv);
+    const std::string iv = no_idx ? std::string("(int64_t)0") : "(int64_t)" + lin(P, at + ".iv", A.iv);
     bool closing = false;
     if (combinable(a) && once) {
-      c += ind + "  if (inb) flush(" + S(a) + ", (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
+      c += ind + "  if constexpr (COMBINE) {\n";
+      c += ind + "    if (inb) flush(" + S(a) + ", (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
            "(uint64_t)(" + iv + " - P->ivmin)), nrep, lt);\n";
-      c += ind + "}\n";
-      return c;
-    }
-    if (combinable(a)) {
+      c += ind + "  } else {\n";
+      closing = true;
+    } else if (combinable(a)) {
       c += ind + "  if constexpr (COMBINE) {\n";
       c += ind + "    if (inb) {\n";
       c += ind + "      const uint32_t bin = (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
@@ -187,13 +202,13 @@ std::string jit_source(const DProg& P, bool split) {
   };
   for (int a = 0; a < P.nacc; a++)
     if (combinable(a)) src += "    uint32_t pb" + S(a) + " = 0xffffffffu, pc" + S(a) + " = 0;\n";
-  // the count pass takes loop-invariant accesses once per unit
+  // the count passes take loop-invariant accesses once per unit
   {
     std::string once;
     for (int a = 0; a < P.nacc; a++)
       if (!P.acc[a].dead && invariant(a)) once += access_code(a, true);
     if (!once.empty()) {
-      src += "    if constexpr (COMBINE) {\n      const uint32_t nrep = (uint32_t)(it1 - it0);\n";
+      src += "    if constexpr (ONCE) {\n      const uint32_t nrep = (uint32_t)(it1 - it0);\n";
       src += "      if (nrep) {\n" + once + "      }\n    }\n";
     }
   }
@@ -213,7 +228,7 @@ std::string jit_source(const DProg& P, bool split) {
   for (int a = 0; a < P.nacc; a++) {
     if (P.acc[a].dead) continue;
     if (invariant(a)) {
-      src += "      if constexpr (!COMBINE) {\n" + access_code(a, false) + "      }\n";
+      src += "      if constexpr (!ONCE) {\n" + access_code(a, false) + "      }\n";
     } else {
       src += access_code(a, false);
     }

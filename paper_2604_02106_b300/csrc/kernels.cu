@@ -56,6 +56,10 @@ struct InterpX {
                               int lt, const int32_t* ic) { step(a, A, inb, bal, idx, iv, b, lt, ic, 1u); });
   }
   // the interpreter hands every instance to step
+  template <int SEL, class Step>
+  __device__ __forceinline__ uint64_t unit_once(int lane, int64_t u, uint32_t only, Step&& step) {
+    return unit<SEL>(lane, u, only, step);
+  }
   template <int SEL, class Step, class Flush>
   __device__ __forceinline__ uint64_t unit_combine(int lane, int64_t u, uint32_t only, Step&& step, Flush&&) {
     return unit<SEL>(lane, u, only, step);
@@ -173,26 +177,32 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_block_kernel(
 // global candidates; an entry's start carries SHARED_ENTRY and both ends are
 // relative to the first shared key (the exact scan adds the global key count)
 constexpr uint64_t SHARED_ENTRY = 1ull << 63;
+// A warp per block; blocks without a bin-table row are skipped.
 __global__ void shared_cand_kernel(const uint64_t* __restrict__ stbl, const uint64_t* __restrict__ sbase, int64_t nblk,
                                    int64_t nb, uint64_t* __restrict__ cand, uint64_t cand_cap, uint64_t* counters) {
   const int lane = threadIdx.x & 31;
-  const uint64_t total = (uint64_t)nblk * (uint64_t)nb;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total; i0 += stride) {
-    const uint64_t i = i0 + threadIdx.x;
-    const uint64_t e = i < total ? stbl[i] : 0ull;
-    const bool has = (uint32_t)e != 0;
-    const unsigned m = __ballot_sync(FULL, has);
-    if (!m) continue;
-    uint64_t base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd((unsigned long long*)&counters[C_NCAND], (unsigned long long)__popc(m));
-    base = __shfl_sync(FULL, base, __ffs(m) - 1);
-    if (has) {
-      const uint64_t g = base + __popc(m & lanemask_lt());
-      const uint64_t s = sbase[i / (uint64_t)nb] + (e >> 32);
-      if (g < cand_cap) {
-        cand[2 * g] = SHARED_ENTRY | s;
-        cand[2 * g + 1] = s + (uint32_t)e;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = gw; b < nblk; b += nw) {
+    const uint64_t sb = sbase[b];
+    if (sb == NO_ROW) continue;
+    for (int64_t i0 = 0; i0 < nb; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const uint64_t e = i < nb ? stbl[(uint64_t)b * (uint64_t)nb + (uint64_t)i] : 0ull;
+      const bool has = (uint32_t)e != 0;
+      const unsigned m = __ballot_sync(FULL, has);
+      if (!m) continue;
+      uint64_t base = 0;
+      if (lane == __ffs(m) - 1)
+        base = atomicAdd((unsigned long long*)&counters[C_NCAND], (unsigned long long)__popc(m));
+      base = __shfl_sync(FULL, base, __ffs(m) - 1);
+      if (has) {
+        const uint64_t g = base + __popc(m & lanemask_lt());
+        const uint64_t s = sb + (e >> 32);
+        if (g < cand_cap) {
+          cand[2 * g] = SHARED_ENTRY | s;
+          cand[2 * g + 1] = s + (uint32_t)e;
+        }
       }
     }
   }
@@ -539,10 +549,16 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
   const uint64_t n = X.n;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t nranges = (n + CA_RANGE - 1) / CA_RANGE;
+  // keys per warp: CA_RANGE, less when there are few keys for the warps (a
+  // multiple of the keys one look-ahead step loads)
+  constexpr uint64_t STEP = 32 * CA_AHEAD;
+  const uint64_t want = (n + nw - 1) / nw;
+  const uint64_t range = want >= (uint64_t)CA_RANGE ? (uint64_t)CA_RANGE
+                                                    : (want <= 2 * STEP ? 2 * STEP : (want + STEP - 1) / STEP * STEP);
+  const uint64_t nranges = (n + range - 1) / range;
   for (uint64_t rg = gw; rg < nranges; rg += nw) {
-    X.r0 = rg * CA_RANGE;
-    X.r1 = X.r0 + CA_RANGE;
+    X.r0 = rg * range;
+    X.r1 = X.r0 + range;
     CandCarry c;
     c.prev = X.r0 > 0 ? keys[X.r0 - 1] : 0;
     c.start = 0;
@@ -711,6 +727,14 @@ __global__ void witness_split_kernel(uint64_t* counters, uint64_t raw_cap) {
   uint64_t n = counters[C_NRAW];
   if (n > raw_cap) n = raw_cap;
   counters[C_NRAWBIG] = n > (uint64_t)WSMALL_MAX ? n : 0;
+}
+
+__global__ void zero_status_kernel(uint64_t* __restrict__ status, const uint64_t* n_dev, uint64_t max_words) {
+  const uint64_t n = *n_dev;
+  uint64_t words = (n + RS_MIN_TILE - 1) / RS_MIN_TILE * RS_RADIX;
+  if (words > max_words) words = max_words;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+    status[i] = 0;
 }
 
 __global__ void zero_kernel(uint64_t* __restrict__ p, const uint64_t* n_dev, uint64_t n_max) {
@@ -955,8 +979,7 @@ cudaError_t launch_expand_block(const Launch& L, int mode, bool wide, const DPro
 
 cudaError_t launch_shared_cand(const Launch& L, const DProg& h_prog, const uint64_t* stbl, const uint64_t* sbase,
                                uint64_t* cand, uint64_t cand_cap, uint64_t* counters) {
-  const uint64_t total = (uint64_t)h_prog.nblk * (uint64_t)h_prog.nsbins;
-  const uint64_t blocks = (total + 255) / 256;
+  const uint64_t blocks = ((uint64_t)h_prog.nblk + 7) / 8;  // a warp per block
   const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(blocks, 1), (uint64_t)L.nsm * 8);
   shared_cand_kernel<<<grid, 256, 0, L.s>>>(stbl, sbase, h_prog.nblk, h_prog.nsbins, cand, cand_cap, counters);
   (*L.launches)++;
@@ -989,6 +1012,14 @@ cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t r
 cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
                                  uint64_t raw_cap) {
   witness_small_kernel<<<1, 1024, 0, L.s>>>(raw, uniq, counters, raw_cap);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_status(const Launch& L, uint64_t* status, const uint64_t* n_dev, uint64_t max_words) {
+  uint64_t blocks = (max_words + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
+  zero_status_kernel<<<grid, 256, 0, L.s>>>(status, n_dev, max_words);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -73,6 +73,9 @@ constexpr int WSMALL_MAX = 4096;
 cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap);
 cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
                                  uint64_t raw_cap);
+// zero the look-back status words of the tiles a sort of *n_dev keys uses
+// (at most max_words)
+cudaError_t launch_zero_status(const Launch& L, uint64_t* status, const uint64_t* n_dev, uint64_t max_words);
 // zero the first min(*n_dev, n_max) words of p
 cudaError_t launch_zero(const Launch& L, uint64_t* p, const uint64_t* n_dev, uint64_t n_max);
 

@@ -86,12 +86,17 @@ def test_jit_loop_invariant_accesses(block):
     # taken once per unit in the count pass (multiplicity = the unit's loop
     # vectors, chunked when the loops are long): counts, out-of-bounds
     # instances and bins must be those of the full walk
+    # (reads of the read-only arrays r, q race with nothing: r's index moves
+    # with the loops but stays in bounds, q's leaves them for some vectors)
     text = ("kernel inv\nloop i 100\nloop j 3\narray s shared 256\narray g global 4096\n"
+            "array r global 4096\narray q global 64\n"
             "access W s ; width 4 ; idx tx % 5\n"
             "access R s ; width 4 ; idx tx + 60 ; iv 1\n"
             "access W s ; width 4 ; idx tx ; if tx < 3 ; iv 1\n"
             "access R s ; width 4 ; idx (i + j) % 64 ; iv 1\n"
-            "access W g ; width 4 ; idx tx + 4*j\n")
+            "access W g ; width 4 ; idx tx + 4*j\n"
+            "access R r ; width 4 ; idx (tx + i) % 1000 ; if tx >= 2\n"
+            "access R q ; width 4 ; idx tx + i\n")
     b = Binding((2, 1, 1), block, ())
     o = oracle.check(text, b, cap=1 << 20)
     k, r = _jit_check(text, b)
