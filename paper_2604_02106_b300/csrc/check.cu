@@ -312,6 +312,27 @@ bool key_less(const Inst& a, const Inst& b) {
          std::tie(b.blk, b.thr, b.it[0], b.it[1], b.it[2], b.it[3]);
 }
 
+// Pinned host staging for the readbacks of collect, one per host thread,
+// grown on demand (copies into it are DMA transfers; it is never freed: the
+// process exit reclaims it, after which the CUDA runtime may be gone).
+struct Pinned {
+  char* p = nullptr;
+  size_t n = 0;
+  char* get(size_t need) {
+    if (need <= n) return p;
+    size_t m = std::max<size_t>(need, 1 << 20);
+    void* q = nullptr;
+    if (cudaHostAlloc(&q, m, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    if (p) cudaFreeHost(p);
+    p = (char*)q;
+    n = m;
+    return p;
+  }
+};
+thread_local Pinned g_pin;
+constexpr uint64_t WIT_PREFIX = 4096;   // witnesses fetched with the counters
+constexpr uint64_t PAIR_PREFIX = 1024;  // pair-search records fetched with their count
+
 int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
             hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, bool want_pair) {
   Layout W;
@@ -322,10 +343,17 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const Bound& B = *d->bound;
   const DProg& HP = B.prog;
   char* ws = (char*)d_ws;
-  uint64_t cnt[C_WORDS];
-  CK(cudaMemcpyAsync(cnt, ws + W.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
-  g_stats.d2h_bytes += sizeof(cnt);
+  // counters and a prefix of the merged witnesses in one round trip
+  const uint64_t* duniq = uniq_buffer(d, W, ws);
+  const uint64_t wpre = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(cap, 1), WIT_PREFIX), W.raw_cap);
+  char* stage = g_pin.get(C_WORDS * 8 + wpre * 8);
+  if (!stage) return fail(HGRD_ENOMEM, "pinned host staging buffer");
+  CK(cudaMemcpyAsync(stage, ws + W.counters, C_WORDS * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(stage + C_WORDS * 8, duniq, wpre * 8, cudaMemcpyDeviceToHost, s));
+  g_stats.d2h_bytes += C_WORDS * 8 + wpre * 8;
   CK(cudaStreamSynchronize(s));
+  uint64_t cnt[C_WORDS];
+  memcpy(cnt, stage, sizeof(cnt));
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
   g_stats.n_sorted_keys = cnt[C_NG];
@@ -349,13 +377,16 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   v->racy = v->n_witness > 0;
   for (int k = 0; k < 3; k++)
     for (int a = 0; a < 32; a++) v->pair_kind[k][a] = (uint32_t)(cnt[C_PAIRS + k * 16 + a / 2] >> (32 * (a & 1)));
-  const uint64_t* duniq = uniq_buffer(d, W, ws);
   const uint64_t ncopy = std::min<uint64_t>(std::max<uint64_t>(cap, 1), v->n_witness);
   std::vector<uint64_t> hw(ncopy);
-  if (ncopy) {
-    CK(cudaMemcpyAsync(hw.data(), duniq, ncopy * 8, cudaMemcpyDeviceToHost, s));
-    g_stats.d2h_bytes += ncopy * 8;
+  memcpy(hw.data(), stage + C_WORDS * 8, std::min(ncopy, wpre) * 8);
+  if (ncopy > wpre) {  // the rest of the requested witnesses
+    char* rest = g_pin.get((ncopy - wpre) * 8);
+    if (!rest) return fail(HGRD_ENOMEM, "pinned host staging buffer");
+    CK(cudaMemcpyAsync(rest, duniq + wpre, (ncopy - wpre) * 8, cudaMemcpyDeviceToHost, s));
+    g_stats.d2h_bytes += (ncopy - wpre) * 8;
     CK(cudaStreamSynchronize(s));
+    memcpy(hw.data() + wpre, rest, (ncopy - wpre) * 8);
   }
   auto unpack = [&](uint64_t w) {
     hgrd_witness x{};
@@ -376,8 +407,7 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     // minimal witness's granule, then take the smallest racing (x, y)
     Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
     PairRec* pr = (PairRec*)(ws + W.pairs);
-    uint64_t zero = 0;
-    CK(cudaMemcpyAsync(ws + W.counters + 8 * C_NPAIR, &zero, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ws + W.counters + 8 * C_NPAIR, 0, 8, s));
     // the specialised kernels when this binding has them (either module holds the search)
     const bool jsplit = jit_ready(B, true), jplain = !jsplit && jit_ready(B, false);
     if ((jsplit || jplain) && !(o && (o->flags & HGRD_NO_JIT)))
@@ -386,17 +416,26 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     else
       CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, nullptr, nullptr, nullptr, 0,
                        (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
-    uint64_t np = 0;
-    CK(cudaMemcpyAsync(&np, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
-    g_stats.h2d_bytes += 8;
-    g_stats.d2h_bytes += 8;
+    // the record count and a prefix of the records in one round trip
+    const uint64_t ppre = std::min<uint64_t>(PAIR_PREFIX, W.pair_cap);
+    char* pst = g_pin.get(16 + ppre * sizeof(PairRec));
+    if (!pst) return fail(HGRD_ENOMEM, "pinned host staging buffer");
+    CK(cudaMemcpyAsync(pst, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pst + 16, pr, ppre * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+    g_stats.d2h_bytes += 8 + ppre * sizeof(PairRec);
     CK(cudaStreamSynchronize(s));
+    uint64_t np = 0;
+    memcpy(&np, pst, 8);
     if (np <= W.pair_cap) {
       std::vector<PairRec> recs(np);
-      if (np) {
-        CK(cudaMemcpyAsync(recs.data(), pr, np * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
-        g_stats.d2h_bytes += np * sizeof(PairRec);
+      memcpy(recs.data(), pst + 16, std::min(np, ppre) * sizeof(PairRec));
+      if (np > ppre) {
+        char* rest = g_pin.get((np - ppre) * sizeof(PairRec));
+        if (!rest) return fail(HGRD_ENOMEM, "pinned host staging buffer");
+        CK(cudaMemcpyAsync(rest, pr + ppre, (np - ppre) * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+        g_stats.d2h_bytes += (np - ppre) * sizeof(PairRec);
         CK(cudaStreamSynchronize(s));
+        memcpy(recs.data() + ppre, rest, (np - ppre) * sizeof(PairRec));
       }
       std::vector<Inst> X, Y;
       for (auto& r : recs) {

@@ -114,9 +114,13 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                      }
                      cursor += (uint64_t)__popc(bal) * G * mult;
                    };
-    // the count pass may take loop-invariant accesses once per unit; the write
-    // pass expands only the accesses whose keys are kept
-    if (MODE == 0)
+    // the count pass may take loop-invariant accesses once per unit, and so
+    // may the pair search (an access whose instances ignore the loop vector
+    // is recorded at the unit's first loop vector only: a thread's later
+    // instances of it have larger keys and race with the same instances, so
+    // the smallest racing pair is among the recorded ones); the write pass
+    // expands only the accesses whose keys are kept
+    if (MODE == 0 || MODE == 2)
       oob += ex.template unit_once<SEL_ALL>(lane, u, only, step);
     else
       oob += ex.template unit<MODE == 1 ? SEL_KEPT : SEL_ALL>(lane, u, only, step);
