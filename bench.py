@@ -195,38 +195,56 @@ def run_suite(args):
     e1.record(s)
     e1.synchronize()
     plain_ms = e0.elapsed_time(e1) / args.steps
-    # batched: tuned, captured into one CUDA graph, replayed
-    b = hg.Batch(ks, graph=True)
-    choice = b.tune(stream=s)
-    res_b = b.check(stream=s)
-    for rp, rb in zip(res_plain, res_b):
-        assert rb.status == 0 and rb.n_witness == rp.n_witness and rb.n_by_kind == rp.n_by_kind
-        assert rb.witnesses == rp.witnesses[:len(rb.witnesses)]
-    for _ in range(max(3, args.warmup)):
-        b.run(stream=s)
-    torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
-        e0.record(s)
-        for _ in range(args.steps):
+    # batched: tuned, captured into one CUDA graph, replayed; with the large
+    # items on interpreted or on specialised expansion kernels
+    def timed_batch(jit):
+        t_c = time.perf_counter()
+        b = hg.Batch(ks, graph=True, jit=jit)
+        compile_ms = 1000 * (time.perf_counter() - t_c)
+        choice = b.tune(stream=s)
+        res_b = b.check(stream=s)
+        for rp, rb in zip(res_plain, res_b):
+            assert rb.status == 0 and rb.n_witness == rp.n_witness and rb.n_by_kind == rp.n_by_kind
+            assert rb.witnesses == rp.witnesses[:len(rb.witnesses)]
+        for _ in range(max(3, args.warmup)):
             b.run(stream=s)
-        e1.record(s)
-        e1.synchronize()
-    batch_ms = e0.elapsed_time(e1) / args.steps
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        b.check(stream=s)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    line = {"metric": METRIC, "value": n_inst / (batch_ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            e0.record(s)
+            for _ in range(args.steps):
+                b.run(stream=s)
+            e1.record(s)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        t_w = time.perf_counter()
+        while time.perf_counter() - t_w < 1.0:  # clocks back at steady state after the sampler's idle gap
+            b.check(stream=s)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.check(stream=s)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        return {"ms": ms, "choice": choice, "res": res_b, "e2e_s": e2e_s, "clk": clk.summary(),
+                "create_ms": compile_ms}
+    interp = timed_batch(False)
+    spec = timed_batch(True)
+    best = spec if spec["ms"] < interp["ms"] else interp
+    res_b = best["res"]
+    line = {"metric": METRIC, "value": n_inst / (best["ms"] / 1000), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": name, "items": len(ks), "instances": n_inst,
                        "racy_items": sum(r.racy for r in res_b), "small_items": sum(r.small for r in res_b),
-                       "tuned": choice, "form": "batched, CUDA graph"},
+                       "tuned": best["choice"],
+                       "form": "batched, CUDA graph, " + ("specialised" if best is spec else "interpreted") +
+                               " expansion for large items"},
             "plain": {"value": n_inst / (plain_ms / 1000), "ms_per_step": plain_ms,
-                      "form": "hgrd_check_enqueue per item, one stream"},
-            "batched_over_plain": plain_ms / batch_ms,
-            "e2e": {"value": n_inst / e2e_s, "unit": UNIT, "ms_per_step": 1000 * e2e_s},
-            "clocks": clk.summary()}
+                      "form": "hgrd_check_enqueue per item, one stream, interpreted"},
+            "batched_interpreted": {"value": n_inst / (interp["ms"] / 1000), "ms_per_step": interp["ms"]},
+            "batched_specialised": {"value": n_inst / (spec["ms"] / 1000), "ms_per_step": spec["ms"],
+                                    "create_and_compile_ms": spec["create_ms"]},
+            "batched_over_plain": plain_ms / best["ms"],
+            "e2e": {"value": n_inst / best["e2e_s"], "unit": UNIT, "ms_per_step": 1000 * best["e2e_s"]},
+            "clocks": best["clk"]}
     print(json.dumps(line), flush=True)
 
 

@@ -224,9 +224,12 @@ typedef struct {
   uint32_t streams;     /* streams: one for the on-chip kernel plus large-item streams (0 = 4, 2..16) */
   uint32_t witness_cap; /* canonical witnesses kept per item (0 = 64) */
   uint32_t flags;       /* HGRD_BATCH_GRAPH: capture the whole batch into a CUDA graph on the first
-                           run and replay it on later runs with the same workspace and stream */
+                           run and replay it on later runs with the same workspace and stream;
+                           HGRD_BATCH_JIT: at creation, compile specialised expansion kernels
+                           (hgrd_jit_compile) for the items too large for the on-chip kernel,
+                           once per program structure (a sweep of one kernel shares one) */
 } hgrd_batch_opts;
-enum { HGRD_BATCH_GRAPH = 1 };
+enum { HGRD_BATCH_GRAPH = 1, HGRD_BATCH_JIT = 2 };
 typedef struct {
   int32_t status;   /* HGRD_OK, or HGRD_ENOMEM (a witness buffer overflowed: rerun with hgrd_check) */
   int32_t racy, small, n_copied;

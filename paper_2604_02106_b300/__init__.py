@@ -32,6 +32,7 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
            "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source"]
 BATCH_GRAPH = 1
+BATCH_JIT = 2
 
 
 class HgrdError(RuntimeError):
@@ -346,10 +347,10 @@ class ItemResult:
 class Batch:
     """Many bound kernels checked together (hgrd_batch_*).  Keeps its kernels alive."""
 
-    def __init__(self, kernels, small_keys=0, streams=0, witness_cap=64, graph=False):
+    def __init__(self, kernels, small_keys=0, streams=0, witness_cap=64, graph=False, jit=False):
         self.kernels = list(kernels)
         arr = (C.c_void_p * len(self.kernels))(*[k._h.value for k in self.kernels])
-        o = BatchOpts(small_keys, streams, witness_cap, BATCH_GRAPH if graph else 0)
+        o = BatchOpts(small_keys, streams, witness_cap, (BATCH_GRAPH if graph else 0) | (BATCH_JIT if jit else 0))
         h = C.c_void_p()
         _raise(lib().hgrd_batch_create(arr, len(self.kernels), C.byref(o), C.byref(h)))
         self._h = h

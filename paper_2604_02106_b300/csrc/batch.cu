@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "hgrd_host.h"
+#include "jit.h"
 #include "kcommon.cuh"
 
 namespace hgrd {
@@ -497,6 +498,14 @@ int hgrd_batch_create(const hgrd_desc* const* items, uint32_t n, const hgrd_batc
       cudaMallocHost((void**)&b->h_order, n * sizeof(uint32_t)) != cudaSuccess)
     return fail(HGRD_EDEVICE, "pinned host allocation failed");
   for (uint32_t i = 0; i < n; i++) b->h_progs[i] = items[i]->bound->prog;
+  // specialised kernels for the items that always run the device-wide pipeline
+  if (b->opts.flags & HGRD_BATCH_JIT)
+    for (uint32_t i = 0; i < n; i++) {
+      const Bound& Bi = *items[i]->bound;
+      if (small_ok(Bi, SB_KEYS)) continue;
+      const int rc = jit_prepare(Bi, Bi.prog.smode != 0, nullptr);
+      if (rc) return rc;
+    }
   b->streams.resize(MAX_STREAMS);
   b->join.resize(MAX_STREAMS);
   for (uint32_t j = 0; j < MAX_STREAMS; j++) {

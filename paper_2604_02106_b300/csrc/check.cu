@@ -47,7 +47,7 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   // the written keys, and the instances on one granule never exceed the keys
   L.raw_cap = (o && o->max_raw_witness)
                   ? o->max_raw_witness
-                  : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 12, 2 * L.key_words));
+                  : std::min<uint64_t>(1ull << 24, std::max<uint64_t>(1ull << 12, 2 * L.key_words));
   L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
   const uint64_t scan_n = std::max(nunits, L.raw_cap);

@@ -52,6 +52,16 @@ def test_sweep_batch_matches_oracle():
     _check_batch(ws, witness_cap=256)
 
 
+def test_batch_with_specialised_kernels_matches_oracle():
+    # large items on specialised expansion kernels (compiled at creation, one
+    # module per program structure), in a replayed CUDA graph
+    ws = workloads.config3()[:15] + [workloads.config4(i, hi_exp=4.6) for i in range(150, 190)]
+    b, res = _check_batch(ws, witness_cap=256, jit=True, graph=True)
+    assert any(not r.small for r in res)
+    again = b.check()
+    assert [i for i in range(len(ws)) if res[i] != again[i]] == []
+
+
 def test_all_large_and_all_small_classes():
     ws = [workloads.config4(i, hi_exp=3.6) for i in range(200, 260)] + [workloads.config1(0)]
     _check_batch(ws, small_keys=1)      # everything through the device-wide path
