@@ -126,8 +126,9 @@ typedef struct {
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
   uint32_t max_shared_keys; /* block-local mode: room for keys of shared-memory bins that can
-                               race (a writer and two threads); 0 = a sixteenth of the shared
-                               keys, at least 2^20.  HGRD_ENOMEM names the count when short */
+                               race (a writer and two threads); 0 = all kept shared keys up to
+                               2^24, a sixteenth of them beyond.  HGRD_ENOMEM names the count
+                               when short */
 } hgrd_check_opts;
 enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4, HGRD_NO_SPLIT = 8, HGRD_JIT = 16, HGRD_NO_JIT = 32 };
 

@@ -970,11 +970,11 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (!P.acc[a].shared) B.nsort_max_split += k;
       else nshared_kept += k;
     }
-    // default room for keys of candidate shared bins: a sixteenth of the
-    // shared keys (at least 2^20, at most all of them, below 2^32); a check
-    // that needs more reports HGRD_ENOMEM with the count
+    // default room for keys of candidate shared bins: all kept shared keys up
+    // to 2^24, a sixteenth of them beyond (below 2^32); a check that needs
+    // more reports HGRD_ENOMEM with the count
     P.scap = std::min<uint64_t>(std::min<uint64_t>(nshared_kept, 0xffffffffull),
-                                std::max<uint64_t>(1ull << 20, nshared_kept / 16));
+                                std::max<uint64_t>(1ull << 24, nshared_kept / 16));
     // Block-local mode: shared-memory runs never leave their block and a
     // shared-memory race needs two threads of one block in one interval
     // (Table 2), so shared keys can be counted per (granule, interval) bin of

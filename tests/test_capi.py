@@ -93,7 +93,7 @@ def test_workspace_scales_with_problem():
     ws = k.workspace_size()
     # two 8-byte key buffers dominate: for the kept keys of the one global
     # write (the reads of the read-only input race with nothing) plus room for
-    # candidate shared-memory bins, a sixteenth of the kept shared keys
+    # candidate shared-memory bins, a sixteenth of the kept shared keys (above 2^24)
     out_keys = 64 * 64 * 256 * 32
     shared_kept = 13 * out_keys
     keys = out_keys + shared_kept // 16
