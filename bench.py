@@ -227,21 +227,26 @@ def run_suite(args):
                 "create_ms": compile_ms}
     interp = timed_batch(False)
     spec = timed_batch(True)
-    best = spec if spec["ms"] < interp["ms"] else interp
+    # the headline is the interpreted batch: checking each binding once, the
+    # specialised kernels' compile time (one module per program structure) is
+    # not paid back; they are reported beside it with the passes to break even
+    best = interp
     res_b = best["res"]
+    gain = interp["ms"] - spec["ms"]
     line = {"metric": METRIC, "value": n_inst / (best["ms"] / 1000), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": name, "items": len(ks), "instances": n_inst,
                        "racy_items": sum(r.racy for r in res_b), "small_items": sum(r.small for r in res_b),
                        "tuned": best["choice"],
-                       "form": "batched, CUDA graph, " + ("specialised" if best is spec else "interpreted") +
-                               " expansion for large items"},
+                       "form": "batched, CUDA graph, interpreted expansion"},
             "plain": {"value": n_inst / (plain_ms / 1000), "ms_per_step": plain_ms,
                       "form": "hgrd_check_enqueue per item, one stream, interpreted"},
             "batched_interpreted": {"value": n_inst / (interp["ms"] / 1000), "ms_per_step": interp["ms"]},
             "batched_specialised": {"value": n_inst / (spec["ms"] / 1000), "ms_per_step": spec["ms"],
-                                    "create_and_compile_ms": spec["create_ms"]},
+                                    "create_and_compile_ms": spec["create_ms"],
+                                    "passes_to_break_even": (spec["create_ms"] - interp["create_ms"]) / gain
+                                    if gain > 0 else None},
             "batched_over_plain": plain_ms / best["ms"],
             "e2e": {"value": n_inst / best["e2e_s"], "unit": UNIT, "ms_per_step": 1000 * best["e2e_s"]},
             "clocks": best["clk"]}

@@ -121,7 +121,10 @@ typedef struct {
                                HGRD_JIT / HGRD_NO_JIT: always / never expand with kernels
                                specialised to the program's structure, compiled at run time
                                (default: when hgrd_jit_compile or an HGRD_JIT check already
-                               compiled them for this binding); same result */
+                               compiled them for this binding); same result;
+                               HGRD_NO_SMALL: never run a small binding (at most 4096 keys, 1024
+                               simulated warps) whole in one CTA; by default it does, and falls
+                               back to the device-wide pipeline when it keeps too few witnesses */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
@@ -130,7 +133,15 @@ typedef struct {
                                2^24, a sixteenth of them beyond.  HGRD_ENOMEM names the count
                                when short */
 } hgrd_check_opts;
-enum { HGRD_NO_PAIR = 1, HGRD_PROFILE = 2, HGRD_STOP_FIRST = 4, HGRD_NO_SPLIT = 8, HGRD_JIT = 16, HGRD_NO_JIT = 32 };
+enum {
+  HGRD_NO_PAIR = 1,
+  HGRD_PROFILE = 2,
+  HGRD_STOP_FIRST = 4,
+  HGRD_NO_SPLIT = 8,
+  HGRD_JIT = 16,
+  HGRD_NO_JIT = 32,
+  HGRD_NO_SMALL = 64
+};
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
  * stream around the stage's kernels. */
@@ -155,6 +166,8 @@ typedef struct {
   uint64_t eval_ops;        /* integer operations of evaluating every instance once (guards,
                                index, bound tests, interval, the ops they read; a term is one
                                multiply-add, a division by a constant 3, a remainder 5) */
+  uint32_t small;           /* 1 when the check ran whole in one CTA */
+  uint32_t reserved2;
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,

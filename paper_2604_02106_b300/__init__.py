@@ -22,6 +22,7 @@ STOP_FIRST = 4
 NO_SPLIT = 8
 JIT = 16
 NO_JIT = 32
+NO_SMALL = 64
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -99,7 +100,8 @@ class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("n_candidates", C.c_uint64), ("n_raw_witness", C.c_uint64),
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
-                ("shared_bins", C.c_uint32), ("jit", C.c_uint32), ("eval_ops", C.c_uint64)]
+                ("shared_bins", C.c_uint32), ("jit", C.c_uint32), ("eval_ops", C.c_uint64),
+                ("small", C.c_uint32), ("reserved2", C.c_uint32)]
 
 
 _lib = None

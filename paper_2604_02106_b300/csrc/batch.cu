@@ -361,7 +361,44 @@ bool small_ok(const Bound& B, uint32_t limit) {
          P.RB <= 8 * SB_PASSES && P.nslot <= SB_SLOTS;
 }
 
+// The one-CTA verdict of a single small check, written where the device-wide
+// pipeline leaves its results: the counters and the merged-witness buffer.
+__global__ void small_finish_kernel(const uint64_t* __restrict__ out, const uint64_t* __restrict__ wits,
+                                    uint32_t wcap, uint64_t* __restrict__ counters, uint64_t* __restrict__ uniq) {
+  if (threadIdx.x == 0) {
+    counters[C_NKEYS] = out[0];
+    counters[C_NOOB] = out[1];
+    counters[C_NUNIQ] = out[2];
+    counters[C_KIND0] = out[3];
+    counters[C_KIND1] = out[4];
+    counters[C_KIND2] = out[5];
+    counters[C_NRAW] = out[7];
+    if (out[6] & F_RAW_OVERFLOW) counters[C_ERR] |= ERR_SMALL_FULL;
+  }
+  if (threadIdx.x < 48) counters[C_PAIRS + threadIdx.x] = out[8 + threadIdx.x];
+  const uint64_t n = out[2] < wcap ? out[2] : wcap;
+  for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) uniq[i] = wits[i];
+}
+
 }  // namespace
+
+bool small_single_ok(const Bound& B) { return small_ok(B, SB_KEYS); }
+
+cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* counters, uint64_t* scratch,
+                                uint64_t* uniq) {
+  const size_t smem = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute((const void*)batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  uint64_t* out = scratch;
+  uint64_t* wits = scratch + 64;
+  batch_small_kernel<<<1, SB_THREADS, smem, L.s>>>(d_prog, (const uint32_t*)(counters + C_SMALLQ + 1), 1,
+                                                  (unsigned long long*)(counters + C_SMALLQ), out, wits, SB_RAW);
+  small_finish_kernel<<<1, 256, 0, L.s>>>(out, wits, SB_RAW, counters, uniq);
+  (*L.launches) += 2;
+  return cudaGetLastError();
+}
+
 }  // namespace hgrd
 
 using namespace hgrd;

@@ -16,6 +16,13 @@
 #include "kernels.cuh"
 
 namespace hgrd {
+// the batch's on-chip kernel for one small check (batch.cu)
+bool small_single_ok(const Bound& B);
+cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* counters, uint64_t* scratch,
+                                uint64_t* uniq);
+}  // namespace hgrd
+
+namespace hgrd {
 
 namespace {
 
@@ -138,6 +145,13 @@ int prechecks(const hgrd_desc* d, void* d_ws, size_t ws_bytes, const hgrd_check_
   return HGRD_OK;
 }
 
+// the buffer holding the merged witnesses after enqueue
+uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
+  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
+  (void)d;
+  return (uint64_t*)(ws + ((WP % 2 == 0) ? W.raw2 : W.raw));
+}
+
 int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
             const DProg* dprog_resident = nullptr) {
   Layout W;
@@ -202,6 +216,18 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     g_stats.h2d_bytes += sizeof(DProg);
   }
   g_prof.mark("setup");
+  // a small check runs whole in one CTA (the batched form's on-chip kernel),
+  // unless specialised kernels were asked for; its verdict lands in the
+  // counters and merged-witness buffer as usual
+  if (!(fl & (HGRD_NO_SMALL | HGRD_JIT)) && !dprog_resident && small_single_ok(B)) {
+    CK(launch_small_single(L, dprog, cnt, U(W.raw2), uniq_buffer(d, W, ws)));
+    g_prof.mark("small");
+    g_stats.small = 1;
+    g_stats.shared_bins = 0;
+    g_stats.jit = 0;
+    g_stats.sort_passes = 0;
+    return HGRD_OK;
+  }
 
   const int P = split ? B.sort_passes_split : B.sort_passes;
   uint64_t* keysA = U(W.keysA);
@@ -294,13 +320,6 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   return HGRD_OK;
 }
 
-// the buffer holding the merged witnesses after enqueue
-uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
-  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
-  (void)d;
-  return (uint64_t*)(ws + ((WP % 2 == 0) ? W.raw2 : W.raw));
-}
-
 struct Inst {
   uint32_t blk, thr;
   uint32_t it[4];
@@ -354,6 +373,14 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(cudaStreamSynchronize(s));
   uint64_t cnt[C_WORDS];
   memcpy(cnt, stage, sizeof(cnt));
+  if (cnt[C_ERR] & ERR_SMALL_FULL) {
+    // more per-run witnesses than the one-CTA path keeps: run the device-wide pipeline
+    hgrd_check_opts o2 = o ? *o : hgrd_check_opts{};
+    o2.flags |= HGRD_NO_SMALL;
+    const int r2 = enqueue(d, &o2, d_ws, ws_bytes, s);
+    if (r2) return r2;
+    return collect(d, &o2, d_ws, ws_bytes, s, host_out, cap, v, want_pair);
+  }
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
   g_stats.n_sorted_keys = cnt[C_NG];
@@ -595,7 +622,7 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   if (o) oo = *o;
   oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
   oo.flags &= ~(uint32_t)HGRD_JIT;      // loading a compiled module takes device memory
-  oo.flags |= HGRD_NO_JIT;
+  oo.flags |= HGRD_NO_JIT | HGRD_NO_SMALL;
   const Layout W = layout(*d->bound, &oo);
   if (W.total > NOALLOC_BYTES)
     return fail(HGRD_ENOMEM, "hgrd_check_noalloc: this binding needs " + std::to_string(W.total) +

@@ -164,9 +164,10 @@ enum {
   C_NRAWBIG,  // raw witnesses left to the device-wide merge (0 when one CTA merges them)
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
+  C_SMALLQ = 120,  // one-CTA path of a small check: work queue, then an order word of zero
   C_WORDS = 128
 };
-enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4 };
+enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4, ERR_SMALL_FULL = 8 };
 
 // the expansion kernels run 8 warps per CTA, one simulated warp per warp
 constexpr int EXP_THREADS = 256;

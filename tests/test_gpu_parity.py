@@ -42,7 +42,13 @@ def oracle_pairs(o):
 
 
 def _both(text, binding, cap=1 << 20, **kw):
+    # a small binding runs whole in one CTA by default; the device-wide
+    # pipeline (NO_SMALL) must give the same result
     g = hg.check(text, binding, cap=cap, **kw)
+    flags = kw.pop("flags", 0)
+    g2 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL, **kw)
+    assert hg.stats()["small"] == 0
+    assert g2 == g
     o = oracle.check(text, binding, cap=cap)
     return g, o
 
@@ -212,14 +218,15 @@ def test_restricted_and_stop_first(seed):
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     nacc = w.meta["n_access"]
     mask = 0b101 & ((1 << nacc) - 1) or 1
-    r = k.check(cap=1 << 20, only_accesses=mask)
     want = [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
-    assert r.witnesses == want
-    f = k.check(cap=1 << 20, flags=hg.STOP_FIRST)
-    assert f.racy == o.racy
     full = {x[:5]: x[5] for x in o.witnesses}
-    for x in f.witnesses:
-        assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
+    for extra in (0, hg.NO_SMALL):
+        r = k.check(cap=1 << 20, only_accesses=mask, flags=extra)
+        assert r.witnesses == want
+        f = k.check(cap=1 << 20, flags=hg.STOP_FIRST | extra)
+        assert f.racy == o.racy
+        for x in f.witnesses:
+            assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
 
 
 @pytest.mark.parametrize("bounds", [(300,), (7, 130), (3, 5, 7, 11)])
@@ -260,12 +267,13 @@ def test_shared_bins_against_oracle(seed):
     w = workloads.random_shared(5000 + seed)
     o = oracle.check(w.text, w.binding, cap=1 << 20)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
-    g = k.check(cap=1 << 20)
+    g = k.check(cap=1 << 20, flags=hg.NO_SMALL)
     st = hg.stats()
     _same(g, o)
+    _same(k.check(cap=1 << 20), o)
     if st["shared_bins"]:
         assert st["n_sorted_keys"] + st["n_binned_keys"] <= g.n_keys
-    n = k.check(cap=1 << 20, flags=hg.NO_SPLIT)
+    n = k.check(cap=1 << 20, flags=hg.NO_SPLIT | hg.NO_SMALL)
     assert hg.stats()["shared_bins"] == 0 and hg.stats()["n_sorted_keys"] <= n.n_keys
     _same(n, o)
 
@@ -274,7 +282,7 @@ def test_shared_bins_are_used():
     used = 0
     for seed in range(48):
         w = workloads.random_shared(5000 + seed)
-        hg.check(w.text, w.binding, cap=16)
+        hg.check(w.text, w.binding, cap=16, flags=hg.NO_SMALL)
         used += hg.stats()["shared_bins"]
     assert used >= 12
 
@@ -285,13 +293,14 @@ def test_shared_bins_restricted_and_stop_first(seed):
     o = oracle.check(w.text, w.binding)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     mask = 0b1011 & ((1 << w.meta["n_access"]) - 1)
-    r = k.check(cap=1 << 20, only_accesses=mask)
-    assert r.witnesses == [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
-    f = k.check(cap=1 << 20, flags=hg.STOP_FIRST)
-    assert f.racy == o.racy
-    full = {x[:5]: x[5] for x in o.witnesses}
-    for x in f.witnesses:
-        assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
+    for extra in (0, hg.NO_SMALL):
+        r = k.check(cap=1 << 20, only_accesses=mask, flags=extra)
+        assert r.witnesses == [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
+        f = k.check(cap=1 << 20, flags=hg.STOP_FIRST | extra)
+        assert f.racy == o.racy
+        full = {x[:5]: x[5] for x in o.witnesses}
+        for x in f.witnesses:
+            assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
 
 
 def test_stencil_bins_skip_the_sort():
@@ -315,7 +324,7 @@ def test_keys_of_accesses_without_partners_are_counted_not_sorted():
             "access A c ; width 4 ; idx 0 ; scope device\naccess A c ; width 4 ; idx 1 ; scope device\n"
             "access W w ; width 4 ; idx tx / 2\n")
     b = Binding((4, 1, 1), (64, 1, 1), ())
-    for flags in (0, hg.JIT):
+    for flags in (hg.NO_SMALL, hg.JIT | hg.NO_SMALL):
         g = hg.check(text, b, cap=1 << 20, flags=flags)
         _same(g, oracle.check(text, b, cap=1 << 20))
         assert hg.stats()["n_sorted_keys"] == 4 * 64
@@ -339,10 +348,31 @@ def test_room_for_shared_keys_reports_and_retries():
     o = oracle.check(text, b, cap=1 << 20)
     k = hg.Kernel(text).bind(b.grid, b.block, b.params)
     ws = k.workspace(max_shared_keys=100)
-    k.enqueue(ws, max_shared_keys=100)
+    k.enqueue(ws, max_shared_keys=100, flags=hg.NO_SMALL)
     with pytest.raises(hg.HgrdError) as e:
-        k.collect(ws, cap=1 << 20, max_shared_keys=100)
+        k.collect(ws, cap=1 << 20, max_shared_keys=100, flags=hg.NO_SMALL)
     assert "ENOMEM" in str(e.value) and "need 2048" in str(e.value)
-    g = k.check(cap=1 << 20, max_shared_keys=100)
+    g = k.check(cap=1 << 20, max_shared_keys=100, flags=hg.NO_SMALL)
     assert hg.stats()["shared_bins"] == 1 and hg.stats()["n_binned_keys"] == 2048
     _same(g, o)
+
+
+# ---------------------------------------------------------------- one-CTA path of small checks
+
+@pytest.mark.parametrize("seed", range(4))
+def test_small_checks_run_in_one_cta(seed):
+    # at most 4096 keys: one CTA (two launches), plus the pair search when racy
+    w = workloads.random_tiny(1000 + seed, max_instances=500)
+    g = hg.check(w.text, w.binding, cap=1 << 20)
+    assert hg.stats()["small"] == 1 and hg.stats()["kernel_launches"] <= 3
+    _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+
+
+def test_small_check_falls_back_when_it_keeps_too_few_witnesses():
+    # 512 runs of two writers and two accesses: 1536 per-run witnesses, more
+    # than the one-CTA path keeps; the device-wide pipeline takes over
+    text = "kernel f\narray a global 4096\naccess W a ; width 4 ; idx tx / 2\naccess W a ; width 4 ; idx tx / 2\n"
+    b = Binding((1, 1, 1), (1024, 1, 1), ())
+    g = hg.check(text, b, cap=1 << 20)
+    assert hg.stats()["small"] == 0
+    _same(g, oracle.check(text, b, cap=1 << 20))
