@@ -253,6 +253,40 @@ def run_suite(args):
     print(json.dumps(line), flush=True)
 
 
+def run_symbolic(args):
+    """Symbolic-parameter mode: is the strided kernel racy under some admissible
+    (N, STRIDE)?  N from host-loop values, STRIDE from the range its asserts
+    admit (open above: 1..64); the grid follows N."""
+    import torch
+    import workloads
+    from paper_2604_02106_b300 import sweep
+
+    torch.cuda.set_device(0)
+    text = workloads.config3_kernel_text()
+    launch = lambda p: ((-(-p["N"] // 256), 1, 1), (256, 1, 1))
+    values = {"N": [1 << e for e in range(10, 21)]}
+    kw = dict(values=values, free=(1, 64), per_param=8)
+    r = sweep.symbolic_check(text, launch, **kw)  # warm-up (and the verdict)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        r = sweep.symbolic_check(text, launch, **kw)
+        t.append(time.perf_counter() - t0)
+    s = sum(t) / len(t)
+    line = {"metric": METRIC, "value": r.instances / s, "unit": UNIT, "n_gpus": 1, "steps": len(t),
+            "warmup": 1, "ms_per_step": 1000 * s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "symbolic-parameter mode: strided kernel, N in 2^10..2^20 (host values) x "
+                                   "STRIDE from its asserts (open above: 1..64), grid = ceil(N/256)",
+                       "admissible": r.admissible, "rejected": r.rejected, "distinct_programs": r.distinct,
+                       "instances": r.instances, "racy_under_some_input": r.racy,
+                       "racy_bindings": len(r.racy_bindings), "verdict_groups": len(r.groups),
+                       "first_racy": {"grid": r.first_racy[0][0], "params": r.first_racy[0][2]} if r.racy else None,
+                       "form": "bind + hash + one batched pass over distinct programs, end to end (host wall time)"}}
+    print(json.dumps(line), flush=True)
+
+
 def _auc(scores, labels):
     import numpy as np
     order = np.argsort(scores)
@@ -357,7 +391,7 @@ def main():
     ap.add_argument("--heldout", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--topk", type=int, default=4)
-    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus", "ranked"])
+    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus", "ranked", "symbolic"])
     ap.add_argument("--items", type=int, default=1000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -379,6 +413,9 @@ def main():
         return
     if args.suite == "ranked":
         run_ranked(args)
+        return
+    if args.suite == "symbolic":
+        run_symbolic(args)
         return
     if args.suite != "stencil":
         run_suite(args)

@@ -371,6 +371,26 @@ int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, void* cuda_
 int hgrd_jit_compile(const hgrd_desc* d, const hgrd_check_opts* o, double* compile_ms);
 int hgrd_jit_source(const hgrd_desc* d, const hgrd_check_opts* o, char* out, size_t cap, size_t* len);
 
+/* ---- Host-admissible inputs (the paper's question: a race under some input) --
+ * A race "under some host-admissible input" (Sec. 3, Sec. 5.1) is decided here
+ * by checking a set of admissible bindings (the batched path), not
+ * symbolically.
+ *   hgrd_desc_params: the parameters of a loaded descriptor, in declaration
+ *     order, with the bounds its asserts put on each parameter alone (asserts
+ *     affine in one parameter after folding constants: `N > 0`, `2*N <= 8192`;
+ *     others, e.g. those with launch dimensions, are enforced at bind time).
+ *     Writes min(cap, n) entries; *n = the parameter count.
+ *   hgrd_bound_hash: a 64-bit hash of everything a check of the bound
+ *     descriptor reads (compiled program, array sizes and granules): two
+ *     bindings with equal hashes have equal verdicts, so a sweep checks one. */
+typedef struct {
+  char name[32];
+  int64_t lo, hi;          /* inclusive; INT64_MIN / INT64_MAX when unbounded */
+  uint32_t has_lo, has_hi;
+} hgrd_param_info;
+int hgrd_desc_params(const hgrd_desc* d, hgrd_param_info* out, uint32_t cap, uint32_t* n);
+int hgrd_bound_hash(const hgrd_desc* d, uint64_t* h);
+
 void hgrd_free_desc(hgrd_desc* d);
 const char* hgrd_last_error(void);
 

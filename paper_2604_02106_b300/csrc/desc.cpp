@@ -1124,6 +1124,88 @@ int load_desc(const char* text, size_t len, hgrd_desc** out) {
   }
 }
 
+// ---- host-admissible parameter ranges (the symbolic-parameter mode)
+// a*P + c of an AST node when it is affine in at most one parameter P and
+// reads no launch dimension, id or loop counter; ok = false otherwise
+struct Aff1 {
+  bool ok;
+  int p;  // parameter index, -1 for a constant
+  __int128 a, c;
+};
+static Aff1 affine1(const hgrd_desc& d, int n, int depth = 0) {
+  const Aff1 bad{false, -1, 0, 0};
+  if (n < 0 || depth > 256) return bad;
+  const AstNode& x = d.ast[n];
+  const __int128 LIM = (__int128)1 << 100;
+  auto fits = [&](const Aff1& r) { return r.ok && r.a < LIM && r.a > -LIM && r.c < LIM && r.c > -LIM; };
+  switch (x.op) {
+    case 'n': return {true, -1, 0, x.val};
+    case 'p': return {true, (int)x.val, 1, 0};
+    case '~': {
+      Aff1 u = affine1(d, x.a, depth + 1);
+      if (!u.ok) return bad;
+      return {true, u.p, -u.a, -u.c};
+    }
+    case '+':
+    case '-': {
+      Aff1 u = affine1(d, x.a, depth + 1), w = affine1(d, x.b, depth + 1);
+      if (!u.ok || !w.ok || (u.p >= 0 && w.p >= 0 && u.p != w.p)) return bad;
+      const __int128 sg = x.op == '+' ? 1 : -1;
+      Aff1 r{true, u.p >= 0 ? u.p : w.p, u.a + sg * w.a, u.c + sg * w.c};
+      return fits(r) ? r : bad;
+    }
+    case '*': {
+      Aff1 u = affine1(d, x.a, depth + 1), w = affine1(d, x.b, depth + 1);
+      if (!u.ok || !w.ok) return bad;
+      if (u.p >= 0 && w.p >= 0) return bad;
+      const Aff1& k = u.p < 0 ? u : w;  // the constant factor
+      const Aff1& v = u.p < 0 ? w : u;
+      Aff1 r{true, v.p, v.a * k.c, v.c * k.c};
+      return fits(r) ? r : bad;
+    }
+    default:
+      return bad;
+  }
+}
+static __int128 floor_div(__int128 a, __int128 b) {
+  __int128 q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+static __int128 ceil_div(__int128 a, __int128 b) { return -floor_div(-a, b); }
+
+// bounds on each parameter from asserts that constrain it alone
+void param_bounds(const hgrd_desc& d, std::vector<__int128>& lo, std::vector<__int128>& hi) {
+  const __int128 INF = (__int128)1 << 100;
+  lo.assign(d.params.size(), -INF);
+  hi.assign(d.params.size(), INF);
+  for (const CondDecl& c : d.asserts) {
+    Aff1 l = affine1(d, c.lhs), r = affine1(d, c.rhs);
+    if (!l.ok || !r.ok || (l.p >= 0 && r.p >= 0 && l.p != r.p)) continue;
+    const int p = l.p >= 0 ? l.p : r.p;
+    if (p < 0) continue;
+    const __int128 a = l.a - r.a, k = r.c - l.c;  // a*P op k
+    if (a == 0) continue;
+    // a*P <= ub and / or a*P >= lb
+    bool has_ub = false, has_lb = false;
+    __int128 ub = 0, lb = 0;
+    switch (c.op) {
+      case '<': has_ub = true; ub = k - 1; break;
+      case 'L': has_ub = true; ub = k; break;
+      case '>': has_lb = true; lb = k + 1; break;
+      case 'G': has_lb = true; lb = k; break;
+      case 'E': has_ub = has_lb = true; ub = lb = k; break;
+      default: break;
+    }
+    if (a < 0) {  // divide by a negative coefficient: the sides swap
+      std::swap(has_ub, has_lb);
+      std::swap(ub, lb);
+    }
+    if (has_ub) hi[p] = std::min(hi[p], floor_div(ub, a));
+    if (has_lb) lo[p] = std::max(lo[p], ceil_div(lb, a));
+  }
+}
+
 }  // namespace hgrd
 
 extern "C" {
@@ -1136,6 +1218,41 @@ int hgrd_bind_host_params(hgrd_desc* d, const hgrd_binding* b) {
 }
 
 void hgrd_free_desc(hgrd_desc* d) { delete d; }
+
+int hgrd_desc_params(const hgrd_desc* d, hgrd_param_info* out, uint32_t cap, uint32_t* n) {
+  if (!d || !n || (cap && !out)) return hgrd::fail(HGRD_EINVAL, "null argument");
+  std::vector<__int128> lo, hi;
+  hgrd::param_bounds(*d, lo, hi);
+  *n = (uint32_t)d->params.size();
+  for (uint32_t i = 0; i < *n && i < cap; i++) {
+    hgrd_param_info& x = out[i];
+    memset(&x, 0, sizeof(x));
+    strncpy(x.name, d->params[i].c_str(), sizeof(x.name) - 1);
+    x.has_lo = lo[i] > -((__int128)1 << 62);
+    x.has_hi = hi[i] < ((__int128)1 << 62);
+    x.lo = x.has_lo ? (int64_t)lo[i] : INT64_MIN;
+    x.hi = x.has_hi ? (int64_t)hi[i] : INT64_MAX;
+  }
+  return HGRD_OK;
+}
+
+int hgrd_bound_hash(const hgrd_desc* d, uint64_t* h) {
+  if (!d || !h) return hgrd::fail(HGRD_EINVAL, "null argument");
+  if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  // FNV-1a over the compiled program (every value the check reads) and the
+  // array sizes and granules (the witnesses' byte addresses)
+  uint64_t x = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t len) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t k = 0; k < len; k++) x = (x ^ c[k]) * 1099511628211ull;
+  };
+  const hgrd::Bound& B = *d->bound;
+  mix(&B.prog, sizeof(B.prog));
+  mix(B.array_bytes.data(), B.array_bytes.size() * sizeof(int64_t));
+  mix(B.array_granule.data(), B.array_granule.size() * sizeof(int64_t));
+  *h = x;
+  return HGRD_OK;
+}
 
 const char* hgrd_last_error(void) { return hgrd::g_err.c_str(); }
 
