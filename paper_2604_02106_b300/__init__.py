@@ -7,6 +7,7 @@ compiled library is missing this module raises on use; there is no fallback.
 from __future__ import annotations
 
 import ctypes as C
+import struct
 import os
 from dataclasses import dataclass
 
@@ -31,7 +32,8 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free", "hgrd_pair_features",
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
-           "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source"]
+           "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source",
+           "hgrd_desc_params", "hgrd_bound_hash"]
 BATCH_GRAPH = 1
 BATCH_JIT = 2
 
@@ -144,7 +146,8 @@ def lib():
         L.hgrd_jit_source.argtypes = [vp, C.POINTER(CheckOpts), C.c_char_p, sz, C.POINTER(sz)]
         for f in ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check",
                   "hgrd_check_enqueue", "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile",
-                  "hgrd_debug_divmod", "hgrd_jit_compile", "hgrd_jit_source"]:
+                  "hgrd_debug_divmod", "hgrd_jit_compile", "hgrd_jit_source",
+           "hgrd_desc_params", "hgrd_bound_hash"]:
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -161,17 +164,19 @@ def _opts(max_raw_witness=0, pair_cap=0, flags=0, only_accesses=0, max_shared_ke
 
 def _pairs(pk):
     """{(a, b): kind_mask} for a <= b from the three 32x32 bit matrices."""
+    rows = struct.unpack("96I", bytes(pk))  # one copy out of the ctypes array
     out = {}
-    for k in range(3):
-        for a in range(32):
-            row = pk[k][a]
-            b = a
-            row >>= a
-            while row:
-                if row & 1:
-                    out[(a, b)] = out.get((a, b), 0) | (1 << k)
-                row >>= 1
-                b += 1
+    for i, row in enumerate(rows):
+        if not row:
+            continue
+        k, a = divmod(i, 32)
+        row >>= a
+        b = a
+        while row:
+            if row & 1:
+                out[(a, b)] = out.get((a, b), 0) | (1 << k)
+            row >>= 1
+            b += 1
     return out
 
 
@@ -238,13 +243,26 @@ class Kernel:
         arr = (C.c_int64 * max(1, len(params)))(*params)
         b = Binding((C.c_int32 * 3)(*grid), (C.c_int32 * 3)(*block), len(params), arr)
         _raise(lib().hgrd_bind_host_params(self._h, C.byref(b)))
+        self.__dict__.pop("_ws_sizes", None)  # sizes follow the binding
         return self
 
     def workspace_size(self, **opts) -> int:
-        n = C.c_size_t()
-        o = _opts(**opts)
-        _raise(lib().hgrd_workspace_size(self._h, C.byref(o), C.byref(n)))
-        return n.value
+        key = tuple(sorted(opts.items()))
+        cache = self.__dict__.setdefault("_ws_sizes", {})
+        if key not in cache:
+            n = C.c_size_t()
+            o = _opts(**opts)
+            _raise(lib().hgrd_workspace_size(self._h, C.byref(o), C.byref(n)))
+            cache[key] = n.value
+        return cache[key]
+
+    def _out(self, cap: int):
+        """A witness buffer of cap records, reused across calls (results copy out of it)."""
+        cache = self.__dict__.setdefault("_outs", {})
+        buf = cache.get(cap)
+        if buf is None:
+            buf = cache[cap] = (Witness * max(1, cap))()
+        return buf
 
     def workspace(self, device="cuda", **opts):
         """A device workspace sized for the current binding (reused when large enough)."""
@@ -259,7 +277,7 @@ class Kernel:
         """Exhaustive check; synchronous.  Retries once with a larger raw-witness buffer."""
         for attempt in range(2):
             ws = workspace if workspace is not None else self.workspace(**opts)
-            out = (Witness * max(1, cap))()
+            out = self._out(cap)
             v = Verdict()
             o = _opts(**opts)
             rc = lib().hgrd_check(self._h, C.byref(o), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream),
@@ -303,7 +321,7 @@ class Kernel:
         """hgrd_check_noalloc: the check on the library's built-in 64 MiB device
         scratch, for callers that cannot allocate device memory.  No instance
         pair search (min_x / min_y are None)."""
-        out = (Witness * max(1, cap))()
+        out = self._out(cap)
         v = Verdict()
         o = _opts(**opts)
         rc = lib().hgrd_check_noalloc(self._h, C.byref(o), _stream_ptr(stream), out, cap, C.byref(v))
@@ -320,7 +338,7 @@ class Kernel:
                                         _stream_ptr(stream)))
 
     def collect(self, workspace, cap: int = 1 << 16, stream=None, **opts) -> Result:
-        out = (Witness * max(1, cap))()
+        out = self._out(cap)
         v = Verdict()
         o = _opts(**opts)
         rc = lib().hgrd_check_collect(self._h, C.byref(o), C.c_void_p(workspace.data_ptr()), workspace.numel(),
