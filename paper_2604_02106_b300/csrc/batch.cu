@@ -387,8 +387,7 @@ bool small_single_ok(const Bound& B) { return small_ok(B, SB_KEYS); }
 cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* counters, uint64_t* scratch,
                                 uint64_t* uniq) {
   const size_t smem = sizeof(SmallSmem);
-  cudaError_t e = cudaFuncSetAttribute((const void*)batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_smem((const void*)batch_small_kernel, smem);
   if (e != cudaSuccess) return e;
   uint64_t* out = scratch;
   uint64_t* wits = scratch + 64;

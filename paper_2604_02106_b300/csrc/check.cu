@@ -435,13 +435,27 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
     PairRec* pr = (PairRec*)(ws + W.pairs);
     CK(cudaMemsetAsync(ws + W.counters + 8 * C_NPAIR, 0, 8, s));
+    // a global-memory witness: search only the blocks of its run (listed in
+    // the unit-offset buffer, free after the write pass); the one-CTA path
+    // sorted nothing, so it searches every unit
+    uint64_t* blist = (uint64_t*)(ws + W.unit_off);
+    CK(cudaMemsetAsync(ws + W.counters + 8 * C_NPB, 0, 8, s));
+    // the path enqueue took for these options (the same decisions, made again)
+    const uint32_t fl = o ? o->flags : 0u;
+    const bool small = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(B);
+    const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
+    const int passes = split ? B.sort_passes_split : B.sort_passes;
+    if (!small) {
+      const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
+      CK(launch_pair_blocks(L, sorted, (const DProg*)(ws + W.prog), duniq, (uint64_t*)(ws + W.counters), blist));
+    }
     // the specialised kernels when this binding has them (either module holds the search)
     const bool jsplit = jit_ready(B, true), jplain = !jsplit && jit_ready(B, false);
     if ((jsplit || jplain) && !(o && (o->flags & HGRD_NO_JIT)))
-      CK(launch_jit_expand(L, B, 2, HP, nullptr, nullptr, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
+      CK(launch_jit_expand(L, B, 2, HP, nullptr, blist, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
                            nullptr, nullptr, 0xffffffffu, jsplit, duniq, pr, W.pair_cap));
     else
-      CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, nullptr, nullptr, nullptr, 0,
+      CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, blist, nullptr, nullptr, 0,
                        (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
     // the record count and a prefix of the records in one round trip
     const uint64_t ppre = std::min<uint64_t>(PAIR_PREFIX, W.pair_cap);

@@ -39,8 +39,9 @@ enum { SEL_ALL = 0, SEL_KEPT = 1, SEL_KEPT_GLOBAL = 2 };
 
 // Modes 0 (count keys per unit + digit histograms of `npass` digits), 1 (write
 // keys at the unit offsets) and 2 (gather the instances of the minimal
-// witness's granule).  Warp = unit, grid-stride over units.  shist: npass x 256
-// words of shared memory (mode 0).
+// witness's granule).  Warp = unit, grid-stride over units; mode 2 visits
+// only the units of the blocks unit_off lists when counters[C_NPB] = 1 + their
+// count.  shist: npass x 256 words of shared memory (mode 0).
 template <typename T, int MODE, class X>
 __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X& ex, uint32_t* shist,
                                                   uint64_t* __restrict__ unit_cnt,
@@ -71,7 +72,11 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
   uint64_t oob = 0, drop = 0;
   const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
   if (MODE == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[C_NKEYS] = counters[C_NG] + counters[C_NDROP];
-  for (int64_t u = (int64_t)blockIdx.x * WPC + warp; u < nunits; u += (int64_t)gridDim.x * WPC) {
+  const uint64_t npb = MODE == 2 ? counters[C_NPB] : 0;
+  const int64_t upb = (int64_t)P->wpb * P->nchunk;
+  const int64_t nvisit = npb ? (int64_t)(npb - 1) * upb : nunits;
+  for (int64_t j = (int64_t)blockIdx.x * WPC + warp; j < nvisit; j += (int64_t)gridDim.x * WPC) {
+    const int64_t u = npb ? (int64_t)unit_off[j / upb] * upb + j % upb : j;
     uint64_t cursor = (MODE == 1) ? unit_off[u] : 0;
     // the write pass expands only the accesses whose keys are kept
     auto step = [&](int a, const DAcc& A, bool inb, unsigned bal, int64_t idx, int64_t iv, int64_t b, int lt,

@@ -162,6 +162,7 @@ enum {
   C_NSC,  // keys of shared arrays in candidate bins (smode: written behind the sorted keys)
   C_NDROP,  // keys of accesses that cannot race with any access (counted, never written)
   C_NRAWBIG,  // raw witnesses left to the device-wide merge (0 when one CTA merges them)
+  C_NPB,      // pair search: 1 + blocks listed for it (0: search every unit)
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_SMALLQ = 120,  // one-CTA path of a small check: work queue, then an order word of zero

@@ -382,12 +382,9 @@ cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const D
     smem = block_body_words(mode, (uint64_t)h_prog.nsbins) * 4;
     need = h_prog.nblk;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  int per = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, EXP_THREADS, smem);
-  if (e != cudaSuccess) return e;
-  int64_t grid = (int64_t)(per < 1 ? 1 : per) * L.nsm;
+  int64_t grid = (int64_t)resident_ctas(fn, EXP_THREADS, smem) * L.nsm;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   void* args[] = {(void*)&h_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s,

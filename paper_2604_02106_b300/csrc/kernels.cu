@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "expand_body.cuh"
 
@@ -705,6 +708,88 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
   }
 }
 
+// ------------------------------------------------------------------ pair search: blocks of the witness's run
+// The instances on a global-memory witness's granule are the keys of its run
+// in the sorted stream, so only their blocks need the pair search.  One CTA
+// finds the run (warp 0: 32 probes per step, the count of probes below the
+// target narrows the range 33-fold), collects its blocks (runs of at most
+// PB_MAX keys; longer runs, and shared-memory witnesses, leave
+// counters[C_NPB] at 0: every unit is searched), sorts them, drops repeats,
+// and lists them in `blocks`.
+constexpr int PB_MAX = 4096;
+__device__ __forceinline__ uint64_t first_at_or_above(const uint64_t* keys, uint64_t n, int sh, uint64_t target,
+                                                     int lane) {
+  uint64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const uint64_t step = (hi - lo) / 33;
+    const uint64_t p = lo + (uint64_t)(lane + 1) * step;  // < hi for every lane
+    const uint32_t c = (uint32_t)__popc(__ballot_sync(FULL, shr64(keys[p], sh) < target));
+    const uint64_t nlo = c ? lo + (uint64_t)c * step + 1 : lo;
+    const uint64_t nhi = c < 32 ? lo + (uint64_t)(c + 1) * step : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  const bool below = lo + lane < hi && shr64(keys[lo + lane], sh) < target;
+  return lo + (uint64_t)__popc(__ballot_sync(FULL, below));
+}
+
+__global__ void __launch_bounds__(256) pair_blocks_kernel(const uint64_t* __restrict__ keys,
+                                                          const DProg* __restrict__ P,
+                                                          const uint64_t* __restrict__ uniq, uint64_t* counters,
+                                                          uint64_t* __restrict__ blocks) {
+  __shared__ uint64_t sb[PB_MAX];
+  __shared__ uint64_t s_run[2];
+  if (counters[C_NUNIQ] == 0) return;
+  const uint64_t w0 = uniq[0];
+  if ((w0 >> 58) & 1) return;
+  const uint32_t arr = (uint32_t)(w0 >> 53) & 31;
+  const uint64_t gran = (w0 >> 13) & ((1ull << 40) - 1);
+  int li = -1;
+  for (int l = 0; l < P->nlay; ++l)
+    if (P->lay_arr[l] == (int32_t)arr && !P->lay_shared[l]) li = l;
+  if (li < 0) return;
+  const uint64_t cell = P->lay_cbase[li] + gran;
+  const uint64_t n = counters[C_NG];
+  const int sh = P->PB + P->IVB;
+  if (threadIdx.x < 32) {
+    const uint64_t lo = first_at_or_above(keys, n, sh, cell, threadIdx.x);
+    const uint64_t hi = first_at_or_above(keys, n, sh, cell + 1, threadIdx.x);
+    if (threadIdx.x == 0) {
+      s_run[0] = lo;
+      s_run[1] = hi;
+    }
+  }
+  __syncthreads();
+  const uint64_t lo = s_run[0], hi = s_run[1];
+  if (hi <= lo || hi - lo > (uint64_t)PB_MAX) return;
+  const uint32_t m = (uint32_t)(hi - lo);
+  uint32_t p2 = 1;
+  while (p2 < m) p2 <<= 1;
+  const int bsh = P->AB + P->TB;
+  for (uint32_t i = threadIdx.x; i < p2; i += 256) sb[i] = i < m ? lowbits(keys[lo + i] >> bsh, P->BB) : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= p2; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < p2; i += 256) {
+        const uint32_t x = i ^ j;
+        if (x > i) {
+          const uint64_t a = sb[i], b = sb[x];
+          if ((a > b) == ((i & k) == 0)) {
+            sb[i] = b;
+            sb[x] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    uint32_t c = 0;
+    for (uint32_t i = 0; i < m; ++i)
+      if (i == 0 || sb[i] != sb[i - 1]) blocks[c++] = sb[i];
+    counters[C_NPB] = (uint64_t)c + 1;
+  }
+}
+
 // ------------------------------------------------------------------ witness merge
 __global__ void heads_kernel(const uint64_t* __restrict__ w, const uint64_t* n_dev, uint64_t n_max,
                              uint64_t* __restrict__ flags) {
@@ -828,14 +913,47 @@ __global__ void kind_counts_kernel(const uint64_t* __restrict__ uniq, uint64_t* 
   }
 }
 
-int occupancy_grid(const void* fn, int threads, size_t smem, int nsm) {
+int occupancy_grid(const void* fn, int threads, size_t smem, int nsm) { return resident_ctas(fn, threads, smem) * nsm; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launch-attribute caches
+// The dynamic shared-memory limit set on each kernel and its resident CTAs
+// per SM, per device: the runtime queries behind them cost microseconds of
+// host time on every launch otherwise.
+namespace {
+std::mutex g_attr_mu;
+std::map<std::tuple<int, const void*>, size_t> g_smem_set;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_resident;
+int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+}  // namespace
+
+cudaError_t allow_smem(const void* fn, size_t smem) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t& have = g_smem_set[std::make_tuple(dev, fn)];
+  if (smem <= have) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) have = smem;
+  return e;
+}
+
+int resident_ctas(const void* fn, int threads, size_t smem) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto key = std::make_tuple(dev, fn, threads, smem);
+  auto it = g_resident.find(key);
+  if (it != g_resident.end()) return it->second;
   int per = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (per < 1) per = 1;
-  return per * nsm;
+  g_resident[key] = per;
+  return per;
 }
-
-}  // namespace
 
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
@@ -854,7 +972,7 @@ cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_p
          : mode == 1 ? (const void*)expand_kernel<int64_t, 1>
                      : (const void*)expand_kernel<int64_t, 2>;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   const int64_t need = (h_prog.nunits + EXP_THREADS / 32 - 1) / (EXP_THREADS / 32);
   int64_t grid = occupancy_grid(fn, EXP_THREADS, smem, L.nsm);
@@ -921,7 +1039,7 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
   const SortVariant& S = V[(dev >= 0 && dev < 64 && g_sort_variant[dev] < nv) ? g_sort_variant[dev] : 0];
   const uint64_t tile = (uint64_t)S.threads * S.kpt;
   const uint64_t tiles = (n_max + tile - 1) / tile;
-  cudaError_t e = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
+  cudaError_t e = allow_smem(S.fn, S.smem);
   if (e != cudaSuccess) return e;
   int grid = occupancy_grid(S.fn, S.threads, S.smem, L.nsm);
   if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
@@ -945,7 +1063,7 @@ cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* 
                          uint64_t* counters, bool stop_first, bool bins) {
   const size_t smem = bins ? 8 * sizeof(BinTables) : 0;
   if (bins) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem((const void*)exact_kernel, smem);
     if (e != cudaSuccess) return e;
   }
   int grid = occupancy_grid((const void*)exact_kernel, 256, smem, L.nsm);
@@ -966,7 +1084,7 @@ cudaError_t launch_expand_block(const Launch& L, int mode, bool wide, const DPro
     fn = mode == 3 ? (const void*)expand_block_kernel<int32_t, 3> : (const void*)expand_block_kernel<int32_t, 4>;
   else
     fn = mode == 3 ? (const void*)expand_block_kernel<int64_t, 3> : (const void*)expand_block_kernel<int64_t, 4>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   int64_t grid = occupancy_grid(fn, EXP_THREADS, smem, L.nsm);
   if (grid > h_prog.nblk) grid = h_prog.nblk;
@@ -1028,6 +1146,13 @@ cudaError_t launch_zero(const Launch& L, uint64_t* p, const uint64_t* n_dev, uin
   uint64_t blocks = (n_max + 255) / 256;
   unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
   zero_kernel<<<grid, 256, 0, L.s>>>(p, n_dev, n_max);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const DProg* d_prog, const uint64_t* uniq,
+                               uint64_t* counters, uint64_t* blocks) {
+  pair_blocks_kernel<<<1, 256, 0, L.s>>>(keys, d_prog, uniq, counters, blocks);
   (*L.launches)++;
   return cudaGetLastError();
 }

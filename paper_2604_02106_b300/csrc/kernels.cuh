@@ -16,6 +16,11 @@ constexpr int CA_AHEAD = 4;        // 32-key steps loaded ahead by each warp
 constexpr int SCAN_TILE = 4096;
 constexpr int MAX_PASSES = 16;
 
+// cached per device: raise a kernel's dynamic shared-memory limit to at least
+// smem (once), and its resident CTAs per SM for a launch shape
+cudaError_t allow_smem(const void* fn, size_t smem);
+int resident_ctas(const void* fn, int threads, size_t smem);
+
 struct Launch {
   cudaStream_t s;
   int nsm;
@@ -66,6 +71,10 @@ cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_d
 cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* flags, const uint64_t* excl,
                          const uint64_t* n_dev, uint64_t n_max, uint64_t* uniq);
 cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters);
+// pair search: the blocks of a global-memory witness's run in the sorted keys
+// (counters[C_NPB] = 1 + their count, or left 0 when every unit must be searched)
+cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const DProg* d_prog, const uint64_t* uniq,
+                               uint64_t* counters, uint64_t* blocks);
 // at most WSMALL_MAX raw witnesses are merged by one CTA: witness_split sets
 // counters[C_NRAWBIG] (0 in that case, else the count) for the device-wide
 // kernels; witness_small then merges the few from `raw` into `uniq`
