@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <tuple>
@@ -145,7 +147,115 @@ int prechecks(const hgrd_desc* d, void* d_ws, size_t ws_bytes, const hgrd_check_
   return HGRD_OK;
 }
 
-// the buffer holding the merged witnesses after enqueue
+// offset of the buffer holding the merged witnesses after enqueue (the
+// device-wide merge sorts raw <-> raw2 in WP passes and merges into the other)
+size_t uniq_off(const Layout& W) {
+  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
+  return (WP % 2 == 0) ? W.raw2 : W.raw;
+}
+
+// the device-wide witness merge: radix sort of the raw words, head flags,
+// scan, OR-merge; its kernels read the count from counters[C_NRAWBIG]
+cudaError_t enqueue_witness_big(const Launch& L, const Layout& W, char* ws, int P) {
+  auto U = [&](size_t off) { return (uint64_t*)(ws + off); };
+  uint64_t* cnt = U(W.counters);
+  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
+  uint64_t* nraw = cnt + C_NRAWBIG;
+  cudaError_t e;
+  if ((e = launch_zero_status(L, U(W.status), nraw, W.status_words)) != cudaSuccess) return e;
+  uint64_t* whist = U(W.hist) + 8 * 256;
+  uint64_t* wgb = U(W.gbase) + 8 * 256;
+  if ((e = launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist)) != cudaSuccess) return e;
+  if ((e = launch_hist_scan(L, whist, wgb, WP)) != cudaSuccess) return e;
+  uint64_t* win = U(W.raw);
+  uint64_t* wout = U(W.raw2);
+  for (int p = 0; p < WP; p++) {
+    if ((e = launch_onesweep(L, win, wout, nraw, W.raw_cap, WIT_SORT_LO + 8 * p, wgb + p * 256, U(W.status),
+                             cnt + C_TICKET0 + P + p, (uint32_t)(P + p + 1), cnt + C_ERR)) != cudaSuccess)
+      return e;
+    std::swap(win, wout);
+  }
+  // win: sorted raw witnesses; wout receives the merged set
+  if ((e = launch_zero(L, wout, nraw, W.raw_cap)) != cudaSuccess) return e;
+  if ((e = launch_heads(L, win, nraw, W.raw_cap, U(W.flags))) != cudaSuccess) return e;
+  if ((e = launch_scan(L, U(W.flags), U(W.excl), nraw, W.raw_cap, U(W.partials), cnt + C_NUNIQ)) != cudaSuccess)
+    return e;
+  return launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout);
+}
+
+// The witness merge as an instantiated graph per (device, workspace, layout,
+// sort passes, onesweep shape): the split kernel, then a conditional IF node
+// whose body (captured from enqueue_witness_big) runs only when the split
+// kernel opens it.  nullptr when graphs are unavailable; the caller then
+// launches the kernels directly.
+std::mutex g_wg_mu;
+std::map<std::vector<uint64_t>, cudaGraphExec_t> g_wg;
+bool g_wg_off = false;
+
+cudaGraphExec_t witness_graph(const Launch& L, const Layout& W, char* ws, int P) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::vector<uint64_t> key = {(uint64_t)dev, (uint64_t)(uintptr_t)ws, W.counters, W.raw, W.raw2, W.flags,
+                                     W.excl, W.partials, W.hist, W.gbase, W.status, W.raw_cap, W.status_words,
+                                     (uint64_t)P, (uint64_t)sort_variant_current()};
+  std::lock_guard<std::mutex> lk(g_wg_mu);
+  auto it = g_wg.find(key);
+  if (it != g_wg.end()) return it->second;
+  if (g_wg_off || g_wg.size() >= 256) return nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle h{};
+  ok = ok && cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNode_t split = nullptr, cond = nullptr;
+  uint64_t* cnt = (uint64_t*)(ws + W.counters);
+  uint64_t raw_cap = W.raw_cap;
+  if (ok) {
+    void* args[] = {(void*)&cnt, (void*)&raw_cap, (void*)&h};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)witness_split_cond_fn();
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    ok = cudaGraphAddKernelNode(&split, g, nullptr, 0, &kp) == cudaSuccess;
+  }
+  cudaGraphNodeParams cp{};
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&cond, g, &split, nullptr, 1, &cp) == cudaSuccess;
+  }
+  if (ok) ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      uint64_t captured = 0;
+      Launch LC{cs, L.nsm, &captured};
+      const bool launched = enqueue_witness_big(LC, W, ws, P) == cudaSuccess;
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && launched;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (cs) cudaStreamDestroy(cs);
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();  // clear a sticky launch-configuration error, if any
+    g_wg_off = true;
+    return nullptr;
+  }
+  g_wg[key] = exec;
+  return exec;
+}
+
+// the buffer holding the merged witnesses after enqueue// the buffer holding the merged witnesses after enqueue
 uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
   (void)d;
@@ -292,28 +402,21 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                   split));
   g_prof.mark("exact");
   // canonical order of the witnesses: up to WSMALL_MAX merged by one CTA in
-  // shared memory, more by the device-wide radix sort and merge (whose kernels
-  // see zero witnesses in the other case)
-  const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
-  CK(launch_witness_split(L, cnt, W.raw_cap));
-  uint64_t* nraw = cnt + C_NRAWBIG;
-  CK(launch_zero_status(L, U(W.status), nraw, W.status_words));
-  uint64_t* whist = U(W.hist) + 8 * 256;
-  uint64_t* wgb = U(W.gbase) + 8 * 256;
-  CK(launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist));
-  CK(launch_hist_scan(L, whist, wgb, WP));
-  uint64_t* win = U(W.raw);
-  uint64_t* wout = U(W.raw2);
-  for (int p = 0; p < WP; p++) {
-    CK(launch_onesweep(L, win, wout, nraw, W.raw_cap, WIT_SORT_LO + 8 * p, wgb + p * 256, U(W.status),
-                       cnt + C_TICKET0 + P + p, (uint32_t)(P + p + 1), cnt + C_ERR));
-    std::swap(win, wout);
+  // shared memory, more by the device-wide radix sort and merge.  Outside a
+  // stream capture the device-wide kernels run as the body of a conditional
+  // graph node that the split kernel opens only when they have work;
+  // otherwise they are launched and find nothing to do.
+  uint64_t* wout = U(uniq_off(W));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cap));
+  cudaGraphExec_t wg = (cap == cudaStreamCaptureStatusNone && !dprog_resident) ? witness_graph(L, W, ws, P) : nullptr;
+  if (wg) {
+    CK(cudaGraphLaunch(wg, s));
+    (*L.launches)++;
+  } else {
+    CK(launch_witness_split(L, cnt, W.raw_cap));
+    CK(enqueue_witness_big(L, W, ws, P));
   }
-  // win: sorted raw witnesses; wout receives the merged set
-  CK(launch_zero(L, wout, nraw, W.raw_cap));
-  CK(launch_heads(L, win, nraw, W.raw_cap, U(W.flags)));
-  CK(launch_scan(L, U(W.flags), U(W.excl), nraw, W.raw_cap, U(W.partials), cnt + C_NUNIQ));
-  CK(launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout));
   CK(launch_witness_small(L, U(W.raw), wout, cnt, W.raw_cap));
   CK(launch_kind_counts(L, wout, cnt));
   g_prof.mark("witness_merge");

@@ -814,6 +814,16 @@ __global__ void witness_split_kernel(uint64_t* counters, uint64_t raw_cap) {
   counters[C_NRAWBIG] = n > (uint64_t)WSMALL_MAX ? n : 0;
 }
 
+// the same decision inside a graph: it also opens (1) or keeps shut (0) the
+// conditional node holding the device-wide merge
+__global__ void witness_split_cond_kernel(uint64_t* counters, uint64_t raw_cap, cudaGraphConditionalHandle h) {
+  uint64_t n = counters[C_NRAW];
+  if (n > raw_cap) n = raw_cap;
+  const bool big = n > (uint64_t)WSMALL_MAX;
+  counters[C_NRAWBIG] = big ? n : 0;
+  cudaGraphSetConditional(h, big ? 1u : 0u);
+}
+
 __global__ void zero_status_kernel(uint64_t* __restrict__ status, const uint64_t* n_dev, uint64_t max_words) {
   const uint64_t n = *n_dev;
   uint64_t words = (n + RS_MIN_TILE - 1) / RS_MIN_TILE * RS_RADIX;
@@ -1030,6 +1040,12 @@ const SortVariant* sort_variants(int* count) {
 }
 int g_sort_variant[64];  // per device; 0 = the default shape
 
+int sort_variant_current() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (dev >= 0 && dev < 64) ? g_sort_variant[dev] : 0;
+}
+
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist, int next_shift) {
@@ -1120,6 +1136,8 @@ cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* fla
   (*L.launches)++;
   return cudaGetLastError();
 }
+
+const void* witness_split_cond_fn() { return (const void*)witness_split_cond_kernel; }
 
 cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap) {
   witness_split_kernel<<<1, 1, 0, L.s>>>(counters, raw_cap);

@@ -80,6 +80,11 @@ cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const DPro
 // kernels; witness_small then merges the few from `raw` into `uniq`
 constexpr int WSMALL_MAX = 4096;
 cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap);
+// the split kernel for a graph: (counters, raw_cap, conditional handle) opens
+// the handle's node when the device-wide merge has work
+const void* witness_split_cond_fn();
+// the onesweep CTA shape in use on the current device
+int sort_variant_current();
 cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
                                  uint64_t raw_cap);
 // zero the look-back status words of the tiles a sort of *n_dev keys uses
