@@ -72,11 +72,11 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
     return at;
   };
   L.counters = take(C_WORDS * 8);
+  L.hist = take(MAX_PASSES * 256 * 8);  // right after the counters: one clear covers both
   L.prog = take(sizeof(DProg));
   L.unit_cnt = take(nunits * 8);
   L.unit_off = take(nunits * 8);
   L.partials = take(((scan_n + SCAN_TILE - 1) / SCAN_TILE + 1) * 8);
-  L.hist = take(MAX_PASSES * 256 * 8);
   L.gbase = take(MAX_PASSES * 256 * 8);
   L.status = take(L.status_words * 8);
   L.keysA = take(L.key_words * 8);
@@ -304,8 +304,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
   const uint64_t nsort = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
-  CK(cudaMemsetAsync(cnt, 0, C_WORDS * 8, s));
-  CK(cudaMemsetAsync(U(W.hist), 0, MAX_PASSES * 256 * 8, s));
+  CK(cudaMemsetAsync(cnt, 0, W.hist + MAX_PASSES * 256 * 8 - W.counters, s));  // counters and histograms
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
   if (!any || B.nkeys_max == 0 || HP.nunits == 0) return HGRD_OK;  // nothing can be live

@@ -207,14 +207,14 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
     if (MODE == 4) {
       const uint64_t base = sbase[b];
       has = base != NO_ROW;
-      if (has) {
+      if (has) {  // (uniform over the CTA: every thread read the same base)
         for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
           const uint64_t e = stbl[(uint64_t)b * NB + i];
           s_cur[i] = (uint32_t)e ? (uint32_t)(e >> 32) : NONE;
         }
         sb = n_g + base;
+        __syncthreads();
       }
-      __syncthreads();
     }
     for (int64_t u = b * upb + warp; u < (b + 1) * upb; u += WPC) {
       uint64_t cursor = MODE == 4 ? unit_off[u] : 0;
@@ -271,7 +271,10 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
         oob += ex.template unit<SEL_KEPT_GLOBAL>(lane, u, only_in, step);
       if (MODE == 3 && lane == 0) unit_cnt[u] = cursor;
     }
-    __syncthreads();
+    // the block's shared tables are read and reset below (count pass) or
+    // reloaded for the next block (write pass with a bin-table row); a write
+    // pass over a block without one touched no shared memory
+    if (MODE == 3 || has) __syncthreads();
     if (MODE == 3) {
       // candidate bins of block b: room in the order of a strided walk
       uint64_t csum = 0, asum = 0;
