@@ -385,6 +385,23 @@ def run_ranked(args):
     print(json.dumps(line), flush=True)
 
 
+def run_once(args):
+    """One check of the side x side stencil: bind, compile the specialised
+    kernels (unless --no-jit), size the workspace, enqueue, collect."""
+    import workloads
+    import paper_2604_02106_b300 as hg
+    w = workloads.config2(0, planted=True, W=args.side, H=args.side)
+    k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+    if not args.no_jit:
+        k.jit_compile()
+    ws = k.workspace()
+    k.enqueue(ws)
+    r = k.collect(ws, cap=1 << 16)
+    assert r.n_witness == w.meta["expected_witnesses"], "verdict differs from the closed form"
+    print(json.dumps({"once": f"stencil {args.side}x{args.side}", "workspace_bytes": ws.numel() * ws.element_size(),
+                      "n_instances": r.n_instances, "n_keys": r.n_keys, "n_witness": r.n_witness}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train-pairs", type=int, default=1000000)
@@ -403,6 +420,9 @@ def main():
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--no-sort-tune", action="store_true")
     ap.add_argument("--no-jit", action="store_true", help="interpreted expansion kernels only")
+    ap.add_argument("--once", action="store_true",
+                    help="bind the stencil workload, compile its kernels and run one check, untimed "
+                         "(the case a profiler capture runs)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -419,6 +439,9 @@ def main():
         return
     if args.suite != "stencil":
         run_suite(args)
+        return
+    if args.once:
+        run_once(args)
         return
 
     import torch

@@ -15,8 +15,10 @@
 //     intra-warp (same warp, warp = 32 consecutive linear thread ids).
 //   * Sec. 6.1 ("Avoiding race checks"): a block barrier between two accesses
 //     leaves only the inter-threadblock check (barrier-interval ids: same
-//     block and different interval = ordered); two loads or two atomics are
-//     trivially race free.
+//     block and different interval = ordered); a warp barrier (syncwarp)
+//     between them rules out the intra-warp race only (warp-interval ids:
+//     same warp and different warp interval = ordered; Sec. 5.2, "Intra-warp
+//     races"); two loads or two atomics are trivially race free.
 //   * Appendix A ("Extending with scoped operations"): two device-scope
 //     atomics never race; two atomics of at least block scope never race
 //     inside a block; a block-scope atomic does not order threads of another
@@ -163,7 +165,7 @@ struct Access {
   int array = 0;
   int64_t width = 0;
   int scope = 1;  // 0 block, 1 device
-  P idx, iv;
+  P idx, iv, wv;  // iv: block-barrier interval; wv: warp-barrier interval
   std::vector<Cond> guards;
 };
 struct Desc {
@@ -434,6 +436,9 @@ Desc parse(const std::string& text) {
         } else if (fw[0] == "iv") {
           a.iv = ps.full_expr(body);
           if (uses_thread(a.iv.get())) ps.bad("interval must not depend on thread or block ids");
+        } else if (fw[0] == "wv") {
+          a.wv = ps.full_expr(body);
+          if (uses_thread(a.wv.get())) ps.bad("warp interval must not depend on thread or block ids");
         } else if (fw[0] == "idx") {
           a.idx = ps.full_expr(body);
           have_idx = true;
@@ -453,6 +458,10 @@ Desc parse(const std::string& text) {
       if (!a.iv) {
         a.iv = std::make_shared<Node>();
         a.iv->k = N_NUM;
+      }
+      if (!a.wv) {
+        a.wv = std::make_shared<Node>();
+        a.wv->k = N_NUM;
       }
       if (d.acc.size() >= 32) ps.bad("at most 32 accesses");
       d.acc.push_back(a);
@@ -488,7 +497,7 @@ struct Inst {
   int64_t blk, thr;
   int64_t it[4];
   int acc;
-  int64_t iv;
+  int64_t iv, wv;
 };
 
 // Kinds a pair of accesses may race with (bit0 inter-block, bit1 intra-block,
@@ -509,7 +518,8 @@ int pair_kind(const Inst& x, const Inst& y) {
   if (x.blk == y.blk && x.thr == y.thr) return 0;  // same thread: program order
   if (x.blk != y.blk) return 1;                    // barriers never order blocks
   if (x.iv != y.iv) return 0;                      // separated by a block barrier
-  return (x.thr / 32 == y.thr / 32) ? 4 : 2;
+  if (x.thr / 32 != y.thr / 32) return 2;          // a warp barrier does not order warps
+  return x.wv == y.wv ? 4 : 0;                     // same warp: a warp barrier orders them
 }
 
 struct Key {
@@ -575,6 +585,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
     for (auto& a : d.acc) {
       collect_divisors(a.idx.get(), divs);
       collect_divisors(a.iv.get(), divs);
+      collect_divisors(a.wv.get(), divs);
       for (auto& g : a.guards) {
         collect_divisors(g.lhs.get(), divs);
         collect_divisors(g.rhs.get(), divs);
@@ -636,6 +647,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
                           for (int l = 0; l < 4; l++) in.it[l] = l < (int)d.loops.size() ? e.loop[l] : 0;
                           in.acc = a;
                           in.iv = eval(A.iv.get(), e);
+                          in.wv = eval(A.wv.get(), e);
                           const int64_t g = d.arrays[A.array].granule;
                           for (int64_t gr = off / g; gr < (off + w) / g; gr++) {
                             n_keys++;

@@ -9,7 +9,8 @@ compares every pair of live, in-bounds instances directly:
     each block owns its copy);
   * the pair is a race of type inter-block (different blocks), intra-block
     (same block and barrier interval, different warps) or intra-warp (same
-    block, interval and warp, different threads) — Sec. 2, Table 2;
+    block, interval, warp and warp interval, different threads) — Sec. 2,
+    Table 2, and Sec. 5.2 for the warp barrier;
   * two loads never race, nor do two device-scope atomics; two atomics of
     block scope or wider never race inside one block (Sec. 6.1, Appendix A).
 
@@ -161,13 +162,15 @@ def parse(text):
             f = [x.strip() for x in rest.split(";")]
             kind, arr = f[0].split()
             a = {"kind": kind, "array": [x["name"] for x in d["arrays"]].index(arr), "iv": ("num", 0),
-                 "guards": [], "scope": "device"}
+                 "wv": ("num", 0), "guards": [], "scope": "device"}
             for x in f[1:]:
                 k, _, body = x.partition(" ")
                 if k == "width":
                     a["width"] = int(body)
                 elif k == "iv":
                     a["iv"] = _Expr(body, d["lets"]).tree
+                elif k == "wv":
+                    a["wv"] = _Expr(body, d["lets"]).tree
                 elif k == "idx":
                     a["idx"] = _Expr(body, d["lets"]).tree
                 elif k == "if":
@@ -215,6 +218,7 @@ def instances(d, binding):
                 thr = tx + ty * bx_ + tz * bx_ * by_
                 out.append({"blk": bx + by * gx + bz * gx * gy, "thr": thr, "warp": thr // 32,
                             "it": tuple(it) + (0,) * (4 - len(it)), "acc": ai, "iv": _ev(a["iv"], e),
+                            "wv": _ev(a["wv"], e),
                             "array": a["array"], "shared": arr["shared"], "g": g,
                             "gran": set(range(off // g, (off + a["width"]) // g))})
     return out, n_oob
@@ -235,8 +239,12 @@ def race_kind(d, x, y):
         kind = 1
     elif x["iv"] != y["iv"]:
         return 0
+    elif x["warp"] != y["warp"]:
+        kind = 2
+    elif x["wv"] != y["wv"]:  # a syncwarp between them
+        return 0
     else:
-        kind = 4 if x["warp"] == y["warp"] else 2
+        kind = 4
     if ka == "A" and kb == "A":
         block_scoped = "block" in (d["acc"][x["acc"]]["scope"], d["acc"][y["acc"]]["scope"])
         if kind != 1 or not block_scoped:

@@ -266,3 +266,58 @@ def test_invariant_thread_relabelling(seed):
     for k in a:
         assert (a[k] & 1) == (b[k] & 1)
         assert bool(a[k] & 6) == bool(b[k] & 6)
+
+
+# ---------------------------------------------------------------- warp barriers (Sec. 5.2, Sec. 6.1)
+
+@pytest.mark.parametrize("seed", range(40))
+def test_oracle_matches_brute_force_warp_barriers(seed):
+    _cmp_brute(workloads.random_warp(3000 + seed))
+
+
+# warp_exchange closed forms: the write of S[t] and the neighbour's read race
+# on every granule of S unless the barriers order them; the kind is
+# intra-warp for the lane + 1 neighbour, intra-block for the next warp.
+# In a loop with one barrier per iteration the read of iteration i and the
+# write of iteration i + 1 stay unordered (a loop-carried race).
+@pytest.mark.parametrize("sync,loops,cross,racy", [
+    ("none", 0, False, True), ("none", 0, True, True), ("none", 3, False, True),
+    ("warp", 0, False, False), ("warp", 0, True, True), ("warp", 3, False, True), ("warp", 3, True, True),
+    ("warp2", 0, False, False), ("warp2", 3, False, False), ("warp2", 3, True, True),
+    ("block", 0, False, False), ("block", 0, True, False), ("block", 3, False, True), ("block", 3, True, True),
+])
+@pytest.mark.parametrize("n_warps", [1, 2, 3])
+def test_warp_exchange_closed_form(sync, loops, cross, racy, n_warps):
+    if cross and n_warps == 1:
+        racy = False  # the "next warp" is the warp itself: thread t reads S[t]
+    w = workloads.warp_exchange(n_warps, loops, sync, cross)
+    r = oracle.check(w.text, w.binding)
+    kind = 4 if not cross else 2
+    want = [(1, 0, 4 * g, 0, 1, kind) for g in range(32 * n_warps)] if racy else []
+    assert r.witnesses == want
+    if racy:
+        # the smallest racing pair: writer thread of granule 0 against its reader
+        rd = (32 * n_warps - 32) if cross else 31
+        assert r.min_x[:2] == (0, 0) and r.min_y[:2] == (0, rd)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_invariant_distinct_warp_intervals_drop_only_intra_warp(seed):
+    # a warp barrier between every two accesses (access k in warp interval k)
+    # orders same-warp pairs of different accesses; it leaves pairs of one
+    # access with itself (other loop vectors, same interval), and every other
+    # kind, as they were
+    w = workloads.random_tiny(11000 + seed, max_instances=600)
+    lines = w.text.splitlines()
+    base = _set_of(oracle.check(w.text, w.binding))
+    for k, li in enumerate(_acc_lines(w.text)):
+        f = lines[li].split(" ; ")
+        f.insert(1, f"wv {k}")
+        lines[li] = " ; ".join(f)
+    got = _set_of(oracle.check("\n".join(lines) + "\n", w.binding))
+    want = {}
+    for key, m in base.items():
+        m2 = m if key[3] == key[4] else m & ~4
+        if m2:
+            want[key] = m2
+    assert got == want

@@ -102,10 +102,12 @@ class _Writer:
     def add(self, line):
         self.lines.append(line)
 
-    def access(self, kind, array, width, idx, iv=None, guards=(), scope=None, line=None):
+    def access(self, kind, array, width, idx, iv=None, guards=(), scope=None, line=None, wv=None):
         f = [f"access {kind} {array}", f"width {width}"]
         if iv is not None:
             f.append(f"iv {iv}")
+        if wv is not None:
+            f.append(f"wv {wv}")
         f.append(f"idx {idx}")
         for g in guards:
             f.append(f"if {g}")
@@ -476,6 +478,76 @@ def random_shared(seed: int, max_instances: int = 60000) -> Workload:
         w.access(kind, f"S{k}", el, expr, iv=iv, guards=guards, scope=scope, line=a_id + 1)
     return Workload(f"shr_{seed}", w.text(), Binding(grid, (bdx, bdy, 1), (Q,)),
                     {"loop_bounds": bounds, "n_access": nacc})
+
+
+def warp_exchange(n_warps: int = 2, loops: int = 0, sync: str = "none", cross_warp: bool = False,
+                  grid: int = 1) -> Workload:
+    """Threads publish a value in shared memory and read a neighbour's (the
+    warp-exchange pattern that Sec. 5.2's warp barrier protects): thread t
+    writes S[t], then reads S[t's lane + 1 mod 32 in its own warp] (or, with
+    cross_warp, S[t + 32 mod blockDim], a thread of the next warp).
+
+    sync: "none" (no barrier), "warp" (one syncwarp between the write and the
+    read), "warp2" (one more syncwarp after the read, so the next loop
+    iteration's write is ordered too), "block" (syncthreads between them).
+    With `loops` > 0 the pair sits in a loop `i < loops`; the interval ids
+    count the barriers executed before each access.  Closed forms: race free
+    iff the barriers order every conflicting pair; every granule of S holds
+    one witness otherwise (see tests)."""
+    n = 32 * n_warps
+    w = _Writer(f"warpx_{n_warps}_{loops}_{sync}_{int(cross_warp)}")
+    if loops:
+        w.add(f"loop i {loops}")
+    w.add(f"array S shared {4 * n}")
+    rd = f"(tx + 32) % {n}" if cross_warp else "tx / 32 * 32 + (tx + 1) % 32"
+    i = "i" if loops else "0"
+    per = {"none": 0, "warp": 1, "warp2": 2, "block": 1}[sync]
+    if sync == "block":  # interval ids count the block barriers before the access
+        w.access("W", "S", 4, "tx", iv=f"{i}" if loops else "0", line=1)
+        w.access("R", "S", 4, rd, iv=f"{i} + 1" if loops else "1", line=2)
+    else:
+        w.access("W", "S", 4, "tx", wv=f"{per}*{i}" if loops else "0", line=1)
+        w.access("R", "S", 4, rd, wv=(f"{per}*{i} + {min(per, 1)}" if loops else str(min(per, 1))), line=2)
+    return Workload(w.lines[0].split()[1], w.text(), Binding((grid, 1, 1), (n, 1, 1), ()),
+                    {"sync": sync, "loops": loops, "cross_warp": cross_warp})
+
+
+def random_warp(seed: int, max_instances: int = 4096) -> Workload:
+    """Random kernel with warp barriers: 1D blocks of 1-4 warps (some with a
+    partial last warp), 1-2 blocks, one loop of 1-3 iterations, shared and
+    global accesses whose indices collide inside and across warps (tx,
+    lane + 1, tx / 2, tx % 8, tx + 32, a constant), barrier intervals in
+    {0, 1} and warp intervals in {0..3}, either of them possibly growing with
+    the loop counter."""
+    rng = SplitMix64(seed)
+    bdx = rng.choice([32, 64, 96, 128, 40, 17])
+    grid = (rng.range(1, 2), 1, 1)
+    bound = rng.range(1, 3)
+    nacc = rng.range(2, 6)
+    while bdx * grid[0] * bound * nacc > max_instances and nacc > 2:
+        nacc -= 1
+    w = _Writer(f"warp_{seed & 0xffff}")
+    w.add(f"loop i {bound}")
+    w.add(f"array S shared {4 * 160}")
+    w.add("array G global 4096")
+    forms = ["tx", "tx / 32 * 32 + (tx + 1) % 32", "tx / 2", "tx % 8", "(tx + 32) % 160", "5", "tx + i"]
+    for a_id in range(nacc):
+        arr = rng.choice(["S", "S", "G"])
+        r = rng.below(10)
+        kind = "R" if r < 5 else ("W" if r < 9 else "A")
+        idx = rng.choice(forms)
+        if arr == "G" and rng.below(2):
+            idx = f"bx * 200 + {idx}"
+        iv = str(rng.range(0, 1))
+        if rng.below(4) == 0:
+            iv = f"{iv} + i"
+        wv = str(rng.range(0, 3))
+        if rng.below(3) == 0:
+            wv = f"{wv} + {rng.range(1, 2)}*i"
+        guards = [f"tx {rng.choice(['<', '>='])} {rng.range(1, 40)}"] if rng.below(4) == 0 else []
+        scope = rng.choice(["block", "device"]) if kind == "A" else None
+        w.access(kind, arr, 4, idx, iv=iv, wv=wv, guards=guards, scope=scope, line=a_id + 1)
+    return Workload(f"warp_{seed}", w.text(), Binding(grid, (bdx, 1, 1), ()), {"n_access": nacc})
 
 
 # --------------------------------------------------------------------------
