@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __
     // stable LSD sort on the (cell, interval) bits
     uint64_t* src = S.ka;
     uint64_t* dst = S.kb;
-    const int passes = (P->RB + 7) / 8;
+    const int passes = (P->RB + P->PB - P->SB + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-      cta_sort_pass(S, src, dst, n, P->PB + 8 * p);
+      cta_sort_pass(S, src, dst, n, P->SB + 8 * p);
       uint64_t* t = src;
       src = dst;
       dst = t;
@@ -358,7 +358,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool small_ok(const Bound& B, uint32_t limit) {
   const DProg& P = B.prog;
   return !B.wide && B.nkeys_max <= limit && B.nkeys_max <= (uint64_t)SB_KEYS && P.nunits <= SB_UNITS &&
-         P.RB <= 8 * SB_PASSES && P.nslot <= SB_SLOTS;
+         P.RB + P.PB - P.SB <= 8 * SB_PASSES && P.nslot <= SB_SLOTS;
 }
 
 // The one-CTA verdict of a single small check, written where the device-wide

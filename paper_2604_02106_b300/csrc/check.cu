@@ -384,9 +384,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // the expansion counted digit 0; each pass counts the digit of the next
   for (int p = 0; p < P; p++) {
     CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
-    CK(launch_onesweep(L, in, out, nkeys, nsort, HP.PB + 8 * p, U(W.gbase) + p * 256, U(W.status),
+    CK(launch_onesweep(L, in, out, nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256, U(W.status),
                        cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
-                       p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.PB + 8 * (p + 1)));
+                       p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1)));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
                                 "sort_pass4", "sort_pass5", "sort_pass6", "sort_pass7"};
@@ -596,11 +596,14 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
         for (size_t j = 0; j < Y.size(); j++) {
           const Inst &x = X[i], &y = Y[j];
           if (lo == hi && !key_less(x, y)) continue;
+          // recorded intervals carry the warp interval in their low WVB bits
+          const int64_t ivx = (x.iv - HP.ivmin) >> HP.WVB, ivy = (y.iv - HP.ivmin) >> HP.WVB;
           uint32_t kind = 0;
           if (x.blk == y.blk && x.thr == y.thr) kind = 0;
           else if (x.blk != y.blk) kind = shared ? 0 : 1;
-          else if (x.iv != y.iv) kind = 0;
-          else kind = (x.thr / 32 == y.thr / 32) ? 4 : 2;
+          else if (ivx != ivy) kind = 0;
+          else if (x.thr / 32 != y.thr / 32) kind = 2;
+          else kind = x.iv == y.iv ? 4 : 0;  // same warp: ordered by a warp barrier unless one interval
           if (kind & allow) {
             auto put = [](hgrd_inst& o2, const Inst& s2) {
               o2.lin_block = s2.blk;

@@ -332,6 +332,9 @@ void parse_desc(hgrd_desc& d, const std::string& text) {
         } else if (key == "iv") {
           a.iv = parse_expr(d, body);
           if (d.ast[a.iv].thread) raise(HGRD_EPARSE, "interval must not depend on thread or block ids");
+        } else if (key == "wv") {
+          a.wv = parse_expr(d, body);
+          if (d.ast[a.wv].thread) raise(HGRD_EPARSE, "warp interval must not depend on thread or block ids");
         } else if (key == "idx") {
           a.idx = parse_expr(d, body);
           has_idx = true;
@@ -658,7 +661,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     }
     // fold every access expression
     struct AccF {
-      Lin idx, iv;
+      Lin idx, iv, wv;
       std::vector<Lin> guards;
       bool dead = false;
     };
@@ -667,6 +670,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       const AccessDecl& A = d.acc[a];
       af[a].idx = F.fold(A.idx);
       if (A.iv >= 0) af[a].iv = F.fold(A.iv);
+      if (A.wv >= 0) af[a].wv = F.fold(A.wv);
       for (auto& g : A.guards) {
         for (Lin& l : guard_lins(F.fold(g.lhs), F.fold(g.rhs), g.op)) af[a].guards.push_back(l);
       }
@@ -714,6 +718,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (af[a].dead) continue;
       see(af[a].idx);
       see(af[a].iv);
+      see(af[a].wv);
       for (auto& g : af[a].guards) see(g);
     }
     for (auto& n : F.nodes) mag = std::max(mag, (__int128)std::max(iabs((__int128)n.lo), iabs((__int128)n.hi)));
@@ -817,6 +822,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     P.nacc = (int)d.acc.size();
     std::vector<DLin> guards;
     int64_t ivmin = INT64_MAX, ivmax = INT64_MIN;
+    int64_t wvmin = INT64_MAX, wvmax = INT64_MIN;
     for (size_t a = 0; a < d.acc.size(); a++) {
       DAcc& X = P.acc[a];
       const AccessDecl& A = d.acc[a];
@@ -830,6 +836,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (X.dead) continue;
       compile_lin(af[a].idx, X.idx);
       compile_lin(af[a].iv, X.iv);
+      compile_lin(af[a].wv, X.wv);
       X.gfirst = (int)guards.size();
       X.ng = (int)af[a].guards.size();
       for (auto& g : af[a].guards) {
@@ -845,6 +852,9 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       C.range(af[a].iv, lo, hi);
       ivmin = std::min(ivmin, lo);
       ivmax = std::max(ivmax, hi);
+      C.range(af[a].wv, lo, hi);
+      wvmin = std::min(wvmin, lo);
+      wvmax = std::max(wvmax, hi);
     }
     // facts kept for the ranker's pair features
     B.acc_info.resize(d.acc.size());
@@ -953,7 +963,15 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     P.AB = ceil_log2((uint64_t)P.nacc);
     P.TB = ceil_log2((uint64_t)nthr);
     P.BB = ceil_log2((uint64_t)nblk);
-    P.PB = P.AB + P.TB + P.BB;
+    // warp-barrier intervals matter only where accesses of one warp can sit
+    // in different ones (one warp with a single thread has no intra-warp pair)
+    if (wvmin > wvmax || nthr < 2) wvmin = wvmax = 0;
+    P.wvmin = wvmin;
+    P.WVB = ceil_log2((uint64_t)(wvmax - wvmin) + 1);
+    if (P.WVB > 16) raise(HGRD_EUNSUPPORTED, "more than 2^16 warp-barrier intervals");
+    if (P.WVB && P.IVB + P.WVB > 62) raise(HGRD_EOVERFLOW, "interval ids need more than 62 bits");
+    P.PB = P.AB + P.TB + P.WVB + P.BB;
+    P.SB = P.WVB ? P.AB + P.TB : P.PB;
     P.RB = ceil_log2(std::max<uint64_t>(cells, 1)) + P.IVB;
     if (P.RB + P.PB > 64) raise(HGRD_EOVERFLOW, "sort key needs more than 64 bits for this binding");
     // key count bound: every live instance of every access, all granules
@@ -1001,13 +1019,15 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         if (!P.acc[a].dead && P.acc[a].shared) per_block += (unsigned __int128)nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
       const uint64_t smem = sizeof(DProg) + (uint64_t)EXP_THREADS * nslot * (wide ? 8 : 4) +
                             (uint64_t)P.nsbins * 13 + 2048;
-      P.smode = any_shared_live && upb >= 4 && P.nsbins > 0 && P.nsbins <= SBIN_MAX &&
+      P.smode = !P.WVB && any_shared_live && upb >= 4 && P.nsbins > 0 && P.nsbins <= SBIN_MAX &&
                 (unsigned __int128)P.nsbins * (uint64_t)nblk <= ((unsigned __int128)1 << 25) &&
                 per_block < 0xffffffffu && smem <= 200 * 1024;
       P.RBG = P.smode ? ceil_log2(std::max<uint64_t>(P.shared_cell_base, 1)) + P.IVB : P.RB;
     }
-    B.sort_passes = (P.RB + 7) / 8;
-    B.sort_passes_split = (P.RBG + 7) / 8;
+    // radix passes from bit SB: the run code, and with warp-barrier
+    // intervals also the block and warp-interval fields below it
+    B.sort_passes = (P.RB + P.PB - P.SB + 7) / 8;
+    B.sort_passes_split = (P.RBG + P.PB - P.SB + 7) / 8;
     B.wide = wide;
     // integer operations of evaluating every instance once (the count pass's
     // algorithmic work): a term is one multiply-add, a guard or bound test
@@ -1025,7 +1045,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       for (int a = 0; a < P.nacc; a++) {
         const DAcc& A = P.acc[a];
         if (A.dead) continue;
-        per_it += (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n;
+        per_it += (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n + (P.WVB ? (uint64_t)A.wv.n + 2 : 0);
         for (int g = 0; g < A.ng; g++) per_it += (uint64_t)P.guard[A.gfirst + g].n + 1;
       }
       B.eval_ops = (uint64_t)nblk * (uint64_t)nthr * (fixed + (uint64_t)nit * per_it);

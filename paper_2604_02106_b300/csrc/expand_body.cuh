@@ -67,7 +67,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
     t_hi = (uint32_t)(w0 >> 3) & 31;
   }
   const int64_t nunits = P->nunits;
-  const int PB = P->PB;
+  const int SB = P->SB;  // lowest sorted key bit
   const uint32_t emask = P->emask;
   uint64_t oob = 0, drop = 0;
   const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                            keys[cursor + (uint64_t)rank * G + j] = key;
                          } else {
                            for (int p = 0; p < npass; ++p)
-                             atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (PB + 8 * p)) & 255u)], mult);
+                             atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (SB + 8 * p)) & 255u)], mult);
                          }
                        }
                      }
@@ -184,7 +184,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
   uint32_t* s_cur = bins;
   const int64_t nblk = P->nblk;
   const int64_t upb = (int64_t)P->wpb * P->nchunk;
-  const int PB = P->PB;
+  const int SB = P->SB;  // lowest sorted key bit
   const uint32_t wmask = P->wmask;
   const uint32_t emask = P->emask;
   uint64_t oob = 0, drop = 0;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                            if (MODE == 4)
                              keys_g[cursor + (uint64_t)rank * G + j] = key;
                            else
-                             atomicAdd(&shist[(uint32_t)(key >> PB) & 255u], mult);
+                             atomicAdd(&shist[(uint32_t)(key >> SB) & 255u], mult);
                          }
                        }
                        cursor += (uint64_t)__popc(bal) * G * mult;

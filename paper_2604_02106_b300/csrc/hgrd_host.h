@@ -33,7 +33,7 @@ struct AccessDecl {
   int arr = -1;
   int64_t width = 0;
   int scope = 1;  // 0 block, 1 device (atomics)
-  int idx = -1, iv = -1;
+  int idx = -1, iv = -1, wv = -1;  // wv: warp-barrier interval (Sec. 5.2)
   int line = 0;
   std::vector<CondDecl> guards;
 };

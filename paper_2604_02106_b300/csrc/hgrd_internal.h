@@ -76,7 +76,7 @@ struct DOp {
   Magic mg;
 };
 struct DAcc {
-  DLin idx, iv;
+  DLin idx, iv, wv;  // index, block-barrier interval, warp-barrier interval
   int32_t gfirst, ng;  // guards: each DLin must be >= 0
   int32_t G;           // granule keys per instance (width / granule)
   int32_t arr;         // descriptor array id
@@ -101,7 +101,9 @@ struct alignas(16) DProg {
   int64_t nchunk;  // chunks per (block, warp)
   int32_t wide, nfix, niter, nslot;
   int32_t nterm, nguard, pad0, pad1;
-  // key layout: key = ((cell << IVB | iv - ivmin) << PB) | lin_b << (TB+AB) | lin_t << AB | access
+  // key layout: key = ((cell << IVB | iv - ivmin) << PB) | lin_b << (WVB+TB+AB)
+  //                   | (wv - wvmin) << (TB+AB) | lin_t << AB | access
+  // (WVB = 0 unless warp barriers split some warp's accesses)
   int32_t AB, TB, BB, IVB, PB, RB;
   int64_t ivmin;
   uint64_t shared_cell_base;  // cell codes at or above this belong to shared arrays
@@ -117,6 +119,11 @@ struct alignas(16) DProg {
   int64_t nsbins;             // bins of one block: shared granules x intervals
   int32_t RBG, pad2;          // run-code bits of the global-array keys (the sorted ones)
   uint64_t scap;              // room for keys of candidate bins (more: HGRD_ENOMEM)
+  // warp-barrier intervals (Sec. 5.2): WVB bits of wv - wvmin sit between the
+  // block and the thread, and the sort then orders keys by (run, interval,
+  // block, warp interval) from bit SB up; without them SB = PB
+  int32_t WVB, SB;
+  int64_t wvmin;
   uint32_t einter[MAXACC], eintra[MAXACC];
   uint64_t lay_cbase[MAXARR + 1];
   uint64_t lay_ngran[MAXARR];

@@ -140,7 +140,7 @@ std::string jit_source(const DProg& P, bool split) {
   auto invariant = [&](int a) {
     const DAcc& A = P.acc[a];
     if (count_only(a)) return true;
-    return !lin_dep(A.idx) && !lin_dep(A.iv) && guards_invariant(a);
+    return !lin_dep(A.idx) && !lin_dep(A.iv) && !(P.WVB && lin_dep(A.wv)) && guards_invariant(a);
   };
   // one access: per loop vector (once = false), or once per unit standing for
   // the unit's nrep loop vectors (once = true, count pass only)
@@ -166,7 +166,11 @@ std::string jit_source(const DProg& P, bool split) {
     else
       c += ind + "  const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
     c += ind + "  oob += (live && !inb) ? " + std::string(once ? "nrep" : "1") + " : 0;\n";
-    const std::string iv = no_idx ? std::string("(int64_t)0") : "(int64_t)" + lin(P, at + ".iv", A.iv);
+    // with warp-barrier intervals the key's interval field carries both ids
+    const std::string iv = no_idx   ? std::string("(int64_t)0")
+                           : P.WVB ? "pack_wv(P, (int64_t)" + lin(P, at + ".iv", A.iv) + ", (int64_t)" +
+                                         lin(P, at + ".wv", A.wv) + ")"
+                                   : "(int64_t)" + lin(P, at + ".iv", A.iv);
     bool closing = false;
     if (combinable(a) && once) {
       c += ind + "  if constexpr (COMBINE) {\n";

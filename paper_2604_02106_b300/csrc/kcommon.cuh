@@ -87,6 +87,12 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, ui
   return r;
 }
 
+// With warp-barrier intervals the interval handed to the key is
+// ivmin + ((iv - ivmin) << WVB | wv - wvmin): make_key splits it again.
+__device__ __forceinline__ int64_t pack_wv(const DProg* __restrict__ P, int64_t iv, int64_t wv) {
+  return P->ivmin + (int64_t)((uint64_t)(iv - P->ivmin) << P->WVB | (uint64_t)(wv - P->wvmin));
+}
+
 // Expansion of unit u = (block b, warp w of the block) of the user kernel,
 // lane = simulated thread.  For every loop vector and every access in `only`
 // (bit per access id), evaluates guards and index and calls
@@ -155,6 +161,7 @@ __device__ __forceinline__ uint64_t expand_unit(const DProg* __restrict__ P, T* 
       if (inb) {
         const DLin vl = A.iv;
         iv = (int64_t)lin_eval<T>(P, vl, sl, lane);
+        if (P->WVB) iv = pack_wv(P, iv, (int64_t)lin_eval<T>(P, A.wv, sl, lane));
       }
       step(a, A, inb, bal, (int64_t)idx, iv, b, lt, ic);
     }
@@ -163,13 +170,15 @@ __device__ __forceinline__ uint64_t expand_unit(const DProg* __restrict__ P, T* 
 }
 
 // granule j of a live in-bounds instance as a sort key:
-// ((cell << IVB | interval - ivmin) << PB) | block << (TB+AB) | thread << AB | access
+// ((cell << IVB | interval - ivmin) << PB) | block << (WVB+TB+AB) | warp interval << (TB+AB)
+//   | thread << AB | access
 __device__ __forceinline__ uint64_t make_key(const DProg* __restrict__ P, const DAcc& A, int a, int64_t idx,
                                              int64_t iv, int64_t b, int lt, int j) {
   const uint64_t cell = A.cbase + (A.shared ? (uint64_t)b * A.ngran : 0ull) + (uint64_t)idx * (uint64_t)A.G + j;
-  const uint64_t ivc = (uint64_t)(iv - P->ivmin);
-  return (((cell << P->IVB) | ivc) << P->PB) | ((uint64_t)b << (P->TB + P->AB)) | ((uint64_t)lt << P->AB) |
-         (uint64_t)a;
+  const uint64_t ivw = (uint64_t)(iv - P->ivmin);  // (interval << WVB) | warp interval
+  const int WVB = P->WVB, TA = P->TB + P->AB;
+  return (((cell << P->IVB) | (ivw >> WVB)) << P->PB) | ((uint64_t)b << (WVB + TA)) |
+         (lowbits(ivw, WVB) << TA) | ((uint64_t)lt << P->AB) | (uint64_t)a;
 }
 
 // min / max of one id over a group of instances
@@ -204,7 +213,9 @@ __device__ __forceinline__ uint32_t racy_row(const Sum& s, int lane) {
 // Exact race kinds of the run starting at key s (end e, or 0 = until the run
 // id changes) of sorted keys[0, n).  Lane a gets, for each access b, whether
 // the pair (a, b) races across blocks (global memory, any interval), inside a
-// block between warps, or inside a warp, in the same interval (Table 2).
+// block between warps, or inside a warp, in the same interval (Table 2) and,
+// for the intra-warp kind, the same warp interval (Sec. 5.2: a warp barrier
+// orders the threads of one warp only).
 struct RunMasks {
   uint64_t rid;
   uint32_t inter, blk, warp;
@@ -212,12 +223,15 @@ struct RunMasks {
 __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, uint64_t e, uint64_t n,
                                               const DProg* __restrict__ P, int lane, uint32_t einter,
                                               uint32_t eintra, bool stop_first = false) {
-  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB;
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB, WVB = P->WVB;
   const int rsh = PB + IVB;
   RunMasks R;
   R.rid = shr64(keys[s], rsh);
   const bool glob = R.rid < P->shared_cell_base;
-  Sum tw, wb, br;  // thread per (iv, block, warp); warp per (iv, block); block per run
+  // thread per (iv, block, warp interval, warp); warp per (iv, block); block
+  // per run.  Keys of one (iv, block) are contiguous and ordered by warp
+  // interval, each warp's keys contiguous inside a warp interval.
+  Sum tw, wb, br;
   tw.reset();
   wb.reset();
   br.reset();
@@ -234,9 +248,10 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
     for (int jj = 0; jj < cnt; ++jj) {
       const uint64_t key = __shfl_sync(FULL, kk, jj);
       const uint64_t sub = shr64(key, PB);
-      const uint32_t b = (uint32_t)lowbits(key >> (AB + TB), BB);
+      const uint32_t b = (uint32_t)lowbits(key >> (AB + TB + WVB), BB);
       const uint32_t t = (uint32_t)lowbits(key >> AB, TB);
       const uint32_t wpi = t >> 5;
+      const uint32_t wgi = (uint32_t)lowbits(key >> (AB + TB), WVB) << 16 | wpi;  // (warp interval, warp)
       const uint32_t a = (uint32_t)lowbits(key, AB);
       if (sub != cur_sub || b != cur_b) {
         m_warp |= racy_row(tw, lane) & eintra;
@@ -245,11 +260,11 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
         wb.reset();
         cur_sub = sub;
         cur_b = b;
-        cur_w = wpi;
-      } else if (wpi != cur_w) {
+        cur_w = wgi;
+      } else if (wgi != cur_w) {
         m_warp |= racy_row(tw, lane) & eintra;
         tw.reset();
-        cur_w = wpi;
+        cur_w = wgi;
       }
       if ((uint32_t)lane == a) {
         tw.add(t);

@@ -540,8 +540,10 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
   // field tests on k ^ previous key: run id, run+interval, block+thread, block
   X.m_run = rsh >= 64 ? 0 : ~0ull << rsh;
   X.m_sub = PB >= 64 ? 0 : ~0ull << PB;
-  X.m_thr = lowbits(~0ull, BB + TB) << AB;
-  X.m_blk = lowbits(~0ull, BB) << (AB + TB);
+  // (block, warp interval, thread) and block fields: a change of warp
+  // interval counts as a change of thread (candidacy is a superset test)
+  X.m_thr = lowbits(~0ull, BB + P->WVB + TB) << AB;
+  X.m_blk = lowbits(~0ull, BB) << (AB + TB + P->WVB);
   // keys below g_lim belong to global-memory runs
   X.g_all = rsh >= 64 ? shbase > 0 : (rsh > 0 && shbase >= (1ull << (64 - rsh)));
   X.g_lim = X.g_all ? ~0ull : (rsh >= 64 ? 0ull : shbase << rsh);
@@ -765,7 +767,7 @@ __global__ void __launch_bounds__(256) pair_blocks_kernel(const uint64_t* __rest
   const uint32_t m = (uint32_t)(hi - lo);
   uint32_t p2 = 1;
   while (p2 < m) p2 <<= 1;
-  const int bsh = P->AB + P->TB;
+  const int bsh = P->AB + P->TB + P->WVB;  // block field
   for (uint32_t i = threadIdx.x; i < p2; i += 256) sb[i] = i < m ? lowbits(keys[lo + i] >> bsh, P->BB) : ~0ull;
   __syncthreads();
   for (uint32_t k = 2; k <= p2; k <<= 1)

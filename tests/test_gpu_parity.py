@@ -376,3 +376,34 @@ def test_small_check_falls_back_when_it_keeps_too_few_witnesses():
     g = hg.check(text, b, cap=1 << 20)
     assert hg.stats()["small"] == 0
     _same(g, oracle.check(text, b, cap=1 << 20))
+
+
+# ---------------------------------------------------------------- warp barriers (Sec. 5.2)
+
+@pytest.mark.parametrize("seed", range(60))
+def test_warp_barrier_random_launches(seed):
+    w = workloads.random_warp(3000 + seed)
+    _same(*_both(w.text, w.binding))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_warp_barrier_random_specialised(seed):
+    w = workloads.random_warp(3500 + seed, max_instances=20000)
+    g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.JIT)
+    _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+
+
+@pytest.mark.parametrize("space", ["shared", "global"])
+@pytest.mark.parametrize("sync,cross", [("none", False), ("warp", False), ("warp2", False), ("warp2", True),
+                                        ("block", True)])
+def test_warp_exchange_many_blocks(space, sync, cross):
+    # 48 blocks of 32 warps, 4 loop iterations: keys span many sort tiles and
+    # every block's exchange is checked; both expansion paths
+    w = workloads.warp_exchange(32, 4, sync, cross, grid=48, space=space)
+    o = oracle.check(w.text, w.binding, cap=1 << 20)
+    for flags in (0, hg.NO_JIT | hg.NO_SMALL, hg.JIT):
+        g = hg.check(w.text, w.binding, cap=1 << 20, flags=flags)
+        _same(g, o)
+    # warp intervals change the key layout: the sort covers block and warp interval
+    if sync in ("warp", "warp2"):
+        assert hg.stats()["sort_passes"] >= 3

@@ -28,6 +28,8 @@ def _bind(w):
     lambda: workloads.config1(0),
     lambda: workloads.random_shared(5003),
     lambda: workloads.random_tiny(1007, max_instances=500),
+    lambda: workloads.random_warp(3003),
+    lambda: workloads.warp_exchange(4, 3, "warp2", False, grid=2, space="global"),
 ])
 def test_generated_source_compiles(make):
     k = _bind(make())
@@ -52,3 +54,11 @@ def test_generated_source_covers_every_live_access():
     for a in range(16):
         assert f"// access {a}\n" in src
     assert "hgrd_jit_expand3" in src and "hgrd_jit_expand4" in src and "hgrd_jit_expand0" not in src
+
+
+def test_warp_intervals_reach_the_key():
+    # a program with warp-barrier intervals packs them next to the interval
+    k = _bind(workloads.warp_exchange(4, 3, "warp2", False, grid=2))
+    assert "pack_wv(" in k.jit_source()
+    k0 = _bind(workloads.warp_exchange(4, 3, "none", False, grid=2))
+    assert "pack_wv(" not in k0.jit_source()

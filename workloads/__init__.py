@@ -481,7 +481,7 @@ def random_shared(seed: int, max_instances: int = 60000) -> Workload:
 
 
 def warp_exchange(n_warps: int = 2, loops: int = 0, sync: str = "none", cross_warp: bool = False,
-                  grid: int = 1) -> Workload:
+                  grid: int = 1, space: str = "shared") -> Workload:
     """Threads publish a value in shared memory and read a neighbour's (the
     warp-exchange pattern that Sec. 5.2's warp barrier protects): thread t
     writes S[t], then reads S[t's lane + 1 mod 32 in its own warp] (or, with
@@ -490,24 +490,29 @@ def warp_exchange(n_warps: int = 2, loops: int = 0, sync: str = "none", cross_wa
     sync: "none" (no barrier), "warp" (one syncwarp between the write and the
     read), "warp2" (one more syncwarp after the read, so the next loop
     iteration's write is ordered too), "block" (syncthreads between them).
+    space "global": S is a global array, block b exchanging in S[b*n, b*n + n)
+    (no two blocks share an element).
     With `loops` > 0 the pair sits in a loop `i < loops`; the interval ids
     count the barriers executed before each access.  Closed forms: race free
     iff the barriers order every conflicting pair; every granule of S holds
     one witness otherwise (see tests)."""
     n = 32 * n_warps
-    w = _Writer(f"warpx_{n_warps}_{loops}_{sync}_{int(cross_warp)}")
+    w = _Writer(f"warpx_{n_warps}_{loops}_{sync}_{int(cross_warp)}_{space}")
     if loops:
         w.add(f"loop i {loops}")
-    w.add(f"array S shared {4 * n}")
+    glob = space == "global"
+    w.add(f"array S global {4 * n * grid}" if glob else f"array S shared {4 * n}")
     rd = f"(tx + 32) % {n}" if cross_warp else "tx / 32 * 32 + (tx + 1) % 32"
+    base = f"bx * {n} + " if glob else ""
     i = "i" if loops else "0"
     per = {"none": 0, "warp": 1, "warp2": 2, "block": 1}[sync]
     if sync == "block":  # interval ids count the block barriers before the access
-        w.access("W", "S", 4, "tx", iv=f"{i}" if loops else "0", line=1)
-        w.access("R", "S", 4, rd, iv=f"{i} + 1" if loops else "1", line=2)
+        w.access("W", "S", 4, base + "tx", iv=f"{i}" if loops else "0", line=1)
+        w.access("R", "S", 4, base + f"({rd})", iv=f"{i} + 1" if loops else "1", line=2)
     else:
-        w.access("W", "S", 4, "tx", wv=f"{per}*{i}" if loops else "0", line=1)
-        w.access("R", "S", 4, rd, wv=(f"{per}*{i} + {min(per, 1)}" if loops else str(min(per, 1))), line=2)
+        w.access("W", "S", 4, base + "tx", wv=f"{per}*{i}" if loops else "0", line=1)
+        w.access("R", "S", 4, base + f"({rd})", wv=(f"{per}*{i} + {min(per, 1)}" if loops else str(min(per, 1))),
+                 line=2)
     return Workload(w.lines[0].split()[1], w.text(), Binding((grid, 1, 1), (n, 1, 1), ()),
                     {"sync": sync, "loops": loops, "cross_warp": cross_warp})
 
