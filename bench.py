@@ -29,7 +29,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "access instances checked/s"
 UNIT = "instances/s"
+L2_FLUSH_BYTES = 256 << 20  # written before every timed step: twice the 126 MB L2
 WORKLOAD = "tiled-stencil 64x64 blocks x 16x16 threads, loop k<32, 16 accesses (536,870,912 instances)"
+# warp-exchange kernel with warp barriers (Sec. 5.2): 1184 blocks (8 per SM) of
+# 1024 threads, loop i < 16, write S[b*1024 + t] / syncwarp / read the next
+# lane's element / syncwarp, global memory; race free
+WARP_GRID, WARP_LOOPS = 1184, 16
+WARP_WORKLOAD = (f"warp exchange with syncwarp: {WARP_GRID} blocks x 1024 threads, loop i<{WARP_LOOPS}, "
+                 f"2 accesses ({WARP_GRID * 1024 * WARP_LOOPS * 2:,} instances)")
 
 
 def _peaks():
@@ -163,6 +170,31 @@ def _alu_peak():
     return 148 * 4 * 32 * sm_mhz * 1e6 / 1e12
 
 
+def l2_flusher(s):
+    """A function that writes L2_FLUSH_BYTES on stream s (evicts the 126 MB L2)."""
+    import torch
+    buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        with torch.cuda.stream(s):
+            buf.zero_()
+    return flush
+
+
+def timed_steps(s, steps, fn, flush):
+    """Device ms per step of fn() on stream s: L2 flushed before every step,
+    each step between its own CUDA events (the flush outside them)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush()
+        a.record(s)
+        fn()
+        b.record(s)
+    evs[-1][1].synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
 def run_suite(args):
     """Batched form vs the plain checker on a set of items (time to all verdicts)."""
     import torch
@@ -186,15 +218,13 @@ def run_suite(args):
         k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
         res_plain.append(k.collect(wsp, cap=64, stream=s, flags=hg.NO_PAIR))
     n_inst = sum(r.n_instances for r in res_plain)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = l2_flusher(s)
     torch.cuda.synchronize()
-    e0.record(s)
-    for _ in range(args.steps):
+
+    def plain_pass():
         for k in ks:
             k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
-    e1.record(s)
-    e1.synchronize()
-    plain_ms = e0.elapsed_time(e1) / args.steps
+    plain_ms = timed_steps(s, args.steps, plain_pass, flush)
     # batched: tuned, captured into one CUDA graph, replayed; with the large
     # items on interpreted or on specialised expansion kernels
     def timed_batch(jit):
@@ -210,19 +240,18 @@ def run_suite(args):
             b.run(stream=s)
         torch.cuda.synchronize()
         with ClockSampler(0) as clk:
-            e0.record(s)
-            for _ in range(args.steps):
-                b.run(stream=s)
-            e1.record(s)
-            e1.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+            ms = timed_steps(s, args.steps, lambda: b.run(stream=s), flush)
         t_w = time.perf_counter()
         while time.perf_counter() - t_w < 1.0:  # clocks back at steady state after the sampler's idle gap
             b.check(stream=s)
-        t0 = time.perf_counter()
+        e2e_s = 0.0
         for _ in range(args.steps):
+            flush()
+            s.synchronize()
+            t0 = time.perf_counter()
             b.check(stream=s)
-        e2e_s = (time.perf_counter() - t0) / args.steps
+            e2e_s += time.perf_counter() - t0
+        e2e_s /= args.steps
         return {"ms": ms, "choice": choice, "res": res_b, "e2e_s": e2e_s, "clk": clk.summary(),
                 "create_ms": compile_ms}
     interp = timed_batch(False)
@@ -408,7 +437,7 @@ def main():
     ap.add_argument("--heldout", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--topk", type=int, default=4)
-    ap.add_argument("--suite", default="stencil", choices=["stencil", "sweep", "corpus", "ranked", "symbolic"])
+    ap.add_argument("--suite", default="stencil", choices=["stencil", "warp", "sweep", "corpus", "ranked", "symbolic"])
     ap.add_argument("--items", type=int, default=1000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -437,7 +466,7 @@ def main():
     if args.suite == "symbolic":
         run_symbolic(args)
         return
-    if args.suite != "stencil":
+    if args.suite not in ("stencil", "warp"):
         run_suite(args)
         return
     if args.once:
@@ -458,7 +487,12 @@ def main():
     if not args.no_sort_tune:
         best, ms = hg.sort_tune()
         tuned = {"variant": best, "pass_ms_32M_keys": [round(x, 4) for x in ms]}
-    w = workloads.config2(rank, planted=True, W=args.side, H=args.side)
+    if args.suite == "warp":
+        w = workloads.warp_exchange(32, WARP_LOOPS, "warp2", False, grid=WARP_GRID, space="global")
+        workload = WARP_WORKLOAD
+    else:
+        w = workloads.config2(rank, planted=True, W=args.side, H=args.side)
+        workload = WORKLOAD
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     # specialised expansion kernels: compiled once per program structure,
     # before the timed region (every later check of the binding uses them)
@@ -475,18 +509,14 @@ def main():
     n_keys = res.n_keys
     n_sorted, n_binned = st0["n_sorted_keys"], st0["n_binned_keys"]
 
-    # ---- device-timed steps
+    # ---- device-timed steps: L2 flushed before every step (a write larger
+    # than the 126 MB L2), each step bracketed by its own events
+    flush_l2 = l2_flusher(s)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        e0.record(s)
-        for _ in range(args.steps):
-            k.enqueue(ws, stream=s)
-        e1.record(s)
-        e1.synchronize()
-    ms = e0.elapsed_time(e1)
+        ms = args.steps * timed_steps(s, args.steps, lambda: k.enqueue(ws, stream=s), flush_l2)
     res2 = k.collect(ws, cap=1 << 16, stream=s)
     assert res2.witnesses == res.witnesses
     torch.cuda.synchronize()
@@ -500,6 +530,7 @@ def main():
     # ---- per-stage times (CUDA events on the launch stream, same steps again)
     stages = {}
     for _ in range(args.steps):
+        flush_l2()
         k.enqueue(ws, stream=s, flags=hg.PROFILE)
         for name, t in hg.last_profile():
             stages.setdefault(name, []).append(t)
@@ -556,6 +587,8 @@ def main():
         n_w += 1
     torch.cuda.synchronize()
     for _ in range(args.steps):
+        flush_l2()
+        s.synchronize()
         t0 = time.perf_counter()
         r = k.check(cap=1 << 16, stream=s)
         t_e2e.append(time.perf_counter() - t0)
@@ -574,13 +607,14 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "instances": n_inst, "keys": n_keys,
+                "config": {"workload": workload, "instances": n_inst, "keys": n_keys,
                            "witnesses": res.n_witness, "sort_passes": st0["sort_passes"],
                            "sorted_keys": n_sorted, "binned_keys": n_binned,
                            "shared_bins": bool(st0["shared_bins"]),
                            "expansion": "specialised" if st0["jit"] else "interpreted",
                            "jit_compile_ms": None if jit_ms is None else round(jit_ms, 1),
-                           "l2": f"sorted keys {8 * n_sorted / 1e9:.2f} GB per buffer > 126 MB L2; no flush needed",
+                           "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write, outside the "
+                                 f"per-step events); sorted keys {8 * n_sorted / 1e6:.1f} MB per buffer",
                            "parallelism": f"replicas{world}", "sort_tuning": tuned},
                 "e2e": e2e,
                 "roofline": roofline,
@@ -588,7 +622,7 @@ def main():
                 "stages_ms": {n: round(t, 4) for n, t in stage_ms.items()},
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches * args.steps)}
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and args.suite == "stencil":
             line["cpu_baseline"] = cpu_baseline(args.ref_side)
         print(json.dumps(line), flush=True)
     if dist:

@@ -399,7 +399,7 @@ struct CandCarry {
 };
 
 struct CandCtx {
-  uint64_t n, r0, r1, m_run, m_sub, m_thr, m_blk, g_lim;
+  uint64_t n, r0, r1, m_run, m_sub, m_blk, m_wv, m_t, m_w, g_lim;
   uint32_t wmask, amask;
   bool g_all;
   unsigned below;
@@ -420,7 +420,10 @@ __device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64
   const uint64_t x = k ^ pk;
   const bool rs = valid && (i == 0 || (x & X.m_run) != 0);
   const bool ss = valid && (rs || (x & X.m_sub) != 0);
-  const bool td = valid && !ss && (x & X.m_thr) != 0;
+  // two instances of one sub-run that may race inside a block: another block
+  // (a superset), else in one warp interval another thread, else another warp
+  // (a warp barrier orders the threads of one warp only)
+  const bool td = valid && !ss && ((x & X.m_blk) != 0 || (x & ((x & X.m_wv) ? X.m_w : X.m_t)) != 0);
   const bool bd = valid && !rs && (x & X.m_blk) != 0;
   const bool w = valid && ((X.wmask >> ((uint32_t)k & X.amask)) & 1u);
   const unsigned RS = __ballot_sync(FULL, rs), SS = __ballot_sync(FULL, ss), TD = __ballot_sync(FULL, td);
@@ -540,10 +543,11 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
   // field tests on k ^ previous key: run id, run+interval, block+thread, block
   X.m_run = rsh >= 64 ? 0 : ~0ull << rsh;
   X.m_sub = PB >= 64 ? 0 : ~0ull << PB;
-  // (block, warp interval, thread) and block fields: a change of warp
-  // interval counts as a change of thread (candidacy is a superset test)
-  X.m_thr = lowbits(~0ull, BB + P->WVB + TB) << AB;
+  // block, warp-interval, thread and warp fields
   X.m_blk = lowbits(~0ull, BB) << (AB + TB + P->WVB);
+  X.m_wv = lowbits(~0ull, P->WVB) << (AB + TB);
+  X.m_t = lowbits(~0ull, TB) << AB;
+  X.m_w = TB > 5 ? (lowbits(~0ull, TB - 5) << (AB + 5)) : 0ull;
   // keys below g_lim belong to global-memory runs
   X.g_all = rsh >= 64 ? shbase > 0 : (rsh > 0 && shbase >= (1ull << (64 - rsh)));
   X.g_lim = X.g_all ? ~0ull : (rsh >= 64 ? 0ull : shbase << rsh);

@@ -321,3 +321,14 @@ def test_invariant_distinct_warp_intervals_drop_only_intra_warp(seed):
         if m2:
             want[key] = m2
     assert got == want
+
+
+@pytest.mark.parametrize("space", ["shared", "global"])
+def test_warp_exchange_expected_counts(space):
+    # the witness count the bench asserts for its warp-barrier workload
+    for nw in (1, 2, 3):
+        for loops in (0, 1, 3):
+            for sync in ("none", "warp", "warp2", "block"):
+                for cross in (False, True):
+                    w = workloads.warp_exchange(nw, loops, sync, cross, grid=2, space=space)
+                    assert oracle.check(w.text, w.binding).n_witness == w.meta["expected_witnesses"]

@@ -513,8 +513,13 @@ def warp_exchange(n_warps: int = 2, loops: int = 0, sync: str = "none", cross_wa
         w.access("W", "S", 4, base + "tx", wv=f"{per}*{i}" if loops else "0", line=1)
         w.access("R", "S", 4, base + f"({rd})", wv=(f"{per}*{i} + {min(per, 1)}" if loops else str(min(per, 1))),
                  line=2)
+    # closed form (a thread of a one-warp block reading "the next warp" reads its own element)
+    racy = not (cross_warp and n_warps == 1) and (
+        sync == "none" or (cross_warp and sync != "block") or
+        (loops > 1 and (sync == "block" or sync == "warp")))
     return Workload(w.lines[0].split()[1], w.text(), Binding((grid, 1, 1), (n, 1, 1), ()),
-                    {"sync": sync, "loops": loops, "cross_warp": cross_warp})
+                    {"sync": sync, "loops": loops, "cross_warp": cross_warp,
+                     "expected_witnesses": (n * (grid if glob else 1)) if racy else 0})
 
 
 def random_warp(seed: int, max_instances: int = 4096) -> Workload:
