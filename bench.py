@@ -564,7 +564,9 @@ def main():
             roofline.update(achieved=a, frac=a / hbm_peak, bytes_per_key=STAGE_BYTES[dom],
                             keys_per_launch=stage_keys[dom])
     else:
-        # the count pass evaluates every instance: integer-issue bound
+        # the count pass evaluates the program: integer-issue bound; its work
+        # is the integer operations of the walk that runs (on the specialised
+        # kernels loop-invariant and loop-guarded accesses once per thread)
         ops = st0["eval_ops"]
         a = ops / (stage_ms[dom] / 1000.0) / 1e12
         pk = _alu_peak()

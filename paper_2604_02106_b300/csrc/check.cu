@@ -299,6 +299,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     }
   }
   g_stats.jit = jit ? 1u : 0u;
+  if (jit) {  // the specialised walk evaluates loop-invariant and ranged accesses once per thread
+    if (!B.eval_ops_jit) B.eval_ops_jit = jit_eval_ops(HP);
+    g_stats.eval_ops = B.eval_ops_jit;
+  }
   const uint32_t only_mask = (jit && restricted) ? only : 0xffffffffu;
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
   g_prof.reset(o && (o->flags & HGRD_PROFILE), s);

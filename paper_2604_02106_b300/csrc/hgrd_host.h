@@ -59,6 +59,7 @@ struct Bound {
   // (one sort of everything) or of global-array accesses (block-local mode)
   uint64_t nsort_max_all = 0, nsort_max_split = 0;
   uint64_t eval_ops = 0;  // integer operations of evaluating every instance once
+  mutable uint64_t eval_ops_jit = 0;  // the same on the specialised kernels (0: not computed yet)
   int sort_passes = 0;        // radix passes over all keys
   int sort_passes_split = 0;  // radix passes over the global-array keys (block-local mode)
   bool wide = false;

@@ -63,6 +63,61 @@ std::string op_code(const DProg& P, int k, bool declare) {
   return std::string("      ") + (declare ? "const T " : "") + "s" + S(op.dst) + " = " + v + ";\n";
 }
 
+// What the generated walk does with each access: which slots depend on the
+// loop counters, and which accesses are evaluated once per unit (loop
+// invariant; count-only; ranged: one instance repeated over the counters its
+// loop guards admit) rather than once per loop vector.
+struct Analysis {
+  const DProg& P;
+  int nl;
+  std::vector<char> dep;  // slot depends on the loop counters
+  explicit Analysis(const DProg& p) : P(p), nl(p.nloop), dep(MAXSLOT + 16, 0) {
+    for (int l = 0; l < nl; l++) dep[6 + l] = 1;
+    for (int k = 0; k < P.nfix + P.niter; k++)
+      if (lin_dep(P.ops[k].lin)) dep[P.ops[k].dst] = 1;
+  }
+  // per shared-array access with one granule per instance: bin updates combine
+  bool combinable(int a) const {
+    const DAcc& A = P.acc[a];
+    return !A.dead && A.shared && A.G == 1 && ((P.emask >> a) & 1u);
+  }
+  bool lin_dep(const DLin& L) const {
+    for (int t = 0; t < L.n; t++)
+      if (dep[P.term[L.first + t].slot]) return true;
+    return false;
+  }
+  bool guards_invariant(int a) const {
+    const DAcc& A = P.acc[a];
+    for (int g = 0; g < A.ng; g++)
+      if (lin_dep(P.guard[A.gfirst + g])) return false;
+    return true;
+  }
+  // keys dropped, index always in bounds, guards loop-invariant: only counted
+  bool count_only(int a) const {
+    const DAcc& A = P.acc[a];
+    return !((P.emask >> a) & 1u) && A.bounds_free && guards_invariant(a);
+  }
+  // guards, index and intervals read no loop-dependent slot
+  bool invariant(int a) const {
+    const DAcc& A = P.acc[a];
+    if (count_only(a)) return true;
+    return !lin_dep(A.idx) && !lin_dep(A.iv) && !(P.WVB && lin_dep(A.wv)) && guards_invariant(a);
+  }
+  // with one loop, a guard that reads the loop counter and nothing else
+  // (c0 + c * k >= 0) bounds k to an interval known per unit
+  bool loop_guard(const DLin& L) const { return nl == 1 && L.n == 1 && P.term[L.first].slot == 6; }
+  // index and intervals ignore the loop, every loop-dependent guard is a loop guard
+  bool ranged(int a) const {
+    const DAcc& A = P.acc[a];
+    if (A.dead || invariant(a) || lin_dep(A.idx) || lin_dep(A.iv) || (P.WVB && lin_dep(A.wv))) return false;
+    for (int g = 0; g < A.ng; g++) {
+      const DLin& L = P.guard[A.gfirst + g];
+      if (lin_dep(L) && !loop_guard(L)) return false;
+    }
+    return true;
+  }
+};
+
 }  // namespace
 
 std::string jit_source(const DProg& P, bool split) {
@@ -72,6 +127,10 @@ std::string jit_source(const DProg& P, bool split) {
   src += "namespace hgrd { namespace dev {\n";
   src += std::string("typedef ") + (P.wide ? "int64_t" : "int32_t") + " T;\n";
   src += "template <typename U> __device__ __forceinline__ U modq(U v, const Magic& g, U d) { return v - divq<U>(v, g) * d; }\n";
+  // c0 + c * k >= 0 (c != 0) narrows [lo, hi]: k >= ceil(-c0 / c) for c > 0, k <= floor(c0 / -c) for c < 0
+  src += "__device__ __forceinline__ int64_t fdiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }\n";
+  src += "__device__ __forceinline__ void loop_guard_range(int64_t c0, int64_t c, int64_t& lo, int64_t& hi) {\n"
+         "  if (c > 0) lo = max(lo, -fdiv(c0, c)); else hi = min(hi, fdiv(c0, -c));\n}\n";
   src += "struct GenX {\n  const DProg* __restrict__ P;\n";
   src += "  template <int SEL, class Step>\n";
   src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
@@ -85,16 +144,33 @@ std::string jit_source(const DProg& P, bool split) {
   src += "    return walk<SEL, true, true>(lane, u, only, step, flush);\n  }\n";
   src += "  template <int SEL, bool COMBINE, bool ONCE, class Step, class Flush>\n";
   src += "  __device__ __forceinline__ uint64_t walk(int lane, int64_t u, uint32_t only, Step&& step, Flush&& flush) {\n";
-  src += "    const int64_t bw = u / P->nchunk;\n";
-  src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
+  // unit -> (block, warp, chunk) and the thread / block coordinates: in
+  // 32-bit unsigned arithmetic when every unit and block id fits (64-bit
+  // division is a long software sequence), skipping divisions by 1
+  const bool u32 = (uint64_t)P.nunits < (1ull << 31) && (uint64_t)P.nblk < (1ull << 31);
+  if (u32) {
+    src += "    const uint32_t uu = (uint32_t)u, nch = (uint32_t)P->nchunk, wpb = (uint32_t)P->wpb;\n";
+    src += "    const uint32_t bw = nch == 1u ? uu : uu / nch;\n";
+    src += "    const int64_t it0 = (int64_t)(uu - bw * nch) * P->itc;\n";
+    src += "    const uint32_t b32 = wpb == 1u ? bw : bw / wpb;\n";
+    src += "    const int64_t b = (int64_t)b32;\n";
+    src += "    const int lt = (int)(bw - b32 * wpb) * 32 + lane;\n";
+    src += "    const uint32_t gx = (uint32_t)P->grid[0], gy = (uint32_t)P->grid[1];\n";
+    src += "    const uint32_t bq = gx == 1u ? b32 : b32 / gx;\n";
+    src += "    const T s3 = (T)(b32 - bq * gx), s4 = (T)(gy == 1u ? 0u : bq % gy), s5 = (T)(gy == 1u ? bq : bq / gy);\n";
+  } else {
+    src += "    const int64_t bw = u / P->nchunk;\n";
+    src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
+    src += "    const int64_t b = bw / P->wpb;\n";
+    src += "    const int lt = (int)(bw - b * P->wpb) * 32 + lane;\n";
+    src += "    const int64_t gdx = P->grid[0], gdy = P->grid[1];\n";
+    src += "    const T s3 = (T)(b % gdx), s4 = (T)((b / gdx) % gdy), s5 = (T)(b / (gdx * gdy));\n";
+  }
   src += "    const int64_t it1 = min(P->nit, it0 + P->itc);\n";
-  src += "    const int64_t b = bw / P->wpb;\n";
-  src += "    const int lt = (int)(bw - b * P->wpb) * 32 + lane;\n";
   src += "    const bool act = lt < P->nthr;\n";
-  src += "    const int bdx = P->block[0], bdy = P->block[1];\n";
-  src += "    const int64_t gdx = P->grid[0], gdy = P->grid[1];\n";
-  src += "    const T s0 = (T)(lt % bdx), s1 = (T)((lt / bdx) % bdy), s2 = (T)(lt / (bdx * bdy));\n";
-  src += "    const T s3 = (T)(b % gdx), s4 = (T)((b / gdx) % gdy), s5 = (T)(b / (gdx * gdy));\n";
+  src += "    const uint32_t bdx = (uint32_t)P->block[0], bdy = (uint32_t)P->block[1], ult = (uint32_t)lt;\n";
+  src += "    const uint32_t tq = bdx == 1u ? ult : ult / bdx;\n";
+  src += "    const T s0 = (T)(ult - tq * bdx), s1 = (T)(bdy == 1u ? 0u : tq % bdy), s2 = (T)(bdy == 1u ? tq : tq / bdy);\n";
   // loop counters: slots 6.. for the live loops, zero for the others
   for (int l = nl; l < MAXLOOP; l++) src += "    const T s" + S(6 + l) + " = 0; (void)s" + S(6 + l) + ";\n";
   src += "    (void)s0; (void)s1; (void)s2; (void)s3; (void)s4; (void)s5;\n";
@@ -106,45 +182,28 @@ std::string jit_source(const DProg& P, bool split) {
   for (int l = nl - 1; l >= 0; l--)
     src += "      ic[" + S(l) + "] = (int32_t)(r % P->ub[" + S(l) + "]); r /= P->ub[" + S(l) + "];\n";
   src += "    }\n    uint64_t oob = 0;\n";
-  // combined bin updates: per shared-array access with one granule per
-  // instance, the bin and count of this lane's run of instances
-  auto combinable = [&](int a) {
+  const Analysis An(P);
+  auto combinable = [&](int a) { return An.combinable(a); };
+  auto lin_dep = [&](const DLin& L) { return An.lin_dep(L); };
+  auto count_only = [&](int a) { return An.count_only(a); };
+  auto invariant = [&](int a) { return An.invariant(a); };
+  auto loop_guard = [&](const DLin& L) { return An.loop_guard(L); };
+  auto ranged = [&](int a) { return An.ranged(a); };
+  // [lo, hi] of the loop counter admitted by access a's loop guards
+  auto range_code = [&](int a, const std::string& ind) {
     const DAcc& A = P.acc[a];
-    return !A.dead && A.shared && A.G == 1 && ((P.emask >> a) & 1u);
-  };
-  // slots whose value depends on the loop counters (the counters, and ops
-  // reading one, directly or through another op)
-  std::vector<char> dep(MAXSLOT + 16, 0);
-  for (int l = 0; l < nl; l++) dep[6 + l] = 1;
-  auto lin_dep = [&](const DLin& L) {
-    for (int t = 0; t < L.n; t++)
-      if (dep[P.term[L.first + t].slot]) return true;
-    return false;
-  };
-  for (int k = 0; k < P.nfix + P.niter; k++)
-    if (lin_dep(P.ops[k].lin)) dep[P.ops[k].dst] = 1;
-  // an access whose guards, index and interval read no such slot has the same
-  // instances at every loop vector of a unit; so does, for the count pass,
-  // one whose keys are dropped and whose index is always in bounds, once its
-  // guards read no such slot (it only counts its live instances)
-  auto guards_invariant = [&](int a) {
-    const DAcc& A = P.acc[a];
-    for (int g = 0; g < A.ng; g++)
-      if (lin_dep(P.guard[A.gfirst + g])) return false;
-    return true;
-  };
-  auto count_only = [&](int a) {
-    const DAcc& A = P.acc[a];
-    return !((P.emask >> a) & 1u) && A.bounds_free && guards_invariant(a);
-  };
-  auto invariant = [&](int a) {
-    const DAcc& A = P.acc[a];
-    if (count_only(a)) return true;
-    return !lin_dep(A.idx) && !lin_dep(A.iv) && !(P.WVB && lin_dep(A.wv)) && guards_invariant(a);
+    std::string c = ind + "int64_t lo" + S(a) + " = 0, hi" + S(a) + " = (int64_t)P->ub[0] - 1;\n";
+    for (int g = 0; g < A.ng; g++) {
+      const DLin& L = P.guard[A.gfirst + g];
+      if (!loop_guard(L)) continue;
+      const std::string gg = "P->guard[" + S(A.gfirst + g) + "]";
+      c += ind + "loop_guard_range(" + gg + ".c0, P->term[" + S(L.first) + "].coef, lo" + S(a) + ", hi" + S(a) + ");\n";
+    }
+    return c;
   };
   // one access: per loop vector (once = false), or once per unit standing for
   // the unit's nrep loop vectors (once = true, count pass only)
-  auto access_code = [&](int a, bool once) {
+  auto access_code = [&](int a, bool once, const std::string& rep = "nrep", const std::string& icv = "ic") {
     const DAcc& A = P.acc[a];
     const std::string at = "P->acc[" + S(a) + "]";
     const std::string ind = once ? "        " : "      ";
@@ -154,10 +213,13 @@ std::string jit_source(const DProg& P, bool split) {
                                S(kept && !A.shared) + "))";
     std::string c;
     c += ind + "if (" + in_sel + " && (only & " + S(1ll << a) + "u)) {  // access " + S(a) +
-         (once ? ", loop-invariant\n" : "\n");
+         (once ? (rep == "nrep" ? ", loop-invariant\n" : ", over its loop guards' range\n") : "\n");
     c += ind + "  bool live = act;\n";
-    for (int g = 0; g < A.ng; g++)
+    for (int g = 0; g < A.ng; g++) {
+      // taken once over a range: the loop guards hold on the whole range
+      if (once && rep != "nrep" && loop_guard(P.guard[A.gfirst + g])) continue;
       c += ind + "  live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
+    }
     // a count-only access taken once per unit never reads its index or interval
     const bool no_idx = once && count_only(a) && (lin_dep(A.idx) || lin_dep(A.iv));
     c += ind + "  const T idx = " + (no_idx ? std::string("0") : lin(P, at + ".idx", A.idx)) + ";\n";
@@ -165,7 +227,7 @@ std::string jit_source(const DProg& P, bool split) {
       c += ind + "  const bool inb = live;\n";
     else
       c += ind + "  const bool inb = live && idx >= 0 && (int64_t)idx <= " + at + ".maxidx;\n";
-    c += ind + "  oob += (live && !inb) ? " + std::string(once ? "nrep" : "1") + " : 0;\n";
+    c += ind + "  oob += (live && !inb) ? " + std::string(once ? rep : "1") + " : 0;\n";
     // with warp-barrier intervals the key's interval field carries both ids
     const std::string iv = no_idx   ? std::string("(int64_t)0")
                            : P.WVB ? "pack_wv(P, (int64_t)" + lin(P, at + ".iv", A.iv) + ", (int64_t)" +
@@ -175,7 +237,7 @@ std::string jit_source(const DProg& P, bool split) {
     if (combinable(a) && once) {
       c += ind + "  if constexpr (COMBINE) {\n";
       c += ind + "    if (inb) flush(" + S(a) + ", (uint32_t)(((uint64_t)" + at + ".sgbase + (uint64_t)idx) * P->niv + " +
-           "(uint64_t)(" + iv + " - P->ivmin)), nrep, lt);\n";
+           "(uint64_t)(" + iv + " - P->ivmin)), " + rep + ", lt);\n";
       c += ind + "  } else {\n";
       closing = true;
     } else if (combinable(a)) {
@@ -198,7 +260,8 @@ std::string jit_source(const DProg& P, bool split) {
     // and its shared / global branch fold away
     c += ind + "    DAcc A = " + at + ";\n";
     c += ind + "    A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
-    c += ind + "    step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, ic, " + (once ? "nrep" : "1u") + ");\n";
+    c += ind + "    step(" + S(a) + ", A, inb, bal, (int64_t)idx, iv, b, lt, " + icv + ", " + (once ? rep : "1u") +
+         ");\n";
     c += ind + "  }\n";
     if (closing) c += ind + "  }\n";
     c += ind + "}\n";
@@ -211,13 +274,64 @@ std::string jit_source(const DProg& P, bool split) {
     std::string once;
     for (int a = 0; a < P.nacc; a++)
       if (!P.acc[a].dead && invariant(a)) once += access_code(a, true);
-    if (!once.empty()) {
+    std::string ranges;
+    for (int a = 0; a < P.nacc; a++) {
+      if (!ranged(a)) continue;
+      // the unit's loop counters [it0, it1) inside the guards' range: one
+      // instance standing for all of them, recorded at the first
+      ranges += range_code(a, "      ");
+      ranges += "      {\n        const int64_t f" + S(a) + " = max(lo" + S(a) + ", it0), l" + S(a) + " = min(hi" + S(a) +
+                ", it1 - 1);\n";
+      ranges += "        const uint32_t m" + S(a) + " = l" + S(a) + " >= f" + S(a) + " ? (uint32_t)(l" + S(a) + " - f" +
+                S(a) + " + 1) : 0u;\n";
+      ranges += "        if (m" + S(a) + ") {\n          int32_t icr[4] = {(int32_t)f" + S(a) + ", 0, 0, 0};\n";
+      std::string body = access_code(a, true, "m" + S(a), "icr");
+      std::string ind2;
+      for (size_t pos = 0; pos < body.size();) {  // two more spaces of indentation
+        size_t e = body.find('\n', pos);
+        ranges += "  " + body.substr(pos, e - pos + 1);
+        pos = e + 1;
+      }
+      ranges += "        }\n      }\n";
+    }
+    if (!once.empty() || !ranges.empty()) {
       src += "    if constexpr (ONCE) {\n      const uint32_t nrep = (uint32_t)(it1 - it0);\n";
-      src += "      if (nrep) {\n" + once + "      }\n    }\n";
+      if (!once.empty()) src += "      if (nrep) {\n" + once + "      }\n";
+      src += ranges + "    }\n";
     }
   }
-  src += "    for (int64_t it = it0; it < it1; ++it) {\n";
-  if (nl > 0) {
+  // the loop visits only loop counters where some access its body evaluates
+  // can be live: with one loop, the union of the ranged accesses' ranges
+  // (any other access evaluated there spans the whole loop)
+  std::string it_lo = "it0", it_hi = "it1";
+  {
+    bool any_ranged = false;
+    for (int a = 0; a < P.nacc; a++) any_ranged |= ranged(a);
+    if (any_ranged) {
+      src += "    int64_t vlo = 0x7fffffffffffffffll, vhi = -1;  // loop counters the body may need\n";
+      for (int a = 0; a < P.nacc; a++) {
+        const DAcc& A = P.acc[a];
+        if (A.dead) continue;
+        const bool kept = (P.emask >> a) & 1u;
+        const std::string sel = "(SEL == SEL_ALL || (SEL == SEL_KEPT && " + S(kept) + ") || (SEL == SEL_KEPT_GLOBAL && " +
+                                S(kept && !A.shared) + ")) && (only & " + S(1ll << a) + "u)";
+        // in a ONCE walk the loop skips invariant and ranged accesses
+        const std::string in_loop = (invariant(a) || ranged(a)) ? "!ONCE && " + sel : sel;
+        if (ranged(a)) {
+          src += "    if (" + in_loop + ") {\n" + range_code(a, "      ");
+          src += "      vlo = min(vlo, lo" + S(a) + ");\n      vhi = max(vhi, hi" + S(a) + ");\n    }\n";
+        } else {
+          src += "    if (" + in_loop + ") { vlo = 0; vhi = (int64_t)P->ub[0] - 1; }\n";
+        }
+      }
+      src += "    const int64_t iv0 = max(it0, vlo), iv1 = min(it1, vhi + 1);\n";
+      it_lo = "iv0";
+      it_hi = "iv1";
+    }
+  }
+  src += "    for (int64_t it = " + it_lo + "; it < " + it_hi + "; ++it) {\n";
+  if (it_lo != "it0") src += "      ic[0] = (int32_t)it;\n      s6 = (T)it;\n";
+  if (nl > 0 && it_lo == "it0") {
     src += "      if (it > it0) {\n";
     std::string close;
     for (int l = nl - 1; l >= 0; l--) {
@@ -231,7 +345,7 @@ std::string jit_source(const DProg& P, bool split) {
   for (int k = P.nfix; k < P.nfix + P.niter; k++) src += op_code(P, k, true);
   for (int a = 0; a < P.nacc; a++) {
     if (P.acc[a].dead) continue;
-    if (invariant(a)) {
+    if (invariant(a) || ranged(a)) {
       src += "      if constexpr (!ONCE) {\n" + access_code(a, false) + "      }\n";
     } else {
       src += access_code(a, false);
@@ -363,6 +477,39 @@ int jit_prepare(const Bound& B, bool split, double* ms) {
   }
   slot = m;
   return m->ok ? HGRD_OK : fail(HGRD_EUNSUPPORTED, "specialised expansion unavailable: " + m->log);
+}
+
+uint64_t jit_eval_ops(const DProg& P) {
+  // the integer operations the specialised count pass evaluates: a term is
+  // one multiply-add, a guard or bound test one compare, a division by a
+  // constant three, a remainder two more; per thread the unit's fixed ops and
+  // every access taken once (loop-invariant, count-only, ranged), per thread
+  // and loop vector the loop ops and the other accesses
+  const Analysis An(P);
+  auto op_cost = [&](const DOp& op) {
+    return (uint64_t)op.lin.n + (op.kind == OP_DIV ? 3u : op.kind == OP_MOD ? 5u : 0u);
+  };
+  auto acc_cost = [&](const DAcc& A) {
+    uint64_t c = (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n + (P.WVB ? (uint64_t)A.wv.n + 2 : 0);
+    for (int g = 0; g < A.ng; g++) c += (uint64_t)P.guard[A.gfirst + g].n + 1;
+    return c;
+  };
+  uint64_t once = 0, per_it = 0;
+  bool loop_body = false;
+  for (int k = 0; k < P.nfix; k++) once += op_cost(P.ops[k]);
+  for (int a = 0; a < P.nacc; a++) {
+    const DAcc& A = P.acc[a];
+    if (A.dead) continue;
+    if (An.invariant(a) || An.ranged(a)) {
+      once += acc_cost(A);
+    } else {
+      per_it += acc_cost(A);
+      loop_body = true;
+    }
+  }
+  if (loop_body)
+    for (int k = P.nfix; k < P.nfix + P.niter; k++) per_it += op_cost(P.ops[k]);
+  return (uint64_t)P.nblk * (uint64_t)P.nthr * (once + (uint64_t)P.nit * per_it);
 }
 
 bool jit_ready(const Bound& B, bool split) {

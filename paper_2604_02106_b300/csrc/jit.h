@@ -16,6 +16,9 @@ std::string jit_source(const DProg& P, bool split);
 // compile (or find in the process cache) the kernels for B; *ms = compile time
 // spent by this call.  HGRD_EUNSUPPORTED with the compiler's log on failure.
 int jit_prepare(const Bound& B, bool split, double* ms);
+// integer operations of the specialised count pass (loop-invariant and
+// ranged accesses taken once per thread, the others per loop vector)
+uint64_t jit_eval_ops(const DProg& P);
 // whether B already holds loaded kernels for the pipeline
 bool jit_ready(const Bound& B, bool split);
 // one expansion launch (mode 0..4) on the specialised kernels of B's plain

@@ -104,3 +104,32 @@ def test_jit_loop_invariant_accesses(block):
     _same(r, o)
     assert r.n_oob == o.n_oob > 0
     _same(k.check(cap=1 << 20, flags=hg.JIT | hg.NO_SPLIT), o)
+
+
+@pytest.mark.parametrize("block", [(40, 1, 1), (128, 2, 1)])
+@pytest.mark.parametrize("bound", [32, 700])
+def test_jit_loop_guard_ranges(block, bound):
+    # accesses whose only loop dependence is a guard on the loop counter
+    # (c0 + c*k >= 0) are taken once per unit over the counters the guards
+    # admit (count pass; multiplicity = their number inside the unit's chunk,
+    # chunked when the loop is long), and the write pass visits only the
+    # counters where a kept access can be live; counts, out-of-bounds
+    # instances, bins and the canonical pair (recorded at the first admitted
+    # counter) must be those of the full walk
+    text = (f"kernel lg\nparam C\nloop k {bound}\narray s shared 512\narray g global 8192\narray o global 1024\n"
+            "access W s ; width 4 ; idx tx ; if k == C\n"
+            "access R s ; width 4 ; idx tx / 2 ; if k >= C ; if 2*k < 3*C ; iv 0\n"
+            "access W g ; width 4 ; idx bx*300 + tx / 3 ; if k > C - 3 ; if k <= C\n"
+            "access R g ; width 4 ; idx bx*300 + tx + 1 ; if 5 - k >= 0\n"
+            "access W o ; width 4 ; idx tx + 200 ; if k == 4\n"   # partly out of bounds
+            "access A g ; width 4 ; idx 7 ; if -k + 3*C >= 0 ; scope block\n")
+    for C in (5, 17):
+        b = Binding((3, 1, 1), block, (C,))
+        o = oracle.check(text, b, cap=1 << 20)
+        k, r = _jit_check(text, b)
+        _same(r, o)
+        assert r.n_oob == o.n_oob and (o.n_oob > 0) == (block[0] * block[1] > 56)
+        _same(k.check(cap=1 << 20, flags=hg.JIT | hg.NO_SPLIT), o)
+        assert r == k.check(cap=1 << 20, flags=hg.NO_JIT | hg.NO_SMALL)
+        r3 = k.check(cap=1 << 20, flags=hg.JIT, only_accesses=0b001100)
+        assert r3.witnesses == [x for x in o.witnesses if x[3] in (2, 3) and x[4] in (2, 3)]
