@@ -124,7 +124,13 @@ typedef struct {
                                compiled them for this binding); same result;
                                HGRD_NO_SMALL: never run a small binding (at most 4096 keys, 1024
                                simulated warps) whole in one CTA; by default it does, and falls
-                               back to the device-wide pipeline when it keeps too few witnesses */
+                               back to the device-wide pipeline when it keeps too few witnesses;
+                               HGRD_GRAPH: run the check as one CUDA graph launch, the graph
+                               captured by the first such check of this binding with this
+                               workspace, these options and this device, and replayed by the
+                               later ones (same result; the program is re-uploaded by every
+                               replay from a pinned copy taken at capture; ignored with
+                               HGRD_PROFILE; a rebind makes a new binding) */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
@@ -140,7 +146,8 @@ enum {
   HGRD_NO_SPLIT = 8,
   HGRD_JIT = 16,
   HGRD_NO_JIT = 32,
-  HGRD_NO_SMALL = 64
+  HGRD_NO_SMALL = 64,
+  HGRD_GRAPH = 128
 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's

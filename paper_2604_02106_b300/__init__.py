@@ -24,6 +24,7 @@ NO_SPLIT = 8
 JIT = 16
 NO_JIT = 32
 NO_SMALL = 64
+GRAPH = 128      # run the check as one CUDA graph launch (captured once per binding, workspace, options)
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",

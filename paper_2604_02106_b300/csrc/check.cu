@@ -255,15 +255,60 @@ cudaGraphExec_t witness_graph(const Launch& L, const Layout& W, char* ws, int P)
   return exec;
 }
 
-// the buffer holding the merged witnesses after enqueue// the buffer holding the merged witnesses after enqueue
+// the buffer holding the merged witnesses after enqueue
 uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
   const int WP = (WIT_SORT_HI - WIT_SORT_LO + 7) / 8;
   (void)d;
   return (uint64_t*)(ws + ((WP % 2 == 0) ? W.raw2 : W.raw));
 }
 
+// An enqueue being captured into a check graph (HGRD_GRAPH): the graph, a
+// pinned copy of the program the upload node reads, and a stream for
+// capturing the conditional witness-merge body.
+struct Capture {
+  cudaGraph_t graph;
+  DProg* pinned_prog;
+  cudaStream_t body_stream;
+};
+
+// The conditional witness merge inside a stream capture on s: the split
+// kernel, then an IF node (appended to the capture's dependencies) whose body
+// is the device-wide merge captured on the capture's body stream.
+cudaError_t capture_witness_cond(const Launch& L, const Layout& W, char* ws, int P, const Capture& cc) {
+  cudaGraphConditionalHandle h{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, cc.graph, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_witness_split_cond(L, (uint64_t*)(ws + W.counters), W.raw_cap, h)) != cudaSuccess) return e;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if ((e = cudaStreamGetCaptureInfo(L.s, &st, nullptr, &g, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond = nullptr;
+  if ((e = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(L.s, &cond, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+      cudaSuccess)
+    return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(cc.body_stream, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return e;
+  uint64_t captured = 0;
+  Launch LC{cc.body_stream, L.nsm, &captured};
+  const cudaError_t eb = enqueue_witness_big(LC, W, ws, P);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(cc.body_stream, &out);
+  return eb != cudaSuccess ? eb : e;
+}
+
 int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
-            const DProg* dprog_resident = nullptr) {
+            const DProg* dprog_resident = nullptr, const Capture* cc = nullptr) {
   Layout W;
   int rc = prechecks(d, d_ws, ws_bytes, o, &W);
   if (rc) return rc;
@@ -324,6 +369,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
           if (!((only >> a) & 1u)) run_prog.acc[a].dead = 1;
       if (split) run_prog.scap = W.scap;
       hprog = &run_prog;
+    }
+    if (cc) {  // a graph's upload node reads a pinned copy that lives as long as the graph
+      memcpy(cc->pinned_prog, hprog, sizeof(DProg));
+      hprog = cc->pinned_prog;
     }
     CK(cudaMemcpyAsync(ws + W.prog, hprog, sizeof(DProg), cudaMemcpyHostToDevice, s));
     g_stats.h2d_bytes += sizeof(DProg);
@@ -416,6 +465,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   if (wg) {
     CK(cudaGraphLaunch(wg, s));
     (*L.launches)++;
+  } else if (cc) {
+    CK(capture_witness_cond(L, W, ws, P, *cc));
   } else {
     CK(launch_witness_split(L, cnt, W.raw_cap));
     CK(enqueue_witness_big(L, W, ws, P));
@@ -424,6 +475,98 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(launch_kind_counts(L, wout, cnt));
   g_prof.mark("witness_merge");
   return HGRD_OK;
+}
+
+// HGRD_GRAPH: one instantiated graph per (device, binding, workspace,
+// options, expansion kernels, sort shape), captured by the first check and
+// replayed by the later ones.  The cache holds at most CG_MAX graphs; past
+// that, checks run uncaptured.
+struct CheckGraph {
+  cudaGraphExec_t exec = nullptr;
+  DProg* pinned = nullptr;  // the program the graph's upload node copies
+  hgrd_stats stats{};       // what the captured enqueue reported
+};
+std::mutex g_cg_mu;
+std::map<std::vector<uint64_t>, CheckGraph> g_cg;
+constexpr size_t CG_MAX = 64;
+
+int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  hgrd_check_opts oo = *o;
+  oo.flags &= ~(uint32_t)HGRD_GRAPH;
+  Layout W;
+  int rc = prechecks(d, d_ws, ws_bytes, &oo, &W);
+  if (rc) return rc;
+  const Bound& B = *d->bound;
+  // the decisions that shape the captured work, taken before the capture
+  // (compiling and loading kernels is no stream work)
+  const bool split = B.prog.smode && !(oo.flags & HGRD_NO_SPLIT);
+  if ((oo.flags & HGRD_JIT) && !(oo.flags & HGRD_NO_JIT)) {
+    rc = jit_prepare(B, split, nullptr);
+    if (rc) return rc;
+  }
+  const bool jit = !(oo.flags & HGRD_NO_JIT) && jit_ready(B, split);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const std::vector<uint64_t> key = {(uint64_t)dev,         B.gen,           (uint64_t)(uintptr_t)d_ws,
+                                     (uint64_t)ws_bytes,    oo.max_raw_witness, oo.pair_cap,
+                                     oo.flags,              oo.only_accesses, oo.max_shared_keys,
+                                     (uint64_t)jit,         (uint64_t)sort_variant_current()};
+  {
+    std::lock_guard<std::mutex> lk(g_cg_mu);
+    auto it = g_cg.find(key);
+    if (it != g_cg.end()) {
+      g_stats = it->second.stats;
+      CK(cudaGraphLaunch(it->second.exec, s));
+      return HGRD_OK;
+    }
+    if (g_cg.size() >= CG_MAX) return enqueue(d, &oo, d_ws, ws_bytes, s);
+  }
+  CheckGraph e;
+  cudaStream_t cs = nullptr, bs = nullptr;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaHostAlloc((void**)&e.pinned, sizeof(DProg), cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaGraphCreate(&g, 0) == cudaSuccess;
+  ok = ok && cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  int erc = HGRD_OK;
+  if (ok) {
+    const Capture cc{g, e.pinned, bs};
+    erc = enqueue(d, &oo, d_ws, ws_bytes, cs, nullptr, &cc);
+    cudaGraph_t out = nullptr;
+    ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && erc == HGRD_OK;
+  }
+  if (ok) {
+    e.stats = g_stats;
+    ok = cudaGraphInstantiate(&e.exec, g, 0) == cudaSuccess;
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (bs) cudaStreamDestroy(bs);
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.pinned) cudaFreeHost(e.pinned);
+    cudaGetLastError();  // a failed capture leaves no sticky error behind
+    if (erc != HGRD_OK && erc != HGRD_EDEVICE) return erc;  // a real refusal of these options
+    return enqueue(d, &oo, d_ws, ws_bytes, s);               // no graph: the same check, launched directly
+  }
+  std::lock_guard<std::mutex> lk(g_cg_mu);
+  auto it = g_cg.emplace(key, e).first;
+  g_stats = it->second.stats;
+  CK(cudaGraphLaunch(it->second.exec, s));
+  return HGRD_OK;
+}
+
+// the public enqueue: captured / replayed as a graph on request
+int enqueue_api(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  if (o && (o->flags & HGRD_GRAPH) && !(o->flags & HGRD_PROFILE) && d && d->bound)
+    return enqueue_graph(d, o, d_ws, ws_bytes, s);
+  if (o && (o->flags & HGRD_GRAPH)) {
+    hgrd_check_opts oo = *o;
+    oo.flags &= ~(uint32_t)HGRD_GRAPH;
+    return enqueue(d, &oo, d_ws, ws_bytes, s);
+  }
+  return enqueue(d, o, d_ws, ws_bytes, s);
 }
 
 struct Inst {
@@ -483,6 +626,7 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     // more per-run witnesses than the one-CTA path keeps: run the device-wide pipeline
     hgrd_check_opts o2 = o ? *o : hgrd_check_opts{};
     o2.flags |= HGRD_NO_SMALL;
+    o2.flags &= ~(uint32_t)HGRD_GRAPH;
     const int r2 = enqueue(d, &o2, d_ws, ws_bytes, s);
     if (r2) return r2;
     return collect(d, &o2, d_ws, ws_bytes, s, host_out, cap, v, want_pair);
@@ -676,7 +820,7 @@ int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n) {
 }
 
 int hgrd_check_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream) {
-  return enqueue(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
+  return enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
@@ -686,7 +830,7 @@ int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws,
 
 int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
                hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
-  int rc = enqueue(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
+  int rc = enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
   if (rc) return rc;
   return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, true);
 }
@@ -746,6 +890,7 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
   oo.flags &= ~(uint32_t)HGRD_JIT;      // loading a compiled module takes device memory
   oo.flags |= HGRD_NO_JIT | HGRD_NO_SMALL;
+  oo.flags &= ~(uint32_t)HGRD_GRAPH;  // the capture would allocate host and device resources
   const Layout W = layout(*d->bound, &oo);
   if (W.total > NOALLOC_BYTES)
     return fail(HGRD_ENOMEM, "hgrd_check_noalloc: this binding needs " + std::to_string(W.total) +

@@ -12,6 +12,7 @@
 //   ten instance variables and div/mod nodes, bounded by interval arithmetic
 //   over the instance box, and compiled into a DProg for the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -608,6 +609,8 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     if (bind->nparams != d.params.size()) raise(HGRD_EBIND, "parameter count does not match the descriptor");
     if (bind->nparams && !bind->params) raise(HGRD_EINVAL, "null parameter array");
     std::unique_ptr<Bound> bp(new Bound());
+    static std::atomic<uint64_t> next_gen{1};
+    bp->gen = next_gen++;
     Bound& B = *bp;
     memset(&B.prog, 0, sizeof(DProg));
     DProg& P = B.prog;

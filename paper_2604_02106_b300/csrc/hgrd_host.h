@@ -50,6 +50,7 @@ struct AccInfo {
 
 // Result of hgrd_bind_host_params: the compiled program and host facts.
 struct Bound {
+  uint64_t gen = 0;  // process-unique id of this binding (keys the cached check graphs)
   std::vector<AccInfo> acc_info;
   DProg prog;
   std::vector<int64_t> array_bytes, array_granule;

@@ -1144,6 +1144,12 @@ cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* fla
 }
 
 const void* witness_split_cond_fn() { return (const void*)witness_split_cond_kernel; }
+cudaError_t launch_witness_split_cond(const Launch& L, uint64_t* counters, uint64_t raw_cap,
+                                      cudaGraphConditionalHandle h) {
+  witness_split_cond_kernel<<<1, 1, 0, L.s>>>(counters, raw_cap, h);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap) {
   witness_split_kernel<<<1, 1, 0, L.s>>>(counters, raw_cap);

@@ -83,6 +83,10 @@ cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t r
 // the split kernel for a graph: (counters, raw_cap, conditional handle) opens
 // the handle's node when the device-wide merge has work
 const void* witness_split_cond_fn();
+// the split kernel of the conditional witness merge, launched on a stream
+// that is being captured into the graph owning h
+cudaError_t launch_witness_split_cond(const Launch& L, uint64_t* counters, uint64_t raw_cap,
+                                      cudaGraphConditionalHandle h);
 // the onesweep CTA shape in use on the current device
 int sort_variant_current();
 cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
