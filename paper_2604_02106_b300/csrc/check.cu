@@ -262,6 +262,44 @@ uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
   return (uint64_t*)(ws + ((WP % 2 == 0) ? W.raw2 : W.raw));
 }
 
+// The canonical-pair search for the minimal witness (device side): the
+// instances of its two accesses on its granule, gathered into the pair
+// records.  Needs only device results (the merged witnesses), so it can
+// follow the witness merge in the same stream or graph; with no witness its
+// kernels find nothing to do.
+cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_check_opts* o, const Layout& W,
+                                char* ws, const uint64_t* duniq) {
+  const Bound& B = *d->bound;
+  const DProg& HP = B.prog;
+  cudaStream_t s = L.s;
+  cudaError_t e;
+  PairRec* pr = (PairRec*)(ws + W.pairs);
+  if ((e = cudaMemsetAsync(ws + W.counters + 8 * C_NPAIR, 0, 8, s)) != cudaSuccess) return e;
+  // a global-memory witness: search only the blocks of its run (listed in
+  // the unit-offset buffer, free after the write pass); the one-CTA path
+  // sorted nothing, so it searches every unit
+  uint64_t* blist = (uint64_t*)(ws + W.unit_off);
+  if ((e = cudaMemsetAsync(ws + W.counters + 8 * C_NPB, 0, 8, s)) != cudaSuccess) return e;
+  // the path enqueue took for these options (the same decisions, made again)
+  const uint32_t fl = o ? o->flags : 0u;
+  const bool small = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(B);
+  const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
+  const int passes = split ? B.sort_passes_split : B.sort_passes;
+  if (!small) {
+    const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
+    if ((e = launch_pair_blocks(L, sorted, (const DProg*)(ws + W.prog), duniq, (uint64_t*)(ws + W.counters),
+                                blist)) != cudaSuccess)
+      return e;
+  }
+  // the specialised kernels when this binding has them (either module holds the search)
+  const bool jsplit = jit_ready(B, true), jplain = !jsplit && jit_ready(B, false);
+  if ((jsplit || jplain) && !(fl & HGRD_NO_JIT))
+    return launch_jit_expand(L, B, 2, HP, nullptr, blist, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
+                             nullptr, nullptr, 0xffffffffu, jsplit, duniq, pr, W.pair_cap);
+  return launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, blist, nullptr, nullptr, 0,
+                       (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap);
+}
+
 // An enqueue being captured into a check graph (HGRD_GRAPH): the graph, a
 // pinned copy of the program the upload node reads, and a stream for
 // capturing the conditional witness-merge body.
@@ -308,7 +346,7 @@ cudaError_t capture_witness_cond(const Launch& L, const Layout& W, char* ws, int
 }
 
 int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
-            const DProg* dprog_resident = nullptr, const Capture* cc = nullptr) {
+            const DProg* dprog_resident = nullptr, const Capture* cc = nullptr, bool pair = false) {
   Layout W;
   int rc = prechecks(d, d_ws, ws_bytes, o, &W);
   if (rc) return rc;
@@ -388,6 +426,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     g_stats.shared_bins = 0;
     g_stats.jit = 0;
     g_stats.sort_passes = 0;
+    if (pair && !(fl & HGRD_NO_PAIR)) CK(enqueue_pair_search(L, d, o, W, ws, uniq_buffer(d, W, ws)));
     return HGRD_OK;
   }
 
@@ -474,6 +513,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(launch_witness_small(L, U(W.raw), wout, cnt, W.raw_cap));
   CK(launch_kind_counts(L, wout, cnt));
   g_prof.mark("witness_merge");
+  if (pair && !(fl & HGRD_NO_PAIR)) {
+    CK(enqueue_pair_search(L, d, o, W, ws, wout));
+    g_prof.mark("pair_search");
+  }
   return HGRD_OK;
 }
 
@@ -490,7 +533,8 @@ std::mutex g_cg_mu;
 std::map<std::vector<uint64_t>, CheckGraph> g_cg;
 constexpr size_t CG_MAX = 64;
 
-int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
+                  bool pair) {
   hgrd_check_opts oo = *o;
   oo.flags &= ~(uint32_t)HGRD_GRAPH;
   Layout W;
@@ -510,7 +554,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   const std::vector<uint64_t> key = {(uint64_t)dev,         B.gen,           (uint64_t)(uintptr_t)d_ws,
                                      (uint64_t)ws_bytes,    oo.max_raw_witness, oo.pair_cap,
                                      oo.flags,              oo.only_accesses, oo.max_shared_keys,
-                                     (uint64_t)jit,         (uint64_t)sort_variant_current()};
+                                     (uint64_t)jit,         (uint64_t)sort_variant_current(), (uint64_t)pair};
   {
     std::lock_guard<std::mutex> lk(g_cg_mu);
     auto it = g_cg.find(key);
@@ -519,7 +563,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
       CK(cudaGraphLaunch(it->second.exec, s));
       return HGRD_OK;
     }
-    if (g_cg.size() >= CG_MAX) return enqueue(d, &oo, d_ws, ws_bytes, s);
+    if (g_cg.size() >= CG_MAX) return enqueue(d, &oo, d_ws, ws_bytes, s, nullptr, nullptr, pair);
   }
   CheckGraph e;
   cudaStream_t cs = nullptr, bs = nullptr;
@@ -532,7 +576,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   int erc = HGRD_OK;
   if (ok) {
     const Capture cc{g, e.pinned, bs};
-    erc = enqueue(d, &oo, d_ws, ws_bytes, cs, nullptr, &cc);
+    erc = enqueue(d, &oo, d_ws, ws_bytes, cs, nullptr, &cc, pair);
     cudaGraph_t out = nullptr;
     ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && erc == HGRD_OK;
   }
@@ -548,7 +592,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
     if (e.pinned) cudaFreeHost(e.pinned);
     cudaGetLastError();  // a failed capture leaves no sticky error behind
     if (erc != HGRD_OK && erc != HGRD_EDEVICE) return erc;  // a real refusal of these options
-    return enqueue(d, &oo, d_ws, ws_bytes, s);               // no graph: the same check, launched directly
+    return enqueue(d, &oo, d_ws, ws_bytes, s, nullptr, nullptr, pair);  // no graph: the same check, launched directly
   }
   std::lock_guard<std::mutex> lk(g_cg_mu);
   auto it = g_cg.emplace(key, e).first;
@@ -557,16 +601,18 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   return HGRD_OK;
 }
 
-// the public enqueue: captured / replayed as a graph on request
-int enqueue_api(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+// the public enqueue: captured / replayed as a graph on request; `pair`
+// appends the canonical-pair search (the synchronous check wants it)
+int enqueue_api(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
+                bool pair = false) {
   if (o && (o->flags & HGRD_GRAPH) && !(o->flags & HGRD_PROFILE) && d && d->bound)
-    return enqueue_graph(d, o, d_ws, ws_bytes, s);
+    return enqueue_graph(d, o, d_ws, ws_bytes, s, pair);
   if (o && (o->flags & HGRD_GRAPH)) {
     hgrd_check_opts oo = *o;
     oo.flags &= ~(uint32_t)HGRD_GRAPH;
-    return enqueue(d, &oo, d_ws, ws_bytes, s);
+    return enqueue(d, &oo, d_ws, ws_bytes, s, nullptr, nullptr, pair);
   }
-  return enqueue(d, o, d_ws, ws_bytes, s);
+  return enqueue(d, o, d_ws, ws_bytes, s, nullptr, nullptr, pair);
 }
 
 struct Inst {
@@ -602,7 +648,7 @@ constexpr uint64_t WIT_PREFIX = 4096;   // witnesses fetched with the counters
 constexpr uint64_t PAIR_PREFIX = 1024;  // pair-search records fetched with their count
 
 int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
-            hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, bool want_pair) {
+            hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v, bool want_pair, bool pair_enqueued = false) {
   Layout W;
   int rc = prechecks(d, d_ws, ws_bytes, o, &W);
   if (rc) return rc;
@@ -614,22 +660,36 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // counters and a prefix of the merged witnesses in one round trip
   const uint64_t* duniq = uniq_buffer(d, W, ws);
   const uint64_t wpre = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(cap, 1), WIT_PREFIX), W.raw_cap);
-  char* stage = g_pin.get(C_WORDS * 8 + wpre * 8);
+  // with the pair search already enqueued, a prefix of its records too
+  const uint64_t ppre = std::min<uint64_t>(PAIR_PREFIX, W.pair_cap);
+  const size_t pair_at = C_WORDS * 8 + wpre * 8;
+  char* stage = g_pin.get(pair_at + (pair_enqueued ? ppre * sizeof(PairRec) : 0));
   if (!stage) return fail(HGRD_ENOMEM, "pinned host staging buffer");
   CK(cudaMemcpyAsync(stage, ws + W.counters, C_WORDS * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(stage + C_WORDS * 8, duniq, wpre * 8, cudaMemcpyDeviceToHost, s));
   g_stats.d2h_bytes += C_WORDS * 8 + wpre * 8;
+  if (pair_enqueued && want_pair && !(o && (o->flags & HGRD_NO_PAIR))) {
+    CK(cudaMemcpyAsync(stage + pair_at, ws + W.pairs, ppre * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+    g_stats.d2h_bytes += ppre * sizeof(PairRec);
+  }
   CK(cudaStreamSynchronize(s));
   uint64_t cnt[C_WORDS];
   memcpy(cnt, stage, sizeof(cnt));
+  // the pair records fetched with the counters, copied out before any later
+  // readback regrows (and so frees) the staging buffer
+  std::vector<PairRec> pair_pre;
+  if (pair_enqueued && want_pair && !(o && (o->flags & HGRD_NO_PAIR))) {
+    pair_pre.resize(std::min<uint64_t>(cnt[C_NPAIR], ppre));
+    memcpy(pair_pre.data(), stage + pair_at, pair_pre.size() * sizeof(PairRec));
+  }
   if (cnt[C_ERR] & ERR_SMALL_FULL) {
     // more per-run witnesses than the one-CTA path keeps: run the device-wide pipeline
     hgrd_check_opts o2 = o ? *o : hgrd_check_opts{};
     o2.flags |= HGRD_NO_SMALL;
     o2.flags &= ~(uint32_t)HGRD_GRAPH;
-    const int r2 = enqueue(d, &o2, d_ws, ws_bytes, s);
+    const int r2 = enqueue(d, &o2, d_ws, ws_bytes, s, nullptr, nullptr, pair_enqueued);
     if (r2) return r2;
-    return collect(d, &o2, d_ws, ws_bytes, s, host_out, cap, v, want_pair);
+    return collect(d, &o2, d_ws, ws_bytes, s, host_out, cap, v, want_pair, pair_enqueued);
   }
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
@@ -682,44 +742,31 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   if (v->racy && want_pair && !(o && (o->flags & HGRD_NO_PAIR))) {
     // canonical instance pair: gather the instances of acc_lo / acc_hi on the
     // minimal witness's granule, then take the smallest racing (x, y)
-    Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
     PairRec* pr = (PairRec*)(ws + W.pairs);
-    CK(cudaMemsetAsync(ws + W.counters + 8 * C_NPAIR, 0, 8, s));
-    // a global-memory witness: search only the blocks of its run (listed in
-    // the unit-offset buffer, free after the write pass); the one-CTA path
-    // sorted nothing, so it searches every unit
-    uint64_t* blist = (uint64_t*)(ws + W.unit_off);
-    CK(cudaMemsetAsync(ws + W.counters + 8 * C_NPB, 0, 8, s));
-    // the path enqueue took for these options (the same decisions, made again)
-    const uint32_t fl = o ? o->flags : 0u;
-    const bool small = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(B);
-    const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
-    const int passes = split ? B.sort_passes_split : B.sort_passes;
-    if (!small) {
-      const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
-      CK(launch_pair_blocks(L, sorted, (const DProg*)(ws + W.prog), duniq, (uint64_t*)(ws + W.counters), blist));
+    if (!pair_enqueued) {
+      Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
+      CK(enqueue_pair_search(L, d, o, W, ws, duniq));
     }
-    // the specialised kernels when this binding has them (either module holds the search)
-    const bool jsplit = jit_ready(B, true), jplain = !jsplit && jit_ready(B, false);
-    if ((jsplit || jplain) && !(o && (o->flags & HGRD_NO_JIT)))
-      CK(launch_jit_expand(L, B, 2, HP, nullptr, blist, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
-                           nullptr, nullptr, 0xffffffffu, jsplit, duniq, pr, W.pair_cap));
-    else
-      CK(launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, blist, nullptr, nullptr, 0,
-                       (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap));
-    // the record count and a prefix of the records in one round trip
-    const uint64_t ppre = std::min<uint64_t>(PAIR_PREFIX, W.pair_cap);
-    char* pst = g_pin.get(16 + ppre * sizeof(PairRec));
-    if (!pst) return fail(HGRD_ENOMEM, "pinned host staging buffer");
-    CK(cudaMemcpyAsync(pst, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(pst + 16, pr, ppre * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
-    g_stats.d2h_bytes += 8 + ppre * sizeof(PairRec);
-    CK(cudaStreamSynchronize(s));
+    // the record count and a prefix of the records in one round trip (made
+    // already, with the counters, when the search ran in the enqueue)
     uint64_t np = 0;
-    memcpy(&np, pst, 8);
+    const char* pre = nullptr;
+    if (pair_enqueued) {
+      np = cnt[C_NPAIR];
+      pre = (const char*)pair_pre.data();
+    } else {
+      char* pst = g_pin.get(16 + ppre * sizeof(PairRec));
+      if (!pst) return fail(HGRD_ENOMEM, "pinned host staging buffer");
+      CK(cudaMemcpyAsync(pst, ws + W.counters + 8 * C_NPAIR, 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(pst + 16, pr, ppre * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+      g_stats.d2h_bytes += 8 + ppre * sizeof(PairRec);
+      CK(cudaStreamSynchronize(s));
+      memcpy(&np, pst, 8);
+      pre = pst + 16;
+    }
     if (np <= W.pair_cap) {
       std::vector<PairRec> recs(np);
-      memcpy(recs.data(), pst + 16, std::min(np, ppre) * sizeof(PairRec));
+      memcpy(recs.data(), pre, std::min(np, ppre) * sizeof(PairRec));
       if (np > ppre) {
         char* rest = g_pin.get((np - ppre) * sizeof(PairRec));
         if (!rest) return fail(HGRD_ENOMEM, "pinned host staging buffer");
@@ -830,9 +877,9 @@ int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws,
 
 int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
                hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
-  int rc = enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
+  int rc = enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream, true);
   if (rc) return rc;
-  return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, true);
+  return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, true, true);
 }
 
 }  // extern "C"
