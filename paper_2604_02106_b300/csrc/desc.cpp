@@ -905,6 +905,10 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       P.nchunk = nit > 0 ? (nit + P.itc - 1) / P.itc : 1;
     }
     P.nunits = nblk * P.wpb * P.nchunk;
+    {
+      const int64_t dvs[6] = {P.nchunk, P.wpb, bind->grid[0], bind->grid[1], bind->block[0], bind->block[1]};
+      for (int k = 0; k < 6; k++) P.dv[k] = make_magic(std::max<int64_t>(1, dvs[k]), 31);
+    }
     P.nloop = (int32_t)d.loops.size();
     for (int l = 0; l < MAXLOOP; l++) P.ub[l] = (int32_t)(l < P.nloop ? ub[l] : 1);
     for (int l = 0; l < P.nloop; l++)

@@ -54,6 +54,8 @@ HGRD_HD int32_t magic_div32(int32_t n, const Magic& g) {
   int32_t q = (int32_t)((a * g.m) >> g.shift);
   return n < 0 ? -q : q;
 }
+// non-negative numerator below 2^31, N = 31 magic number
+HGRD_HD uint32_t magic_udiv31(uint32_t n, const Magic& g) { return (uint32_t)(((uint64_t)n * g.m) >> g.shift); }
 HGRD_HD int64_t magic_div64(int64_t n, const Magic& g) {
   uint64_t a = (uint64_t)(n < 0 ? -n : n);
   int64_t q = (int64_t)magic_udiv(a, g);
@@ -124,6 +126,9 @@ struct alignas(16) DProg {
   // block, warp interval) from bit SB up; without them SB = PB
   int32_t WVB, SB;
   int64_t wvmin;
+  // division by nchunk, wpb, grid x, grid y, block x, block y of numerators
+  // below 2^31 (unit, block and thread ids): magic numbers with N = 31
+  Magic dv[6];
   uint32_t einter[MAXACC], eintra[MAXACC];
   uint64_t lay_cbase[MAXARR + 1];
   uint64_t lay_ngran[MAXARR];

@@ -150,14 +150,14 @@ std::string jit_source(const DProg& P, bool split) {
   const bool u32 = (uint64_t)P.nunits < (1ull << 31) && (uint64_t)P.nblk < (1ull << 31);
   if (u32) {
     src += "    const uint32_t uu = (uint32_t)u, nch = (uint32_t)P->nchunk, wpb = (uint32_t)P->wpb;\n";
-    src += "    const uint32_t bw = nch == 1u ? uu : uu / nch;\n";
+    src += "    const uint32_t bw = nch == 1u ? uu : magic_udiv31(uu, P->dv[0]);\n";
     src += "    const int64_t it0 = (int64_t)(uu - bw * nch) * P->itc;\n";
-    src += "    const uint32_t b32 = wpb == 1u ? bw : bw / wpb;\n";
+    src += "    const uint32_t b32 = magic_udiv31(bw, P->dv[1]);\n";
     src += "    const int64_t b = (int64_t)b32;\n";
     src += "    const int lt = (int)(bw - b32 * wpb) * 32 + lane;\n";
     src += "    const uint32_t gx = (uint32_t)P->grid[0], gy = (uint32_t)P->grid[1];\n";
-    src += "    const uint32_t bq = gx == 1u ? b32 : b32 / gx;\n";
-    src += "    const T s3 = (T)(b32 - bq * gx), s4 = (T)(gy == 1u ? 0u : bq % gy), s5 = (T)(gy == 1u ? bq : bq / gy);\n";
+    src += "    const uint32_t bq = magic_udiv31(b32, P->dv[2]), bq2 = magic_udiv31(bq, P->dv[3]);\n";
+    src += "    const T s3 = (T)(b32 - bq * gx), s4 = (T)(bq - bq2 * gy), s5 = (T)bq2;\n";
   } else {
     src += "    const int64_t bw = u / P->nchunk;\n";
     src += "    const int64_t it0 = (u - bw * P->nchunk) * P->itc;\n";
@@ -169,8 +169,8 @@ std::string jit_source(const DProg& P, bool split) {
   src += "    const int64_t it1 = min(P->nit, it0 + P->itc);\n";
   src += "    const bool act = lt < P->nthr;\n";
   src += "    const uint32_t bdx = (uint32_t)P->block[0], bdy = (uint32_t)P->block[1], ult = (uint32_t)lt;\n";
-  src += "    const uint32_t tq = bdx == 1u ? ult : ult / bdx;\n";
-  src += "    const T s0 = (T)(ult - tq * bdx), s1 = (T)(bdy == 1u ? 0u : tq % bdy), s2 = (T)(bdy == 1u ? tq : tq / bdy);\n";
+  src += "    const uint32_t tq = magic_udiv31(ult, P->dv[4]), tq2 = magic_udiv31(tq, P->dv[5]);\n";
+  src += "    const T s0 = (T)(ult - tq * bdx), s1 = (T)(tq - tq2 * bdy), s2 = (T)tq2;\n";
   // loop counters: slots 6.. for the live loops, zero for the others
   for (int l = nl; l < MAXLOOP; l++) src += "    const T s" + S(6 + l) + " = 0; (void)s" + S(6 + l) + ";\n";
   src += "    (void)s0; (void)s1; (void)s2; (void)s3; (void)s4; (void)s5;\n";
@@ -367,9 +367,12 @@ std::string jit_source(const DProg& P, bool split) {
   src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand2" + std::string(sig);
   src += "  expand_units_body<T, 2>(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, hist, "
          "npass, counters, uniq, pairs, pair_cap, only);\n}\n";
+  // the write kernels (1, 4) are register hungry (key stores of every kept
+  // access in flight); three CTAs per SM keep them at 80 registers
   if (!split) {
     for (int m : {0, 1}) {
-      src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand" + S(m) + sig;
+      src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS" + std::string(m == 1 ? ", 3" : "") +
+             ") hgrd_jit_expand" + S(m) + sig;
       src += "  expand_units_body<T, " + S(m) +
              ">(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, hist, npass, counters, "
              "nullptr, nullptr, 0, only);\n}\n";
@@ -377,7 +380,8 @@ std::string jit_source(const DProg& P, bool split) {
   }
   for (int m : {3, 4}) {
     if (!split) break;
-    src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS) hgrd_jit_expand" + S(m) + sig;
+    src += "extern \"C\" __global__ void __launch_bounds__(EXP_THREADS" + std::string(m == 4 ? ", 3" : "") +
+           ") hgrd_jit_expand" + S(m) + sig;
     src += "  expand_block_body<T, " + S(m) +
            ">(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, keys_s, hist, counters, "
            "stbl, sbase, only);\n}\n";
