@@ -407,3 +407,15 @@ def test_warp_exchange_many_blocks(space, sync, cross):
     # warp intervals change the key layout: the sort covers block and warp interval
     if sync in ("warp", "warp2"):
         assert hg.stats()["sort_passes"] >= 3
+
+
+@pytest.mark.parametrize("grid", [2047, 2100])
+def test_many_units_one_access(grid):
+    # ~65k simulated warps of one write access, neighbouring blocks overlapping
+    # by one element: grid - 1 inter-block witnesses
+    text = "kernel bigscan\narray a global 8800000\naccess W a ; width 4 ; idx bx*1023 + tx\n"
+    b = Binding((grid, 1, 1), (1024, 1, 1), ())
+    o = oracle.check(text, b, cap=1 << 20)
+    assert o.n_witness == grid - 1
+    for flags in (hg.NO_SMALL, hg.JIT):
+        _same(hg.check(text, b, cap=1 << 20, flags=flags), o)
