@@ -449,6 +449,9 @@ def main():
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--no-sort-tune", action="store_true")
     ap.add_argument("--no-jit", action="store_true", help="interpreted expansion kernels only")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch each check's kernels directly instead of replaying its CUDA graph "
+                         "(ncu cannot profile kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--once", action="store_true",
                     help="bind the stencil workload, compile its kernels and run one check, untimed "
                          "(the case a profiler capture runs)")
@@ -500,7 +503,7 @@ def main():
     ws = k.workspace()
     s = torch.cuda.Stream()
     # every check runs as one CUDA graph launch (captured by the first warm-up step)
-    G = hg.GRAPH
+    G = 0 if args.no_graph else hg.GRAPH
     for _ in range(max(3, args.warmup)):
         k.enqueue(ws, stream=s, flags=G)
     res = k.collect(ws, cap=1 << 16, stream=s, flags=G)
@@ -621,7 +624,8 @@ def main():
                            "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write, outside the "
                                  f"per-step events); sorted keys {8 * n_sorted / 1e6:.1f} MB per buffer",
                            "parallelism": f"replicas{world}", "sort_tuning": tuned,
-                           "launch": "one CUDA graph launch per check (HGRD_GRAPH; stage times: direct launches)"},
+                           "launch": "direct kernel launches" if args.no_graph else
+                           "one CUDA graph launch per check (HGRD_GRAPH; stage times: direct launches)"},
                 "e2e": e2e,
                 "roofline": roofline,
                 "roofline_hbm": roof_hbm,
