@@ -125,6 +125,11 @@ typedef struct {
                                HGRD_NO_SMALL: never run a small binding (at most 4096 keys, 1024
                                simulated warps) whole in one CTA; by default it does, and falls
                                back to the device-wide pipeline when it keeps too few witnesses;
+                               HGRD_NO_CELL_FILTER / HGRD_CELL_FILTER: never / always (when its
+                               table fits: at most 2^23 cells) sort only the keys of locations
+                               that two threads touch with a writer among them, found with a
+                               per-location table the count pass fills (default: when at least
+                               2^16 keys may be sorted); same result;
                                HGRD_GRAPH: run the check as one CUDA graph launch, the graph
                                captured by the first such check of this binding with this
                                workspace, these options and this device, and replayed by the
@@ -147,7 +152,9 @@ enum {
   HGRD_JIT = 16,
   HGRD_NO_JIT = 32,
   HGRD_NO_SMALL = 64,
-  HGRD_GRAPH = 128
+  HGRD_GRAPH = 128,
+  HGRD_NO_CELL_FILTER = 256,
+  HGRD_CELL_FILTER = 512
 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
@@ -170,11 +177,13 @@ typedef struct {
   uint64_t n_binned_keys;   /* shared-array keys written into candidate bins (block-local mode) */
   uint32_t shared_bins;     /* 1 when the shared-array keys were checked in per-block bins */
   uint32_t jit;             /* 1 when the expansion ran specialised kernels (HGRD_JIT) */
-  uint64_t eval_ops;        /* integer operations of evaluating every instance once (guards,
+  uint64_t eval_ops;        /* integer operations of the count pass's evaluation (guards,
                                index, bound tests, interval, the ops they read; a term is one
-                               multiply-add, a division by a constant 3, a remainder 5) */
+                               multiply-add, a division by a constant 3, a remainder 5); on
+                               specialised kernels loop-invariant and loop-guarded accesses
+                               count once per thread */
   uint32_t small;           /* 1 when the check ran whole in one CTA */
-  uint32_t reserved2;
+  uint32_t cell_filter;     /* 1 when only keys of cells with a writer and two threads were sorted */
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,

@@ -25,6 +25,8 @@ JIT = 16
 NO_JIT = 32
 NO_SMALL = 64
 GRAPH = 128      # run the check as one CUDA graph launch (captured once per binding, workspace, options)
+NO_CELL_FILTER = 256  # sort every kept key (no per-cell pre-filter)
+CELL_FILTER = 512     # pre-filter keys by cell whenever the table fits (default: only for many keys)
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -104,7 +106,7 @@ class Stats(C.Structure):
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
                 ("shared_bins", C.c_uint32), ("jit", C.c_uint32), ("eval_ops", C.c_uint64),
-                ("small", C.c_uint32), ("reserved2", C.c_uint32)]
+                ("small", C.c_uint32), ("cell_filter", C.c_uint32)]
 
 
 _lib = None

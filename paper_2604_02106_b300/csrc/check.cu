@@ -32,7 +32,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
-      pairs, stbl, sbase, total;
+      pairs, stbl, sbase, cells, keysC, total;
+  bool cfilter;        // the cell filter runs (its table and third key buffer exist)
   uint64_t raw_cap, pair_cap, status_words;
   uint64_t scap;       // room for keys of candidate shared bins (block-local mode)
   uint64_t key_words;  // length of each key buffer
@@ -59,7 +60,9 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
                   : std::min<uint64_t>(1ull << 24, std::max<uint64_t>(1ull << 12, 2 * L.key_words));
   L.pair_cap = (o && o->pair_cap) ? o->pair_cap : std::min<uint64_t>(1ull << 20, nk);
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
-  const uint64_t scan_n = std::max(nunits, L.raw_cap);
+  const uint32_t lfl = o ? o->flags : 0u;
+  L.cfilter = P.cfilter && !(lfl & HGRD_NO_CELL_FILTER) && ((lfl & HGRD_CELL_FILTER) || P.cfilter_auto);
+  const uint64_t scan_n = std::max(std::max(nunits, L.raw_cap), L.cfilter ? L.key_words : 0);
   // look-back status of the sort passes: tiles of the larger of the key sort
   // and the witness sort
   const uint64_t ns = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
@@ -90,6 +93,10 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   // the base of every block's candidate keys
   L.stbl = take(P.smode ? (size_t)P.nblk * (size_t)P.nsbins * 8 : 0);
   L.sbase = take(P.smode ? (size_t)P.nblk * 8 : 0);
+  // cell filter: per-cell table (two words per cell, writer bits) and a third
+  // key buffer (flags and offsets of the written keys, then a sort buffer)
+  L.cells = take(L.cfilter ? (size_t)P.ncells * 8 + ((size_t)P.ncells + 31) / 32 * 4 : 0);
+  L.keysC = take(L.cfilter ? L.key_words * 8 : 0);
   L.total = off;
   return L;
 }
@@ -286,9 +293,11 @@ cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_
   const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
   const int passes = split ? B.sort_passes_split : B.sort_passes;
   if (!small) {
-    const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
-    if ((e = launch_pair_blocks(L, sorted, (const DProg*)(ws + W.prog), duniq, (uint64_t*)(ws + W.counters),
-                                blist)) != cudaSuccess)
+    const uint64_t* sorted = (uint64_t*)(ws + (W.cfilter ? ((passes & 1) ? W.keysC : W.keysB)
+                                                         : ((passes & 1) ? W.keysB : W.keysA)));
+    const uint64_t* nsorted = (const uint64_t*)(ws + W.counters) + (W.cfilter ? C_NGC : C_NG);
+    if ((e = launch_pair_blocks(L, sorted, nsorted, (const DProg*)(ws + W.prog), duniq,
+                                (uint64_t*)(ws + W.counters), blist)) != cudaSuccess)
       return e;
   }
   // the specialised kernels when this binding has them (either module holds the search)
@@ -437,31 +446,45 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // that may race), only those of global arrays in block-local mode (the
   // candidate bins follow them in the final buffer)
   uint64_t* nkeys = cnt + C_NG;
+  // cell filter: the count pass fills the per-cell table (its key pointer),
+  // the written keys of cells without a writer and two threads are dropped
+  // before the sort; the sort then runs keysB <-> keysC and candidate-bin
+  // keys go to its final buffer
+  const bool cf = W.cfilter;
+  uint64_t* keysC = cf ? U(W.keysC) : nullptr;
+  uint32_t* ctab = cf ? (uint32_t*)(ws + W.cells) : nullptr;
+  if (cf) {
+    const uint64_t used = split ? HP.shared_cell_base : HP.ncells;  // cells the count pass can note
+    CK(cudaMemsetAsync(ctab, 0xff, used * 8, s));
+    CK(cudaMemsetAsync(ctab + 2 * HP.ncells, 0, (used + 31) / 32 * 4, s));
+  }
+  uint64_t* fin = cf ? ((P & 1) ? keysC : keysB) : ((P & 1) ? keysB : keysA);  // where the sorted keys end
+  uint64_t* cnt_tab = cf ? (uint64_t*)ctab : nullptr;
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
-    CK(launch_jit_expand(L, B, m0, *hprog, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), 1, cnt, U(W.stbl),
+    CK(launch_jit_expand(L, B, m0, *hprog, U(W.unit_cnt), nullptr, cnt_tab, nullptr, U(W.hist), 1, cnt, U(W.stbl),
                          U(W.sbase), only_mask, split));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
     // look-back status of the tiles the key sort will use: no stale epoch may survive
     CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
-    CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr, P, cnt,
-                         U(W.stbl), U(W.sbase), only_mask, split));
+    CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, fin, nullptr, P, cnt, U(W.stbl),
+                         U(W.sbase), only_mask, split));
     g_prof.mark("expand_write");
   } else if (split) {
-    CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, nullptr, U(W.hist), cnt,
+    CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, cnt_tab, nullptr, U(W.hist), cnt,
                            U(W.stbl), U(W.sbase)));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
     // look-back status of the tiles the key sort will use: no stale epoch may survive
     CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
-    CK(launch_expand_block(L, 4, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, (P & 1) ? keysB : keysA, nullptr,
-                           cnt, U(W.stbl), U(W.sbase)));
+    CK(launch_expand_block(L, 4, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, fin, nullptr, cnt, U(W.stbl),
+                           U(W.sbase)));
     g_prof.mark("expand_write");
   } else {
-    CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, nullptr, U(W.hist), 1, cnt, nullptr, nullptr,
+    CK(launch_expand(L, 0, B.wide, dprog, HP, U(W.unit_cnt), nullptr, cnt_tab, U(W.hist), 1, cnt, nullptr, nullptr,
                      0));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
@@ -473,7 +496,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   uint64_t* in = keysA;
   uint64_t* out = keysB;
-  // the expansion counted digit 0; each pass counts the digit of the next
+  if (cf) {
+    // keysA (written, emission order) -> keysB (kept, same order); flags and
+    // offsets in keysC below any candidate-bin keys (those start at C_NG)
+    CK(launch_cell_filter(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, keysC, U(W.partials),
+                          cnt + C_NGC, keysB, U(W.hist), HP.SB));
+    nkeys = cnt + C_NGC;
+    in = keysB;
+    out = keysC;
+    g_prof.mark("cell_filter");
+  }
+  // the expansion (or the filter) counted digit 0; each pass counts the digit of the next
   for (int p = 0; p < P; p++) {
     CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
     CK(launch_onesweep(L, in, out, nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256, U(W.status),
@@ -693,7 +726,8 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
-  g_stats.n_sorted_keys = cnt[C_NG];
+  g_stats.n_sorted_keys = W.cfilter ? cnt[C_NGC] : cnt[C_NG];
+  g_stats.cell_filter = (W.cfilter && !g_stats.small) ? 1u : 0u;
   g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
   g_stats.n_raw_witness = cnt[C_NRAW];
   if (cnt[C_ERR] & ERR_SHARED_FULL)
@@ -936,7 +970,7 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   if (o) oo = *o;
   oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
   oo.flags &= ~(uint32_t)HGRD_JIT;      // loading a compiled module takes device memory
-  oo.flags |= HGRD_NO_JIT | HGRD_NO_SMALL;
+  oo.flags |= HGRD_NO_JIT | HGRD_NO_SMALL | HGRD_NO_CELL_FILTER;  // smallest workspace
   oo.flags &= ~(uint32_t)HGRD_GRAPH;  // the capture would allocate host and device resources
   const Layout W = layout(*d->bound, &oo);
   if (W.total > NOALLOC_BYTES)

@@ -995,6 +995,11 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (!P.acc[a].shared) B.nsort_max_split += k;
       else nshared_kept += k;
     }
+    // cell filter: worth a per-cell table when many keys would be sorted and
+    // the table (8 B per cell) stays small; the (block, thread) id is 31 bits
+    P.ncells = P.lay_cbase[P.nlay];
+    P.cfilter = P.ncells <= (1ull << 23) && P.BB + P.TB <= 31;
+    P.cfilter_auto = P.cfilter && B.nsort_max_all >= (1ull << 16);
     // default room for keys of candidate shared bins: all kept shared keys up
     // to 2^24, a sixteenth of them beyond (below 2^32); a check that needs
     // more reports HGRD_ENOMEM with the count

@@ -35,6 +35,16 @@
 namespace hgrd {
 namespace dev {
 
+// Cell filter (count pass): note that (block << TB | thread) `gid` touched
+// cell c, as a writer or not.  tab[2c] keeps the smallest gid, tab[2c + 1]
+// the complement of the largest (both by atomicMin from all-ones), the writer
+// bits follow the 2 * ncells words.  Idempotent, so multiplicities need no care.
+__device__ __forceinline__ void cell_note(uint32_t* tab, uint64_t ncells, uint64_t c, uint32_t gid, bool w) {
+  atomicMin(&tab[2 * c], gid);
+  atomicMin(&tab[2 * c + 1], ~gid);
+  if (w) atomicOr(&tab[2 * ncells + (c >> 5)], 1u << (c & 31));
+}
+
 enum { SEL_ALL = 0, SEL_KEPT = 1, SEL_KEPT_GLOBAL = 2 };
 
 // Modes 0 (count keys per unit + digit histograms of `npass` digits), 1 (write
@@ -111,6 +121,9 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                          const uint64_t key = make_key(P, A, a, idx, iv, b, lt, j);
                          if (MODE == 1) {
                            keys[cursor + (uint64_t)rank * G + j] = key;
+                         } else if (keys) {  // count pass with the cell filter: `keys` is its table
+                           cell_note(reinterpret_cast<uint32_t*>(keys), P->ncells, shr64(key, P->PB + P->IVB),
+                                     (uint32_t)((uint64_t)b << P->TB | (uint64_t)lt), (P->wmask >> a) & 1u);
                          } else {
                            for (int p = 0; p < npass; ++p)
                              atomicAdd(&shist[p * 256 + ((uint32_t)(key >> (SB + 8 * p)) & 255u)], mult);
@@ -249,6 +262,9 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                            const uint64_t key = make_key(P, A, a, idx, iv, bb, lt, j);
                            if (MODE == 4)
                              keys_g[cursor + (uint64_t)rank * G + j] = key;
+                           else if (keys_g)  // count pass with the cell filter: `keys_g` is its table
+                             cell_note(reinterpret_cast<uint32_t*>(keys_g), P->ncells, shr64(key, P->PB + P->IVB),
+                                       (uint32_t)((uint64_t)bb << P->TB | (uint64_t)lt), (wmask >> a) & 1u);
                            else
                              atomicAdd(&shist[(uint32_t)(key >> SB) & 255u], mult);
                          }

@@ -126,6 +126,13 @@ struct alignas(16) DProg {
   // block, warp interval) from bit SB up; without them SB = PB
   int32_t WVB, SB;
   int64_t wvmin;
+  // cell filter: the count pass records per cell (granule of an array copy)
+  // the smallest and largest (block << TB | thread) touching it and whether a
+  // writer did; only keys of cells with a writer and two threads are sorted.
+  // Table at the count pass's key pointer: gmin[ncells], gmax[ncells] (u32),
+  // writer bits[(ncells + 31) / 32]
+  int32_t cfilter, cfilter_auto;  // table fits; worth it by default
+  uint64_t ncells;
   // division by nchunk, wpb, grid x, grid y, block x, block y of numerators
   // below 2^31 (unit, block and thread ids): magic numbers with N = 31
   Magic dv[6];
@@ -175,6 +182,7 @@ enum {
   C_NDROP,  // keys of accesses that cannot race with any access (counted, never written)
   C_NRAWBIG,  // raw witnesses left to the device-wide merge (0 when one CTA merges them)
   C_NPB,      // pair search: 1 + blocks listed for it (0: search every unit)
+  C_NGC = 33,  // cell filter: global keys kept for the sort (C_NG: all written ones)
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_SMALLQ = 120,  // one-CTA path of a small check: work queue, then an order word of zero

@@ -211,6 +211,45 @@ __global__ void shared_cand_kernel(const uint64_t* __restrict__ stbl, const uint
   }
 }
 
+// ------------------------------------------------------------------ cell filter
+// A key is kept for the sort when its cell saw a writer and two different
+// (block, thread) ids in the count pass (only such a cell can hold a race).
+__device__ __forceinline__ bool cell_kept(const uint32_t* __restrict__ tab, uint64_t ncells, uint64_t c) {
+  if (c >= ncells) return true;
+  const bool w = (tab[2 * ncells + (c >> 5)] >> (c & 31)) & 1u;
+  return w && tab[2 * c] < ~tab[2 * c + 1];
+}
+
+__global__ void __launch_bounds__(256) cell_flags_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                         uint64_t n_max, const uint32_t* __restrict__ tab,
+                                                         uint64_t ncells, int rsh, uint64_t* __restrict__ flags) {
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = cell_kept(tab, ncells, shr64(keys[i], rsh)) ? 1u : 0u;
+}
+
+// kept keys to their scanned positions (emission order kept), with the digit
+// histogram of the first sort pass
+__global__ void __launch_bounds__(256) cell_compact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                           uint64_t n_max, const uint32_t* __restrict__ tab,
+                                                           uint64_t ncells, int rsh, const uint64_t* __restrict__ offs,
+                                                           uint64_t* __restrict__ out, uint64_t* __restrict__ hist,
+                                                           int shift) {
+  __shared__ uint32_t sh[256];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t n = dev_n(n_dev, n_max);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    if (cell_kept(tab, ncells, shr64(k, rsh))) {
+      out[offs[i]] = k;
+      atomicAdd(&sh[(uint32_t)(k >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  if (sh[threadIdx.x]) atomicAdd((unsigned long long*)&hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
+}
+
 // ------------------------------------------------------------------ radix sort
 __global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                         uint64_t n_max, int shift0, int npass,
@@ -665,7 +704,8 @@ __device__ __forceinline__ RunMasks exact_bin(const uint64_t* keys, uint64_t s, 
 
 // Entries of the block-local mode's candidate bins carry SHARED_ENTRY and
 // offsets relative to the first shared key, which sits right after the
-// *n_dev global keys; their kinds come from exact_bin and the warp's tables
+// counters[C_NG] written global keys (the *n_dev sorted ones unless the cell
+// filter dropped some); their kinds come from exact_bin and the warp's tables
 // in dynamic shared memory (launched with `bins` set).
 __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                     const DProg* __restrict__ P, const uint64_t* __restrict__ cand,
@@ -674,6 +714,9 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
   extern __shared__ __align__(16) unsigned char xsm[];
   const int lane = threadIdx.x & 31;
   const uint64_t n = *n_dev;
+  // candidate-bin keys sit behind all written global keys (counters[C_NG]),
+  // which is n unless the cell filter dropped some before the sort
+  const uint64_t nsb = counters[C_NG];
   uint64_t ncand = counters[C_NCAND];
   if (ncand > cand_cap) ncand = cand_cap;
   const uint32_t einter = lane < P->nacc ? P->einter[lane] : 0u;
@@ -686,7 +729,7 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
     if (stop_first && *(volatile uint64_t*)&counters[C_NRAW] != 0) break;
     const uint64_t c0 = cand[2 * c], c1 = cand[2 * c + 1];
     const RunMasks R = (c0 & SHARED_ENTRY)
-                           ? exact_bin(keys, n + (c0 & ~SHARED_ENTRY), n + c1, P, lane, eintra, T)
+                           ? exact_bin(keys, nsb + (c0 & ~SHARED_ENTRY), nsb + c1, P, lane, eintra, T)
                            : exact_run(keys, c0, c1, n, P, lane, einter, eintra, stop_first != 0);
     record_pairs(counters + C_PAIRS, R, lane);
     uint32_t row = witness_row(R, lane);
@@ -739,7 +782,7 @@ __device__ __forceinline__ uint64_t first_at_or_above(const uint64_t* keys, uint
   return lo + (uint64_t)__popc(__ballot_sync(FULL, below));
 }
 
-__global__ void __launch_bounds__(256) pair_blocks_kernel(const uint64_t* __restrict__ keys,
+__global__ void __launch_bounds__(256) pair_blocks_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                           const DProg* __restrict__ P,
                                                           const uint64_t* __restrict__ uniq, uint64_t* counters,
                                                           uint64_t* __restrict__ blocks) {
@@ -755,7 +798,7 @@ __global__ void __launch_bounds__(256) pair_blocks_kernel(const uint64_t* __rest
     if (P->lay_arr[l] == (int32_t)arr && !P->lay_shared[l]) li = l;
   if (li < 0) return;
   const uint64_t cell = P->lay_cbase[li] + gran;
-  const uint64_t n = counters[C_NG];
+  const uint64_t n = *n_dev;  // sorted keys
   const int sh = P->PB + P->IVB;
   if (threadIdx.x < 32) {
     const uint64_t lo = first_at_or_above(keys, n, sh, cell, threadIdx.x);
@@ -1021,6 +1064,20 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
   return cudaGetLastError();
 }
 
+cudaError_t launch_cell_filter(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
+                               const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* flags, uint64_t* partials,
+                               uint64_t* n_kept, uint64_t* out, uint64_t* hist, int shift) {
+  uint64_t blocks = (n_max + 255) / 256;
+  unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
+  cell_flags_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, flags);
+  (*L.launches)++;
+  cudaError_t e = launch_scan(L, flags, flags, n_dev, n_max, partials, n_kept);
+  if (e != cudaSuccess) return e;
+  cell_compact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, flags, out, hist, shift);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass) {
   hist_scan_kernel<<<1, 256, 0, L.s>>>(hist, gbase, npass);
   (*L.launches)++;
@@ -1180,9 +1237,9 @@ cudaError_t launch_zero(const Launch& L, uint64_t* p, const uint64_t* n_dev, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const DProg* d_prog, const uint64_t* uniq,
-                               uint64_t* counters, uint64_t* blocks) {
-  pair_blocks_kernel<<<1, 256, 0, L.s>>>(keys, d_prog, uniq, counters, blocks);
+cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                               const uint64_t* uniq, uint64_t* counters, uint64_t* blocks) {
+  pair_blocks_kernel<<<1, 256, 0, L.s>>>(keys, n_dev, d_prog, uniq, counters, blocks);
   (*L.launches)++;
   return cudaGetLastError();
 }

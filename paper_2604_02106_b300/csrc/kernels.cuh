@@ -42,6 +42,13 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
                              int npass, uint64_t* hist);
 // per-pass exclusive prefix of the digit counts
 cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass);
+// cell filter: keep the keys [0, *n_dev) whose cell (key >> rsh) the count
+// pass found written and touched by two threads; flags / scanned offsets in
+// `flags`, kept keys to out[0, *n_kept) in order, first-pass histogram at
+// `shift` added to hist
+cudaError_t launch_cell_filter(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
+                               const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* flags, uint64_t* partials,
+                               uint64_t* n_kept, uint64_t* out, uint64_t* hist, int shift);
 // one stable onesweep pass on the digit at `shift`; when next_hist is given,
 // also counts the digit at `next_shift` for the following pass
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
@@ -73,8 +80,8 @@ cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* fla
 cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters);
 // pair search: the blocks of a global-memory witness's run in the sorted keys
 // (counters[C_NPB] = 1 + their count, or left 0 when every unit must be searched)
-cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const DProg* d_prog, const uint64_t* uniq,
-                               uint64_t* counters, uint64_t* blocks);
+cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
+                               const uint64_t* uniq, uint64_t* counters, uint64_t* blocks);
 // at most WSMALL_MAX raw witnesses are merged by one CTA: witness_split sets
 // counters[C_NRAWBIG] (0 in that case, else the count) for the device-wide
 // kernels; witness_small then merges the few from `raw` into `uniq`

@@ -133,3 +133,13 @@ def test_jit_loop_guard_ranges(block, bound):
         assert r == k.check(cap=1 << 20, flags=hg.NO_JIT | hg.NO_SMALL)
         r3 = k.check(cap=1 << 20, flags=hg.JIT, only_accesses=0b001100)
         assert r3.witnesses == [x for x in o.witnesses if x[3] in (2, 3) and x[4] in (2, 3)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_jit_with_cell_filter(seed):
+    w = workloads.random_shared(5100 + seed)
+    o = oracle.check(w.text, w.binding, cap=1 << 20)
+    for extra in (hg.CELL_FILTER, hg.CELL_FILTER | hg.NO_SPLIT):
+        k, r = _jit_check(w.text, w.binding, flags=extra)
+        assert hg.stats()["cell_filter"] == 1
+        _same(r, o)

@@ -49,6 +49,10 @@ def _both(text, binding, cap=1 << 20, **kw):
     g2 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL, **kw)
     assert hg.stats()["small"] == 0
     assert g2 == g
+    # with and without the per-cell pre-filter of the sorted keys
+    g3 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL | hg.CELL_FILTER, **kw)
+    g4 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL | hg.NO_CELL_FILTER, **kw)
+    assert g3 == g and g4 == g
     o = oracle.check(text, binding, cap=cap)
     return g, o
 
@@ -333,7 +337,7 @@ def test_keys_of_accesses_without_partners_are_counted_not_sorted():
 
 def test_stencil_sorts_only_the_output_keys():
     w = workloads.config2(0, planted=True, W=256, H=256, K=8)
-    g = hg.check(w.text, w.binding, cap=1 << 20)
+    g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.NO_CELL_FILTER)
     st = hg.stats()
     assert st["n_sorted_keys"] == 256 * 256  # one Out write per thread; the In reads race with nothing
     _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
@@ -419,3 +423,19 @@ def test_many_units_one_access(grid):
     assert o.n_witness == grid - 1
     for flags in (hg.NO_SMALL, hg.JIT):
         _same(hg.check(text, b, cap=1 << 20, flags=flags), o)
+
+
+@pytest.mark.parametrize("planted", [True, False])
+def test_cell_filter_sorts_only_shared_cells(planted):
+    # stencil 256x256: 256x256x8 possible output keys; with the planted row
+    # stride only the 255 cells two blocks write keep their 2 keys each
+    w = workloads.config2(0, planted=planted, W=256, H=256, K=8)
+    o = oracle.check(w.text, w.binding, cap=1 << 20)
+    for flags in (hg.NO_JIT, hg.JIT):
+        g = hg.check(w.text, w.binding, cap=1 << 20, flags=flags)
+        st = hg.stats()
+        assert st["cell_filter"] == 1
+        assert st["n_sorted_keys"] == (2 * 255 if planted else 0)
+        _same(g, o)
+        _same(hg.check(w.text, w.binding, cap=1 << 20, flags=flags | hg.NO_CELL_FILTER), o)
+        assert hg.stats()["cell_filter"] == 0 and hg.stats()["n_sorted_keys"] == 256 * 256
