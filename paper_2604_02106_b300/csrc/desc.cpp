@@ -826,6 +826,8 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     std::vector<DLin> guards;
     int64_t ivmin = INT64_MAX, ivmax = INT64_MIN;
     int64_t wvmin = INT64_MAX, wvmax = INT64_MIN;
+    // block-barrier interval range of each live access (whole range: dead)
+    std::vector<int64_t> acc_ivlo(d.acc.size(), INT64_MIN), acc_ivhi(d.acc.size(), INT64_MAX);
     for (size_t a = 0; a < d.acc.size(); a++) {
       DAcc& X = P.acc[a];
       const AccessDecl& A = d.acc[a];
@@ -853,6 +855,8 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (__int128(std::max(iabs((__int128)lo), iabs((__int128)hi))) * A.width >= ((__int128)1 << 62))
         raise(HGRD_EOVERFLOW, "byte offsets can exceed 2^62");
       C.range(af[a].iv, lo, hi);
+      acc_ivlo[a] = lo;
+      acc_ivhi[a] = hi;
       ivmin = std::min(ivmin, lo);
       ivmax = std::max(ivmax, hi);
       C.range(af[a].wv, lo, hi);
@@ -916,6 +920,10 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     P.nit = nit;
 
     // ---- pair rule E (Sec. 6.1 trivially race free; Appendix A scopes)
+    // Two instances of one block are ordered unless they share a barrier
+    // interval (Sec. 6.1, block barrier; Table 2), so accesses whose interval
+    // ranges are disjoint can form no intra-block or intra-warp pair; in
+    // shared memory, where every pair is of one block, no pair at all.
     for (int a = 0; a < P.nacc; a++) {
       const AccessDecl& x = d.acc[a];
       if (x.kind != 0) P.wmask |= 1u << a;
@@ -925,6 +933,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         int m = 7;
         if (x.kind == 2 && y.kind == 2) m = (x.scope == 0 || y.scope == 0) ? 1 : 0;
         if (d.arrays[x.arr].space == HGRD_SPACE_SHARED) m &= ~1;
+        if (acc_ivhi[a] < acc_ivlo[b] || acc_ivhi[b] < acc_ivlo[a]) m &= 1;
         if (m & 1) P.einter[a] |= 1u << b;
         if (m & 6) P.eintra[a] |= 1u << b;
       }

@@ -93,10 +93,13 @@ def test_workspace_scales_with_problem():
     ws = k.workspace_size()
     # two 8-byte key buffers dominate: for the kept keys of the one global
     # write (the reads of the read-only input race with nothing) plus room for
-    # candidate shared-memory bins, a sixteenth of the kept shared keys (above 2^24)
+    # candidate shared-memory bins: all kept shared keys up to 2^24, a
+    # sixteenth of them beyond; the kept shared keys are those of the tile's
+    # three writes (the ten reads of the tile share no barrier interval with a
+    # write, so they race with nothing either)
     out_keys = 64 * 64 * 256 * 32
-    shared_kept = 13 * out_keys
-    keys = out_keys + shared_kept // 16
+    shared_kept = 3 * out_keys
+    keys = out_keys + min(shared_kept, max(1 << 24, shared_kept // 16))
     # (+ four raw-witness buffers of at most 2^24 words and small tables); the
     # cell filter adds a third key buffer and 8 bytes per cell (3.4M cells)
     cells = 2 * 1024 * 1024 + 4096 * 324

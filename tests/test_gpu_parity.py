@@ -335,6 +335,24 @@ def test_keys_of_accesses_without_partners_are_counted_not_sorted():
     assert g.n_keys == 5 * 4 * 64
 
 
+@pytest.mark.parametrize("space", ["shared", "global"])
+@pytest.mark.parametrize("jit", [0, hg.JIT])
+def test_accesses_in_disjoint_barrier_intervals(space, jit):
+    # reads whose interval range meets no write's race with nothing inside a
+    # block (shared memory: with nothing at all); loop-dependent intervals
+    # that meet still race; the verdict is the oracle's either way
+    text = (f"kernel iv\nloop k 4\narray S {space} 4096\n"
+            "access W S ; width 4 ; iv 0 ; idx tx + 64*bx\n"
+            "access R S ; width 4 ; iv 1 ; idx tx + 1 + 64*bx\n"
+            "access W S ; width 4 ; iv 2*k + 2 ; idx (tx + k) % 64 + 64*bx\n"
+            "access R S ; width 4 ; iv 5 ; idx (tx + 2) % 64 + 64*bx\n"
+            "access R S ; width 4 ; iv 9 ; idx tx + 64*bx\n")
+    b = Binding((8, 1, 1), (64, 1, 1), ())
+    g, o = _both(text, b, flags=jit)
+    _same(g, o)
+    assert o.racy and g.n_keys == 5 * 8 * 64 * 4
+
+
 def test_stencil_sorts_only_the_output_keys():
     w = workloads.config2(0, planted=True, W=256, H=256, K=8)
     g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.NO_CELL_FILTER)

@@ -50,3 +50,19 @@ def test_pair_features_list_the_eligible_pairs():
     assert ab == want
     f2, ab2 = ranker.pair_features(k)
     assert ab2 == ab and (f2 == f).all()
+
+
+def test_pairs_in_disjoint_barrier_intervals():
+    # one block's instances in different barrier intervals are ordered
+    # (Sec. 6.1, block barrier): in shared memory such a pair is never
+    # eligible; in global memory it stays eligible for the inter-block kind
+    text = ("kernel iv\nloop k 4\narray S shared 256\narray G global 256\n"
+            "access W S ; width 4 ; iv 0 ; idx tx\n"          # 0
+            "access R S ; width 4 ; iv 1 ; idx tx + 1\n"      # 1: no writer in interval 1
+            "access W S ; width 4 ; iv 2*k + 2 ; idx tx\n"    # 2: intervals 2..8
+            "access R S ; width 4 ; iv 5 ; idx tx + 2\n"      # 3: meets 2's range
+            "access W G ; width 4 ; iv 0 ; idx tx\n"          # 4
+            "access R G ; width 4 ; iv 1 ; idx tx + 1\n")     # 5
+    k = hg.Kernel(text).bind((2, 1, 1), (32, 1, 1), ())
+    _, ab = ranker.pair_features(k)
+    assert ab == [(0, 0), (2, 2), (2, 3), (4, 4), (4, 5)]
