@@ -345,7 +345,7 @@ def test_accesses_in_disjoint_barrier_intervals(space, jit):
             "access W S ; width 4 ; iv 0 ; idx tx + 64*bx\n"
             "access R S ; width 4 ; iv 1 ; idx tx + 1 + 64*bx\n"
             "access W S ; width 4 ; iv 2*k + 2 ; idx (tx + k) % 64 + 64*bx\n"
-            "access R S ; width 4 ; iv 5 ; idx (tx + 2) % 64 + 64*bx\n"
+            "access R S ; width 4 ; iv 4 ; idx (tx + 2) % 64 + 64*bx\n"
             "access R S ; width 4 ; iv 9 ; idx tx + 64*bx\n")
     b = Binding((8, 1, 1), (64, 1, 1), ())
     g, o = _both(text, b, flags=jit)
