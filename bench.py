@@ -139,6 +139,8 @@ def cpu_baseline(side):
                       f"one whole oracle run, {dt:.1f} s"}
 
 
+# keys of one sort-tuner pass (hgrd_sort_tune with the binding's default 600 MB workspace)
+SORT_TUNE_KEYS = 1 << 25
 # algorithmic bytes per key of each HBM-bound stage (the roofline's numerator)
 STAGE_BYTES = {"expand_write": 8, "candidates": 8}
 for _p in range(8):
@@ -487,9 +489,18 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     tuned = None
+    roof_sort = None
     if not args.no_sort_tune:
         best, ms = hg.sort_tune()
         tuned = {"variant": best, "pass_ms_32M_keys": [round(x, 4) for x in ms]}
+        # the sort kernel where HBM bounds it: one onesweep pass over the
+        # tuner's 2^25 random keys reads and writes 8 B per key (best of three
+        # repetitions of the chosen shape, CUDA events on its stream)
+        hbm_peak, peak_kind = _peaks()
+        a = 16 * SORT_TUNE_KEYS / (ms[best] / 1000.0) / 1e9
+        roof_sort = {"bound": "hbm", "kernel": f"onesweep_kernel shape {best}", "achieved": a, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": a / hbm_peak, "peak_kind": peak_kind, "bytes_per_key": 16,
+                     "keys_per_launch": SORT_TUNE_KEYS, "ms_per_launch": ms[best]}
     if args.suite == "warp":
         w = workloads.warp_exchange(32, WARP_LOOPS, "warp2", False, grid=WARP_GRID, space="global")
         workload = WARP_WORKLOAD
@@ -629,6 +640,7 @@ def main():
                 "e2e": e2e,
                 "roofline": roofline,
                 "roofline_hbm": roof_hbm,
+                "roofline_sort": roof_sort,
                 "stages_ms": {n: round(t, 4) for n, t in stage_ms.items()},
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches * args.steps)}

@@ -32,8 +32,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
-      pairs, stbl, sbase, cells, keysC, total;
-  bool cfilter;        // the cell filter runs (its table and third key buffer exist)
+      pairs, stbl, sbase, cells, total;
+  bool cfilter;        // the cell filter's table exists (the filter runs in the first sort pass)
   uint64_t raw_cap, pair_cap, status_words;
   uint64_t scap;       // room for keys of candidate shared bins (block-local mode)
   uint64_t key_words;  // length of each key buffer
@@ -62,7 +62,7 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   const uint64_t nunits = std::max<int64_t>(P.nunits, 1);
   const uint32_t lfl = o ? o->flags : 0u;
   L.cfilter = P.cfilter && !(lfl & HGRD_NO_CELL_FILTER) && ((lfl & HGRD_CELL_FILTER) || P.cfilter_auto);
-  const uint64_t scan_n = std::max(std::max(nunits, L.raw_cap), L.cfilter ? L.key_words : 0);
+  const uint64_t scan_n = std::max(nunits, L.raw_cap);
   // look-back status of the sort passes: tiles of the larger of the key sort
   // and the witness sort
   const uint64_t ns = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
@@ -93,13 +93,14 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   // the base of every block's candidate keys
   L.stbl = take(P.smode ? (size_t)P.nblk * (size_t)P.nsbins * 8 : 0);
   L.sbase = take(P.smode ? (size_t)P.nblk * 8 : 0);
-  // cell filter: per-cell table (two words per cell, writer bits) and a third
-  // key buffer (flags and offsets of the written keys, then a sort buffer)
-  L.cells = take(L.cfilter ? (size_t)P.ncells * 8 + ((size_t)P.ncells + 31) / 32 * 4 : 0);
-  L.keysC = take(L.cfilter ? L.key_words * 8 : 0);
+  // cell filter: one state word per cell
+  L.cells = take(L.cfilter ? (size_t)P.ncells * 4 : 0);
   L.total = off;
   return L;
 }
+
+// the cell filter runs inside the first sort pass, when there is one
+bool filter_runs(const Layout& W, int passes) { return W.cfilter && passes > 0; }
 
 int nsm_of_current_device() {
   static thread_local int cached_dev = -1, cached_n = 0;
@@ -293,9 +294,8 @@ cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_
   const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
   const int passes = split ? B.sort_passes_split : B.sort_passes;
   if (!small) {
-    const uint64_t* sorted = (uint64_t*)(ws + (W.cfilter ? ((passes & 1) ? W.keysC : W.keysB)
-                                                         : ((passes & 1) ? W.keysB : W.keysA)));
-    const uint64_t* nsorted = (const uint64_t*)(ws + W.counters) + (W.cfilter ? C_NGC : C_NG);
+    const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
+    const uint64_t* nsorted = (const uint64_t*)(ws + W.counters) + (filter_runs(W, passes) ? C_NGC : C_NG);
     if ((e = launch_pair_blocks(L, sorted, nsorted, (const DProg*)(ws + W.prog), duniq,
                                 (uint64_t*)(ws + W.counters), blist)) != cudaSuccess)
       return e;
@@ -446,19 +446,18 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // that may race), only those of global arrays in block-local mode (the
   // candidate bins follow them in the final buffer)
   uint64_t* nkeys = cnt + C_NG;
-  // cell filter: the count pass fills the per-cell table (its key pointer),
-  // the written keys of cells without a writer and two threads are dropped
-  // before the sort; the sort then runs keysB <-> keysC and candidate-bin
-  // keys go to its final buffer
-  const bool cf = W.cfilter;
-  uint64_t* keysC = cf ? U(W.keysC) : nullptr;
+  // cell filter: the count pass fills the per-cell table (its key pointer);
+  // the first sort pass drops the written keys of cells without a writer and
+  // two threads, so later passes and the scans see only the kept ones.
+  // Candidate-bin keys go behind all written global keys in the final buffer
+  // (at C_NG), which no pass writes.
+  const bool cf = filter_runs(W, P);
   uint32_t* ctab = cf ? (uint32_t*)(ws + W.cells) : nullptr;
   if (cf) {
     const uint64_t used = split ? HP.shared_cell_base : HP.ncells;  // cells the count pass can note
-    CK(cudaMemsetAsync(ctab, 0xff, used * 8, s));
-    CK(cudaMemsetAsync(ctab + 2 * HP.ncells, 0, (used + 31) / 32 * 4, s));
+    CK(cudaMemsetAsync(ctab, 0, used * 4, s));
   }
-  uint64_t* fin = cf ? ((P & 1) ? keysC : keysB) : ((P & 1) ? keysB : keysA);  // where the sorted keys end
+  uint64_t* fin = (P & 1) ? keysB : keysA;  // where the sorted keys end
   uint64_t* cnt_tab = cf ? (uint64_t*)ctab : nullptr;
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
@@ -496,22 +495,20 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   uint64_t* in = keysA;
   uint64_t* out = keysB;
+  const uint64_t* nsorted = nkeys;  // keys the first pass reads
   if (cf) {
-    // keysA (written, emission order) -> keysB (kept, same order); flags and
-    // offsets in keysC below any candidate-bin keys (those start at C_NG)
-    CK(launch_cell_filter(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, keysC, U(W.partials),
-                          cnt + C_NGC, keysB, U(W.hist), HP.SB));
+    // digit histogram of the first pass over the kept keys, and their count
+    CK(launch_cell_hist(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, U(W.hist), HP.SB, cnt + C_NGC));
     nkeys = cnt + C_NGC;
-    in = keysB;
-    out = keysC;
     g_prof.mark("cell_filter");
   }
   // the expansion (or the filter) counted digit 0; each pass counts the digit of the next
   for (int p = 0; p < P; p++) {
     CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
-    CK(launch_onesweep(L, in, out, nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256, U(W.status),
-                       cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
-                       p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1)));
+    CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256,
+                       U(W.status), cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
+                       p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1),
+                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
                                 "sort_pass4", "sort_pass5", "sort_pass6", "sort_pass7"};
@@ -726,8 +723,14 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
   g_stats.n_candidates = cnt[C_NCAND];
-  g_stats.n_sorted_keys = W.cfilter ? cnt[C_NGC] : cnt[C_NG];
-  g_stats.cell_filter = (W.cfilter && !g_stats.small) ? 1u : 0u;
+  {
+    const uint32_t fl = o ? o->flags : 0u;
+    const int passes = (d->bound->prog.smode && !(fl & HGRD_NO_SPLIT)) ? d->bound->sort_passes_split
+                                                                       : d->bound->sort_passes;
+    const bool cf = filter_runs(W, passes) && !g_stats.small;
+    g_stats.n_sorted_keys = cf ? cnt[C_NGC] : cnt[C_NG];
+    g_stats.cell_filter = cf ? 1u : 0u;
+  }
   g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
   g_stats.n_raw_witness = cnt[C_NRAW];
   if (cnt[C_ERR] & ERR_SHARED_FULL)

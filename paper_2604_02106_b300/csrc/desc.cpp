@@ -1005,9 +1005,9 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       else nshared_kept += k;
     }
     // cell filter: worth a per-cell table when many keys would be sorted and
-    // the table (8 B per cell) stays small; the (block, thread) id is 31 bits
+    // the table (4 B per cell) stays small; the (block, thread) id fits 30 bits
     P.ncells = P.lay_cbase[P.nlay];
-    P.cfilter = P.ncells <= (1ull << 23) && P.BB + P.TB <= 31;
+    P.cfilter = P.ncells <= (1ull << 23) && P.BB + P.TB <= 30;
     P.cfilter_auto = P.cfilter && B.nsort_max_all >= (1ull << 16);
     // default room for keys of candidate shared bins: all kept shared keys up
     // to 2^24, a sixteenth of them beyond (below 2^32); a check that needs

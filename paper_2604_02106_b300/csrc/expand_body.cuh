@@ -36,13 +36,32 @@ namespace hgrd {
 namespace dev {
 
 // Cell filter (count pass): note that (block << TB | thread) `gid` touched
-// cell c, as a writer or not.  tab[2c] keeps the smallest gid, tab[2c + 1]
-// the complement of the largest (both by atomicMin from all-ones), the writer
-// bits follow the 2 * ncells words.  Idempotent, so multiplicities need no care.
-__device__ __forceinline__ void cell_note(uint32_t* tab, uint64_t ncells, uint64_t c, uint32_t gid, bool w) {
-  atomicMin(&tab[2 * c], gid);
-  atomicMin(&tab[2 * c + 1], ~gid);
-  if (w) atomicOr(&tab[2 * ncells + (c >> 5)], 1u << (c & 31));
+// cell c, as a writer or not.  One word per cell: 0 = untouched; otherwise
+// bit 31 = a writer touched it and bits 0..30 = gid + 1 of the one id seen so
+// far, or CELL_MANY once two different ids were seen.  The word only moves
+// forward (untouched -> one id -> many, writer bit 0 -> 1), so the
+// compare-and-swap loop ends after at most three changes by other threads;
+// the first note of a cell is one CAS.  Idempotent, so multiplicities need
+// no care.  gid + 1 < CELL_MANY holds because gid has at most 30 bits.
+constexpr uint32_t CELL_MANY = 0x7fffffffu, CELL_W = 0x80000000u;
+__device__ __forceinline__ void cell_note(uint32_t* tab, uint64_t c, uint32_t gid, bool w) {
+  const uint32_t me = (gid + 1u) | (w ? CELL_W : 0u);
+  uint32_t old = atomicCAS(&tab[c], 0u, me);
+  while (old != 0u) {
+    const uint32_t id = (old & CELL_MANY) == gid + 1u ? gid + 1u : CELL_MANY;
+    const uint32_t nv = id | ((old | me) & CELL_W);
+    if (nv == old) break;
+    const uint32_t prev = atomicCAS(&tab[c], old, nv);
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
+// A key is kept for the sort when its cell saw a writer and two different
+// (block, thread) ids (only such a cell can hold a race); cells past the
+// table (shared memory) are always kept.
+__device__ __forceinline__ bool cell_kept(const uint32_t* __restrict__ tab, uint64_t ncells, uint64_t c) {
+  return c >= ncells || tab[c] == (CELL_MANY | CELL_W);
 }
 
 enum { SEL_ALL = 0, SEL_KEPT = 1, SEL_KEPT_GLOBAL = 2 };
@@ -122,7 +141,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                          if (MODE == 1) {
                            keys[cursor + (uint64_t)rank * G + j] = key;
                          } else if (keys) {  // count pass with the cell filter: `keys` is its table
-                           cell_note(reinterpret_cast<uint32_t*>(keys), P->ncells, shr64(key, P->PB + P->IVB),
+                           cell_note(reinterpret_cast<uint32_t*>(keys), shr64(key, P->PB + P->IVB),
                                      (uint32_t)((uint64_t)b << P->TB | (uint64_t)lt), (P->wmask >> a) & 1u);
                          } else {
                            for (int p = 0; p < npass; ++p)
@@ -263,7 +282,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
                            if (MODE == 4)
                              keys_g[cursor + (uint64_t)rank * G + j] = key;
                            else if (keys_g)  // count pass with the cell filter: `keys_g` is its table
-                             cell_note(reinterpret_cast<uint32_t*>(keys_g), P->ncells, shr64(key, P->PB + P->IVB),
+                             cell_note(reinterpret_cast<uint32_t*>(keys_g), shr64(key, P->PB + P->IVB),
                                        (uint32_t)((uint64_t)bb << P->TB | (uint64_t)lt), (wmask >> a) & 1u);
                            else
                              atomicAdd(&shist[(uint32_t)(key >> SB) & 255u], mult);

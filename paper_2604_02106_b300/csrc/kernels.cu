@@ -212,40 +212,26 @@ __global__ void shared_cand_kernel(const uint64_t* __restrict__ stbl, const uint
 }
 
 // ------------------------------------------------------------------ cell filter
-// A key is kept for the sort when its cell saw a writer and two different
-// (block, thread) ids in the count pass (only such a cell can hold a race).
-__device__ __forceinline__ bool cell_kept(const uint32_t* __restrict__ tab, uint64_t ncells, uint64_t c) {
-  if (c >= ncells) return true;
-  const bool w = (tab[2 * ncells + (c >> 5)] >> (c & 31)) & 1u;
-  return w && tab[2 * c] < ~tab[2 * c + 1];
-}
-
-__global__ void __launch_bounds__(256) cell_flags_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
-                                                         uint64_t n_max, const uint32_t* __restrict__ tab,
-                                                         uint64_t ncells, int rsh, uint64_t* __restrict__ flags) {
-  const uint64_t n = dev_n(n_dev, n_max);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    flags[i] = cell_kept(tab, ncells, shr64(keys[i], rsh)) ? 1u : 0u;
-}
-
-// kept keys to their scanned positions (emission order kept), with the digit
-// histogram of the first sort pass
-__global__ void __launch_bounds__(256) cell_compact_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
-                                                           uint64_t n_max, const uint32_t* __restrict__ tab,
-                                                           uint64_t ncells, int rsh, const uint64_t* __restrict__ offs,
-                                                           uint64_t* __restrict__ out, uint64_t* __restrict__ hist,
-                                                           int shift) {
+// Cell filter: the digit histogram of the first sort pass over the keys it
+// keeps, and their count
+__global__ void __launch_bounds__(256) cell_hist_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+                                                        uint64_t n_max, const uint32_t* __restrict__ tab,
+                                                        uint64_t ncells, int rsh, uint64_t* __restrict__ hist, int shift,
+                                                        uint64_t* __restrict__ n_kept) {
   __shared__ uint32_t sh[256];
   sh[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t n = dev_n(n_dev, n_max);
+  uint32_t kept = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
     if (cell_kept(tab, ncells, shr64(k, rsh))) {
-      out[offs[i]] = k;
       atomicAdd(&sh[(uint32_t)(k >> shift) & 255u], 1u);
+      ++kept;
     }
   }
+  for (int o = 16; o; o >>= 1) kept += __shfl_down_sync(FULL, kept, o);
+  if ((threadIdx.x & 31) == 0 && kept) atomicAdd((unsigned long long*)n_kept, (unsigned long long)kept);
   __syncthreads();
   if (sh[threadIdx.x]) atomicAdd((unsigned long long*)&hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
 }
@@ -280,16 +266,20 @@ constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull <
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
 // Onesweep pass, templated on the CTA shape (threads T, keys per thread KPT,
-// CTAs per SM the registers are budgeted for); the sort autotuner picks the
-// shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
+// CTAs per SM the registers are budgeted for) and on the warp ranking (RA:
+// the leader of each digit's peers takes the warp's running count with one
+// shared atomic add and passes it on by shuffle, so the slots pipeline; else
+// a read, a leader write and two warp barriers per slot); the sort
+// autotuner picks the shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
 // handled in increasing order and the look-back only waits on tiles held by
 // running CTAs.
-template <int T, int KPT, int MINB>
+template <int T, int KPT, int MINB, bool RA = false>
 __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                           const uint64_t* n_dev, uint64_t n_max, int shift,
                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
                                                           unsigned long long* ticket, uint32_t epoch, uint64_t* err,
-                                                          uint64_t* next_hist, int next_shift) {
+                                                          uint64_t* next_hist, int next_shift,
+                                                          const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh) {
   constexpr int W = T / 32, TILE = T * KPT;
   extern __shared__ __align__(16) unsigned char osm[];
   uint32_t* whist = reinterpret_cast<uint32_t*>(osm);  // [W][256]
@@ -299,6 +289,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
   uint64_t* gofs = reinterpret_cast<uint64_t*>(dsum + RS_RADIX);
   uint64_t* stage = gofs + RS_RADIX;
   uint64_t* s_tile = stage + TILE;
+  uint32_t* s_kept = reinterpret_cast<uint32_t*>(s_tile + 1);  // keys of the tile that stay
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + TILE - 1) / TILE;
@@ -324,15 +315,24 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
 #pragma unroll
     for (int s = 0; s < KPT; ++s) {
       const uint64_t i = wbase + (uint64_t)s * 32 + lane;
-      const uint32_t d = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
+      const bool live = i < n && (!ctab || cell_kept(ctab, ncells, shr64(k[s], rsh)));
+      const uint32_t d = live ? (uint32_t)((k[s] >> shift) & 255) : 256u;
       if (next_hist && d < 256u) atomicAdd(&nhist[(uint32_t)(k[s] >> next_shift) & 255u], 1u);
       const unsigned peers = __match_any_sync(FULL, d);
       uint32_t old = 0;
-      if (d < 256u) old = whist[warp * RS_RADIX + d];
-      dr[s] = d | ((old + __popc(peers & lt)) << 9);
-      __syncwarp();
-      if (d < 256u && lane == __ffs(peers) - 1) whist[warp * RS_RADIX + d] = old + __popc(peers);
-      __syncwarp();
+      if constexpr (RA) {
+        // one warp's atomics reach shared memory in issue order, slot after slot
+        const int leader = __ffs(peers) - 1;
+        if (d < 256u && lane == leader) old = atomicAdd(&whist[warp * RS_RADIX + d], (uint32_t)__popc(peers));
+        old = __shfl_sync(FULL, old, leader);
+        dr[s] = d | ((old + __popc(peers & lt)) << 9);
+      } else {
+        if (d < 256u) old = whist[warp * RS_RADIX + d];
+        dr[s] = d | ((old + __popc(peers & lt)) << 9);
+        __syncwarp();
+        if (d < 256u && lane == __ffs(peers) - 1) whist[warp * RS_RADIX + d] = old + __popc(peers);
+        __syncwarp();
+      }
     }
     __syncthreads();
     // digits: counts across warps, warp-exclusive prefixes, look-back
@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
         tstart[lane * 8 + j] = run;
         run += v[j];
       }
+      if (lane == 31) *s_kept = run;
     }
     __syncthreads();
 #pragma unroll
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
       if (d < 256u) stage[tstart[d] + whist[warp * RS_RADIX + d] + (dr[s] >> 9)] = k[s];
     }
     __syncthreads();
-    const uint64_t cnt = (n - base) < (uint64_t)TILE ? (n - base) : (uint64_t)TILE;
+    const uint32_t cnt = *s_kept;
     for (uint32_t i = threadIdx.x; i < cnt; i += T) {
       const uint64_t key = stage[i];
       const uint32_t d = (uint32_t)((key >> shift) & 255);
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
 
 template <int T, int KPT>
 constexpr size_t onesweep_smem() {
-  return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16;
+  return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16;  // + ticket, kept
 }
 
 // ------------------------------------------------------------------ conflict scan, phase A
@@ -1064,16 +1065,12 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
   return cudaGetLastError();
 }
 
-cudaError_t launch_cell_filter(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
-                               const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* flags, uint64_t* partials,
-                               uint64_t* n_kept, uint64_t* out, uint64_t* hist, int shift) {
+cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
+                             const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
+                             uint64_t* n_kept) {
   uint64_t blocks = (n_max + 255) / 256;
   unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
-  cell_flags_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, flags);
-  (*L.launches)++;
-  cudaError_t e = launch_scan(L, flags, flags, n_dev, n_max, partials, n_kept);
-  if (e != cudaSuccess) return e;
-  cell_compact_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, flags, out, hist, shift);
+  cell_hist_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, hist, shift, n_kept);
   (*L.launches)++;
   return cudaGetLastError();
 }
@@ -1097,6 +1094,9 @@ const SortVariant* sort_variants(int* count) {
       {(const void*)onesweep_kernel<384, 12, 2>, 384, 12, onesweep_smem<384, 12>()},
       {(const void*)onesweep_kernel<256, 24, 2>, 256, 24, onesweep_smem<256, 24>()},
       {(const void*)onesweep_kernel<128, 16, 8>, 128, 16, onesweep_smem<128, 16>()},
+      {(const void*)onesweep_kernel<256, 16, 3, true>, 256, 16, onesweep_smem<256, 16>()},
+      {(const void*)onesweep_kernel<256, 12, 4, true>, 256, 12, onesweep_smem<256, 12>()},
+      {(const void*)onesweep_kernel<512, 8, 2, true>, 512, 8, onesweep_smem<512, 8>()},
   };
   *count = (int)(sizeof(v) / sizeof(v[0]));
   return v;
@@ -1111,7 +1111,8 @@ int sort_variant_current() {
 
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
-                            uint64_t* err, uint64_t* next_hist, int next_shift) {
+                            uint64_t* err, uint64_t* next_hist, int next_shift, const uint32_t* ctab,
+                            uint64_t ncells, int rsh) {
   int nv = 0, dev = 0;
   const SortVariant* V = sort_variants(&nv);
   cudaGetDevice(&dev);
@@ -1124,7 +1125,8 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
   if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
   unsigned long long* tk = (unsigned long long*)ticket;
   void* args[] = {(void*)&in, (void*)&out, (void*)&n_dev, (void*)&n_max, (void*)&shift, (void*)&gbase,
-                  (void*)&status, (void*)&tk, (void*)&epoch, (void*)&err, (void*)&next_hist, (void*)&next_shift};
+                  (void*)&status, (void*)&tk, (void*)&epoch, (void*)&err, (void*)&next_hist, (void*)&next_shift,
+                  (void*)&ctab, (void*)&ncells, (void*)&rsh};
   (*L.launches)++;
   return cudaLaunchKernel(S.fn, dim3(grid), dim3(S.threads), args, S.smem, L.s);
 }

@@ -42,18 +42,19 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
                              int npass, uint64_t* hist);
 // per-pass exclusive prefix of the digit counts
 cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass);
-// cell filter: keep the keys [0, *n_dev) whose cell (key >> rsh) the count
-// pass found written and touched by two threads; flags / scanned offsets in
-// `flags`, kept keys to out[0, *n_kept) in order, first-pass histogram at
-// `shift` added to hist
-cudaError_t launch_cell_filter(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
-                               const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* flags, uint64_t* partials,
-                               uint64_t* n_kept, uint64_t* out, uint64_t* hist, int shift);
+// cell filter: the first pass's digit histogram (at `shift`, added to hist)
+// of the keys [0, *n_dev) whose cell (key >> rsh) the count pass found
+// written and touched by two threads, and their count (added to *n_kept)
+cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
+                             const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
+                             uint64_t* n_kept);
 // one stable onesweep pass on the digit at `shift`; when next_hist is given,
-// also counts the digit at `next_shift` for the following pass
+// also counts the digit at `next_shift` for the following pass; with a cell
+// table, only the keys the cell filter keeps are sorted (to out[0, kept))
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
-                            uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0);
+                            uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0,
+                            const uint32_t* ctab = nullptr, uint64_t ncells = 0, int rsh = 0);
 
 // conflict scan, phase A: runs that may hold a race -> (start, end) list
 cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,

@@ -101,11 +101,11 @@ def test_workspace_scales_with_problem():
     shared_kept = 3 * out_keys
     keys = out_keys + min(shared_kept, max(1 << 24, shared_kept // 16))
     # (+ four raw-witness buffers of at most 2^24 words and small tables); the
-    # cell filter adds a third key buffer and 8 bytes per cell (3.4M cells)
+    # cell filter adds 4 bytes per cell (3.4M cells)
     cells = 2 * 1024 * 1024 + 4096 * 324
     base = k.workspace_size(flags=hg.NO_CELL_FILTER)
     assert 16 * keys <= base < 16 * keys + 4 * 8 * (1 << 24) + (200 << 20)
-    assert 24 * keys + 8 * cells <= ws < base + 8 * keys + 8 * cells + (1 << 20)
+    assert base + 4 * cells <= ws < base + 4 * cells + (1 << 20)
     # one global sort of every kept key needs buffers for all of them
     assert k.workspace_size(flags=hg.NO_SPLIT) >= 16 * (out_keys + shared_kept)
     # a caller-given room for shared keys sizes the buffers

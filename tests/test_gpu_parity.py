@@ -258,6 +258,11 @@ def test_every_sort_shape_gives_the_same_result():
             hg.sort_variant(v)
             for w, o in zip(ws, want):
                 _same(hg.check(w.text, w.binding, cap=1 << 20), o)
+                # every key through the sort: one global sort, no cell filter
+                _same(hg.check(w.text, w.binding, cap=1 << 20,
+                               flags=hg.NO_SMALL | hg.NO_SPLIT | hg.NO_CELL_FILTER), o)
+                if w is ws[1]:
+                    assert hg.stats()["n_sorted_keys"] > 100000
     finally:
         hg.sort_variant(cur)
 
