@@ -269,11 +269,13 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // CTAs per SM the registers are budgeted for) and on the warp ranking (RA:
 // the leader of each digit's peers takes the warp's running count with one
 // shared atomic add and passes it on by shuffle, so the slots pipeline; else
-// a read, a leader write and two warp barriers per slot); the sort
-// autotuner picks the shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
+// a read, a leader write and two warp barriers per slot) and on how a lane
+// finds the lanes with its digit (MS: nine ballots, one per digit bit and
+// one for "has a key"; else the match instruction); the sort autotuner picks
+// the shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
 // handled in increasing order and the look-back only waits on tiles held by
 // running CTAs.
-template <int T, int KPT, int MINB, bool RA = false>
+template <int T, int KPT, int MINB, bool RA = false, bool MS = false>
 __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                           const uint64_t* n_dev, uint64_t n_max, int shift,
                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
@@ -318,7 +320,18 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
       const bool live = i < n && (!ctab || cell_kept(ctab, ncells, shr64(k[s], rsh)));
       const uint32_t d = live ? (uint32_t)((k[s] >> shift) & 255) : 256u;
       if (next_hist && d < 256u) atomicAdd(&nhist[(uint32_t)(k[s] >> next_shift) & 255u], 1u);
-      const unsigned peers = __match_any_sync(FULL, d);
+      unsigned peers;
+      if constexpr (MS) {
+        const unsigned has = __ballot_sync(FULL, d < 256u);
+        peers = d < 256u ? has : ~has;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const unsigned bb = __ballot_sync(FULL, (d >> b) & 1u);
+          peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+      } else {
+        peers = __match_any_sync(FULL, d);
+      }
       uint32_t old = 0;
       if constexpr (RA) {
         // one warp's atomics reach shared memory in issue order, slot after slot
@@ -1097,6 +1110,8 @@ const SortVariant* sort_variants(int* count) {
       {(const void*)onesweep_kernel<256, 16, 3, true>, 256, 16, onesweep_smem<256, 16>()},
       {(const void*)onesweep_kernel<256, 12, 4, true>, 256, 12, onesweep_smem<256, 12>()},
       {(const void*)onesweep_kernel<512, 8, 2, true>, 512, 8, onesweep_smem<512, 8>()},
+      {(const void*)onesweep_kernel<256, 16, 3, true, true>, 256, 16, onesweep_smem<256, 16>()},
+      {(const void*)onesweep_kernel<512, 8, 2, true, true>, 512, 8, onesweep_smem<512, 8>()},
   };
   *count = (int)(sizeof(v) / sizeof(v[0]));
   return v;
