@@ -220,8 +220,9 @@ std::string jit_source(const DProg& P, bool split) {
       if (once && rep != "nrep" && loop_guard(P.guard[A.gfirst + g])) continue;
       c += ind + "  live = live && " + lin(P, "P->guard[" + S(A.gfirst + g) + "]", P.guard[A.gfirst + g]) + " >= 0;\n";
     }
-    // a count-only access taken once per unit never reads its index or interval
-    const bool no_idx = once && count_only(a) && (lin_dep(A.idx) || lin_dep(A.iv));
+    // a count-only access taken once per unit never reads its index or
+    // interval: in bounds everywhere, its live instances are its keys
+    const bool no_idx = once && count_only(a);
     c += ind + "  const T idx = " + (no_idx ? std::string("0") : lin(P, at + ".idx", A.idx)) + ";\n";
     if (A.bounds_free)
       c += ind + "  const bool inb = live;\n";
@@ -493,26 +494,47 @@ uint64_t jit_eval_ops(const DProg& P) {
   auto op_cost = [&](const DOp& op) {
     return (uint64_t)op.lin.n + (op.kind == OP_DIV ? 3u : op.kind == OP_MOD ? 5u : 0u);
   };
-  auto acc_cost = [&](const DAcc& A) {
-    uint64_t c = (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n + (P.WVB ? (uint64_t)A.wv.n + 2 : 0);
+  // (a count-only access: its guards alone)
+  auto acc_cost = [&](int a) {
+    const DAcc& A = P.acc[a];
+    uint64_t c = An.count_only(a) ? 0 : (uint64_t)A.idx.n + 2 + (uint64_t)A.iv.n + (P.WVB ? (uint64_t)A.wv.n + 2 : 0);
     for (int g = 0; g < A.ng; g++) c += (uint64_t)P.guard[A.gfirst + g].n + 1;
     return c;
   };
+  // an op counts when an evaluated expression reads it (directly or through
+  // later ops); ops only count-only accesses' indexes read are never computed
+  std::vector<char> need(MAXSLOT, 0);
+  auto mark = [&](const DLin& L) {
+    for (int t = 0; t < L.n; t++) need[P.term[L.first + t].slot] = 1;
+  };
+  for (int a = 0; a < P.nacc; a++) {
+    const DAcc& A = P.acc[a];
+    if (A.dead) continue;
+    if (!An.count_only(a)) {
+      mark(A.idx);
+      mark(A.iv);
+      if (P.WVB) mark(A.wv);
+    }
+    for (int g = 0; g < A.ng; g++) mark(P.guard[A.gfirst + g]);
+  }
+  for (int k = P.nfix + P.niter - 1; k >= 0; k--)
+    if (need[P.ops[k].dst]) mark(P.ops[k].lin);
+  auto op_need = [&](int k) { return need[P.ops[k].dst] ? op_cost(P.ops[k]) : (uint64_t)0; };
   uint64_t once = 0, per_it = 0;
   bool loop_body = false;
-  for (int k = 0; k < P.nfix; k++) once += op_cost(P.ops[k]);
+  for (int k = 0; k < P.nfix; k++) once += op_need(k);
   for (int a = 0; a < P.nacc; a++) {
     const DAcc& A = P.acc[a];
     if (A.dead) continue;
     if (An.invariant(a) || An.ranged(a)) {
-      once += acc_cost(A);
+      once += acc_cost(a);
     } else {
-      per_it += acc_cost(A);
+      per_it += acc_cost(a);
       loop_body = true;
     }
   }
   if (loop_body)
-    for (int k = P.nfix; k < P.nfix + P.niter; k++) per_it += op_cost(P.ops[k]);
+    for (int k = P.nfix; k < P.nfix + P.niter; k++) per_it += op_need(k);
   return (uint64_t)P.nblk * (uint64_t)P.nthr * (once + (uint64_t)P.nit * per_it);
 }
 

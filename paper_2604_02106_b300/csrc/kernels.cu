@@ -163,6 +163,39 @@ __global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ i
   }
 }
 
+// Up to SCAN_ONE_MAX values: one CTA of 1024 threads, each summing a run of
+// consecutive values, a block scan of the 1024 sums, then the runs written
+// (in place allowed: a thread reads each value before it writes it).
+constexpr uint64_t SCAN_ONE_MAX = 1024 * 64;
+__global__ void __launch_bounds__(1024) scan_one_kernel(const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
+                                                        uint64_t n_max, uint64_t* total) {
+  __shared__ uint64_t ws[32];
+  const uint64_t n = dev_n(n_dev, n_max);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t per = (n + 1023) / 1024;
+  const uint64_t b0 = (uint64_t)threadIdx.x * per;
+  uint64_t s = 0;
+  for (uint64_t k = 0; k < per; ++k)
+    if (b0 + k < n) s += in[b0 + k];
+  const uint64_t x = warp_incl_scan(s, lane);
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t t = ws[lane];
+    const uint64_t ti = warp_incl_scan(t, lane);
+    ws[lane] = ti - t;
+    if (lane == 31 && total) *total = ti;
+  }
+  __syncthreads();
+  uint64_t run = x - s + ws[warp];
+  for (uint64_t k = 0; k < per; ++k)
+    if (b0 + k < n) {
+      const uint64_t v = in[b0 + k];
+      out[b0 + k] = run;
+      run += v;
+    }
+}
+
 // ------------------------------------------------------------------ expand, block-local shared bins
 template <typename T, int MODE>
 __global__ void __launch_bounds__(EXP_THREADS) expand_block_kernel(
@@ -295,6 +328,9 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + TILE - 1) / TILE;
+  // the grid is sized for the most keys the pass can see; CTAs past the
+  // tiles there are leave before touching the ticket
+  if ((uint64_t)blockIdx.x >= ntiles) return;
   const uint64_t ep = (uint64_t)epoch << 56;
   for (int d = threadIdx.x; d < RS_RADIX; d += T) nhist[d] = 0;
   for (;;) {
@@ -1059,6 +1095,11 @@ cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_p
 
 cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                         uint64_t* partials, uint64_t* total) {
+  if (n_max <= SCAN_ONE_MAX) {
+    scan_one_kernel<<<1, 1024, 0, L.s>>>(in, out, n_dev, n_max, total);
+    (*L.launches)++;
+    return cudaGetLastError();
+  }
   uint64_t tiles = (n_max + SCAN_TILE - 1) / SCAN_TILE;
   if (tiles == 0) tiles = 1;
   unsigned grid = (unsigned)(tiles < (uint64_t)L.nsm * 8 ? tiles : (uint64_t)L.nsm * 8);
