@@ -163,37 +163,36 @@ __global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ i
   }
 }
 
-// Up to SCAN_ONE_MAX values: one CTA of 1024 threads, each summing a run of
-// consecutive values, a block scan of the 1024 sums, then the runs written
-// (in place allowed: a thread reads each value before it writes it).
-constexpr uint64_t SCAN_ONE_MAX = 1024 * 64;
-__global__ void __launch_bounds__(1024) scan_one_kernel(const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
-                                                        uint64_t n_max, uint64_t* total) {
-  __shared__ uint64_t ws[32];
+// Up to SCAN_FUSE_TILES tiles: scan_apply_fused takes the raw tile sums of
+// scan_reduce and adds up the ones before its tile itself (no partials pass);
+// the CTA holding the last tile writes the total.
+constexpr uint64_t SCAN_FUSE_TILES = 256;
+__global__ void __launch_bounds__(256) scan_apply_fused(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                        const uint64_t* n_dev, uint64_t n_max,
+                                                        const uint64_t* __restrict__ sums, uint64_t* total) {
   const uint64_t n = dev_n(n_dev, n_max);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t per = (n + 1023) / 1024;
-  const uint64_t b0 = (uint64_t)threadIdx.x * per;
-  uint64_t s = 0;
-  for (uint64_t k = 0; k < per; ++k)
-    if (b0 + k < n) s += in[b0 + k];
-  const uint64_t x = warp_incl_scan(s, lane);
-  if (lane == 31) ws[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    const uint64_t t = ws[lane];
-    const uint64_t ti = warp_incl_scan(t, lane);
-    ws[lane] = ti - t;
-    if (lane == 31 && total) *total = ti;
-  }
-  __syncthreads();
-  uint64_t run = x - s + ws[warp];
-  for (uint64_t k = 0; k < per; ++k)
-    if (b0 + k < n) {
-      const uint64_t v = in[b0 + k];
-      out[b0 + k] = run;
-      run += v;
+  const uint64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  __shared__ uint64_t ws[8];
+  __shared__ uint64_t tot;
+  for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    // tiles before this one: thread i holds sums[i] (nt <= 256)
+    const uint64_t before = threadIdx.x < tile ? sums[threadIdx.x] : 0;
+    block_excl_scan(before, ws, &tot);
+    const uint64_t base = tot;
+    if (tile == nt - 1 && threadIdx.x == 0 && total) *total = base + sums[tile];
+    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * 16;
+    uint64_t v[16], s = 0;
+    for (int k = 0; k < 16; ++k) {
+      v[k] = (b0 + k < n) ? in[b0 + k] : 0;
+      s += v[k];
     }
+    uint64_t run = base + block_excl_scan(s, ws, &tot);
+    for (int k = 0; k < 16; ++k) {
+      if (b0 + k < n) out[b0 + k] = run;
+      run += v[k];
+    }
+  }
+  if (nt == 0 && blockIdx.x == 0 && threadIdx.x == 0 && total) *total = 0;
 }
 
 // ------------------------------------------------------------------ expand, block-local shared bins
@@ -1095,14 +1094,15 @@ cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_p
 
 cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                         uint64_t* partials, uint64_t* total) {
-  if (n_max <= SCAN_ONE_MAX) {
-    scan_one_kernel<<<1, 1024, 0, L.s>>>(in, out, n_dev, n_max, total);
-    (*L.launches)++;
-    return cudaGetLastError();
-  }
   uint64_t tiles = (n_max + SCAN_TILE - 1) / SCAN_TILE;
   if (tiles == 0) tiles = 1;
   unsigned grid = (unsigned)(tiles < (uint64_t)L.nsm * 8 ? tiles : (uint64_t)L.nsm * 8);
+  if (tiles <= SCAN_FUSE_TILES) {
+    scan_reduce<<<grid, 256, 0, L.s>>>(in, n_dev, n_max, partials);
+    scan_apply_fused<<<grid, 256, 0, L.s>>>(in, out, n_dev, n_max, partials, total);
+    (*L.launches) += 2;
+    return cudaGetLastError();
+  }
   scan_reduce<<<grid, 256, 0, L.s>>>(in, n_dev, n_max, partials);
   scan_partials<<<1, 256, 0, L.s>>>(partials, n_dev, n_max, total);
   scan_apply<<<grid, 256, 0, L.s>>>(in, out, n_dev, n_max, partials);
