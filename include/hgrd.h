@@ -330,8 +330,13 @@ int hgrd_mlp_sync_bf16(void* d_model, void* cuda_stream);
  * at its first race, and only if that finds none runs the full check (also
  * stopping at its first race).  The ranked check runs only when the best
  * pair's score (a logit) reaches min_score, so kernels the model deems clean
- * go straight to the full check.  The verdict's racy flag is exact; when racy,
- * the witnesses are the races found (each a real race), not the full set.
+ * go straight to the full check.  With at most `topk` eligible pairs no
+ * scores are computed: every pair is checked at once.  When the checked
+ * accesses cover every eligible pair, the restricted check is the whole
+ * verdict (accesses in no eligible pair race with nothing, Sec. 6.1); its
+ * n_keys / n_oob then count the checked accesses only.  The racy flag is
+ * exact; when racy, the witnesses are the races found (each a real race),
+ * not the full set.  A restricted check small enough for one CTA runs there.
  * Workspace: hgrd_ranked_workspace_size. */
 typedef struct {
   uint32_t n_pairs, stage; /* stage 1: race found by the ranked check; 2: the full check decided */

@@ -355,11 +355,13 @@ __global__ void gather_kernel(const uint64_t* __restrict__ cnt, const uint64_t* 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool small_ok(const Bound& B, uint32_t limit) {
+// nkeys: the most keys the check can make
+bool small_ok_keys(const Bound& B, uint32_t limit, uint64_t nkeys) {
   const DProg& P = B.prog;
-  return !B.wide && B.nkeys_max <= limit && B.nkeys_max <= (uint64_t)SB_KEYS && P.nunits <= SB_UNITS &&
+  return !B.wide && nkeys <= limit && nkeys <= (uint64_t)SB_KEYS && P.nunits <= SB_UNITS &&
          P.RB + P.PB - P.SB <= 8 * SB_PASSES && P.nslot <= SB_SLOTS;
 }
+bool small_ok(const Bound& B, uint32_t limit) { return small_ok_keys(B, limit, B.nkeys_max); }
 
 // The one-CTA verdict of a single small check, written where the device-wide
 // pipeline leaves its results: the counters and the merged-witness buffer.
@@ -382,7 +384,17 @@ __global__ void small_finish_kernel(const uint64_t* __restrict__ out, const uint
 
 }  // namespace
 
-bool small_single_ok(const Bound& B) { return small_ok(B, SB_KEYS); }
+// a check restricted to the accesses in `only` (0 or all ones: every access)
+// can make keys of those accesses alone
+bool small_single_ok(const Bound& B, uint32_t only) {
+  if (only == 0u || only == 0xffffffffu) return small_ok(B, SB_KEYS);
+  const DProg& P = B.prog;
+  uint64_t nk = 0;
+  for (int a = 0; a < P.nacc; a++)
+    if (!P.acc[a].dead && ((only >> a) & 1u))
+      nk += (uint64_t)P.nblk * (uint64_t)P.nthr * (uint64_t)P.nit * (uint64_t)P.acc[a].G;
+  return small_ok_keys(B, SB_KEYS, nk);
+}
 
 cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* counters, uint64_t* scratch,
                                 uint64_t* uniq) {

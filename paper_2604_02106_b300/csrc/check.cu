@@ -19,7 +19,7 @@
 
 namespace hgrd {
 // the batch's on-chip kernel for one small check (batch.cu)
-bool small_single_ok(const Bound& B);
+bool small_single_ok(const Bound& B, uint32_t only);
 cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* counters, uint64_t* scratch,
                                 uint64_t* uniq);
 }  // namespace hgrd
@@ -290,7 +290,7 @@ cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_
   if ((e = cudaMemsetAsync(ws + W.counters + 8 * C_NPB, 0, 8, s)) != cudaSuccess) return e;
   // the path enqueue took for these options (the same decisions, made again)
   const uint32_t fl = o ? o->flags : 0u;
-  const bool small = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(B);
+  const bool small = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(B, o ? o->only_accesses : 0u);
   const bool split = HP.smode && !(fl & HGRD_NO_SPLIT);
   const int passes = split ? B.sort_passes_split : B.sort_passes;
   if (!small) {
@@ -428,7 +428,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // a small check runs whole in one CTA (the batched form's on-chip kernel),
   // unless specialised kernels were asked for; its verdict lands in the
   // counters and merged-witness buffer as usual
-  if (!(fl & (HGRD_NO_SMALL | HGRD_JIT)) && !dprog_resident && small_single_ok(B)) {
+  if (!(fl & (HGRD_NO_SMALL | HGRD_JIT)) && !dprog_resident && small_single_ok(B, restricted ? only : 0u)) {
     CK(launch_small_single(L, dprog, cnt, U(W.raw2), uniq_buffer(d, W, ws)));
     g_prof.mark("small");
     g_stats.small = 1;

@@ -62,8 +62,14 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
     if (rc < 0) return rc;
   }
   inf.n_pairs = np;
+  // the accesses of every eligible pair: the only ones that can race
+  uint32_t cover = 0;
+  for (uint32_t k = 0; k < np; k++) cover |= (1u << ab[2 * k]) | (1u << ab[2 * k + 1]);
+  // with at most top-k pairs every pair is checked first: no scores needed
+  const bool all_pairs = np && np <= topk;
   std::vector<float> score(np, 0.f);
-  if (np && host_scores) {
+  if (all_pairs) {
+  } else if (np && host_scores) {
     std::copy(host_scores, host_scores + np, score.begin());
   } else if (np && d_model) {
     char* w = (char*)d_ws + base;
@@ -84,7 +90,7 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
   oo.flags |= HGRD_NO_PAIR | HGRD_STOP_FIRST;
   // 2. restricted check of the accesses of the top-k pairs
   const float best = np ? *std::max_element(score.begin(), score.end()) : 0.f;
-  if (np && (d_model || host_scores) && topk && best >= min_score) {
+  if (np && (d_model || host_scores) && topk && (all_pairs || best >= min_score)) {
     std::vector<uint32_t> ord(np);
     std::iota(ord.begin(), ord.end(), 0u);
     std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return score[x] > score[y]; });
@@ -97,6 +103,14 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
     inf.keys_ranked = v->n_keys;
     if (v->racy) {
       inf.stage = 1;
+      v->n_instances = d->bound->n_instances;
+      if (info) *info = inf;
+      return rc;
+    }
+    // the checked accesses cover every eligible pair: no race anywhere (an
+    // access in no eligible pair races with nothing, Sec. 6.1)
+    if (mask == cover) {
+      inf.stage = 2;
       v->n_instances = d->bound->n_instances;
       if (info) *info = inf;
       return rc;

@@ -105,3 +105,37 @@ def test_trained_network_beats_random_order(trained):
         hit_r += info_r["stage"] == 1
     assert racy >= 40
     assert hit_t > hit_r + 0.15 * racy, (hit_t, hit_r, racy)
+
+
+def test_restricted_check_small_enough_runs_in_one_cta():
+    # 8192 keys in all, 2048 of the two checked accesses: the restricted check
+    # runs whole in one CTA and finds exactly the oracle's races of that pair
+    text = ("kernel r\narray a global 65536\narray b global 65536\n"
+            "access W a ; width 4 ; idx tx + 64*bx\naccess R a ; width 4 ; idx tx + 1 + 64*bx\n"
+            "access W b ; width 4 ; idx tx\naccess R b ; width 4 ; idx 2*tx + bx\n")
+    from workloads import Binding
+    bnd = Binding((32, 1, 1), (64, 1, 1), ())
+    k = hg.Kernel(text).bind(bnd.grid, bnd.block, bnd.params)
+    o = oracle.check(text, bnd, cap=1 << 20)
+    for mask in (0b0011, 0b1100):
+        g = k.check(cap=1 << 20, only_accesses=mask)
+        assert hg.stats()["small"] == 1
+        assert g.witnesses == [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
+    k.check(cap=1 << 20)
+    assert hg.stats()["small"] == 0
+
+
+def test_ranked_check_of_few_pairs_is_one_restricted_check():
+    # at most top-k eligible pairs: no scores, one restricted check covering
+    # every eligible pair decides both verdicts
+    from workloads import Binding
+    bnd = Binding((4, 1, 1), (64, 1, 1), ())
+    for text, racy in ((("kernel c\narray a global 4096\narray r global 4096\n"
+                         "access W a ; width 4 ; idx tx + 64*bx\naccess R r ; width 4 ; idx tx\n"), False),
+                       (("kernel d\narray a global 4096\narray r global 4096\n"
+                         "access W a ; width 4 ; idx tx\naccess R r ; width 4 ; idx tx\n"), True)):
+        k = hg.Kernel(text).bind(bnd.grid, bnd.block, bnd.params)
+        res, info = rk.check_ranked(k, None, scores=[0.0], topk=4)
+        assert res.racy == racy == oracle.check(text, bnd).racy
+        assert info["n_pairs"] == 1 and info["access_mask"] == 1
+        assert info["stage"] == (1 if racy else 2) and info["keys_full"] == 0
