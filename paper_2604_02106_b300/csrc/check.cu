@@ -712,8 +712,10 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     pair_pre.resize(std::min<uint64_t>(cnt[C_NPAIR], ppre));
     memcpy(pair_pre.data(), stage + pair_at, pair_pre.size() * sizeof(PairRec));
   }
-  if (cnt[C_ERR] & ERR_SMALL_FULL) {
-    // more per-run witnesses than the one-CTA path keeps: run the device-wide pipeline
+  // more per-run witnesses than the one-CTA path keeps: run the device-wide
+  // pipeline, unless the caller wants the first races only (those kept are
+  // real races, and there is at least one)
+  if ((cnt[C_ERR] & ERR_SMALL_FULL) && !(o && (o->flags & HGRD_STOP_FIRST))) {
     hgrd_check_opts o2 = o ? *o : hgrd_check_opts{};
     o2.flags |= HGRD_NO_SMALL;
     o2.flags &= ~(uint32_t)HGRD_GRAPH;

@@ -108,7 +108,7 @@ def test_trained_network_beats_random_order(trained):
 
 
 def test_restricted_check_small_enough_runs_in_one_cta():
-    # 8192 keys in all, 2048 of the two checked accesses: the restricted check
+    # 8192 keys in all, 4096 of the two checked accesses: the restricted check
     # runs whole in one CTA and finds exactly the oracle's races of that pair
     text = ("kernel r\narray a global 65536\narray b global 65536\n"
             "access W a ; width 4 ; idx tx + 64*bx\naccess R a ; width 4 ; idx tx + 1 + 64*bx\n"
@@ -117,10 +117,17 @@ def test_restricted_check_small_enough_runs_in_one_cta():
     bnd = Binding((32, 1, 1), (64, 1, 1), ())
     k = hg.Kernel(text).bind(bnd.grid, bnd.block, bnd.params)
     o = oracle.check(text, bnd, cap=1 << 20)
-    for mask in (0b0011, 0b1100):
-        g = k.check(cap=1 << 20, only_accesses=mask)
-        assert hg.stats()["small"] == 1
-        assert g.witnesses == [x for x in o.witnesses if (mask >> x[3]) & 1 and (mask >> x[4]) & 1]
+    sel = lambda m: [x for x in o.witnesses if (m >> x[3]) & 1 and (m >> x[4]) & 1]
+    g = k.check(cap=1 << 20, only_accesses=0b1100)  # 128 witnesses
+    assert hg.stats()["small"] == 1 and g.witnesses == sel(0b1100)
+    # 2047 witnesses: more than one CTA keeps, so the full set comes from the
+    # device-wide pipeline; stopping at the first races keeps the CTA's
+    g = k.check(cap=1 << 20, only_accesses=0b0011)
+    assert hg.stats()["small"] == 0 and g.witnesses == sel(0b0011)
+    g = k.check(cap=1 << 20, only_accesses=0b0011, flags=hg.STOP_FIRST)
+    assert hg.stats()["small"] == 1 and g.racy and g.witnesses
+    full = {x[:5]: x[5] for x in sel(0b0011)}
+    assert all(x[:5] in full and (x[5] & ~full[x[:5]]) == 0 for x in g.witnesses)
     k.check(cap=1 << 20)
     assert hg.stats()["small"] == 0
 
