@@ -367,7 +367,7 @@ def run_ranked(args):
     wsb = torch.empty(max(rk.ranked_workspace_size(k) for k in hk), dtype=torch.uint8, device="cuda")
     for k in hk[:20]:  # warm-up
         k.check(cap=1 << 10, flags=hg.NO_PAIR, workspace=wsb)
-        rk.check_ranked(k, r, topk=args.topk, workspace=wsb)
+        rk.check_ranked(k, r, topk=args.topk, workspace=wsb, cap=1 << 10)
     plain_res = []
     torch.cuda.synchronize()
     ts = time.perf_counter()
@@ -382,9 +382,9 @@ def run_ranked(args):
         keys = stage1 = 0
         for j, k in enumerate(hk):
             if kw is None:
-                res, info = rk.check_ranked(k, scores=rand_scores[j], topk=args.topk, workspace=wsb)
+                res, info = rk.check_ranked(k, scores=rand_scores[j], topk=args.topk, workspace=wsb, cap=1 << 10)
             else:
-                res, info = rk.check_ranked(k, topk=args.topk, workspace=wsb, **kw)
+                res, info = rk.check_ranked(k, topk=args.topk, workspace=wsb, cap=1 << 10, **kw)
             assert res.racy == plain_res[j].racy
             keys += info["keys_ranked"] + info["keys_full"]
             stage1 += info["stage"] == 1

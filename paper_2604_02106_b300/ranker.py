@@ -161,13 +161,15 @@ def check_ranked(kernel: Kernel, ranker: Ranker | None = None, scores=None, topk
     import torch
     L = _setup()
     o = _opts()
-    n = C.c_size_t()
-    _raise(L.hgrd_ranked_workspace_size(kernel._h, C.byref(o), C.byref(n)))
-    ws = workspace if workspace is not None else getattr(kernel, "_rws", None)
-    if ws is None or ws.numel() < n.value:
-        ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
-        kernel._rws = ws
-    out = (Witness * max(1, cap))()
+    ws = workspace
+    if ws is None:
+        n = C.c_size_t()
+        _raise(L.hgrd_ranked_workspace_size(kernel._h, C.byref(o), C.byref(n)))
+        ws = getattr(kernel, "_rws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+            kernel._rws = ws
+    out = kernel._out(cap)  # reused across calls, like the plain check's
     v = Verdict()
     info = RankInfo()
     sc = None
