@@ -16,6 +16,7 @@
 
 namespace hgrd {
 void pair_features(const hgrd_desc& d, int a, int b, float* f);
+bool small_single_ok(const Bound& B, uint32_t only);
 }
 
 using namespace hgrd;
@@ -53,12 +54,26 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
   cudaStream_t s = (cudaStream_t)stream;
   hgrd_rank_info inf{};
   auto t0 = std::chrono::steady_clock::now();
-  // 1. eligible pairs and their scores
-  std::vector<float> feat((size_t)MAXPAIRS * HGRD_MLP_IN);
+  // a check small enough for one CTA costs about what a restricted check
+  // would: no ranking, straight to the full check
+  const uint32_t fl = o ? o->flags : 0u;
+  const bool one_cta = !(fl & (HGRD_NO_SMALL | HGRD_JIT)) && small_single_ok(*d->bound, 0u);
+  // 1. eligible pairs and their scores (features and scores staged in pinned
+  // host buffers kept per thread)
+  static thread_local float* feat = nullptr;
+  static thread_local float* zs = nullptr;
+  if (!feat) {
+    if (cudaMallocHost((void**)&feat, (size_t)MAXPAIRS * HGRD_MLP_IN * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&zs, (size_t)MAXPAIRS * 4) != cudaSuccess) {
+      if (feat) cudaFreeHost(feat);
+      feat = nullptr;
+      return fail(HGRD_EDEVICE, "pinned staging buffers");
+    }
+  }
   std::vector<uint8_t> ab(2 * MAXPAIRS);
   uint32_t np = 0;
-  if (d_model || host_scores) {
-    rc = hgrd_pair_features(d, feat.data(), ab.data(), MAXPAIRS, &np);
+  if ((d_model || host_scores) && !one_cta) {
+    rc = hgrd_pair_features(d, feat, ab.data(), MAXPAIRS, &np);
     if (rc < 0) return rc;
   }
   inf.n_pairs = np;
@@ -76,13 +91,14 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
     float* dx = (float*)w;
     float* dz = (float*)(w + a256((size_t)MAXPAIRS * HGRD_MLP_IN * 4));
     void* mws = w + a256((size_t)MAXPAIRS * HGRD_MLP_IN * 4) + a256((size_t)MAXPAIRS * 4);
-    if (cudaMemcpyAsync(dx, feat.data(), (size_t)np * HGRD_MLP_IN * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(dx, feat, (size_t)np * HGRD_MLP_IN * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return fail(HGRD_EDEVICE, "feature upload failed");
     rc = hgrd_mlp_predict(d_model, dx, np, dz, mws, hgrd_mlp_workspace_bytes(MAXPAIRS), s);
     if (rc) return rc;
-    if (cudaMemcpyAsync(score.data(), dz, (size_t)np * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(zs, dz, (size_t)np * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(HGRD_EDEVICE, "score download failed");
+    std::copy(zs, zs + np, score.begin());
   }
   inf.ms_rank = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
   hgrd_check_opts oo{};
