@@ -155,12 +155,13 @@ def ranked_workspace_size(kernel: Kernel) -> int:
 
 
 def check_ranked(kernel: Kernel, ranker: Ranker | None = None, scores=None, topk: int = 4, cap: int = 1 << 16,
-                 stream=None, min_score: float = float("-inf"), workspace=None):
+                 stream=None, min_score: float = float("-inf"), workspace=None, **opts):
     """hgrd_check_ranked: (Result, info dict).  With neither a ranker nor scores
-    only the full check runs (stopping at its first race)."""
+    only the full check runs (stopping at its first race).  `opts` as for
+    Kernel.check (e.g. flags=NO_SMALL ranks kernels one CTA would check)."""
     import torch
     L = _setup()
-    o = _opts()
+    o = _opts(**opts)
     ws = workspace
     if ws is None:
         n = C.c_size_t()

@@ -98,10 +98,10 @@ def test_trained_network_beats_random_order(trained):
         if not w.meta["planted"]:
             continue
         racy += 1
-        _, info = rk.check_ranked(k, r, topk=2)
+        _, info = rk.check_ranked(k, r, topk=2, flags=hg.NO_SMALL)
         hit_t += info["stage"] == 1
         n = info["n_pairs"]
-        _, info_r = rk.check_ranked(k, scores=rng.random(n), topk=2)
+        _, info_r = rk.check_ranked(k, scores=rng.random(n), topk=2, flags=hg.NO_SMALL)
         hit_r += info_r["stage"] == 1
     assert racy >= 40
     assert hit_t > hit_r + 0.15 * racy, (hit_t, hit_r, racy)
@@ -134,15 +134,20 @@ def test_restricted_check_small_enough_runs_in_one_cta():
 
 def test_ranked_check_of_few_pairs_is_one_restricted_check():
     # at most top-k eligible pairs: no scores, one restricted check covering
-    # every eligible pair decides both verdicts
+    # every eligible pair decides both verdicts (16384 keys: more than one
+    # CTA's check, which would skip the ranking altogether)
     from workloads import Binding
-    bnd = Binding((4, 1, 1), (64, 1, 1), ())
-    for text, racy in ((("kernel c\narray a global 4096\narray r global 4096\n"
+    bnd = Binding((128, 1, 1), (64, 1, 1), ())
+    for text, racy in ((("kernel c\narray a global 16384\narray r global 16384\n"
                          "access W a ; width 4 ; idx tx + 64*bx\naccess R r ; width 4 ; idx tx\n"), False),
-                       (("kernel d\narray a global 4096\narray r global 4096\n"
+                       (("kernel d\narray a global 16384\narray r global 16384\n"
                          "access W a ; width 4 ; idx tx\naccess R r ; width 4 ; idx tx\n"), True)):
         k = hg.Kernel(text).bind(bnd.grid, bnd.block, bnd.params)
         res, info = rk.check_ranked(k, None, scores=[0.0], topk=4)
         assert res.racy == racy == oracle.check(text, bnd).racy
         assert info["n_pairs"] == 1 and info["access_mask"] == 1
         assert info["stage"] == (1 if racy else 2) and info["keys_full"] == 0
+    # a kernel whose full check runs in one CTA is not ranked
+    k = hg.Kernel(text).bind((4, 1, 1), (64, 1, 1), ())
+    res, info = rk.check_ranked(k, None, scores=[0.0], topk=4)
+    assert res.racy and info["n_pairs"] == 0 and info["stage"] == 2
