@@ -146,7 +146,7 @@ STAGE_BYTES = {"expand_write": 8, "candidates": 8}
 for _p in range(8):
     STAGE_BYTES[f"sort_pass{_p}"] = 16
 # stages that are one kernel launch (the others group several launches)
-SINGLE_KERNEL = {"expand_count", "expand_write", "candidates", "exact"} | {f"sort_pass{_p}" for _p in range(8)}
+SINGLE_KERNEL = {"expand_count", "expand_write", "cell_filter", "candidates", "exact"} | {f"sort_pass{_p}" for _p in range(8)}
 
 
 def _sources_sha1():
@@ -553,17 +553,22 @@ def main():
             stages.setdefault(name, []).append(t)
     stage_ms = {n: sum(v) / len(v) for n, v in stages.items()}
     hbm_peak, peak_kind = _peaks()
-    # keys each HBM-bound stage moves: the sort and the candidate scan walk the
-    # sorted (global-array) keys; the write stage stores those plus the keys of
-    # candidate shared-memory bins
-    stage_keys = {n: n_sorted for n in stage_ms}
-    stage_keys["expand_write"] = n_sorted + n_binned
-    hbm_stages = {n: t for n, t in stage_ms.items() if n in STAGE_BYTES}
-    hdom = max(hbm_stages, key=hbm_stages.get)
-    achieved = STAGE_BYTES[hdom] * stage_keys[hdom] / (hbm_stages[hdom] / 1000.0) / 1e9
+    # bytes each HBM-bound stage moves: the write stage stores the written
+    # global keys and the keys of candidate shared-memory bins; the cell
+    # filter reads the written keys; the first sort pass reads the written
+    # keys and writes the kept ones (the cell filter runs inside it); later
+    # passes read and write, the candidate scan reads, the kept keys
+    n_written = st0["n_written_keys"]
+    stage_bytes = {n: STAGE_BYTES[n] * n_sorted for n in stage_ms if n in STAGE_BYTES}
+    stage_bytes["expand_write"] = 8 * (n_written + n_binned)
+    if "sort_pass0" in stage_bytes:
+        stage_bytes["sort_pass0"] = 8 * (n_written + n_sorted)
+    if "cell_filter" in stage_ms:
+        stage_bytes["cell_filter"] = 8 * n_written
+    hdom = max(stage_bytes, key=lambda n: stage_ms[n])
+    achieved = stage_bytes[hdom] / (stage_ms[hdom] / 1000.0) / 1e9
     roof_hbm = {"bound": "hbm", "kernel": hdom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "bytes_per_key": STAGE_BYTES[hdom],
-                "keys_per_launch": stage_keys[hdom]}
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "bytes_per_launch": stage_bytes[hdom]}
     # the dominant kernel: the longest single-launch stage
     dom = max((n for n in stage_ms if n in SINGLE_KERNEL), key=stage_ms.get)
     traffic = None
@@ -574,12 +579,11 @@ def main():
             traffic = tr["per_launch_bytes"][dom]
     except Exception:
         traffic = None
-    if dom in STAGE_BYTES:
+    if dom in stage_bytes:
         roofline = dict(roof_hbm, kernel=dom, traffic=traffic)
         if dom != hdom:
-            a = STAGE_BYTES[dom] * stage_keys[dom] / (stage_ms[dom] / 1000.0) / 1e9
-            roofline.update(achieved=a, frac=a / hbm_peak, bytes_per_key=STAGE_BYTES[dom],
-                            keys_per_launch=stage_keys[dom])
+            a = stage_bytes[dom] / (stage_ms[dom] / 1000.0) / 1e9
+            roofline.update(achieved=a, frac=a / hbm_peak, bytes_per_launch=stage_bytes[dom])
     else:
         # the count pass evaluates the program: integer-issue bound; its work
         # is the integer operations of the walk that runs (on the specialised

@@ -184,6 +184,8 @@ typedef struct {
                                count once per thread */
   uint32_t small;           /* 1 when the check ran whole in one CTA */
   uint32_t cell_filter;     /* 1 when only keys of cells with a writer and two threads were sorted */
+  uint64_t n_written_keys;  /* global-array keys the expansion wrote (the first sort pass reads
+                               them all; with the cell filter it keeps n_sorted_keys of them) */
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,

@@ -106,7 +106,7 @@ class Stats(C.Structure):
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
                 ("shared_bins", C.c_uint32), ("jit", C.c_uint32), ("eval_ops", C.c_uint64),
-                ("small", C.c_uint32), ("cell_filter", C.c_uint32)]
+                ("small", C.c_uint32), ("cell_filter", C.c_uint32), ("n_written_keys", C.c_uint64)]
 
 
 _lib = None

@@ -731,6 +731,7 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                                                                        : d->bound->sort_passes;
     const bool cf = filter_runs(W, passes) && !g_stats.small;
     g_stats.n_sorted_keys = cf ? cnt[C_NGC] : cnt[C_NG];
+    g_stats.n_written_keys = g_stats.small ? 0 : cnt[C_NG];
     g_stats.cell_filter = cf ? 1u : 0u;
   }
   g_stats.n_binned_keys = g_stats.shared_bins ? cnt[C_NSC] : 0;
