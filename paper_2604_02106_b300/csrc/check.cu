@@ -502,13 +502,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     nkeys = cnt + C_NGC;
     g_prof.mark("cell_filter");
   }
-  // the expansion (or the filter) counted digit 0; each pass counts the digit of the next
+  // the expansion (or the filter) counted digit 0; each pass counts the digit
+  // of the next.  After the first pass, at most 4096 keys left are sorted on
+  // the remaining digits by one CTA, straight into the final buffer, and the
+  // later passes return at once.
   for (int p = 0; p < P; p++) {
     CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
     CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256,
                        U(W.status), cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
                        p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1),
-                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB));
+                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB, p > 0 ? cnt + C_TAIL : nullptr));
+    if (p == 0 && P > 1) CK(launch_tail_sort(L, out, fin, nkeys, nsort, HP.SB + 8, P - 1, cnt + C_TAIL));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
                                 "sort_pass4", "sort_pass5", "sort_pass6", "sort_pass7"};

@@ -313,7 +313,9 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
                                                           unsigned long long* ticket, uint32_t epoch, uint64_t* err,
                                                           uint64_t* next_hist, int next_shift,
-                                                          const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh) {
+                                                          const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh,
+                                                          const uint64_t* skip) {
+  if (skip && *skip) return;  // one CTA already sorted the remaining digits
   constexpr int W = T / 32, TILE = T * KPT;
   extern __shared__ __align__(16) unsigned char osm[];
   uint32_t* whist = reinterpret_cast<uint32_t*>(osm);  // [W][256]
@@ -458,6 +460,96 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
   }
   for (int d = threadIdx.x; d < RS_RADIX; d += T)
     if (next_hist && nhist[d]) atomicAdd((unsigned long long*)&next_hist[d], (unsigned long long)nhist[d]);
+}
+
+// The digits after the first pass of a sort that kept at most TAIL_MAX keys:
+// one CTA loads them into shared memory and runs the remaining LSD passes
+// there (the onesweep ranking, nine ballots and a shared atomic per slot,
+// with one tile and so no look-back), writes the result where the last pass
+// would have, and sets *done so the device-wide passes after it return at
+// once.  With more keys it does nothing.
+constexpr int TAIL_T = 1024, TAIL_KPT = 4, TAIL_MAX = TAIL_T * TAIL_KPT;
+constexpr size_t tail_smem() { return (size_t)2 * TAIL_MAX * 8 + (size_t)(TAIL_T / 32) * RS_RADIX * 4 + RS_RADIX * 4; }
+__global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
+                                                           uint64_t n_max, int shift0, int npass, uint64_t* done) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  uint64_t* A = reinterpret_cast<uint64_t*>(tsm);
+  uint64_t* Bk = A + TAIL_MAX;
+  uint32_t* whist = reinterpret_cast<uint32_t*>(Bk + TAIL_MAX);  // [32 warps][256]
+  uint32_t* dbase = whist + (TAIL_T / 32) * RS_RADIX;             // digit starts
+  const uint64_t n = dev_n(n_dev, n_max);
+  if (n > (uint64_t)TAIL_MAX || npass <= 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) A[i] = in[i];
+  for (int p = 0; p < npass; ++p) {
+    const int shift = shift0 + 8 * p;
+    for (int i = threadIdx.x; i < (TAIL_T / 32) * RS_RADIX; i += TAIL_T) whist[i] = 0;
+    __syncthreads();
+    // warp w ranks keys [128 w, 128 w + 128), slot after slot
+    uint64_t k[TAIL_KPT];
+    uint32_t dr[TAIL_KPT];
+#pragma unroll
+    for (int s = 0; s < TAIL_KPT; ++s) {
+      const uint32_t i = (uint32_t)warp * (TAIL_KPT * 32) + (uint32_t)s * 32 + lane;
+      k[s] = i < n ? A[i] : 0;
+      const uint32_t d = i < n ? (uint32_t)((k[s] >> shift) & 255) : 256u;
+      const unsigned has = __ballot_sync(FULL, d < 256u);
+      unsigned peers = d < 256u ? has : ~has;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const unsigned bb = __ballot_sync(FULL, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
+      }
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (d < 256u && lane == leader) old = atomicAdd(&whist[warp * RS_RADIX + d], (uint32_t)__popc(peers));
+      old = __shfl_sync(FULL, old, leader);
+      dr[s] = d | ((old + __popc(peers & lt)) << 9);
+    }
+    __syncthreads();
+    if (threadIdx.x < RS_RADIX) {  // per digit: starts of the warps' shares, digit total
+      uint32_t sum = 0;
+      for (int w = 0; w < TAIL_T / 32; ++w) {
+        const uint32_t c = whist[w * RS_RADIX + threadIdx.x];
+        whist[w * RS_RADIX + threadIdx.x] = sum;
+        sum += c;
+      }
+      dbase[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (warp == 0) {  // digit starts: lane l scans digits 8l .. 8l+7
+      uint32_t v[8], s8 = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = dbase[lane * 8 + j];
+        s8 += v[j];
+      }
+      uint32_t x = s8;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t run = x - s8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        dbase[lane * 8 + j] = run;
+        run += v[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < TAIL_KPT; ++s) {
+      const uint32_t d = dr[s] & 511u;
+      if (d < 256u) Bk[dbase[d] + whist[warp * RS_RADIX + d] + (dr[s] >> 9)] = k[s];
+    }
+    __syncthreads();
+    uint64_t* t = A;
+    A = Bk;
+    Bk = t;
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) out[i] = A[i];
+  if (threadIdx.x == 0) *done = 1;
 }
 
 template <int T, int KPT>
@@ -1168,7 +1260,7 @@ int sort_variant_current() {
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist, int next_shift, const uint32_t* ctab,
-                            uint64_t ncells, int rsh) {
+                            uint64_t ncells, int rsh, const uint64_t* skip) {
   int nv = 0, dev = 0;
   const SortVariant* V = sort_variants(&nv);
   cudaGetDevice(&dev);
@@ -1182,9 +1274,18 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
   unsigned long long* tk = (unsigned long long*)ticket;
   void* args[] = {(void*)&in, (void*)&out, (void*)&n_dev, (void*)&n_max, (void*)&shift, (void*)&gbase,
                   (void*)&status, (void*)&tk, (void*)&epoch, (void*)&err, (void*)&next_hist, (void*)&next_shift,
-                  (void*)&ctab, (void*)&ncells, (void*)&rsh};
+                  (void*)&ctab, (void*)&ncells, (void*)&rsh, (void*)&skip};
   (*L.launches)++;
   return cudaLaunchKernel(S.fn, dim3(grid), dim3(S.threads), args, S.smem, L.s);
+}
+
+cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                             int shift0, int npass, uint64_t* done) {
+  cudaError_t e = allow_smem((const void*)tail_sort_kernel, tail_smem());
+  if (e != cudaSuccess) return e;
+  tail_sort_kernel<<<1, TAIL_T, tail_smem(), L.s>>>(in, out, n_dev, n_max, shift0, npass, done);
+  (*L.launches)++;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,

@@ -54,7 +54,13 @@ cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0,
-                            const uint32_t* ctab = nullptr, uint64_t ncells = 0, int rsh = 0);
+                            const uint32_t* ctab = nullptr, uint64_t ncells = 0, int rsh = 0,
+                            const uint64_t* skip = nullptr);
+// the passes after the first over the digits from shift0 (npass of them) in
+// one CTA when at most 4096 keys remain; sets *done then (the passes given
+// `skip` = done return at once)
+cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
+                             int shift0, int npass, uint64_t* done);
 
 // conflict scan, phase A: runs that may hold a race -> (start, end) list
 cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
