@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
       }
     }
     __syncthreads();
-    // digits: counts across warps, warp-exclusive prefixes, look-back
+    // digits: counts across warps, warp-exclusive prefixes; the tile's
+    // aggregate is published before its keys move, the look-back comes after
     for (int t = threadIdx.x; t < RS_RADIX; t += T) {
       uint32_t sum = 0;
 #pragma unroll
@@ -395,32 +396,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
         sum += c;
       }
       dsum[t] = sum;
-      uint64_t* my = status + tile * RS_RADIX + t;
-      uint64_t excl = 0;
-      if (tile == 0) {
-        st_relaxed(my, ep | ST_PREFIX | sum);
-      } else {
-        st_relaxed(my, ep | ST_AGG | sum);
-        uint64_t p = tile - 1;
-        uint32_t spins = 0;
-        for (;;) {
-          const uint64_t wv = ld_relaxed(status + p * RS_RADIX + t);
-          const bool ready = (wv >> 56) == epoch && (wv & (3ull << 54)) != 0;
-          if (!ready) {
-            if (++spins > SPIN_LIMIT) {
-              atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-            continue;
-          }
-          excl += wv & ST_VAL;
-          if ((wv & ST_PREFIX) || p == 0) break;
-          --p;
-        }
-        st_relaxed(my, ep | ST_PREFIX | (excl + sum));
-      }
-      gofs[t] = gbase[t] + excl;
+      st_relaxed(status + tile * RS_RADIX + t, ep | (tile == 0 ? ST_PREFIX : ST_AGG) | sum);
     }
     __syncthreads();
     if (warp == 0) {  // tile-local digit starts: lane l scans digits 8l .. 8l+7
@@ -448,6 +424,51 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
     for (int s = 0; s < KPT; ++s) {
       const uint32_t d = dr[s] & 511u;
       if (d < 256u) stage[tstart[d] + whist[warp * RS_RADIX + d] + (dr[s] >> 9)] = k[s];
+    }
+    // look-back: the keys of the tile before this one with each digit
+    for (int t = threadIdx.x; t < RS_RADIX; t += T) {
+      uint64_t excl = 0;
+      if (tile != 0) {
+        // walk back over the predecessors LBW at a time: the loads of a
+        // window are independent, so one memory round trip covers LBW tiles;
+        // aggregates add up to the nearest inclusive prefix (tile 0 always
+        // publishes one), a tile not yet published is read again
+        constexpr int LBW = 4;
+        uint64_t p = tile - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const int m = p >= (uint64_t)(LBW - 1) ? LBW : (int)p + 1;
+          uint64_t wv[LBW];
+#pragma unroll
+          for (int j = 0; j < LBW; ++j)
+            if (j < m) wv[j] = ld_relaxed(status + (p - (uint64_t)j) * RS_RADIX + t);
+          bool done = false, stall = false;
+          uint64_t used = 0;
+#pragma unroll
+          for (int j = 0; j < LBW; ++j) {
+            if (j >= m || done || stall) continue;
+            const bool ready = (wv[j] >> 56) == epoch && (wv[j] & (3ull << 54)) != 0;
+            if (!ready) {
+              stall = true;
+              continue;
+            }
+            excl += wv[j] & ST_VAL;
+            if ((wv[j] & ST_PREFIX) || p == (uint64_t)j) done = true;
+            else ++used;
+          }
+          if (done) break;
+          p -= used;
+          if (stall) {
+            if (++spins > SPIN_LIMIT) {
+              atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        st_relaxed(status + tile * RS_RADIX + t, ep | ST_PREFIX | (excl + dsum[t]));
+      }
+      gofs[t] = gbase[t] + excl;
     }
     __syncthreads();
     const uint32_t cnt = *s_kept;
