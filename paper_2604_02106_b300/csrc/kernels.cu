@@ -307,7 +307,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // the shape.  Each CTA loops over tiles taken from a ticket counter, so tiles are
 // handled in increasing order and the look-back only waits on tiles held by
 // running CTAs.
-template <int T, int KPT, int MINB, bool RA = false, bool MS = false>
+template <int T, int KPT, int MINB, bool RA = false, int MS = 0>
 __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                           const uint64_t* n_dev, uint64_t n_max, int shift,
                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
       const uint32_t d = live ? (uint32_t)((k[s] >> shift) & 255) : 256u;
       if (next_hist && d < 256u) atomicAdd(&nhist[(uint32_t)(k[s] >> next_shift) & 255u], 1u);
       unsigned peers;
-      if constexpr (MS) {
+      // MS 1: ballots in every slot; MS 2: ballots in odd slots, the match
+      // instruction in even ones (the ALU and the shared-memory pipe share the work)
+      if (MS == 1 || (MS == 2 && (s & 1))) {
         const unsigned has = __ballot_sync(FULL, d < 256u);
         peers = d < 256u ? has : ~has;
 #pragma unroll
@@ -1264,8 +1266,10 @@ const SortVariant* sort_variants(int* count) {
       {(const void*)onesweep_kernel<256, 16, 3, true>, 256, 16, onesweep_smem<256, 16>()},
       {(const void*)onesweep_kernel<256, 12, 4, true>, 256, 12, onesweep_smem<256, 12>()},
       {(const void*)onesweep_kernel<512, 8, 2, true>, 512, 8, onesweep_smem<512, 8>()},
-      {(const void*)onesweep_kernel<256, 16, 3, true, true>, 256, 16, onesweep_smem<256, 16>()},
-      {(const void*)onesweep_kernel<512, 8, 2, true, true>, 512, 8, onesweep_smem<512, 8>()},
+      {(const void*)onesweep_kernel<256, 16, 3, true, 1>, 256, 16, onesweep_smem<256, 16>()},
+      {(const void*)onesweep_kernel<512, 8, 2, true, 1>, 512, 8, onesweep_smem<512, 8>()},
+      {(const void*)onesweep_kernel<256, 16, 3, true, 2>, 256, 16, onesweep_smem<256, 16>()},
+      {(const void*)onesweep_kernel<512, 8, 2, true, 2>, 512, 8, onesweep_smem<512, 8>()},
   };
   *count = (int)(sizeof(v) / sizeof(v[0]));
   return v;
