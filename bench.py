@@ -149,11 +149,19 @@ for _p in range(8):
 SINGLE_KERNEL = {"expand_count", "expand_write", "cell_filter", "candidates", "exact"} | {f"sort_pass{_p}" for _p in range(8)}
 
 
-def _sources_sha1():
-    """Hash of the sources the profiled kernels are built from."""
+# sources each profiled kernel is built from: the expansion kernels are
+# generated by jit.cpp from the device headers; the sort, filter and scan
+# kernels live in kernels.cu
+SOURCE_GROUPS = {"expand": ("jit.cpp", "expand_body.cuh", "kcommon.cuh", "hgrd_internal.h"),
+                 "kernels": ("kernels.cu", "expand_body.cuh", "kcommon.cuh", "hgrd_internal.h")}
+STAGE_GROUP = {"expand_count": "expand", "expand_write": "expand"}
+
+
+def _sources_sha1(group):
+    """Hash of the sources a group of profiled kernels is built from."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("kernels.cu", "kcommon.cuh", "expand_body.cuh", "jit.cpp", "hgrd_internal.h"):
+    for f in SOURCE_GROUPS[group]:
         with open(os.path.join(ROOT, "paper_2604_02106_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -575,7 +583,8 @@ def main():
     try:  # DRAM bytes per launch from an ncu capture of these very sources
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("sources_sha1") == _sources_sha1() and dom in tr.get("per_launch_bytes", {}):
+        grp = STAGE_GROUP.get(dom, "kernels")
+        if tr.get("sources_sha1", {}).get(grp) == _sources_sha1(grp) and dom in tr.get("per_launch_bytes", {}):
             traffic = tr["per_launch_bytes"][dom]
     except Exception:
         traffic = None
