@@ -338,7 +338,10 @@ int hgrd_mlp_sync_bf16(void* d_model, void* cuda_stream);
  * verdict (accesses in no eligible pair race with nothing, Sec. 6.1); its
  * n_keys / n_oob then count the checked accesses only.  The racy flag is
  * exact; when racy, the witnesses are the races found (each a real race),
- * not the full set.  A restricted check small enough for one CTA runs there.
+ * not the full set.  A restricted check small enough for one CTA runs there,
+ * and a kernel whose full check runs in one CTA is not ranked at all.  The
+ * first call on a host thread allocates 200 KB of pinned host memory for the
+ * features and scores, kept for the thread's lifetime.
  * Workspace: hgrd_ranked_workspace_size. */
 typedef struct {
   uint32_t n_pairs, stage; /* stage 1: race found by the ranked check; 2: the full check decided */
