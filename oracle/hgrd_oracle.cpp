@@ -23,6 +23,15 @@
 //     atomics never race; two atomics of at least block scope never race
 //     inside a block; a block-scope atomic does not order threads of another
 //     block (race of insufficient scope).
+//   * Sec. 6.5 ("Support acquire-release synchronization") and Table 2's
+//     highlighted addr(syn(Ai)) != addr(syn(Aj)) constraint: two instances
+//     whose accesses are both guarded by acquire-release (a lock, or a
+//     producer's release and a consumer's acquire) at the same address do not
+//     race; guarded at different addresses, or only one of them guarded, they
+//     still may.  Appendix A ("Scoped acquire-release"): an inter-threadblock
+//     pair needs device scope on both, an intra-threadblock or intra-warp pair
+//     block scope or wider (always the case); the scope of a guard is the
+//     narrower of its parts.
 //   * Table 1 / Table 2: addr, tb, id, wp constraints per race type.
 //   * Sec. 4 / 5.1, host classes (1)-(5): the binding supplies every parameter
 //     and launch dimension; `assert` lines must hold for it.
@@ -167,6 +176,9 @@ struct Access {
   int scope = 1;  // 0 block, 1 device
   P idx, iv, wv;  // iv: block-barrier interval; wv: warp-barrier interval
   std::vector<Cond> guards;
+  int sync_array = -1;  // acquire-release guard (Sec. 6.5): array of its address, -1 none
+  P sync;               // element of that array the guard acquires / releases
+  int sync_scope = 1;   // 0 block, 1 device (the narrower of the guard's parts)
 };
 struct Desc {
   std::vector<std::string> params;
@@ -448,6 +460,19 @@ Desc parse(const std::string& text) {
           if (body == "block") a.scope = 0;
           else if (body == "device") a.scope = 1;
           else ps.bad("scope must be block or device");
+        } else if (fw[0] == "sync") {
+          // sync <array> <element>: the access is guarded by acquire-release at that address
+          if (fw.size() < 3) ps.bad("sync needs an array and an element");
+          int sa = -1;
+          for (size_t k = 0; k < d.arrays.size(); k++)
+            if (d.arrays[k].name == fw[1]) sa = (int)k;
+          if (sa < 0) ps.bad("unknown sync array '" + fw[1] + "'");
+          a.sync_array = sa;
+          a.sync = ps.full_expr(trim(body.substr(body.find(fw[1]) + fw[1].size())));
+        } else if (fw[0] == "syncscope") {
+          if (body == "block") a.sync_scope = 0;
+          else if (body == "device") a.sync_scope = 1;
+          else ps.bad("syncscope must be block or device");
         } else if (fw[0] == "line") {
           // source line of the access: informational
         } else {
@@ -498,6 +523,7 @@ struct Inst {
   int64_t it[4];
   int acc;
   int64_t iv, wv;
+  int64_t sync;  // element of the access's acquire-release guard (when it has one)
 };
 
 // Kinds a pair of accesses may race with (bit0 inter-block, bit1 intra-block,
@@ -520,6 +546,20 @@ int pair_kind(const Inst& x, const Inst& y) {
   if (x.iv != y.iv) return 0;                      // separated by a block barrier
   if (x.thr / 32 != y.thr / 32) return 2;          // a warp barrier does not order warps
   return x.wv == y.wv ? 4 : 0;                     // same warp: a warp barrier orders them
+}
+
+// Race type of one pair of instances once acquire-release is taken into
+// account (Sec. 6.5, Table 2, Appendix A): guards at one address order the
+// pair if their scope covers its type.
+int race_kind(const Desc& d, const Inst& x, const Inst& y) {
+  const int k = pair_kind(x, y);
+  if (!k) return 0;
+  const Access &A = d.acc[x.acc], &B = d.acc[y.acc];
+  if (A.sync_array < 0 || B.sync_array < 0) return k;       // syn() is NULL for one of them
+  if (A.sync_array != B.sync_array || x.sync != y.sync) return k;  // the guard addresses differ
+  const int scope = std::min(A.sync_scope, B.sync_scope);
+  if (k == 1 && scope == 0) return k;  // inter-threadblock needs device scope
+  return 0;
 }
 
 struct Key {
@@ -586,6 +626,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
       collect_divisors(a.idx.get(), divs);
       collect_divisors(a.iv.get(), divs);
       collect_divisors(a.wv.get(), divs);
+      if (a.sync_array >= 0) collect_divisors(a.sync.get(), divs);
       for (auto& g : a.guards) {
         collect_divisors(g.lhs.get(), divs);
         collect_divisors(g.rhs.get(), divs);
@@ -648,6 +689,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
                           in.acc = a;
                           in.iv = eval(A.iv.get(), e);
                           in.wv = eval(A.wv.get(), e);
+                          in.sync = A.sync_array >= 0 ? eval(A.sync.get(), e) : 0;
                           const int64_t g = d.arrays[A.array].granule;
                           for (int64_t gr = off / g; gr < (off + w) / g; gr++) {
                             n_keys++;
@@ -675,7 +717,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
           int mask = 0;
           for (size_t i = 0; i < by[a].size() && mask != allow; i++)
             for (size_t j = (a == b ? i + 1 : 0); j < by[b].size() && mask != allow; j++)
-              mask |= pair_kind(*by[a][i], *by[b][j]) & allow;
+              mask |= race_kind(d, *by[a][i], *by[b][j]) & allow;
           if (mask) {
             const int64_t byte = kv.first.granule * d.arrays[kv.first.array].granule;
             wit[{kv.first.space, kv.first.array, byte, a, b}] |= mask;
@@ -717,7 +759,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
           for (const Inst& y : kv.second) {
             if (y.acc != mw.acc_hi) continue;
             if (mw.acc_lo == mw.acc_hi && !key_less(x, y)) continue;
-            if (!(pair_kind(x, y) & allow)) continue;
+            if (!(race_kind(d, x, y) & allow)) continue;
             bool better = !found || key_less(x, bx) || (!key_less(bx, x) && key_less(y, byy));
             if (better) {
               bx = x;

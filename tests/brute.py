@@ -12,7 +12,10 @@ compares every pair of live, in-bounds instances directly:
     block, interval, warp and warp interval, different threads) — Sec. 2,
     Table 2, and Sec. 5.2 for the warp barrier;
   * two loads never race, nor do two device-scope atomics; two atomics of
-    block scope or wider never race inside one block (Sec. 6.1, Appendix A).
+    block scope or wider never race inside one block (Sec. 6.1, Appendix A);
+  * two accesses both guarded by acquire-release at the same address do not
+    race, if the guards' narrower scope covers the race type: device for
+    inter-block, block or device otherwise (Sec. 6.5, Table 2, Appendix A).
 
 Used only to pin the CPU oracle on launches of at most a few hundred instances.
 """
@@ -162,7 +165,7 @@ def parse(text):
             f = [x.strip() for x in rest.split(";")]
             kind, arr = f[0].split()
             a = {"kind": kind, "array": [x["name"] for x in d["arrays"]].index(arr), "iv": ("num", 0),
-                 "wv": ("num", 0), "guards": [], "scope": "device"}
+                 "wv": ("num", 0), "guards": [], "scope": "device", "sync": None, "syncscope": "device"}
             for x in f[1:]:
                 k, _, body = x.partition(" ")
                 if k == "width":
@@ -177,6 +180,11 @@ def parse(text):
                     a["guards"].append(_cond(body, d["lets"]))
                 elif k == "scope":
                     a["scope"] = body.strip()
+                elif k == "sync":
+                    sarr, sexpr = body.strip().split(None, 1)
+                    a["sync"] = ([x["name"] for x in d["arrays"]].index(sarr), _Expr(sexpr, d["lets"]).tree)
+                elif k == "syncscope":
+                    a["syncscope"] = body.strip()
             d["acc"].append(a)
     for k, arr in enumerate(d["arrays"]):
         if arr["granule"] is None:
@@ -219,6 +227,7 @@ def instances(d, binding):
                 out.append({"blk": bx + by * gx + bz * gx * gy, "thr": thr, "warp": thr // 32,
                             "it": tuple(it) + (0,) * (4 - len(it)), "acc": ai, "iv": _ev(a["iv"], e),
                             "wv": _ev(a["wv"], e),
+                            "sync": None if a["sync"] is None else (a["sync"][0], _ev(a["sync"][1], e)),
                             "array": a["array"], "shared": arr["shared"], "g": g,
                             "gran": set(range(off // g, (off + a["width"]) // g))})
     return out, n_oob
@@ -247,6 +256,10 @@ def race_kind(d, x, y):
         kind = 4
     if ka == "A" and kb == "A":
         block_scoped = "block" in (d["acc"][x["acc"]]["scope"], d["acc"][y["acc"]]["scope"])
+        if kind != 1 or not block_scoped:
+            return 0
+    if x["sync"] is not None and x["sync"] == y["sync"]:  # one acquire-release address
+        block_scoped = "block" in (d["acc"][x["acc"]]["syncscope"], d["acc"][y["acc"]]["syncscope"])
         if kind != 1 or not block_scoped:
             return 0
     return kind

@@ -332,3 +332,66 @@ def test_warp_exchange_expected_counts(space):
                 for cross in (False, True):
                     w = workloads.warp_exchange(nw, loops, sync, cross, grid=2, space=space)
                     assert oracle.check(w.text, w.binding).n_witness == w.meta["expected_witnesses"]
+
+
+# ---------------------------------------------------------------- acquire-release (Sec. 6.5)
+
+@pytest.mark.parametrize("seed", range(60))
+def test_oracle_matches_brute_force_acquire_release(seed):
+    _cmp_brute(workloads.random_sync(7000 + seed))
+
+
+def _kinds(text, grid=(2, 1, 1), block=(64, 1, 1)):
+    r = oracle.check(text, Binding(grid, block, ()))
+    return {(w[3], w[4]): w[5] for w in r.witnesses}
+
+
+def test_acquire_release_closed_forms():
+    # a read-modify-write of one counter by every thread of two blocks of two
+    # warps: every race type between the read and the write and among writes
+    rmw = "kernel c\narray c global 4\narray L global 64\narray F global 64\n"
+    R, W = "access R c ; width 4 ; idx 0", "access W c ; width 4 ; idx 0"
+    assert _kinds(rmw + f"{R}\n{W}\n") == {(0, 1): 7, (1, 1): 7}
+    # both inside one device-scope lock (Sec. 6.5 "Lock/unlock"): no race
+    assert _kinds(rmw + f"{R} ; sync L 0\n{W} ; sync L 0\n") == {}
+    # a block-scope lock orders one block's threads only (Appendix A): with
+    # both guards block scoped every inter-block pair races; with the read's
+    # block scoped, the read-write pairs do, the writes (device) do not
+    assert _kinds(rmw + f"{R} ; sync L 0 ; syncscope block\n{W} ; sync L 0 ; syncscope block\n") == \
+        {(0, 1): 1, (1, 1): 1}
+    assert _kinds(rmw + f"{R} ; sync L 0 ; syncscope block\n{W} ; sync L 0 ; syncscope device\n") == {(0, 1): 1}
+    # only the write guarded: the read still races with it; writes do not
+    assert _kinds(rmw + f"{R}\n{W} ; sync L 0\n") == {(0, 1): 7}
+    # locks of different addresses do not order (Table 2, addr(syn) differ)
+    assert _kinds(rmw + f"{R} ; sync L 0\n{W} ; sync L 1\n") == {(0, 1): 7}
+    # a lock per thread: other threads hold other locks
+    assert _kinds(rmw + f"{R} ; sync L tx\n{W} ; sync L tx\n") == {(0, 1): 7, (1, 1): 7}
+    # a lock per block: one block's threads are ordered, blocks are not
+    assert _kinds(rmw + f"{R} ; sync L bx\n{W} ; sync L bx\n") == {(0, 1): 1, (1, 1): 1}
+    # per-element locks of a histogram (any function of the element) order it;
+    # a lock index that two threads of one element do not share does not
+    h = "kernel h\narray h global 16\narray L global 64\n"
+    for lk, racy in (("tx % 4", False), ("tx % 2", False), ("(tx + 1) % 4", False), ("tx % 8", True)):
+        t = h + f"access R h ; width 4 ; idx tx % 4 ; sync L {lk}\naccess W h ; width 4 ; idx tx % 4 ; sync L {lk}\n"
+        assert bool(_kinds(t, grid=(1, 1, 1), block=(32, 1, 1))) == racy, lk
+    # producer / consumer (Sec. 6.5): the producer's write released at flag
+    # F[0], the consumers' reads acquired at it
+    pc = "kernel p\narray d global 4\narray F global 64\naccess W d ; width 4 ; idx 0 ; if tx == 0 ; sync F 0\n"
+    assert _kinds(pc + "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 0\n") == {}
+    # (the two blocks' producers stay ordered by their common flag)
+    assert _kinds(pc + "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 1\n") == {(0, 1): 7}
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_invariant_guards_never_add_races(seed):
+    # dropping every acquire-release guard keeps every witness and may add
+    # some; a witness keeps every kind it had
+    w = workloads.random_sync(8000 + seed)
+    g = oracle.check(w.text, w.binding, cap=1 << 20)
+    bare = "\n".join(" ; ".join(f for f in l.split(" ; ") if not f.startswith(("sync ", "syncscope ")))
+                     for l in w.text.splitlines()) + "\n"
+    u = oracle.check(bare, w.binding, cap=1 << 20)
+    full = {x[:5]: x[5] for x in u.witnesses}
+    for x in g.witnesses:
+        assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
+    assert g.n_keys == u.n_keys and g.n_oob == u.n_oob

@@ -102,7 +102,8 @@ class _Writer:
     def add(self, line):
         self.lines.append(line)
 
-    def access(self, kind, array, width, idx, iv=None, guards=(), scope=None, line=None, wv=None):
+    def access(self, kind, array, width, idx, iv=None, guards=(), scope=None, line=None, wv=None, sync=None,
+               syncscope=None):
         f = [f"access {kind} {array}", f"width {width}"]
         if iv is not None:
             f.append(f"iv {iv}")
@@ -113,6 +114,10 @@ class _Writer:
             f.append(f"if {g}")
         if scope is not None:
             f.append(f"scope {scope}")
+        if sync is not None:
+            f.append(f"sync {sync}")
+        if syncscope is not None:
+            f.append(f"syncscope {syncscope}")
         if line is not None:
             f.append(f"line {line}")
         self.lines.append(" ; ".join(f))
@@ -400,6 +405,41 @@ def random_tiny(seed: int, max_instances: int = 2048) -> Workload:
     params = (P, Q)
     return Workload(f"tiny_{seed}", w.text(), Binding(tuple(grid), tuple(block), params),
                     {"loop_bounds": bounds, "n_access": nacc})
+
+
+def random_sync(seed: int, max_instances: int = 1500, supported: bool = False) -> Workload:
+    """Tiny kernel whose accesses may be guarded by acquire-release (Sec. 6.5):
+    `sync L <element>` with a global lock (a constant element), a lock per
+    data element (the access's own index), a lock per thread or per block, in
+    block or device scope; one data array (global or shared), reads, writes
+    and atomics, barrier intervals.  With `supported`, guards are only of the
+    two forms the exhaustive check decides statically: a constant element, or
+    the access's own index on accesses of one width."""
+    rng = SplitMix64(seed)
+    grid = (rng.range(1, 3), 1, 1)
+    block = (rng.choice([2, 3, 8, 16, 33, 40]), rng.range(1, 2), 1)
+    nacc = rng.range(2, 4)
+    while math.prod(grid) * math.prod(block) * nacc > max_instances and block[0] > 2:
+        block = (block[0] // 2, block[1], 1)
+    space = rng.choice(["global", "global", "shared"])
+    w = _Writer(f"sync_{seed & 0xffff}")
+    w.add("param Q")
+    w.add(f"array D {space} 256")
+    w.add("array L global 64")
+    forms = ["0", "1", "tx", "bx", "own"] if not supported else ["0", "1", "own"]
+    for a_id in range(nacc):
+        r = rng.below(10)
+        kind = "R" if r < 4 else ("W" if r < 8 else "A")
+        idx = rng.choice(["0", "tx % Q", "tx / 2", "(tx + bx) % 4", "tx", "3"])
+        iv = str(rng.range(0, 1)) if rng.below(3) == 0 else None
+        sync = syncscope = None
+        if rng.below(3) != 0:
+            f = rng.choice(forms)
+            sync = "L " + (idx if f == "own" else f)
+            syncscope = rng.choice(["block", "device", None])
+        scope = rng.choice(["block", "device"]) if kind == "A" else None
+        w.access(kind, "D", 4, idx, iv=iv, scope=scope, sync=sync, syncscope=syncscope, line=a_id + 1)
+    return Workload(f"sync_{seed}", w.text(), Binding(grid, block, (rng.range(1, 4),)), {"n_access": nacc})
 
 
 def random_shared(seed: int, max_instances: int = 60000) -> Workload:
