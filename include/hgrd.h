@@ -201,7 +201,11 @@ int hgrd_load_desc(const char* text, size_t len, hgrd_desc** out);
  * array sizes >= 0 and every `assert` (HGRD_EHOSTCONSTRAINT when one fails),
  * folds the values into per-access coefficient tables, bounds every
  * expression over the instance box (HGRD_EOVERFLOW when int64 can
- * overflow) and plans the key layout.  Rebinding replaces the old binding. */
+ * overflow) and plans the key layout.  Acquire-release guards (`sync`
+ * fields, Sec. 6.5 with the scopes of Appendix A) are decided here, per pair
+ * of guarded accesses on one lock array: both guard elements constant, or
+ * each access guarded at its own index with equal widths; any other pair of
+ * guard forms is HGRD_EUNSUPPORTED.  Rebinding replaces the old binding. */
 int hgrd_bind_host_params(hgrd_desc* d, const hgrd_binding* b);
 
 /* Device workspace bytes hgrd_check needs for the bound descriptor.  The

@@ -467,6 +467,7 @@ Desc parse(const std::string& text) {
           for (size_t k = 0; k < d.arrays.size(); k++)
             if (d.arrays[k].name == fw[1]) sa = (int)k;
           if (sa < 0) ps.bad("unknown sync array '" + fw[1] + "'");
+          if (d.arrays[sa].space != 0) ps.bad("a sync array must be global");
           a.sync_array = sa;
           a.sync = ps.full_expr(trim(body.substr(body.find(fw[1]) + fw[1].size())));
         } else if (fw[0] == "syncscope") {

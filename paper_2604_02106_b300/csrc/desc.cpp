@@ -345,6 +345,18 @@ void parse_desc(hgrd_desc& d, const std::string& text) {
           if (body == "block") a.scope = 0;
           else if (body == "device") a.scope = 1;
           else raise(HGRD_EPARSE, "scope must be block or device");
+        } else if (key == "sync") {
+          std::string sexpr;
+          const std::string sname = trim(first_word(body, &sexpr));
+          for (size_t k = 0; k < d.arrays.size(); k++)
+            if (d.arrays[k].name == sname) a.sync_arr = (int)k;
+          if (a.sync_arr < 0) raise(HGRD_EPARSE, "unknown sync array '" + sname + "'");
+          if (d.arrays[a.sync_arr].space != HGRD_SPACE_GLOBAL) raise(HGRD_EPARSE, "a sync array must be global");
+          a.sync = parse_expr(d, sexpr);
+        } else if (key == "syncscope") {
+          if (body == "block") a.sync_scope = 0;
+          else if (body == "device") a.sync_scope = 1;
+          else raise(HGRD_EPARSE, "syncscope must be block or device");
         } else if (key == "line") {
           a.line = (int)std::stoll(body);
         } else {
@@ -678,6 +690,19 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         for (Lin& l : guard_lins(F.fold(g.lhs), F.fold(g.rhs), g.op)) af[a].guards.push_back(l);
       }
     }
+    // acquire-release guards (Sec. 6.5): the form of each guard's element, a
+    // constant, the access's own index, or another; folded on a copy of the
+    // folder so that no expression node of theirs joins the program
+    std::vector<char> s_const(d.acc.size(), 0), s_own(d.acc.size(), 0);  // (both, when the index is constant)
+    std::vector<int64_t> sval(d.acc.size(), 0);
+    for (size_t a = 0; a < d.acc.size(); a++) {
+      if (d.acc[a].sync_arr < 0) continue;
+      Folder F2 = F;
+      const Lin s = F2.fold(d.acc[a].sync);
+      s_const[a] = s.is_const();
+      sval[a] = s.c0;
+      s_own[a] = s.key() == af[a].idx.key();
+    }
     // node ranges and loop dependence, in creation order (operands first)
     for (size_t i = 0; i < F.nodes.size(); i++) {
       Node& n = F.nodes[i];
@@ -934,6 +959,25 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         if (x.kind == 2 && y.kind == 2) m = (x.scope == 0 || y.scope == 0) ? 1 : 0;
         if (d.arrays[x.arr].space == HGRD_SPACE_SHARED) m &= ~1;
         if (acc_ivhi[a] < acc_ivlo[b] || acc_ivhi[b] < acc_ivlo[a]) m &= 1;
+        // acquire-release guards at one global address order a pair when
+        // their narrower scope covers its type: always inside a block, across
+        // blocks with device scope on both (Sec. 6.5, Table 2, Appendix A).
+        // Decided here when every racing instance pair of the two accesses
+        // has equal guard elements (both constant and equal, or each access
+        // guarded at its own index with equal widths: one location, one
+        // element) or none has (two different constants).
+        if (m && x.sync_arr >= 0 && x.sync_arr == y.sync_arr && !af[a].dead && !af[b].dead) {
+          bool same = false;
+          if (s_own[a] && s_own[b] && x.width == y.width)
+            same = true;
+          else if (s_const[a] && s_const[b])
+            same = sval[a] == sval[b];
+          else
+            raise(HGRD_EUNSUPPORTED,
+                  "acquire-release guards of two accesses on one array must both be constant or both the "
+                  "access's own index (equal widths)");
+          if (same) m &= std::min(x.sync_scope, y.sync_scope) == 1 ? 0 : 1;
+        }
         if (m & 1) P.einter[a] |= 1u << b;
         if (m & 6) P.eintra[a] |= 1u << b;
       }

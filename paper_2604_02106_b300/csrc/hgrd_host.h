@@ -34,6 +34,8 @@ struct AccessDecl {
   int64_t width = 0;
   int scope = 1;  // 0 block, 1 device (atomics)
   int idx = -1, iv = -1, wv = -1;  // wv: warp-barrier interval (Sec. 5.2)
+  int sync_arr = -1, sync = -1;    // acquire-release guard (Sec. 6.5): global array and element
+  int sync_scope = 1;              // 0 block, 1 device (the narrower of the guard's parts)
   int line = 0;
   std::vector<CondDecl> guards;
 };

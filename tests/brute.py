@@ -183,6 +183,7 @@ def parse(text):
                 elif k == "sync":
                     sarr, sexpr = body.strip().split(None, 1)
                     a["sync"] = ([x["name"] for x in d["arrays"]].index(sarr), _Expr(sexpr, d["lets"]).tree)
+                    assert not d["arrays"][a["sync"][0]]["shared"], "a sync array must be global"
                 elif k == "syncscope":
                     a["syncscope"] = body.strip()
             d["acc"].append(a)

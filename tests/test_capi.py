@@ -110,3 +110,38 @@ def test_workspace_scales_with_problem():
     assert k.workspace_size(flags=hg.NO_SPLIT) >= 16 * (out_keys + shared_kept)
     # a caller-given room for shared keys sizes the buffers
     assert k.workspace_size(max_shared_keys=1 << 20) < ws
+
+
+def test_acquire_release_guards_bind():
+    # acquire-release guards (Sec. 6.5): decided at bind time when both guards
+    # of a pair on one lock array are constant, or both the access's own index
+    # (equal widths); other forms guarding one pair are rejected, a guard
+    # without a guarded partner is fine; a lock array must be global
+    base = "kernel k\narray d global 256\narray L global 64\narray S shared 64\n"
+    ok = [("access W d ; width 4 ; idx 0 ; sync L 0", "access R d ; width 4 ; idx 0 ; sync L 1"),
+          ("access W d ; width 4 ; idx tx % 4 ; sync L tx % 4", "access R d ; width 4 ; idx tx / 8 ; sync L tx / 8"),
+          ("access R d ; width 4 ; idx 0 ; sync L tx", "access W d ; width 4 ; idx 0"),
+          ("access W d ; width 4 ; idx 3 ; sync L 3", "access R d ; width 4 ; idx tx ; sync L tx")]
+    for a, b in ok:
+        hg.Kernel(base + a + "\n" + b + "\n").bind((2, 1, 1), (32, 1, 1), ())
+    bad = [("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0"),
+           ("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0 ; sync L 0"),
+           ("access W d ; width 4 ; idx tx % 4 ; sync L tx % 2", "access R d ; width 4 ; idx 0"),
+           ("access W d ; width 8 ; idx tx ; sync L tx", "access R d ; width 4 ; idx tx ; sync L tx")]
+    for a, b in bad:
+        assert _err(base + a + "\n" + b + "\n", grid=(2, 1, 1)) == -9
+    assert _err(base + "access W d ; width 4 ; idx 0 ; sync S 0\n") == -2   # shared lock array
+    assert _err(base + "access W d ; width 4 ; idx 0 ; sync M 0\n") == -2   # unknown array
+    assert _err(base + "access W d ; width 4 ; idx 0 ; sync L 0 ; syncscope grid\n") == -2
+
+
+def test_acquire_release_pairs_leave_the_pair_rule():
+    # both guarded at one device-scope lock: the pair is no longer eligible;
+    # block scope keeps it for the inter-block kind only
+    from paper_2604_02106_b300 import ranker
+    base = "kernel k\narray c global 4\narray L global 64\n"
+    for scope, want in (("device", []), ("block", [(0, 1), (1, 1)])):
+        t = (base + f"access R c ; width 4 ; idx 0 ; sync L 0 ; syncscope {scope}\n"
+             f"access W c ; width 4 ; idx 0 ; sync L 0 ; syncscope {scope}\n")
+        k = hg.Kernel(t).bind((2, 1, 1), (64, 1, 1), ())
+        assert ranker.pair_features(k)[1] == want

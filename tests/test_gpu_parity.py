@@ -462,3 +462,41 @@ def test_cell_filter_sorts_only_shared_cells(planted):
         _same(g, o)
         _same(hg.check(w.text, w.binding, cap=1 << 20, flags=flags | hg.NO_CELL_FILTER), o)
         assert hg.stats()["cell_filter"] == 0 and hg.stats()["n_sorted_keys"] == 256 * 256
+
+
+# ---------------------------------------------------------------- acquire-release guards (Sec. 6.5)
+
+@pytest.mark.parametrize("seed", range(40))
+def test_acquire_release_random_against_oracle(seed):
+    # guards of the forms decided at bind time (constant elements, or each
+    # access's own index), block or device scope, global or shared data
+    w = workloads.random_sync(9000 + seed, supported=True)
+    _same(*_both(w.text, w.binding))
+
+
+_RMW = "kernel c\narray c global 4\narray L global 64\narray F global 64\n"
+_R, _W = "access R c ; width 4 ; idx 0", "access W c ; width 4 ; idx 0"
+
+
+@pytest.mark.parametrize("text", [
+    _RMW + f"{_R}\n{_W}\n",
+    _RMW + f"{_R} ; sync L 0\n{_W} ; sync L 0\n",
+    _RMW + f"{_R} ; sync L 0 ; syncscope block\n{_W} ; sync L 0 ; syncscope block\n",
+    _RMW + f"{_R} ; sync L 0 ; syncscope block\n{_W} ; sync L 0\n",
+    _RMW + f"{_R}\n{_W} ; sync L 0\n",
+    _RMW + f"{_R} ; sync L 0\n{_W} ; sync L 1\n",
+    "kernel h\narray h global 64\narray L global 64\n"
+    "access R h ; width 4 ; idx tx % 4 ; sync L tx % 4\naccess W h ; width 4 ; idx tx % 4 ; sync L tx % 4\n",
+    "kernel p\narray d global 4\narray F global 64\naccess W d ; width 4 ; idx 0 ; if tx == 0 ; sync F 0\n"
+    "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 0\n",
+    "kernel p\narray d global 4\narray F global 64\naccess W d ; width 4 ; idx 0 ; if tx == 0 ; sync F 0\n"
+    "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 1\n",
+])
+@pytest.mark.parametrize("jit", [0, hg.JIT])
+def test_acquire_release_fixtures(text, jit):
+    # counter read-modify-write under no lock, one lock (device or block
+    # scope), a lock on one side, two locks; per-element locks; producer /
+    # consumer flags: each result equals the oracle's
+    b = Binding((4, 1, 1), (64, 1, 1), ())
+    g, o = _both(text, b, flags=jit)
+    _same(g, o)

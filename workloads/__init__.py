@@ -13,7 +13,8 @@ fields of ``array`` and ``access`` lines are separated by ``;``)::
     loop VAR BOUND                   0 <= VAR < BOUND, outermost first, at most 4
     array NAME global|shared BYTES [; granule G]
     let NAME = EXPR                  textual macro over everything declared
-    access R|W|A ARRAY ; width W [; iv EXPR] ; idx EXPR [; if COND]* [; scope block|device] [; line N]
+    access R|W|A ARRAY ; width W [; iv EXPR] [; wv EXPR] ; idx EXPR [; if COND]* [; scope block|device]
+           [; sync LOCKARRAY EXPR [; syncscope block|device]] [; line N]
     assert COND                      host-code fact over params and launch dims
 
 Expressions use + - * / % (C semantics: division truncates toward zero),
@@ -22,8 +23,11 @@ unary minus, parentheses, integer literals and the names tx ty tz bx by bz
 variables, params and lets.  COND is ``EXPR op EXPR`` with op one of
 ``< <= > >= ==`` (and ``!=`` in asserts only).  ``idx`` is an element index
 in units of the access width (C pointer arithmetic on a typed pointer), ``iv``
-is the barrier-interval id (affine in loop variables), R/W/A = read, write,
-atomic.
+is the barrier-interval id (affine in loop variables), ``wv`` the warp-barrier
+interval id, R/W/A = read, write, atomic.  ``sync`` names the acquire-release
+guard of the access (a lock held around it, or a producer's release / a
+consumer's acquire): the global array and element of its address;
+``syncscope`` is the narrower scope of the guard's parts (default device).
 
 The workload shapes follow the five benchmark configurations of this project
 (plain 4x64 check, tiled 64x64x(16x16) stencil, 64-tuple host sweep,
@@ -413,8 +417,8 @@ def random_sync(seed: int, max_instances: int = 1500, supported: bool = False) -
     data element (the access's own index), a lock per thread or per block, in
     block or device scope; one data array (global or shared), reads, writes
     and atomics, barrier intervals.  With `supported`, guards are only of the
-    two forms the exhaustive check decides statically: a constant element, or
-    the access's own index on accesses of one width."""
+    forms the exhaustive check decides statically: constant elements, or each
+    access's own index (accesses of one width), one family per kernel."""
     rng = SplitMix64(seed)
     grid = (rng.range(1, 3), 1, 1)
     block = (rng.choice([2, 3, 8, 16, 33, 40]), rng.range(1, 2), 1)
@@ -426,7 +430,8 @@ def random_sync(seed: int, max_instances: int = 1500, supported: bool = False) -
     w.add("param Q")
     w.add(f"array D {space} 256")
     w.add("array L global 64")
-    forms = ["0", "1", "tx", "bx", "own"] if not supported else ["0", "1", "own"]
+    # the decided forms: constants only, or own indexes only, per kernel
+    forms = ["0", "1", "tx", "bx", "own"] if not supported else rng.choice([["0", "1"], ["own"]])
     for a_id in range(nacc):
         r = rng.below(10)
         kind = "R" if r < 4 else ("W" if r < 8 else "A")
