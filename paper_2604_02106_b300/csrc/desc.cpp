@@ -944,6 +944,91 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       if (ub[l] > INT32_MAX) raise(HGRD_EUNSUPPORTED, "loop bound above 2^31");
     P.nit = nit;
 
+    // ---- block-pair pruning: an access of a global array whose index is
+    // affine (no division or remainder) covers, in block b, at most the
+    // bytes [(lo + s(b)) w, (hi + s(b)) w + w), with [lo, hi] the index range
+    // over the threads and loop counters and s(b) its block-id terms.  Two
+    // accesses whose hulls of two different blocks never meet cannot race
+    // across blocks; their inter-block kind leaves the pair rule.  (A sweep
+    // over the blocks' hulls sorted by start; skipped past a work budget.)
+    std::vector<char> affine(d.acc.size(), 0);
+    std::vector<int64_t> hlo(d.acc.size(), 0), hhi(d.acc.size(), 0);
+    for (size_t a = 0; a < d.acc.size(); a++) {
+      const Lin& L = af[a].idx;
+      if (af[a].dead || d.arrays[d.acc[a].arr].space != HGRD_SPACE_GLOBAL || !L.cn.empty()) continue;
+      int64_t lo = L.c0, hi = L.c0;
+      bool empty = false;
+      auto widen = [&](int64_t c, int64_t r) {
+        if (r <= 0) empty = true;
+        const int64_t t = c * (r - 1);
+        (t < 0 ? lo : hi) += t;
+      };
+      for (int k = 0; k < 3; k++) widen(L.cv[k], dims[k]);
+      for (size_t l = 0; l < d.loops.size(); l++) widen(L.cv[6 + l], ub[l]);
+      affine[a] = !empty;
+      hlo[a] = lo;
+      hhi[a] = hi;
+    }
+    auto bshift = [&](size_t a, int64_t b) {
+      const int64_t bx = b % dims[3], by = (b / dims[3]) % dims[4], bz = b / (dims[3] * dims[4]);
+      return af[a].idx.cv[3] * bx + af[a].idx.cv[4] * by + af[a].idx.cv[5] * bz;
+    };
+    std::vector<std::vector<signed char>> disj(d.acc.size(), std::vector<signed char>(d.acc.size(), -1));
+    int64_t sweep_budget = (int64_t)1 << 24;
+    auto blocks_disjoint = [&](int a, int b) -> bool {
+      if (disj[a][b] >= 0) return disj[a][b] != 0;
+      const int sides = a == b ? 1 : 2;
+      if (nblk * sides > sweep_budget) return false;
+      sweep_budget -= nblk * sides;
+      struct Hull {
+        int64_t lo, hi, blk;
+        int side;
+      };
+      std::vector<Hull> v;
+      v.reserve((size_t)(nblk * sides));
+      const int acc2[2] = {a, b};
+      for (int sd = 0; sd < sides; sd++) {
+        const int x = acc2[sd];
+        const int64_t w = d.acc[x].width;
+        for (int64_t blk = 0; blk < nblk; blk++) {
+          const int64_t s0 = bshift((size_t)x, blk);
+          v.push_back({(hlo[x] + s0) * w, (hhi[x] + s0) * w + w - 1, blk, sd});
+        }
+      }
+      std::sort(v.begin(), v.end(), [](const Hull& p, const Hull& q) { return p.lo < q.lo; });
+      // per side: the largest hull ends of two different blocks seen so far
+      int64_t hi1[2] = {INT64_MIN, INT64_MIN}, hi2[2] = {INT64_MIN, INT64_MIN};
+      int64_t bk1[2] = {-1, -1}, bk2[2] = {-1, -1};
+      bool meet = false;
+      for (const Hull& h : v) {
+        const int o = sides == 1 ? 0 : 1 - h.side;
+        if ((bk1[o] != h.blk ? hi1[o] : hi2[o]) >= h.lo) {
+          meet = true;
+          break;
+        }
+        const int sd = h.side;
+        if (h.blk == bk1[sd]) {
+          hi1[sd] = std::max(hi1[sd], h.hi);
+        } else if (h.blk == bk2[sd]) {
+          hi2[sd] = std::max(hi2[sd], h.hi);
+          if (hi2[sd] > hi1[sd]) {
+            std::swap(hi1[sd], hi2[sd]);
+            std::swap(bk1[sd], bk2[sd]);
+          }
+        } else if (h.hi > hi1[sd]) {
+          hi2[sd] = hi1[sd];
+          bk2[sd] = bk1[sd];
+          hi1[sd] = h.hi;
+          bk1[sd] = h.blk;
+        } else if (h.hi > hi2[sd]) {
+          hi2[sd] = h.hi;
+          bk2[sd] = h.blk;
+        }
+      }
+      disj[a][b] = disj[b][a] = meet ? 0 : 1;
+      return !meet;
+    };
+
     // ---- pair rule E (Sec. 6.1 trivially race free; Appendix A scopes)
     // Two instances of one block are ordered unless they share a barrier
     // interval (Sec. 6.1, block barrier; Table 2), so accesses whose interval
@@ -978,6 +1063,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
                   "access's own index (equal widths)");
           if (same) m &= std::min(x.sync_scope, y.sync_scope) == 1 ? 0 : 1;
         }
+        if ((m & 1) && affine[a] && affine[b] && blocks_disjoint(a, b)) m &= ~1;
         if (m & 1) P.einter[a] |= 1u << b;
         if (m & 6) P.eintra[a] |= 1u << b;
       }

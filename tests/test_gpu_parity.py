@@ -500,3 +500,22 @@ def test_acquire_release_fixtures(text, jit):
     b = Binding((4, 1, 1), (64, 1, 1), ())
     g, o = _both(text, b, flags=jit)
     _same(g, o)
+
+
+# ---------------------------------------------------------------- block-pair pruning
+
+@pytest.mark.parametrize("text", [
+    # own slices: the neighbour read races inside a block only
+    "kernel s\narray G global 4096\naccess W G ; width 4 ; idx bx*64 + tx\n"
+    "access R G ; width 4 ; idx bx*64 + (tx + 1) % 64\n",
+    # slices that meet through the loop: an inter-block race at every seam
+    "kernel m\nloop i 2\narray G global 4096\naccess W G ; width 4 ; idx bx*64 + tx + i\n",
+    # own slices in another interval: the read races with nothing
+    "kernel o\narray G global 4096\naccess W G ; width 4 ; idx bx*64 + tx\n"
+    "access R G ; width 4 ; iv 1 ; idx bx*64 + tx\naccess W G ; width 4 ; iv 1 ; idx bx*64 + 63 - tx\n",
+])
+def test_block_pair_pruning_against_oracle(text):
+    b = Binding((8, 1, 1), (64, 1, 1), ())
+    for jit in (0, hg.JIT):
+        g, o = _both(text, b, flags=jit)
+        _same(g, o)

@@ -39,7 +39,9 @@ def test_generated_source_compiles(make):
 
 def test_source_depends_on_structure_only():
     # one sweep's items (N, block size) on one pipeline share their source
-    items = [w for w in workloads.config3() if w.meta["stride"] == 3]
+    # (items of one block excepted: with no second block nothing races across
+    # blocks, which the pair rule, and so the source, records)
+    items = [w for w in workloads.config3() if w.meta["stride"] == 3 and w.binding.grid[0] > 1]
     srcs = {_bind(w).jit_source(flags=hg.NO_SPLIT) for w in items[:4]}
     assert len(srcs) == 1
     a = _bind(workloads.config2(0, planted=True, W=64, H=64, K=4))

@@ -66,3 +66,47 @@ def test_pairs_in_disjoint_barrier_intervals():
     k = hg.Kernel(text).bind((2, 1, 1), (32, 1, 1), ())
     _, ab = ranker.pair_features(k)
     assert ab == [(0, 0), (2, 2), (2, 3), (4, 4), (4, 5)]
+
+
+def test_block_pair_pruning_examples():
+    # per-block hulls of affine global indexes: blocks writing their own
+    # slices cannot race across blocks (inter kind pruned, intra kept); a
+    # shared slice keeps it; a pair pruned of every kind leaves the list
+    def pairs(text, grid=(4, 1, 1), block=(64, 1, 1)):
+        k = hg.Kernel(text).bind(grid, block, ())
+        f, ab = ranker.pair_features(k)
+        return {p: (int(r[64 + 3]), int(r[64 + 4])) for p, r in zip(ab, f)}
+    base = "kernel b\nloop i 2\narray G global 4096\n"
+    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\n") == {(0, 0): (0, 1)}
+    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx + i\n") == {(0, 0): (1, 1)}  # hulls meet
+    assert pairs(base + "access W G ; width 4 ; idx bx*65 + tx + i\n") == {(0, 0): (0, 1)}
+    assert pairs(base + "access W G ; width 4 ; idx tx\n") == {(0, 0): (1, 1)}
+    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\naccess R G ; width 4 ; iv 1 ; idx bx*64 + tx\n") == \
+        {(0, 0): (0, 1)}  # (0, 1): other interval, own slice: races with nothing
+    assert pairs(base + "access W G ; width 16 ; idx bx*16 + tx / 4\n") == {(0, 0): (1, 1)}  # a division: not pruned
+
+
+def test_block_pair_pruning_against_brute_force():
+    # every pair whose inter-block kind was pruned has no two instances of
+    # different blocks on one granule (independent enumeration of tests/brute.py)
+    import brute
+    pruned = 0
+    for seed in range(120):
+        w = workloads.random_tiny(4000 + seed, max_instances=400)
+        k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+        f, ab = ranker.pair_features(k)
+        d = brute.parse(w.text)
+        inst, _ = brute.instances(d, w.binding)
+        for (a, b), r in zip(ab, f):
+            if r[64 + 3] or d["arrays"][d["acc"][a]["array"]]["shared"]:
+                continue
+            ka, kb = d["acc"][a]["kind"], d["acc"][b]["kind"]
+            if ka == "A" and kb == "A":
+                continue  # atomics: pruned by their scopes, not by addresses
+            pruned += 1
+            xa = [x for x in inst if x["acc"] == a]
+            xb = [x for x in inst if x["acc"] == b]
+            for x in xa:
+                for y in xb:
+                    assert x["blk"] == y["blk"] or not (x["gran"] & y["gran"]), (seed, a, b)
+    assert pruned > 20
