@@ -974,7 +974,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       return af[a].idx.cv[3] * bx + af[a].idx.cv[4] * by + af[a].idx.cv[5] * bz;
     };
     std::vector<std::vector<signed char>> disj(d.acc.size(), std::vector<signed char>(d.acc.size(), -1));
-    int64_t sweep_budget = (int64_t)1 << 24;
+    int64_t sweep_budget = (int64_t)1 << 21;  // block hulls swept in all (32 B each on the host)
     auto blocks_disjoint = [&](int a, int b) -> bool {
       if (disj[a][b] >= 0) return disj[a][b] != 0;
       const int sides = a == b ? 1 : 2;
