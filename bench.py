@@ -180,6 +180,23 @@ def _alu_peak():
     return 148 * 4 * 32 * sm_mhz * 1e6 / 1e12
 
 
+def max_over_ranks(value, dist=None):
+    """The largest value over the ranks (the time the whole job waits for);
+    the value itself on one rank.  NCCL reduces a device tensor, gloo a host one."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(world, units_per_rank_step, steps, seconds):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def l2_flusher(s):
     """A function that writes L2_FLUSH_BYTES on stream s (evicts the 126 MB L2)."""
     import torch
@@ -544,12 +561,9 @@ def main():
     res2 = k.collect(ws, cap=1 << 16, stream=s, flags=G)
     assert res2.witnesses == res.witnesses
     torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
-    value = world * n_inst * args.steps / (ms / 1000.0)
+    value = job_throughput(world, n_inst, args.steps, ms / 1000.0)
 
     # ---- per-stage times (CUDA events on the launch stream, same steps again)
     stages = {}
@@ -626,11 +640,8 @@ def main():
         t_e2e.append(time.perf_counter() - t0)
     st = hg.stats()
     e2e_s = sum(t_e2e)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e = {"value": world * n_inst * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, dist)
+    e2e = {"value": job_throughput(world, n_inst, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(st["h2d_bytes"]), "d2h_bytes_per_step": int(st["d2h_bytes"]),
            "ms_per_step": 1000 * e2e_s / args.steps}
     assert r.witnesses == res.witnesses
