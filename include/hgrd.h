@@ -430,6 +430,16 @@ const char* hgrd_last_error(void);
  * Host-side computation of exactly the arithmetic the device performs. */
 int hgrd_debug_divmod(int64_t n, int64_t d, int wide, int64_t* q, int64_t* r);
 
+/* Failure-path self-test of the bounded device waits: one sort pass over
+ * 12288 random keys whose first tile is never taken (its tile ticket starts
+ * past it), so every other tile's look-back waits on a status nothing will
+ * publish.  Each wait gives up after its iteration limit (a few seconds at
+ * most), the kernel records the timeout and returns, and this call returns
+ * HGRD_ETIMEOUT with the context still usable; HGRD_OK would mean the wait
+ * did not run out.  Workspace: at least 256 KB, 256-byte aligned.  Has no
+ * counterpart in the paper: it exercises this library's own error path. */
+int hgrd_debug_lookback_timeout(void* d_ws, size_t ws_bytes, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ CELL_FILTER = 512     # pre-filter keys by cell whenever the table fits (default
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
            "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile", "hgrd_free_desc", "hgrd_last_error",
-           "hgrd_debug_divmod", "hgrd_check_noalloc", "hgrd_batch_create", "hgrd_batch_workspace_size",
+           "hgrd_debug_divmod", "hgrd_debug_lookback_timeout", "hgrd_check_noalloc", "hgrd_batch_create",
+           "hgrd_batch_workspace_size",
            "hgrd_batch_run", "hgrd_batch_collect", "hgrd_batch_tune", "hgrd_batch_free", "hgrd_pair_features",
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
@@ -478,3 +479,17 @@ def debug_divmod(n: int, d: int, wide: bool):
     q, r = C.c_int64(), C.c_int64()
     _raise(lib().hgrd_debug_divmod(n, d, int(wide), C.byref(q), C.byref(r)))
     return q.value, r.value
+
+
+def debug_lookback_timeout(stream=None) -> int:
+    """hgrd_debug_lookback_timeout: a sort pass whose look-back waits on a tile
+    nobody processes; returns the library's status code (HGRD_ETIMEOUT, -8,
+    when the bounded wait ran out as it should)."""
+    import torch
+    L = lib()
+    L.hgrd_debug_lookback_timeout.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p]
+    L.hgrd_debug_lookback_timeout.restype = C.c_int
+    ws = torch.empty(256 << 10, dtype=torch.uint8, device="cuda")
+    rc = L.hgrd_debug_lookback_timeout(C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    torch.cuda.synchronize()
+    return rc

@@ -1465,6 +1465,41 @@ extern "C" int hgrd_sort_variant(int set, int* current, int* count) {
   return HGRD_OK;
 }
 
+extern "C" int hgrd_debug_lookback_timeout(void* d_ws, size_t ws_bytes, void* stream) {
+  using namespace hgrd;
+  constexpr uint64_t n = 12288;
+  const uint64_t tiles = (n + RS_MIN_TILE - 1) / RS_MIN_TILE;
+  const size_t need = (2 * n + tiles * RS_RADIX + 256 + 16) * 8;
+  if (!d_ws) return fail(HGRD_EINVAL, "null workspace");
+  if (ws_bytes < need) return fail(HGRD_ENOMEM, "workspace too small: need " + std::to_string(need));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t* kin = (uint64_t*)d_ws;
+  uint64_t* kout = kin + n;
+  uint64_t* status = kout + n;
+  uint64_t* gb = status + tiles * RS_RADIX;
+  uint64_t* cnt = gb + 256;  // n, ticket, err
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint64_t launches = 0;
+  Launch L{s, 1, &launches};
+  cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
+  // keys, zero digit offsets (every position stays below n), no status yet,
+  // and the ticket of the first tile already handed out
+  random_keys_kernel<<<L.nsm, 256, 0, s>>>(kin, n, 0x7153);
+  const uint64_t host[3] = {n, 1, 0};
+  if (cudaMemsetAsync(gb, 0, 256 * 8, s) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, tiles * RS_RADIX * 8, s) != cudaSuccess ||
+      cudaMemcpyAsync(cnt, host, sizeof(host), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(HGRD_EDEVICE, "set-up copies failed");
+  cudaError_t e = launch_onesweep(L, kin, kout, cnt, n, 0, gb, status, cnt + 1, 1, cnt + 2);
+  uint64_t errw = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&errw, cnt + 2, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e));
+  if (errw & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
+  return HGRD_OK;
+}
+
 extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* best, float* ms, int cap) {
   using namespace hgrd;
   if (!d_ws) return fail(HGRD_EINVAL, "null workspace");
