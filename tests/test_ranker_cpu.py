@@ -110,3 +110,13 @@ def test_block_pair_pruning_against_brute_force():
                 for y in xb:
                     assert x["blk"] == y["blk"] or not (x["gran"] & y["gran"]), (seed, a, b)
     assert pruned > 20
+
+
+def test_block_pair_pruning_work_budget():
+    # past the sweep budget (2^21 block hulls) the pair keeps its inter-block
+    # kind: pruning is an optimisation, never required for exactness
+    text = "kernel g\narray G global 4*64*4194304\naccess W G ; width 4 ; idx bx*64 + tx\n"
+    for gx, inter in ((1 << 20, 0), ((1 << 21) + 1, 1)):
+        k = hg.Kernel(text).bind((gx, 1, 1), (64, 1, 1), ())
+        f, ab = ranker.pair_features(k)
+        assert ab == [(0, 0)] and int(f[0][64 + 3]) == inter and int(f[0][64 + 4]) == 1
