@@ -342,8 +342,12 @@ def test_oracle_matches_brute_force_acquire_release(seed):
 
 
 def _kinds(text, grid=(2, 1, 1), block=(64, 1, 1)):
-    r = oracle.check(text, Binding(grid, block, ()))
-    return {(w[3], w[4]): w[5] for w in r.witnesses}
+    """{(acc_lo, acc_hi): OR of the kind masks of that pair's witnesses}"""
+    r = oracle.check(text, Binding(grid, block, ()), cap=1 << 20)
+    out = {}
+    for w in r.witnesses:
+        out[(w[3], w[4])] = out.get((w[3], w[4]), 0) | w[5]
+    return out
 
 
 def test_acquire_release_closed_forms():
@@ -395,3 +399,21 @@ def test_invariant_guards_never_add_races(seed):
     for x in g.witnesses:
         assert x[:5] in full and (x[5] & ~full[x[:5]]) == 0
     assert g.n_keys == u.n_keys and g.n_oob == u.n_oob
+
+
+def test_acquire_release_with_barriers_and_widths():
+    # barrier intervals still order one block; guards decide the rest
+    rmw = "kernel c\narray c global 4\narray L global 64\n"
+    t = (rmw + "access R c ; width 4 ; iv 0 ; idx 0 ; sync L 0 ; syncscope {s}\n"
+         "access W c ; width 4 ; iv 1 ; idx 0 ; sync L 0 ; syncscope {s}\n")
+    assert _kinds(t.format(s="block")) == {(0, 1): 1, (1, 1): 1}
+    assert _kinds(t.format(s="device")) == {}
+    # a float4 write guarded at its element, int reads of its words guarded at
+    # the word's element (another address) or at the float4's (the same one);
+    # thread t reads the word written by thread t / 4: the same warp for
+    # t < 32, the other warp beyond
+    v = ("kernel v\narray d global 1024\narray L global 1024\n"
+         "access W d ; width 16 ; idx tx ; sync L tx\n"
+         "access R d ; width 4 ; idx tx ; sync L {r}\n")
+    assert _kinds(v.format(r="tx"), grid=(1, 1, 1), block=(64, 1, 1)) == {(0, 1): 6}
+    assert _kinds(v.format(r="tx / 4"), grid=(1, 1, 1), block=(64, 1, 1)) == {}
