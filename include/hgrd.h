@@ -135,7 +135,12 @@ typedef struct {
                                workspace, these options and this device, and replayed by the
                                later ones (same result; the program is re-uploaded by every
                                replay from a pinned copy taken at capture; ignored with
-                               HGRD_PROFILE; a rebind makes a new binding) */
+                               HGRD_PROFILE; a rebind makes a new binding);
+                               HGRD_ALL_KEYS: write and sort the keys of every live access,
+                               also of those the pair rule shows can race with nothing, in one
+                               global sort on the interpreted kernels (implies HGRD_NO_SPLIT,
+                               HGRD_NO_JIT, HGRD_NO_SMALL); same result: a measurement mode that
+                               puts every key of the check through the sort and the scan */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
@@ -154,7 +159,8 @@ enum {
   HGRD_NO_SMALL = 64,
   HGRD_GRAPH = 128,
   HGRD_NO_CELL_FILTER = 256,
-  HGRD_CELL_FILTER = 512
+  HGRD_CELL_FILTER = 512,
+  HGRD_ALL_KEYS = 1024
 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's
@@ -186,6 +192,9 @@ typedef struct {
   uint32_t cell_filter;     /* 1 when only keys of cells with a writer and two threads were sorted */
   uint64_t n_written_keys;  /* global-array keys the expansion wrote (the first sort pass reads
                                them all; with the cell filter it keeps n_sorted_keys of them) */
+  uint64_t cuda_objects_created; /* process-wide, not per call: CUDA objects and buffers this
+                               library has created since it was loaded (streams, events,
+                               instantiated graphs, pinned host buffers, loaded modules) */
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,
@@ -367,15 +376,20 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
  *     loads the library holds it until the process exits.
  *   * Bindings whose hgrd_workspace_size exceeds 64 MiB are rejected with
  *     HGRD_ENOMEM before any work is enqueued.
- *   * The call allocates nothing: no cudaMalloc/cudaFree, no CUDA events, no
- *     host staging buffer (witnesses are widened in place inside host_out).
+ *   * The call allocates nothing: no cudaMalloc/cudaFree, no streams, events
+ *     or graphs (the witness merge is launched directly, never through a
+ *     cached graph), no pinned host staging (witnesses are widened in place
+ *     inside host_out); hgrd_stats.cuda_objects_created does not move.
  *   * The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *     cudaGetSymbolAddress (once per device, with that device current).
+ *   * Never on a capturing stream: the call reads its results back and
+ *     synchronises the stream, so a capturing stream gets HGRD_EINVAL.
  *   * All calls share the one array, which keeps the previous call's data;
  *     each call clears what must start at zero.  Calls whose GPU work
  *     overlaps (other host threads, other streams) race on the array.
- *   * Outputs as hgrd_check, except that the canonical instance pair is not
- *     searched (pair_found = 0).  Synchronous on return. */
+ *   * Outputs as hgrd_check (witnesses, counts, racy-pair matrices), except
+ *     that the canonical instance pair is not searched (pair_found = 0).
+ *     Synchronous on return. */
 int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, void* cuda_stream, hgrd_witness* host_out,
                        uint64_t cap, hgrd_verdict* v);
 
@@ -419,6 +433,11 @@ typedef struct {
   uint32_t has_lo, has_hi;
 } hgrd_param_info;
 int hgrd_desc_params(const hgrd_desc* d, hgrd_param_info* out, uint32_t cap, uint32_t* n);
+/* Size of a bound check, known at bind time without a device: the
+ * (block, thread, loop vector, access) instances it enumerates (Sec. 6.2's
+ * instance space under the host binding, before guards) and the most keys
+ * its live instances can make.  Cost model for splitting batches. */
+int hgrd_bound_info(const hgrd_desc* d, uint64_t* n_instances, uint64_t* max_keys);
 int hgrd_bound_hash(const hgrd_desc* d, uint64_t* h);
 
 void hgrd_free_desc(hgrd_desc* d);

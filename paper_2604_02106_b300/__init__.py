@@ -27,6 +27,7 @@ NO_SMALL = 64
 GRAPH = 128      # run the check as one CUDA graph launch (captured once per binding, workspace, options)
 NO_CELL_FILTER = 256  # sort every kept key (no per-cell pre-filter)
 CELL_FILTER = 512     # pre-filter keys by cell whenever the table fits (default: only for many keys)
+ALL_KEYS = 1024       # write and sort the keys of every live access (one global sort, interpreted kernels)
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",
@@ -37,7 +38,7 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
            "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source",
-           "hgrd_desc_params", "hgrd_bound_hash"]
+           "hgrd_desc_params", "hgrd_bound_hash", "hgrd_bound_info"]
 BATCH_GRAPH = 1
 BATCH_JIT = 2
 
@@ -107,7 +108,8 @@ class Stats(C.Structure):
                 ("sort_passes", C.c_uint32), ("int64_path", C.c_uint32), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_sorted_keys", C.c_uint64), ("n_binned_keys", C.c_uint64),
                 ("shared_bins", C.c_uint32), ("jit", C.c_uint32), ("eval_ops", C.c_uint64),
-                ("small", C.c_uint32), ("cell_filter", C.c_uint32), ("n_written_keys", C.c_uint64)]
+                ("small", C.c_uint32), ("cell_filter", C.c_uint32), ("n_written_keys", C.c_uint64),
+                ("cuda_objects_created", C.c_uint64)]
 
 
 _lib = None
@@ -148,10 +150,11 @@ def lib():
         L.hgrd_debug_divmod.argtypes = [C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.hgrd_jit_compile.argtypes = [vp, C.POINTER(CheckOpts), C.POINTER(C.c_double)]
         L.hgrd_jit_source.argtypes = [vp, C.POINTER(CheckOpts), C.c_char_p, sz, C.POINTER(sz)]
+        L.hgrd_bound_info.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
         for f in ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check",
                   "hgrd_check_enqueue", "hgrd_check_collect", "hgrd_last_stats", "hgrd_last_profile",
                   "hgrd_debug_divmod", "hgrd_jit_compile", "hgrd_jit_source",
-           "hgrd_desc_params", "hgrd_bound_hash"]:
+                  "hgrd_desc_params", "hgrd_bound_hash", "hgrd_bound_info"]:
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -249,6 +252,12 @@ class Kernel:
         _raise(lib().hgrd_bind_host_params(self._h, C.byref(b)))
         self.__dict__.pop("_ws_sizes", None)  # sizes follow the binding
         return self
+
+    def info(self) -> tuple:
+        """(instances, most keys) of the current binding (no device needed)."""
+        n, k = C.c_uint64(), C.c_uint64()
+        _raise(lib().hgrd_bound_info(self._h, C.byref(n), C.byref(k)))
+        return n.value, k.value
 
     def workspace_size(self, **opts) -> int:
         key = tuple(sorted(opts.items()))

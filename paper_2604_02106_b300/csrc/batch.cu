@@ -542,6 +542,7 @@ int hgrd_batch_create(const hgrd_desc* const* items, uint32_t n, const hgrd_batc
     if (!items[i] || !items[i]->bound) return fail(HGRD_EINVAL, "batch item " + std::to_string(i) + " is not bound");
     b->items.push_back(items[i]);
   }
+  note_created(2);
   if (cudaMallocHost((void**)&b->h_progs, n * sizeof(DProg)) != cudaSuccess ||
       cudaMallocHost((void**)&b->h_order, n * sizeof(uint32_t)) != cudaSuccess)
     return fail(HGRD_EDEVICE, "pinned host allocation failed");
@@ -556,6 +557,7 @@ int hgrd_batch_create(const hgrd_desc* const* items, uint32_t n, const hgrd_batc
     }
   b->streams.resize(MAX_STREAMS);
   b->join.resize(MAX_STREAMS);
+  note_created(2 * MAX_STREAMS + 1);
   for (uint32_t j = 0; j < MAX_STREAMS; j++) {
     if (cudaStreamCreateWithFlags(&b->streams[j], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) != cudaSuccess)
@@ -604,6 +606,7 @@ int hgrd_batch_run(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream) {
   if (!b->exec || b->exec_ws != d_ws || b->exec_stream != s) {
     drop_graph(b);
     cudaStream_t cap = nullptr;
+    note_created(2);  // the capture stream and the instantiated graph
     BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     BK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_batch(b, (char*)d_ws, cap);
@@ -686,6 +689,7 @@ int hgrd_batch_tune(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream, hg
   const uint32_t limits[] = {0, 1024, (uint32_t)SB_KEYS};
   const uint32_t nstreams[] = {2, 4, 8, 16};
   cudaEvent_t e0, e1;
+  note_created(2);
   BK(cudaEventCreate(&e0));
   BK(cudaEventCreate(&e1));
   float best = 1e30f;

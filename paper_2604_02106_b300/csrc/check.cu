@@ -30,6 +30,16 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// HGRD_ALL_KEYS runs one global sort on the interpreted kernels: the flags
+// it implies are set here, once, at every entry point that takes options
+const hgrd_check_opts* norm_opts(const hgrd_check_opts* o, hgrd_check_opts* tmp) {
+  if (!o || !(o->flags & HGRD_ALL_KEYS)) return o;
+  *tmp = *o;
+  tmp->flags |= HGRD_NO_SPLIT | HGRD_NO_JIT | HGRD_NO_SMALL;
+  tmp->flags &= ~(uint32_t)HGRD_JIT;
+  return tmp;
+}
+
 struct Layout {
   size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
       pairs, stbl, sbase, cells, total;
@@ -38,6 +48,7 @@ struct Layout {
   uint64_t scap;       // room for keys of candidate shared bins (block-local mode)
   uint64_t key_words;  // length of each key buffer
   uint64_t cand_cap;   // candidate entries (two words each) the spare key buffer holds
+  uint64_t nsort;      // most keys the global sort can see
 };
 
 Layout layout(const Bound& B, const hgrd_check_opts* o) {
@@ -47,9 +58,11 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   // the key buffers hold what can be written: kept keys of every access (one
   // sort of everything), or kept global keys plus room for candidate shared
   // bins (block-local mode)
-  const bool split = P.smode && !(o && (o->flags & HGRD_NO_SPLIT));
+  const bool all = o && (o->flags & HGRD_ALL_KEYS);
+  const bool split = P.smode && !(o && (o->flags & HGRD_NO_SPLIT)) && !all;
   L.scap = split ? ((o && o->max_shared_keys) ? o->max_shared_keys : P.scap) : 0;
-  L.key_words = std::max<uint64_t>(split ? B.nsort_max_split + L.scap : B.nsort_max_all, 1);
+  const uint64_t nsort_all = all ? B.nkeys_max : B.nsort_max_all;  // every live key, or the kept ones
+  L.key_words = std::max<uint64_t>(split ? B.nsort_max_split + L.scap : nsort_all, 1);
   // a candidate run holds at least two keys
   L.cand_cap = std::max<uint64_t>(L.key_words / 2, 1);
   // defaults scale with the problem and come back as HGRD_ENOMEM (with the
@@ -65,7 +78,8 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   const uint64_t scan_n = std::max(nunits, L.raw_cap);
   // look-back status of the sort passes: tiles of the larger of the key sort
   // and the witness sort
-  const uint64_t ns = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
+  const uint64_t ns = std::max<uint64_t>(split ? B.nsort_max_split : nsort_all, 1);
+  L.nsort = ns;
   const uint64_t tiles = std::max((ns + RS_MIN_TILE - 1) / RS_MIN_TILE, (L.raw_cap + RS_MIN_TILE - 1) / RS_MIN_TILE);
   L.status_words = tiles * RS_RADIX;
   size_t off = 0;
@@ -130,6 +144,7 @@ struct Prof {
   void mark(const char* name) {
     if (!on) return;
     cudaEvent_t e;
+    note_created();
     if (cudaEventCreate(&e) != cudaSuccess) return;
     cudaEventRecord(e, s);
     ev.push_back(e);
@@ -210,6 +225,7 @@ cudaGraphExec_t witness_graph(const Launch& L, const Layout& W, char* ws, int P)
   auto it = g_wg.find(key);
   if (it != g_wg.end()) return it->second;
   if (g_wg_off || g_wg.size() >= 256) return nullptr;
+  note_created(2);  // a capture stream and the instantiated graph
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
@@ -354,8 +370,11 @@ cudaError_t capture_witness_cond(const Launch& L, const Layout& W, char* ws, int
   return eb != cudaSuccess ? eb : e;
 }
 
+// `noalloc`: create no CUDA object on the way (no profiling events, no
+// cached witness-merge graph); hgrd_check_noalloc's promise rests on it
 int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, cudaStream_t s,
-            const DProg* dprog_resident = nullptr, const Capture* cc = nullptr, bool pair = false) {
+            const DProg* dprog_resident = nullptr, const Capture* cc = nullptr, bool pair = false,
+            bool noalloc = false) {
   Layout W;
   int rc = prechecks(d, d_ws, ws_bytes, o, &W);
   if (rc) return rc;
@@ -397,9 +416,10 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   const uint32_t only_mask = (jit && restricted) ? only : 0xffffffffu;
   Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
-  g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
+  if (noalloc) g_prof.on = false;  // the events of an earlier profiled check stay readable, none are made
+  else g_prof.reset(o && (o->flags & HGRD_PROFILE), s);
 
-  const uint64_t nsort = std::max<uint64_t>(split ? B.nsort_max_split : B.nsort_max_all, 1);
+  const uint64_t nsort = W.nsort;
   CK(cudaMemsetAsync(cnt, 0, W.hist + MAX_PASSES * 256 * 8 - W.counters, s));  // counters and histograms
   bool any = false;
   for (int a = 0; a < HP.nacc; a++) any |= !HP.acc[a].dead;
@@ -408,9 +428,13 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // the accesses (the others marked dead) or has its own room for shared keys
   const DProg* hprog = &HP;
   if (!dprog_resident) {
-    if (restricted || (split && W.scap != HP.scap)) {
+    const bool all_keys = o && (o->flags & HGRD_ALL_KEYS);
+    if (restricted || (split && W.scap != HP.scap) || all_keys) {
       static thread_local DProg run_prog;
       run_prog = HP;
+      if (all_keys)  // every live access writes its keys
+        for (int a = 0; a < run_prog.nacc; a++)
+          if (!run_prog.acc[a].dead) run_prog.emask |= 1u << a;
       if (restricted)
         for (int a = 0; a < run_prog.nacc; a++)
           if (!((only >> a) & 1u)) run_prog.acc[a].dead = 1;
@@ -534,7 +558,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   uint64_t* wout = U(uniq_off(W));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(s, &cap));
-  cudaGraphExec_t wg = (cap == cudaStreamCaptureStatusNone && !dprog_resident) ? witness_graph(L, W, ws, P) : nullptr;
+  cudaGraphExec_t wg =
+      (cap == cudaStreamCaptureStatusNone && !dprog_resident && !noalloc) ? witness_graph(L, W, ws, P) : nullptr;
   if (wg) {
     CK(cudaGraphLaunch(wg, s));
     (*L.launches)++;
@@ -602,6 +627,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   CheckGraph e;
   cudaStream_t cs = nullptr, bs = nullptr;
   cudaGraph_t g = nullptr;
+  note_created(4);  // pinned program copy, two capture streams, the instantiated graph
   bool ok = cudaHostAlloc((void**)&e.pinned, sizeof(DProg), cudaHostAllocDefault) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
@@ -670,6 +696,7 @@ struct Pinned {
     if (need <= n) return p;
     size_t m = std::max<size_t>(need, 1 << 20);
     void* q = nullptr;
+    note_created();
     if (cudaHostAlloc(&q, m, cudaHostAllocDefault) != cudaSuccess) return nullptr;
     if (p) cudaFreeHost(p);
     p = (char*)q;
@@ -887,6 +914,8 @@ using namespace hgrd;
 extern "C" {
 
 int hgrd_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes) {
+  hgrd_check_opts tmp;
+  o = norm_opts(o, &tmp);
   if (!d || !bytes) return fail(HGRD_EINVAL, "null argument");
   if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound");
   *bytes = layout(*d->bound, o).total;
@@ -911,16 +940,22 @@ int hgrd_last_profile(hgrd_stage_time* out, uint32_t cap, uint32_t* n) {
 }
 
 int hgrd_check_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream) {
+  hgrd_check_opts tmp;
+  o = norm_opts(o, &tmp);
   return enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
                        hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
+  hgrd_check_opts tmp;
+  o = norm_opts(o, &tmp);
   return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, false);
 }
 
 int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* stream,
                hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v) {
+  hgrd_check_opts tmp;
+  o = norm_opts(o, &tmp);
   int rc = enqueue_api(d, o, d_ws, ws_bytes, (cudaStream_t)stream, true);
   if (rc) return rc;
   return collect(d, o, d_ws, ws_bytes, (cudaStream_t)stream, host_out, cap, v, true, true);
@@ -976,8 +1011,17 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   if (!d || !v) return fail(HGRD_EINVAL, "null argument");
   if (cap && !host_out) return fail(HGRD_EINVAL, "null witness buffer with nonzero capacity");
   if (!d->bound) return fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  {
+    // the readbacks below synchronise the stream, which a capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(HGRD_EINVAL, "hgrd_check_noalloc cannot run on a capturing stream (it reads results back)");
+  }
   hgrd_check_opts oo{};
   if (o) oo = *o;
+  if (oo.flags & HGRD_ALL_KEYS) oo.flags |= HGRD_NO_SPLIT;
   oo.flags &= ~(uint32_t)HGRD_PROFILE;  // stage timing would create CUDA events
   oo.flags &= ~(uint32_t)HGRD_JIT;      // loading a compiled module takes device memory
   oo.flags |= HGRD_NO_JIT | HGRD_NO_SMALL | HGRD_NO_CELL_FILTER;  // smallest workspace
@@ -991,7 +1035,7 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   int rc = noalloc_base(&base);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  rc = enqueue(d, &oo, base, NOALLOC_BYTES, s);
+  rc = enqueue(d, &oo, base, NOALLOC_BYTES, s, nullptr, nullptr, false, true);
   if (rc) return rc;
   char* ws = (char*)base;
   uint64_t cnt[C_WORDS];
@@ -1015,6 +1059,8 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   v->n_by_kind[1] = cnt[C_KIND1];
   v->n_by_kind[2] = cnt[C_KIND2];
   v->racy = v->n_witness > 0;
+  for (int k = 0; k < 3; k++)
+    for (int a = 0; a < 32; a++) v->pair_kind[k][a] = (uint32_t)(cnt[C_PAIRS + k * 16 + a / 2] >> (32 * (a & 1)));
   auto unpack = [&](uint64_t w) {
     hgrd_witness x{};
     x.space = (uint8_t)((w >> 58) & 1);

@@ -28,6 +28,7 @@ namespace hgrd {
 
 thread_local std::string g_err;
 thread_local hgrd_stats g_stats;
+std::atomic<uint64_t> g_created{0};
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -1407,6 +1408,14 @@ int hgrd_desc_params(const hgrd_desc* d, hgrd_param_info* out, uint32_t cap, uin
   return HGRD_OK;
 }
 
+int hgrd_bound_info(const hgrd_desc* d, uint64_t* n_instances, uint64_t* max_keys) {
+  if (!d || !n_instances || !max_keys) return hgrd::fail(HGRD_EINVAL, "null argument");
+  if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
+  *n_instances = d->bound->n_instances;
+  *max_keys = d->bound->nkeys_max;
+  return HGRD_OK;
+}
+
 int hgrd_bound_hash(const hgrd_desc* d, uint64_t* h) {
   if (!d || !h) return hgrd::fail(HGRD_EINVAL, "null argument");
   if (!d->bound) return hgrd::fail(HGRD_EINVAL, "descriptor is not bound (call hgrd_bind_host_params)");
@@ -1430,6 +1439,7 @@ const char* hgrd_last_error(void) { return hgrd::g_err.c_str(); }
 int hgrd_last_stats(hgrd_stats* s) {
   if (!s) return hgrd::fail(HGRD_EINVAL, "null argument");
   *s = hgrd::g_stats;
+  s->cuda_objects_created = hgrd::g_created.load(std::memory_order_relaxed);
   return HGRD_OK;
 }
 

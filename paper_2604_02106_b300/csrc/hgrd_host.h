@@ -1,5 +1,6 @@
 // Host-side library state: parsed descriptors and their bindings.
 #pragma once
+#include <atomic>
 #include <map>
 #include <memory>
 #include <string>
@@ -72,6 +73,11 @@ struct Bound {
 };
 extern thread_local std::string g_err;
 extern thread_local hgrd_stats g_stats;
+// CUDA objects and buffers the library has created since it was loaded
+// (streams, events, instantiated graphs, pinned host buffers, loaded
+// modules); reported in hgrd_stats.cuda_objects_created
+extern std::atomic<uint64_t> g_created;
+inline void note_created(uint64_t n = 1) { g_created.fetch_add(n, std::memory_order_relaxed); }
 int fail(int code, const std::string& msg);
 }  // namespace hgrd
 

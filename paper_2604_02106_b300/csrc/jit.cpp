@@ -437,6 +437,7 @@ JitModule* compile(const std::string& src, double* ms) {
       nvrtcGetCUBINSize(prog, &n);
       std::vector<char> cubin(n);
       nvrtcGetCUBIN(prog, cubin.data());
+      note_created();
       cudaError_t e = cudaLibraryLoadData(&mod->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
       if (e != cudaSuccess) {
         mod->log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);

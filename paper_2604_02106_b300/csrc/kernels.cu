@@ -1530,6 +1530,7 @@ extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* be
   launch_histogram(L, kin, cnt, n, 0, 1, hist);
   launch_hist_scan(L, hist, gb, 1);
   cudaEvent_t e0, e1;
+  note_created(2);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int saved = g_sort_variant[dev];

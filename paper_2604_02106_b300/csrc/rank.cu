@@ -63,6 +63,7 @@ int hgrd_check_ranked(const hgrd_desc* d, const hgrd_check_opts* o, const void* 
   static thread_local float* feat = nullptr;
   static thread_local float* zs = nullptr;
   if (!feat) {
+    note_created(2);
     if (cudaMallocHost((void**)&feat, (size_t)MAXPAIRS * HGRD_MLP_IN * 4) != cudaSuccess ||
         cudaMallocHost((void**)&zs, (size_t)MAXPAIRS * 4) != cudaSuccess) {
       if (feat) cudaFreeHost(feat);
