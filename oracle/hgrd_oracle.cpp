@@ -605,10 +605,16 @@ typedef struct {
 // buckets of that array whose granule lies in [gran_lo, gran_hi) (a sample of
 // the full answer, used on workloads too large to bucket whole); counts of
 // instances, keys and out-of-bounds instances are always whole-kernel.
+// filter_array == -2 keeps the buckets of every array whose granule g has
+// g % gran_hi == gran_lo (band gran_lo of gran_hi): the bands partition the
+// buckets, and with them the witnesses, so separate runs can share the work.
+// flags bit 0 skips the search for the canonical instance pair (min_x and
+// min_y stay zero); everything else is computed as without it.
 int orc_check(const char* text, const orc_binding* bind, int filter_array, uint64_t gran_lo, uint64_t gran_hi,
-              orc_witness* out, uint64_t cap, orc_verdict* v, char* err, size_t errlen) {
+              orc_witness* out, uint64_t cap, orc_verdict* v, char* err, size_t errlen, int flags) {
   try {
     if (!text || !bind || !v) throw Fail{EINVAL_, "null argument"};
+    if (filter_array == -2 && (gran_hi == 0 || gran_lo >= gran_hi)) throw Fail{EINVAL_, "bad band"};
     memset(v, 0, sizeof(*v));
     Desc d = parse(std::string(text));
     if (bind->nparams != d.params.size()) throw Fail{EBIND, "parameter count does not match the descriptor"};
@@ -697,6 +703,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
                             if (filter_array >= 0 &&
                                 (A.array != filter_array || gr < (int64_t)gran_lo || gr >= (int64_t)gran_hi))
                               continue;
+                            if (filter_array == -2 && (uint64_t)gr % gran_hi != gran_lo) continue;
                             const int sp = d.arrays[A.array].space;
                             buckets[Key{sp, A.array, sp == 1 ? in.blk : -1, gr}].push_back(in);
                           }
@@ -745,7 +752,7 @@ int orc_check(const char* text, const orc_binding* bind, int filter_array, uint6
     // canonical instance pair of the minimal witness: the smallest
     // (key(x), key(y)) with x of access acc_lo, y of access acc_hi, both on the
     // witness's granule (any block for shared memory), racing
-    if (v->racy) {
+    if (v->racy && !(flags & 1)) {
       const orc_witness& mw = v->min_w;
       const int64_t g = d.arrays[mw.array].granule;
       const int allow = allowed_kinds(d, mw.acc_lo, mw.acc_hi);

@@ -49,6 +49,18 @@ def test_oracle_matches_brute_force_tiny(seed):
 
 def test_oracle_matches_brute_force_config1():
     _cmp_brute(workloads.config1(0))
+    _cmp_brute(workloads.plain_random(0))
+
+
+def test_config1_holds_exactly_the_planted_race():
+    # the five drawn accesses are race free by construction (read-only G,
+    # thread-owned S slots in intervals with an S write); the planted write
+    # of thread 0 in every block is the one race, inter-block write-write
+    for item in range(24):
+        w = workloads.config1(item)
+        o = oracle.check(w.text, w.binding)
+        assert o.n_witness == 1 and o.n_by_kind == (1, 0, 0), item
+        assert (o.witnesses[0][3], o.witnesses[0][4], o.witnesses[0][5]) == (5, 5, 1)
 
 
 def _gold(name):
@@ -56,7 +68,7 @@ def _gold(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name", sorted(os.listdir(GOLD)))
+@pytest.mark.parametrize("name", sorted(n for n in os.listdir(GOLD) if n.startswith("fig")))
 def test_paper_worked_examples(name):
     g = _gold(name)
     for case in g["cases"]:
@@ -417,3 +429,36 @@ def test_acquire_release_with_barriers_and_widths():
          "access R d ; width 4 ; idx tx ; sync L {r}\n")
     assert _kinds(v.format(r="tx"), grid=(1, 1, 1), block=(64, 1, 1)) == {(0, 1): 6}
     assert _kinds(v.format(r="tx / 4"), grid=(1, 1, 1), block=(64, 1, 1)) == {}
+
+
+def test_vectorised_stride_closed_form_matches_hand_form_and_oracle():
+    # the array form of the strided sweep's closed form (used at N up to 2^20
+    # on the GPU) against the per-element hand form and the oracle
+    import closed_forms as cf
+    for N, S, bd in [(96, 1, 64), (100, 3, 64), (64, 4, 32), (70, 8, 64), (40, 32, 64), (1000, 1, 64),
+                     (513, 3, 256), (777, 2, 96)]:
+        b, lo, hi, k = cf.stride_witnesses(N, S, bd)
+        got = [(0, 0, int(x), int(y), int(z), int(m)) for x, y, z, m in zip(b, lo, hi, k)]
+        assert got == sorted(_stride_closed_form(N, S, bd)), (N, S, bd)
+    for w in workloads.config3()[:15]:
+        N, S = w.binding.params
+        bd, g = w.binding.block[0], w.binding.grid[0]
+        o = oracle.check(w.text, w.binding, pair=False)
+        b, lo, hi, k = cf.stride_witnesses(N, S, bd)
+        assert o.witnesses == [(0, 0, int(x), int(y), int(z), int(m)) for x, y, z, m in zip(b, lo, hi, k)]
+        assert o.n_keys == cf.stride_keys(N, g, bd) and o.n_oob == 0
+
+
+def test_parallel_oracle_equals_the_oracle():
+    # the bands partition the buckets (granule % jobs), so the merged result
+    # of the banded runs is the whole-kernel result
+    import multiprocessing as mp
+    cases = [workloads.plain_random(1), workloads.config1(2), workloads.random_tiny(77, max_instances=4000),
+             workloads.config2(0, planted=True, W=64, H=64, K=4), workloads.random_shared(5, max_instances=8000)]
+    with mp.get_context("spawn").Pool(3) as pool:
+        for w in cases:
+            want = oracle.check(w.text, w.binding)
+            got = oracle.check_parallel(w.text, w.binding, jobs=3, pool=pool)
+            assert (got.witnesses, got.n_witness, got.n_by_kind, got.n_keys, got.n_oob, got.n_instances) == \
+                   (want.witnesses, want.n_witness, want.n_by_kind, want.n_keys, want.n_oob, want.n_instances)
+            assert (got.min_w, got.min_x, got.min_y) == (want.min_w, want.min_x, want.min_y)

@@ -28,6 +28,67 @@ def test_reference_gradients_match_finite_differences():
         assert abs(fd - g[i]) <= 1e-6 + 1e-4 * abs(fd), (i, fd, g[i])
 
 
+def hand_network():
+    """A network whose every weight and activation is a small binary fraction
+    (exact in bf16), with values worked out by hand below.  Rows are output
+    units, columns input units (W[out][in]); W2 is not symmetric, so a
+    transposed W2 changes the logits."""
+    q = {name: np.zeros(n) for name, n in mlp_ref.SIZES}
+    W1 = q["W1"].reshape(mlp_ref.HID, mlp_ref.IN)
+    W2 = q["W2"].reshape(mlp_ref.HID, mlp_ref.HID)
+    W1[0, 0], W1[0, 1], q["b1"][0] = 1.0, -2.0, 0.5    # h1[0] = relu(x0 - 2 x1 + 0.5)
+    W1[1, 2], q["b1"][1] = 3.0, -1.0                   # h1[1] = relu(3 x2 - 1)
+    W1[2, 0] = -1.0                                    # h1[2] = relu(-x0)
+    W2[0, 0], W2[0, 1], q["b2"][0] = 2.0, 1.0, -0.25   # h2[0] = relu(2 h1[0] + h1[1] - 0.25)
+    W2[3, 2] = 1.0                                     # h2[3] = relu(h1[2])
+    W2[5, 1], q["b2"][5] = -1.0, 0.5                   # h2[5] = relu(0.5 - h1[1])
+    q["W3"][0], q["W3"][3], q["W3"][5], q["b3"][0] = 1.5, -2.0, 0.5, -0.75
+    p = np.concatenate([q[name].ravel() for name, _ in mlp_ref.SIZES])
+    x = np.zeros((2, mlp_ref.IN))
+    x[0, :3] = (1.0, 0.5, 2.0)
+    x[1, :3] = (-2.0, 1.0, 0.25)
+    x[:, 95] = 7.0  # an input no weight reads
+    # sample 0: h1 = (0.5, 5, 0), h2[0] = 5.75, h2[3] = 0, h2[5] = 0 -> z = 1.5*5.75 - 0.75
+    # sample 1: h1 = (0, 0, 2),  h2[0] = 0, h2[3] = 2, h2[5] = 0.5 -> z = -4 + 0.25 - 0.75
+    return p, x, np.array([7.875, -4.5])
+
+
+def test_reference_forward_on_a_hand_worked_network():
+    p, x, z_hand = hand_network()
+    for rnd in (True, False):
+        z, (_, h1, h2) = mlp_ref.forward(p, x, rnd=rnd)
+        assert list(z) == list(z_hand)
+        assert list(h1[0, :3]) == [0.5, 5.0, 0.0] and list(h1[1, :3]) == [0.0, 0.0, 2.0]
+        assert (h2[0, 0], h2[0, 3], h2[0, 5]) == (5.75, 0.0, 0.0)
+        assert (h2[1, 0], h2[1, 3], h2[1, 5]) == (0.0, 2.0, 0.5)
+        assert not h1[:, 3:].any() and np.count_nonzero(h2) == 3
+
+
+def test_reference_loss_is_weighted_binary_cross_entropy():
+    # the textbook form -[y log s + (1 - y) log(1 - s)], s = 1 / (1 + e^-z),
+    # weighted and divided by the weight sum
+    import math
+    p, x, z = hand_network()
+    y, w = np.array([1.0, 0.0]), np.array([1.0, 3.0])
+    s = [1 / (1 + math.exp(-v)) for v in z]
+    want = (-w[0] * math.log(s[0]) - w[1] * math.log(1 - s[1])) / 4.0
+    loss, g = mlp_ref.loss_and_grad(p, x, y, w, rnd=False)
+    assert abs(loss - want) <= 1e-12 * abs(want)
+    # d loss / d b3 = sum_i w_i (s_i - y_i) / sum w
+    o = mlp_ref.NPARAM - 1
+    assert abs(g[o] - (w[0] * (s[0] - 1) + w[1] * s[1]) / 4.0) <= 1e-12
+    # d loss / d W3[3] = sum_i w_i (s_i - y_i) h2_i[3] / sum w: only sample 1 has h2[3] = 2
+    assert abs(g[o - 256 + 3] - 3.0 * s[1] * 2.0 / 4.0) <= 1e-12
+    # a logit fixed by the output bias alone (all weights zero)
+    q = np.zeros(mlp_ref.NPARAM)
+    for b3, yy, want in ((0.0, 1.0, math.log(2)), (0.0, 0.0, math.log(2)), (40.0, 1.0, math.exp(-40.0)),
+                         (40.0, 0.0, 40.0 + math.exp(-40.0)), (-40.0, 1.0, 40.0 + math.exp(-40.0)),
+                         (-40.0, 0.0, math.exp(-40.0))):
+        q[-1] = b3
+        loss, _ = mlp_ref.loss_and_grad(q, x[:1], np.array([yy]), None, rnd=True)
+        assert abs(loss - want) <= 1e-12 * max(1.0, want), (b3, yy, loss, want)
+
+
 def test_bf16_rounding_is_round_to_nearest_even():
     vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 3.0e38, 1e-30])
     r = mlp_ref.bf16(vals)
@@ -36,7 +97,7 @@ def test_bf16_rounding_is_round_to_nearest_even():
 
 
 def test_pair_features_list_the_eligible_pairs():
-    w = workloads.config1(0)
+    w = workloads.plain_random(0)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     f, ab = ranker.pair_features(k)
     assert f.shape == (len(ab), 96) and np.isfinite(f).all()

@@ -149,13 +149,64 @@ def _lin(a, v):
 #   global, 6 accesses idx = a*tx + b*bx + c*i + d*N + e with a,b,c,d drawn
 #   in [-4, 4], N = 64 bound by the host, loop i < 8, barrier intervals
 #   {0,1,2}.  The offset e makes the smallest index of the access zero.  The
-#   last access is the planted race: thread 0 of every block writes one
-#   G element (the shape of the paper's reduceFinal, Fig. 2).
+#   five drawn accesses are race free by construction:
+#     * G is read only (reads never race with reads);
+#     * in a barrier interval where S is written, every S access of that
+#       interval uses one index expression with a nonzero thread coefficient
+#       and no loop term, so each thread owns its slot (shared memory races
+#       only inside a block, and a block's threads then never share a slot);
+#     * S accesses in intervals without an S write are reads, drawn freely.
+#   The sixth access is the planted race: thread 0 of every block writes one
+#   G element (the shape of the paper's reduceFinal, Fig. 2) at index 1024 or
+#   more, beyond every read of G (the largest read index is 4*63 + 4*3 + 4*7),
+#   so the kernel has exactly one racy access pair, (5, 5), inter-block.
+
+def _c1_expr(a, b, c, d, N, TB, GB, ITER):
+    lo = min(0, a * (TB - 1)) + min(0, b * (GB - 1)) + min(0, c * (ITER - 1)) + d * N
+    e = -lo
+    expr = "0" + _lin(a, "tx") + _lin(b, "bx") + _lin(c, "i") + _lin(d, "N")
+    return expr + (f" + {e}" if e >= 0 else f" - {-e}")
+
 
 def config1(item: int = 0) -> Workload:
-    rng = SplitMix64(seed_for(1, item))
+    rng = SplitMix64(seed_for(1, item) ^ 0xC1)
     N, TB, GB, ITER = 64, 64, 4, 8
     w = _Writer(f"plain_c1_{item}")
+    w.add("param N")
+    w.add("loop i 8")
+    w.add("array S shared 1024")
+    w.add("array G global 16384")
+    draws = []
+    for _ in range(5):
+        arr = "S" if rng.below(2) == 0 else "G"
+        kind = "W" if arr == "S" and rng.below(2) == 0 else "R"
+        draws.append((arr, kind, rng.below(3)))
+    slot = {}  # barrier interval with an S write -> the thread-owned index expression
+    for arr, kind, iv in draws:
+        if arr == "S" and kind == "W" and iv not in slot:
+            a = rng.range(1, 4) * (1 if rng.below(2) else -1)
+            b, d = rng.range(-4, 4), rng.range(-4, 4)
+            slot[iv] = _c1_expr(a, b, 0, d, N, TB, GB, ITER)
+    for a_id, (arr, kind, iv) in enumerate(draws):
+        if arr == "S" and iv in slot:
+            expr = slot[iv]
+        else:
+            expr = _c1_expr(*(rng.range(-4, 4) for _ in range(4)), N, TB, GB, ITER)
+        w.access(kind, arr, 4, expr, iv=iv, line=10 + a_id)
+    d = rng.range(-4, 4)
+    e = -d * N + 1024 + rng.below(64)
+    w.access("W", "G", 4, f"{d}*N + {e}", iv=rng.below(3), guards=["tx == 0"], line=20)
+    return Workload(f"c1_{item}", w.text(), Binding((GB, 1, 1), (TB, 1, 1), (N,)),
+                    {"config": 1, "loop_bounds": [ITER], "n_access": 6})
+
+
+def plain_random(item: int = 0) -> Workload:
+    """The config-1 launch shape with five unconstrained random accesses
+    (racy almost everywhere) plus the Fig. 2 write: many witnesses on few
+    instances, for tests of truncation and buffer retries."""
+    rng = SplitMix64(seed_for(1, item))
+    N, TB, GB, ITER = 64, 64, 4, 8
+    w = _Writer(f"plain_random_{item}")
     w.add("param N")
     w.add("loop i 8")
     w.add("array S shared 1024")
@@ -164,15 +215,11 @@ def config1(item: int = 0) -> Workload:
         arr = "S" if rng.below(2) == 0 else "G"
         kind = "R" if rng.below(2) == 0 else "W"
         a, b, c, d = (rng.range(-4, 4) for _ in range(4))
-        lo = min(0, a * (TB - 1)) + min(0, b * (GB - 1)) + min(0, c * (ITER - 1)) + d * N
-        e = -lo
-        expr = "0" + _lin(a, "tx") + _lin(b, "bx") + _lin(c, "i") + _lin(d, "N")
-        expr += f" + {e}" if e >= 0 else f" - {-e}"
-        w.access(kind, arr, 4, expr, iv=rng.below(3), line=10 + a_id)
+        w.access(kind, arr, 4, _c1_expr(a, b, c, d, N, TB, GB, ITER), iv=rng.below(3), line=10 + a_id)
     d = rng.range(-4, 4)
     e = -d * N + rng.below(64)
     w.access("W", "G", 4, f"{d}*N + {e}", iv=rng.below(3), guards=["tx == 0"], line=20)
-    return Workload(f"c1_{item}", w.text(), Binding((GB, 1, 1), (TB, 1, 1), (N,)),
+    return Workload(f"pr_{item}", w.text(), Binding((GB, 1, 1), (TB, 1, 1), (N,)),
                     {"config": 1, "loop_bounds": [ITER], "n_access": 6})
 
 
