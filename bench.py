@@ -95,48 +95,88 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def cpu_info():
+    """Host CPU model (lscpu) and the cores this process may use."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    return model, cores
+
+
 def run_reference(args, rank):
-    """CPU oracle on a bounded sample of the same workload (rank 0 only)."""
+    """The CPU oracle on a bounded sample of the same workload, on all the
+    host cores (its parallel mode: buckets split into one band per core);
+    rank 0 only."""
     if rank != 0:
         return
+    import multiprocessing as mp
     import oracle
     import workloads
     oracle.build()
+    model, cores = cpu_info()
     side = args.ref_side
     w = workloads.config2(0, planted=True, W=side, H=side, K=32)
-    for _ in range(args.warmup if args.ref_warmup else 0):
-        oracle.check(w.text, w.binding)
     t = []
     n = 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = oracle.check(w.text, w.binding)
-        t.append(time.perf_counter() - t0)
-        n += r.n_instances
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(args.warmup if args.ref_warmup else 0):
+            oracle.check_parallel(w.text, w.binding, cores, pool=pool)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = oracle.check_parallel(w.text, w.binding, cores, pool=pool)
+            t.append(time.perf_counter() - t0)
+            n += r.n_instances
+    assert r.n_witness == w.meta["expected_witnesses"]
     total = sum(t)
     value = n / total
     sample = (f"same stencil kernel on a {side}x{side} image ({side // 16}x{side // 16} blocks, "
-              f"{r.n_instances:,} instances per step), whole oracle per step")
+              f"{r.n_instances:,} instances per step), the whole oracle per step on {cores} processes "
+              f"(one band of granules each)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample_side": side},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": model, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(side):
+def cpu_baseline(side, side_n):
+    """The oracle as it stands on the host: one core on a side x side stencil,
+    and all cores (parallel mode) on a side_n x side_n one."""
+    import multiprocessing as mp
     import oracle
     import workloads
     oracle.build()
+    model, cores = cpu_info()
     w = workloads.config2(0, planted=True, W=side, H=side, K=32)
     t0 = time.perf_counter()
     r = oracle.check(w.text, w.binding)
     dt = time.perf_counter() - t0
-    return {"value": r.n_instances / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"same stencil kernel on a {side}x{side} image ({r.n_instances:,} instances), "
-                      f"one whole oracle run, {dt:.1f} s"}
+    out = {"value": r.n_instances / dt, "unit": UNIT, "cores": 1, "cpu": model, "kind": "oracle",
+           "sample": f"same stencil kernel on a {side}x{side} image ({r.n_instances:,} instances), "
+                     f"one whole oracle run on one core, {dt:.1f} s"}
+    wn = workloads.config2(0, planted=True, W=side_n, H=side_n, K=32)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        rn = oracle.check_parallel(wn.text, wn.binding, cores, pool=pool)
+        dtn = time.perf_counter() - t0
+    assert rn.n_witness == wn.meta["expected_witnesses"]
+    out["all_cores"] = {"value": rn.n_instances / dtn, "unit": UNIT, "cores": cores, "cpu": model,
+                        "kind": "oracle, parallel mode (buckets in one band of granules per process)",
+                        "sample": f"same stencil kernel on a {side_n}x{side_n} image ({rn.n_instances:,} "
+                                  f"instances), one whole run on {cores} processes, {dtn:.1f} s"}
+    return out
 
 
 # keys of one sort-tuner pass (hgrd_sort_tune with the binding's default 600 MB workspace)
@@ -309,6 +349,59 @@ def run_suite(args):
     print(json.dumps(line), flush=True)
 
 
+def run_suite_sharded(args, rank, world, local):
+    """A batch suite on several GPUs: the items split by longest-processing-
+    time-first on their instance counts (shard.lpt_partition), each rank's
+    share one batched check on its GPU, the verdicts gathered on the host at
+    the end (no data-path exchange).  Total work is fixed: strong scaling."""
+    import torch
+    import torch.distributed as dist
+    import workloads
+    import paper_2604_02106_b300 as hg
+    from paper_2604_02106_b300 import shard
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.suite == "sweep":
+        ws = workloads.config3()
+        name = "host-loop sweep: one 12-access kernel under 64 bindings (N 2^8..2^20 x stride {1,2,3,4,32})"
+    else:
+        ws = [workloads.config4(i) for i in range(args.items)]
+        name = f"corpus of {args.items} seeded kernels, log-uniform 1e3..1e7 instances"
+    ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in ws]
+    costs = [k.info()[0] for k in ks]
+    share = shard.lpt_partition(costs, world)[rank]
+    mine = [ks[i] for i in share]
+    s = torch.cuda.Stream()
+    b = hg.Batch(mine, graph=True) if mine else None
+    if b:
+        b.tune(stream=s)
+        res = b.check(stream=s)
+        for _ in range(max(3, args.warmup)):
+            b.run(stream=s)
+    flush = l2_flusher(s)
+    torch.cuda.synchronize()
+    dist.barrier()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(s, args.steps, (lambda: b.run(stream=s)) if b else (lambda: None), flush)
+    ms = max_over_ranks(ms, dist)
+    allres = shard.gather(dict(zip(share, res if b else [])), len(ks), dist)
+    n_inst = sum(costs)
+    assert [r.n_instances for r in allres] == costs
+    if rank == 0:
+        line = {"metric": METRIC, "value": n_inst / (ms / 1000), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": name, "items": len(ks), "instances": n_inst,
+                           "racy_items": sum(r.racy for r in allres),
+                           "parallelism": f"items split over {world} ranks (longest first), verdicts gathered",
+                           "form": "batched, CUDA graph, interpreted expansion"},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def run_symbolic(args):
     """Symbolic-parameter mode: is the strided kernel racy under some admissible
     (N, STRIDE)?  N from host-loop values, STRIDE from the range its asserts
@@ -471,10 +564,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hgrd", choices=["hgrd", "reference"])
     ap.add_argument("--ref-side", type=int, default=256)
+    ap.add_argument("--ref-side-all", type=int, default=512,
+                    help="stencil side of the all-cores oracle sample in the CPU baseline")
     ap.add_argument("--ref-warmup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=1024)
     ap.add_argument("--no-sort-tune", action="store_true")
+    ap.add_argument("--no-full-sort", action="store_true",
+                    help="skip the measurement of the sort and scan with every key of the check sorted")
     ap.add_argument("--no-jit", action="store_true", help="interpreted expansion kernels only")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each check's kernels directly instead of replaying its CUDA graph "
@@ -497,7 +594,10 @@ def main():
         run_symbolic(args)
         return
     if args.suite not in ("stencil", "warp"):
-        run_suite(args)
+        if world > 1:
+            run_suite_sharded(args, rank, world, local)
+        else:
+            run_suite(args)
         return
     if args.once:
         run_once(args)
@@ -618,6 +718,43 @@ def main():
                     "peak_kind": "derived: 148 SMs x 128 int32 lanes x max SM clock", "traffic": traffic,
                     "ops_per_launch": ops, "instances_per_launch": n_inst}
 
+    # ---- the sort and the scan at the check's own key scale: the same check
+    # with every live key written, sorted and scanned (HGRD_ALL_KEYS: no key
+    # dropped by the pair rule, one global sort, no cell filter), per-stage
+    # CUDA events, L2 flushed before every step; same verdict
+    roof_full = None
+    if args.suite == "stencil" and not args.no_full_sort:
+        FF = hg.ALL_KEYS | hg.NO_CELL_FILTER | hg.NO_PAIR
+        wsf = torch.empty(k.workspace_size(flags=FF), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            k.enqueue(wsf, stream=s, flags=FF | hg.PROFILE)
+        rf = k.collect(wsf, cap=1 << 16, stream=s, flags=FF)
+        assert rf.witnesses == res.witnesses and rf.n_keys == res.n_keys
+        stf = hg.stats()
+        full_stages = {}
+        for _ in range(args.steps):
+            flush_l2()
+            k.enqueue(wsf, stream=s, flags=FF | hg.PROFILE)
+            for name, t in hg.last_profile():
+                full_stages.setdefault(name, []).append(t)
+        fms = {n: sum(v) / len(v) for n, v in full_stages.items()}
+        ns = stf["n_sorted_keys"]
+        del wsf
+        passes = [n for n in fms if n.startswith("sort_pass")]
+
+        def roof(name, nbytes, what):
+            a = nbytes / (fms[name] / 1000.0) / 1e9
+            return {"bound": "hbm", "kernel": name, "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": a / hbm_peak, "peak_kind": peak_kind, "bytes_per_launch": nbytes,
+                    "ms_per_launch": fms[name], "bytes_rule": what}
+        roof_full = {
+            "workload": f"{workload}, every live key written and sorted (HGRD_ALL_KEYS | NO_CELL_FILTER)",
+            "sorted_keys": ns, "sort_passes": len(passes), "stages_ms": {n: round(t, 4) for n, t in fms.items()},
+            "sort": [roof(n, 16 * ns, "8 B read + 8 B written per key") for n in passes],
+            "scan": roof("candidates", 8 * ns, "8 B read per sorted key"),
+            "expand_write": roof("expand_write", 8 * ns, "8 B written per key"),
+            "check_ms": sum(fms.values())}
+
     # ---- end to end through the public synchronous call
     torch.cuda.synchronize()
     if dist:
@@ -665,11 +802,12 @@ def main():
                 "roofline": roofline,
                 "roofline_hbm": roof_hbm,
                 "roofline_sort": roof_sort,
+                "roofline_full_sort": roof_full,
                 "stages_ms": {n: round(t, 4) for n, t in stage_ms.items()},
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches * args.steps)}
         if not args.no_cpu_baseline and args.suite == "stencil":
-            line["cpu_baseline"] = cpu_baseline(args.ref_side)
+            line["cpu_baseline"] = cpu_baseline(args.ref_side, args.ref_side_all)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
