@@ -695,7 +695,9 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
     // constant, the access's own index, or another; folded on a copy of the
     // folder so that no expression node of theirs joins the program
     std::vector<char> s_const(d.acc.size(), 0), s_own(d.acc.size(), 0);  // (both, when the index is constant)
+    std::vector<char> s_ids(d.acc.size(), 0);  // affine in thread and block ids alone
     std::vector<int64_t> sval(d.acc.size(), 0);
+    std::vector<Lin> slin(d.acc.size());
     for (size_t a = 0; a < d.acc.size(); a++) {
       if (d.acc[a].sync_arr < 0) continue;
       Folder F2 = F;
@@ -703,6 +705,10 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       s_const[a] = s.is_const();
       sval[a] = s.c0;
       s_own[a] = s.key() == af[a].idx.key();
+      bool ids = s.cn.empty();
+      for (int k = 6; k < NVAR; k++) ids = ids && s.cv[k] == 0;
+      s_ids[a] = ids;
+      slin[a] = s;
     }
     // node ranges and loop dependence, in creation order (operands first)
     for (size_t i = 0; i < F.nodes.size(); i++) {
@@ -1053,20 +1059,43 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         // guarded at its own index with equal widths: one location, one
         // element) or none has (two different constants).
         if (m && x.sync_arr >= 0 && x.sync_arr == y.sync_arr && !af[a].dead && !af[b].dead) {
-          bool same = false;
+          bool same = false, per_instance = false;
           if (s_own[a] && s_own[b] && x.width == y.width)
             same = true;
           else if (s_const[a] && s_const[b])
             same = sval[a] == sval[b];
+          else if ((s_own[a] || s_ids[a]) && (s_own[b] || s_ids[b]))
+            per_instance = true;  // elements from the ids or the location: compared per instance pair
           else
             raise(HGRD_EUNSUPPORTED,
-                  "acquire-release guards of two accesses on one array must both be constant or both the "
-                  "access's own index (equal widths)");
+                  "an acquire-release guard element must be constant, the access's own index, or affine in "
+                  "thread and block ids (no loop counter, division or remainder)");
           if (same) m &= std::min(x.sync_scope, y.sync_scope) == 1 ? 0 : 1;
+          if (per_instance) {
+            P.lockpair[a] |= 1u << b;
+            P.lockpair[b] |= 1u << a;
+            P.lockany = 1;
+          }
         }
         if ((m & 1) && affine[a] && affine[b] && blocks_disjoint(a, b)) m &= ~1;
         if (m & 1) P.einter[a] |= 1u << b;
         if (m & 6) P.eintra[a] |= 1u << b;
+      }
+    }
+    // guard elements of the accesses decided per instance pair: affine in the
+    // ids (evaluated from the key's block and thread), else the access's own
+    // element (from the location)
+    for (int a = 0; a < P.nacc; a++) {
+      if (!P.lockpair[a]) continue;
+      DLock& L = P.lock[a];
+      L.arr = d.acc[a].sync_arr;
+      L.scope = d.acc[a].sync_scope;
+      if (s_ids[a]) {
+        L.form = LOCK_AFFINE;
+        L.c0 = slin[a].c0;
+        for (int v = 0; v < 6; v++) L.c[v] = slin[a].cv[v];
+      } else {
+        L.form = LOCK_OWN;
       }
     }
 
@@ -1171,7 +1200,11 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         if (!P.acc[a].dead && P.acc[a].shared) per_block += (unsigned __int128)nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;
       const uint64_t smem = sizeof(DProg) + (uint64_t)EXP_THREADS * nslot * (wide ? 8 : 4) +
                             (uint64_t)P.nsbins * 13 + 2048;
-      P.smode = !P.WVB && any_shared_live && upb >= 4 && P.nsbins > 0 && P.nsbins <= SBIN_MAX &&
+      // shared locations with guards decided per instance pair go through the
+      // global sort and the exact scan's pairwise check
+      bool shared_lock = false;
+      for (int a = 0; a < P.nacc; a++) shared_lock |= P.lockpair[a] && P.acc[a].shared;
+      P.smode = !P.WVB && !shared_lock && any_shared_live && upb >= 4 && P.nsbins > 0 && P.nsbins <= SBIN_MAX &&
                 (unsigned __int128)P.nsbins * (uint64_t)nblk <= ((unsigned __int128)1 << 25) &&
                 per_block < 0xffffffffu && smem <= 200 * 1024;
       P.RBG = P.smode ? ceil_log2(std::max<uint64_t>(P.shared_cell_base, 1)) + P.IVB : P.RB;

@@ -90,6 +90,17 @@ struct DAcc {
   int64_t sgbase;  // shared arrays: first granule of the array among one block's shared granules
 };
 
+// The acquire-release guard of an access whose guard element the exact scan
+// evaluates per instance (Sec. 6.5): AFFINE, c0 + sum c[v] * id[v] over the
+// thread and block ids (tx ty tz bx by bz; constants included), or OWN, the
+// access's own element (granule / G of the location).
+enum { LOCK_NONE = 0, LOCK_AFFINE = 1, LOCK_OWN = 2 };
+struct DLock {
+  int32_t form, arr;   // LOCK_*, lock array
+  int32_t scope, pad;  // narrower scope of the guard's parts: 0 block, 1 device
+  int64_t c0, c[6];
+};
+
 // Everything the kernels need about one bound descriptor.  Lives in the
 // device workspace; all lanes read it with uniform addresses.
 struct alignas(16) DProg {
@@ -137,6 +148,12 @@ struct alignas(16) DProg {
   // below 2^31 (unit, block and thread ids): magic numbers with N = 31
   Magic dv[6];
   uint32_t einter[MAXACC], eintra[MAXACC];
+  // access pairs guarded at one lock array whose guard elements can differ
+  // between instances: the exact scan decides them pair by pair of
+  // instances (lockpair[a] bit b), the other pairs from the summaries
+  uint32_t lockpair[MAXACC];
+  int32_t lockany, pad5;
+  DLock lock[MAXACC];
   uint64_t lay_cbase[MAXARR + 1];
   uint64_t lay_ngran[MAXARR];
   int32_t lay_arr[MAXARR], lay_shared[MAXARR];
@@ -189,7 +206,10 @@ enum {
   C_SMALLQ = 120,  // one-CTA path of a small check: work queue, then an order word of zero
   C_WORDS = 128
 };
-enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4, ERR_SMALL_FULL = 8 };
+enum { ERR_TIMEOUT = 1, ERR_OVERFLOW = 2, ERR_SHARED_FULL = 4, ERR_SMALL_FULL = 8, ERR_LOCK_RUN = 16 };
+// most keys of one location the exact scan checks instance pair by instance
+// pair for guards whose elements vary (more: ERR_LOCK_RUN)
+constexpr uint64_t LOCK_RUN_MAX = 8192;
 
 // the expansion kernels run 8 warps per CTA, one simulated warp per warp
 constexpr int EXP_THREADS = 256;

@@ -219,7 +219,89 @@ __device__ __forceinline__ uint32_t racy_row(const Sum& s, int lane) {
 struct RunMasks {
   uint64_t rid;
   uint32_t inter, blk, warp;
+  bool lock_overflow = false;  // guards decided per instance on a run longer than LOCK_RUN_MAX
 };
+
+// (space, array, granule) of run id `rid` in the array layout
+__device__ __forceinline__ void run_location(const DProg* __restrict__ P, uint64_t rid, uint32_t* space, uint32_t* arr,
+                                             uint64_t* gran) {
+  int li = 0;
+  while (li + 1 < P->nlay && P->lay_cbase[li + 1] <= rid) ++li;
+  const uint64_t cell = rid - P->lay_cbase[li];
+  const bool sh = P->lay_shared[li];
+  *gran = sh ? cell % P->lay_ngran[li] : cell;
+  *arr = (uint32_t)P->lay_arr[li];
+  *space = sh ? 1u : 0u;
+}
+
+// The element a guarded instance holds (Sec. 6.5's syn() address): affine in
+// the ids of its thread and block, or its own element on granule `gran`.
+__device__ __forceinline__ int64_t lock_element(const DProg* __restrict__ P, int a, uint32_t blk, uint32_t thr,
+                                                uint64_t gran) {
+  const DLock& L = P->lock[a];
+  if (L.form == LOCK_OWN) return (int64_t)(gran / (uint64_t)P->acc[a].G);
+  const int64_t tx = thr % P->block[0], ty = (thr / P->block[0]) % P->block[1], tz = thr / (P->block[0] * P->block[1]);
+  const int64_t bx = blk % P->grid[0], by = (blk / P->grid[0]) % P->grid[1], bz = blk / (P->grid[0] * P->grid[1]);
+  return L.c0 + L.c[0] * tx + L.c[1] * ty + L.c[2] * tz + L.c[3] * bx + L.c[4] * by + L.c[5] * bz;
+}
+
+// Race kinds of the guarded pairs whose elements vary, instance pair by
+// instance pair over the run [s, end) (Table 2 with Sec. 6.5's addr(syn)
+// test): a pair of different threads races with its kind (inter-block
+// across blocks in global memory; else same barrier interval, different
+// warps: intra-block; same warp and warp interval: intra-warp) unless both
+// are guarded at one element and the guards' narrower scope covers the kind
+// (device scope across blocks).  Rows by lane = access, as the summaries.
+__device__ __forceinline__ void lock_pairs_run(const uint64_t* keys, uint64_t s, uint64_t end, const DProg* __restrict__ P,
+                                               int lane, bool glob, uint64_t gran, RunMasks& R) {
+  const int PB = P->PB, AB = P->AB, TB = P->TB, BB = P->BB, WVB = P->WVB;
+  uint32_t mi = 0, mb = 0, mw = 0;
+  for (uint64_t xi = s; xi < end; ++xi) {
+    const uint64_t kx = keys[xi];
+    const uint32_t ax = (uint32_t)lowbits(kx, AB);
+    const uint32_t rowx = P->lockpair[ax];
+    if (!rowx) continue;
+    const uint32_t bx = (uint32_t)lowbits(kx >> (AB + TB + WVB), BB), tx = (uint32_t)lowbits(kx >> AB, TB);
+    const uint64_t subx = shr64(kx, PB);
+    const uint32_t wvx = (uint32_t)lowbits(kx >> (AB + TB), WVB);
+    const int64_t lx = lock_element(P, (int)ax, bx, tx, gran);
+    const uint32_t allow_inter = P->einter[ax], allow_intra = P->eintra[ax];
+    for (uint64_t y0 = xi + 1; y0 < end; y0 += 32) {
+      const uint64_t yi = y0 + lane;
+      uint32_t k = 0, ay = 0;
+      if (yi < end) {
+        const uint64_t ky = keys[yi];
+        ay = (uint32_t)lowbits(ky, AB);
+        if ((rowx >> ay) & 1u) {
+          const uint32_t by = (uint32_t)lowbits(ky >> (AB + TB + WVB), BB), ty = (uint32_t)lowbits(ky >> AB, TB);
+          if (bx != by) k = glob ? 1u : 0u;
+          else if (tx == ty || shr64(ky, PB) != subx) k = 0;
+          else if ((tx >> 5) != (ty >> 5)) k = 2;
+          else k = (uint32_t)lowbits(ky >> (AB + TB), WVB) == wvx ? 4u : 0u;
+          k &= ((allow_inter >> ay) & 1u) | (((allow_intra >> ay) & 1u) ? 6u : 0u);
+          if (k && P->lock[ax].arr == P->lock[ay].arr && lx == lock_element(P, (int)ay, by, ty, gran) &&
+              (k != 1u || min(P->lock[ax].scope, P->lock[ay].scope) == 1))
+            k = 0;  // ordered by the acquire-release both hold
+        }
+      }
+      const uint32_t r1 = __reduce_or_sync(FULL, (k & 1u) ? 1u << ay : 0u);
+      const uint32_t r2 = __reduce_or_sync(FULL, (k & 2u) ? 1u << ay : 0u);
+      const uint32_t r4 = __reduce_or_sync(FULL, (k & 4u) ? 1u << ay : 0u);
+      if ((uint32_t)lane == ax) {
+        mi |= r1;
+        mb |= r2;
+        mw |= r4;
+      }
+      mi |= ((r1 >> lane) & 1u) << ax;
+      mb |= ((r2 >> lane) & 1u) << ax;
+      mw |= ((r4 >> lane) & 1u) << ax;
+    }
+  }
+  R.inter |= mi;
+  R.blk |= mb;
+  R.warp |= mw;
+}
+
 __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, uint64_t e, uint64_t n,
                                               const DProg* __restrict__ P, int lane, uint32_t einter,
                                               uint32_t eintra, bool stop_first = false) {
@@ -228,6 +310,12 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
   RunMasks R;
   R.rid = shr64(keys[s], rsh);
   const bool glob = R.rid < P->shared_cell_base;
+  // pairs decided instance pair by instance pair stay out of the summaries
+  if (P->lockany && lane < MAXACC) {
+    einter &= ~P->lockpair[lane];
+    eintra &= ~P->lockpair[lane];
+  }
+  uint64_t end = s;
   // thread per (iv, block, warp interval, warp); warp per (iv, block); block
   // per run.  Keys of one (iv, block) are contiguous and ordered by warp
   // interval, each warp's keys contiguous inside a warp interval.
@@ -245,6 +333,7 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
     const bool inrun = ok && shr64(kk, rsh) == R.rid;
     const unsigned m = __ballot_sync(FULL, inrun);
     const int cnt = __popc(m);
+    end = pos + cnt;
     for (int jj = 0; jj < cnt; ++jj) {
       const uint64_t key = __shfl_sync(FULL, kk, jj);
       const uint64_t sub = shr64(key, PB);
@@ -285,19 +374,25 @@ __device__ __forceinline__ RunMasks exact_run(const uint64_t* keys, uint64_t s, 
   R.inter = m_inter;
   R.blk = m_blk;
   R.warp = m_warp;
+  if (P->lockany) {
+    // the run's own end (a stop-at-first scan may have left it early)
+    while (true) {
+      const uint64_t i = end + lane;
+      const bool inrun = i < n && (e == 0 || i < e) && shr64(keys[i], rsh) == R.rid;
+      const unsigned m = __ballot_sync(FULL, inrun);
+      end += __popc(m);
+      if (m != FULL) break;
+    }
+    if (end - s > LOCK_RUN_MAX) {
+      R.lock_overflow = true;
+    } else {
+      uint32_t space, arr;
+      uint64_t gran;
+      run_location(P, R.rid, &space, &arr, &gran);
+      lock_pairs_run(keys, s, end, P, lane, glob, gran, R);
+    }
+  }
   return R;
-}
-
-// (space, array, granule) of run id `rid` in the array layout
-__device__ __forceinline__ void run_location(const DProg* __restrict__ P, uint64_t rid, uint32_t* space, uint32_t* arr,
-                                             uint64_t* gran) {
-  int li = 0;
-  while (li + 1 < P->nlay && P->lay_cbase[li + 1] <= rid) ++li;
-  const uint64_t cell = rid - P->lay_cbase[li];
-  const bool sh = P->lay_shared[li];
-  *gran = sh ? cell % P->lay_ngran[li] : cell;
-  *arr = (uint32_t)P->lay_arr[li];
-  *space = sh ? 1u : 0u;
 }
 
 // OR this lane's rows of the run into the racy-pair matrices (two 32-bit rows per word)

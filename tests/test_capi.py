@@ -115,19 +115,26 @@ def test_workspace_scales_with_problem():
 def test_acquire_release_guards_bind():
     # acquire-release guards (Sec. 6.5): decided at bind time when both guards
     # of a pair on one lock array are constant, or both the access's own index
-    # (equal widths); other forms guarding one pair are rejected, a guard
-    # without a guarded partner is fine; a lock array must be global
-    base = "kernel k\narray d global 256\narray L global 64\narray S shared 64\n"
+    # (equal widths); decided per instance pair by the exact scan when each
+    # guard element is constant, affine in thread and block ids, or the
+    # access's own index; other forms guarding a pair are rejected (a loop
+    # counter, or a division or remainder that is not the access's own
+    # index); a guard without a guarded partner is fine; a lock array must be
+    # global
+    base = "kernel k\nloop i 2\narray d global 256\narray L global 64\narray S shared 64\n"
     ok = [("access W d ; width 4 ; idx 0 ; sync L 0", "access R d ; width 4 ; idx 0 ; sync L 1"),
           ("access W d ; width 4 ; idx tx % 4 ; sync L tx % 4", "access R d ; width 4 ; idx tx / 8 ; sync L tx / 8"),
           ("access R d ; width 4 ; idx 0 ; sync L tx", "access W d ; width 4 ; idx 0"),
-          ("access W d ; width 4 ; idx 3 ; sync L 3", "access R d ; width 4 ; idx tx ; sync L tx")]
+          ("access W d ; width 4 ; idx 3 ; sync L 3", "access R d ; width 4 ; idx tx ; sync L tx"),
+          ("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0"),
+          ("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0 ; sync L 0"),
+          ("access W d ; width 8 ; idx tx ; sync L tx", "access R d ; width 4 ; idx tx ; sync L tx"),
+          ("access W d ; width 4 ; idx tx % 4 ; sync L tx % 4", "access R d ; width 4 ; idx 0 ; sync L bx + 2")]
     for a, b in ok:
         hg.Kernel(base + a + "\n" + b + "\n").bind((2, 1, 1), (32, 1, 1), ())
-    bad = [("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0"),
-           ("access W d ; width 4 ; idx 0 ; sync L tx", "access R d ; width 4 ; idx 0 ; sync L 0"),
-           ("access W d ; width 4 ; idx tx % 4 ; sync L tx % 2", "access R d ; width 4 ; idx 0"),
-           ("access W d ; width 8 ; idx tx ; sync L tx", "access R d ; width 4 ; idx tx ; sync L tx")]
+    bad = [("access W d ; width 4 ; idx tx % 4 ; sync L tx % 2", "access R d ; width 4 ; idx 0"),
+           ("access W d ; width 4 ; idx 0 ; sync L i", "access R d ; width 4 ; idx 0 ; sync L 0"),
+           ("access W d ; width 4 ; idx 0 ; sync L tx / 2", "access R d ; width 4 ; idx 0")]
     for a, b in bad:
         assert _err(base + a + "\n" + b + "\n", grid=(2, 1, 1)) == -9
     assert _err(base + "access W d ; width 4 ; idx 0 ; sync S 0\n") == -2   # shared lock array

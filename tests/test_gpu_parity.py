@@ -485,6 +485,17 @@ def test_acquire_release_random_against_oracle(seed):
     _same(*_both(w.text, w.binding))
 
 
+@pytest.mark.parametrize("seed", range(80))
+def test_acquire_release_per_instance_against_oracle(seed):
+    # guard elements mixed per kernel (constants, per-thread tx, per-block bx,
+    # each access's own index): pairs whose elements can differ between
+    # instances are decided instance pair by instance pair in the exact scan
+    w = workloads.random_sync(11000 + seed, supported=False)
+    _same(*_both(w.text, w.binding))
+    _same(hg.check(w.text, w.binding, cap=1 << 20, flags=hg.NO_SMALL | hg.JIT),
+          oracle.check(w.text, w.binding, cap=1 << 20))
+
+
 _RMW = "kernel c\narray c global 4\narray L global 64\narray F global 64\n"
 _R, _W = "access R c ; width 4 ; idx 0", "access W c ; width 4 ; idx 0"
 
@@ -502,6 +513,14 @@ _R, _W = "access R c ; width 4 ; idx 0", "access W c ; width 4 ; idx 0"
     "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 0\n",
     "kernel p\narray d global 4\narray F global 64\naccess W d ; width 4 ; idx 0 ; if tx == 0 ; sync F 0\n"
     "access R d ; width 4 ; idx 0 ; if tx > 0 ; sync F 1\n",
+    # a lock per block: ordered inside a block, not across blocks
+    _RMW + f"{_R} ; sync L bx\n{_W} ; sync L bx\n",
+    # a lock per thread orders nothing between threads
+    _RMW + f"{_R} ; sync L tx\n{_W} ; sync L tx\n",
+    # a lock per block in block scope
+    _RMW + f"{_R} ; sync L bx + 4 ; syncscope block\n{_W} ; sync L bx + 4 ; syncscope block\n",
+    # two lock families on one pair: equal elements only where tx == bx
+    _RMW + f"{_R} ; sync L tx\n{_W} ; sync L bx\n",
 ])
 @pytest.mark.parametrize("jit", [0, hg.JIT])
 def test_acquire_release_fixtures(text, jit):
