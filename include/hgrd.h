@@ -296,6 +296,36 @@ int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_st
 int hgrd_batch_tune(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* cuda_stream, hgrd_batch_opts* chosen);
 void hgrd_batch_free(hgrd_batch* b);
 
+/* Ranked batch (the learned ranker over a whole batch; the paper has no
+ * learned part).  hgrd_batch_rank_prepare lists every item's eligible access
+ * pairs with their 96 features (as hgrd_pair_features; static per binding,
+ * computed once on the host).  hgrd_batch_check_ranked then, on the stream:
+ *   1. scores every pair of every item in one inference (hgrd_mlp_predict)
+ *      and takes each item's top-k pairs on the device (ties to the lower
+ *      pair index); an item with at most k eligible pairs takes them all,
+ *      one whose best logit is below min_score is not ranked;
+ *   2. runs the batch once, each ranked large item restricted to the
+ *      accesses of its top pairs (small items run whole on chip);
+ *   3. runs the whole check of every ranked item that stage 2 found clean,
+ *      unless its checked accesses covered every eligible pair.
+ * Verdicts (racy) are exact for every item.  An item decided racy by its
+ * restricted check reports the races found there (each a race of the item,
+ * Sec. 6.1: races are pairwise), not its full witness set.  stage[n] (may be
+ * NULL): 0 whole check in the first run, 1 race found by the restricted
+ * check, 2 whole check in the second run, 3 clean on a restricted check
+ * covering every eligible pair.  Features are uploaded into the workspace on
+ * the first call with it.  Synchronous on return (two host round trips). */
+typedef struct {
+  uint32_t n_pairs, ranked, confirmed, second; /* pairs scored, items ranked, races confirmed, second-run items */
+  float ms_score, ms_stage1, ms_stage2;        /* host wall time of each part */
+  float pad;
+} hgrd_batch_rank_info;
+int hgrd_batch_rank_prepare(hgrd_batch* b);
+int hgrd_batch_ranked_workspace_size(const hgrd_batch* b, size_t* bytes);
+int hgrd_batch_check_ranked(hgrd_batch* b, const void* d_model, uint32_t topk, float min_score, void* d_ws,
+                            size_t ws_bytes, void* cuda_stream, hgrd_item_verdict* v, hgrd_witness* w, uint32_t wcap,
+                            uint8_t* stage, hgrd_batch_rank_info* info);
+
 /* ---- The learned ranker (an AI-systems addition; the paper has no learned part)
  * An MLP 96 -> 256 -> 256 -> 1 (ReLU) scores access pairs of a bound kernel
  * so that likely races are checked first.  BF16 operands, FP32 accumulation

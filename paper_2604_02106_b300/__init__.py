@@ -38,7 +38,8 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_mlp_model_bytes", "hgrd_mlp_workspace_bytes", "hgrd_mlp_init", "hgrd_mlp_predict", "hgrd_mlp_grad",
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
            "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source",
-           "hgrd_desc_params", "hgrd_bound_hash", "hgrd_bound_info"]
+           "hgrd_desc_params", "hgrd_bound_hash", "hgrd_bound_info", "hgrd_batch_rank_prepare",
+           "hgrd_batch_ranked_workspace_size", "hgrd_batch_check_ranked"]
 BATCH_GRAPH = 1
 BATCH_JIT = 2
 
@@ -99,6 +100,11 @@ class ItemVerdict(C.Structure):
                 ("n_keys", C.c_uint64), ("n_oob", C.c_uint64), ("pair_kind", (C.c_uint32 * 32) * 3)]
 
 
+class BatchRankInfo(C.Structure):
+    _fields_ = [("n_pairs", C.c_uint32), ("ranked", C.c_uint32), ("confirmed", C.c_uint32), ("second", C.c_uint32),
+                ("ms_score", C.c_float), ("ms_stage1", C.c_float), ("ms_stage2", C.c_float), ("pad", C.c_float)]
+
+
 class StageTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_float)]
 
@@ -139,8 +145,14 @@ def lib():
         L.hgrd_batch_tune.argtypes = [vp, vp, sz, vp, C.POINTER(BatchOpts)]
         L.hgrd_batch_free.argtypes = [vp]
         L.hgrd_batch_free.restype = None
+        L.hgrd_batch_rank_prepare.argtypes = [vp]
+        L.hgrd_batch_ranked_workspace_size.argtypes = [vp, C.POINTER(sz)]
+        L.hgrd_batch_check_ranked.argtypes = [vp, vp, C.c_uint32, C.c_float, vp, sz, vp, C.POINTER(ItemVerdict),
+                                              C.POINTER(Witness), C.c_uint32, C.POINTER(C.c_uint8),
+                                              C.POINTER(BatchRankInfo)]
         for f in ["hgrd_batch_create", "hgrd_batch_workspace_size", "hgrd_batch_run", "hgrd_batch_collect",
-                  "hgrd_batch_tune"]:
+                  "hgrd_batch_tune", "hgrd_batch_rank_prepare", "hgrd_batch_ranked_workspace_size",
+                  "hgrd_batch_check_ranked"]:
             getattr(L, f).restype = C.c_int
         L.hgrd_last_stats.argtypes = [C.POINTER(Stats)]
         L.hgrd_last_profile.argtypes = [C.POINTER(StageTime), C.c_uint32, C.POINTER(C.c_uint32)]
@@ -430,6 +442,43 @@ class Batch:
         self.run(stream)
         return self.collect(stream)
 
+    def rank_prepare(self):
+        """hgrd_batch_rank_prepare: every item's eligible pairs and features (host, once)."""
+        _raise(lib().hgrd_batch_rank_prepare(self._h))
+        n = C.c_size_t()
+        _raise(lib().hgrd_batch_ranked_workspace_size(self._h, C.byref(n)))
+        import torch
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = None
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self._ranked = True
+
+    def check_ranked(self, model, topk: int = 4, min_score: float = float("-inf"), stream=None):
+        """hgrd_batch_check_ranked with a ranker's model buffer (a torch uint8
+        tensor): (results, stages, info).  Verdicts are exact; an item a
+        restricted check found racy lists the races found there."""
+        if not getattr(self, "_ranked", False):
+            self.rank_prepare()
+        ws = self._ws
+        n = len(self.kernels)
+        v = (ItemVerdict * n)()
+        wc = self.witness_cap
+        w = (Witness * max(1, n * wc))()
+        st = (C.c_uint8 * n)()
+        info = BatchRankInfo()
+        rc = lib().hgrd_batch_check_ranked(self._h, C.c_void_p(model.data_ptr()) if model is not None else None,
+                                           topk, min_score, C.c_void_p(ws.data_ptr()), ws.numel(),
+                                           _stream_ptr(stream), v, w, wc, st, C.byref(info))
+        if rc < 0 and rc != -6:
+            _raise(rc)
+        out = []
+        for i in range(n):
+            x = v[i]
+            out.append(ItemResult(x.status, bool(x.racy), bool(x.small), x.n_witness, tuple(x.n_by_kind),
+                                  x.n_instances, x.n_keys, x.n_oob,
+                                  [_wt(w[i * wc + k]) for k in range(x.n_copied)], _pairs(x.pair_kind)))
+        return out, list(st), {k: getattr(info, k) for k, _ in BatchRankInfo._fields_ if k != "pad"}
+
     def tune(self, stream=None) -> dict:
         ws = self.workspace()
         o = BatchOpts()
@@ -446,8 +495,8 @@ def sort_tune(workspace_bytes: int = 600 << 20, stream=None):
     L.hgrd_sort_tune.restype = C.c_int
     ws = torch.empty(workspace_bytes, dtype=torch.uint8, device="cuda")
     best = C.c_int()
-    ms = (C.c_float * 16)()
-    _raise(L.hgrd_sort_tune(C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), C.byref(best), ms, 16))
+    ms = (C.c_float * 64)()
+    _raise(L.hgrd_sort_tune(C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), C.byref(best), ms, 64))
     n = C.c_int()
     L.hgrd_sort_variant.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     _raise(L.hgrd_sort_variant(-1, None, C.byref(n)))

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <string>
@@ -44,7 +46,7 @@ constexpr int SB_RAW = 1024;    // per-run witnesses of one small item
 constexpr int SB_SLOTS = 64;    // slot file entries per simulated lane
 constexpr int SB_PASSES = 4;    // radix passes (32 sorted bits)
 constexpr int OUT_WORDS = 56;   // n_keys, n_oob, n_witness, kind0..2, flags, n_raw, 48 racy-pair words
-enum { F_RAW_OVERFLOW = 1, F_TIMEOUT = 2, F_CAND_OVERFLOW = 4, F_SHARED_OVERFLOW = 8 };
+enum { F_RAW_OVERFLOW = 1, F_TIMEOUT = 2, F_CAND_OVERFLOW = 4, F_SHARED_OVERFLOW = 8, F_LOCK_RUN = 16 };
 
 struct SmallSmem {
   DProg prog;
@@ -137,7 +139,8 @@ __device__ void cta_sort_pass(SmallSmem& S, const uint64_t* src, uint64_t* dst, 
 __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __restrict__ progs,
                                                                  const uint32_t* __restrict__ order, uint32_t nsmall,
                                                                  unsigned long long* queue, uint64_t* __restrict__ outs,
-                                                                 uint64_t* __restrict__ wits, uint32_t wcap) {
+                                                                 uint64_t* __restrict__ wits, uint32_t wcap,
+                                                                 const uint32_t* __restrict__ masks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& S = *reinterpret_cast<SmallSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -151,6 +154,10 @@ __global__ void __launch_bounds__(SB_THREADS) batch_small_kernel(const DProg* __
       uint4* dst = reinterpret_cast<uint4*>(&S.prog);
       for (int i = threadIdx.x; i < (int)(sizeof(DProg) / 16); i += SB_THREADS) dst[i] = src[i];
     }
+    __syncthreads();
+    // a restricted check: the accesses outside the item's mask are not run
+    if (masks && threadIdx.x < MAXACC && threadIdx.x < S.prog.nacc && !((masks[item] >> threadIdx.x) & 1u))
+      S.prog.acc[threadIdx.x].dead = 1;
     if (threadIdx.x == 0) {
       S.oob = 0;
       S.nraw = 0;
@@ -344,6 +351,7 @@ __global__ void gather_kernel(const uint64_t* __restrict__ cnt, const uint64_t* 
     out[4] = cnt[C_KIND1];
     out[5] = cnt[C_KIND2];
     out[6] = (cnt[C_NRAW] > raw_cap ? F_RAW_OVERFLOW : 0) | ((cnt[C_ERR] & ERR_TIMEOUT) ? F_TIMEOUT : 0) |
+             ((cnt[C_ERR] & ERR_LOCK_RUN) ? F_LOCK_RUN : 0) |
              (cnt[C_NCAND] > cand_cap ? F_CAND_OVERFLOW : 0) | ((cnt[C_ERR] & ERR_SHARED_FULL) ? F_SHARED_OVERFLOW : 0);
     out[7] = cnt[C_NRAW];
   }
@@ -382,6 +390,53 @@ __global__ void small_finish_kernel(const uint64_t* __restrict__ out, const uint
   for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) uniq[i] = wits[i];
 }
 
+// The top-k pairs of every item by the ranker's logits (one warp per item,
+// k rounds of a warp arg-max, ties to the lower pair index: the order of a
+// stable sort by decreasing score), as the mask of their accesses.  An item
+// with at most k eligible pairs checks all of them (its cover); an item
+// whose best logit is below min_score, or without pairs, is not ranked (0).
+__global__ void topk_mask_kernel(const float* __restrict__ logits, const uint32_t* __restrict__ poff,
+                                 const uint32_t* __restrict__ pab, const uint32_t* __restrict__ cover, uint32_t n,
+                                 uint32_t topk, float min_score, uint32_t* __restrict__ mask_out) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = w0; i < n; i += nw) {
+    const uint32_t lo = poff[i], np = poff[i + 1] - lo;
+    uint32_t mask = 0;
+    if (np && np <= topk) {
+      mask = cover[i];
+    } else if (np) {
+      // pairs lane, lane + 32, ...: at most 528 per item, 17 per lane
+      uint32_t taken = 0;
+      for (uint32_t r = 0; r < topk; ++r) {
+        float best = -INFINITY;
+        uint32_t bi = 0xffffffffu;
+        for (uint32_t j = lane, q = 0; j < np; j += 32, ++q) {
+          const float z = logits[lo + j];
+          if (!((taken >> q) & 1u) && (z > best || (z == best && j < bi))) {
+            best = z;
+            bi = j;
+          }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const float zb = __shfl_xor_sync(FULL, best, o);
+          const uint32_t jb = __shfl_xor_sync(FULL, bi, o);
+          if (zb > best || (zb == best && jb < bi)) {
+            best = zb;
+            bi = jb;
+          }
+        }
+        if (r == 0 && !(best >= min_score)) break;  // not ranked
+        if (bi == 0xffffffffu) break;
+        if ((bi & 31u) == (uint32_t)lane) taken |= 1u << (bi >> 5);
+        const uint32_t ab = pab[lo + bi];
+        mask |= (1u << (ab & 31u)) | (1u << ((ab >> 8) & 31u));
+      }
+    }
+    if (lane == 0) mask_out[i] = mask;
+  }
+}
+
 }  // namespace
 
 // a check restricted to the accesses in `only` (0 or all ones: every access)
@@ -404,7 +459,8 @@ cudaError_t launch_small_single(const Launch& L, const DProg* d_prog, uint64_t* 
   uint64_t* out = scratch;
   uint64_t* wits = scratch + 64;
   batch_small_kernel<<<1, SB_THREADS, smem, L.s>>>(d_prog, (const uint32_t*)(counters + C_SMALLQ + 1), 1,
-                                                  (unsigned long long*)(counters + C_SMALLQ), out, wits, SB_RAW);
+                                                  (unsigned long long*)(counters + C_SMALLQ), out, wits, SB_RAW,
+                                                  nullptr);
   small_finish_kernel<<<1, 256, 0, L.s>>>(out, wits, SB_RAW, counters, uniq);
   (*L.launches) += 2;
   return cudaGetLastError();
@@ -431,6 +487,17 @@ struct hgrd_batch {
   void* exec_ws = nullptr;
   cudaStream_t exec_stream = nullptr;
   uint32_t* h_order = nullptr;
+  // ranked form (hgrd_batch_rank_prepare): eligible pairs of every item and
+  // their features, pinned staging for selections and restricted programs
+  bool rank_ready = false;
+  std::vector<uint32_t> pair_off, pair_ab, cover;  // pairs of item i: [pair_off[i], pair_off[i+1])
+  std::vector<float> feat;                          // 96 features per pair
+  std::vector<uint32_t> sel;    // small items of a selective run
+  std::vector<uint32_t> rmask;  // accesses each item checks in a selective run
+  std::vector<DProg> lprog;     // restricted programs of large items
+  const void* feat_ws = nullptr;  // workspace the features were uploaded to
+  size_t off_feat = 0, off_logit = 0, off_poff = 0, off_pab = 0, off_cover = 0, off_dmask = 0, off_rmask = 0,
+         off_mlp = 0, rank_total = 0;
 };
 
 namespace {
@@ -472,12 +539,45 @@ int drop_graph(hgrd_batch* b) {
     if (e_ != cudaSuccess) return fail(HGRD_EDEVICE, std::string("CUDA: ") + cudaGetErrorString(e_)); \
   } while (0)
 
-int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s) {
+// Enqueue the batch.  A selective run (run != nullptr) checks only the items
+// with run[i] set, each on the accesses of masks[i] (all ones: the whole item;
+// fewer: a restricted check, whose races are races of the item): small items
+// through the on-chip kernel with the masks applied there, large ones on
+// restricted copies of their programs.
+int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s, const uint8_t* run = nullptr,
+                  const uint32_t* masks = nullptr) {
   const size_t n = b->items.size();
   hgrd_check_opts io{};
   io.flags = HGRD_NO_PAIR;
   BK(cudaMemcpyAsync(ws + b->off_progs, b->h_progs, n * sizeof(DProg), cudaMemcpyHostToDevice, s));
-  BK(cudaMemcpyAsync(ws + b->off_order, b->h_order, std::max<size_t>(1, b->small.size()) * 4, cudaMemcpyHostToDevice, s));
+  uint32_t nsmall = (uint32_t)b->small.size();
+  const uint32_t* d_masks = nullptr;
+  if (run) {
+    // (pageable host copies: each returns once its source is staged)
+    b->sel.clear();
+    for (uint32_t id : b->small)
+      if (run[id]) b->sel.push_back(id);
+    nsmall = (uint32_t)b->sel.size();
+    if (nsmall)
+      BK(cudaMemcpyAsync(ws + b->off_order, b->sel.data(), (size_t)nsmall * 4, cudaMemcpyHostToDevice, s));
+    b->rmask.assign(masks, masks + n);
+    BK(cudaMemcpyAsync(ws + b->off_rmask, b->rmask.data(), n * 4, cudaMemcpyHostToDevice, s));
+    d_masks = (const uint32_t*)(ws + b->off_rmask);
+    // restricted programs of the large items that run on part of their accesses
+    b->lprog.resize(b->large.size());
+    uint32_t k = 0;
+    for (uint32_t id : b->large) {
+      if (!run[id] || masks[id] == 0xffffffffu) continue;
+      DProg& q = b->lprog[k++];
+      q = b->h_progs[id];
+      for (int a = 0; a < q.nacc; a++)
+        if (!((masks[id] >> a) & 1u)) q.acc[a].dead = 1;
+      BK(cudaMemcpyAsync(ws + b->off_progs + (size_t)id * sizeof(DProg), &q, sizeof(DProg), cudaMemcpyHostToDevice, s));
+    }
+  } else {
+    BK(cudaMemcpyAsync(ws + b->off_order, b->h_order, std::max<size_t>(1, b->small.size()) * 4,
+                       cudaMemcpyHostToDevice, s));
+  }
   BK(cudaMemsetAsync(ws + b->off_queue, 0, 256, s));
   BK(cudaMemsetAsync(ws + b->off_outs, 0, n * OUT_WORDS * 8, s));
   BK(cudaEventRecord(b->fork, s));
@@ -489,19 +589,19 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s) {
   cudaGetDevice(&dev);
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (!b->small.empty()) {
+  if (nsmall) {
     const size_t smem = sizeof(SmallSmem);
     BK(cudaFuncSetAttribute((const void*)batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const uint32_t grid = (uint32_t)std::min<size_t>(b->small.size(), (size_t)nsm);
+    const uint32_t grid = (uint32_t)std::min<size_t>(nsmall, (size_t)nsm);
     batch_small_kernel<<<grid, SB_THREADS, smem, b->streams[0]>>>(dprogs, (const uint32_t*)(ws + b->off_order),
-                                                                  (uint32_t)b->small.size(),
-                                                                  (unsigned long long*)(ws + b->off_queue), outs, wits,
-                                                                  b->wcap);
+                                                                  nsmall, (unsigned long long*)(ws + b->off_queue),
+                                                                  outs, wits, b->wcap, d_masks);
     BK(cudaGetLastError());
     g_stats.kernel_launches++;
   }
   for (size_t k = 0; k < b->large.size(); k++) {
     const uint32_t id = b->large[k];
+    if (run && !run[id]) continue;
     const int j = b->large_stream[k];
     char* reg = ws + b->off_regions + (size_t)(j - 1) * b->region_bytes;
     uint64_t* cnt = nullptr;
@@ -509,7 +609,11 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s) {
     uint64_t raw_cap = 0, cand_cap = 0;
     const uint64_t launches = g_stats.kernel_launches;
     hgrd_stats keep = g_stats;
-    int rc = item_enqueue(b->items[id], &io, reg, b->region_bytes, b->streams[j], dprogs + id, &cnt, &uq, &raw_cap,
+    hgrd_check_opts jo = io;
+    // a restricted program runs on the interpreted kernels (specialised ones
+    // are built for the whole program's structure)
+    if (run && masks[id] != 0xffffffffu) jo.flags |= HGRD_NO_JIT;
+    int rc = item_enqueue(b->items[id], &jo, reg, b->region_bytes, b->streams[j], dprogs + id, &cnt, &uq, &raw_cap,
                           &cand_cap);
     keep.kernel_launches = launches + g_stats.kernel_launches;
     g_stats = keep;
@@ -525,6 +629,55 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s) {
   }
   return HGRD_OK;
 }
+
+// every item's verdict words and kept witnesses, read back in one round trip
+int read_outs(hgrd_batch* b, char* ws, cudaStream_t s, std::vector<uint64_t>* outs, std::vector<uint64_t>* wits) {
+  const size_t n = b->items.size();
+  outs->resize(n * OUT_WORDS);
+  wits->resize((size_t)n * b->wcap);
+  BK(cudaMemcpyAsync(outs->data(), ws + b->off_outs, outs->size() * 8, cudaMemcpyDeviceToHost, s));
+  BK(cudaMemcpyAsync(wits->data(), ws + b->off_wits, wits->size() * 8, cudaMemcpyDeviceToHost, s));
+  BK(cudaStreamSynchronize(s));
+  return HGRD_OK;
+}
+
+// item i's verdict from its words o and witnesses q (into w + i * wcap)
+int decode_item(const hgrd_batch* b, size_t i, const uint64_t* o, const uint64_t* q, hgrd_item_verdict* v,
+                hgrd_witness* w, uint32_t wcap) {
+  const Bound& B = *b->items[i]->bound;
+  hgrd_item_verdict& x = *v;
+  memset(&x, 0, sizeof(x));
+  x.n_instances = B.n_instances;
+  x.n_keys = o[0];
+  x.n_oob = o[1];
+  x.n_witness = o[2];
+  x.n_by_kind[0] = o[3];
+  x.n_by_kind[1] = o[4];
+  x.n_by_kind[2] = o[5];
+  x.racy = o[2] > 0;
+  for (int k = 0; k < 3; k++)
+    for (int a = 0; a < 32; a++) x.pair_kind[k][a] = (uint32_t)(o[8 + k * 16 + a / 2] >> (32 * (a & 1)));
+  x.small = std::find(b->small.begin(), b->small.end(), (uint32_t)i) != b->small.end();
+  x.status = (o[6] & F_TIMEOUT)                                               ? HGRD_ETIMEOUT
+             : (o[6] & F_LOCK_RUN)                                               ? HGRD_EUNSUPPORTED
+             : (o[6] & (F_RAW_OVERFLOW | F_CAND_OVERFLOW | F_SHARED_OVERFLOW)) ? HGRD_ENOMEM
+                                                                                : HGRD_OK;
+  if (x.status) return x.status;
+  const uint32_t nc = (uint32_t)std::min<uint64_t>({(uint64_t)wcap, (uint64_t)b->wcap, o[2]});
+  x.n_copied = nc;
+  for (uint32_t k = 0; k < nc; k++) {
+    hgrd_witness& y = w[i * (size_t)wcap + k];
+    memset(&y, 0, sizeof(y));
+    y.space = (uint8_t)((q[k] >> 58) & 1);
+    y.array = (uint8_t)((q[k] >> 53) & 31);
+    y.acc_lo = (uint8_t)((q[k] >> 8) & 31);
+    y.acc_hi = (uint8_t)((q[k] >> 3) & 31);
+    y.kind_mask = (uint8_t)(q[k] & 7);
+    y.byte_addr = ((q[k] >> 13) & ((1ull << 40) - 1)) * (uint64_t)B.array_granule[y.array];
+  }
+  return HGRD_OK;
+}
+
 
 }  // namespace
 
@@ -635,49 +788,13 @@ int hgrd_batch_collect(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream,
   if (!b || !d_ws || !v) return fail(HGRD_EINVAL, "null argument");
   if (ws_bytes < b->total) return fail(HGRD_ENOMEM, "workspace too small");
   if (wcap && !w) return fail(HGRD_EINVAL, "null witness buffer");
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = b->items.size();
-  std::vector<uint64_t> outs(n * OUT_WORDS), wits((size_t)n * b->wcap);
-  BK(cudaMemcpyAsync(outs.data(), (char*)d_ws + b->off_outs, outs.size() * 8, cudaMemcpyDeviceToHost, s));
-  BK(cudaMemcpyAsync(wits.data(), (char*)d_ws + b->off_wits, wits.size() * 8, cudaMemcpyDeviceToHost, s));
-  BK(cudaStreamSynchronize(s));
+  std::vector<uint64_t> outs, wits;
+  int rc = read_outs(b, (char*)d_ws, (cudaStream_t)stream, &outs, &wits);
+  if (rc) return rc;
   int worst = HGRD_OK;
-  for (size_t i = 0; i < n; i++) {
-    const uint64_t* o = &outs[i * OUT_WORDS];
-    const Bound& B = *b->items[i]->bound;
-    hgrd_item_verdict& x = v[i];
-    memset(&x, 0, sizeof(x));
-    x.n_instances = B.n_instances;
-    x.n_keys = o[0];
-    x.n_oob = o[1];
-    x.n_witness = o[2];
-    x.n_by_kind[0] = o[3];
-    x.n_by_kind[1] = o[4];
-    x.n_by_kind[2] = o[5];
-    x.racy = o[2] > 0;
-    for (int k = 0; k < 3; k++)
-      for (int a = 0; a < 32; a++) x.pair_kind[k][a] = (uint32_t)(o[8 + k * 16 + a / 2] >> (32 * (a & 1)));
-    x.small = std::find(b->small.begin(), b->small.end(), (uint32_t)i) != b->small.end();
-    x.status = (o[6] & F_TIMEOUT)                                               ? HGRD_ETIMEOUT
-               : (o[6] & (F_RAW_OVERFLOW | F_CAND_OVERFLOW | F_SHARED_OVERFLOW)) ? HGRD_ENOMEM
-                                                                                  : HGRD_OK;
-    if (x.status) {
-      worst = x.status;
-      continue;
-    }
-    const uint32_t nc = (uint32_t)std::min<uint64_t>({(uint64_t)wcap, (uint64_t)b->wcap, o[2]});
-    x.n_copied = nc;
-    for (uint32_t k = 0; k < nc; k++) {
-      const uint64_t q = wits[i * b->wcap + k];
-      hgrd_witness& y = w[i * (size_t)wcap + k];
-      memset(&y, 0, sizeof(y));
-      y.space = (uint8_t)((q >> 58) & 1);
-      y.array = (uint8_t)((q >> 53) & 31);
-      y.acc_lo = (uint8_t)((q >> 8) & 31);
-      y.acc_hi = (uint8_t)((q >> 3) & 31);
-      y.kind_mask = (uint8_t)(q & 7);
-      y.byte_addr = ((q >> 13) & ((1ull << 40) - 1)) * (uint64_t)B.array_granule[y.array];
-    }
+  for (size_t i = 0; i < b->items.size(); i++) {
+    const int st = decode_item(b, i, &outs[i * OUT_WORDS], &wits[i * b->wcap], &v[i], w, wcap);
+    if (st) worst = st;
   }
   return worst;
 }
@@ -729,6 +846,151 @@ int hgrd_batch_tune(hgrd_batch* b, void* d_ws, size_t ws_bytes, void* stream, hg
     chosen->streams = best_s;
   }
   return HGRD_OK;
+}
+
+int hgrd_batch_rank_prepare(hgrd_batch* b) {
+  if (!b) return fail(HGRD_EINVAL, "null argument");
+  constexpr uint32_t MAXP = 32 * 33 / 2;
+  const size_t n = b->items.size();
+  b->pair_off.assign(n + 1, 0);
+  b->pair_ab.clear();
+  b->cover.assign(n, 0);
+  b->feat.clear();
+  std::vector<float> f((size_t)MAXP * HGRD_MLP_IN);
+  std::vector<uint8_t> ab(2 * MAXP);
+  for (size_t i = 0; i < n; i++) {
+    uint32_t np = 0;
+    const int rc = hgrd_pair_features(b->items[i], f.data(), ab.data(), MAXP, &np);
+    if (rc < 0) return rc;
+    b->feat.insert(b->feat.end(), f.begin(), f.begin() + (size_t)np * HGRD_MLP_IN);
+    for (uint32_t k = 0; k < np; k++) {
+      b->pair_ab.push_back((uint32_t)ab[2 * k] | ((uint32_t)ab[2 * k + 1] << 8));
+      b->cover[i] |= (1u << ab[2 * k]) | (1u << ab[2 * k + 1]);
+    }
+    b->pair_off[i + 1] = b->pair_off[i] + np;
+  }
+  const size_t np = b->pair_off[n];
+  size_t off = align256(b->total);
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  b->off_feat = take(np * HGRD_MLP_IN * 4);
+  b->off_logit = take(np * 4);
+  b->off_poff = take((n + 1) * 4);
+  b->off_pab = take(np * 4);
+  b->off_cover = take(n * 4);
+  b->off_dmask = take(n * 4);
+  b->off_rmask = take(n * 4);
+  b->off_mlp = take(hgrd_mlp_workspace_bytes((uint32_t)std::max<size_t>(np, 1)));
+  b->rank_total = off;
+  b->rank_ready = true;
+  b->feat_ws = nullptr;
+  return HGRD_OK;
+}
+
+int hgrd_batch_ranked_workspace_size(const hgrd_batch* b, size_t* bytes) {
+  if (!b || !bytes) return fail(HGRD_EINVAL, "null argument");
+  if (!b->rank_ready) return fail(HGRD_EINVAL, "call hgrd_batch_rank_prepare first");
+  *bytes = b->rank_total;
+  return HGRD_OK;
+}
+
+int hgrd_batch_check_ranked(hgrd_batch* b, const void* d_model, uint32_t topk, float min_score, void* d_ws,
+                            size_t ws_bytes, void* stream, hgrd_item_verdict* v, hgrd_witness* w, uint32_t wcap,
+                            uint8_t* stage, hgrd_batch_rank_info* info) {
+  if (!b || !d_ws || !v) return fail(HGRD_EINVAL, "null argument");
+  if (!b->rank_ready) return fail(HGRD_EINVAL, "call hgrd_batch_rank_prepare first");
+  if (((uintptr_t)d_ws & 255) != 0) return fail(HGRD_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < b->rank_total) return fail(HGRD_ENOMEM, "workspace too small: need " + std::to_string(b->rank_total));
+  if (wcap && !w) return fail(HGRD_EINVAL, "null witness buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)d_ws;
+  const size_t n = b->items.size();
+  const uint32_t np = b->pair_off[n];
+  hgrd_batch_rank_info inf{};
+  inf.n_pairs = np;
+  g_stats = hgrd_stats{};
+  auto t0 = std::chrono::steady_clock::now();
+  // 1. the features are static per binding: uploaded once per workspace
+  if (b->feat_ws != d_ws) {
+    BK(cudaMemcpyAsync(ws + b->off_feat, b->feat.data(), b->feat.size() * 4, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(ws + b->off_poff, b->pair_off.data(), (n + 1) * 4, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(ws + b->off_pab, b->pair_ab.data(), (size_t)np * 4, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(ws + b->off_cover, b->cover.data(), n * 4, cudaMemcpyHostToDevice, s));
+    b->feat_ws = d_ws;
+  }
+  // 2. one inference over every eligible pair of every item, then the
+  // top-k access masks on the device
+  std::vector<uint32_t> dmask(n, 0);
+  if (np && d_model && topk) {
+    int rc = hgrd_mlp_predict(d_model, (const float*)(ws + b->off_feat), np, (float*)(ws + b->off_logit),
+                              ws + b->off_mlp, hgrd_mlp_workspace_bytes(np), s);
+    if (rc) return rc;
+    const uint32_t grid = (uint32_t)std::min<size_t>((n + 7) / 8, 4096);
+    topk_mask_kernel<<<grid, 256, 0, s>>>((const float*)(ws + b->off_logit), (const uint32_t*)(ws + b->off_poff),
+                                          (const uint32_t*)(ws + b->off_pab), (const uint32_t*)(ws + b->off_cover),
+                                          (uint32_t)n, topk, min_score, (uint32_t*)(ws + b->off_dmask));
+    BK(cudaGetLastError());
+    g_stats.kernel_launches += 5;
+    BK(cudaMemcpyAsync(dmask.data(), ws + b->off_dmask, n * 4, cudaMemcpyDeviceToHost, s));
+    BK(cudaStreamSynchronize(s));
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  // 3. stage one: every item, large ranked items restricted to the accesses of
+  // their top pairs (small items are whole checks on chip already)
+  std::vector<uint8_t> is_small(n, 0), run(n, 1), done(n, 1);
+  for (uint32_t id : b->small) is_small[id] = 1;
+  std::vector<uint32_t> masks(n, 0xffffffffu);
+  for (size_t i = 0; i < n; i++)
+    if (!is_small[i] && dmask[i]) {
+      masks[i] = dmask[i];
+      inf.ranked++;
+    }
+  int rc = enqueue_batch(b, ws, s, run.data(), masks.data());
+  if (rc) return rc;
+  std::vector<uint64_t> outs, wits;
+  rc = read_outs(b, ws, s, &outs, &wits);
+  if (rc) return rc;
+  int worst = HGRD_OK;
+  for (size_t i = 0; i < n; i++) {
+    const uint64_t* o = &outs[i * OUT_WORDS];
+    const bool racy = o[2] > 0;
+    if (masks[i] != 0xffffffffu && !racy && masks[i] != b->cover[i]) {
+      done[i] = 0;  // clean on part of its accesses: the whole check decides
+      continue;
+    }
+    if (masks[i] != 0xffffffffu) inf.confirmed += racy;
+    if (stage) stage[i] = masks[i] == 0xffffffffu ? 0 : (racy ? 1 : 3);
+    const int st = decode_item(b, i, o, &wits[i * b->wcap], &v[i], w, wcap);
+    if (st) worst = st;
+  }
+  auto t2 = std::chrono::steady_clock::now();
+  // 4. stage two: the whole check of the items stage one left open
+  for (size_t i = 0; i < n; i++) {
+    run[i] = !done[i];
+    masks[i] = 0xffffffffu;
+    inf.second += run[i];
+  }
+  if (inf.second) {
+    rc = enqueue_batch(b, ws, s, run.data(), masks.data());
+    if (rc) return rc;
+    rc = read_outs(b, ws, s, &outs, &wits);
+    if (rc) return rc;
+    for (size_t i = 0; i < n; i++) {
+      if (!run[i]) continue;
+      if (stage) stage[i] = 2;
+      const int st = decode_item(b, i, &outs[i * OUT_WORDS], &wits[i * b->wcap], &v[i], w, wcap);
+      if (st) worst = st;
+    }
+  }
+  auto t3 = std::chrono::steady_clock::now();
+  inf.ms_score = std::chrono::duration<float, std::milli>(t1 - t0).count();
+  inf.ms_stage1 = std::chrono::duration<float, std::milli>(t2 - t1).count();
+  inf.ms_stage2 = std::chrono::duration<float, std::milli>(t3 - t2).count();
+  if (info) *info = inf;
+  return worst;
 }
 
 void hgrd_batch_free(hgrd_batch* b) {

@@ -232,3 +232,30 @@ def test_ranked_verdicts_on_all_heldout_kernels(trained):
         assert res.racy == row["racy"], row["item"]
         stage1 += info["stage"] == 1
     assert stage1 > 0
+
+
+def test_ranked_batch_on_all_heldout_kernels(trained):
+    # the batched ranked form: one inference over every pair of the 2,000
+    # held-out kernels, restricted checks of the ranked large items, whole
+    # checks of what they leave open; every verdict equals the oracle's and
+    # every reported race is one of the oracle's
+    from test_gpu_configs import heldout_verdicts
+    r, _ = trained
+    rows = heldout_verdicts()
+    ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+          for w in (workloads.config4(row["item"], hi_exp=6.0) for row in rows)]
+    b = hg.Batch(ks, witness_cap=16)
+    res, stages, info = b.check_ranked(r.model, topk=4, min_score=0.0)
+    reruns = 0
+    for row, k, x, st in zip(rows, ks, res, stages):
+        if x.status == -6:
+            x = k.check(cap=16, flags=hg.NO_PAIR)
+            reruns += 1
+        assert x.racy == row["racy"], row["item"]
+        full = {tuple(int(v) for v in p.split(",")): m for p, m in row["pairs"].items()}
+        for pair, m in x.pairs.items():
+            assert pair in full and (m & ~full[pair]) == 0, row["item"]
+        if st in (0, 2):  # a whole check: the whole verdict
+            assert x.n_witness == row["n_witness"] and x.pairs == full
+    assert info["n_pairs"] > 1000 and info["ranked"] > 0 and info["confirmed"] > 0
+    assert reruns < 100
