@@ -755,6 +755,9 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     return collect(d, &o2, d_ws, ws_bytes, s, host_out, cap, v, want_pair, pair_enqueued);
   }
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
+  if (cnt[C_ERR] & ERR_LOCK_RUN)
+    return fail(HGRD_EUNSUPPORTED, "acquire-release guards with varying elements on a location with more than " +
+                                       std::to_string(LOCK_RUN_MAX) + " keys");
   g_stats.n_candidates = cnt[C_NCAND];
   {
     const uint32_t fl = o ? o->flags : 0u;
@@ -870,6 +873,22 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
           else if (ivx != ivy) kind = 0;
           else if (x.thr / 32 != y.thr / 32) kind = 2;
           else kind = x.iv == y.iv ? 4 : 0;  // same warp: ordered by a warp barrier unless one interval
+          if ((kind & allow) && ((HP.lockpair[lo] >> hi) & 1u)) {
+            // guards decided per instance: ordered when both hold one element
+            // and the narrower scope covers the kind (device across blocks)
+            const uint64_t gran = v->min_w.byte_addr / (uint64_t)B.array_granule[v->min_w.array];
+            auto elem = [&](int a, const Inst& s2) -> int64_t {
+              const DLock& Lk = HP.lock[a];
+              if (Lk.form == LOCK_OWN) return (int64_t)(gran / (uint64_t)HP.acc[a].G);
+              const int64_t t = s2.thr, b = s2.blk;
+              const int64_t tx = t % HP.block[0], ty = (t / HP.block[0]) % HP.block[1], tz = t / (HP.block[0] * HP.block[1]);
+              const int64_t bx = b % HP.grid[0], by = (b / HP.grid[0]) % HP.grid[1], bz = b / (HP.grid[0] * HP.grid[1]);
+              return Lk.c0 + Lk.c[0] * tx + Lk.c[1] * ty + Lk.c[2] * tz + Lk.c[3] * bx + Lk.c[4] * by + Lk.c[5] * bz;
+            };
+            if (HP.lock[lo].arr == HP.lock[hi].arr && elem(lo, x) == elem(hi, y) &&
+                (kind != 1 || std::min(HP.lock[lo].scope, HP.lock[hi].scope) == 1))
+              kind = 0;
+          }
           if (kind & allow) {
             auto put = [](hgrd_inst& o2, const Inst& s2) {
               o2.lin_block = s2.blk;
@@ -1042,6 +1061,9 @@ extern "C" int hgrd_check_noalloc(const hgrd_desc* d, const hgrd_check_opts* o, 
   CK(cudaMemcpyAsync(cnt, ws + W.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (cnt[C_ERR] & ERR_TIMEOUT) return fail(HGRD_ETIMEOUT, "a bounded device wait (sort look-back) gave up");
+  if (cnt[C_ERR] & ERR_LOCK_RUN)
+    return fail(HGRD_EUNSUPPORTED, "acquire-release guards with varying elements on a location with more than " +
+                                       std::to_string(LOCK_RUN_MAX) + " keys");
   if (cnt[C_ERR] & ERR_SHARED_FULL)
     return fail(HGRD_ENOMEM, "room for keys of candidate shared-memory bins too small: need " +
                                  std::to_string(cnt[C_NSC]) + " (hgrd_check_opts.max_shared_keys)");

@@ -575,6 +575,237 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
   if (threadIdx.x == 0) *done = 1;
 }
 
+// Onesweep pass with early counts (the shapes the tuner prefers on B300).
+// Per tile: keys to registers, then each warp's digit histogram with shared
+// atomics; the tile's digit counts are published at once (before any key is
+// ranked) and the first window of the look-back is loaded, so predecessors
+// and successors rarely wait on each other; the tile-local start of every
+// (warp, digit) follows from one scan.  The stable ranking then walks the
+// warp's keys slot by slot in memory order (RANK 3: each lane sets its bit in
+// a per-(warp, digit) mask with a shared atomic OR and reads back its peers;
+// RANK 0: the match instruction; RANK 5: per warp, the match instruction when
+// the warp's keys hold at most 16 distinct digits, counted while its
+// histogram is built, else the atomic OR) and stores every key straight to
+// its place in the shared staging tile.  The look-back finishes, and the keys
+// leave in digit runs.  With the cell filter, keys of unkept cells take no
+// part.  At the start of a tile the tile one grid ahead (the one this CTA will
+// likely take next) is prefetched into L2.
+template <int T, int KPT, int MINB, int RANK>
+__global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                           const uint64_t* n_dev, uint64_t n_max, int shift,
+                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
+                                                           unsigned long long* ticket, uint32_t epoch, uint64_t* err,
+                                                           uint64_t* next_hist, int next_shift,
+                                                           const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh,
+                                                           const uint64_t* skip) {
+  static_assert(T >= RS_RADIX && KPT <= 32, "one thread per digit; live keys fit a 32-bit mask");
+  if (skip && *skip) return;  // one CTA already sorted the remaining digits
+  constexpr int W = T / 32, TILE = T * KPT, LBW = 4;
+  extern __shared__ __align__(16) unsigned char osm[];
+  uint64_t* stage = reinterpret_cast<uint64_t*>(osm);            // TILE keys in digit order
+  int64_t* gdst = reinterpret_cast<int64_t*>(stage + TILE);      // per digit: output index - tile start
+  uint32_t* whist = reinterpret_cast<uint32_t*>(gdst + RS_RADIX);  // [W][256] counts, then starts
+  uint32_t* wmask = whist + W * RS_RADIX;                         // [W][256] peer masks (RANK 3, 5)
+  uint32_t* dstart = wmask + (RANK != 0 ? W * RS_RADIX : 0);      // tile-local start of each digit
+  uint32_t* nhist = dstart + RS_RADIX;                            // digit counts of the next pass
+  uint32_t* wsum = nhist + RS_RADIX;                              // 8 warp totals + tile total
+  uint32_t* s_tile = wsum + 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+  const uint64_t n = dev_n(n_dev, n_max);
+  const uint64_t ntiles = (n + TILE - 1) / TILE;
+  if ((uint64_t)blockIdx.x >= ntiles) return;
+  const uint64_t ep = (uint64_t)epoch << 56;
+  for (int d = t; d < RS_RADIX; d += T) nhist[d] = 0;
+  if (RANK != 0)
+    for (int i = t; i < W * RS_RADIX; i += T) wmask[i] = 0;
+  const unsigned lt = lanemask_lt();
+  uint32_t* wh = whist + warp * RS_RADIX;
+  uint32_t* wm = wmask + warp * RS_RADIX;
+  for (;;) {
+    if (t == 0) {
+      const unsigned long long tk = atomicAdd(ticket, 1ull);
+      s_tile[0] = (uint32_t)tk;
+      s_tile[1] = (uint32_t)(tk >> 32);
+    }
+    for (int i = t; i < W * RS_RADIX; i += T) whist[i] = 0;
+    __syncthreads();
+    const uint64_t tile = (uint64_t)s_tile[0] | ((uint64_t)s_tile[1] << 32);
+    if (tile >= ntiles) break;
+    const uint64_t base = tile * TILE;
+    const bool full = base + TILE <= n;
+    const uint32_t rem = full ? TILE : (uint32_t)(n - base);
+    if (t == 0) {  // the tile one grid ahead, into L2 (a hint: 16-byte multiples inside the input)
+      const uint64_t nt = tile + gridDim.x;
+      if (nt < ntiles) {
+        const uint64_t nb = nt * TILE;
+        const uint32_t bytes = (uint32_t)(((nb + TILE <= n ? (uint64_t)TILE : n - nb) * 8) & ~15ull);
+        if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + nb), "r"(bytes) : "memory");
+      }
+    }
+    const uint64_t* src = in + base + warp * (KPT * 32) + lane;
+    uint64_t k[KPT];
+    if (full) {
+#pragma unroll
+      for (int s = 0; s < KPT; ++s) k[s] = __ldcs(src + s * 32);
+    } else {
+#pragma unroll
+      for (int s = 0; s < KPT; ++s) {
+        const uint32_t i = warp * (KPT * 32) + s * 32 + lane;
+        k[s] = i < rem ? src[s * 32] : 0;
+      }
+    }
+    // live keys (in range, and of a kept cell when the filter runs); the
+    // warp's digit histogram (RANK 5 also counts the warp's distinct digits:
+    // a lane whose add finds zero opened one)
+    uint32_t live = 0, distinct = 0;
+#pragma unroll
+    for (int s = 0; s < KPT; ++s) {
+      const uint32_t i = warp * (KPT * 32) + s * 32 + lane;
+      const bool l = i < rem && (!ctab || cell_kept(ctab, ncells, shr64(k[s], rsh)));
+      live |= (uint32_t)l << s;
+      if (RANK == 5) {
+        uint32_t old = 1;
+        if (l) old = atomicAdd(&wh[(uint32_t)(k[s] >> shift) & 255u], 1u);
+        distinct += __popc(__ballot_sync(FULL, old == 0));
+      } else if (l) {
+        atomicAdd(&wh[(uint32_t)(k[s] >> shift) & 255u], 1u);
+      }
+    }
+    const bool use_match = RANK == 0 || (RANK == 5 && distinct <= 16);
+    __syncthreads();
+    // per digit: the tile's count, published at once, and each warp's
+    // exclusive prefix; the first window of predecessors is loaded now and
+    // read after the ranking
+    uint32_t dsum = 0;
+    uint64_t wv[LBW];
+    const uint64_t p0 = tile - 1;
+    const int m0 = tile == 0 ? 0 : (p0 >= (uint64_t)(LBW - 1) ? LBW : (int)p0 + 1);
+    if (t < RS_RADIX) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = whist[w * RS_RADIX + t];
+        whist[w * RS_RADIX + t] = dsum;
+        dsum += c;
+      }
+      st_relaxed(status + tile * RS_RADIX + t, ep | (tile == 0 ? ST_PREFIX : ST_AGG) | dsum);
+#pragma unroll
+      for (int j = 0; j < LBW; ++j)
+        if (j < m0) wv[j] = ld_relaxed(status + (p0 - (uint64_t)j) * RS_RADIX + t);
+      // tile-local digit starts: scan of the counts, warps of 32 digits
+      uint32_t x = dsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      dstart[t] = x - dsum;
+    }
+    __syncthreads();
+    if (t < RS_RADIX) {
+      uint32_t add = 0;
+#pragma unroll
+      for (int w = 0; w < RS_RADIX / 32; ++w) add += (w < (t >> 5)) ? wsum[w] : 0u;
+      const uint32_t ds = dstart[t] + add;
+      dstart[t] = ds;
+#pragma unroll
+      for (int w = 0; w < W; ++w) whist[w * RS_RADIX + t] += ds;
+    }
+    __syncthreads();
+    // stable ranking in memory order (slot after slot, lanes in order);
+    // every key goes straight to its place in the staging tile
+#pragma unroll
+    for (int s = 0; s < KPT; ++s) {
+      const bool l = (live >> s) & 1u;
+      const uint32_t d = (uint32_t)(k[s] >> shift) & 255u;
+      unsigned peers;
+      if (!use_match) {
+        if (l) atomicOr(&wm[d], 1u << lane);
+        __syncwarp();
+        peers = l ? wm[d] : 0u;
+      } else {
+        peers = __match_any_sync(FULL, l ? d : 256u + lane);
+      }
+      const uint32_t old = l ? wh[d] : 0u;
+      if (l) stage[old + __popc(peers & lt)] = k[s];
+      __syncwarp();
+      if (l && lane == 31 - __clz(peers)) {
+        wh[d] = old + __popc(peers);
+        if (!use_match) wm[d] = 0u;
+      }
+      __syncwarp();
+    }
+    // the look-back: the keys of the tiles before this one with each digit
+    if (t < RS_RADIX) {
+      uint64_t excl = 0;
+      if (tile != 0) {
+        uint64_t p = p0;
+        int m = m0;
+        uint32_t spins = 0;
+        for (;;) {
+          bool done = false, stall = false;
+          uint64_t used = 0;
+#pragma unroll
+          for (int j = 0; j < LBW; ++j) {
+            if (j >= m || done || stall) continue;
+            const bool ready = (wv[j] >> 56) == epoch && (wv[j] & (3ull << 54)) != 0;
+            if (!ready) {
+              stall = true;
+              continue;
+            }
+            excl += wv[j] & ST_VAL;
+            if ((wv[j] & ST_PREFIX) || p == (uint64_t)j) done = true;
+            else ++used;
+          }
+          if (done) break;
+          p -= used;
+          if (stall) {
+            if (++spins > SPIN_LIMIT) {
+              atomicOr((unsigned long long*)err, (unsigned long long)ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+          m = p >= (uint64_t)(LBW - 1) ? LBW : (int)p + 1;
+#pragma unroll
+          for (int j = 0; j < LBW; ++j)
+            if (j < m) wv[j] = ld_relaxed(status + (p - (uint64_t)j) * RS_RADIX + t);
+        }
+        st_relaxed(status + tile * RS_RADIX + t, ep | ST_PREFIX | (excl + dsum));
+      }
+      gdst[t] = (int64_t)(gbase[t] + excl) - (int64_t)dstart[t];
+      if (t == RS_RADIX - 1) wsum[8] = dstart[t] + dsum;  // keys kept in this tile
+    }
+    __syncthreads();
+    // out in digit runs (consecutive keys of a digit go to consecutive places)
+    if (full && !ctab) {
+#pragma unroll 4
+      for (int j = 0; j < KPT; ++j) {
+        const uint32_t i = j * T + t;
+        const uint64_t key = stage[i];
+        __stcs(out + (gdst[(uint32_t)(key >> shift) & 255u] + i), key);
+        if (next_hist) atomicAdd(&nhist[(uint32_t)(key >> next_shift) & 255u], 1u);
+      }
+    } else {
+      const uint32_t kept = wsum[8];
+      for (uint32_t i = t; i < kept; i += T) {
+        const uint64_t key = stage[i];
+        out[gdst[(uint32_t)(key >> shift) & 255u] + i] = key;
+        if (next_hist) atomicAdd(&nhist[(uint32_t)(key >> next_shift) & 255u], 1u);
+      }
+    }
+    __syncthreads();
+  }
+  for (int d = t; d < RS_RADIX; d += T)
+    if (next_hist && nhist[d]) atomicAdd((unsigned long long*)&next_hist[d], (unsigned long long)nhist[d]);
+}
+
+template <int T, int KPT, int RANK>
+constexpr size_t onesweep3_smem() {
+  return (size_t)T * KPT * 8 + RS_RADIX * 8 + (size_t)(T / 32) * RS_RADIX * 4 * (RANK != 0 ? 2 : 1) +
+         2 * RS_RADIX * 4 + 16 * 4 + 16;
+}
+
 template <int T, int KPT>
 constexpr size_t onesweep_smem() {
   return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16;  // + ticket, kept
@@ -777,16 +1008,25 @@ __global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* 
     c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
     c.glob = X.g_all || c.prev < X.g_lim;
     bool done = false;
+    // two groups of CA_AHEAD steps in flight: the next group's loads are
+    // issued before the current group is scanned
+    uint64_t kk[CA_AHEAD], nx[CA_AHEAD];
+#pragma unroll
+    for (int j = 0; j < CA_AHEAD; ++j) {
+      const uint64_t i = X.r0 + 32 * j + X.lane;
+      kk[j] = i < n ? __ldcs(keys + i) : 0;
+    }
     for (uint64_t p = X.r0; !done && p < n; p += 32 * CA_AHEAD) {
-      uint64_t kk[CA_AHEAD];
 #pragma unroll
       for (int j = 0; j < CA_AHEAD; ++j) {
-        const uint64_t i = p + 32 * j + X.lane;
-        kk[j] = i < n ? keys[i] : 0;
+        const uint64_t i = p + 32 * (CA_AHEAD + j) + X.lane;
+        nx[j] = i < n ? __ldcs(keys + i) : 0;
       }
 #pragma unroll
       for (int j = 0; j < CA_AHEAD; ++j)
         if (!done && p + 32 * j < n) done = cand_step(X, c, kk[j], p + 32 * j);
+#pragma unroll
+      for (int j = 0; j < CA_AHEAD; ++j) kk[j] = nx[j];
     }
     if (!done && c.owned) {  // the array ended inside a run of this warp
       const bool last = c.runC || (c.subW && c.subTD) || ((X.g_all || c.prev < X.g_lim) && c.runW && c.runBD);
@@ -895,6 +1135,7 @@ __global__ void __launch_bounds__(256) exact_kernel(const uint64_t* __restrict__
     const RunMasks R = (c0 & SHARED_ENTRY)
                            ? exact_bin(keys, nsb + (c0 & ~SHARED_ENTRY), nsb + c1, P, lane, eintra, T)
                            : exact_run(keys, c0, c1, n, P, lane, einter, eintra, stop_first != 0);
+    if (R.lock_overflow && lane == 0) atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_LOCK_RUN);
     record_pairs(counters + C_PAIRS, R, lane);
     uint32_t row = witness_row(R, lane);
     const uint32_t cntw = (uint32_t)__popc(row);
@@ -1270,6 +1511,11 @@ const SortVariant* sort_variants(int* count) {
       {(const void*)onesweep_kernel<512, 8, 2, true, 1>, 512, 8, onesweep_smem<512, 8>()},
       {(const void*)onesweep_kernel<256, 16, 3, true, 2>, 256, 16, onesweep_smem<256, 16>()},
       {(const void*)onesweep_kernel<512, 8, 2, true, 2>, 512, 8, onesweep_smem<512, 8>()},
+      {(const void*)onesweep3_kernel<256, 28, 2, 3>, 256, 28, onesweep3_smem<256, 28, 3>()},
+      {(const void*)onesweep3_kernel<256, 32, 2, 3>, 256, 32, onesweep3_smem<256, 32, 3>()},
+      {(const void*)onesweep3_kernel<256, 28, 2, 5>, 256, 28, onesweep3_smem<256, 28, 5>()},
+      {(const void*)onesweep3_kernel<256, 32, 2, 5>, 256, 32, onesweep3_smem<256, 32, 5>()},
+      {(const void*)onesweep3_kernel<256, 32, 2, 0>, 256, 32, onesweep3_smem<256, 32, 0>()},
   };
   *count = (int)(sizeof(v) / sizeof(v[0]));
   return v;
