@@ -755,6 +755,34 @@ def main():
                     "peak_kind": "derived: 148 SMs x 128 int32 lanes x max SM clock", "traffic": traffic,
                     "ops_per_launch": ops, "instances_per_launch": n_inst}
 
+    # ---- end to end through the public synchronous call
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_e2e = []
+    # warm-up of the synchronous path: first use of its kernels, and clocks
+    # back at steady state after the idle gap that ends the sampled region
+    # (measured: about a second of calls; at least W calls and 1 s)
+    t_w = time.perf_counter()
+    n_w = 0
+    while n_w < max(3, args.warmup) or time.perf_counter() - t_w < 1.0:
+        k.check(cap=1 << 16, stream=s, flags=G)
+        n_w += 1
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush_l2()
+        s.synchronize()
+        t0 = time.perf_counter()
+        r = k.check(cap=1 << 16, stream=s, flags=G)
+        t_e2e.append(time.perf_counter() - t0)
+    st = hg.stats()
+    e2e_s = sum(t_e2e)
+    e2e_s = max_over_ranks(e2e_s, dist)
+    e2e = {"value": job_throughput(world, n_inst, args.steps, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": int(st["h2d_bytes"]), "d2h_bytes_per_step": int(st["d2h_bytes"]),
+           "ms_per_step": 1000 * e2e_s / args.steps}
+    assert r.witnesses == res.witnesses
+
     # ---- the sort and the scan at the check's own key scale: the same check
     # with every live key written, sorted and scanned (HGRD_ALL_KEYS: no key
     # dropped by the pair rule, one global sort, no cell filter), per-stage
@@ -791,34 +819,6 @@ def main():
             "scan": roof("candidates", 8 * ns, "8 B read per sorted key"),
             "expand_write": roof("expand_write", 8 * ns, "8 B written per key"),
             "check_ms": sum(fms.values())}
-
-    # ---- end to end through the public synchronous call
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t_e2e = []
-    # warm-up of the synchronous path: first use of its kernels, and clocks
-    # back at steady state after the idle gap that ends the sampled region
-    # (measured: about a second of calls; at least W calls and 1 s)
-    t_w = time.perf_counter()
-    n_w = 0
-    while n_w < max(3, args.warmup) or time.perf_counter() - t_w < 1.0:
-        k.check(cap=1 << 16, stream=s, flags=G)
-        n_w += 1
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush_l2()
-        s.synchronize()
-        t0 = time.perf_counter()
-        r = k.check(cap=1 << 16, stream=s, flags=G)
-        t_e2e.append(time.perf_counter() - t0)
-    st = hg.stats()
-    e2e_s = sum(t_e2e)
-    e2e_s = max_over_ranks(e2e_s, dist)
-    e2e = {"value": job_throughput(world, n_inst, args.steps, e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": int(st["h2d_bytes"]), "d2h_bytes_per_step": int(st["d2h_bytes"]),
-           "ms_per_step": 1000 * e2e_s / args.steps}
-    assert r.witnesses == res.witnesses
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -236,11 +236,14 @@ int hgrd_check_enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws,
 int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* cuda_stream,
                        hgrd_witness* host_out, uint64_t cap, hgrd_verdict* v);
 
-/* Radix-sort autotuner.  The onesweep pass comes in several CTA shapes
- * (threads x keys per thread: 256x16, 256x12, 512x8, 384x12, 256x24, 128x16);
- * hgrd_sort_tune times one pass of each on up to 2^25 random keys in the
- * given device workspace (about 17.4 bytes per key), keeps the fastest for
- * the current device and writes per-shape times (ms) to ms[0 .. cap).
+/* Radix-sort autotuner.  The onesweep pass comes in several shapes: the
+ * early-count kernels (shapes 0-6: 256 threads x 32 or 28 keys, 384 x 16;
+ * warp ranking by shared atomic-OR peer masks, the match instruction, or per
+ * warp by its digit diversity; shape 0 is the default) and the earlier ones
+ * (shapes 7-19: 256x16, 256x12, 512x8, 384x12, 256x24, 128x16 with several
+ * rankings).  hgrd_sort_tune times one pass of each on up to 2^25 random keys
+ * in the given device workspace (about 17.4 bytes per key), keeps the fastest
+ * for the current device and writes per-shape times (ms) to ms[0 .. cap).
  * hgrd_sort_variant selects a shape (set >= 0) or queries it (set < 0). */
 int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* cuda_stream, int* best, float* ms, int cap);
 int hgrd_sort_variant(int set, int* current, int* count);

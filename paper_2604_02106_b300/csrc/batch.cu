@@ -557,6 +557,10 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s, const uint8_t* run = 
     b->sel.clear();
     for (uint32_t id : b->small)
       if (run[id]) b->sel.push_back(id);
+    // a large item restricted to few enough keys runs whole on chip too
+    for (uint32_t id : b->large)
+      if (run[id] && masks[id] != 0xffffffffu && small_single_ok(*b->items[id]->bound, masks[id]))
+        b->sel.push_back(id);
     nsmall = (uint32_t)b->sel.size();
     if (nsmall)
       BK(cudaMemcpyAsync(ws + b->off_order, b->sel.data(), (size_t)nsmall * 4, cudaMemcpyHostToDevice, s));
@@ -567,7 +571,7 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s, const uint8_t* run = 
     b->lprog.resize(b->large.size());
     uint32_t k = 0;
     for (uint32_t id : b->large) {
-      if (!run[id] || masks[id] == 0xffffffffu) continue;
+      if (!run[id] || masks[id] == 0xffffffffu || small_single_ok(*b->items[id]->bound, masks[id])) continue;
       DProg& q = b->lprog[k++];
       q = b->h_progs[id];
       for (int a = 0; a < q.nacc; a++)
@@ -601,7 +605,8 @@ int enqueue_batch(hgrd_batch* b, char* ws, cudaStream_t s, const uint8_t* run = 
   }
   for (size_t k = 0; k < b->large.size(); k++) {
     const uint32_t id = b->large[k];
-    if (run && !run[id]) continue;
+    if (run && (!run[id] || (masks[id] != 0xffffffffu && small_single_ok(*b->items[id]->bound, masks[id]))))
+      continue;  // not in this run, or restricted to the on-chip kernel
     const int j = b->large_stream[k];
     char* reg = ws + b->off_regions + (size_t)(j - 1) * b->region_bytes;
     uint64_t* cnt = nullptr;

@@ -338,19 +338,22 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
         ws[9] = base;
       }
       __syncthreads();
-      if (ws[9] != NO_ROW)
-        for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+      // the block's bin-table row, and every bin reset for the next block in
+      // the same walk (a thread resets the bins it reads; the writer bits,
+      // shared by 32 bins, after a barrier)
+      const bool row = ws[9] != NO_ROW;
+      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
+        if (row) {
           const uint32_t c = s_cnt[i];
           const bool cand = ((s_wb[i >> 5] >> (i & 31)) & 1u) && s_mn[i] < s_mx[i];
           stbl[(uint64_t)b * NB + i] = cand ? ((start << 32) | c) : 0ull;
           if (cand) start += c;
         }
-      __syncthreads();
-      for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {
         s_cnt[i] = 0;
         s_mn[i] = NONE;
         s_mx[i] = 0;
       }
+      __syncthreads();
       for (int i = threadIdx.x; i < NW; i += EXP_THREADS) s_wb[i] = 0;
       __syncthreads();
     }

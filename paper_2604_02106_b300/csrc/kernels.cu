@@ -584,8 +584,8 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
 // warp's keys slot by slot in memory order (RANK 3: each lane sets its bit in
 // a per-(warp, digit) mask with a shared atomic OR and reads back its peers;
 // RANK 0: the match instruction; RANK 5: per warp, the match instruction when
-// the warp's keys hold at most 16 distinct digits, counted while its
-// histogram is built, else the atomic OR) and stores every key straight to
+// the warp's keys hold at most 16 distinct digits, counted from its histogram
+// by the digit threads, else the atomic OR) and stores every key straight to
 // its place in the shared staging tile.  The look-back finishes, and the keys
 // leave in digit runs.  With the cell filter, keys of unkept cells take no
 // part.  At the start of a tile the tile one grid ahead (the one this CTA will
@@ -610,6 +610,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
   uint32_t* nhist = dstart + RS_RADIX;                            // digit counts of the next pass
   uint32_t* wsum = nhist + RS_RADIX;                              // 8 warp totals + tile total
   uint32_t* s_tile = wsum + 16;
+  uint32_t* wdist = s_tile + 2;                                   // [W] distinct digits of each warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + TILE - 1) / TILE;
@@ -628,6 +629,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
       s_tile[1] = (uint32_t)(tk >> 32);
     }
     for (int i = t; i < W * RS_RADIX; i += T) whist[i] = 0;
+    if (RANK == 5 && t < W) wdist[t] = 0;
     __syncthreads();
     const uint64_t tile = (uint64_t)s_tile[0] | ((uint64_t)s_tile[1] << 32);
     if (tile >= ntiles) break;
@@ -655,23 +657,15 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
       }
     }
     // live keys (in range, and of a kept cell when the filter runs); the
-    // warp's digit histogram (RANK 5 also counts the warp's distinct digits:
-    // a lane whose add finds zero opened one)
-    uint32_t live = 0, distinct = 0;
+    // warp's digit histogram
+    uint32_t live = 0;
 #pragma unroll
     for (int s = 0; s < KPT; ++s) {
       const uint32_t i = warp * (KPT * 32) + s * 32 + lane;
       const bool l = i < rem && (!ctab || cell_kept(ctab, ncells, shr64(k[s], rsh)));
       live |= (uint32_t)l << s;
-      if (RANK == 5) {
-        uint32_t old = 1;
-        if (l) old = atomicAdd(&wh[(uint32_t)(k[s] >> shift) & 255u], 1u);
-        distinct += __popc(__ballot_sync(FULL, old == 0));
-      } else if (l) {
-        atomicAdd(&wh[(uint32_t)(k[s] >> shift) & 255u], 1u);
-      }
+      if (l) atomicAdd(&wh[(uint32_t)(k[s] >> shift) & 255u], 1u);
     }
-    const bool use_match = RANK == 0 || (RANK == 5 && distinct <= 16);
     __syncthreads();
     // per digit: the tile's count, published at once, and each warp's
     // exclusive prefix; the first window of predecessors is loaded now and
@@ -686,6 +680,10 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
         const uint32_t c = whist[w * RS_RADIX + t];
         whist[w * RS_RADIX + t] = dsum;
         dsum += c;
+        if (RANK == 5) {  // the distinct digits of warp w, 32 at a time
+          const uint32_t nz = __popc(__ballot_sync(FULL, c != 0));
+          if (lane == 0 && nz) atomicAdd(&wdist[w], nz);
+        }
       }
       st_relaxed(status + tile * RS_RADIX + t, ep | (tile == 0 ? ST_PREFIX : ST_AGG) | dsum);
 #pragma unroll
@@ -712,6 +710,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
       for (int w = 0; w < W; ++w) whist[w * RS_RADIX + t] += ds;
     }
     __syncthreads();
+    const bool use_match = RANK == 0 || (RANK == 5 && wdist[warp] <= 16);
     // stable ranking in memory order (slot after slot, lanes in order);
     // every key goes straight to its place in the staging tile
 #pragma unroll
@@ -803,7 +802,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
 template <int T, int KPT, int RANK>
 constexpr size_t onesweep3_smem() {
   return (size_t)T * KPT * 8 + RS_RADIX * 8 + (size_t)(T / 32) * RS_RADIX * 4 * (RANK != 0 ? 2 : 1) +
-         2 * RS_RADIX * 4 + 16 * 4 + 16;
+         2 * RS_RADIX * 4 + 32 * 4 + 16;
 }
 
 template <int T, int KPT>
@@ -1498,6 +1497,14 @@ struct SortVariant {
 };
 const SortVariant* sort_variants(int* count) {
   static const SortVariant v[] = {
+      // early-count shapes first: index 0 is the default before any tuning
+      {(const void*)onesweep3_kernel<256, 32, 2, 3>, 256, 32, onesweep3_smem<256, 32, 3>()},
+      {(const void*)onesweep3_kernel<256, 28, 2, 3>, 256, 28, onesweep3_smem<256, 28, 3>()},
+      {(const void*)onesweep3_kernel<256, 32, 2, 5>, 256, 32, onesweep3_smem<256, 32, 5>()},
+      {(const void*)onesweep3_kernel<256, 28, 2, 5>, 256, 28, onesweep3_smem<256, 28, 5>()},
+      {(const void*)onesweep3_kernel<256, 32, 2, 0>, 256, 32, onesweep3_smem<256, 32, 0>()},
+      {(const void*)onesweep3_kernel<384, 16, 2, 3>, 384, 16, onesweep3_smem<384, 16, 3>()},
+      {(const void*)onesweep3_kernel<384, 16, 2, 5>, 384, 16, onesweep3_smem<384, 16, 5>()},
       {(const void*)onesweep_kernel<256, 16, 3>, 256, 16, onesweep_smem<256, 16>()},
       {(const void*)onesweep_kernel<256, 12, 4>, 256, 12, onesweep_smem<256, 12>()},
       {(const void*)onesweep_kernel<512, 8, 2>, 512, 8, onesweep_smem<512, 8>()},
@@ -1511,16 +1518,11 @@ const SortVariant* sort_variants(int* count) {
       {(const void*)onesweep_kernel<512, 8, 2, true, 1>, 512, 8, onesweep_smem<512, 8>()},
       {(const void*)onesweep_kernel<256, 16, 3, true, 2>, 256, 16, onesweep_smem<256, 16>()},
       {(const void*)onesweep_kernel<512, 8, 2, true, 2>, 512, 8, onesweep_smem<512, 8>()},
-      {(const void*)onesweep3_kernel<256, 28, 2, 3>, 256, 28, onesweep3_smem<256, 28, 3>()},
-      {(const void*)onesweep3_kernel<256, 32, 2, 3>, 256, 32, onesweep3_smem<256, 32, 3>()},
-      {(const void*)onesweep3_kernel<256, 28, 2, 5>, 256, 28, onesweep3_smem<256, 28, 5>()},
-      {(const void*)onesweep3_kernel<256, 32, 2, 5>, 256, 32, onesweep3_smem<256, 32, 5>()},
-      {(const void*)onesweep3_kernel<256, 32, 2, 0>, 256, 32, onesweep3_smem<256, 32, 0>()},
   };
   *count = (int)(sizeof(v) / sizeof(v[0]));
   return v;
 }
-int g_sort_variant[64];  // per device; 0 = the default shape
+int g_sort_variant[64];  // per device; 0 = the default shape (onesweep3 256 x 32, atomic-OR ranking)
 
 int sort_variant_current() {
   int dev = 0;
