@@ -805,20 +805,25 @@ def main():
                 for name, t in hg.last_profile():
                     st.setdefault(name, []).append(t)
             return {n: sum(v) / len(v) for n, v in st.items()}
-        # the sort shape for this key stream: each early-count shape times the
-        # check's own sort passes (two checks each), the fastest is kept
+        # the sort shapes for this key stream: each early-count shape times the
+        # check's own sort passes (two checks each); each pass keeps its
+        # fastest shape (the digit diversity a warp sees differs by pass)
         tuned_v, _ = hg.sort_variant()
         shape_ms = {}
         for v in range(7):
             hg.sort_variant(v)
             m = full_stage_ms(2)
-            shape_ms[v] = sum(t for n, t in m.items() if n.startswith("sort_pass"))
-        best_v = min(shape_ms, key=shape_ms.get)
-        hg.sort_variant(best_v)
+            shape_ms[v] = {n: t for n, t in m.items() if n.startswith("sort_pass")}
+        hg.sort_variant(tuned_v)
+        npass = len(shape_ms[0])
+        best_v = [min(shape_ms, key=lambda v: shape_ms[v][f"sort_pass{p}"]) for p in range(npass)]
+        for p, v in enumerate(best_v):
+            hg.sort_pass_variant(p, v)
         rf2 = k.check(cap=1 << 16, stream=s, workspace=wsf, flags=FF)
         assert rf2.witnesses == res.witnesses
         fms = full_stage_ms(args.steps)
-        hg.sort_variant(tuned_v)
+        for p in range(npass):
+            hg.sort_pass_variant(p, -1)
         ns = stf["n_sorted_keys"]
         del wsf
         passes = [n for n in fms if n.startswith("sort_pass")]
@@ -831,7 +836,8 @@ def main():
         roof_full = {
             "workload": f"{workload}, every live key written and sorted (HGRD_ALL_KEYS | NO_CELL_FILTER)",
             "sorted_keys": ns, "sort_passes": len(passes), "stages_ms": {n: round(t, 4) for n, t in fms.items()},
-            "sort_shape": best_v, "sort_ms_by_shape": {v: round(t, 4) for v, t in shape_ms.items()},
+            "sort_shape_per_pass": best_v,
+            "sort_pass_ms_by_shape": {v: {n: round(t, 4) for n, t in m.items()} for v, m in shape_ms.items()},
             "sort": [roof(n, 16 * ns, "8 B read + 8 B written per key") for n in passes],
             "scan": roof("candidates", 8 * ns, "8 B read per sorted key"),
             "expand_write": roof("expand_write", 8 * ns, "8 B written per key"),

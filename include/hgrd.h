@@ -247,6 +247,12 @@ int hgrd_check_collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws,
  * hgrd_sort_variant selects a shape (set >= 0) or queries it (set < 0). */
 int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* cuda_stream, int* best, float* ms, int cap);
 int hgrd_sort_variant(int set, int* current, int* count);
+/* The shape of one pass of the key sort (pass 0 = the lowest digit) on the
+ * current device: set >= 0 selects a shape for that pass, -1 returns it to
+ * the device's shape, below -1 only queries; *current (may be NULL) = the
+ * pass's shape, -1 when it follows the device's.  Lets a tuner pick a shape
+ * per pass on the check's own keys (digit diversity differs by pass). */
+int hgrd_sort_pass_variant(int pass, int set, int* current);
 
 /* Counters of the last check on this thread. */
 int hgrd_last_stats(hgrd_stats* s);

@@ -39,7 +39,7 @@ EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hg
            "hgrd_mlp_train_step", "hgrd_mlp_params", "hgrd_mlp_sync_bf16", "hgrd_ranked_workspace_size",
            "hgrd_check_ranked", "hgrd_sort_tune", "hgrd_sort_variant", "hgrd_jit_compile", "hgrd_jit_source",
            "hgrd_desc_params", "hgrd_bound_hash", "hgrd_bound_info", "hgrd_batch_rank_prepare",
-           "hgrd_batch_ranked_workspace_size", "hgrd_batch_check_ranked"]
+           "hgrd_batch_ranked_workspace_size", "hgrd_batch_check_ranked", "hgrd_sort_pass_variant"]
 BATCH_GRAPH = 1
 BATCH_JIT = 2
 
@@ -511,6 +511,16 @@ def sort_variant(v: int = -1):
     cur, n = C.c_int(), C.c_int()
     _raise(L.hgrd_sort_variant(v, C.byref(cur), C.byref(n)))
     return cur.value, n.value
+
+
+def sort_pass_variant(p: int, v: int = -2) -> int:
+    """Select (v >= 0), reset (v == -1) or query (v < -1) the sort shape of key-sort pass p."""
+    L = lib()
+    L.hgrd_sort_pass_variant.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.hgrd_sort_pass_variant.restype = C.c_int
+    cur = C.c_int()
+    _raise(L.hgrd_sort_pass_variant(p, v, C.byref(cur)))
+    return cur.value
 
 
 def stats() -> dict:

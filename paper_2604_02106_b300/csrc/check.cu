@@ -220,7 +220,7 @@ cudaGraphExec_t witness_graph(const Launch& L, const Layout& W, char* ws, int P)
   cudaGetDevice(&dev);
   const std::vector<uint64_t> key = {(uint64_t)dev, (uint64_t)(uintptr_t)ws, W.counters, W.raw, W.raw2, W.flags,
                                      W.excl, W.partials, W.hist, W.gbase, W.status, W.raw_cap, W.status_words,
-                                     (uint64_t)P, (uint64_t)sort_variant_current()};
+                                     (uint64_t)P, sort_variant_key()};
   std::lock_guard<std::mutex> lk(g_wg_mu);
   auto it = g_wg.find(key);
   if (it != g_wg.end()) return it->second;
@@ -535,7 +535,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256,
                        U(W.status), cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
                        p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1),
-                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB, p > 0 ? cnt + C_TAIL : nullptr));
+                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB, p > 0 ? cnt + C_TAIL : nullptr, p));
     if (p == 0 && P > 1) CK(launch_tail_sort(L, out, fin, nkeys, nsort, HP.SB + 8, P - 1, cnt + C_TAIL));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",
@@ -613,7 +613,7 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   const std::vector<uint64_t> key = {(uint64_t)dev,         B.gen,           (uint64_t)(uintptr_t)d_ws,
                                      (uint64_t)ws_bytes,    oo.max_raw_witness, oo.pair_cap,
                                      oo.flags,              oo.only_accesses, oo.max_shared_keys,
-                                     (uint64_t)jit,         (uint64_t)sort_variant_current(), (uint64_t)pair};
+                                     (uint64_t)jit,         sort_variant_key(), (uint64_t)pair};
   {
     std::lock_guard<std::mutex> lk(g_cg_mu);
     auto it = g_cg.find(key);

@@ -1036,6 +1036,54 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       return !meet;
     };
 
+    // ---- thread-tile pruning: two accesses of one width whose index terms
+    // on the thread and block ids are equal reach element c0 + L(v) + l, with
+    // L(v) the id terms of thread v and l the loop terms.  When L is
+    // injective over the launch with every two values at least S apart (a
+    // mixed-radix test: id coefficients sorted by size, each at least S plus
+    // the span of the smaller ones), and the two accesses' element ranges
+    // around L(v) fit inside a window narrower than S, no two different
+    // threads ever touch one element: the pair cannot race in any kind
+    // (Table 2 needs two threads).  In shared memory only the thread ids
+    // count (the block's own copy).  Exact: a superset of each thread's
+    // elements, guards only removing instances.
+    auto threads_disjoint = [&](int a, int b) -> bool {
+      const Lin &A = af[a].idx, &B = af[b].idx;
+      if (!A.cn.empty() || !B.cn.empty() || d.acc[a].width != d.acc[b].width) return false;
+      const bool shared = d.arrays[d.acc[a].arr].space == HGRD_SPACE_SHARED;
+      const int nid = shared ? 3 : 6;
+      for (int k = 0; k < nid; k++)
+        if (A.cv[k] != B.cv[k]) return false;
+      // loop-term ranges of each access
+      auto lrange = [&](const Lin& L, int64_t* lo, int64_t* hi) {
+        *lo = L.c0;
+        *hi = L.c0;
+        for (size_t l = 0; l < d.loops.size(); l++) {
+          if (ub[l] <= 0) return false;
+          const int64_t t = L.cv[6 + l] * (ub[l] - 1);
+          (t < 0 ? *lo : *hi) += t;
+        }
+        return true;
+      };
+      int64_t alo, ahi, blo, bhi;
+      if (!lrange(A, &alo, &ahi) || !lrange(B, &blo, &bhi)) return false;
+      // L(v1) - L(v2) must avoid [blo - ahi, bhi - alo] for v1 != v2
+      const int64_t need = std::max(std::abs(blo - ahi), std::abs(bhi - alo)) + 1;
+      std::vector<std::pair<int64_t, int64_t>> t;  // (|coefficient|, range) of the ids that vary
+      for (int k = 0; k < nid; k++) {
+        if (dims[k] <= 1) continue;
+        if (A.cv[k] == 0) return false;  // two threads differing in this id alone meet
+        t.push_back({std::abs(A.cv[k]), dims[k]});
+      }
+      std::sort(t.begin(), t.end());
+      __int128 below = 0;  // span of the smaller terms
+      for (auto& [c, r] : t) {
+        if ((__int128)c < below + need) return false;
+        below += (__int128)c * (r - 1);
+      }
+      return true;
+    };
+
     // ---- pair rule E (Sec. 6.1 trivially race free; Appendix A scopes)
     // Two instances of one block are ordered unless they share a barrier
     // interval (Sec. 6.1, block barrier; Table 2), so accesses whose interval
@@ -1051,6 +1099,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         if (x.kind == 2 && y.kind == 2) m = (x.scope == 0 || y.scope == 0) ? 1 : 0;
         if (d.arrays[x.arr].space == HGRD_SPACE_SHARED) m &= ~1;
         if (acc_ivhi[a] < acc_ivlo[b] || acc_ivhi[b] < acc_ivlo[a]) m &= 1;
+        if (m && !af[a].dead && !af[b].dead && threads_disjoint(a, b)) m = 0;
         // acquire-release guards at one global address order a pair when
         // their narrower scope covers its type: always inside a block, across
         // blocks with device scope on both (Sec. 6.5, Table 2, Appendix A).

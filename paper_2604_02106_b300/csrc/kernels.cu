@@ -962,7 +962,7 @@ __device__ __forceinline__ bool cand_step(const CandCtx& X, CandCarry& c, uint64
   return p + 32 >= X.r1 && !c.owned;
 }
 
-__global__ void __launch_bounds__(CA_THREADS) candidates_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
+__global__ void __launch_bounds__(CA_THREADS, 2) candidates_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                                const DProg* __restrict__ P, uint64_t* __restrict__ cand,
                                                                uint64_t cand_cap, uint64_t* counters) {
   CandCtx X;
@@ -1523,6 +1523,8 @@ const SortVariant* sort_variants(int* count) {
   return v;
 }
 int g_sort_variant[64];  // per device; 0 = the default shape (onesweep3 256 x 32, atomic-OR ranking)
+// per device and key-sort pass: 1 + the shape chosen for that pass, 0 = the device's shape
+int g_sort_pass_variant[64][MAX_PASSES];
 
 int sort_variant_current() {
   int dev = 0;
@@ -1530,14 +1532,26 @@ int sort_variant_current() {
   return (dev >= 0 && dev < 64) ? g_sort_variant[dev] : 0;
 }
 
+uint64_t sort_variant_key() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 0;
+  uint64_t h = (uint64_t)g_sort_variant[dev];
+  for (int p = 0; p < MAX_PASSES; p++) h = h * 31 + (uint64_t)g_sort_pass_variant[dev][p];
+  return h;
+}
+
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist, int next_shift, const uint32_t* ctab,
-                            uint64_t ncells, int rsh, const uint64_t* skip) {
+                            uint64_t ncells, int rsh, const uint64_t* skip, int pass) {
   int nv = 0, dev = 0;
   const SortVariant* V = sort_variants(&nv);
   cudaGetDevice(&dev);
-  const SortVariant& S = V[(dev >= 0 && dev < 64 && g_sort_variant[dev] < nv) ? g_sort_variant[dev] : 0];
+  int v = (dev >= 0 && dev < 64) ? g_sort_variant[dev] : 0;
+  if (dev >= 0 && dev < 64 && pass >= 0 && pass < MAX_PASSES && g_sort_pass_variant[dev][pass] > 0)
+    v = g_sort_pass_variant[dev][pass] - 1;
+  const SortVariant& S = V[v < nv ? v : 0];
   const uint64_t tile = (uint64_t)S.threads * S.kpt;
   const uint64_t tiles = (n_max + tile - 1) / tile;
   cudaError_t e = allow_smem(S.fn, S.smem);
@@ -1710,6 +1724,19 @@ extern "C" int hgrd_sort_variant(int set, int* current, int* count) {
   if (set >= 0) g_sort_variant[dev] = set;
   if (current) *current = g_sort_variant[dev];
   if (count) *count = nv;
+  return HGRD_OK;
+}
+
+extern "C" int hgrd_sort_pass_variant(int pass, int set, int* current) {
+  using namespace hgrd;
+  int nv = 0, dev = 0;
+  sort_variants(&nv);
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return fail(HGRD_EUNSUPPORTED, "device index too large");
+  if (pass < 0 || pass >= MAX_PASSES) return fail(HGRD_EINVAL, "no such sort pass");
+  if (set >= nv) return fail(HGRD_EINVAL, "no such sort variant");
+  if (set >= -1) g_sort_pass_variant[dev][pass] = set + 1;
+  if (current) *current = g_sort_pass_variant[dev][pass] - 1;
   return HGRD_OK;
 }
 

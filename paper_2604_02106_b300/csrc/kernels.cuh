@@ -55,7 +55,10 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
                             int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0,
                             const uint32_t* ctab = nullptr, uint64_t ncells = 0, int rsh = 0,
-                            const uint64_t* skip = nullptr);
+                            const uint64_t* skip = nullptr, int pass = -1);
+// the sort shapes in force on the current device (the device's shape and the
+// per-pass choices), as one number for cache keys
+uint64_t sort_variant_key();
 // the passes after the first over the digits from shift0 (npass of them) in
 // one CTA when at most 4096 keys remain; sets *done then (the passes given
 // `skip` = done return at once)

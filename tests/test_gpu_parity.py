@@ -472,7 +472,10 @@ def test_cell_filter_sorts_only_shared_cells(planted):
         assert st["n_sorted_keys"] == (2 * 255 if planted else 0)
         _same(g, o)
         _same(hg.check(w.text, w.binding, cap=1 << 20, flags=flags | hg.NO_CELL_FILTER), o)
-        assert hg.stats()["cell_filter"] == 0 and hg.stats()["n_sorted_keys"] == 256 * 256
+        # without the planted stride every thread writes its own output
+        # element: the write races with nothing (thread-tile pruning) and no
+        # global key is written at all
+        assert hg.stats()["cell_filter"] == 0 and hg.stats()["n_sorted_keys"] == (256 * 256 if planted else 0)
 
 
 # ---------------------------------------------------------------- acquire-release guards (Sec. 6.5)
@@ -567,3 +570,23 @@ def test_every_key_through_the_sort_on_the_stencil():
     g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.ALL_KEYS | hg.NO_CELL_FILTER)
     assert hg.stats()["n_sorted_keys"] == g.n_keys  # every live key went through the sort
     _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+
+
+def test_sort_shapes_chosen_per_pass():
+    # each pass of the key sort on its own shape (the tuner's per-pass
+    # choice): the stable LSD sort composes, the result is the oracle's
+    w = workloads.config2(0, planted=True, W=128, H=128, K=8)
+    o = oracle.check(w.text, w.binding, cap=1 << 20)
+    _, n = hg.sort_variant()
+    try:
+        for shapes in ((0, 4, 7), (4, 2, 0), (6, 5, 11)):
+            for p, v in enumerate(shapes):
+                hg.sort_pass_variant(p, v % n)
+            assert [hg.sort_pass_variant(p) for p in range(3)] == [v % n for v in shapes]
+            g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.ALL_KEYS | hg.NO_CELL_FILTER)
+            assert hg.stats()["sort_passes"] == 3
+            _same(g, o)
+    finally:
+        for p in range(3):
+            hg.sort_pass_variant(p, -1)
+    assert hg.sort_pass_variant(0) == -1

@@ -45,9 +45,14 @@ def test_source_depends_on_structure_only():
     srcs = {_bind(w).jit_source(flags=hg.NO_SPLIT) for w in items[:4]}
     assert len(srcs) == 1
     a = _bind(workloads.config2(0, planted=True, W=64, H=64, K=4))
-    b = _bind(workloads.config2(0, planted=False, W=128, H=128, K=8))
+    b = _bind(workloads.config2(0, planted=True, W=128, H=128, K=8))
     assert a.jit_source() == b.jit_source()
     assert a.jit_source() != a.jit_source(flags=hg.NO_SPLIT)
+    # without the planted stride every thread writes its own output element:
+    # the write races with nothing (thread-tile pruning), so its keys are
+    # never written and the source says so
+    c = _bind(workloads.config2(0, planted=False, W=128, H=128, K=8))
+    assert c.jit_source() != b.jit_source()
 
 
 def test_generated_source_covers_every_live_access():

@@ -126,7 +126,9 @@ def test_pairs_in_disjoint_barrier_intervals():
             "access R G ; width 4 ; iv 1 ; idx tx + 1\n")     # 5
     k = hg.Kernel(text).bind((2, 1, 1), (32, 1, 1), ())
     _, ab = ranker.pair_features(k)
-    assert ab == [(0, 0), (2, 2), (2, 3), (4, 4), (4, 5)]
+    # (0, 0) and (2, 2): each thread writes its own element of the block's
+    # copy (thread-tile pruning); (4, 4): both blocks write G[tx]
+    assert ab == [(2, 3), (4, 4), (4, 5)]
 
 
 def test_block_pair_pruning_examples():
@@ -138,12 +140,18 @@ def test_block_pair_pruning_examples():
         f, ab = ranker.pair_features(k)
         return {p: (int(r[64 + 3]), int(r[64 + 4])) for p, r in zip(ab, f)}
     base = "kernel b\nloop i 2\narray G global 4096\n"
-    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\n") == {(0, 0): (0, 1)}
+    # one element per thread (thread-tile pruning): no pair at all
+    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\n") == {}
+    assert pairs(base + "access W G ; width 4 ; idx bx*128 + tx*2 + i\n") == {}
+    assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx*2 + i\n") == {(0, 0): (1, 1)}  # thread 32 meets block 1
+    # two elements per thread, the write reaching the next thread's read
+    assert pairs(base + "access W G ; width 4 ; idx (bx*64 + tx)*2 + i + 1\naccess R G ; width 4 ; idx bx*128 + tx*2\n") == \
+        {(0, 1): (1, 1)}
     assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx + i\n") == {(0, 0): (1, 1)}  # hulls meet
     assert pairs(base + "access W G ; width 4 ; idx bx*65 + tx + i\n") == {(0, 0): (0, 1)}
     assert pairs(base + "access W G ; width 4 ; idx tx\n") == {(0, 0): (1, 1)}
     assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\naccess R G ; width 4 ; iv 1 ; idx bx*64 + tx\n") == \
-        {(0, 0): (0, 1)}  # (0, 1): other interval, own slice: races with nothing
+        {}  # every thread its own element, in both intervals
     assert pairs(base + "access W G ; width 16 ; idx bx*16 + tx / 4\n") == {(0, 0): (1, 1)}  # a division: not pruned
 
 
@@ -173,11 +181,34 @@ def test_block_pair_pruning_against_brute_force():
     assert pruned > 20
 
 
+def test_pair_rule_keeps_every_racing_pair():
+    # the library's pair rule (with interval, block-pair and thread-tile
+    # pruning) may drop only pairs that never race: every racy access pair of
+    # the oracle is eligible; kernels whose threads own private regions lose
+    # those pairs
+    import oracle
+    dropped = 0
+    ws = [workloads.random_tiny(6000 + s, max_instances=3000) for s in range(80)] + \
+         [workloads.config4(i, hi_exp=3.8) for i in range(60)]
+    for w in ws:
+        k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+        _, ab = ranker.pair_features(k)
+        o = oracle.check(w.text, w.binding, pair=False)
+        assert {(x[3], x[4]) for x in o.witnesses} <= set(ab), w.name
+        if w.name.startswith("c4") or "corpus" in w.text.splitlines()[0]:
+            acc = [l for l in w.text.splitlines() if l.startswith("access")]
+            for a, line in enumerate(acc):
+                if line.startswith("access W D") and "gid*SPAN + off" in line and (a, a) not in ab:
+                    dropped += 1
+    assert dropped > 20
+
+
 def test_block_pair_pruning_work_budget():
     # past the sweep budget (2^21 block hulls) the pair keeps its inter-block
     # kind: pruning is an optimisation, never required for exactness
     text = "kernel g\narray G global 4*64*4194304\naccess W G ; width 4 ; idx bx*64 + tx\n"
     for gx, inter in ((1 << 20, 0), ((1 << 21) + 1, 1)):
-        k = hg.Kernel(text).bind((gx, 1, 1), (64, 1, 1), ())
+        # two threads (ty 0 and 1) share each element: no thread-tile pruning
+        k = hg.Kernel(text).bind((gx, 1, 1), (64, 2, 1), ())
         f, ab = ranker.pair_features(k)
         assert ab == [(0, 0)] and int(f[0][64 + 3]) == inter and int(f[0][64 + 4]) == 1
