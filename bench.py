@@ -590,9 +590,9 @@ def run_once(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train-pairs", type=int, default=1000000)
+    ap.add_argument("--train-pairs", type=int, default=300000)
     ap.add_argument("--heldout", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--topk", type=int, default=4)
     ap.add_argument("--suite", default="stencil", choices=["stencil", "warp", "sweep", "corpus", "ranked", "symbolic"])
     ap.add_argument("--items", type=int, default=1000)

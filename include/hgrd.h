@@ -348,8 +348,8 @@ enum { HGRD_MLP_IN = 96, HGRD_MLP_HIDDEN = 256, HGRD_MLP_PARAMS = 90881 };
  * Appendix A; neither access dead) with 96 features each: per access, its kind
  * and scope, width, memory space, the folded coefficients on thread, block
  * and loop ids, div/mod and guard counts, its index range against the array;
- * per pair, interval overlap, race kinds the pair rule allows, byte-range
- * overlap, coefficient differences, launch and array sizes.  Host memory:
+ * per pair, interval overlap and identical interval ranges, race kinds the
+ * pair rule allows, byte-range overlap, coefficient differences, launch and array sizes.  Host memory:
  * out[cap * 96], pairs[cap * 2]; *n = number of eligible pairs (ETRUNCATED
  * when it exceeds cap). */
 int hgrd_pair_features(const hgrd_desc* d, float* out, uint8_t* pairs, uint32_t cap, uint32_t* n);

@@ -1361,7 +1361,9 @@ void pair_features(const hgrd_desc& d, int a, int b, float* f) {
                                                                                                                 : 0.f;
   h[30] = (float)std::min(1.0, (std::min(ahi, bhi) - std::max(alo, blo)) / std::max(1.0, std::min(ahi - alo, bhi - blo)));
   if (h[30] < 0) h[30] = 0;
-  h[31] = 1.f;  // bias-like constant
+  // the two accesses span the same barrier intervals (a read one interval
+  // after the write it pairs with differs here)
+  h[31] = (A.iv_lo == Bb.iv_lo && A.iv_hi == Bb.iv_hi) ? 1.f : 0.f;
 }
 
 int load_desc(const char* text, size_t len, hgrd_desc** out) {

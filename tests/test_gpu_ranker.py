@@ -121,12 +121,12 @@ def _corpus(first, n, hi=4.4):
 @pytest.fixture(scope="module")
 def trained():
     # training kernels: seeds disjoint from the held-out ones below
-    ws, ks = _corpus(50000, 400)
+    ws, ks = _corpus(50000, 1000)
     res = hg.Batch(ks, witness_cap=1).check()
     X, y = rk.labelled_pairs(ks, res)
-    assert y.sum() > 20 and len(y) > 2000
+    assert y.sum() > 200 and len(y) - y.sum() > 1000
     r = rk.Ranker(seed=11)
-    losses = r.fit(X, y, epochs=6, batch=2048, lr=2e-3)
+    losses = r.fit(X, y, epochs=30, batch=256, lr=2e-3)
     return r, losses
 
 
@@ -151,8 +151,9 @@ def test_ranked_verdicts_match_the_oracle(trained):
 
 
 def test_trained_network_beats_random_order(trained):
-    # how often the ranked stage alone confirms a racy kernel: trained scores
-    # against uniformly random scores for the same pairs
+    # how often the ranked stage alone confirms a racy kernel from its single
+    # top pair: trained scores against uniformly random scores for the same
+    # pairs (random order finds about 69% of them on this corpus)
     r, _ = trained
     ws, ks = _corpus(70000, 300)
     rng = np.random.default_rng(0)
@@ -161,10 +162,10 @@ def test_trained_network_beats_random_order(trained):
         if not w.meta["planted"]:
             continue
         racy += 1
-        _, info = rk.check_ranked(k, r, topk=2, flags=hg.NO_SMALL)
+        _, info = rk.check_ranked(k, r, topk=1, flags=hg.NO_SMALL)
         hit_t += info["stage"] == 1
         n = info["n_pairs"]
-        _, info_r = rk.check_ranked(k, scores=rng.random(n), topk=2, flags=hg.NO_SMALL)
+        _, info_r = rk.check_ranked(k, scores=rng.random(n), topk=1, flags=hg.NO_SMALL)
         hit_r += info_r["stage"] == 1
     assert racy >= 40
     assert hit_t > hit_r + 0.15 * racy, (hit_t, hit_r, racy)
@@ -197,12 +198,15 @@ def test_restricted_check_small_enough_runs_in_one_cta():
 
 def test_ranked_check_of_few_pairs_is_one_restricted_check():
     # at most top-k eligible pairs: no scores, one restricted check covering
-    # every eligible pair decides both verdicts (16384 keys: more than one
-    # CTA's check, which would skip the ranking altogether)
+    # every eligible pair decides both verdicts (12288 and 16384 keys: more
+    # than one CTA's check, which would skip the ranking altogether).  The
+    # race-free write is injective only under its guard, so no bind-time
+    # test drops its pair
     from workloads import Binding
     bnd = Binding((128, 1, 1), (64, 1, 1), ())
     for text, racy in ((("kernel c\narray a global 16384\narray r global 16384\n"
-                         "access W a ; width 4 ; idx tx + 64*bx\naccess R r ; width 4 ; idx tx\n"), False),
+                         "access W a ; width 4 ; idx tx/2 + 32*bx ; if tx % 2 == 0\n"
+                         "access R r ; width 4 ; idx tx\n"), False),
                        (("kernel d\narray a global 16384\narray r global 16384\n"
                          "access W a ; width 4 ; idx tx\naccess R r ; width 4 ; idx tx\n"), True)):
         k = hg.Kernel(text).bind(bnd.grid, bnd.block, bnd.params)

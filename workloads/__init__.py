@@ -685,6 +685,58 @@ def _dims(total, rng, maxdims):
     return dims
 
 
+def _c4_lookalikes(w, item, nthr, nblk, span, has_shared, planted):
+    """Append 0-3 blocks of two accesses whose addresses overlap across the
+    threads of a block, so that no bind-time disjointness test can drop the
+    pair and only the exact check decides it.  A block is a halo exchange on
+    the global array H (each thread writes its own slot in iteration i at
+    interval 2i, then reads the next thread's slot of its own block at 2i+1)
+    or a broadcast through the shared array Bc (thread 0 writes at 2i+1,
+    every thread reads at 2i+2).  Both are race free.  In a planted kernel
+    one block may instead take its racy twin: the read in the writer's
+    interval, or the halo read crossing the block edge (only with more than
+    one block).  The draws come from a second generator stream, so the rest
+    of the kernel is the same with or without these blocks.  Returns the
+    racy twin's name or None."""
+    rng = SplitMix64((seed_for(4, item) * 0x9E3779B97F4A7C15 + 0x632BE59BD9B4E019) & MASK64)
+    used = sum(1 for l in w.lines if l.startswith("access"))
+    blocks = []
+    for _ in range(rng.below(4)):
+        if used + 2 > 32:
+            break
+        blocks.append("broadcast" if has_shared and rng.below(2) else "halo")
+        used += 2
+    racy_at = rng.below(len(blocks)) if planted and blocks and rng.below(2) == 0 else -1
+    if not blocks:
+        return None
+    decl = []
+    if "halo" in blocks:
+        decl.append(f"array H global {4 * (nthr * nblk + 1) * span}")
+    if "broadcast" in blocks:
+        decl.append(f"array Bc shared {4 * span}")
+    at = next(n for n, l in enumerate(w.lines) if l.startswith("assert"))
+    w.lines[at:at] = decl
+    twin = None
+    for n, b in enumerate(blocks):
+        line = 200 + 2 * n
+        if b == "halo":
+            w.access("W", "H", 4, "gid*SPAN + off", iv="2*i", line=line)
+            rd, iv = f"(lb*{nthr} + (lt + 1) % {nthr})*SPAN + off", "2*i + 1"
+            if n == racy_at:
+                if nblk > 1 and rng.below(2):
+                    twin, rd = "halo_cross", "(gid + 1)*SPAN + off"
+                else:
+                    twin, iv = "halo_early", "2*i"
+            w.access("R", "H", 4, rd, iv=iv, line=line + 1)
+        else:
+            w.access("W", "Bc", 4, "off", iv="2*i + 1", guards=["lt == 0"], line=line)
+            iv = "2*i + 2"
+            if n == racy_at:
+                twin, iv = "broadcast_early", "2*i + 1"
+            w.access("R", "Bc", 4, "off", iv=iv, line=line + 1)
+    return twin
+
+
 def config4(item: int, lo_exp: float = 3.0, hi_exp: float = 7.0, planted=None) -> Workload:
     rng = SplitMix64(seed_for(4, item))
     target = int(10 ** (lo_exp + (hi_exp - lo_exp) * rng.uniform()))
@@ -801,7 +853,8 @@ def config4(item: int, lo_exp: float = 3.0, hi_exp: float = 7.0, planted=None) -
             w.access("W", "S", 4, "lt*SPAN + off", iv=1, guards=guards, line=line)
         elif kind == "shared_read":
             w.access("R", "S", 4, f"((lt + 1) % {nthr})*SPAN + off", iv=2, guards=guards, line=line)
+    pattern_race = _c4_lookalikes(w, item, nthr, nblk, span, has_shared, plant is not None)
     inst = nblk * nthr * span * len([l for l in w.lines if l.startswith("access")])
     return Workload(f"c4_{item}", w.text(), Binding(tuple(grid), tuple(block), (span, nvalid)),
-                    {"config": 4, "planted": plant, "target": target, "instances": inst,
+                    {"config": 4, "planted": plant, "pattern_race": pattern_race, "target": target, "instances": inst,
                      "n_access": sum(1 for l in w.lines if l.startswith("access"))})
