@@ -1084,6 +1084,18 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       return true;
     };
 
+    // Accesses whose byte ranges over the whole launch never meet share no
+    // location: no pair in any kind.  Exact: each range holds every element
+    // its access can reach (interval arithmetic over the ids, the loop
+    // counters and the division and remainder nodes; guards only remove
+    // instances).
+    auto ranges_disjoint = [&](int a, int b) -> bool {
+      const AccInfo &X = B.acc_info[a], &Y = B.acc_info[b];
+      const __int128 xlo = (__int128)X.idx_lo * X.width, xhi = (__int128)X.idx_hi * X.width + X.width;
+      const __int128 ylo = (__int128)Y.idx_lo * Y.width, yhi = (__int128)Y.idx_hi * Y.width + Y.width;
+      return xhi <= ylo || yhi <= xlo;
+    };
+
     // ---- pair rule E (Sec. 6.1 trivially race free; Appendix A scopes)
     // Two instances of one block are ordered unless they share a barrier
     // interval (Sec. 6.1, block barrier; Table 2), so accesses whose interval
@@ -1099,7 +1111,7 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
         if (x.kind == 2 && y.kind == 2) m = (x.scope == 0 || y.scope == 0) ? 1 : 0;
         if (d.arrays[x.arr].space == HGRD_SPACE_SHARED) m &= ~1;
         if (acc_ivhi[a] < acc_ivlo[b] || acc_ivhi[b] < acc_ivlo[a]) m &= 1;
-        if (m && !af[a].dead && !af[b].dead && threads_disjoint(a, b)) m = 0;
+        if (m && !af[a].dead && !af[b].dead && (ranges_disjoint(a, b) || threads_disjoint(a, b))) m = 0;
         // acquire-release guards at one global address order a pair when
         // their narrower scope covers its type: always inside a block, across
         // blocks with device scope on both (Sec. 6.5, Table 2, Appendix A).
@@ -1242,8 +1254,10 @@ int bind_desc(hgrd_desc& d, const hgrd_binding* bind) {
       P.niv = (int32_t)((ivmax - ivmin) + 1);
       P.nsbins = (int64_t)(sgran * (uint64_t)P.niv);
       const int64_t upb = (int64_t)P.wpb * P.nchunk;
+      // (only when some shared-array key is written: accesses whose keys are
+      // counted, never written, need no bins)
       bool any_shared_live = false;
-      for (int a = 0; a < P.nacc; a++) any_shared_live |= !P.acc[a].dead && P.acc[a].shared;
+      for (int a = 0; a < P.nacc; a++) any_shared_live |= !P.acc[a].dead && P.acc[a].shared && ((P.emask >> a) & 1u);
       unsigned __int128 per_block = 0;
       for (int a = 0; a < P.nacc; a++)
         if (!P.acc[a].dead && P.acc[a].shared) per_block += (unsigned __int128)nthr * (uint64_t)nit * (uint64_t)P.acc[a].G;

@@ -91,15 +91,15 @@ def test_workspace_scales_with_problem():
     w = workloads.config2(0)
     k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
     ws = k.workspace_size()
-    # two 8-byte key buffers dominate: for the kept keys of the one global
-    # write (the reads of the read-only input race with nothing) plus room for
-    # candidate shared-memory bins: all kept shared keys up to 2^24, a
-    # sixteenth of them beyond; the kept shared keys are those of the tile's
-    # three writes (the ten reads of the tile share no barrier interval with a
-    # write, so they race with nothing either)
+    # two 8-byte key buffers dominate, for the kept keys of the one global
+    # write: the reads of the read-only input race with nothing, the ten
+    # reads of the tile share no barrier interval with a write, the tile's
+    # two staging writes cover the byte ranges [0, 1024) and [1024, 1296),
+    # which never meet, and each maps distinct threads to distinct elements,
+    # as does the centre write, so no shared-memory key is kept
     out_keys = 64 * 64 * 256 * 32
-    shared_kept = 3 * out_keys
-    keys = out_keys + min(shared_kept, max(1 << 24, shared_kept // 16))
+    shared_kept = 0
+    keys = out_keys
     # (+ four raw-witness buffers of at most 2^24 words and small tables); the
     # cell filter adds 4 bytes per cell (3.4M cells)
     cells = 2 * 1024 * 1024 + 4096 * 324
@@ -108,8 +108,15 @@ def test_workspace_scales_with_problem():
     assert base + 4 * cells <= ws < base + 4 * cells + (1 << 20)
     # one global sort of every kept key needs buffers for all of them
     assert k.workspace_size(flags=hg.NO_SPLIT) >= 16 * (out_keys + shared_kept)
-    # a caller-given room for shared keys sizes the buffers
-    assert k.workspace_size(max_shared_keys=1 << 20) < ws
+    # room for candidate shared-memory bins: all kept shared keys up to 2^24,
+    # a sixteenth of them beyond, or a caller-given room
+    text = ("kernel t\narray S shared 1024\naccess W S ; width 4 ; idx tx\n"
+            "access R S ; width 4 ; idx (tx + 1) % 256\n")
+    ks = hg.Kernel(text).bind((4096, 1, 1), (256, 1, 1), ())
+    kept = 2 * 4096 * 256
+    assert ks.workspace_size(flags=hg.NO_SPLIT) >= 16 * kept
+    assert 16 * kept <= ks.workspace_size(flags=hg.NO_CELL_FILTER) < 16 * kept + 4 * 8 * (1 << 24) + (200 << 20)
+    assert ks.workspace_size(max_shared_keys=1 << 10) < ks.workspace_size()
 
 
 def test_acquire_release_guards_bind():

@@ -47,7 +47,12 @@ def test_source_depends_on_structure_only():
     a = _bind(workloads.config2(0, planted=True, W=64, H=64, K=4))
     b = _bind(workloads.config2(0, planted=True, W=128, H=128, K=8))
     assert a.jit_source() == b.jit_source()
-    assert a.jit_source() != a.jit_source(flags=hg.NO_SPLIT)
+    # no shared-memory key of the stencil is written (the tile's accesses race
+    # with nothing), so it takes no block-local bins; a kernel with racing
+    # shared accesses does
+    assert a.jit_source() == a.jit_source(flags=hg.NO_SPLIT)
+    r = _bind(workloads.random_shared(5000))
+    assert r.jit_source() != r.jit_source(flags=hg.NO_SPLIT)
     # without the planted stride every thread writes its own output element:
     # the write races with nothing (thread-tile pruning), so its keys are
     # never written and the source says so
@@ -60,7 +65,10 @@ def test_generated_source_covers_every_live_access():
     src = _bind(w).jit_source()
     for a in range(16):
         assert f"// access {a}\n" in src
-    assert "hgrd_jit_expand3" in src and "hgrd_jit_expand4" in src and "hgrd_jit_expand0" not in src
+    # no shared key is written: the plain count and write passes, no block-local ones
+    assert "hgrd_jit_expand0" in src and "hgrd_jit_expand1" in src and "hgrd_jit_expand3" not in src
+    r = _bind(workloads.random_shared(5000)).jit_source()
+    assert "hgrd_jit_expand3" in r and "hgrd_jit_expand4" in r and "hgrd_jit_expand0" not in r
 
 
 def test_warp_intervals_reach_the_key():

@@ -153,32 +153,49 @@ def test_block_pair_pruning_examples():
     assert pairs(base + "access W G ; width 4 ; idx bx*64 + tx\naccess R G ; width 4 ; iv 1 ; idx bx*64 + tx\n") == \
         {}  # every thread its own element, in both intervals
     assert pairs(base + "access W G ; width 16 ; idx bx*16 + tx / 4\n") == {(0, 0): (1, 1)}  # a division: not pruned
+    # byte ranges that never meet: [0, 128) and [128, 256) by the remainders'
+    # bounds (each access alone races: threads 0 and 32 share an element)
+    two = "access W G ; width 4 ; idx tx % 32\naccess W G ; width 4 ; idx 32 + tx % 32\n"
+    assert pairs(base + two) == {(0, 0): (1, 1), (1, 1): (1, 1)}
+    # one element further and they meet (threads 32 and 63 against 0)
+    assert pairs(base + two.replace("32 + tx", "31 + tx")) == {(0, 0): (1, 1), (0, 1): (1, 1), (1, 1): (1, 1)}
+    # different widths: [0, 128) against bytes [128, 256) of 16-byte elements
+    assert (0, 1) not in pairs(base + "access W G ; width 4 ; idx tx % 32\naccess R G ; width 16 ; idx 8 + tx % 8\n")
+    assert (0, 1) in pairs(base + "access W G ; width 4 ; idx tx % 32\naccess R G ; width 16 ; idx 7 + tx % 8\n")
 
 
 def test_block_pair_pruning_against_brute_force():
-    # every pair whose inter-block kind was pruned has no two instances of
-    # different blocks on one granule (independent enumeration of tests/brute.py)
+    # every global-memory pair whose inter-block kind was pruned (listed
+    # without it, or not listed at all: byte ranges that never meet, or
+    # threads that own disjoint elements) has no two instances of different
+    # blocks on one granule (independent enumeration of tests/brute.py)
     import brute
-    pruned = 0
+    pruned = unlisted = 0
     for seed in range(120):
         w = workloads.random_tiny(4000 + seed, max_instances=400)
         k = hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
         f, ab = ranker.pair_features(k)
+        inter = {p: r[64 + 3] for p, r in zip(ab, f)}
         d = brute.parse(w.text)
         inst, _ = brute.instances(d, w.binding)
-        for (a, b), r in zip(ab, f):
-            if r[64 + 3] or d["arrays"][d["acc"][a]["array"]]["shared"]:
-                continue
-            ka, kb = d["acc"][a]["kind"], d["acc"][b]["kind"]
-            if ka == "A" and kb == "A":
-                continue  # atomics: pruned by their scopes, not by addresses
-            pruned += 1
-            xa = [x for x in inst if x["acc"] == a]
-            xb = [x for x in inst if x["acc"] == b]
-            for x in xa:
-                for y in xb:
-                    assert x["blk"] == y["blk"] or not (x["gran"] & y["gran"]), (seed, a, b)
-    assert pruned > 20
+        acc = d["acc"]
+        for a in range(len(acc)):
+            for b in range(a, len(acc)):
+                if acc[a]["array"] != acc[b]["array"] or d["arrays"][acc[a]["array"]]["shared"]:
+                    continue
+                ka, kb = acc[a]["kind"], acc[b]["kind"]
+                if (ka == "R" and kb == "R") or (ka == "A" and kb == "A"):
+                    continue  # loads, and atomics (pruned by their scopes, not by addresses)
+                if inter.get((a, b), 0):
+                    continue
+                pruned += 1
+                unlisted += (a, b) not in inter
+                xa = [x for x in inst if x["acc"] == a]
+                xb = [x for x in inst if x["acc"] == b]
+                for x in xa:
+                    for y in xb:
+                        assert x["blk"] == y["blk"] or not (x["gran"] & y["gran"]), (seed, a, b)
+    assert pruned > 20 and 0 < unlisted < pruned, (pruned, unlisted)
 
 
 def test_pair_rule_keeps_every_racing_pair():
