@@ -140,7 +140,10 @@ typedef struct {
                                also of those the pair rule shows can race with nothing, in one
                                global sort on the interpreted kernels (implies HGRD_NO_SPLIT,
                                HGRD_NO_JIT, HGRD_NO_SMALL); same result: a measurement mode that
-                               puts every key of the check through the sort and the scan */
+                               puts every key of the check through the sort and the scan;
+                               HGRD_SCAN_BALLOT: run the first phase of the conflict scan as
+                               32-key warp steps (one key per lane, ballots per step) instead of
+                               rows of 16 keys per lane staged by tensor copies; same result */
   uint32_t only_accesses;   /* nonzero: check only the accesses whose bit is set (a restricted
                                check: every witness is a real race of the full kernel, but a
                                clean result says nothing about the other accesses) */
@@ -160,7 +163,8 @@ enum {
   HGRD_GRAPH = 128,
   HGRD_NO_CELL_FILTER = 256,
   HGRD_CELL_FILTER = 512,
-  HGRD_ALL_KEYS = 1024
+  HGRD_ALL_KEYS = 1024,
+  HGRD_SCAN_BALLOT = 2048
 };
 
 /* One timed pipeline stage (HGRD_PROFILE): events recorded on the check's

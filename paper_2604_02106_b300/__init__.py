@@ -28,6 +28,7 @@ GRAPH = 128      # run the check as one CUDA graph launch (captured once per bin
 NO_CELL_FILTER = 256  # sort every kept key (no per-cell pre-filter)
 CELL_FILTER = 512     # pre-filter keys by cell whenever the table fits (default: only for many keys)
 ALL_KEYS = 1024       # write and sort the keys of every live access (one global sort, interpreted kernels)
+SCAN_BALLOT = 2048    # first scan phase as 32-key warp steps instead of tensor-copied rows (same result)
 
 # symbols include/hgrd.h declares
 EXPORTS = ["hgrd_load_desc", "hgrd_bind_host_params", "hgrd_workspace_size", "hgrd_check", "hgrd_check_enqueue",

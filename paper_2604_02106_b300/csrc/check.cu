@@ -62,7 +62,8 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   const bool split = P.smode && !(o && (o->flags & HGRD_NO_SPLIT)) && !all;
   L.scap = split ? ((o && o->max_shared_keys) ? o->max_shared_keys : P.scap) : 0;
   const uint64_t nsort_all = all ? B.nkeys_max : B.nsort_max_all;  // every live key, or the kept ones
-  L.key_words = std::max<uint64_t>(split ? B.nsort_max_split + L.scap : nsort_all, 1);
+  // (whole rows of 16 keys: the candidate scan reads its keys by rows)
+  L.key_words = (std::max<uint64_t>(split ? B.nsort_max_split + L.scap : nsort_all, 1) + 63) & ~63ull;
   // a candidate run holds at least two keys
   L.cand_cap = std::max<uint64_t>(L.key_words / 2, 1);
   // defaults scale with the problem and come back as HGRD_ENOMEM (with the
@@ -544,7 +545,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   // `in` holds the sorted keys; `out` is free for the candidate list
   const uint64_t cand_cap = W.cand_cap;
-  CK(launch_candidates(L, in, nkeys, dprog, out, cand_cap, cnt));
+  CK(launch_candidates(L, in, W.key_words, nkeys, dprog, out, cand_cap, cnt, o && (o->flags & HGRD_SCAN_BALLOT)));
   if (split) CK(launch_shared_cand(L, HP, U(W.stbl), U(W.sbase), out, cand_cap, cnt));
   g_prof.mark("candidates");
   CK(launch_exact(L, in, nkeys, dprog, out, cand_cap, U(W.raw), W.raw_cap, cnt, o && (o->flags & HGRD_STOP_FIRST),

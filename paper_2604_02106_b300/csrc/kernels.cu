@@ -17,6 +17,7 @@
 //             block, warp and thread per barrier interval and block; pairs
 //             are decided with ballots and __match_any_sync (Table 2).
 //  witness    merge per-run witnesses into the canonical set.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1040,6 +1041,374 @@ __global__ void __launch_bounds__(CA_THREADS, 2) candidates_kernel(const uint64_
   }
 }
 
+// ------------------------------------------------------------------ conflict scan, phase A, lane rows
+// The same decision as candidates_kernel with each lane walking a row of 16
+// consecutive keys in order, so the field tests run once per key on one lane
+// instead of once per key on a warp-wide step.  A warp's step is 512 keys
+// (32 rows of 128 bytes), brought to shared memory by one tensor copy (TMA)
+// with the 128-byte swizzle: chunk c (16 bytes) of row r lands at chunk
+// c ^ (r & 7), so the lanes reading their rows chunk by chunk hit distinct
+// banks.  Each warp runs its own pipeline of CB_STAGES steps (one mbarrier
+// per stage), across the ranges it owns.  A warp owns the runs that start in
+// its range and reads past the range end, with plain loads, to finish its
+// last run.
+//
+// Per lane, one walk over its row keeps the flags of the sub-run (interval)
+// and the run open at each key, closes the runs that start and end inside
+// the row at once, and leaves three parts for the warp: the part before its
+// first sub-run start (pre), the sub-runs closed before its first run start,
+// and the part after its last run start (suf).  Ballots over the lanes give
+// each lane the flags carried into its row (an OR over the lanes since the
+// last start, as in candidates_kernel's steps), which close the run that
+// was open at the row's start.
+constexpr int CB_THREADS = 128, CB_STAGES = 4, CB_ROW = 16, CB_STEP = 32 * CB_ROW, CB_STEP_BYTES = CB_STEP * 8;
+constexpr int CB_RANGE = 8 * CB_STEP;
+constexpr uint32_t CB_SPIN_LIMIT = 1u << 24;
+
+struct RowCarry {
+  uint64_t prev, start;
+  bool owned, runW, runBD, runC, subW, subTD;
+};
+
+__device__ __forceinline__ void cb_mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cb_issue(uint32_t bar, uint32_t dst, const CUtensorMap* tm, uint64_t row) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(CB_STEP_BYTES) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"((int32_t)row), "r"(bar)
+      : "memory");
+}
+// bounded wait on a stage's phase; false when the limit ran out
+__device__ __forceinline__ bool cb_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t spins = 0; spins < CB_SPIN_LIMIT; ++spins) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+struct RowCtx {
+  uint64_t n, r0, r1, m_blk, m_wv, m_w, m_t, g_lim;
+  uint32_t mr_h, mr_l, ms_h, ms_l;  // run and sub-run fields (halves of ~0 << (PB + IVB), ~0 << PB)
+  const uint64_t* keys;
+  uint32_t wmask, amask;
+  bool g_all;
+  int lane;
+  unsigned below;
+  uint64_t* cand;
+  uint64_t cand_cap;
+  uint64_t* counters;
+};
+
+__device__ __forceinline__ void cb_put(const RowCtx& X, uint64_t g, uint64_t s, uint64_t e) {
+  if (g < X.cand_cap) {
+    X.cand[2 * g] = s;
+    X.cand[2 * g + 1] = e;
+  }
+}
+
+// Segmented prefix OR inside one 16-bit row half: bit p of the result is the
+// OR of f over [the last start at or before p, p]; bit 0 of each half always
+// starts a segment, so two 16-bit rows packed in one word stay apart
+// (Kogge-Stone doubling over the "continues from p - 1" mask).
+__device__ __forceinline__ uint32_t seg_or(uint32_t f, uint32_t starts) {
+  uint32_t c = ~starts & 0xfffefffeu;
+  f |= (f << 1) & c;
+  c &= c << 1;
+  f |= (f << 2) & c;
+  c &= c << 2;
+  f |= (f << 4) & c;
+  c &= c << 4;
+  f |= (f << 8) & c;
+  return f;
+}
+
+// one step of 512 keys from p on, this lane's row in k.  Bit j of the row
+// masks is key j: RS run start, SS sub-run start, W writer, TD a new thread
+// of the sub-run, BD a new block of the run (as in cand_step).
+template <bool LO32>
+__device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, const uint64_t (&k)[CB_ROW], uint64_t p) {
+  const int lane = X.lane;
+  const uint64_t i0 = p + (uint64_t)lane * CB_ROW;
+  uint64_t pk = __shfl_up_sync(FULL, k[CB_ROW - 1], 1);
+  if (lane == 0) pk = i0 == 0 ? ~k[0] : c.prev;  // the array's first key starts a run
+  const uint64_t pk0 = pk;
+  uint32_t RS = 0, SS = 0, TD = 0, BD = 0, W = 0;
+#pragma unroll
+  for (int j = 0; j < CB_ROW; ++j) {
+    const uint64_t key = k[j];
+    const uint32_t xl = (uint32_t)key ^ (uint32_t)pk, xh = (uint32_t)(key >> 32) ^ (uint32_t)(pk >> 32);
+    const bool rs = ((xh & X.mr_h) | (xl & X.mr_l)) != 0;
+    const bool ss = ((xh & X.ms_h) | (xl & X.ms_l)) != 0;
+    bool blk, wv, wp, th;
+    if (LO32) {
+      blk = (xl & (uint32_t)X.m_blk) != 0;
+      wv = (xl & (uint32_t)X.m_wv) != 0;
+      wp = (xl & (uint32_t)X.m_w) != 0;
+      th = (xl & (uint32_t)X.m_t) != 0;
+    } else {
+      const uint64_t x = ((uint64_t)xh << 32) | xl;
+      blk = (x & X.m_blk) != 0;
+      wv = (x & X.m_wv) != 0;
+      wp = (x & X.m_w) != 0;
+      th = (x & X.m_t) != 0;
+    }
+    const bool td = !ss && (blk || (wv ? wp : th));
+    const bool bd = !rs && blk;
+    const bool w = (X.wmask >> ((uint32_t)key & X.amask)) & 1u;
+    RS |= (uint32_t)rs << j;
+    SS |= (uint32_t)ss << j;
+    TD |= (uint32_t)td << j;
+    BD |= (uint32_t)bd << j;
+    W |= (uint32_t)w << j;
+    pk = key;
+  }
+  // positions past the array's end take no part
+  const uint64_t rem = i0 < X.n ? X.n - i0 : 0;
+  const uint32_t VM = rem >= (uint64_t)CB_ROW ? 0xffffu : ((1u << rem) - 1u);
+  RS &= VM;
+  SS &= VM;
+  TD &= VM;
+  BD &= VM;
+  W &= VM;
+  // global-memory runs: keys below g_lim (monotone in the sorted order)
+  uint32_t GL;
+  if (X.g_all || k[CB_ROW - 1] < X.g_lim) {
+    GL = 0xffffu;
+  } else if (k[0] >= X.g_lim) {
+    GL = 0;
+  } else {
+    GL = 0;
+#pragma unroll
+    for (int j = 0; j < CB_ROW; ++j) GL |= (uint32_t)(k[j] < X.g_lim) << j;
+  }
+  const bool gprev = X.g_all || pk0 < X.g_lim;
+  const bool seenSS = SS != 0, seenRS = RS != 0;
+  const uint32_t lt_fSS = seenSS ? (SS & (0u - SS)) - 1u : 0xffffu;  // before the first sub-run start
+  const uint32_t lt_fRS = seenRS ? (RS & (0u - RS)) - 1u : 0xffffu;  // before the first run start
+  const uint32_t ge_lSS = seenSS ? (0xffffu & ~((1u << (31 - __clz(SS))) - 1u)) : 0xffffu;  // from the last one on
+  const uint32_t ge_lRS = seenRS ? (0xffffu & ~((1u << (31 - __clz(RS))) - 1u)) : 0xffffu;
+  // sub-runs: writer and new thread so far (two rows of 16 in one word), and
+  // the ends of the sub-runs that start and end inside the row that may race
+  const uint32_t gs = seg_or(W | (TD << 16), SS | (SS << 16));
+  const uint32_t SC = gs & (gs >> 16) & (SS >> 1) & ~lt_fSS & 0xffffu;
+  // runs: writer and new block so far, and any racing sub-run so far
+  const uint32_t gr = seg_or(W | (BD << 16), RS | (RS << 16));
+  const uint32_t gc = seg_or(SC, RS);
+  // runs that start and end inside the row: ends at the positions before a run start
+  const bool rowOwned = i0 >= X.r0 && i0 < X.r1;
+  const uint32_t em = rowOwned ? ((RS >> 1) & ~lt_fRS & (gc | (GL & gr & (gr >> 16))) & 0xffffu) : 0u;
+  const bool preSW = (W & lt_fSS) != 0, preSTD = (TD & lt_fSS) != 0;
+  const bool preRW = (W & lt_fRS) != 0, preRBD = (BD & lt_fRS) != 0, preRC = (SC & lt_fRS) != 0;
+  const int fRS = seenRS ? __ffs(RS) - 1 : 0;
+  const bool preG = fRS == 0 ? gprev : ((GL >> (fRS - 1)) & 1u) != 0;
+  // flags carried into each row: OR over the lanes since the last start
+  const unsigned below = X.below;
+  const unsigned SSL = __ballot_sync(FULL, seenSS), RSL = __ballot_sync(FULL, seenRS);
+  const unsigned BSW = __ballot_sync(FULL, (W & ge_lSS) != 0), BSTD = __ballot_sync(FULL, (TD & ge_lSS) != 0);
+  const int qs = top_bit(SSL & below);
+  const unsigned rg_s = qs >= 0 ? (below & ~m_lt(qs)) : below;
+  const bool inSW = (BSW & rg_s) != 0 || (qs < 0 && c.subW);
+  const bool inSTD = (BSTD & rg_s) != 0 || (qs < 0 && c.subTD);
+  // the sub-run open at the row's start, closed inside the row
+  const bool firstSubC = seenSS && (inSW || preSW) && (inSTD || preSTD);
+  const bool sufRC = (SC & ge_lRS) != 0 || (!seenRS && firstSubC);
+  const unsigned BRW = __ballot_sync(FULL, (W & ge_lRS) != 0), BRBD = __ballot_sync(FULL, (BD & ge_lRS) != 0);
+  const unsigned BRC = __ballot_sync(FULL, sufRC);
+  const int qr = top_bit(RSL & below);
+  const unsigned rg_r = qr >= 0 ? (below & ~m_lt(qr)) : below;
+  const bool inRW = (BRW & rg_r) != 0 || (qr < 0 && c.runW);
+  const bool inRBD = (BRBD & rg_r) != 0 || (qr < 0 && c.runBD);
+  const bool inRC = (BRC & rg_r) != 0 || (qr < 0 && c.runC);
+  const uint64_t lastStart = i0 + (uint64_t)(seenRS ? 31 - __clz(RS) : 0);
+  const uint64_t srcStart = __shfl_sync(FULL, lastStart, qr >= 0 ? qr : 0);
+  const uint64_t inStart = qr >= 0 ? srcStart : c.start;
+  const bool inOwned = qr >= 0 ? (inStart >= X.r0 && inStart < X.r1) : c.owned;
+  const bool firstEmit =
+      seenRS && inOwned && (inRC || preRC || firstSubC || (preG && (inRW || preRW) && (inRBD || preRBD)));
+  // candidate entries of the step: one atomic per warp
+  const uint32_t cnt = (uint32_t)__popc(em) + (firstEmit ? 1u : 0u);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  if (total) {
+    uint64_t base = 0;
+    if (lane == 31) base = atomicAdd((unsigned long long*)&X.counters[C_NCAND], (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31) + (incl - cnt);
+    if (firstEmit) cb_put(X, base++, inStart, i0 + (uint64_t)fRS);
+    for (uint32_t m = em; m; m &= m - 1) {
+      const int e = __ffs(m) - 1;                    // the run's last key
+      const int s = 31 - __clz(RS & ((2u << e) - 1u));  // its first: the last run start at or before e
+      cb_put(X, base++, i0 + (uint64_t)s, i0 + (uint64_t)e + 1);
+    }
+  }
+  // carries for the next step: the lanes from the last start on
+  const int ql = top_bit(RSL);
+  if (ql >= 0) {
+    c.start = __shfl_sync(FULL, lastStart, ql);
+    c.owned = c.start >= X.r0 && c.start < X.r1;
+    const unsigned up = ~m_lt(ql);
+    c.runW = (BRW & up) != 0;
+    c.runBD = (BRBD & up) != 0;
+    c.runC = (BRC & up) != 0;
+  } else {
+    c.runW |= BRW != 0;
+    c.runBD |= BRBD != 0;
+    c.runC |= BRC != 0;
+  }
+  const int qsl = top_bit(SSL);
+  if (qsl >= 0) {
+    const unsigned up = ~m_lt(qsl);
+    c.subW = (BSW & up) != 0;
+    c.subTD = (BSTD & up) != 0;
+  } else {
+    c.subW |= BSW != 0;
+    c.subTD |= BSTD != 0;
+  }
+  // the step's last key
+  const uint64_t srem = X.n - p;
+  c.prev = srem >= (uint64_t)CB_STEP ? __shfl_sync(FULL, k[CB_ROW - 1], 31) : X.keys[X.n - 1];
+  // a run longer than CA_LONG goes to the exact scan with its end unknown
+  if (c.owned && p + CB_STEP - c.start > (uint64_t)CA_LONG) {
+    if (lane == 0) {
+      const uint64_t g = atomicAdd((unsigned long long*)&X.counters[C_NCAND], 1ull);
+      cb_put(X, g, c.start, 0);
+    }
+    c.owned = false;
+  }
+}
+
+__global__ void __launch_bounds__(CB_THREADS) candidates_rows_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                    const uint64_t* __restrict__ keys,
+                                                                    const uint64_t* n_dev, const DProg* __restrict__ P,
+                                                                    uint64_t* __restrict__ cand, uint64_t cand_cap,
+                                                                    uint64_t* counters) {
+  extern __shared__ __align__(16) unsigned char cbsm[];
+  __shared__ __align__(8) uint64_t bars[CB_THREADS / 32][CB_STAGES];
+  RowCtx X;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  X.lane = lane;
+  X.below = m_lt(lane);
+  X.n = *n_dev;
+  const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB, WVB = P->WVB;
+  const int rsh = PB + IVB;
+  const uint64_t m_run = rsh >= 64 ? 0 : ~0ull << rsh, m_sub = PB >= 64 ? 0 : ~0ull << PB;
+  X.mr_h = (uint32_t)(m_run >> 32);
+  X.mr_l = (uint32_t)m_run;
+  X.ms_h = (uint32_t)(m_sub >> 32);
+  X.ms_l = (uint32_t)m_sub;
+  X.keys = keys;
+  X.wmask = P->wmask;
+  X.amask = AB ? (1u << AB) - 1u : 0u;
+  X.m_blk = lowbits(~0ull, BB) << (AB + TB + WVB);
+  X.m_wv = lowbits(~0ull, WVB) << (AB + TB);
+  X.m_t = lowbits(~0ull, TB) << AB;
+  X.m_w = TB > 5 ? (lowbits(~0ull, TB - 5) << (AB + 5)) : 0ull;
+  const bool lo32 = PB <= 32;  // the block, warp-interval and thread fields sit in the low word
+  const uint64_t shbase = P->shared_cell_base;
+  X.g_all = rsh >= 64 ? shbase > 0 : (rsh > 0 && shbase >= (1ull << (64 - rsh)));
+  X.g_lim = X.g_all ? ~0ull : (rsh >= 64 ? 0ull : shbase << rsh);
+  X.cand = cand;
+  X.cand_cap = cand_cap;
+  X.counters = counters;
+  const uint64_t n = X.n;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // keys per range: CB_RANGE, fewer (whole steps) when there are few keys for the warps
+  const uint64_t want = (n + nw - 1) / nw;
+  const uint64_t range = want >= (uint64_t)CB_RANGE ? (uint64_t)CB_RANGE
+                                                    : ((want + CB_STEP - 1) / CB_STEP > 0 ? (want + CB_STEP - 1) / CB_STEP : 1) * CB_STEP;
+  const uint64_t nranges = (n + range - 1) / range;
+  if (gw >= nranges) return;
+  const uint64_t nr_w = (nranges - 1 - gw) / nw + 1;  // ranges of this warp
+  const uint64_t spr = range / CB_STEP;
+  const uint64_t last_r0 = (gw + (nr_w - 1) * nw) * range;
+  const uint64_t last_r1 = last_r0 + range < n ? last_r0 + range : n;
+  const uint64_t nq = (nr_w - 1) * spr + (last_r1 - last_r0 + CB_STEP - 1) / CB_STEP;
+  // the warp's stages: 1024-byte aligned in the shared window (the swizzle pattern repeats every 1024 bytes)
+  const uint32_t sm0 = (uint32_t)__cvta_generic_to_shared(cbsm);
+  const uint32_t buf0 = ((sm0 + 1023u) & ~1023u) + (uint32_t)wib * CB_STAGES * CB_STEP_BYTES;
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[wib][0]);
+  auto step_row = [&](uint64_t q) {  // first row of the q-th step of this warp
+    return ((gw + (q / spr) * nw) * range + (q % spr) * CB_STEP) / CB_ROW;
+  };
+  if (lane == 0) {
+    for (int s = 0; s < CB_STAGES; ++s) cb_mbar_init(bar0 + 8 * s);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int s = 0; s < CB_STAGES && (uint64_t)s < nq; ++s)
+      cb_issue(bar0 + 8 * s, buf0 + s * CB_STEP_BYTES, &tmap, step_row(s));
+  }
+  __syncwarp();
+  bool failed = false;
+  uint64_t q = 0;
+  const uint32_t swz = (uint32_t)(lane & 7);
+  for (uint64_t m = 0; m < nr_w && !failed; ++m) {
+    X.r0 = (gw + m * nw) * range;
+    X.r1 = X.r0 + range < n ? X.r0 + range : n;
+    RowCarry c;
+    c.prev = X.r0 > 0 ? keys[X.r0 - 1] : 0;
+    c.start = 0;
+    c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
+    uint64_t p = X.r0;
+    for (; p < X.r1; p += CB_STEP, ++q) {
+      const int st = (int)(q % CB_STAGES);
+      if (!cb_wait(bar0 + 8 * st, (uint32_t)((q / CB_STAGES) & 1))) {
+        failed = true;
+        break;
+      }
+      uint64_t k[CB_ROW];
+      const uint32_t row = buf0 + st * CB_STEP_BYTES + (uint32_t)lane * 128u;
+#pragma unroll
+      for (int ch = 0; ch < CB_ROW / 2; ++ch)
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
+                     : "=l"(k[2 * ch]), "=l"(k[2 * ch + 1])
+                     : "r"(row + ((((uint32_t)ch) ^ swz) << 4)));
+      if (lo32) row_step<true>(X, c, k, p);
+      else row_step<false>(X, c, k, p);
+      // the stage is free again (its keys are consumed): the step CB_STAGES ahead
+      __syncwarp();
+      if (lane == 0 && q + CB_STAGES < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        cb_issue(bar0 + 8 * st, buf0 + st * CB_STEP_BYTES, &tmap, step_row(q + CB_STAGES));
+      }
+    }
+    if (failed) break;
+    // past the range: plain loads until the warp's last run ends
+    for (; c.owned && p < n; p += CB_STEP) {
+      uint64_t k[CB_ROW];
+      const uint64_t r = p + (uint64_t)lane * CB_ROW;
+#pragma unroll
+      for (int j = 0; j < CB_ROW; ++j) k[j] = r + j < n ? keys[r + j] : 0;
+      if (lo32) row_step<true>(X, c, k, p);
+      else row_step<false>(X, c, k, p);
+    }
+    if (c.owned && p >= n && lane == 0) {  // the array ended inside a run of this warp
+      const bool last = c.runC || (c.subW && c.subTD) || ((X.g_all || c.prev < X.g_lim) && c.runW && c.runBD);
+      if (last) {
+        const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
+        cb_put(X, g, c.start, n);
+      }
+    }
+  }
+  if (failed) {
+    if (lane == 0) atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_TIMEOUT);
+    // copies still in flight land before the CTA leaves (each wait bounded)
+    for (uint64_t r = q; r < nq && r < q + CB_STAGES; ++r)
+      if (!cb_wait(bar0 + 8 * (int)(r % CB_STAGES), (uint32_t)((r / CB_STAGES) & 1))) break;
+  }
+}
+
 // ------------------------------------------------------------------ conflict scan, phase B
 // Exact kinds of one candidate bin of the block-local mode: keys [s, e) of one
 // shared granule, one interval and one block, in any order.  Lane = access a:
@@ -1575,10 +1944,52 @@ cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out,
   return cudaGetLastError();
 }
 
-cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
-                              uint64_t* cand, uint64_t cand_cap, uint64_t* counters) {
-  int grid = occupancy_grid((const void*)candidates_kernel, CA_THREADS, 0, L.nsm);
-  candidates_kernel<<<grid, CA_THREADS, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, counters);
+namespace {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependence on the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+// the key buffer as rows of 16 keys (128 B), boxes of 32 rows, 128-byte swizzle
+bool key_rows_map(CUtensorMap* tm, const uint64_t* keys, uint64_t key_cap) {
+  EncodeTiledFn enc = encode_tiled();
+  const uint64_t rows = key_cap / CB_ROW;
+  if (!enc || rows == 0 || rows > (1ull << 31) || (reinterpret_cast<uintptr_t>(keys) & 127u)) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)CB_ROW, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)CB_ROW * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)CB_ROW, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(keys), dim, stride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, uint64_t key_cap, const uint64_t* n_dev,
+                              const DProg* d_prog, uint64_t* cand, uint64_t cand_cap, uint64_t* counters,
+                              bool ballot) {
+  CUtensorMap tm;
+  if (!ballot && key_rows_map(&tm, keys, key_cap)) {
+    const size_t smem = (size_t)(CB_THREADS / 32) * CB_STAGES * CB_STEP_BYTES + 1024;
+    cudaError_t e = allow_smem((const void*)candidates_rows_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = occupancy_grid((const void*)candidates_rows_kernel, CB_THREADS, smem, L.nsm);
+    candidates_rows_kernel<<<grid, CB_THREADS, smem, L.s>>>(tm, keys, n_dev, d_prog, cand, cand_cap, counters);
+  } else {
+    const int grid = occupancy_grid((const void*)candidates_kernel, CA_THREADS, 0, L.nsm);
+    candidates_kernel<<<grid, CA_THREADS, 0, L.s>>>(keys, n_dev, d_prog, cand, cand_cap, counters);
+  }
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -65,9 +65,12 @@ uint64_t sort_variant_key();
 cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
                              int shift0, int npass, uint64_t* done);
 
-// conflict scan, phase A: runs that may hold a race -> (start, end) list
-cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
-                              uint64_t* cand, uint64_t cand_cap, uint64_t* counters);
+// conflict scan, phase A: runs that may hold a race -> (start, end) list.
+// keys holds key_cap words (a multiple of 16 for the row form, which reads
+// whole rows of 16 keys); ballot = the 32-key warp-step form
+cudaError_t launch_candidates(const Launch& L, const uint64_t* keys, uint64_t key_cap, const uint64_t* n_dev,
+                              const DProg* d_prog, uint64_t* cand, uint64_t cand_cap, uint64_t* counters,
+                              bool ballot = false);
 // conflict scan, phase B: exact per-access summaries -> packed raw witnesses
 cudaError_t launch_exact(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                          const uint64_t* cand, uint64_t cand_cap, uint64_t* raw, uint64_t raw_cap,

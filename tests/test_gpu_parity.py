@@ -53,6 +53,9 @@ def _both(text, binding, cap=1 << 20, **kw):
     g3 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL | hg.CELL_FILTER, **kw)
     g4 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL | hg.NO_CELL_FILTER, **kw)
     assert g3 == g and g4 == g
+    # the first scan phase as 32-key warp steps instead of tensor-copied rows
+    g5 = hg.check(text, binding, cap=cap, flags=flags | hg.NO_SMALL | hg.SCAN_BALLOT, **kw)
+    assert g5 == g
     o = oracle.check(text, binding, cap=cap)
     return g, o
 
@@ -572,6 +575,7 @@ def test_every_key_through_the_sort(seed):
     st = hg.stats()
     assert st["shared_bins"] == 0 and st["jit"] == 0 and st["small"] == 0
     _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+    assert hg.check(w.text, w.binding, cap=1 << 20, flags=hg.ALL_KEYS | hg.SCAN_BALLOT) == g
 
 
 def test_every_key_through_the_sort_on_the_stencil():
@@ -579,6 +583,7 @@ def test_every_key_through_the_sort_on_the_stencil():
     g = hg.check(w.text, w.binding, cap=1 << 20, flags=hg.ALL_KEYS | hg.NO_CELL_FILTER)
     assert hg.stats()["n_sorted_keys"] == g.n_keys  # every live key went through the sort
     _same(g, oracle.check(w.text, w.binding, cap=1 << 20))
+    assert hg.check(w.text, w.binding, cap=1 << 20, flags=hg.ALL_KEYS | hg.NO_CELL_FILTER | hg.SCAN_BALLOT) == g
 
 
 def test_sort_shapes_chosen_per_pass():
