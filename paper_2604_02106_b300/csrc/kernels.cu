@@ -1042,26 +1042,27 @@ __global__ void __launch_bounds__(CA_THREADS, 2) candidates_kernel(const uint64_
 }
 
 // ------------------------------------------------------------------ conflict scan, phase A, lane rows
-// The same decision as candidates_kernel with each lane walking a row of 16
-// consecutive keys in order, so the field tests run once per key on one lane
-// instead of once per key on a warp-wide step.  A warp's step is 512 keys
-// (32 rows of 128 bytes), brought to shared memory by one tensor copy (TMA)
-// with the 128-byte swizzle: chunk c (16 bytes) of row r lands at chunk
-// c ^ (r & 7), so the lanes reading their rows chunk by chunk hit distinct
-// banks.  Each warp runs its own pipeline of CB_STAGES steps (one mbarrier
-// per stage), across the ranges it owns.  A warp owns the runs that start in
-// its range and reads past the range end, with plain loads, to finish its
-// last run.
+// The same decision as candidates_kernel with each lane walking a row of 32
+// consecutive keys, so the field tests run once per key on one lane instead
+// of once per key on a warp-wide step.  A warp's step is 1024 keys (64 tile
+// rows of 16 keys, 128 bytes each), brought to shared memory by one tensor
+// copy (TMA) with the 128-byte swizzle: chunk c (16 bytes) of tile row r
+// lands at chunk c ^ (r & 7).  Each warp runs its own pipeline of CB_STAGES
+// steps (one mbarrier per stage) across the ranges it owns.  A warp owns the
+// runs that start in its range and reads past the range end, with plain
+// loads, to finish its last run.
 //
-// Per lane, one walk over its row keeps the flags of the sub-run (interval)
-// and the run open at each key, closes the runs that start and end inside
-// the row at once, and leaves three parts for the warp: the part before its
-// first sub-run start (pre), the sub-runs closed before its first run start,
-// and the part after its last run start (suf).  Ballots over the lanes give
-// each lane the flags carried into its row (an OR over the lanes since the
-// last start, as in candidates_kernel's steps), which close the run that
-// was open at the row's start.
-constexpr int CB_THREADS = 128, CB_STAGES = 4, CB_ROW = 16, CB_STEP = 32 * CB_ROW, CB_STEP_BYTES = CB_STEP * 8;
+// Per lane, the flags of its 32 keys become bit masks (bit j = key j: run
+// start, sub-run start, writer, a new thread of the sub-run, a new block of
+// the run, as in cand_step); segmented prefix ORs over the masks close the
+// runs that start and end inside the row at once, and leave three parts for
+// the warp: the part before the row's first sub-run start, the sub-runs
+// closed before its first run start, and the part after its last run start.
+// Ballots over the lanes give each lane the flags carried into its row (an
+// OR over the lanes since the last start, as in candidates_kernel's steps),
+// which close the run that was open at the row's start.
+constexpr int CB_THREADS = 128, CB_STAGES = 2, CB_ROW = 32, CB_STEP = 32 * CB_ROW, CB_STEP_BYTES = CB_STEP * 8;
+constexpr int CB_TILE_ROW = 16;  // keys per 128-byte tile row of the tensor copy
 constexpr int CB_RANGE = 8 * CB_STEP;
 constexpr uint32_t CB_SPIN_LIMIT = 1u << 24;
 
@@ -1096,9 +1097,11 @@ __device__ __forceinline__ bool cb_wait(uint32_t bar, uint32_t parity) {
 
 struct RowCtx {
   uint64_t n, r0, r1, m_blk, m_wv, m_w, m_t, g_lim;
+  int rsh;                          // run code: key >> rsh
   uint32_t mr_h, mr_l, ms_h, ms_l;  // run and sub-run fields (halves of ~0 << (PB + IVB), ~0 << PB)
+  uint32_t m_bt;                    // block and thread fields (low word)
   const uint64_t* keys;
-  uint32_t wmask, amask;
+  uint32_t wrep;  // writer bit of each access id, repeated every 2^AB bits over the word
   bool g_all;
   int lane;
   unsigned below;
@@ -1114,12 +1117,11 @@ __device__ __forceinline__ void cb_put(const RowCtx& X, uint64_t g, uint64_t s, 
   }
 }
 
-// Segmented prefix OR inside one 16-bit row half: bit p of the result is the
-// OR of f over [the last start at or before p, p]; bit 0 of each half always
-// starts a segment, so two 16-bit rows packed in one word stay apart
+// Segmented prefix OR over a row: bit p of the result is the OR of f over
+// [the last start at or before p, p], bit 0 always starting a segment
 // (Kogge-Stone doubling over the "continues from p - 1" mask).
 __device__ __forceinline__ uint32_t seg_or(uint32_t f, uint32_t starts) {
-  uint32_t c = ~starts & 0xfffefffeu;
+  uint32_t c = ~starts & 0xfffffffeu;
   f |= (f << 1) & c;
   c &= c << 1;
   f |= (f << 2) & c;
@@ -1127,84 +1129,166 @@ __device__ __forceinline__ uint32_t seg_or(uint32_t f, uint32_t starts) {
   f |= (f << 4) & c;
   c &= c << 4;
   f |= (f << 8) & c;
+  c &= c << 8;
+  f |= (f << 16) & c;
   return f;
 }
 
-// one step of 512 keys from p on, this lane's row in k.  Bit j of the row
-// masks is key j: RS run start, SS sub-run start, W writer, TD a new thread
-// of the sub-run, BD a new block of the run (as in cand_step).
-template <bool LO32>
-__device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, const uint64_t (&k)[CB_ROW], uint64_t p) {
-  const int lane = X.lane;
-  const uint64_t i0 = p + (uint64_t)lane * CB_ROW;
-  uint64_t pk = __shfl_up_sync(FULL, k[CB_ROW - 1], 1);
-  if (lane == 0) pk = i0 == 0 ? ~k[0] : c.prev;  // the array's first key starts a run
-  const uint64_t pk0 = pk;
-  uint32_t RS = 0, SS = 0, TD = 0, BD = 0, W = 0;
+// Flags of 16 keys (k, the key before them pk) into bits sh .. sh + 15 of the
+// row masks.  FORM 2: the run code starts in the low word (PB + IVB <= 32) and
+// there are no warp intervals; FORM 1: the block, warp-interval and thread
+// fields sit in the low word (PB <= 32); FORM 0: any layout.
+template <int FORM>
+__device__ __forceinline__ void row_flags(const RowCtx& X, const uint64_t (&k)[CB_TILE_ROW], uint64_t& pk, int sh,
+                                          uint32_t& RS, uint32_t& SS, uint32_t& TD, uint32_t& BD, uint32_t& W) {
 #pragma unroll
-  for (int j = 0; j < CB_ROW; ++j) {
+  for (int j = 0; j < CB_TILE_ROW; ++j) {
     const uint64_t key = k[j];
     const uint32_t xl = (uint32_t)key ^ (uint32_t)pk, xh = (uint32_t)(key >> 32) ^ (uint32_t)(pk >> 32);
-    const bool rs = ((xh & X.mr_h) | (xl & X.mr_l)) != 0;
-    const bool ss = ((xh & X.ms_h) | (xl & X.ms_l)) != 0;
-    bool blk, wv, wp, th;
-    if (LO32) {
-      blk = (xl & (uint32_t)X.m_blk) != 0;
-      wv = (xl & (uint32_t)X.m_wv) != 0;
-      wp = (xl & (uint32_t)X.m_w) != 0;
-      th = (xl & (uint32_t)X.m_t) != 0;
+    // writer: bit (key mod 32) of the writer bits repeated every 2^AB places
+    const uint32_t wr = __funnelshift_r(X.wrep, X.wrep, (uint32_t)key) & 1u;
+    const uint32_t bit = 1u << (sh + j);
+    if (FORM == 2) {
+      // each flag a predicate that sets its bit by a predicated OR
+      const uint32_t rv = xh | (xl & X.mr_l), sv = xh | (xl & X.ms_l);
+      asm("{\n\t.reg .pred prs, pss, ptd, pbd, pw;\n\t"
+          "setp.ne.u32 prs, %5, 0;\n\t"
+          "setp.ne.u32 pss, %6, 0;\n\t"
+          "setp.ne.and.u32 ptd, %7, 0, !pss;\n\t"
+          "setp.ne.and.u32 pbd, %8, 0, !prs;\n\t"
+          "setp.ne.u32 pw, %9, 0;\n\t"
+          "@prs or.b32 %0, %0, %10;\n\t"
+          "@pss or.b32 %1, %1, %10;\n\t"
+          "@ptd or.b32 %2, %2, %10;\n\t"
+          "@pbd or.b32 %3, %3, %10;\n\t"
+          "@pw or.b32 %4, %4, %10;\n\t}"
+          : "+r"(RS), "+r"(SS), "+r"(TD), "+r"(BD), "+r"(W)
+          : "r"(rv), "r"(sv), "r"(xl & X.m_bt), "r"(xl & (uint32_t)X.m_blk), "r"(wr), "r"(bit));
     } else {
-      const uint64_t x = ((uint64_t)xh << 32) | xl;
-      blk = (x & X.m_blk) != 0;
-      wv = (x & X.m_wv) != 0;
-      wp = (x & X.m_w) != 0;
-      th = (x & X.m_t) != 0;
+      bool rs, ss, blk, wv, wp, th;
+      rs = ((xh & X.mr_h) | (xl & X.mr_l)) != 0;
+      ss = ((xh & X.ms_h) | (xl & X.ms_l)) != 0;
+      if (FORM == 1) {
+        blk = (xl & (uint32_t)X.m_blk) != 0;
+        wv = (xl & (uint32_t)X.m_wv) != 0;
+        wp = (xl & (uint32_t)X.m_w) != 0;
+        th = (xl & (uint32_t)X.m_t) != 0;
+      } else {
+        const uint64_t x = ((uint64_t)xh << 32) | xl;
+        blk = (x & X.m_blk) != 0;
+        wv = (x & X.m_wv) != 0;
+        wp = (x & X.m_w) != 0;
+        th = (x & X.m_t) != 0;
+      }
+      const bool td = !ss && (blk || (wv ? wp : th));
+      const bool bd = !rs && blk;
+      if (rs) RS |= bit;
+      if (ss) SS |= bit;
+      if (td) TD |= bit;
+      if (bd) BD |= bit;
+      if (wr) W |= bit;
     }
-    const bool td = !ss && (blk || (wv ? wp : th));
-    const bool bd = !rs && blk;
-    const bool w = (X.wmask >> ((uint32_t)key & X.amask)) & 1u;
-    RS |= (uint32_t)rs << j;
-    SS |= (uint32_t)ss << j;
-    TD |= (uint32_t)td << j;
-    BD |= (uint32_t)bd << j;
-    W |= (uint32_t)w << j;
     pk = key;
   }
-  // positions past the array's end take no part
-  const uint64_t rem = i0 < X.n ? X.n - i0 : 0;
-  const uint32_t VM = rem >= (uint64_t)CB_ROW ? 0xffffu : ((1u << rem) - 1u);
-  RS &= VM;
-  SS &= VM;
-  TD &= VM;
-  BD &= VM;
-  W &= VM;
+}
+
+// One step of the keys [p, p + lim) (lim <= CB_STEP; lane l's row starts at
+// p + 32 l): the rows come from the step's shared-memory tile rows at srow,
+// or from global memory (srow = ~0), and are flagged, closed and carried.
+// own: the step lies inside the warp's range (every run starting in it
+// belongs to the warp).
+template <int FORM>
+__device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, uint32_t srow, uint64_t p, bool own,
+                                         uint32_t lim) {
+  const int lane = X.lane;
+  const bool full = lim == (uint32_t)CB_STEP;
+  const uint64_t end = p + lim;
+  const uint64_t i0 = p + (uint64_t)lane * CB_ROW;
+  uint64_t pk;
+  uint32_t RS = 0, SS = 0, TD = 0, BD = 0, W = 0;
+  uint64_t klast, kfirst;
+  {
+    // the key before the row: the last one of the lane before (lane 0: the carry)
+    uint64_t prevk = 0;
+    if (srow != 0xffffffffu) {
+      if (lane > 0) {
+        const uint32_t r = 2 * lane - 1;
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(prevk) : "r"(srow + r * 128u + (((7u ^ (r & 7u)) << 4) | 8u)));
+      }
+    } else if (lane > 0 && i0 < end) {
+      prevk = X.keys[i0 - 1];
+    }
+    pk = lane == 0 ? (i0 == 0 ? ~0ull : c.prev) : prevk;
+  }
+  const uint64_t pk0 = pk;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint64_t k[CB_TILE_ROW];
+    if (srow != 0xffffffffu) {
+      const uint32_t r = 2 * (uint32_t)lane + h;
+      const uint32_t base = srow + r * 128u;
+#pragma unroll
+      for (int ch = 0; ch < CB_TILE_ROW / 2; ++ch)
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
+                     : "=l"(k[2 * ch]), "=l"(k[2 * ch + 1])
+                     : "r"(base + ((((uint32_t)ch) ^ (r & 7u)) << 4)));
+    } else {
+      const uint64_t r = i0 + (uint64_t)h * CB_TILE_ROW;
+#pragma unroll
+      for (int j = 0; j < CB_TILE_ROW; ++j) k[j] = r + j < end ? X.keys[r + j] : 0;
+    }
+    if (h == 0) {
+      kfirst = k[0];
+      if (i0 == 0) pk = ~k[0];  // the array's first key starts a run
+    }
+    row_flags<FORM>(X, k, pk, 16 * h, RS, SS, TD, BD, W);
+    if (h == 1) klast = k[CB_TILE_ROW - 1];
+  }
+  if (!full) {  // positions past the array's end take no part
+    const uint64_t rem = i0 < end ? end - i0 : 0;
+    const uint32_t VM = rem >= (uint64_t)CB_ROW ? 0xffffffffu : ((1u << rem) - 1u);
+    RS &= VM;
+    SS &= VM;
+    TD &= VM;
+    BD &= VM;
+    W &= VM;
+  }
   // global-memory runs: keys below g_lim (monotone in the sorted order)
   uint32_t GL;
-  if (X.g_all || k[CB_ROW - 1] < X.g_lim) {
-    GL = 0xffffu;
-  } else if (k[0] >= X.g_lim) {
+  if (X.g_all || klast < X.g_lim) {
+    GL = 0xffffffffu;
+  } else if (kfirst >= X.g_lim) {
     GL = 0;
-  } else {
+  } else {  // the row crosses into the shared arrays: find where
     GL = 0;
-#pragma unroll
-    for (int j = 0; j < CB_ROW; ++j) GL |= (uint32_t)(k[j] < X.g_lim) << j;
+    for (int j = 0; j < CB_ROW; ++j) {
+      const uint64_t kj = srow != 0xffffffffu
+                              ? 0
+                              : (i0 + j < end ? X.keys[i0 + j] : ~0ull);
+      uint64_t ks = kj;
+      if (srow != 0xffffffffu) {
+        const uint32_t r = 2 * (uint32_t)lane + (j >> 4), ch = (uint32_t)(j & 15) >> 1;
+        asm volatile("ld.shared.u64 %0, [%1];"
+                     : "=l"(ks)
+                     : "r"(srow + r * 128u + (((ch ^ (r & 7u)) << 4) | (uint32_t)((j & 1) << 3))));
+      }
+      if (ks < X.g_lim) GL |= 1u << j;
+    }
   }
   const bool gprev = X.g_all || pk0 < X.g_lim;
   const bool seenSS = SS != 0, seenRS = RS != 0;
-  const uint32_t lt_fSS = seenSS ? (SS & (0u - SS)) - 1u : 0xffffu;  // before the first sub-run start
-  const uint32_t lt_fRS = seenRS ? (RS & (0u - RS)) - 1u : 0xffffu;  // before the first run start
-  const uint32_t ge_lSS = seenSS ? (0xffffu & ~((1u << (31 - __clz(SS))) - 1u)) : 0xffffu;  // from the last one on
-  const uint32_t ge_lRS = seenRS ? (0xffffu & ~((1u << (31 - __clz(RS))) - 1u)) : 0xffffu;
-  // sub-runs: writer and new thread so far (two rows of 16 in one word), and
-  // the ends of the sub-runs that start and end inside the row that may race
-  const uint32_t gs = seg_or(W | (TD << 16), SS | (SS << 16));
-  const uint32_t SC = gs & (gs >> 16) & (SS >> 1) & ~lt_fSS & 0xffffu;
-  // runs: writer and new block so far, and any racing sub-run so far
-  const uint32_t gr = seg_or(W | (BD << 16), RS | (RS << 16));
-  const uint32_t gc = seg_or(SC, RS);
-  // runs that start and end inside the row: ends at the positions before a run start
-  const bool rowOwned = i0 >= X.r0 && i0 < X.r1;
-  const uint32_t em = rowOwned ? ((RS >> 1) & ~lt_fRS & (gc | (GL & gr & (gr >> 16))) & 0xffffu) : 0u;
+  const uint32_t lt_fSS = seenSS ? (SS & (0u - SS)) - 1u : 0xffffffffu;  // before the first sub-run start
+  const uint32_t lt_fRS = seenRS ? (RS & (0u - RS)) - 1u : 0xffffffffu;  // before the first run start
+  const int lRS = seenRS ? 31 - __clz(RS) : 0;
+  const uint32_t ge_lSS = seenSS ? ~((1u << (31 - __clz(SS))) - 1u) : 0xffffffffu;  // from the last one on
+  const uint32_t ge_lRS = seenRS ? ~((1u << lRS) - 1u) : 0xffffffffu;
+  // sub-runs: writer and new thread so far, and the ends of the sub-runs that
+  // start and end inside the row that may race
+  const uint32_t SC = seg_or(W, SS) & seg_or(TD, SS) & (SS >> 1) & ~lt_fSS;
+  // runs: writer and new block so far, and any racing sub-run so far; runs
+  // that start and end inside the row end at the positions before a run start
+  const uint32_t em =
+      own ? ((RS >> 1) & ~lt_fRS & (seg_or(SC, RS) | (GL & seg_or(W, RS) & seg_or(BD, RS)))) : 0u;
   const bool preSW = (W & lt_fSS) != 0, preSTD = (TD & lt_fSS) != 0;
   const bool preRW = (W & lt_fRS) != 0, preRBD = (BD & lt_fRS) != 0, preRC = (SC & lt_fRS) != 0;
   const int fRS = seenRS ? __ffs(RS) - 1 : 0;
@@ -1227,28 +1311,19 @@ __device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, const uin
   const bool inRW = (BRW & rg_r) != 0 || (qr < 0 && c.runW);
   const bool inRBD = (BRBD & rg_r) != 0 || (qr < 0 && c.runBD);
   const bool inRC = (BRC & rg_r) != 0 || (qr < 0 && c.runC);
-  const uint64_t lastStart = i0 + (uint64_t)(seenRS ? 31 - __clz(RS) : 0);
-  const uint64_t srcStart = __shfl_sync(FULL, lastStart, qr >= 0 ? qr : 0);
-  const uint64_t inStart = qr >= 0 ? srcStart : c.start;
-  const bool inOwned = qr >= 0 ? (inStart >= X.r0 && inStart < X.r1) : c.owned;
+  const uint32_t lastOff = (uint32_t)lane * CB_ROW + (uint32_t)lRS;  // the last run start, from p
+  const uint32_t srcOff = __shfl_sync(FULL, lastOff, qr >= 0 ? qr : 0);
+  const uint64_t inStart = qr >= 0 ? p + srcOff : c.start;
+  const bool inOwned = qr >= 0 ? own : c.owned;
   const bool firstEmit =
       seenRS && inOwned && (inRC || preRC || firstSubC || (preG && (inRW || preRW) && (inRBD || preRBD)));
-  // candidate entries of the step: one atomic per warp
+  // candidate entries: one atomic per lane that has any
   const uint32_t cnt = (uint32_t)__popc(em) + (firstEmit ? 1u : 0u);
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(FULL, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const uint32_t total = __shfl_sync(FULL, incl, 31);
-  if (total) {
-    uint64_t base = 0;
-    if (lane == 31) base = atomicAdd((unsigned long long*)&X.counters[C_NCAND], (unsigned long long)total);
-    base = __shfl_sync(FULL, base, 31) + (incl - cnt);
+  if (cnt) {
+    uint64_t base = atomicAdd((unsigned long long*)&X.counters[C_NCAND], (unsigned long long)cnt);
     if (firstEmit) cb_put(X, base++, inStart, i0 + (uint64_t)fRS);
     for (uint32_t m = em; m; m &= m - 1) {
-      const int e = __ffs(m) - 1;                    // the run's last key
+      const int e = __ffs(m) - 1;                       // the run's last key
       const int s = 31 - __clz(RS & ((2u << e) - 1u));  // its first: the last run start at or before e
       cb_put(X, base++, i0 + (uint64_t)s, i0 + (uint64_t)e + 1);
     }
@@ -1256,8 +1331,8 @@ __device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, const uin
   // carries for the next step: the lanes from the last start on
   const int ql = top_bit(RSL);
   if (ql >= 0) {
-    c.start = __shfl_sync(FULL, lastStart, ql);
-    c.owned = c.start >= X.r0 && c.start < X.r1;
+    c.start = p + __shfl_sync(FULL, lastOff, ql);
+    c.owned = own;
     const unsigned up = ~m_lt(ql);
     c.runW = (BRW & up) != 0;
     c.runBD = (BRBD & up) != 0;
@@ -1277,15 +1352,114 @@ __device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, const uin
     c.subTD |= BSTD != 0;
   }
   // the step's last key
-  const uint64_t srem = X.n - p;
-  c.prev = srem >= (uint64_t)CB_STEP ? __shfl_sync(FULL, k[CB_ROW - 1], 31) : X.keys[X.n - 1];
+  c.prev = full ? __shfl_sync(FULL, klast, 31) : X.keys[end - 1];
   // a run longer than CA_LONG goes to the exact scan with its end unknown
-  if (c.owned && p + CB_STEP - c.start > (uint64_t)CA_LONG) {
+  if (c.owned && end - c.start > (uint64_t)CA_LONG) {
     if (lane == 0) {
       const uint64_t g = atomicAdd((unsigned long long*)&X.counters[C_NCAND], 1ull);
       cb_put(X, g, c.start, 0);
     }
     c.owned = false;
+  }
+}
+
+template <int FORM>
+__device__ __forceinline__ void scan_ranges(const CUtensorMap* tmap, RowCtx& X, uint64_t gw, uint64_t nw,
+                                            uint64_t range, uint64_t nr_w, uint32_t buf0, uint32_t bar0,
+                                            uint64_t* counters) {
+  const int lane = X.lane;
+  const uint64_t n = X.n;
+  const uint32_t spr = (uint32_t)(range / CB_STEP);
+  const uint64_t last_r0 = (gw + (nr_w - 1) * nw) * range;
+  const uint64_t last_r1 = last_r0 + range < n ? last_r0 + range : n;
+  const uint64_t nq = (nr_w - 1) * spr + (last_r1 - last_r0 + CB_STEP - 1) / CB_STEP;  // steps of this warp
+  // the producer walks the same step sequence CB_STAGES steps ahead: first
+  // tile row of the next step to load, and its place in its range
+  uint64_t nrow = gw * range / CB_TILE_ROW, nrange_row = nrow;
+  uint32_t nstep = 0;
+  auto advance = [&]() {
+    if (++nstep == spr) {
+      nstep = 0;
+      nrange_row += nw * range / CB_TILE_ROW;
+      nrow = nrange_row;
+    } else {
+      nrow += CB_STEP / CB_TILE_ROW;
+    }
+  };
+  if (lane == 0) {
+    for (int s = 0; s < CB_STAGES; ++s) cb_mbar_init(bar0 + 8 * s);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  uint64_t issued = 0;
+  for (; issued < CB_STAGES && issued < nq; ++issued) {
+    if (lane == 0) cb_issue(bar0 + 8 * (uint32_t)issued, buf0 + (uint32_t)issued * CB_STEP_BYTES, tmap, nrow);
+    advance();
+  }
+  __syncwarp();
+  bool failed = false;
+  uint64_t q = 0;
+  for (uint64_t m = 0; m < nr_w && !failed; ++m) {
+    X.r0 = (gw + m * nw) * range;
+    X.r1 = X.r0 + range < n ? X.r0 + range : n;
+    RowCarry c;
+    c.prev = X.r0 > 0 ? X.keys[X.r0 - 1] : 0;
+    c.start = 0;
+    c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
+    uint64_t p = X.r0;
+    for (; p < X.r1; p += CB_STEP, ++q) {
+      const uint32_t st = (uint32_t)q % CB_STAGES;
+      if (!cb_wait(bar0 + 8 * st, (uint32_t)(q / CB_STAGES) & 1u)) {
+        failed = true;
+        break;
+      }
+      const uint32_t srow = buf0 + st * CB_STEP_BYTES;
+      row_step<FORM>(X, c, srow, p, true, p + CB_STEP <= n ? (uint32_t)CB_STEP : (uint32_t)(n - p));
+      // the stage is free again (its keys are consumed): the step CB_STAGES ahead
+      __syncwarp();
+      if (issued < nq) {
+        if (lane == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          cb_issue(bar0 + 8 * st, buf0 + st * CB_STEP_BYTES, tmap, nrow);
+        }
+        ++issued;
+        advance();
+      }
+    }
+    if (failed) break;
+    if (!c.owned) continue;
+    // past the range: the warp's last run ends at e, the first key of another
+    // run (found 32 keys at a time), or at the array's end; its keys past the
+    // range are flagged with plain loads, then the run is closed
+    uint64_t e = p;
+    bool found = false;
+    const uint64_t rid = shr64(c.prev, X.rsh);
+    while (!found && e < n && e - c.start <= (uint64_t)CA_LONG) {
+      const uint64_t i = e + (uint64_t)lane;
+      const unsigned other = __ballot_sync(FULL, i < n && shr64(X.keys[i], X.rsh) != rid);
+      if (other) {
+        e += (uint64_t)(__ffs(other) - 1);
+        found = true;
+      } else {
+        e = e + 32 < n ? e + 32 : n;
+      }
+    }
+    for (; c.owned && p < e; p += CB_STEP)
+      row_step<FORM>(X, c, 0xffffffffu, p, false, p + CB_STEP <= e ? (uint32_t)CB_STEP : (uint32_t)(e - p));
+    if (c.owned && lane == 0) {
+      if (!found && e < n) {  // longer than CA_LONG: the exact scan finds the end
+        const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
+        cb_put(X, g, c.start, 0);
+      } else if (c.runC || (c.subW && c.subTD) || ((X.g_all || c.prev < X.g_lim) && c.runW && c.runBD)) {
+        const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
+        cb_put(X, g, c.start, e);
+      }
+    }
+  }
+  if (failed) {
+    if (lane == 0) atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_TIMEOUT);
+    // copies still in flight land before the CTA leaves (each wait bounded)
+    for (uint64_t r = q; r < issued; ++r)
+      if (!cb_wait(bar0 + 8 * (uint32_t)(r % CB_STAGES), (uint32_t)(r / CB_STAGES) & 1u)) break;
   }
 }
 
@@ -1304,18 +1478,19 @@ __global__ void __launch_bounds__(CB_THREADS) candidates_rows_kernel(const __gri
   const int PB = P->PB, IVB = P->IVB, AB = P->AB, TB = P->TB, BB = P->BB, WVB = P->WVB;
   const int rsh = PB + IVB;
   const uint64_t m_run = rsh >= 64 ? 0 : ~0ull << rsh, m_sub = PB >= 64 ? 0 : ~0ull << PB;
+  X.rsh = rsh;
   X.mr_h = (uint32_t)(m_run >> 32);
   X.mr_l = (uint32_t)m_run;
   X.ms_h = (uint32_t)(m_sub >> 32);
   X.ms_l = (uint32_t)m_sub;
   X.keys = keys;
-  X.wmask = P->wmask;
-  X.amask = AB ? (1u << AB) - 1u : 0u;
+  X.wrep = P->wmask;
+  for (int sh = 1 << AB; sh < 32; sh <<= 1) X.wrep |= X.wrep << sh;
   X.m_blk = lowbits(~0ull, BB) << (AB + TB + WVB);
   X.m_wv = lowbits(~0ull, WVB) << (AB + TB);
   X.m_t = lowbits(~0ull, TB) << AB;
   X.m_w = TB > 5 ? (lowbits(~0ull, TB - 5) << (AB + 5)) : 0ull;
-  const bool lo32 = PB <= 32;  // the block, warp-interval and thread fields sit in the low word
+  X.m_bt = (uint32_t)(X.m_blk | X.m_t);
   const uint64_t shbase = P->shared_cell_base;
   X.g_all = rsh >= 64 ? shbase > 0 : (rsh > 0 && shbase >= (1ull << (64 - rsh)));
   X.g_lim = X.g_all ? ~0ull : (rsh >= 64 ? 0ull : shbase << rsh);
@@ -1327,86 +1502,19 @@ __global__ void __launch_bounds__(CB_THREADS) candidates_rows_kernel(const __gri
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   // keys per range: CB_RANGE, fewer (whole steps) when there are few keys for the warps
   const uint64_t want = (n + nw - 1) / nw;
-  const uint64_t range = want >= (uint64_t)CB_RANGE ? (uint64_t)CB_RANGE
-                                                    : ((want + CB_STEP - 1) / CB_STEP > 0 ? (want + CB_STEP - 1) / CB_STEP : 1) * CB_STEP;
+  const uint64_t range = want >= (uint64_t)CB_RANGE
+                             ? (uint64_t)CB_RANGE
+                             : ((want + CB_STEP - 1) / CB_STEP > 0 ? (want + CB_STEP - 1) / CB_STEP : 1) * CB_STEP;
   const uint64_t nranges = (n + range - 1) / range;
   if (gw >= nranges) return;
   const uint64_t nr_w = (nranges - 1 - gw) / nw + 1;  // ranges of this warp
-  const uint64_t spr = range / CB_STEP;
-  const uint64_t last_r0 = (gw + (nr_w - 1) * nw) * range;
-  const uint64_t last_r1 = last_r0 + range < n ? last_r0 + range : n;
-  const uint64_t nq = (nr_w - 1) * spr + (last_r1 - last_r0 + CB_STEP - 1) / CB_STEP;
   // the warp's stages: 1024-byte aligned in the shared window (the swizzle pattern repeats every 1024 bytes)
   const uint32_t sm0 = (uint32_t)__cvta_generic_to_shared(cbsm);
   const uint32_t buf0 = ((sm0 + 1023u) & ~1023u) + (uint32_t)wib * CB_STAGES * CB_STEP_BYTES;
   const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[wib][0]);
-  auto step_row = [&](uint64_t q) {  // first row of the q-th step of this warp
-    return ((gw + (q / spr) * nw) * range + (q % spr) * CB_STEP) / CB_ROW;
-  };
-  if (lane == 0) {
-    for (int s = 0; s < CB_STAGES; ++s) cb_mbar_init(bar0 + 8 * s);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int s = 0; s < CB_STAGES && (uint64_t)s < nq; ++s)
-      cb_issue(bar0 + 8 * s, buf0 + s * CB_STEP_BYTES, &tmap, step_row(s));
-  }
-  __syncwarp();
-  bool failed = false;
-  uint64_t q = 0;
-  const uint32_t swz = (uint32_t)(lane & 7);
-  for (uint64_t m = 0; m < nr_w && !failed; ++m) {
-    X.r0 = (gw + m * nw) * range;
-    X.r1 = X.r0 + range < n ? X.r0 + range : n;
-    RowCarry c;
-    c.prev = X.r0 > 0 ? keys[X.r0 - 1] : 0;
-    c.start = 0;
-    c.owned = c.runW = c.runBD = c.runC = c.subW = c.subTD = false;
-    uint64_t p = X.r0;
-    for (; p < X.r1; p += CB_STEP, ++q) {
-      const int st = (int)(q % CB_STAGES);
-      if (!cb_wait(bar0 + 8 * st, (uint32_t)((q / CB_STAGES) & 1))) {
-        failed = true;
-        break;
-      }
-      uint64_t k[CB_ROW];
-      const uint32_t row = buf0 + st * CB_STEP_BYTES + (uint32_t)lane * 128u;
-#pragma unroll
-      for (int ch = 0; ch < CB_ROW / 2; ++ch)
-        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];"
-                     : "=l"(k[2 * ch]), "=l"(k[2 * ch + 1])
-                     : "r"(row + ((((uint32_t)ch) ^ swz) << 4)));
-      if (lo32) row_step<true>(X, c, k, p);
-      else row_step<false>(X, c, k, p);
-      // the stage is free again (its keys are consumed): the step CB_STAGES ahead
-      __syncwarp();
-      if (lane == 0 && q + CB_STAGES < nq) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        cb_issue(bar0 + 8 * st, buf0 + st * CB_STEP_BYTES, &tmap, step_row(q + CB_STAGES));
-      }
-    }
-    if (failed) break;
-    // past the range: plain loads until the warp's last run ends
-    for (; c.owned && p < n; p += CB_STEP) {
-      uint64_t k[CB_ROW];
-      const uint64_t r = p + (uint64_t)lane * CB_ROW;
-#pragma unroll
-      for (int j = 0; j < CB_ROW; ++j) k[j] = r + j < n ? keys[r + j] : 0;
-      if (lo32) row_step<true>(X, c, k, p);
-      else row_step<false>(X, c, k, p);
-    }
-    if (c.owned && p >= n && lane == 0) {  // the array ended inside a run of this warp
-      const bool last = c.runC || (c.subW && c.subTD) || ((X.g_all || c.prev < X.g_lim) && c.runW && c.runBD);
-      if (last) {
-        const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCAND], 1ull);
-        cb_put(X, g, c.start, n);
-      }
-    }
-  }
-  if (failed) {
-    if (lane == 0) atomicOr((unsigned long long*)&counters[C_ERR], (unsigned long long)ERR_TIMEOUT);
-    // copies still in flight land before the CTA leaves (each wait bounded)
-    for (uint64_t r = q; r < nq && r < q + CB_STAGES; ++r)
-      if (!cb_wait(bar0 + 8 * (int)(r % CB_STAGES), (uint32_t)((r / CB_STAGES) & 1))) break;
-  }
+  if (rsh < 32 && WVB == 0) scan_ranges<2>(&tmap, X, gw, nw, range, nr_w, buf0, bar0, counters);
+  else if (PB <= 32) scan_ranges<1>(&tmap, X, gw, nw, range, nr_w, buf0, bar0, counters);
+  else scan_ranges<0>(&tmap, X, gw, nw, range, nr_w, buf0, bar0, counters);
 }
 
 // ------------------------------------------------------------------ conflict scan, phase B
@@ -1961,14 +2069,14 @@ EncodeTiledFn encode_tiled() {
   }();
   return fn;
 }
-// the key buffer as rows of 16 keys (128 B), boxes of 32 rows, 128-byte swizzle
+// the key buffer as rows of 16 keys (128 B), boxes of one scan step's rows, 128-byte swizzle
 bool key_rows_map(CUtensorMap* tm, const uint64_t* keys, uint64_t key_cap) {
   EncodeTiledFn enc = encode_tiled();
-  const uint64_t rows = key_cap / CB_ROW;
+  const uint64_t rows = key_cap / CB_TILE_ROW;
   if (!enc || rows == 0 || rows > (1ull << 31) || (reinterpret_cast<uintptr_t>(keys) & 127u)) return false;
-  const cuuint64_t dim[2] = {(cuuint64_t)CB_ROW, (cuuint64_t)rows};
-  const cuuint64_t stride[1] = {(cuuint64_t)CB_ROW * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)CB_ROW, 32};
+  const cuuint64_t dim[2] = {(cuuint64_t)CB_TILE_ROW, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)CB_TILE_ROW * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)CB_TILE_ROW, (cuuint32_t)(CB_STEP / CB_TILE_ROW)};
   const cuuint32_t estr[2] = {1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(keys), dim, stride, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
