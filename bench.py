@@ -262,6 +262,109 @@ def timed_steps(s, steps, fn, flush):
     return sum(a.elapsed_time(b) for a, b in evs) / steps
 
 
+def _plain_vs_batched(ks, steps, s, flush):
+    """Device ms to all verdicts of a set of bindings: one plain check per
+    binding (one stream, one shared workspace) against one tuned batch
+    replayed from its CUDA graph; the verdicts must agree."""
+    import torch
+    import paper_2604_02106_b300 as hg
+    need = max(k.workspace_size(flags=hg.NO_PAIR) for k in ks)
+    wsp = torch.empty(need, dtype=torch.uint8, device="cuda")
+    res_plain = []
+    for k in ks:
+        k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
+        res_plain.append(k.collect(wsp, cap=64, stream=s, flags=hg.NO_PAIR))
+
+    def plain_pass():
+        for k in ks:
+            k.enqueue(wsp, stream=s, flags=hg.NO_PAIR)
+    plain_pass()
+    plain_ms = timed_steps(s, steps, plain_pass, flush)
+    del wsp
+    b = hg.Batch(ks, graph=True)
+    b.tune(stream=s)
+    res_b = b.check(stream=s)
+    for rp, rb in zip(res_plain, res_b):
+        assert rb.status == 0 and rb.n_witness == rp.n_witness and rb.n_by_kind == rp.n_by_kind
+    for _ in range(3):
+        b.run(stream=s)
+    batch_ms = timed_steps(s, steps, lambda: b.run(stream=s), flush)
+    n_inst = sum(r.n_instances for r in res_plain)
+    return {"items": len(ks), "instances": n_inst, "racy_items": sum(r.racy for r in res_plain),
+            "plain_ms": round(plain_ms, 3), "batched_ms": round(batch_ms, 3),
+            "batched_over_plain": plain_ms / batch_ms, "verdicts": "identical"}
+
+
+def _ranked_forms(train_pairs, heldout, topk, epochs):
+    """Time to all verdicts (host wall clock, best of three) of the held-out
+    corpus kernels: plain checks one by one, the batch, and the ranked batch
+    (ranker trained here on exact labels of other seeded kernels); the
+    verdicts must agree."""
+    import numpy as np
+    import torch
+    import workloads
+    import paper_2604_02106_b300 as hg
+    from paper_2604_02106_b300 import ranker as rk
+    t0 = time.perf_counter()
+    X, y, i = [], [], 0
+    while sum(len(v) for v in y) < train_pairs:
+        ws = [workloads.config4(100000 + i + j, hi_exp=5.5) for j in range(2000)]
+        ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in ws]
+        xb, yb = rk.labelled_pairs(ks, hg.Batch(ks, witness_cap=1).check())
+        X.append(xb)
+        y.append(yb)
+        i += 2000
+    X, y = np.concatenate(X), np.concatenate(y)
+    r = rk.Ranker(seed=1)
+    r.fit(X, y, epochs=epochs, batch=8192, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    hw = [workloads.config4(200000 + j, hi_exp=6.0) for j in range(heldout)]
+    hk = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in hw]
+    wsb = torch.empty(max(k.workspace_size(flags=hg.NO_PAIR) for k in hk), dtype=torch.uint8, device="cuda")
+    plain = [k.check(cap=16, flags=hg.NO_PAIR, workspace=wsb) for k in hk]
+    want = [x.racy for x in plain]
+    bb = hg.Batch(hk, witness_cap=16)
+    bb.tune()
+    bb.rank_prepare()
+
+    def verdicts(res):
+        return [k.check(cap=16, flags=hg.NO_PAIR).racy if x.status == -6 else x.racy for k, x in zip(hk, res)]
+    assert verdicts(bb.check()) == want
+    assert verdicts(bb.check_ranked(r.model, topk=topk, min_score=0.0)[0]) == want
+    best = {}
+    for name, fn in (("plain", lambda: [k.check(cap=16, flags=hg.NO_PAIR, workspace=wsb) for k in hk]),
+                     ("batched", lambda: bb.check()),
+                     ("batched_ranked", lambda: bb.check_ranked(r.model, topk=topk, min_score=0.0))):
+        for _ in range(3):
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            fn()
+            dt = time.perf_counter() - ts
+            best[name] = dt if name not in best else min(best[name], dt)
+    return {"items": len(hk), "instances": sum(x.n_instances for x in plain), "racy_items": sum(want),
+            "train_pairs": int(len(y)), "label_and_train_s": round(t_train, 1),
+            "plain_s": round(best["plain"], 4), "batched_s": round(best["batched"], 4),
+            "batched_ranked_s": round(best["batched_ranked"], 4),
+            "batched_over_plain": best["plain"] / best["batched"],
+            "batched_ranked_over_plain": best["plain"] / best["batched_ranked"],
+            "batched_ranked_over_batched": best["batched"] / best["batched_ranked"], "verdicts": "identical"}
+
+
+def forms_summary(args, s, flush):
+    """The batched and ranked forms against the plain checker, on the
+    host-loop sweep, a corpus sample and the ranker's held-out kernels."""
+    import workloads
+    import paper_2604_02106_b300 as hg
+    out = {}
+    ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params) for w in workloads.config3()]
+    out["sweep_64_bindings"] = _plain_vs_batched(ks, 3, s, flush)
+    ks = [hg.Kernel(w.text).bind(w.binding.grid, w.binding.block, w.binding.params)
+          for w in (workloads.config4(i) for i in range(args.forms_items))]
+    out[f"corpus_{args.forms_items}_kernels"] = _plain_vs_batched(ks, 3, s, flush)
+    out[f"ranked_{args.heldout}_heldout"] = _ranked_forms(args.forms_train_pairs, args.heldout, args.topk, args.epochs)
+    return out
+
+
 def run_suite(args):
     """Batched form vs the plain checker on a set of items (time to all verdicts)."""
     import torch
@@ -613,6 +716,11 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each check's kernels directly instead of replaying its CUDA graph "
                          "(ncu cannot profile kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and ranked forms against the plain checker")
+    ap.add_argument("--forms-items", type=int, default=300, help="corpus kernels in the forms comparison")
+    ap.add_argument("--forms-train-pairs", type=int, default=100000,
+                    help="exact pair labels the forms comparison trains its ranker on")
     ap.add_argument("--once", action="store_true",
                     help="bind the stencil workload, compile its kernels and run one check, untimed "
                          "(the case a profiler capture runs)")
@@ -871,6 +979,8 @@ def main():
                 "gpu_launches": int(launches * args.steps)}
         if not args.no_cpu_baseline and args.suite == "stencil":
             line["cpu_baseline"] = cpu_baseline(args.ref_side, args.ref_side_all)
+        if not args.no_forms and args.suite == "stencil" and world == 1:
+            line["forms"] = forms_summary(args, s, flush_l2)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
