@@ -202,7 +202,12 @@ typedef struct {
 } hgrd_stats;
 
 /* Parse a descriptor (format: kernel/param/loop/array/let/access/assert lines,
- * documented in the project's workload module).  Static checks: names, at
+ * documented in the project's workload module).  A descriptor states what the
+ * paper's front end extracts from the kernel code (Sec. 6.2, Table 1): per
+ * access its address expression over thread ids, block ids, loop counters and
+ * parameters, its guards, its read/write/atomic kind and width, and the block-
+ * and warp-barrier intervals it falls in (Sec. 6.1, Sec. 5.2); `param` and
+ * `assert` lines carry the host code's facts (Sec. 4).  Static checks: names, at
  * most 32 accesses, 32 arrays, 4 loops, quasi-affine expressions (a product
  * needs one uniform factor, divisors are uniform), intervals free of thread
  * and block ids, uniform loop bounds, sizes and asserts.  `text` need not be
@@ -216,17 +221,29 @@ int hgrd_load_desc(const char* text, size_t len, hgrd_desc** out);
  * expression over the instance box (HGRD_EOVERFLOW when int64 can
  * overflow) and plans the key layout.  Acquire-release guards (`sync`
  * fields, Sec. 6.5 with the scopes of Appendix A) are decided here, per pair
- * of guarded accesses on one lock array: both guard elements constant, or
- * each access guarded at its own index with equal widths; any other pair of
- * guard forms is HGRD_EUNSUPPORTED.  Rebinding replaces the old binding. */
+ * of guarded accesses on one lock array, when both guard elements are
+ * constant or each access is guarded at its own index with equal widths;
+ * pairs whose elements can differ between instances (constant, affine in
+ * thread and block ids, or the access's own element) are left to the exact
+ * scan, instance pair by instance pair; guard elements with a loop counter,
+ * or with a division or remainder other than the access's own index, are
+ * HGRD_EUNSUPPORTED.  Rebinding replaces the old binding. */
 int hgrd_bind_host_params(hgrd_desc* d, const hgrd_binding* b);
 
-/* Device workspace bytes hgrd_check needs for the bound descriptor.  The
+/* Device workspace bytes hgrd_check needs for the bound descriptor: the
+ * instance keys, their sorted copy and the witness buffers of the exhaustive
+ * decision that stands in for the paper's constraint solve (Sec. 6.4).  The
  * workspace must be 256-byte aligned. */
 int hgrd_workspace_size(const hgrd_desc* d, const hgrd_check_opts* o, size_t* bytes);
 
 /* Exhaustive check of the bound descriptor on `cuda_stream` (a cudaStream_t,
- * NULL = legacy default stream).  Synchronous on return: writes up to `cap`
+ * NULL = legacy default stream).  Decides the paper's race (Sec. 2: two
+ * threads, an overlapping address, at least one write, not both atomic,
+ * unordered by barriers; shared memory within a block, global memory across
+ * the grid) for the bound host values, with the trivially race-free pairs of
+ * Sec. 6.1 and Table 2's constraints for the three race types (inter-block,
+ * intra-block, intra-warp), and reports racy access pairs with their types
+ * (Sec. 5) plus per-location witnesses.  Synchronous on return: writes up to `cap`
  * canonical witnesses to host_out (may be NULL when cap is 0) and the verdict
  * to *v.  The workspace contents are scratch. */
 int hgrd_check(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_bytes, void* cuda_stream,
