@@ -1064,7 +1064,7 @@ __global__ void __launch_bounds__(CA_THREADS, 2) candidates_kernel(const uint64_
 constexpr int CB_THREADS = 128, CB_STAGES = 2, CB_ROW = 32, CB_STEP = 32 * CB_ROW, CB_STEP_BYTES = CB_STEP * 8;
 constexpr int CB_TILE_ROW = 16;  // keys per 128-byte tile row of the tensor copy
 constexpr int CB_RANGE = 8 * CB_STEP;
-constexpr uint32_t CB_SPIN_LIMIT = 1u << 24;
+constexpr uint32_t CB_SPIN_LIMIT = 1u << 22;
 
 struct RowCarry {
   uint64_t prev, start;
@@ -1081,16 +1081,19 @@ __device__ __forceinline__ void cb_issue(uint32_t bar, uint32_t dst, const CUten
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"((int32_t)row), "r"(bar)
       : "memory");
 }
-// bounded wait on a stage's phase; false when the limit ran out
+// bounded wait on a stage's phase (non-blocking tests, a short sleep after
+// the first few; at most CB_SPIN_LIMIT tests, well under a second); false
+// when the limit ran out
 __device__ __forceinline__ bool cb_wait(uint32_t bar, uint32_t parity) {
   for (uint32_t spins = 0; spins < CB_SPIN_LIMIT; ++spins) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (spins >= 8) __nanosleep(64);
   }
   return false;
 }
