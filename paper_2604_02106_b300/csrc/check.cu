@@ -204,7 +204,8 @@ cudaError_t enqueue_witness_big(const Launch& L, const Layout& W, char* ws, int 
   if ((e = launch_heads(L, win, nraw, W.raw_cap, U(W.flags))) != cudaSuccess) return e;
   if ((e = launch_scan(L, U(W.flags), U(W.excl), nraw, W.raw_cap, U(W.partials), cnt + C_NUNIQ)) != cudaSuccess)
     return e;
-  return launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout);
+  if ((e = launch_merge(L, win, U(W.flags), U(W.excl), nraw, W.raw_cap, wout)) != cudaSuccess) return e;
+  return launch_kind_counts(L, wout, cnt, nraw);
 }
 
 // The witness merge as an instantiated graph per (device, workspace, layout,
@@ -571,7 +572,6 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     CK(enqueue_witness_big(L, W, ws, P));
   }
   CK(launch_witness_small(L, U(W.raw), wout, cnt, W.raw_cap));
-  CK(launch_kind_counts(L, wout, cnt));
   g_prof.mark("witness_merge");
   if (pair && !(fl & HGRD_NO_PAIR)) {
     CK(enqueue_pair_search(L, d, o, W, ws, wout));

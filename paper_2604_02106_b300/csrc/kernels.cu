@@ -1256,26 +1256,26 @@ __device__ __forceinline__ void row_step(const RowCtx& X, RowCarry& c, uint32_t 
     BD &= VM;
     W &= VM;
   }
-  // global-memory runs: keys below g_lim (monotone in the sorted order)
+  // global-memory runs: keys below g_lim (monotone in the sorted order; a
+  // row's last key counts only when the whole row lies below the end)
   uint32_t GL;
-  if (X.g_all || klast < X.g_lim) {
+  if (X.g_all || (full && klast < X.g_lim)) {
     GL = 0xffffffffu;
   } else if (kfirst >= X.g_lim) {
     GL = 0;
-  } else {  // the row crosses into the shared arrays: find where
+  } else {  // the row may cross into the shared arrays: find where
     GL = 0;
     for (int j = 0; j < CB_ROW; ++j) {
-      const uint64_t kj = srow != 0xffffffffu
-                              ? 0
-                              : (i0 + j < end ? X.keys[i0 + j] : ~0ull);
-      uint64_t ks = kj;
+      uint64_t kj;
       if (srow != 0xffffffffu) {
         const uint32_t r = 2 * (uint32_t)lane + (j >> 4), ch = (uint32_t)(j & 15) >> 1;
         asm volatile("ld.shared.u64 %0, [%1];"
-                     : "=l"(ks)
+                     : "=l"(kj)
                      : "r"(srow + r * 128u + (((ch ^ (r & 7u)) << 4) | (uint32_t)((j & 1) << 3))));
+      } else {
+        kj = i0 + j < end ? X.keys[i0 + j] : ~0ull;
       }
-      if (ks < X.g_lim) GL |= 1u << j;
+      if (kj < X.g_lim) GL |= 1u << j;
     }
   }
   const bool gprev = X.g_all || pk0 < X.g_lim;
@@ -1787,22 +1787,44 @@ __global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __r
   uint32_t m = 1;
   while (m < n) m <<= 1;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? raw[i] : ~0ull;
-  __syncthreads();
-  for (uint32_t k = 2; k <= m; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = tid; i < m; i += 1024) {
-        const uint32_t x = i ^ j;
-        if (x > i) {
-          const uint64_t a = s[i], b = s[x];
-          if ((a > b) == ((i & k) == 0)) {
-            s[i] = b;
-            s[x] = a;
+  if (m <= 1024) {
+    // one element per thread: partners inside a warp meet by shuffles, the
+    // others through shared memory (bitonic network, ascending)
+    uint64_t v = tid < n ? raw[tid] : ~0ull;
+    for (uint32_t k = 2; k <= m; k <<= 1)
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        uint64_t o;
+        if (j < 32) {
+          o = __shfl_xor_sync(FULL, v, (int)j);
+        } else {
+          s[tid] = v;
+          __syncthreads();
+          o = s[tid ^ j];
+          __syncthreads();
+        }
+        const bool keep_min = ((tid & j) == 0) == ((tid & k) == 0);
+        v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+      }
+    if (tid < m) s[tid] = v;
+  } else {
+    for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? raw[i] : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= m; k <<= 1)
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = tid; i < m; i += 1024) {
+          const uint32_t x = i ^ j;
+          if (x > i) {
+            const uint64_t a = s[i], b = s[x];
+            if ((a > b) == ((i & k) == 0)) {
+              s[i] = b;
+              s[x] = a;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
-    }
+  }
+  __syncthreads();
   // group heads over contiguous chunks, a CTA-wide exclusive scan of their counts
   const uint32_t chunk = (n + 1023) / 1024;
   const uint32_t c0 = min(n, tid * chunk), c1 = min(n, c0 + chunk);
@@ -1827,15 +1849,30 @@ __global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __r
   }
   __syncthreads();
   uint32_t u = wsum[warp] + x - heads;
+  uint32_t k0 = 0, k1 = 0, k2 = 0;  // witnesses of each race kind
   for (uint32_t i = c0; i < c1; ++i) {
     if (!(i == 0 || (s[i] >> WIT_SORT_LO) != (s[i - 1] >> WIT_SORT_LO))) continue;
     uint64_t w = s[i];
     for (uint32_t j = i + 1; j < n && (s[j] >> WIT_SORT_LO) == (s[i] >> WIT_SORT_LO); ++j) w |= s[j];
     uniq[u++] = w;
+    k0 += (uint32_t)w & 1u;
+    k1 += (uint32_t)(w >> 1) & 1u;
+    k2 += (uint32_t)(w >> 2) & 1u;
+  }
+  for (int o = 16; o; o >>= 1) {
+    k0 += __shfl_down_sync(FULL, k0, o);
+    k1 += __shfl_down_sync(FULL, k1, o);
+    k2 += __shfl_down_sync(FULL, k2, o);
+  }
+  if (lane == 0) {
+    if (k0) atomicAdd((unsigned long long*)&counters[C_KIND0], (unsigned long long)k0);
+    if (k1) atomicAdd((unsigned long long*)&counters[C_KIND1], (unsigned long long)k1);
+    if (k2) atomicAdd((unsigned long long*)&counters[C_KIND2], (unsigned long long)k2);
   }
 }
 
-__global__ void kind_counts_kernel(const uint64_t* __restrict__ uniq, uint64_t* counters) {
+__global__ void kind_counts_kernel(const uint64_t* __restrict__ uniq, uint64_t* counters, const uint64_t* gate) {
+  if (*gate == 0) return;  // the one-CTA merge counted them
   const uint64_t n = counters[C_NUNIQ];
   uint64_t c0 = 0, c1 = 0, c2 = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -2212,8 +2249,8 @@ cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const uint
   return cudaGetLastError();
 }
 
-cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters) {
-  kind_counts_kernel<<<L.nsm, 256, 0, L.s>>>(uniq, counters);
+cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters, const uint64_t* gate) {
+  kind_counts_kernel<<<L.nsm, 256, 0, L.s>>>(uniq, counters, gate);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -90,7 +90,8 @@ cudaError_t launch_shared_cand(const Launch& L, const DProg& h_prog, const uint6
 cudaError_t launch_heads(const Launch& L, const uint64_t* w, const uint64_t* n_dev, uint64_t n_max, uint64_t* flags);
 cudaError_t launch_merge(const Launch& L, const uint64_t* w, const uint64_t* flags, const uint64_t* excl,
                          const uint64_t* n_dev, uint64_t n_max, uint64_t* uniq);
-cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters);
+// (kind counts of a device-wide merge; *gate = 0 means the one-CTA merge ran and counted them)
+cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* counters, const uint64_t* gate);
 // pair search: the blocks of a global-memory witness's run in the sorted keys
 // (counters[C_NPB] = 1 + their count, or left 0 when every unit must be searched)
 cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
