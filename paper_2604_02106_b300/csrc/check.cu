@@ -41,7 +41,7 @@ const hgrd_check_opts* norm_opts(const hgrd_check_opts* o, hgrd_check_opts* tmp)
 }
 
 struct Layout {
-  size_t counters, prog, unit_cnt, unit_off, partials, hist, gbase, status, keysA, keysB, raw, raw2, flags, excl,
+  size_t counters, prog, unit_cnt, unit_off, partials, hist, status, keysA, keysB, raw, raw2, flags, excl,
       pairs, stbl, sbase, cells, total;
   bool cfilter;        // the cell filter's table exists (the filter runs in the first sort pass)
   uint64_t raw_cap, pair_cap, status_words;
@@ -95,7 +95,6 @@ Layout layout(const Bound& B, const hgrd_check_opts* o) {
   L.unit_cnt = take(nunits * 8);
   L.unit_off = take(nunits * 8);
   L.partials = take(((scan_n + SCAN_TILE - 1) / SCAN_TILE + 1) * 8);
-  L.gbase = take(MAX_PASSES * 256 * 8);
   L.status = take(L.status_words * 8);
   L.keysA = take(L.key_words * 8);
   L.keysB = take(L.key_words * 8);
@@ -188,13 +187,11 @@ cudaError_t enqueue_witness_big(const Launch& L, const Layout& W, char* ws, int 
   cudaError_t e;
   if ((e = launch_zero_status(L, U(W.status), nraw, W.status_words)) != cudaSuccess) return e;
   uint64_t* whist = U(W.hist) + 8 * 256;
-  uint64_t* wgb = U(W.gbase) + 8 * 256;
   if ((e = launch_histogram(L, U(W.raw), nraw, W.raw_cap, WIT_SORT_LO, WP, whist)) != cudaSuccess) return e;
-  if ((e = launch_hist_scan(L, whist, wgb, WP)) != cudaSuccess) return e;
   uint64_t* win = U(W.raw);
   uint64_t* wout = U(W.raw2);
   for (int p = 0; p < WP; p++) {
-    if ((e = launch_onesweep(L, win, wout, nraw, W.raw_cap, WIT_SORT_LO + 8 * p, wgb + p * 256, U(W.status),
+    if ((e = launch_onesweep(L, win, wout, nraw, W.raw_cap, WIT_SORT_LO + 8 * p, whist + p * 256, U(W.status),
                              cnt + C_TICKET0 + P + p, (uint32_t)(P + p + 1), cnt + C_ERR)) != cudaSuccess)
       return e;
     std::swap(win, wout);
@@ -221,7 +218,7 @@ cudaGraphExec_t witness_graph(const Launch& L, const Layout& W, char* ws, int P)
   int dev = 0;
   cudaGetDevice(&dev);
   const std::vector<uint64_t> key = {(uint64_t)dev, (uint64_t)(uintptr_t)ws, W.counters, W.raw, W.raw2, W.flags,
-                                     W.excl, W.partials, W.hist, W.gbase, W.status, W.raw_cap, W.status_words,
+                                     W.excl, W.partials, W.hist, W.status, W.raw_cap, W.status_words,
                                      (uint64_t)P, sort_variant_key()};
   std::lock_guard<std::mutex> lk(g_wg_mu);
   auto it = g_wg.find(key);
@@ -533,8 +530,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // the remaining digits by one CTA, straight into the final buffer, and the
   // later passes return at once.
   for (int p = 0; p < P; p++) {
-    CK(launch_hist_scan(L, U(W.hist) + p * 256, U(W.gbase) + p * 256, 1));
-    CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.gbase) + p * 256,
+    CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.hist) + p * 256,
                        U(W.status), cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
                        p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1),
                        p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB, p > 0 ? cnt + C_TAIL : nullptr, p));

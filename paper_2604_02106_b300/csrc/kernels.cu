@@ -286,16 +286,32 @@ __global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restri
     if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
 }
 
-__global__ void __launch_bounds__(256) hist_scan_kernel(const uint64_t* __restrict__ hist, uint64_t* __restrict__ gbase,
-                                                        int npass) {
-  __shared__ uint64_t ws[8];
-  for (int p = 0; p < npass; ++p) {
-    uint64_t v = hist[p * 256 + threadIdx.x];
-    gbase[p * 256 + threadIdx.x] = block_excl_scan(v, ws, nullptr);
+constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull << 54) - 1;
+
+// The pass's global start of each digit, from its digit counts: one warp
+// scans the 256 counts (eight per lane) into sgb (shared memory).
+__device__ __forceinline__ void digit_bases(const uint64_t* __restrict__ dcount, uint64_t* sgb) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  uint64_t v[8], s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[j] = dcount[lane * 8 + j];
+    s += v[j];
+  }
+  uint64_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  uint64_t run = x - s;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    sgb[lane * 8 + j] = run;
+    run += v[j];
   }
 }
-
-constexpr uint64_t ST_AGG = 1ull << 54, ST_PREFIX = 2ull << 54, ST_VAL = (1ull << 54) - 1;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
 // Onesweep pass, templated on the CTA shape (threads T, keys per thread KPT,
@@ -311,7 +327,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 template <int T, int KPT, int MINB, bool RA = false, int MS = 0>
 __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                           const uint64_t* n_dev, uint64_t n_max, int shift,
-                                                          const uint64_t* __restrict__ gbase, uint64_t* status,
+                                                          const uint64_t* __restrict__ dcount, uint64_t* status,
                                                           unsigned long long* ticket, uint32_t epoch, uint64_t* err,
                                                           uint64_t* next_hist, int next_shift,
                                                           const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh,
@@ -327,6 +343,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
   uint64_t* stage = gofs + RS_RADIX;
   uint64_t* s_tile = stage + TILE;
   uint32_t* s_kept = reinterpret_cast<uint32_t*>(s_tile + 1);  // keys of the tile that stay
+  uint64_t* gbase = s_tile + 2;                                 // the pass's start of each digit
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + TILE - 1) / TILE;
@@ -335,6 +352,7 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
   if ((uint64_t)blockIdx.x >= ntiles) return;
   const uint64_t ep = (uint64_t)epoch << 56;
   for (int d = threadIdx.x; d < RS_RADIX; d += T) nhist[d] = 0;
+  digit_bases(dcount, gbase);
   for (;;) {
     if (threadIdx.x == 0) *s_tile = atomicAdd(ticket, 1ull);
     for (int i = threadIdx.x; i < W * RS_RADIX; i += T) whist[i] = 0;
@@ -594,7 +612,7 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
 template <int T, int KPT, int MINB, int RANK>
 __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                            const uint64_t* n_dev, uint64_t n_max, int shift,
-                                                           const uint64_t* __restrict__ gbase, uint64_t* status,
+                                                           const uint64_t* __restrict__ dcount, uint64_t* status,
                                                            unsigned long long* ticket, uint32_t epoch, uint64_t* err,
                                                            uint64_t* next_hist, int next_shift,
                                                            const uint32_t* __restrict__ ctab, uint64_t ncells, int rsh,
@@ -612,12 +630,14 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
   uint32_t* wsum = nhist + RS_RADIX;                              // 8 warp totals + tile total
   uint32_t* s_tile = wsum + 16;
   uint32_t* wdist = s_tile + 2;                                   // [W] distinct digits of each warp
+  uint64_t* gbase = reinterpret_cast<uint64_t*>(wdist + 32);      // the pass's start of each digit
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
   const uint64_t n = dev_n(n_dev, n_max);
   const uint64_t ntiles = (n + TILE - 1) / TILE;
   if ((uint64_t)blockIdx.x >= ntiles) return;
   const uint64_t ep = (uint64_t)epoch << 56;
   for (int d = t; d < RS_RADIX; d += T) nhist[d] = 0;
+  digit_bases(dcount, gbase);
   if (RANK != 0)
     for (int i = t; i < W * RS_RADIX; i += T) wmask[i] = 0;
   const unsigned lt = lanemask_lt();
@@ -803,12 +823,13 @@ __global__ void __launch_bounds__(T, MINB) onesweep3_kernel(const uint64_t* __re
 template <int T, int KPT, int RANK>
 constexpr size_t onesweep3_smem() {
   return (size_t)T * KPT * 8 + RS_RADIX * 8 + (size_t)(T / 32) * RS_RADIX * 4 * (RANK != 0 ? 2 : 1) +
-         2 * RS_RADIX * 4 + 32 * 4 + 16;
+         2 * RS_RADIX * 4 + 32 * 4 + 16 + 32 * 4 + RS_RADIX * 8;
 }
 
 template <int T, int KPT>
 constexpr size_t onesweep_smem() {
-  return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16;  // + ticket, kept
+  return (size_t)(T / 32) * RS_RADIX * 4 + 3 * RS_RADIX * 4 + RS_RADIX * 8 + (size_t)T * KPT * 8 + 16 +
+         RS_RADIX * 8;  // + ticket, kept, digit starts
 }
 
 // ------------------------------------------------------------------ conflict scan, phase A
@@ -2001,12 +2022,6 @@ cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64
   return cudaGetLastError();
 }
 
-cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass) {
-  hist_scan_kernel<<<1, 256, 0, L.s>>>(hist, gbase, npass);
-  (*L.launches)++;
-  return cudaGetLastError();
-}
-
 struct SortVariant {
   const void* fn;
   int threads, kpt;
@@ -2059,7 +2074,7 @@ uint64_t sort_variant_key() {
 }
 
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                            int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
+                            int shift, const uint64_t* dcount, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist, int next_shift, const uint32_t* ctab,
                             uint64_t ncells, int rsh, const uint64_t* skip, int pass) {
   int nv = 0, dev = 0;
@@ -2076,7 +2091,7 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
   int grid = occupancy_grid(S.fn, S.threads, S.smem, L.nsm);
   if ((uint64_t)grid > tiles) grid = (int)(tiles ? tiles : 1);
   unsigned long long* tk = (unsigned long long*)ticket;
-  void* args[] = {(void*)&in, (void*)&out, (void*)&n_dev, (void*)&n_max, (void*)&shift, (void*)&gbase,
+  void* args[] = {(void*)&in, (void*)&out, (void*)&n_dev, (void*)&n_max, (void*)&shift, (void*)&dcount,
                   (void*)&status, (void*)&tk, (void*)&epoch, (void*)&err, (void*)&next_hist, (void*)&next_shift,
                   (void*)&ctab, (void*)&ncells, (void*)&rsh, (void*)&skip};
   (*L.launches)++;
@@ -2317,8 +2332,8 @@ extern "C" int hgrd_debug_lookback_timeout(void* d_ws, size_t ws_bytes, void* st
   uint64_t launches = 0;
   Launch L{s, 1, &launches};
   cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
-  // keys, zero digit offsets (every position stays below n), no status yet,
-  // and the ticket of the first tile already handed out
+  // keys, zero digit counts (every digit starts at 0, every position stays
+  // below n), no status yet, and the ticket of the first tile already handed out
   random_keys_kernel<<<L.nsm, 256, 0, s>>>(kin, n, 0x7153);
   const uint64_t host[3] = {n, 1, 0};
   if (cudaMemsetAsync(gb, 0, 256 * 8, s) != cudaSuccess ||
@@ -2342,7 +2357,7 @@ extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* be
   const SortVariant* V = sort_variants(&nv);
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return fail(HGRD_EUNSUPPORTED, "device index too large");
-  // keys in | keys out | status | hist | gbase | counters
+  // keys in | keys out | status | hist | counters
   const size_t fixed = 3 * 4096 + 256;
   uint64_t n = ws_bytes > fixed ? (uint64_t)((ws_bytes - fixed) / (16.0 + 256.0 * 8 / RS_MIN_TILE)) : 0;
   n = std::min<uint64_t>(n, 1ull << 25) & ~(uint64_t)4095;
@@ -2353,8 +2368,7 @@ extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* be
   uint64_t* status = kout + n;
   const size_t sw = ((n + RS_MIN_TILE - 1) / RS_MIN_TILE) * RS_RADIX;
   uint64_t* hist = status + sw;
-  uint64_t* gb = hist + 256;
-  uint64_t* cnt = gb + 256;  // n, ticket, err
+  uint64_t* cnt = hist + 256;  // n, ticket, err
   uint64_t launches = 0;
   Launch L{s, 1, &launches};
   cudaDeviceGetAttribute(&L.nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -2362,7 +2376,6 @@ extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* be
   cudaMemcpyAsync(cnt, &n, 8, cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(hist, 0, 256 * 8, s);
   launch_histogram(L, kin, cnt, n, 0, 1, hist);
-  launch_hist_scan(L, hist, gb, 1);
   cudaEvent_t e0, e1;
   note_created(2);
   cudaEventCreate(&e0);
@@ -2378,7 +2391,7 @@ extern "C" int hgrd_sort_tune(void* d_ws, size_t ws_bytes, void* stream, int* be
       cudaMemsetAsync(status, 0, sw * 8, s);
       cudaMemsetAsync(cnt + 1, 0, 16, s);
       cudaEventRecord(e0, s);
-      cudaError_t e = launch_onesweep(L, kin, kout, cnt, n, 0, gb, status, cnt + 1, epoch, cnt + 2);
+      cudaError_t e = launch_onesweep(L, kin, kout, cnt, n, 0, hist, status, cnt + 1, epoch, cnt + 2);
       cudaEventRecord(e1, s);
       if (e != cudaSuccess) {
         g_sort_variant[dev] = saved;

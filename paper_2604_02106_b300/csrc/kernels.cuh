@@ -40,19 +40,19 @@ cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, cons
 // histograms of npass 8-bit digits starting at bit `shift0` of n keys
 cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max, int shift0,
                              int npass, uint64_t* hist);
-// per-pass exclusive prefix of the digit counts
-cudaError_t launch_hist_scan(const Launch& L, const uint64_t* hist, uint64_t* gbase, int npass);
 // cell filter: the first pass's digit histogram (at `shift`, added to hist)
 // of the keys [0, *n_dev) whose cell (key >> rsh) the count pass found
 // written and touched by two threads, and their count (added to *n_kept)
 cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
                              const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
                              uint64_t* n_kept);
-// one stable onesweep pass on the digit at `shift`; when next_hist is given,
-// also counts the digit at `next_shift` for the following pass; with a cell
-// table, only the keys the cell filter keeps are sorted (to out[0, kept))
+// one stable onesweep pass on the digit at `shift`, given the pass's 256
+// digit counts (each CTA scans them into the digits' starts); when next_hist
+// is given, also counts the digit at `next_shift` for the following pass;
+// with a cell table, only the keys the cell filter keeps are sorted (to
+// out[0, kept))
 cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                            int shift, const uint64_t* gbase, uint64_t* status, uint64_t* ticket, uint32_t epoch,
+                            int shift, const uint64_t* dcount, uint64_t* status, uint64_t* ticket, uint32_t epoch,
                             uint64_t* err, uint64_t* next_hist = nullptr, int next_shift = 0,
                             const uint32_t* ctab = nullptr, uint64_t ncells = 0, int rsh = 0,
                             const uint64_t* skip = nullptr, int pass = -1);
