@@ -488,8 +488,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                          U(W.sbase), only_mask, split));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
-    // look-back status of the tiles the key sort will use: no stale epoch may survive
-    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
+    // look-back status of the tiles the key sort will use: no stale epoch may
+    // survive (with the cell filter, its histogram kernel clears them)
+    if (!cf) CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, fin, nullptr, P, cnt, U(W.stbl),
                          U(W.sbase), only_mask, split));
@@ -499,8 +500,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                            U(W.stbl), U(W.sbase)));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
-    // look-back status of the tiles the key sort will use: no stale epoch may survive
-    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
+    // look-back status of the tiles the key sort will use: no stale epoch may
+    // survive (with the cell filter, its histogram kernel clears them)
+    if (!cf) CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_expand_block(L, 4, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, fin, nullptr, cnt, U(W.stbl),
                            U(W.sbase)));
@@ -510,8 +512,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                      0));
     g_prof.mark("expand_count");
     CK(launch_scan(L, U(W.unit_cnt), U(W.unit_off), nullptr, (uint64_t)HP.nunits, U(W.partials), nkeys));
-    // look-back status of the tiles the key sort will use: no stale epoch may survive
-    CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
+    // look-back status of the tiles the key sort will use: no stale epoch may
+    // survive (with the cell filter, its histogram kernel clears them)
+    if (!cf) CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
     g_prof.mark("expand_write");
@@ -521,7 +524,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const uint64_t* nsorted = nkeys;  // keys the first pass reads
   if (cf) {
     // digit histogram of the first pass over the kept keys, and their count
-    CK(launch_cell_hist(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, U(W.hist), HP.SB, cnt + C_NGC));
+    CK(launch_cell_hist(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, U(W.hist), HP.SB, cnt + C_NGC,
+                        U(W.status), W.status_words));
     nkeys = cnt + C_NGC;
     g_prof.mark("cell_filter");
   }

@@ -250,11 +250,18 @@ __global__ void shared_cand_kernel(const uint64_t* __restrict__ stbl, const uint
 __global__ void __launch_bounds__(256) cell_hist_kernel(const uint64_t* __restrict__ keys, const uint64_t* n_dev,
                                                         uint64_t n_max, const uint32_t* __restrict__ tab,
                                                         uint64_t ncells, int rsh, uint64_t* __restrict__ hist, int shift,
-                                                        uint64_t* __restrict__ n_kept) {
+                                                        uint64_t* __restrict__ n_kept, uint64_t* __restrict__ status,
+                                                        uint64_t max_words) {
   __shared__ uint32_t sh[256];
   sh[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t n = dev_n(n_dev, n_max);
+  {  // the look-back status of the tiles the first sort pass will use
+    uint64_t words = (n + RS_MIN_TILE - 1) / RS_MIN_TILE * RS_RADIX;
+    if (words > max_words) words = max_words;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+      status[i] = 0;
+  }
   uint32_t kept = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
@@ -2014,10 +2021,11 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
 
 cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
                              const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
-                             uint64_t* n_kept) {
+                             uint64_t* n_kept, uint64_t* status, uint64_t max_words) {
   uint64_t blocks = (n_max + 255) / 256;
   unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
-  cell_hist_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, hist, shift, n_kept);
+  cell_hist_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, hist, shift, n_kept, status,
+                                          max_words);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -42,10 +42,12 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
                              int npass, uint64_t* hist);
 // cell filter: the first pass's digit histogram (at `shift`, added to hist)
 // of the keys [0, *n_dev) whose cell (key >> rsh) the count pass found
-// written and touched by two threads, and their count (added to *n_kept)
+// written and touched by two threads, and their count (added to *n_kept);
+// it also clears the look-back status words the first sort pass over those
+// keys uses (at most max_words)
 cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
                              const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
-                             uint64_t* n_kept);
+                             uint64_t* n_kept, uint64_t* status, uint64_t max_words);
 // one stable onesweep pass on the digit at `shift`, given the pass's 256
 // digit counts (each CTA scans them into the digits' starts); when next_hist
 // is given, also counts the digit at `next_shift` for the following pass;
