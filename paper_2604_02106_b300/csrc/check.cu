@@ -477,8 +477,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   const bool cf = filter_runs(W, P);
   uint32_t* ctab = cf ? (uint32_t*)(ws + W.cells) : nullptr;
   if (cf) {
-    const uint64_t used = split ? HP.shared_cell_base : HP.ncells;  // cells the count pass can note
-    CK(cudaMemsetAsync(ctab, 0, used * 4, s));
+    // the cells the count pass can note: those of the accesses whose keys
+    // are written (in the block-local mode, of the global arrays only)
+    uint64_t lo = ~0ull, hi = 0;
+    for (int a = 0; a < hprog->nacc; a++) {
+      const DAcc& A = hprog->acc[a];
+      if (!((hprog->emask >> a) & 1u) || A.dead || (split && A.shared)) continue;
+      const uint64_t end = A.cbase + (A.shared ? (uint64_t)hprog->nblk * A.ngran : A.ngran);
+      lo = std::min(lo, A.cbase);
+      hi = std::max(hi, end);
+    }
+    if (hi > lo) CK(cudaMemsetAsync(ctab + lo, 0, (hi - lo) * 4, s));
   }
   uint64_t* fin = (P & 1) ? keysB : keysA;  // where the sorted keys end
   uint64_t* cnt_tab = cf ? (uint64_t*)ctab : nullptr;
