@@ -149,15 +149,15 @@ __global__ void __launch_bounds__(256) scan_apply(const uint64_t* __restrict__ i
   __shared__ uint64_t ws[8];
   __shared__ uint64_t tot;
   for (uint64_t tile = blockIdx.x; tile * SCAN_TILE < n; tile += gridDim.x) {
-    // each thread owns 16 consecutive elements of the tile
-    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * 16;
-    uint64_t v[16], s = 0;
-    for (int k = 0; k < 16; ++k) {
+    // each thread owns SCAN_PER consecutive elements of the tile
+    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    uint64_t v[SCAN_PER], s = 0;
+    for (int k = 0; k < SCAN_PER; ++k) {
       v[k] = (b0 + k < n) ? in[b0 + k] : 0;
       s += v[k];
     }
     uint64_t run = partials[tile] + block_excl_scan(s, ws, &tot);
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < SCAN_PER; ++k) {
       if (b0 + k < n) out[b0 + k] = run;
       run += v[k];
     }
@@ -181,14 +181,14 @@ __global__ void __launch_bounds__(256) scan_apply_fused(const uint64_t* __restri
     block_excl_scan(before, ws, &tot);
     const uint64_t base = tot;
     if (tile == nt - 1 && threadIdx.x == 0 && total) *total = base + sums[tile];
-    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * 16;
-    uint64_t v[16], s = 0;
-    for (int k = 0; k < 16; ++k) {
+    const uint64_t b0 = tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    uint64_t v[SCAN_PER], s = 0;
+    for (int k = 0; k < SCAN_PER; ++k) {
       v[k] = (b0 + k < n) ? in[b0 + k] : 0;
       s += v[k];
     }
     uint64_t run = base + block_excl_scan(s, ws, &tot);
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < SCAN_PER; ++k) {
       if (b0 + k < n) out[b0 + k] = run;
       run += v[k];
     }

@@ -13,7 +13,8 @@ constexpr int CA_THREADS = 256;    // candidate scan
 constexpr int CA_LONG = 1 << 16;   // a run longer than this is handed to the exact scan unmeasured
 constexpr int CA_RANGE = 2048;     // keys owned by one warp of the candidate scan
 constexpr int CA_AHEAD = 4;        // 32-key steps loaded ahead by each warp
-constexpr int SCAN_TILE = 4096;
+constexpr int SCAN_TILE = 1024;               // values per CTA of the exclusive scans
+constexpr int SCAN_PER = SCAN_TILE / 256;     // per thread (256 threads)
 constexpr int MAX_PASSES = 16;
 
 // cached per device: raise a kernel's dynamic shared-memory limit to at least
