@@ -491,6 +491,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   }
   uint64_t* fin = (P & 1) ? keysB : keysA;  // where the sorted keys end
   uint64_t* cnt_tab = cf ? (uint64_t*)ctab : nullptr;
+  // compact form (cell filter, plain pipeline): the write pass, which runs
+  // with the cell table complete, also appends the keys of kept cells to a
+  // compact buffer (the raw-witness buffer, free until the exact scan); when
+  // they all fit (at most TAIL_KEYS), one CTA sorts them whole, on every key
+  // bit from the warp id up (the order the scans need), into the final
+  // buffer, and the filter's histogram, the sort passes and the tail return
+  // at once.  Otherwise the filter and the passes run as below.
+  const bool compact = cf && !split;
+  uint64_t* cbuf = compact ? U(W.raw) : nullptr;
+  const uint64_t ccap = compact ? std::min<uint64_t>(W.raw_cap, TAIL_KEYS) : 0;
+  const uint32_t* wtab = compact ? ctab : nullptr;
   if (jit) {
     const int m0 = split ? 3 : 0, m1 = split ? 4 : 1;
     CK(launch_jit_expand(L, B, m0, *hprog, U(W.unit_cnt), nullptr, cnt_tab, nullptr, U(W.hist), 1, cnt, U(W.stbl),
@@ -502,7 +513,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     if (!cf) CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
     CK(launch_jit_expand(L, B, m1, *hprog, nullptr, U(W.unit_off), keysA, fin, nullptr, P, cnt, U(W.stbl),
-                         U(W.sbase), only_mask, split));
+                         U(W.sbase), only_mask, split, nullptr, nullptr, 0, wtab, cbuf, ccap));
     g_prof.mark("expand_write");
   } else if (split) {
     CK(launch_expand_block(L, 3, B.wide, dprog, HP, U(W.unit_cnt), nullptr, cnt_tab, nullptr, U(W.hist), cnt,
@@ -525,8 +536,17 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     // survive (with the cell filter, its histogram kernel clears them)
     if (!cf) CK(launch_zero_status(L, U(W.status), nkeys, W.status_words));
     g_prof.mark("unit_scan");
-    CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0));
+    CK(launch_expand(L, 1, B.wide, dprog, HP, nullptr, U(W.unit_off), keysA, nullptr, P, cnt, nullptr, nullptr, 0,
+                     wtab, cbuf, ccap));
     g_prof.mark("expand_write");
+  }
+  if (compact) {
+    int cb = 0;  // cell codes stay below 2^cb
+    while (cb < 63 && (1ull << cb) < HP.ncells) cb++;
+    const int kbits = std::min(64, HP.PB + HP.IVB + cb);
+    const int shift0 = HP.AB + std::min(HP.TB, 5);
+    const int npass = std::max(1, (kbits - shift0 + 7) / 8);
+    CK(launch_tail_sort(L, cbuf, fin, cnt + C_NCOMPACT, ccap, shift0, npass, cnt + C_TAIL, cnt + C_NGC));
   }
   uint64_t* in = keysA;
   uint64_t* out = keysB;
@@ -534,7 +554,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   if (cf) {
     // digit histogram of the first pass over the kept keys, and their count
     CK(launch_cell_hist(L, keysA, nkeys, nsort, ctab, HP.ncells, HP.PB + HP.IVB, U(W.hist), HP.SB, cnt + C_NGC,
-                        U(W.status), W.status_words));
+                        U(W.status), W.status_words, compact ? cnt + C_TAIL : nullptr));
     nkeys = cnt + C_NGC;
     g_prof.mark("cell_filter");
   }
@@ -546,7 +566,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     CK(launch_onesweep(L, in, out, p == 0 ? nsorted : nkeys, nsort, HP.SB + 8 * p, U(W.hist) + p * 256,
                        U(W.status), cnt + C_TICKET0 + p, (uint32_t)(p + 1), cnt + C_ERR,
                        p + 1 < P ? U(W.hist) + (p + 1) * 256 : nullptr, HP.SB + 8 * (p + 1),
-                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB, p > 0 ? cnt + C_TAIL : nullptr, p));
+                       p == 0 ? ctab : nullptr, HP.ncells, HP.PB + HP.IVB,
+                       (p > 0 || compact) ? cnt + C_TAIL : nullptr, p));
     if (p == 0 && P > 1) CK(launch_tail_sort(L, out, fin, nkeys, nsort, HP.SB + 8, P - 1, cnt + C_TAIL));
     std::swap(in, out);
     static const char* pn[8] = {"sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3",

@@ -67,8 +67,10 @@ __device__ __forceinline__ bool cell_kept(const uint32_t* __restrict__ tab, uint
 enum { SEL_ALL = 0, SEL_KEPT = 1, SEL_KEPT_GLOBAL = 2 };
 
 // Modes 0 (count keys per unit + digit histograms of `npass` digits), 1 (write
-// keys at the unit offsets) and 2 (gather the instances of the minimal
-// witness's granule).  Warp = unit, grid-stride over units; mode 2 visits
+// keys at the unit offsets; with `cbuf`, keys of the cells the filter table
+// `ctab` keeps are also appended to cbuf[0, ccap), their count in
+// counters[C_NCOMPACT]) and 2 (gather the instances of the minimal witness's
+// granule).  Warp = unit, grid-stride over units; mode 2 visits
 // only the units of the blocks unit_off lists when counters[C_NPB] = 1 + their
 // count.  shist: npass x 256 words of shared memory (mode 0).
 template <typename T, int MODE, class X>
@@ -77,7 +79,9 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                                                   const uint64_t* __restrict__ unit_off, uint64_t* __restrict__ keys,
                                                   uint64_t* __restrict__ hist, int npass, uint64_t* __restrict__ counters,
                                                   const uint64_t* __restrict__ uniq, PairRec* __restrict__ pairs,
-                                                  uint64_t pair_cap, uint32_t only_in) {
+                                                  uint64_t pair_cap, uint32_t only_in,
+                                                  const uint32_t* __restrict__ ctab = nullptr,
+                                                  uint64_t* __restrict__ cbuf = nullptr, uint64_t ccap = 0) {
   constexpr int WPC = EXP_THREADS / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (MODE == 0) {
@@ -140,6 +144,12 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
                          const uint64_t key = make_key(P, A, a, idx, iv, b, lt, j);
                          if (MODE == 1) {
                            keys[cursor + (uint64_t)rank * G + j] = key;
+                           // with the cell filter's table complete, a key of a cell that
+                           // can race is also appended to the compact buffer (any order)
+                           if (cbuf && cell_kept(ctab, P->ncells, shr64(key, P->PB + P->IVB))) {
+                             const uint64_t g = atomicAdd((unsigned long long*)&counters[C_NCOMPACT], 1ull);
+                             if (g < ccap) cbuf[g] = key;
+                           }
                          } else if (keys) {  // count pass with the cell filter: `keys` is its table
                            cell_note(reinterpret_cast<uint32_t*>(keys), shr64(key, P->PB + P->IVB),
                                      (uint32_t)((uint64_t)b << P->TB | (uint64_t)lt), (P->wmask >> a) & 1u);

@@ -201,6 +201,7 @@ enum {
   C_NPB,      // pair search: 1 + blocks listed for it (0: search every unit)
   C_NGC = 33,  // cell filter: global keys kept for the sort (C_NG: all written ones)
   C_TAIL = 34,  // 1 when one CTA sorted the keys on the digits after the first pass
+  C_NCOMPACT = 35,  // cell filter: kept keys the write pass also appended to the compact buffer
   C_TICKET0 = 16,  // one tile ticket per sort pass (up to 16 passes)
   C_PAIRS = 64,    // racy access-pair matrices: 3 kinds x 32 rows x 32 bits, two rows per word
   C_SMALLQ = 120,  // one-CTA path of a small check: work queue, then an order word of zero

@@ -361,7 +361,8 @@ std::string jit_source(const DProg& P, bool split) {
   const char* sig =
       "(const __grid_constant__ DProg Pp, uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys_g, "
       "uint64_t* keys_s, uint64_t* hist, int npass, uint64_t* counters, uint64_t* stbl, uint64_t* sbase, "
-      "uint32_t only, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {\n"
+      "uint32_t only, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap, const uint32_t* ctab, uint64_t* cbuf, "
+      "uint64_t ccap) {\n"
       "  extern __shared__ __align__(16) unsigned char smem[];\n  GenX ex{&Pp};\n";
   // the pair search (2), and the count and write kernels of one pipeline:
   // block-local (3, 4) or plain (0, 1)
@@ -376,7 +377,7 @@ std::string jit_source(const DProg& P, bool split) {
              ") hgrd_jit_expand" + S(m) + sig;
       src += "  expand_units_body<T, " + S(m) +
              ">(&Pp, ex, reinterpret_cast<uint32_t*>(smem), unit_cnt, unit_off, keys_g, hist, npass, counters, "
-             "nullptr, nullptr, 0, only);\n}\n";
+             "nullptr, nullptr, 0, only" + std::string(m == 1 ? ", ctab, cbuf, ccap" : "") + ");\n}\n";
     }
   }
   for (int m : {3, 4}) {
@@ -548,7 +549,8 @@ bool jit_ready(const Bound& B, bool split) {
 cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const DProg& h_prog, uint64_t* unit_cnt,
                               const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s, uint64_t* hist, int npass,
                               uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only, bool split,
-                              const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {
+                              const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap, const uint32_t* ctab,
+                              uint64_t* cbuf, uint64_t ccap) {
   const JitModule* m = (const JitModule*)B.jit[split ? 1 : 0];
   const void* fn = (const void*)m->k[mode];
   size_t smem = 0;
@@ -567,7 +569,8 @@ cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const D
   if (grid < 1) grid = 1;
   void* args[] = {(void*)&h_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys_g, (void*)&keys_s,
                   (void*)&hist,   (void*)&npass,    (void*)&counters, (void*)&stbl,   (void*)&sbase,
-                  (void*)&only,   (void*)&uniq,     (void*)&pairs,    (void*)&pair_cap};
+                  (void*)&only,   (void*)&uniq,     (void*)&pairs,    (void*)&pair_cap,
+                  (void*)&ctab,   (void*)&cbuf,     (void*)&ccap};
   (*L.launches)++;
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
 }

@@ -26,6 +26,7 @@ bool jit_ready(const Bound& B, bool split);
 cudaError_t launch_jit_expand(const Launch& L, const Bound& B, int mode, const DProg& h_prog, uint64_t* unit_cnt,
                               const uint64_t* unit_off, uint64_t* keys_g, uint64_t* keys_s, uint64_t* hist, int npass,
                               uint64_t* counters, uint64_t* stbl, uint64_t* sbase, uint32_t only, bool split,
-                              const uint64_t* uniq = nullptr, PairRec* pairs = nullptr, uint64_t pair_cap = 0);
+                              const uint64_t* uniq = nullptr, PairRec* pairs = nullptr, uint64_t pair_cap = 0,
+                              const uint32_t* ctab = nullptr, uint64_t* cbuf = nullptr, uint64_t ccap = 0);
 
 }  // namespace hgrd

@@ -91,12 +91,14 @@ __global__ void __launch_bounds__(EXP_THREADS) expand_kernel(const DProg* __rest
                                                              uint64_t* __restrict__ keys, uint64_t* __restrict__ hist,
                                                              int npass, uint64_t* __restrict__ counters,
                                                              const uint64_t* __restrict__ uniq,
-                                                             PairRec* __restrict__ pairs, uint64_t pair_cap) {
+                                                             PairRec* __restrict__ pairs, uint64_t pair_cap,
+                                                             const uint32_t* __restrict__ ctab,
+                                                             uint64_t* __restrict__ cbuf, uint64_t ccap) {
   extern __shared__ __align__(16) unsigned char smem[];
   InterpX<T> ex;
   uint32_t* shist = reinterpret_cast<uint32_t*>(stage_program<T>(Pg, smem, &ex));
   expand_units_body<T, MODE>(ex.P, ex, shist, unit_cnt, unit_off, keys, hist, npass, counters, uniq, pairs, pair_cap,
-                             0xffffffffu);
+                             0xffffffffu, ctab, cbuf, ccap);
 }
 
 // ------------------------------------------------------------------ scan
@@ -251,7 +253,8 @@ __global__ void __launch_bounds__(256) cell_hist_kernel(const uint64_t* __restri
                                                         uint64_t n_max, const uint32_t* __restrict__ tab,
                                                         uint64_t ncells, int rsh, uint64_t* __restrict__ hist, int shift,
                                                         uint64_t* __restrict__ n_kept, uint64_t* __restrict__ status,
-                                                        uint64_t max_words) {
+                                                        uint64_t max_words, const uint64_t* skip) {
+  if (skip && *skip) return;  // the compact form sorted the kept keys already
   __shared__ uint32_t sh[256];
   sh[threadIdx.x] = 0;
   __syncthreads();
@@ -518,16 +521,22 @@ __global__ void __launch_bounds__(T, MINB) onesweep_kernel(const uint64_t* __res
 // would have, and sets *done so the device-wide passes after it return at
 // once.  With more keys it does nothing.
 constexpr int TAIL_T = 1024, TAIL_KPT = 4, TAIL_MAX = TAIL_T * TAIL_KPT;
+static_assert(TAIL_MAX == TAIL_KEYS, "the compact form's capacity");
 constexpr size_t tail_smem() { return (size_t)2 * TAIL_MAX * 8 + (size_t)(TAIL_T / 32) * RS_RADIX * 4 + RS_RADIX * 4; }
 __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
-                                                           uint64_t n_max, int shift0, int npass, uint64_t* done) {
+                                                           uint64_t n_max, int shift0, int npass, uint64_t* done,
+                                                           uint64_t* kept_out) {
   extern __shared__ __align__(16) unsigned char tsm[];
   uint64_t* A = reinterpret_cast<uint64_t*>(tsm);
   uint64_t* Bk = A + TAIL_MAX;
   uint32_t* whist = reinterpret_cast<uint32_t*>(Bk + TAIL_MAX);  // [32 warps][256]
   uint32_t* dbase = whist + (TAIL_T / 32) * RS_RADIX;             // digit starts
-  const uint64_t n = dev_n(n_dev, n_max);
-  if (n > (uint64_t)TAIL_MAX || npass <= 0) return;
+  // the compact form (kept_out given) sorts the write pass's compact buffer
+  // when every key it counted fits (n_max of them); the tail after the first
+  // pass finds nothing to do once the compact form has sorted the keys
+  if (!kept_out && *done) return;
+  const uint64_t n = kept_out ? *n_dev : dev_n(n_dev, n_max);
+  if ((kept_out && n > n_max) || n > (uint64_t)TAIL_MAX || npass <= 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) A[i] = in[i];
@@ -598,7 +607,10 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
     Bk = t;
   }
   for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) out[i] = A[i];
-  if (threadIdx.x == 0) *done = 1;
+  if (threadIdx.x == 0) {
+    if (kept_out) *kept_out = n;
+    *done = 1;
+  }
 }
 
 // Onesweep pass with early counts (the shapes the tuner prefers on B300).
@@ -1966,7 +1978,8 @@ int resident_ctas(const void* fn, int threads, size_t smem) {
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
                           uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys, uint64_t* hist, int npass,
-                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap) {
+                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap,
+                          const uint32_t* ctab, uint64_t* cbuf, uint64_t ccap) {
   const size_t esz = wide ? 8 : 4;
   const size_t smem = sizeof(DProg) + (size_t)(EXP_THREADS / 32) * h_prog.nslot * 32 * esz +
                       (mode == 0 ? (size_t)npass * 256 * 4 : 0);
@@ -1986,8 +1999,9 @@ cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_p
   int64_t grid = occupancy_grid(fn, EXP_THREADS, smem, L.nsm);
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  void* args[] = {(void*)&d_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys, (void*)&hist,
-                  (void*)&npass,  (void*)&counters, (void*)&uniq,     (void*)&pairs, (void*)&pair_cap};
+  void* args[] = {(void*)&d_prog, (void*)&unit_cnt, (void*)&unit_off, (void*)&keys,     (void*)&hist,
+                  (void*)&npass,  (void*)&counters, (void*)&uniq,     (void*)&pairs,    (void*)&pair_cap,
+                  (void*)&ctab,   (void*)&cbuf,     (void*)&ccap};
   (*L.launches)++;
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(EXP_THREADS), args, smem, L.s);
 }
@@ -2021,11 +2035,11 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
 
 cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
                              const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
-                             uint64_t* n_kept, uint64_t* status, uint64_t max_words) {
+                             uint64_t* n_kept, uint64_t* status, uint64_t max_words, const uint64_t* skip) {
   uint64_t blocks = (n_max + 255) / 256;
   unsigned grid = (unsigned)(blocks < (uint64_t)L.nsm * 8 ? (blocks ? blocks : 1) : (uint64_t)L.nsm * 8);
   cell_hist_kernel<<<grid, 256, 0, L.s>>>(keys, n_dev, n_max, tab, ncells, rsh, hist, shift, n_kept, status,
-                                          max_words);
+                                          max_words, skip);
   (*L.launches)++;
   return cudaGetLastError();
 }
@@ -2107,10 +2121,10 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
 }
 
 cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                             int shift0, int npass, uint64_t* done) {
+                             int shift0, int npass, uint64_t* done, uint64_t* kept_out) {
   cudaError_t e = allow_smem((const void*)tail_sort_kernel, tail_smem());
   if (e != cudaSuccess) return e;
-  tail_sort_kernel<<<1, TAIL_T, tail_smem(), L.s>>>(in, out, n_dev, n_max, shift0, npass, done);
+  tail_sort_kernel<<<1, TAIL_T, tail_smem(), L.s>>>(in, out, n_dev, n_max, shift0, npass, done, kept_out);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -30,9 +30,12 @@ struct Launch {
 
 // expansion: mode 0 = count keys per unit + digit histograms + out-of-bounds,
 // 1 = write keys, 2 = gather the instances of the minimal witness
+// (mode 1 with cbuf: keys of the cells the filter table ctab keeps are also
+// appended to cbuf[0, ccap), their count in counters[C_NCOMPACT])
 cudaError_t launch_expand(const Launch& L, int mode, bool wide, const DProg* d_prog, const DProg& h_prog,
                           uint64_t* unit_cnt, const uint64_t* unit_off, uint64_t* keys, uint64_t* hist, int npass,
-                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap);
+                          uint64_t* counters, const uint64_t* uniq, PairRec* pairs, uint64_t pair_cap,
+                          const uint32_t* ctab = nullptr, uint64_t* cbuf = nullptr, uint64_t ccap = 0);
 
 // exclusive scan of uint64 values; n = min(*n_dev, n_max) when n_dev is given
 cudaError_t launch_scan(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
@@ -45,10 +48,10 @@ cudaError_t launch_histogram(const Launch& L, const uint64_t* keys, const uint64
 // of the keys [0, *n_dev) whose cell (key >> rsh) the count pass found
 // written and touched by two threads, and their count (added to *n_kept);
 // it also clears the look-back status words the first sort pass over those
-// keys uses (at most max_words)
+// keys uses (at most max_words); nothing when *skip is set
 cudaError_t launch_cell_hist(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, uint64_t n_max,
                              const uint32_t* tab, uint64_t ncells, int rsh, uint64_t* hist, int shift,
-                             uint64_t* n_kept, uint64_t* status, uint64_t max_words);
+                             uint64_t* n_kept, uint64_t* status, uint64_t max_words, const uint64_t* skip = nullptr);
 // one stable onesweep pass on the digit at `shift`, given the pass's 256
 // digit counts (each CTA scans them into the digits' starts); when next_hist
 // is given, also counts the digit at `next_shift` for the following pass;
@@ -64,9 +67,12 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
 uint64_t sort_variant_key();
 // the passes after the first over the digits from shift0 (npass of them) in
 // one CTA when at most 4096 keys remain; sets *done then (the passes given
-// `skip` = done return at once)
+// `skip` = done return at once).  Compact form (kept_out given): the whole
+// sort of the write pass's compact buffer, when all *n_dev keys it counted
+// are there (at most n_max); writes their count to *kept_out and sets *done
+constexpr int TAIL_KEYS = 4096;
 cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                             int shift0, int npass, uint64_t* done);
+                             int shift0, int npass, uint64_t* done, uint64_t* kept_out = nullptr);
 
 // conflict scan, phase A: runs that may hold a race -> (start, end) list.
 // keys holds key_cap words (a multiple of 16 for the row form, which reads

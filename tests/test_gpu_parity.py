@@ -604,3 +604,23 @@ def test_sort_shapes_chosen_per_pass():
         for p in range(3):
             hg.sort_pass_variant(p, -1)
     assert hg.sort_pass_variant(0) == -1
+
+
+@pytest.mark.parametrize("pairs_of_writers", [100, 2047, 2048, 6000])
+def test_cell_filter_compact_form_and_fallback(pairs_of_writers):
+    # two threads write each element: with the cell filter every written key
+    # is kept; up to 4096 kept keys one CTA sorts them whole from the write
+    # pass's compact buffer, beyond that the filter and the sort passes run
+    n = 2 * pairs_of_writers
+    text = (f"kernel pairs\narray a global {4 * pairs_of_writers}\narray r global {4 * n}\n"
+            "access W a ; width 4 ; idx (bx*256 + tx)/2\n"
+            "access R r ; width 4 ; idx bx*256 + tx\n"
+            "access W a ; width 4 ; idx 0 ; if 0 - bx*256 - tx >= 0\n")
+    b = Binding(((n + 255) // 256, 1, 1), (256, 1, 1), ())
+    o = oracle.check(text, b, cap=1 << 20)
+    for flags in (hg.CELL_FILTER | hg.NO_SMALL, hg.CELL_FILTER | hg.NO_SMALL | hg.JIT):
+        g = hg.check(text, b, cap=1 << 20, flags=flags)
+        st = hg.stats()
+        assert st["cell_filter"] == 1
+        assert st["n_sorted_keys"] == n + 1  # every write of `a` (the lone write of a[0] included)
+        _same(g, o)
