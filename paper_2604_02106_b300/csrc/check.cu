@@ -494,8 +494,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   // compact form (cell filter, plain pipeline): the write pass, which runs
   // with the cell table complete, also appends the keys of kept cells to a
   // compact buffer (the raw-witness buffer, free until the exact scan); when
-  // they all fit (at most TAIL_KEYS), one CTA sorts them whole, on every key
-  // bit from the warp id up (the order the scans need), into the final
+  // they all fit (at most TAIL_KEYS), one CTA sorts them whole by the full
+  // key (the scans need a run's keys ordered by interval, block, warp
+  // interval and warp; the lanes of a warp in any order) into the final
   // buffer, and the filter's histogram, the sort passes and the tail return
   // at once.  Otherwise the filter and the passes run as below.
   const bool compact = cf && !split;
@@ -540,14 +541,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
                      wtab, cbuf, ccap));
     g_prof.mark("expand_write");
   }
-  if (compact) {
-    int cb = 0;  // cell codes stay below 2^cb
-    while (cb < 63 && (1ull << cb) < HP.ncells) cb++;
-    const int kbits = std::min(64, HP.PB + HP.IVB + cb);
-    const int shift0 = HP.AB + std::min(HP.TB, 5);
-    const int npass = std::max(1, (kbits - shift0 + 7) / 8);
-    CK(launch_tail_sort(L, cbuf, fin, cnt + C_NCOMPACT, ccap, shift0, npass, cnt + C_TAIL, cnt + C_NGC));
-  }
+  if (compact) CK(launch_compact_sort(L, cbuf, fin, cnt + C_NCOMPACT, ccap, cnt + C_TAIL, cnt + C_NGC));
   uint64_t* in = keysA;
   uint64_t* out = keysB;
   const uint64_t* nsorted = nkeys;  // keys the first pass reads

@@ -524,19 +524,15 @@ constexpr int TAIL_T = 1024, TAIL_KPT = 4, TAIL_MAX = TAIL_T * TAIL_KPT;
 static_assert(TAIL_MAX == TAIL_KEYS, "the compact form's capacity");
 constexpr size_t tail_smem() { return (size_t)2 * TAIL_MAX * 8 + (size_t)(TAIL_T / 32) * RS_RADIX * 4 + RS_RADIX * 4; }
 __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
-                                                           uint64_t n_max, int shift0, int npass, uint64_t* done,
-                                                           uint64_t* kept_out) {
+                                                           uint64_t n_max, int shift0, int npass, uint64_t* done) {
   extern __shared__ __align__(16) unsigned char tsm[];
   uint64_t* A = reinterpret_cast<uint64_t*>(tsm);
   uint64_t* Bk = A + TAIL_MAX;
   uint32_t* whist = reinterpret_cast<uint32_t*>(Bk + TAIL_MAX);  // [32 warps][256]
   uint32_t* dbase = whist + (TAIL_T / 32) * RS_RADIX;             // digit starts
-  // the compact form (kept_out given) sorts the write pass's compact buffer
-  // when every key it counted fits (n_max of them); the tail after the first
-  // pass finds nothing to do once the compact form has sorted the keys
-  if (!kept_out && *done) return;
-  const uint64_t n = kept_out ? *n_dev : dev_n(n_dev, n_max);
-  if ((kept_out && n > n_max) || n > (uint64_t)TAIL_MAX || npass <= 0) return;
+  if (*done) return;  // the compact form sorted the keys already
+  const uint64_t n = dev_n(n_dev, n_max);
+  if (n > (uint64_t)TAIL_MAX || npass <= 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) A[i] = in[i];
@@ -607,8 +603,40 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
     Bk = t;
   }
   for (uint32_t i = threadIdx.x; i < n; i += TAIL_T) out[i] = A[i];
-  if (threadIdx.x == 0) {
-    if (kept_out) *kept_out = n;
+  if (threadIdx.x == 0) *done = 1;
+}
+
+// The compact form's sort: the write pass's compact buffer of kept keys (any
+// order), when every key it counted is there (at most n_max), sorted whole
+// by one CTA in shared memory (a bitonic network on the full keys; keys
+// equal to the last bit are the same key, so the order is total) into the
+// final buffer; their count to *kept_out, and *done set.
+__global__ void __launch_bounds__(1024) compact_sort_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                            const uint64_t* n_dev, uint64_t n_max, uint64_t* done,
+                                                            uint64_t* kept_out) {
+  __shared__ uint64_t s[TAIL_MAX];
+  const uint64_t n64 = *n_dev;
+  if (n64 > n_max || n64 > (uint64_t)TAIL_MAX) return;
+  const uint32_t n = (uint32_t)n64, tid = threadIdx.x;
+  uint32_t m = 1;
+  while (m < n) m <<= 1;
+  for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? in[i] : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= m; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < m / 2; i += 1024) {
+        const uint32_t lo = 2 * i - (i & (j - 1)), hi = lo + j;  // the i-th pair of this step
+        const uint64_t a = s[lo], b = s[hi];
+        if ((a > b) == ((lo & k) == 0)) {
+          s[lo] = b;
+          s[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  for (uint32_t i = tid; i < n; i += 1024) out[i] = s[i];
+  if (tid == 0) {
+    *kept_out = n;
     *done = 1;
   }
 }
@@ -2121,10 +2149,17 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
 }
 
 cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                             int shift0, int npass, uint64_t* done, uint64_t* kept_out) {
+                             int shift0, int npass, uint64_t* done) {
   cudaError_t e = allow_smem((const void*)tail_sort_kernel, tail_smem());
   if (e != cudaSuccess) return e;
-  tail_sort_kernel<<<1, TAIL_T, tail_smem(), L.s>>>(in, out, n_dev, n_max, shift0, npass, done, kept_out);
+  tail_sort_kernel<<<1, TAIL_T, tail_smem(), L.s>>>(in, out, n_dev, n_max, shift0, npass, done);
+  (*L.launches)++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
+                                uint64_t n_max, uint64_t* done, uint64_t* kept_out) {
+  compact_sort_kernel<<<1, 1024, 0, L.s>>>(in, out, n_dev, n_max, done, kept_out);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -67,12 +67,15 @@ cudaError_t launch_onesweep(const Launch& L, const uint64_t* in, uint64_t* out, 
 uint64_t sort_variant_key();
 // the passes after the first over the digits from shift0 (npass of them) in
 // one CTA when at most 4096 keys remain; sets *done then (the passes given
-// `skip` = done return at once).  Compact form (kept_out given): the whole
-// sort of the write pass's compact buffer, when all *n_dev keys it counted
-// are there (at most n_max); writes their count to *kept_out and sets *done
+// `skip` = done return at once; so does this one when *done is set already)
 constexpr int TAIL_KEYS = 4096;
 cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev, uint64_t n_max,
-                             int shift0, int npass, uint64_t* done, uint64_t* kept_out = nullptr);
+                             int shift0, int npass, uint64_t* done);
+// compact form: the whole sort of the write pass's compact buffer by one CTA,
+// when all *n_dev keys it counted are there (at most n_max <= TAIL_KEYS);
+// writes their count to *kept_out and sets *done
+cudaError_t launch_compact_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
+                                uint64_t n_max, uint64_t* done, uint64_t* kept_out);
 
 // conflict scan, phase A: runs that may hold a race -> (start, end) list.
 // keys holds key_cap words (a multiple of 16 for the row form, which reads
