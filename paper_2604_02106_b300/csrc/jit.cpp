@@ -253,6 +253,17 @@ std::string jit_source(const DProg& P, bool split) {
       c += ind + "  } else {\n";
       closing = true;
     }
+    if (no_idx && !closing) {
+      // a count-only access taken once: its live instances are counted by
+      // the lanes that hold them, no ballot
+      c += ind + "  if (inb) {\n";
+      c += ind + "    DAcc A = " + at + ";\n";
+      c += ind + "    A.G = " + S(A.G) + "; A.shared = " + S(A.shared) + "; A.arr = " + S(A.arr) + ";\n";
+      c += ind + "    step(" + S(a) + ", A, true, 0u, (int64_t)0, (int64_t)0, b, lt, " + icv + ", " + rep + ");\n";
+      c += ind + "  }\n";
+      c += ind + "}\n";
+      return c;
+    }
     c += ind + "  const unsigned bal = __ballot_sync(0xffffffffu, inb);\n";
     c += ind + "  if (bal) {\n";
     c += ind + "    int64_t iv = 0;\n";
