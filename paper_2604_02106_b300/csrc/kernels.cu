@@ -607,37 +607,39 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
 }
 
 // The compact form's sort: the write pass's compact buffer of kept keys (any
-// order), when every key it counted is there (at most n_max), sorted whole
-// by one CTA in shared memory (a bitonic network on the full keys; keys
-// equal to the last bit are the same key, so the order is total) into the
-// final buffer; their count to *kept_out, and *done set.
-__global__ void __launch_bounds__(1024) compact_sort_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                            const uint64_t* n_dev, uint64_t n_max, uint64_t* done,
-                                                            uint64_t* kept_out) {
+// order), when every key it counted is there (at most n_max), placed by rank
+// into the final buffer: key e goes to the number of keys below it plus the
+// number of equal keys before it in the buffer (equal keys are the same
+// key, so any order of them is the sorted one).  Every CTA stages the whole
+// buffer in shared memory and each warp ranks its keys against it, 32
+// comparisons a step, so a few thousand keys take a few microseconds across
+// the GPU rather than a barrier-bound network in one CTA.  Their count to
+// *kept_out, and *done set.
+constexpr int CR_T = 512, CR_W = CR_T / 32;
+__global__ void __launch_bounds__(CR_T) compact_sort_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                           const uint64_t* n_dev, uint64_t n_max, uint64_t* done,
+                                                           uint64_t* kept_out) {
   __shared__ uint64_t s[TAIL_MAX];
   const uint64_t n64 = *n_dev;
   if (n64 > n_max || n64 > (uint64_t)TAIL_MAX) return;
-  const uint32_t n = (uint32_t)n64, tid = threadIdx.x;
-  uint32_t m = 1;
-  while (m < n) m <<= 1;
-  for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? in[i] : ~0ull;
-  __syncthreads();
-  for (uint32_t k = 2; k <= m; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = tid; i < m / 2; i += 1024) {
-        const uint32_t lo = 2 * i - (i & (j - 1)), hi = lo + j;  // the i-th pair of this step
-        const uint64_t a = s[lo], b = s[hi];
-        if ((a > b) == ((lo & k) == 0)) {
-          s[lo] = b;
-          s[hi] = a;
-        }
-      }
-      __syncthreads();
-    }
-  for (uint32_t i = tid; i < n; i += 1024) out[i] = s[i];
-  if (tid == 0) {
+  const uint32_t n = (uint32_t)n64, lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     *kept_out = n;
     *done = 1;
+  }
+  if (blockIdx.x * CR_W >= n) return;  // no key for this CTA
+  for (uint32_t i = threadIdx.x; i < n; i += CR_T) s[i] = in[i];
+  __syncthreads();
+  for (uint32_t e = blockIdx.x * CR_W + (threadIdx.x >> 5); e < n; e += gridDim.x * CR_W) {
+    const uint64_t x = s[e];
+    uint32_t r = 0;
+#pragma unroll 4
+    for (uint32_t j = lane; j < n; j += 32) {
+      const uint64_t y = s[j];
+      r += (uint32_t)(y < x) + (uint32_t)((y == x) & (j < e));
+    }
+    r = __reduce_add_sync(FULL, r);
+    if (lane == 0) out[r] = x;
   }
 }
 
@@ -1839,8 +1841,69 @@ __global__ void zero_kernel(uint64_t* __restrict__ p, const uint64_t* n_dev, uin
     p[i] = 0;
 }
 
+// Bitonic network (ascending) over m <= 1024 * E keys held E to a thread,
+// thread t holding keys tE .. tE+E-1 (n real keys, the rest all ones):
+// partners in the same thread meet in registers, partners in the same warp
+// by shuffles, the rest through shared memory (stored E planes of 1024, so
+// a warp's accesses fall in distinct banks).  The sorted keys are left in
+// s[0, m) in order.
+template <int E>
+__device__ __forceinline__ void wsmall_bitonic(const uint64_t* __restrict__ raw, uint32_t n, uint32_t m, uint64_t* s) {
+  const uint32_t tid = threadIdx.x;
+  uint64_t v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const uint32_t i = tid * E + q;
+    v[q] = i < n ? raw[i] : ~0ull;
+  }
+  for (uint32_t k = 2; k <= m; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j < (uint32_t)E) {
+#pragma unroll
+        for (int jj = 1; jj < E; jj <<= 1) {
+          if ((uint32_t)jj != j) continue;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            if (q & jj) continue;
+            const bool up = ((tid * E + q) & k) == 0;
+            const uint64_t a = v[q], b = v[q + jj];
+            if ((a > b) == up) {
+              v[q] = b;
+              v[q + jj] = a;
+            }
+          }
+        }
+        continue;
+      }
+      if (j < 32u * E) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const uint64_t o = __shfl_xor_sync(FULL, v[q], (int)(j / E));
+          const uint32_t i = tid * E + q;
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[q] = keep_min ? (o < v[q] ? o : v[q]) : (o > v[q] ? o : v[q]);
+        }
+        continue;
+      }
+#pragma unroll
+      for (int q = 0; q < E; ++q) s[q * 1024 + tid] = v[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const uint32_t i = tid * E + q;
+        const uint64_t o = s[q * 1024 + (tid ^ (j / E))];
+        const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+        v[q] = keep_min ? (o < v[q] ? o : v[q]) : (o > v[q] ? o : v[q]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+  for (int q = 0; q < E; ++q)
+    if (tid * E + q < m) s[tid * E + q] = v[q];
+}
+
 // One CTA merges up to WSMALL_MAX raw witnesses: bitonic sort of the packed
-// words in shared memory (the kind mask sits in the lowest bits, so the words
+// words, one, two or four to a thread (the kind mask sits in the lowest bits, so the words
 // of one (space, array, granule, acc_lo, acc_hi) end up adjacent and in
 // canonical order), then one output word per group with the kinds OR-ed.
 __global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __restrict__ raw,
@@ -1855,43 +1918,12 @@ __global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __r
   uint32_t m = 1;
   while (m < n) m <<= 1;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (m <= 1024) {
-    // one element per thread: partners inside a warp meet by shuffles, the
-    // others through shared memory (bitonic network, ascending)
-    uint64_t v = tid < n ? raw[tid] : ~0ull;
-    for (uint32_t k = 2; k <= m; k <<= 1)
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        uint64_t o;
-        if (j < 32) {
-          o = __shfl_xor_sync(FULL, v, (int)j);
-        } else {
-          s[tid] = v;
-          __syncthreads();
-          o = s[tid ^ j];
-          __syncthreads();
-        }
-        const bool keep_min = ((tid & j) == 0) == ((tid & k) == 0);
-        v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
-      }
-    if (tid < m) s[tid] = v;
-  } else {
-    for (uint32_t i = tid; i < m; i += 1024) s[i] = i < n ? raw[i] : ~0ull;
-    __syncthreads();
-    for (uint32_t k = 2; k <= m; k <<= 1)
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = tid; i < m; i += 1024) {
-          const uint32_t x = i ^ j;
-          if (x > i) {
-            const uint64_t a = s[i], b = s[x];
-            if ((a > b) == ((i & k) == 0)) {
-              s[i] = b;
-              s[x] = a;
-            }
-          }
-        }
-        __syncthreads();
-      }
-  }
+  if (m <= 1024)
+    wsmall_bitonic<1>(raw, n, m, s);
+  else if (m <= 2048)
+    wsmall_bitonic<2>(raw, n, m, s);
+  else
+    wsmall_bitonic<4>(raw, n, m, s);
   __syncthreads();
   // group heads over contiguous chunks, a CTA-wide exclusive scan of their counts
   const uint32_t chunk = (n + 1023) / 1024;
@@ -2159,7 +2191,9 @@ cudaError_t launch_tail_sort(const Launch& L, const uint64_t* in, uint64_t* out,
 
 cudaError_t launch_compact_sort(const Launch& L, const uint64_t* in, uint64_t* out, const uint64_t* n_dev,
                                 uint64_t n_max, uint64_t* done, uint64_t* kept_out) {
-  compact_sort_kernel<<<1, 1024, 0, L.s>>>(in, out, n_dev, n_max, done, kept_out);
+  const uint64_t ctas = (n_max + CR_W - 1) / CR_W;
+  const unsigned grid = (unsigned)(ctas < (uint64_t)L.nsm ? (ctas ? ctas : 1) : (uint64_t)L.nsm);
+  compact_sort_kernel<<<grid, CR_T, 0, L.s>>>(in, out, n_dev, n_max, done, kept_out);
   (*L.launches)++;
   return cudaGetLastError();
 }

@@ -426,6 +426,22 @@ def test_small_check_falls_back_when_it_keeps_too_few_witnesses():
     _same(g, oracle.check(text, b, cap=1 << 20))
 
 
+@pytest.mark.parametrize("n_loc", [1, 31, 1000, 1024, 1025, 2000, 2048, 2049, 3500, 4096, 4097, 5000])
+def test_witness_merge_sizes(n_loc):
+    # n_loc locations, each written by two threads of one access: one raw
+    # witness per location.  Up to 1024, 2048 and 4096 raw witnesses the
+    # one-CTA merge holds one, two and four per thread; above, the
+    # device-wide merge runs.
+    text = (f"kernel wm\narray a global {4 * n_loc}\n"
+            f"access W a ; width 4 ; idx (bx*512 + tx) / 2 ; if bx*512 + tx < {2 * n_loc}\n")
+    b = Binding(((2 * n_loc + 511) // 512, 1, 1), (512, 1, 1), ())
+    g = hg.check(text, b, cap=1 << 20, flags=hg.NO_SMALL)
+    assert hg.stats()["n_raw_witness"] == n_loc
+    o = oracle.check(text, b, cap=1 << 20)
+    assert o.n_witness == n_loc
+    _same(g, o)
+
+
 # ---------------------------------------------------------------- warp barriers (Sec. 5.2)
 
 @pytest.mark.parametrize("seed", range(60))
