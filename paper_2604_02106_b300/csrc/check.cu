@@ -595,7 +595,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     CK(launch_witness_split(L, cnt, W.raw_cap));
     CK(enqueue_witness_big(L, W, ws, P));
   }
-  CK(launch_witness_small(L, U(W.raw), wout, cnt, W.raw_cap));
+  CK(launch_witness_small(L, U(W.raw), U(W.raw2), wout, cnt, W.raw_cap));
   g_prof.mark("witness_merge");
   if (pair && !(fl & HGRD_NO_PAIR)) {
     CK(enqueue_pair_search(L, d, o, W, ws, wout));

@@ -606,28 +606,18 @@ __global__ void __launch_bounds__(TAIL_T) tail_sort_kernel(const uint64_t* in, u
   if (threadIdx.x == 0) *done = 1;
 }
 
-// The compact form's sort: the write pass's compact buffer of kept keys (any
-// order), when every key it counted is there (at most n_max), placed by rank
-// into the final buffer: key e goes to the number of keys below it plus the
-// number of equal keys before it in the buffer (equal keys are the same
-// key, so any order of them is the sorted one).  Every CTA stages the whole
-// buffer in shared memory and each warp ranks its keys against it, 32
-// comparisons a step, so a few thousand keys take a few microseconds across
-// the GPU rather than a barrier-bound network in one CTA.  Their count to
-// *kept_out, and *done set.
+// Sort of at most TAIL_MAX keys by rank, across the GPU: key e goes to the
+// number of keys below it plus the number of equal keys before it in the
+// input (equal keys are the same word, so any order of them is the sorted
+// one).  Every CTA that has keys to place stages the whole input in shared
+// memory and each warp ranks its keys against it, 32 comparisons a step: a
+// few thousand keys take a few microseconds spread over the GPU rather than
+// a barrier-bound network in one CTA.
 constexpr int CR_T = 512, CR_W = CR_T / 32;
-__global__ void __launch_bounds__(CR_T) compact_sort_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                           const uint64_t* n_dev, uint64_t n_max, uint64_t* done,
-                                                           uint64_t* kept_out) {
-  __shared__ uint64_t s[TAIL_MAX];
-  const uint64_t n64 = *n_dev;
-  if (n64 > n_max || n64 > (uint64_t)TAIL_MAX) return;
-  const uint32_t n = (uint32_t)n64, lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *kept_out = n;
-    *done = 1;
-  }
+__device__ __forceinline__ void rank_place(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t n,
+                                           uint64_t* s) {
   if (blockIdx.x * CR_W >= n) return;  // no key for this CTA
+  const uint32_t lane = threadIdx.x & 31;
   for (uint32_t i = threadIdx.x; i < n; i += CR_T) s[i] = in[i];
   __syncthreads();
   for (uint32_t e = blockIdx.x * CR_W + (threadIdx.x >> 5); e < n; e += gridDim.x * CR_W) {
@@ -641,6 +631,22 @@ __global__ void __launch_bounds__(CR_T) compact_sort_kernel(const uint64_t* __re
     r = __reduce_add_sync(FULL, r);
     if (lane == 0) out[r] = x;
   }
+}
+
+// The compact form's sort: the write pass's compact buffer of kept keys (any
+// order), when every key it counted is there (at most n_max), placed by rank
+// into the final buffer; their count to *kept_out, and *done set.
+__global__ void __launch_bounds__(CR_T) compact_sort_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                           const uint64_t* n_dev, uint64_t n_max, uint64_t* done,
+                                                           uint64_t* kept_out) {
+  __shared__ uint64_t s[TAIL_MAX];
+  const uint64_t n64 = *n_dev;
+  if (n64 > n_max || n64 > (uint64_t)TAIL_MAX) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *kept_out = n64;
+    *done = 1;
+  }
+  rank_place(in, out, (uint32_t)n64, s);
 }
 
 // Onesweep pass with early counts (the shapes the tuner prefers on B300).
@@ -1841,72 +1847,22 @@ __global__ void zero_kernel(uint64_t* __restrict__ p, const uint64_t* n_dev, uin
     p[i] = 0;
 }
 
-// Bitonic network (ascending) over m <= 1024 * E keys held E to a thread,
-// thread t holding keys tE .. tE+E-1 (n real keys, the rest all ones):
-// partners in the same thread meet in registers, partners in the same warp
-// by shuffles, the rest through shared memory (stored E planes of 1024, so
-// a warp's accesses fall in distinct banks).  The sorted keys are left in
-// s[0, m) in order.
-template <int E>
-__device__ __forceinline__ void wsmall_bitonic(const uint64_t* __restrict__ raw, uint32_t n, uint32_t m, uint64_t* s) {
-  const uint32_t tid = threadIdx.x;
-  uint64_t v[E];
-#pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const uint32_t i = tid * E + q;
-    v[q] = i < n ? raw[i] : ~0ull;
-  }
-  for (uint32_t k = 2; k <= m; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      if (j < (uint32_t)E) {
-#pragma unroll
-        for (int jj = 1; jj < E; jj <<= 1) {
-          if ((uint32_t)jj != j) continue;
-#pragma unroll
-          for (int q = 0; q < E; ++q) {
-            if (q & jj) continue;
-            const bool up = ((tid * E + q) & k) == 0;
-            const uint64_t a = v[q], b = v[q + jj];
-            if ((a > b) == up) {
-              v[q] = b;
-              v[q + jj] = a;
-            }
-          }
-        }
-        continue;
-      }
-      if (j < 32u * E) {
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-          const uint64_t o = __shfl_xor_sync(FULL, v[q], (int)(j / E));
-          const uint32_t i = tid * E + q;
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          v[q] = keep_min ? (o < v[q] ? o : v[q]) : (o > v[q] ? o : v[q]);
-        }
-        continue;
-      }
-#pragma unroll
-      for (int q = 0; q < E; ++q) s[q * 1024 + tid] = v[q];
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const uint32_t i = tid * E + q;
-        const uint64_t o = s[q * 1024 + (tid ^ (j / E))];
-        const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-        v[q] = keep_min ? (o < v[q] ? o : v[q]) : (o > v[q] ? o : v[q]);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-  for (int q = 0; q < E; ++q)
-    if (tid * E + q < m) s[tid * E + q] = v[q];
+// Up to WSMALL_MAX raw witnesses are merged in two steps: the packed words
+// are sorted by rank across the GPU into a scratch buffer (the kind mask
+// sits in the lowest bits, so the words of one (space, array, granule,
+// acc_lo, acc_hi) end up adjacent and in canonical order), then one CTA
+// writes one output word per group with the kinds OR-ed.
+__global__ void __launch_bounds__(CR_T) witness_rank_kernel(const uint64_t* __restrict__ raw,
+                                                           uint64_t* __restrict__ sorted, const uint64_t* counters,
+                                                           uint64_t raw_cap) {
+  __shared__ uint64_t s[WSMALL_MAX];
+  uint64_t n64 = counters[C_NRAW];
+  if (n64 > raw_cap) n64 = raw_cap;
+  if (n64 == 0 || n64 > (uint64_t)WSMALL_MAX) return;
+  rank_place(raw, sorted, (uint32_t)n64, s);
 }
 
-// One CTA merges up to WSMALL_MAX raw witnesses: bitonic sort of the packed
-// words, one, two or four to a thread (the kind mask sits in the lowest bits, so the words
-// of one (space, array, granule, acc_lo, acc_hi) end up adjacent and in
-// canonical order), then one output word per group with the kinds OR-ed.
-__global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __restrict__ raw,
+__global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __restrict__ sorted,
                                                              uint64_t* __restrict__ uniq, uint64_t* counters,
                                                              uint64_t raw_cap) {
   __shared__ uint64_t s[WSMALL_MAX];
@@ -1915,15 +1871,8 @@ __global__ void __launch_bounds__(1024) witness_small_kernel(const uint64_t* __r
   if (n64 > raw_cap) n64 = raw_cap;
   if (n64 == 0 || n64 > (uint64_t)WSMALL_MAX) return;
   const uint32_t n = (uint32_t)n64;
-  uint32_t m = 1;
-  while (m < n) m <<= 1;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (m <= 1024)
-    wsmall_bitonic<1>(raw, n, m, s);
-  else if (m <= 2048)
-    wsmall_bitonic<2>(raw, n, m, s);
-  else
-    wsmall_bitonic<4>(raw, n, m, s);
+  for (uint32_t i = tid; i < n; i += 1024) s[i] = sorted[i];
   __syncthreads();
   // group heads over contiguous chunks, a CTA-wide exclusive scan of their counts
   const uint32_t chunk = (n + 1023) / 1024;
@@ -2325,10 +2274,13 @@ cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t r
   return cudaGetLastError();
 }
 
-cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
-                                 uint64_t raw_cap) {
-  witness_small_kernel<<<1, 1024, 0, L.s>>>(raw, uniq, counters, raw_cap);
-  (*L.launches)++;
+cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* sorted, uint64_t* uniq,
+                                 uint64_t* counters, uint64_t raw_cap) {
+  const unsigned ctas = (unsigned)((WSMALL_MAX + CR_W - 1) / CR_W);
+  witness_rank_kernel<<<ctas < (unsigned)L.nsm ? ctas : (unsigned)L.nsm, CR_T, 0, L.s>>>(raw, sorted, counters,
+                                                                                        raw_cap);
+  witness_small_kernel<<<1, 1024, 0, L.s>>>(sorted, uniq, counters, raw_cap);
+  (*L.launches) += 2;
   return cudaGetLastError();
 }
 

@@ -108,9 +108,9 @@ cudaError_t launch_kind_counts(const Launch& L, const uint64_t* uniq, uint64_t* 
 // (counters[C_NPB] = 1 + their count, or left 0 when every unit must be searched)
 cudaError_t launch_pair_blocks(const Launch& L, const uint64_t* keys, const uint64_t* n_dev, const DProg* d_prog,
                                const uint64_t* uniq, uint64_t* counters, uint64_t* blocks);
-// at most WSMALL_MAX raw witnesses are merged by one CTA: witness_split sets
-// counters[C_NRAWBIG] (0 in that case, else the count) for the device-wide
-// kernels; witness_small then merges the few from `raw` into `uniq`
+// at most WSMALL_MAX raw witnesses are merged by witness_small: witness_split
+// sets counters[C_NRAWBIG] (0 in that case, else the count) for the
+// device-wide kernels
 constexpr int WSMALL_MAX = 4096;
 cudaError_t launch_witness_split(const Launch& L, uint64_t* counters, uint64_t raw_cap);
 // the split kernel for a graph: (counters, raw_cap, conditional handle) opens
@@ -122,8 +122,11 @@ cudaError_t launch_witness_split_cond(const Launch& L, uint64_t* counters, uint6
                                       cudaGraphConditionalHandle h);
 // the onesweep CTA shape in use on the current device
 int sort_variant_current();
-cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* uniq, uint64_t* counters,
-                                 uint64_t raw_cap);
+// witness_small: the few raw words sorted by rank across the GPU into
+// `sorted` (room for min(n, WSMALL_MAX) words), then merged by one CTA into
+// `uniq`, which may be `raw`
+cudaError_t launch_witness_small(const Launch& L, const uint64_t* raw, uint64_t* sorted, uint64_t* uniq,
+                                 uint64_t* counters, uint64_t raw_cap);
 // zero the look-back status words of the tiles a sort of *n_dev keys uses
 // (at most max_words)
 cudaError_t launch_zero_status(const Launch& L, uint64_t* status, const uint64_t* n_dev, uint64_t max_words);
