@@ -129,8 +129,12 @@ std::string jit_source(const DProg& P, bool split) {
   src += "template <typename U> __device__ __forceinline__ U modq(U v, const Magic& g, U d) { return v - divq<U>(v, g) * d; }\n";
   // c0 + c * k >= 0 (c != 0) narrows [lo, hi]: k >= ceil(-c0 / c) for c > 0, k <= floor(c0 / -c) for c < 0
   src += "__device__ __forceinline__ int64_t fdiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }\n";
+  // (unit coefficients, the usual case, skip the 64-bit division: it runs per unit)
   src += "__device__ __forceinline__ void loop_guard_range(int64_t c0, int64_t c, int64_t& lo, int64_t& hi) {\n"
-         "  if (c > 0) lo = max(lo, -fdiv(c0, c)); else hi = min(hi, fdiv(c0, -c));\n}\n";
+         "  if (c == 1) lo = max(lo, -c0);\n"
+         "  else if (c == -1) hi = min(hi, c0);\n"
+         "  else if (c > 0) lo = max(lo, -fdiv(c0, c));\n"
+         "  else hi = min(hi, fdiv(c0, -c));\n}\n";
   src += "struct GenX {\n  const DProg* __restrict__ P;\n";
   src += "  template <int SEL, class Step>\n";
   src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
