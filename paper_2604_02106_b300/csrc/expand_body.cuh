@@ -101,7 +101,7 @@ __device__ __forceinline__ void expand_units_body(const DProg* __restrict__ P, X
   }
   const int64_t nunits = P->nunits;
   const int SB = P->SB;  // lowest sorted key bit
-  const uint32_t emask = P->emask;
+  const uint32_t emask = ex.emask_of(P);  // a constant in the specialised kernels
   uint64_t oob = 0, drop = 0;
   const uint32_t only = MODE == 2 ? ((1u << t_lo) | (1u << t_hi)) : only_in;
   if (MODE == 1 && blockIdx.x == 0 && threadIdx.x == 0) counters[C_NKEYS] = counters[C_NG] + counters[C_NDROP];
@@ -228,7 +228,7 @@ __device__ __forceinline__ void expand_block_body(const DProg* __restrict__ P, X
   const int64_t upb = (int64_t)P->wpb * P->nchunk;
   const int SB = P->SB;  // lowest sorted key bit
   const uint32_t wmask = P->wmask;
-  const uint32_t emask = P->emask;
+  const uint32_t emask = ex.emask_of(P);  // a constant in the specialised kernels
   uint64_t oob = 0, drop = 0;
   if (MODE == 3) {
     for (int i = threadIdx.x; i < NB; i += EXP_THREADS) {

@@ -136,6 +136,8 @@ std::string jit_source(const DProg& P, bool split) {
          "  else if (c > 0) lo = max(lo, -fdiv(c0, c));\n"
          "  else hi = min(hi, fdiv(c0, -c));\n}\n";
   src += "struct GenX {\n  const DProg* __restrict__ P;\n";
+  // the accesses whose keys are written, as the source was generated for
+  src += "  __device__ __forceinline__ uint32_t emask_of(const DProg*) const { return " + S(P.emask) + "u; }\n";
   src += "  template <int SEL, class Step>\n";
   src += "  __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {\n";
   src += "    return walk<SEL, false, false>(lane, u, only, step, [](int, uint32_t, uint32_t, int) {});\n  }\n";

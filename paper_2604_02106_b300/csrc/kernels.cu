@@ -49,6 +49,7 @@ template <typename T>
 struct InterpX {
   const DProg* P;
   T* sl;
+  __device__ __forceinline__ uint32_t emask_of(const DProg* Q) const { return Q->emask; }
   template <int SEL, class Step>
   __device__ __forceinline__ uint64_t unit(int lane, int64_t u, uint32_t only, Step&& step) {
     if (SEL != SEL_ALL) only &= P->emask;
