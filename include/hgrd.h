@@ -133,9 +133,11 @@ typedef struct {
                                HGRD_GRAPH: run the check as one CUDA graph launch, the graph
                                captured by the first such check of this binding with this
                                workspace, these options and this device, and replayed by the
-                               later ones (same result; the program is re-uploaded by every
-                               replay from a pinned copy taken at capture; ignored with
-                               HGRD_PROFILE; a rebind makes a new binding);
+                               later ones (same result; the graph's kernels read the program
+                               from the graph's own device copy, filled from a pinned copy
+                               taken at capture: once by hgrd_check_enqueue, before every
+                               replay by hgrd_check; ignored with HGRD_PROFILE; a rebind
+                               makes a new binding);
                                HGRD_ALL_KEYS: write and sort the keys of every live access,
                                also of those the pair rule shows can race with nothing, in one
                                global sort on the interpreted kernels (implies HGRD_NO_SPLIT,

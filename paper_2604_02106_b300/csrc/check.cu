@@ -291,7 +291,7 @@ uint64_t* uniq_buffer(const hgrd_desc* d, const Layout& W, char* ws) {
 // follow the witness merge in the same stream or graph; with no witness its
 // kernels find nothing to do.
 cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_check_opts* o, const Layout& W,
-                                char* ws, const uint64_t* duniq) {
+                                char* ws, const uint64_t* duniq, const DProg* dprog) {
   const Bound& B = *d->bound;
   const DProg& HP = B.prog;
   cudaStream_t s = L.s;
@@ -311,7 +311,7 @@ cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_
   if (!small) {
     const uint64_t* sorted = (uint64_t*)(ws + ((passes & 1) ? W.keysB : W.keysA));
     const uint64_t* nsorted = (const uint64_t*)(ws + W.counters) + (filter_runs(W, passes) ? C_NGC : C_NG);
-    if ((e = launch_pair_blocks(L, sorted, nsorted, (const DProg*)(ws + W.prog), duniq,
+    if ((e = launch_pair_blocks(L, sorted, nsorted, dprog, duniq,
                                 (uint64_t*)(ws + W.counters), blist)) != cudaSuccess)
       return e;
   }
@@ -320,18 +320,35 @@ cudaError_t enqueue_pair_search(const Launch& L, const hgrd_desc* d, const hgrd_
   if ((jsplit || jplain) && !(fl & HGRD_NO_JIT))
     return launch_jit_expand(L, B, 2, HP, nullptr, blist, nullptr, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
                              nullptr, nullptr, 0xffffffffu, jsplit, duniq, pr, W.pair_cap);
-  return launch_expand(L, 2, B.wide, (const DProg*)(ws + W.prog), HP, nullptr, blist, nullptr, nullptr, 0,
-                       (uint64_t*)(ws + W.counters), duniq, pr, W.pair_cap);
+  return launch_expand(L, 2, B.wide, dprog, HP, nullptr, blist, nullptr, nullptr, 0, (uint64_t*)(ws + W.counters),
+                       duniq, pr, W.pair_cap);
 }
 
 // An enqueue being captured into a check graph (HGRD_GRAPH): the graph, a
-// pinned copy of the program the upload node reads, and a stream for
-// capturing the conditional witness-merge body.
+// pinned copy of the program, the device copy the graph's kernels read (owned
+// by the graph, filled from the pinned copy outside the graph), and a stream
+// for capturing the conditional witness-merge body.
 struct Capture {
   cudaGraph_t graph;
   DProg* pinned_prog;
+  DProg* dev_prog;
   cudaStream_t body_stream;
 };
+
+// The device program the last check enqueued on a workspace ran with (its
+// slot in the workspace, or a check graph's own copy): a later pair search
+// from collect reads the same one.
+std::mutex g_wsprog_mu;
+std::map<const void*, const DProg*> g_wsprog;
+void note_ws_prog(const void* ws, const DProg* p) {
+  std::lock_guard<std::mutex> lk(g_wsprog_mu);
+  g_wsprog[ws] = p;
+}
+const DProg* ws_prog(const void* ws, const DProg* dflt) {
+  std::lock_guard<std::mutex> lk(g_wsprog_mu);
+  auto it = g_wsprog.find(ws);
+  return it == g_wsprog.end() ? dflt : it->second;
+}
 
 // The conditional witness merge inside a stream capture on s: the split
 // kernel, then an IF node (appended to the capture's dependencies) whose body
@@ -382,8 +399,9 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   char* ws = (char*)d_ws;
   auto U = [&](size_t off) { return (uint64_t*)(ws + off); };
   uint64_t* cnt = U(W.counters);
-  // the compiled program: uploaded into the workspace, or already resident
-  const DProg* dprog = dprog_resident ? dprog_resident : (const DProg*)(ws + W.prog);
+  // the compiled program: uploaded into the workspace, already resident, or
+  // (in a check graph) the graph's own device copy
+  const DProg* dprog = dprog_resident ? dprog_resident : cc ? cc->dev_prog : (const DProg*)(ws + W.prog);
   // a check restricted to a subset of the accesses runs a copy of the
   // program with the other accesses removed (their keys are never made)
   const uint32_t only = o ? o->only_accesses : 0u;
@@ -440,13 +458,14 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
       if (split) run_prog.scap = W.scap;
       hprog = &run_prog;
     }
-    if (cc) {  // a graph's upload node reads a pinned copy that lives as long as the graph
+    if (cc) {  // the graph's device copy is filled from this pinned one, outside the graph
       memcpy(cc->pinned_prog, hprog, sizeof(DProg));
-      hprog = cc->pinned_prog;
+    } else {
+      CK(cudaMemcpyAsync(ws + W.prog, hprog, sizeof(DProg), cudaMemcpyHostToDevice, s));
+      g_stats.h2d_bytes += sizeof(DProg);
     }
-    CK(cudaMemcpyAsync(ws + W.prog, hprog, sizeof(DProg), cudaMemcpyHostToDevice, s));
-    g_stats.h2d_bytes += sizeof(DProg);
   }
+  if (!cc && !noalloc) note_ws_prog(ws, dprog);  // (the no-allocation check runs no later pair search)
   g_prof.mark("setup");
   // a small check runs whole in one CTA (the batched form's on-chip kernel),
   // unless specialised kernels were asked for; its verdict lands in the
@@ -458,7 +477,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     g_stats.shared_bins = 0;
     g_stats.jit = 0;
     g_stats.sort_passes = 0;
-    if (pair && !(fl & HGRD_NO_PAIR)) CK(enqueue_pair_search(L, d, o, W, ws, uniq_buffer(d, W, ws)));
+    if (pair && !(fl & HGRD_NO_PAIR)) CK(enqueue_pair_search(L, d, o, W, ws, uniq_buffer(d, W, ws), dprog));
     return HGRD_OK;
   }
 
@@ -598,7 +617,7 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
   CK(launch_witness_small(L, U(W.raw), U(W.raw2), wout, cnt, W.raw_cap));
   g_prof.mark("witness_merge");
   if (pair && !(fl & HGRD_NO_PAIR)) {
-    CK(enqueue_pair_search(L, d, o, W, ws, wout));
+    CK(enqueue_pair_search(L, d, o, W, ws, wout, dprog));
     g_prof.mark("pair_search");
   }
   return HGRD_OK;
@@ -610,7 +629,8 @@ int enqueue(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
 // that, checks run uncaptured.
 struct CheckGraph {
   cudaGraphExec_t exec = nullptr;
-  DProg* pinned = nullptr;  // the program the graph's upload node copies
+  DProg* pinned = nullptr;  // the program, pinned host copy
+  DProg* dprog = nullptr;   // its device copy, which the graph's kernels read
   hgrd_stats stats{};       // what the captured enqueue reported
 };
 std::mutex g_cg_mu;
@@ -639,28 +659,40 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
                                      (uint64_t)ws_bytes,    oo.max_raw_witness, oo.pair_cap,
                                      oo.flags,              oo.only_accesses, oo.max_shared_keys,
                                      (uint64_t)jit,         sort_variant_key(), (uint64_t)pair};
+  // The graph's kernels read the program from the graph's own device copy,
+  // which stays resident between replays.  The synchronous check (`pair`)
+  // copies it in from the pinned host copy before every replay, as one
+  // self-contained check whose inputs cross the bus each call; the enqueue
+  // path copies it once, when the graph is made.
+  auto launch = [&](const CheckGraph& e, bool upload) -> int {
+    g_stats = e.stats;
+    if (upload) {
+      CK(cudaMemcpyAsync(e.dprog, e.pinned, sizeof(DProg), cudaMemcpyHostToDevice, s));
+      g_stats.h2d_bytes += sizeof(DProg);
+    }
+    note_ws_prog(d_ws, e.dprog);
+    CK(cudaGraphLaunch(e.exec, s));
+    return HGRD_OK;
+  };
   {
     std::lock_guard<std::mutex> lk(g_cg_mu);
     auto it = g_cg.find(key);
-    if (it != g_cg.end()) {
-      g_stats = it->second.stats;
-      CK(cudaGraphLaunch(it->second.exec, s));
-      return HGRD_OK;
-    }
+    if (it != g_cg.end()) return launch(it->second, pair);
     if (g_cg.size() >= CG_MAX) return enqueue(d, &oo, d_ws, ws_bytes, s, nullptr, nullptr, pair);
   }
   CheckGraph e;
   cudaStream_t cs = nullptr, bs = nullptr;
   cudaGraph_t g = nullptr;
-  note_created(4);  // pinned program copy, two capture streams, the instantiated graph
+  note_created(5);  // pinned and device program copies, two capture streams, the instantiated graph
   bool ok = cudaHostAlloc((void**)&e.pinned, sizeof(DProg), cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&e.dprog, sizeof(DProg)) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaGraphCreate(&g, 0) == cudaSuccess;
   ok = ok && cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   int erc = HGRD_OK;
   if (ok) {
-    const Capture cc{g, e.pinned, bs};
+    const Capture cc{g, e.pinned, e.dprog, bs};
     erc = enqueue(d, &oo, d_ws, ws_bytes, cs, nullptr, &cc, pair);
     cudaGraph_t out = nullptr;
     ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && erc == HGRD_OK;
@@ -675,15 +707,14 @@ int enqueue_graph(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size
   if (!ok) {
     if (e.exec) cudaGraphExecDestroy(e.exec);
     if (e.pinned) cudaFreeHost(e.pinned);
+    if (e.dprog) cudaFree(e.dprog);
     cudaGetLastError();  // a failed capture leaves no sticky error behind
     if (erc != HGRD_OK && erc != HGRD_EDEVICE) return erc;  // a real refusal of these options
     return enqueue(d, &oo, d_ws, ws_bytes, s, nullptr, nullptr, pair);  // no graph: the same check, launched directly
   }
   std::lock_guard<std::mutex> lk(g_cg_mu);
   auto it = g_cg.emplace(key, e).first;
-  g_stats = it->second.stats;
-  CK(cudaGraphLaunch(it->second.exec, s));
-  return HGRD_OK;
+  return launch(it->second, true);
 }
 
 // the public enqueue: captured / replayed as a graph on request; `pair`
@@ -844,7 +875,7 @@ int collect(const hgrd_desc* d, const hgrd_check_opts* o, void* d_ws, size_t ws_
     PairRec* pr = (PairRec*)(ws + W.pairs);
     if (!pair_enqueued) {
       Launch L{s, nsm_of_current_device(), &g_stats.kernel_launches};
-      CK(enqueue_pair_search(L, d, o, W, ws, duniq));
+      CK(enqueue_pair_search(L, d, o, W, ws, duniq, ws_prog(ws, (const DProg*)(ws + W.prog))));
     }
     // the record count and a prefix of the records in one round trip (made
     // already, with the counters, when the search ran in the enqueue)

@@ -1,7 +1,8 @@
 """Checks replayed as one CUDA graph (HGRD_GRAPH) against the direct launch
 and the oracle: the first check of a binding captures the graph, the later
-ones replay it (program upload, counter clearing, expansion, sort, scans and
-the conditional witness merge all inside the graph)."""
+ones replay it (counter clearing, expansion, sort, scans and the conditional
+witness merge all inside the graph; the program in the graph's own device
+copy)."""
 import pytest
 
 import oracle
@@ -39,7 +40,7 @@ def test_graph_replays_match_direct_launch(name, flags):
 
 
 def test_graph_survives_other_checks_in_the_same_workspace():
-    # the replay uploads its program and clears its counters itself
+    # the replay reads its own device program and clears its counters itself
     a = _bind(workloads.config2(0, planted=True, W=128, H=128, K=4))
     b = _bind(workloads.random_shared(5011))
     need = max(a.workspace_size(), b.workspace_size())
@@ -50,6 +51,30 @@ def test_graph_survives_other_checks_in_the_same_workspace():
     assert a.check(cap=1 << 20, workspace=buf, flags=hg.GRAPH) == ra
     assert b.check(cap=1 << 20, workspace=buf, flags=hg.GRAPH) == rb
     assert a.check(cap=1 << 20, workspace=buf, flags=hg.GRAPH) == ra
+
+
+def test_graph_enqueue_keeps_its_program_between_other_checks():
+    # enqueued replays read the graph's own device program (copied in once):
+    # another binding's checks in the same workspace between them change
+    # nothing (collect reports no instance pair; hgrd_check does)
+    import torch
+    wa = workloads.config2(0, planted=True, W=128, H=128, K=4)
+    wb = workloads.random_shared(5011)
+    a, b = _bind(wa), _bind(wb)
+    buf = torch.empty(max(a.workspace_size(), b.workspace_size()), dtype=torch.uint8, device="cuda")
+    oa = oracle.check(wa.text, wa.binding, cap=1 << 20)
+    ob = oracle.check(wb.text, wb.binding, cap=1 << 20)
+    for _ in range(2):
+        a.enqueue(buf, flags=hg.GRAPH)
+        _same(a.collect(buf, cap=1 << 20, flags=hg.GRAPH), oa, pair=False)
+        b.enqueue(buf)  # direct launches: its program goes into the workspace
+        _same(b.collect(buf, cap=1 << 20), ob, pair=False)
+        b.enqueue(buf, flags=hg.GRAPH)
+        _same(b.collect(buf, cap=1 << 20, flags=hg.GRAPH), ob, pair=False)
+        a.enqueue(buf)
+        _same(a.collect(buf, cap=1 << 20), oa, pair=False)
+    _same(a.check(cap=1 << 20, workspace=buf, flags=hg.GRAPH), oa)
+    _same(b.check(cap=1 << 20, workspace=buf, flags=hg.GRAPH), ob)
 
 
 def test_graph_enqueue_collect_and_rebind():
